@@ -1,0 +1,248 @@
+"""FP64 CPU oracle for the linear lattice-Boltzmann acoustic scheme.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import this package.  The
+product library never imports, links or runs it, and it shares no code with
+the CUDA path: the stepper is plain C in ``lbref.c`` (FP64, push streaming),
+built here with gcc and loaded through ctypes.
+
+What each C routine computes, and the passage of arXiv:1704.03172 it follows,
+is stated at the top of ``lbref.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["lbref.c", "lbrefine.c", "lbadjoint.c"]
+_SO = os.path.join(_HERE, "liblbref.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, no fast-math, no FMA contraction)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "lbref.h")])
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-Wall", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = ctypes.CDLL(_SO)
+            _declare(_lib)
+        return _lib
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("Q", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("periodic", ctypes.c_int), ("mrt", ctypes.c_int),
+        ("tau", ctypes.c_double), ("s", ctypes.c_double * 9), ("w_ref", ctypes.c_double * 3),
+        ("c_map", ctypes.POINTER(ctypes.c_float)), ("c_ref", ctypes.c_double),
+        ("sponge_width", ctypes.c_int), ("sponge_sigma_max", ctypes.c_double),
+        ("src_x", ctypes.c_int), ("src_y", ctypes.c_int),
+        ("src", ctypes.POINTER(ctypes.c_double)), ("nt_src", ctypes.c_int),
+        ("rec_xy", ctypes.POINTER(ctypes.c_int)), ("nrec", ctypes.c_int),
+        ("nthreads", ctypes.c_int),
+    ]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_pp = ctypes.POINTER(_Problem)
+
+
+def _declare(L):
+    L.orc_velocities.argtypes = [ctypes.c_int, _ip]
+    L.orc_moment_matrix.argtypes = [ctypes.c_int, _dp]
+    L.orc_moment_inverse.argtypes = [ctypes.c_int, _dp]
+    L.orc_weights.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
+    L.orc_equilibrium.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, _dp]
+    L.orc_equilibrium.restype = None
+    L.orc_collide.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp,
+                              ctypes.c_double, _dp, _dp]
+    L.orc_sponge_sigma.argtypes = [ctypes.c_int] * 5 + [ctypes.c_double]
+    L.orc_sponge_sigma.restype = ctypes.c_double
+    L.orc_init_pressure.argtypes = [_pp, _dp, _dp]
+    L.orc_pressure.argtypes = [_pp, _dp, _dp]
+    L.orc_run.argtypes = [_pp, _dp, ctypes.c_int, ctypes.c_int, _dp]
+    L.orc_max_threads.argtypes = []
+    for name in ("orc_velocities", "orc_moment_matrix", "orc_moment_inverse", "orc_weights",
+                 "orc_collide", "orc_init_pressure", "orc_pressure", "orc_run",
+                 "orc_max_threads"):
+        getattr(L, name).restype = ctypes.c_int
+    if hasattr(L, "orc_refined_run"):
+        _declare_refine(L)
+    if hasattr(L, "orc_adjoint"):
+        _declare_adjoint(L)
+
+
+def _declare_refine(L):  # filled in by the refinement oracle
+    pass
+
+
+def _declare_adjoint(L):  # filled in by the adjoint oracle
+    pass
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+class Problem:
+    """One LB problem as the oracle sees it (all fields FP64 except c_map).
+
+    Q: 5 or 9; nx, ny; periodic; mrt; tau (BGK); s: MRT rates, diagonal of S
+    in the moment order of App. A; w_ref: D2Q9 (w0, w1, w5) at eta = 1;
+    c_map: [ny, nx] float32 sound speed; c_ref; sponge_width, sponge_sigma_max;
+    source (x, y, wavelet[nt]) or None; receivers [nrec, 2] int (x, y).
+    """
+
+    def __init__(self, Q, nx, ny, c_map, c_ref=None, periodic=False, mrt=False, tau=0.5,
+                 s=None, w_ref=(4 / 9, 1 / 9, 1 / 36), sponge_width=0, sponge_sigma_max=0.0,
+                 source=None, receivers=None, nthreads=0):
+        self.Q, self.nx, self.ny = int(Q), int(nx), int(ny)
+        self.c_map = np.ascontiguousarray(c_map, dtype=np.float32).reshape(ny, nx)
+        self.c_ref = float(c_ref if c_ref is not None else self.c_map.max())
+        self.periodic, self.mrt, self.tau = bool(periodic), bool(mrt), float(tau)
+        s = list(s) if s is not None else [1.0] * self.Q
+        self.s = np.zeros(9)
+        self.s[: len(s)] = s
+        self.w_ref = np.asarray(w_ref, dtype=np.float64)
+        self.sponge_width, self.sponge_sigma_max = int(sponge_width), float(sponge_sigma_max)
+        self.source = None
+        if source is not None:
+            sx, sy, wav = source
+            self.source = (int(sx), int(sy), np.ascontiguousarray(wav, dtype=np.float64))
+        self.receivers = (np.ascontiguousarray(receivers, dtype=np.int32).reshape(-1, 2)
+                          if receivers is not None else np.zeros((0, 2), np.int32))
+        self.nthreads = int(nthreads)
+
+    def _struct(self):
+        P = _Problem()
+        P.Q, P.nx, P.ny = self.Q, self.nx, self.ny
+        P.periodic, P.mrt, P.tau = int(self.periodic), int(self.mrt), self.tau
+        for k in range(9):
+            P.s[k] = self.s[k]
+        for k in range(3):
+            P.w_ref[k] = self.w_ref[k]
+        P.c_map = _ptr(self.c_map, ctypes.c_float)
+        P.c_ref = self.c_ref
+        P.sponge_width, P.sponge_sigma_max = self.sponge_width, self.sponge_sigma_max
+        if self.source is not None:
+            P.src_x, P.src_y = self.source[0], self.source[1]
+            P.src = _ptr(self.source[2], ctypes.c_double)
+            P.nt_src = len(self.source[2])
+        P.rec_xy = _ptr(self.receivers, ctypes.c_int)
+        P.nrec = len(self.receivers)
+        P.nthreads = self.nthreads
+        return P
+
+    def zeros(self):
+        return np.zeros((self.Q, self.ny, self.nx), dtype=np.float64)
+
+
+def init_pressure(P: Problem, p0=None) -> np.ndarray:
+    """g = g^eq(rho = p0 / c_s^2, j = 0) at every site."""
+    g = P.zeros()
+    p = None if p0 is None else np.ascontiguousarray(p0, dtype=np.float64).reshape(P.ny, P.nx)
+    S = P._struct()
+    rc = lib().orc_init_pressure(ctypes.byref(S), _ptr(p, ctypes.c_double) if p is not None
+                                 else None, _ptr(g, ctypes.c_double))
+    assert rc == 0
+    return g
+
+
+def pressure(P: Problem, g: np.ndarray) -> np.ndarray:
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    p = np.zeros((P.ny, P.nx))
+    S = P._struct()
+    assert lib().orc_pressure(ctypes.byref(S), _ptr(g, ctypes.c_double),
+                              _ptr(p, ctypes.c_double)) == 0
+    return p
+
+
+def run(P: Problem, g: np.ndarray, nsteps: int, t0: int = 0):
+    """Advance g (pre-collision state at time t0) by nsteps; returns (g, trace).
+
+    trace[n, r] is the pressure at receiver r at time t0 + n (before that step).
+    """
+    g = np.ascontiguousarray(g, dtype=np.float64).copy()
+    trace = np.zeros((nsteps, len(P.receivers)))
+    S = P._struct()
+    rc = lib().orc_run(ctypes.byref(S), _ptr(g, ctypes.c_double), int(t0), int(nsteps),
+                       _ptr(trace, ctypes.c_double))
+    assert rc == 0, rc
+    return g, trace
+
+
+def velocities(Q: int) -> np.ndarray:
+    c = np.zeros(2 * Q, dtype=np.int32)
+    assert lib().orc_velocities(Q, _ptr(c, ctypes.c_int)) == 0
+    return c.reshape(Q, 2)
+
+
+def moment_matrix(Q: int) -> np.ndarray:
+    M = np.zeros(Q * Q)
+    assert lib().orc_moment_matrix(Q, _ptr(M, ctypes.c_double)) == 0
+    return M.reshape(Q, Q)
+
+
+def moment_inverse(Q: int) -> np.ndarray:
+    M = np.zeros(Q * Q)
+    assert lib().orc_moment_inverse(Q, _ptr(M, ctypes.c_double)) == 0
+    return M.reshape(Q, Q)
+
+
+def weights(Q: int, eta: float, w_ref=(4 / 9, 1 / 9, 1 / 36)):
+    w = np.zeros(Q)
+    wr = np.asarray(w_ref, dtype=np.float64)
+    cs2 = ctypes.c_double()
+    assert lib().orc_weights(Q, float(eta), _ptr(wr, ctypes.c_double), _ptr(w, ctypes.c_double),
+                             ctypes.byref(cs2)) == 0
+    return w, cs2.value
+
+
+def equilibrium(Q, w, cs2, rho, jx, jy):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    geq = np.zeros(Q)
+    lib().orc_equilibrium(Q, _ptr(w, ctypes.c_double), float(cs2), float(rho), float(jx),
+                          float(jy), _ptr(geq, ctypes.c_double))
+    return geq
+
+
+def collide(Q, mrt, tau, s, w, cs2, g):
+    s9 = np.zeros(9)
+    s9[: len(s)] = s
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros(Q)
+    assert lib().orc_collide(Q, int(mrt), float(tau), _ptr(s9, ctypes.c_double),
+                             _ptr(w, ctypes.c_double), float(cs2), _ptr(g, ctypes.c_double),
+                             _ptr(out, ctypes.c_double)) == 0
+    return out
+
+
+def sponge_sigma(x, y, nx, ny, W, smax):
+    return lib().orc_sponge_sigma(int(x), int(y), int(nx), int(ny), int(W), float(smax))
+
+
+def max_threads() -> int:
+    return lib().orc_max_threads()

@@ -1,0 +1,49 @@
+/*
+ * lbref.h -- interface of the FP64 CPU oracle for the linear LB acoustic
+ * scheme (arXiv:1704.03172).  TEST INFRASTRUCTURE: only the tests, the smoke
+ * check and the CPU-baseline leg of the benchmark use it.  It is independent
+ * of the CUDA library and of include/lbac.h.
+ *
+ * Arrays: populations g[Q][ny][nx] (x fastest), FP64, pre-collision state at
+ * the current time.  c_map[ny][nx] FP32 sound speeds (the same values the CUDA
+ * path receives).  rec_xy[nrec][2] = (x, y).  trace[nsteps][nrec].
+ */
+#ifndef LBREF_H
+#define LBREF_H
+#include <stddef.h>
+
+typedef struct {
+    int Q;                 /* 5 (D2Q5) or 9 (D2Q9) */
+    int nx, ny;
+    int periodic;          /* 1: periodic; 0: zero ghost outside the domain */
+    int mrt;               /* 0: BGK, 1: MRT */
+    double tau;            /* BGK relaxation time */
+    double s[9];           /* MRT rates: diagonal of S in moment order (App. A) */
+    double w_ref[3];       /* D2Q9 weights (w0, w1, w5) at eta = 1 */
+    const float *c_map;    /* [ny][nx] sound speed */
+    double c_ref;          /* eta = c / c_ref */
+    int sponge_width;      /* W; 0 = no sponge */
+    double sponge_sigma_max;
+    int src_x, src_y;
+    const double *src;     /* S^n for n < nt_src; NULL: no source */
+    int nt_src;
+    const int *rec_xy;     /* [nrec][2] */
+    int nrec;
+    int nthreads;          /* OpenMP threads, <= 0: runtime default */
+} orc_problem;
+
+int orc_velocities(int Q, int *c);
+int orc_moment_matrix(int Q, double *M);
+int orc_moment_inverse(int Q, double *Minv);
+int orc_weights(int Q, double eta, const double *w_ref, double *w, double *cs2);
+void orc_equilibrium(int Q, const double *w, double cs2, double rho, double jx, double jy,
+                     double *geq);
+int orc_collide(int Q, int mrt, double tau, const double *s, const double *w, double cs2,
+                const double *g, double *gs);
+double orc_sponge_sigma(int x, int y, int nx, int ny, int W, double smax);
+int orc_init_pressure(const orc_problem *P, const double *p0, double *g);
+int orc_pressure(const orc_problem *P, const double *g, double *p);
+int orc_run(const orc_problem *P, double *g, int t0, int nsteps, double *trace);
+int orc_max_threads(void);
+
+#endif

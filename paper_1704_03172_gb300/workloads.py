@@ -1,0 +1,144 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds input generators only: sound-speed maps, source wavelets,
+receiver layouts, initial pulses and relaxation-rate draws.  It contains none
+of the lattice-Boltzmann arithmetic, so both the CUDA path and the FP64 oracle
+can be fed from it without sharing any of the method's code.
+
+All randomness comes from ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+DEFAULT_SEED = 20240601
+
+
+def gaussian_pulse(nx, ny, cx, cy, width, amp):
+    """p0(x, y) = amp * exp(-r^2 / (2 width^2)) centred on node (cx, cy)."""
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    r2 = (x - cx) ** 2 + (y - cy) ** 2
+    return (amp * np.exp(-r2 / (2.0 * width * width))).astype(np.float64)
+
+
+def ricker(nt, fc, t0=0.0):
+    """Source wavelet of the paper's Eq. (source)/(tau), sampled at t = t0 + n.
+
+    S(t) = -(1 - 4 xi^2) exp(-2 xi^2),  xi = (2 pi fc / 3)(t - 3 / (2 fc)),
+    with fc the central frequency in cycles per time step.
+    """
+    t = t0 + np.arange(nt, dtype=np.float64)
+    xi = (2.0 * math.pi * fc / 3.0) * (t - 3.0 / (2.0 * fc))
+    return -(1.0 - 4.0 * xi * xi) * np.exp(-2.0 * xi * xi)
+
+
+def uniform_map(nx, ny, c=1.0):
+    return np.full((ny, nx), c, dtype=np.float32)
+
+
+def two_layer(nx, ny, c_top=1.0, c_bottom=2.0, split=None):
+    """Two-layer medium, contrast c_top : c_bottom at row ``split`` (default mid-depth)."""
+    split = ny // 2 if split is None else split
+    c = np.full((ny, nx), c_top, dtype=np.float32)
+    c[split:, :] = c_bottom
+    return c
+
+
+def random_medium(nx, ny, seed, c_lo=0.4, c_hi=1.0):
+    """Smooth-free random heterogeneous medium (each site independent)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(c_lo, c_hi, size=(ny, nx)).astype(np.float32)
+
+
+def block_model(nx, ny, bx0, by0, bw, bh, c_bg=1.0, c_block=1.0 / 3.0):
+    """Homogeneous background with a rectangular slow block (grid-refinement workload)."""
+    c = np.full((ny, nx), c_bg, dtype=np.float32)
+    c[by0:by0 + bh, bx0:bx0 + bw] = np.float32(c_block)
+    return c
+
+
+def layered_fault_model(nx, ny, seed, n_layers=20, c_lo=1500.0, c_hi=5500.0, n_faults=4,
+                        max_slope=0.1, dip_deg=(45.0, 85.0), throw=(20.0, 200.0)):
+    """Layered model with dipping interfaces and normal faults.
+
+    n_layers - 1 interface depths uniform in (0, ny), sorted; each interface has a
+    slope uniform in [-max_slope, max_slope]; layer speeds uniform in [c_lo, c_hi];
+    ``n_faults`` faults with x position uniform in (0, nx), dip angle uniform in
+    ``dip_deg`` and throw uniform in ``throw`` cells (hanging wall shifted down).
+    """
+    rng = np.random.default_rng(seed)
+    depths = np.sort(rng.uniform(0, ny, size=n_layers - 1))
+    slopes = rng.uniform(-max_slope, max_slope, size=n_layers - 1)
+    speeds = rng.uniform(c_lo, c_hi, size=n_layers)
+    fx = rng.uniform(0, nx, size=n_faults)
+    fdip = np.deg2rad(rng.uniform(dip_deg[0], dip_deg[1], size=n_faults))
+    fthrow = rng.uniform(throw[0], throw[1], size=n_faults)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    ye = y.copy()
+    for k in range(n_faults):
+        hanging = x > fx[k] + y / np.tan(fdip[k])
+        ye = np.where(hanging, ye - fthrow[k], ye)
+    layer = np.zeros((ny, nx), dtype=np.int64)
+    for k in range(n_layers - 1):
+        layer += (ye > depths[k] + slopes[k] * (x - nx / 2.0)).astype(np.int64)
+    return speeds[layer].astype(np.float32)
+
+
+def line_receivers(n, y, x_start, x_span):
+    """n receivers on row y at x = x_start + floor(i * x_span / n)."""
+    i = np.arange(n, dtype=np.int64)
+    xs = x_start + (i * x_span) // n
+    return np.stack([xs, np.full(n, y)], axis=1).astype(np.int32)
+
+
+def ring_receivers(cx, cy, r, angles_deg):
+    pts = [(int(round(cx + r * math.cos(math.radians(a)))),
+            int(round(cy + r * math.sin(math.radians(a))))) for a in angles_deg]
+    return np.asarray(pts, dtype=np.int32)
+
+
+def mrt_rates(Q, seed, lo=0.5, hi=1.9):
+    """Relaxation rates drawn uniformly in (lo, hi), arranged on the diagonal of S.
+
+    D2Q5 S = diag(s_rho, s_v, s_v, s_e, s_p); D2Q9 S = diag(s_rho, s_v, s_v, s_e,
+    s_p, s_eps, s_q, s_q, s_p) (the structure given with Eq. MRT-LB basic).
+    """
+    rng = np.random.default_rng(seed)
+    if Q == 5:
+        s_rho, s_v, s_e, s_p = rng.uniform(lo, hi, size=4)
+        return [s_rho, s_v, s_v, s_e, s_p]
+    s_rho, s_v, s_e, s_p, s_eps, s_q = rng.uniform(lo, hi, size=6)
+    return [s_rho, s_v, s_v, s_e, s_p, s_eps, s_q, s_q, s_p]
+
+
+# --- the five workloads -------------------------------------------------------------
+
+# Two-layer workload: the source sits in the slow layer (c = 1, c_ref = 2, so
+# eta = 0.5 and the D2Q5 lattice sound speed is 0.5/sqrt(2) = 0.35355 cells/step).
+# A central wavelength of nx/30 cells therefore means fc = 0.35355 / (nx/30)
+# cycles per step; for nx = 4096 that is 1/386.2.
+TWO_LAYER_FC_4096 = 0.5 / math.sqrt(2.0) / (4096.0 / 30.0)
+
+
+def two_layer_workload(n=4096, lattice=5, collision="bgk", seed=DEFAULT_SEED + 2, nrec=512,
+                       sponge=40, sigma_max=0.1):
+    """The 4096^2 two-layer workload (scaled to n^2 when n differs).
+
+    Returns a dict of plain inputs: c_map, c_ref, source (x, y, wavelet), receivers,
+    tau / s, w_ref, sponge settings and the step count of the full run.
+    """
+    scale = n / 4096.0
+    c = two_layer(n, n, 1.0, 2.0)
+    fc = TWO_LAYER_FC_4096 / scale
+    nt = 5000
+    src = (n // 2, n // 4, ricker(nt, fc))
+    rec = line_receivers(nrec, n // 4, int(round(40 * scale)), n - 2 * int(round(40 * scale)))
+    d = dict(nx=n, ny=n, c_map=c, c_ref=2.0, source=src, receivers=rec, steps=nt,
+             lattice=lattice, collision=collision, tau=0.5, sponge_width=int(round(sponge * scale))
+             if sponge else 0, sponge_sigma_max=sigma_max, periodic=False,
+             w_ref=(0.0, 0.01, 0.24) if lattice == 9 else (4 / 9, 1 / 9, 1 / 36))
+    if collision == "mrt":
+        d["s"] = mrt_rates(lattice, seed)
+    return d
