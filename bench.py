@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused linear-LB step on GB300.
+
+Workload: the 4096^2 two-layer medium (contrast 1:2 at mid-depth), D2Q5 BGK
+tau = 1/2, FP32 populations, 40-cell sponge, Ricker point source, 512
+receivers (the paper's recommended scheme, Sec. 5.1).  One bench step is one
+LB time step of the whole grid (stream + collide + source + sponge + receiver
+gather, one fused launch).  Metric: GLUPS (1e9 lattice-site updates / s).
+
+--impl reference times the FP64 CPU oracle on this machine's host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1704_03172_gb300 import workloads as W  # noqa: E402
+
+METRIC = "GLUPS & % of HBM roofline (D2Q5 step, FP32 vs BF16); served shots/s, p50/p99"
+UNIT = "GLUPS"
+N_GRID = 4096
+FALLBACK_HBM_GBS = 6800.0
+BYTES_PER_SITE = {  # algorithmic HBM bytes per site update: read + write every population + eta^2
+    (5, "f32"): 2 * 5 * 4 + 4, (9, "f32"): 2 * 9 * 4 + 4,
+    (5, "bf16"): 2 * 5 * 2 + 4, (5, "f16"): 2 * 5 * 2 + 4,
+    (9, "bf16"): 2 * 9 * 2 + 4, (9, "f16"): 2 * 9 * 2 + 4,
+}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            if d.get("hbm_gbs"):
+                return float(d["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(lattice=5, storage="f32", collision="bgk"):
+    wl = W.two_layer_workload(N_GRID, lattice=lattice, collision=collision)
+    if lattice == 9 and collision == "mrt":
+        wl["s"] = [1.0, 1.0, 1.0, 2.0, 2.0, 2.0, 1.0, 1.0, 2.0]
+    wl["storage"] = storage
+    return wl
+
+
+def _make_sim(LBSim, wl, nt_cap):
+    sim = LBSim(wl["c_map"], lattice=wl["lattice"], collision=wl["collision"], tau=wl["tau"],
+                s=wl.get("s"), storage=wl["storage"], c_ref=wl["c_ref"],
+                sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"],
+                w_ref=wl["w_ref"])
+    sx, sy, wav = wl["source"]
+    sim.set_source(sx, sy, wav)
+    sim.set_receivers(wl["receivers"], nt_cap)
+    sim.init_pressure(None)
+    return sim
+
+
+def _time_steps(torch, sim, steps, warmup):
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    stream = sim.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def _variant(torch, LBSim, lattice, storage, collision, steps, warmup):
+    wl = _workload(lattice, storage, collision)
+    sim = _make_sim(LBSim, wl, steps + warmup)
+    try:
+        sec = _time_steps(torch, sim, steps, warmup)
+    finally:
+        sim.close()
+    sites = N_GRID * N_GRID
+    glups = sites * steps / sec / 1e9
+    bps = BYTES_PER_SITE[(lattice, storage)]
+    return {"glups": round(glups, 2), "bytes_per_site": bps,
+            "achieved_gbs": round(glups * bps, 1), "ms_per_step": round(sec / steps * 1e3, 4)}
+
+
+def _e2e(torch, LBSim, steps_shot):
+    """One full shot through the public API with host buffers (create .. traces .. destroy)."""
+    from paper_1704_03172_gb300.sim import LBSim as _S  # noqa: F401
+    wl = _workload()
+    c_host = np.ascontiguousarray(wl["c_map"], dtype=np.float32)
+    sx, sy, wav = wl["source"]
+    rec = wl["receivers"]
+    out = np.empty((steps_shot, len(rec)), dtype=np.float32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = LBSim(c_host, lattice=5, collision="bgk", tau=0.5, c_ref=wl["c_ref"],
+                sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"])
+    sim.set_source(sx, sy, wav)
+    sim.set_receivers(rec, steps_shot)
+    sim.init_pressure(None)
+    sim.step(steps_shot)
+    from paper_1704_03172_gb300 import lbac
+    import ctypes
+    n = lbac.lb_record_receivers(sim.ctx, ctypes.c_void_p(out.ctypes.data), steps_shot, 0)
+    sim.close()
+    sec = time.perf_counter() - t0
+    assert n == steps_shot
+    h2d = c_host.nbytes + len(wav) * 8 + rec.nbytes
+    return {"value": round(N_GRID * N_GRID * steps_shot / sec / 1e9, 2), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes),
+            "step": f"one {steps_shot}-step shot: lb_create(host c_map) .. lb_step .. "
+                    "lb_record_receivers(host) .. lb_destroy", "seconds": round(sec, 4)}
+
+
+def _cpu_sample(target_s=12.0, lattice=5):
+    """Time the FP64 oracle on a bounded sample of the workload (rows of the 4096^2 grid)."""
+    import oracle
+    oracle.build()
+    wl = _workload(lattice)
+    rows = 256
+    c = wl["c_map"][: rows]
+    P = oracle.Problem(lattice, N_GRID, rows, c, c_ref=wl["c_ref"], tau=wl["tau"],
+                       sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"],
+                       w_ref=wl["w_ref"])
+    g = P.zeros()
+    t0 = time.perf_counter()
+    oracle.run(P, g, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, int(target_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.run(P, g, steps)
+    sec = time.perf_counter() - t0
+    glups = N_GRID * rows * steps / sec / 1e9
+    return {"value": round(glups, 4), "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} steps of a {N_GRID}x{rows} band of the two-layer workload "
+                      f"(FP64 C, OpenMP over rows), {sec:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    wl = _workload()
+    rows = max(4, min(N_GRID, int(os.environ.get("LB_REF_ROWS", "64"))))
+    c = wl["c_map"][: rows]
+    P = oracle.Problem(5, N_GRID, rows, c, c_ref=wl["c_ref"], tau=wl["tau"],
+                       sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"])
+    g = P.zeros()
+    for _ in range(args.warmup):
+        g, _ = oracle.run(P, g, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g, _ = oracle.run(P, g, 1)
+    sec = time.perf_counter() - t0
+    glups = N_GRID * rows * args.steps / sec / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(glups, 5), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sec / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"two-layer {N_GRID}x{N_GRID} D2Q5 BGK tau=1/2, sponge 40, "
+                                   f"sampled as a {N_GRID}x{rows} band per step",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": round(glups, 5), "unit": UNIT, "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": f"one LB step of a {N_GRID}x{rows} band per bench step"},
+            "e2e": {"value": round(glups, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_1704_03172_gb300 import build
+    build.build()
+    from paper_1704_03172_gb300.sim import LBSim
+
+    wl = _workload()
+    sim = _make_sim(LBSim, wl, args.steps + args.warmup)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)            # let the sampler start before the timed region
+        t0 = time.perf_counter()
+        e0.record(sim.stream)
+        sim.step(args.steps)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if ws > 1:
+        dist.barrier()
+    sec = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        t = torch.tensor([sec], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    tr = sim.traces(args.steps + args.warmup)
+    finite = bool(torch.isfinite(tr).all().item())
+    sim.close()
+    sites = N_GRID * N_GRID
+    value = ws * sites * args.steps / sec / 1e9
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+    peak, peak_kind = _peaks()
+    bps = BYTES_PER_SITE[(5, "f32")]
+    per_launch_s = sec / args.steps
+    achieved = bps * sites / per_launch_s / 1e9
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(sec / args.steps * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"two-layer {N_GRID}x{N_GRID} (c 1:2 at mid-depth), D2Q5 BGK "
+                               "tau=1/2, FP32 populations, 40-cell sponge, Ricker source, "
+                               "512 receivers; one bench step = one LB time step",
+                   "parallelism": f"replicas x{ws} (independent shots)",
+                   "l2": "inputs larger than L2 (671 MB population state + 67 MB medium)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": None, "kernel": "lbk::step_kernel<5,false,false,float>",
+                     "algorithmic_bytes_per_launch": bps * sites},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "wall_s": round(wall, 4),
+        "finite": finite,
+    }
+    if not args.no_variants:
+        v = {}
+        for lat, st, coll in ((5, "f32", "mrt"), (9, "f32", "bgk"), (9, "f32", "mrt")):
+            try:
+                v[f"d2q{lat}_{coll}_{st}"] = _variant(torch, LBSim, lat, st, coll,
+                                                       max(200, args.steps // 5), 10)
+            except Exception as ex:  # report, do not hide
+                v[f"d2q{lat}_{coll}_{st}"] = {"error": str(ex)[:200]}
+        line["variants"] = v
+    if not args.no_e2e:
+        line["e2e"] = _e2e(torch, LBSim, args.e2e_steps)
+    if not args.no_cpu:
+        line["cpu_baseline"] = _cpu_sample(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=5000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,158 @@
+/*
+ * lbac.h -- C ABI of the GB300 (sm_103a) linear lattice-Boltzmann acoustic
+ * solver.  The method is the linear LB scheme of Dhuri, Hanasoge, Perlekar and
+ * Robertsson, arXiv:1704.03172 ("the paper"): Chopard's linear equilibrium
+ * (Eq. linear eqm dist), BGK (Eq. BGK-LB) or MRT (Eq. MRT-LB basic / Eq. MRT-LB)
+ * collision on the D2Q5 or D2Q9 lattice (Table I, App. A), a point source added
+ * as w_i S (Eq. MRT-LB linear acoustic), a spatially varying sound speed set
+ * through the rest-particle weight (Eq. 0th lattice weight), and the two-level
+ * grid refinement of Sec. 4 (Eq. grid refinement eqm dist, Eq. coarse-fine
+ * dist connect).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an lb_status; nothing throws or exits across the ABI.
+ *  - Lattice units: one cell per step.  Arrays are row-major [y][x], x fastest.
+ *    Population index i follows the rows of M in App. A: c_0 = (0,0),
+ *    c_1 = (1,0), c_2 = (0,1), c_3 = (-1,0), c_4 = (0,-1), and for D2Q9
+ *    c_5 = (1,1), c_6 = (-1,1), c_7 = (-1,-1), c_8 = (1,-1).
+ *  - "Time t" is the number of steps taken.  Step t collides the state at time
+ *    t, adds the source sample S[t] at the source site, applies the sponge and
+ *    streams, producing the state at time t+1.
+ *  - Input arrays are read (copied) during the call; the caller keeps
+ *    ownership.  Output buffers are caller-owned.  A pointer flagged
+ *    "on_device" must be a device pointer on the context's device.
+ *  - Work is queued asynchronously on the context's CUDA stream; a device-side
+ *    error surfaces as LB_ECUDA from the next call that synchronises
+ *    (lb_sync, lb_record_receivers, lb_get_pressure, lb_get_state, ...).
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - lb_last_error(ctx) returns a message for the last failing call on ctx
+ *    (or, with ctx == NULL, the last lb_create failure of this thread).
+ */
+#ifndef LBAC_H
+#define LBAC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = -1,     /* invalid argument or configuration */
+    LB_ENOMEM = -2,     /* device or host allocation failed */
+    LB_ECUDA = -3,      /* a CUDA call or kernel failed */
+    LB_EUNSTABLE = -4,  /* the state became non-finite */
+    LB_ETIMEOUT = -5,   /* a bounded device wait gave up */
+    LB_ESTATE = -6      /* call not valid in the context's current state */
+} lb_status;
+
+enum { LB_D2Q5 = 5, LB_D2Q9 = 9 };                 /* lattice (Table I) */
+enum { LB_BGK = 0, LB_MRT = 1 };                   /* collision operator */
+enum { LB_F32 = 0, LB_BF16 = 1, LB_F16 = 2 };      /* population storage in HBM */
+enum { LB_ZERO_GHOST = 0, LB_PERIODIC = 1 };       /* outer boundary */
+
+/* One refined patch (Sec. 4).  The fine grid covers the coarse rectangle of
+ * nodes [x0, x0 + nx_c] x [y0, y0 + ny_c] with (2 nx_c + 1) x (2 ny_c + 1) fine
+ * nodes; fine node (2a, 2b) coincides with coarse node (x0 + a, y0 + b).
+ * ratio must be 2 (the paper's n; "multiples of 2", Sec. 4). */
+typedef struct {
+    int x0, y0;
+    int nx_c, ny_c;
+    int ratio;
+} lb_patch;
+
+typedef struct {
+    int lattice;              /* LB_D2Q5 or LB_D2Q9 */
+    int collision;            /* LB_BGK or LB_MRT */
+    int storage;              /* LB_F32, LB_BF16 or LB_F16 (16-bit: per-population scale) */
+    int boundary;             /* LB_ZERO_GHOST or LB_PERIODIC */
+    int nx, ny;               /* grid size in nodes (coarse grid when refined) */
+    int sponge_width;         /* absorbing layer width W in cells, 0 = none */
+    double sponge_sigma_max;  /* sigma(d) = sigma_max ((W - d)/W)^2, d = distance to edge */
+    const float *c_map;       /* [ny][nx] sound speed (> 0), host unless c_map_on_device */
+    int c_map_on_device;
+    double c_ref;             /* eta = c / c_ref <= 1 (Eq. 0th lattice weight); <= 0: max(c_map) */
+    double dx;                /* metres per cell, informational (lb_info) */
+    double tau;               /* BGK relaxation time, tau >= 1/2 (Eq. BGK-LB) */
+    double s[9];              /* MRT: diagonal of S in the moment order of App. A, 0 < s <= 2 */
+    double w_ref[3];          /* D2Q9 weights (w0, w1, w5) at eta = 1; ignored for D2Q5 */
+    const lb_patch *patches;  /* refinement patches (at most 1), or NULL */
+    int n_patches;
+    void *cuda_stream;        /* cudaStream_t to run on; NULL: the context creates its own
+                                 non-blocking stream (pass cudaStreamLegacy for the legacy
+                                 default stream, whose handle is NULL) */
+    int time_block;           /* steps fused per launch (temporal blocking); <= 1: one */
+    /* Optional device allocator (e.g. PyTorch's caching allocator).  NULL: cudaMalloc. */
+    void *(*dev_alloc)(size_t bytes, void *user);
+    void (*dev_free)(void *ptr, void *user);
+    void *alloc_user;
+} lb_config;
+
+/* Fill *cfg with defaults: D2Q5, BGK tau = 1/2, F32, zero ghost, no sponge,
+ * conventional D2Q9 weights (4/9, 1/9, 1/36), c_ref = max(c_map). */
+lb_status lb_config_default(lb_config *cfg);
+
+/* Validate cfg, allocate the device state and build the per-site medium
+ * (eta^2 = (c / c_ref)^2, from which every weight and c_s^2 follow).
+ * Errors: LB_EINVAL (bad sizes, tau < 1/2, s outside (0, 2], eta > 1,
+ * c <= 0, negative weights, bad patch), LB_ENOMEM, LB_ECUDA.  *out is NULL on
+ * failure. */
+lb_status lb_create(const lb_config *cfg, lb_ctx **out);
+lb_status lb_destroy(lb_ctx *ctx);
+
+/* Point source at node (x, y) with samples S[n] for steps t = n (Eq. source
+ * gives the paper's wavelet; any samples are accepted).  Steps t >= nt add
+ * nothing.  The populations receive w_i(x, y) S[t] (Eq. MRT-LB linear
+ * acoustic).  nt = 0 removes the source.  Host pointer, FP64 samples. */
+lb_status lb_set_source(lb_ctx *ctx, int x, int y, const double *wavelet, int nt);
+
+/* Receivers at nodes xy[r] = (x, y).  Row n of the trace is the pressure
+ * p = c_s^2 rho (Eq. state) at time t0 + n, where t0 is the context time when
+ * this call is made; at most nt_capacity rows are kept.  Host pointer. */
+lb_status lb_set_receivers(lb_ctx *ctx, const int *xy, int nrec, int nt_capacity);
+
+/* Set the state to equilibrium with pressure p0 and zero velocity:
+ * g_i = (w_i / c_s^2) p0 (Eq. linear eqm dist with j = 0).  p0 == NULL sets
+ * every population to 0.  Resets the time to 0.  p0: [ny][nx] FP32. */
+lb_status lb_init_pressure(lb_ctx *ctx, const float *p0, int on_device);
+
+/* Advance n >= 0 steps (asynchronous). */
+lb_status lb_step(lb_ctx *ctx, int n);
+
+/* Copy trace rows [0, min(recorded, nt_max)) to out ([rows][nrec], FP32) and
+ * report the row count in *nt_out.  Synchronises the stream. */
+lb_status lb_record_receivers(lb_ctx *ctx, float *out, int nt_max, int *nt_out, int on_device);
+
+/* Pressure p = c_s^2 sum_i g_i at the current time, [ny][nx] FP32.
+ * With a refined patch, nodes inside the patch come from the fine grid. */
+lb_status lb_get_pressure(lb_ctx *ctx, float *out, int on_device);
+
+/* Populations g_i(x) at the current time (before its collision), as
+ * [Q][ny][nx] FP32.  lb_set_state is the inverse and resets nothing else. */
+lb_status lb_get_state(lb_ctx *ctx, float *out, int on_device);
+lb_status lb_set_state(lb_ctx *ctx, const float *in, int on_device);
+
+/* Current time (steps taken since lb_init_pressure / lb_create). */
+lb_status lb_get_time(const lb_ctx *ctx, long long *t);
+
+/* Wait for all queued work; LB_ECUDA if any of it failed. */
+lb_status lb_sync(lb_ctx *ctx);
+
+/* Device bytes lb_create would allocate for cfg, plus the receiver trace for
+ * nt steps when nrec > 0, plus adjoint checkpoints when want_adjoint. */
+lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint, size_t *bytes);
+
+/* Sizes and derived constants: info[0] = Q, info[1] = row pitch in elements,
+ * info[2] = bytes per stored population value, info[3] = physical time step
+ * dt = dx c_s(eta=1) / c_ref (seconds; 0 when dx or c_ref is 0). */
+lb_status lb_info(const lb_ctx *ctx, double *info, int n_info);
+
+const char *lb_last_error(const lb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBAC_H */

@@ -1,0 +1,446 @@
+// lb_kernels.cuh -- fused pull-stream / collide kernels for the linear LB
+// acoustic scheme (arXiv:1704.03172) on sm_103a.
+//
+// State layout (HBM): SoA populations h[Q][ny][pitch], pitch a multiple of 32
+// elements, storing the POST-collision populations of the previous step.  One
+// launch of step t
+//   1. pulls g_i(x, t) = h_i(x - c_i, t-1)                 (streaming, Eq. BGK-LB lhs)
+//   2. forms rho, j and the linear equilibrium               (Eq. linear eqm dist)
+//   3. collides (BGK, Eq. BGK-LB; or MRT, Eq. MRT-LB basic)
+//   4. adds w_i S[t] at the source node                      (Eq. MRT-LB linear acoustic)
+//   5. multiplies by (1 - sigma(x)) in the sponge            (Sec. 4, sponge layers)
+//   6. stores h_i(x, t) in place of the other buffer.
+// Receiver pressures p = c_s^2 rho at time t are gathered by trailing blocks
+// of the same launch, which pull from the (read-only) input buffer.
+// After lb_set_state / lb_init_pressure the buffer holds the state g(t)
+// itself, unshifted ("raw"), so that every population of an arbitrary initial
+// state survives at zero-ghost edges; the first launch then reads it in place.
+//
+// Each thread owns 4 consecutive x-sites of one row: aligned 16-byte (FP32)
+// or 8-byte (16-bit) vector loads/stores; the +-1 x-shift of the moving
+// populations is done with warp shuffles, and only lanes 0 / 31 issue one
+// extra scalar load for the neighbouring warp's edge element.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbk {
+
+constexpr int kThreads = 256;            // threads per block (8 warps)
+constexpr int kWarps = kThreads / 32;
+constexpr int kSitesPerWarp = 128;       // 32 lanes x 4 sites
+
+template <int Q> struct Lat;
+template <> struct Lat<5> {
+    __host__ __device__ static constexpr int cx(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
+    __host__ __device__ static constexpr int cy(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
+};
+template <> struct Lat<9> {
+    __host__ __device__ static constexpr int cx(int i) {
+        return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+    }
+};
+
+// Arguments of one step launch (passed by value).
+struct StepArgs {
+    const void *in;          // h^{t-1}  [Q][ny][pitch]
+    void *out;               // h^{t}
+    const float *eta2;       // [ny][pitch] (c / c_ref)^2
+    int nx, ny, pitch;
+    long long plane;         // ny * pitch
+    int segs;                // warps per row = ceil(nx / 128)
+    int main_blocks;         // blocks doing sites; the rest gather receivers
+    // collision
+    float omega;             // BGK: 1 / tau
+    float s[9];              // MRT: diagonal of S (moment order of App. A)
+    float w1r, w5r, c2r;     // D2Q9 reference weights at eta = 1, c2r = 2 w1r + 4 w5r
+    float a1, a5;            // D2Q9 w_i / c_s^2 of axis / diagonal links (eta independent)
+    // sponge
+    int sponge_w;
+    float sponge_smax, sponge_inv_w;
+    // source
+    const float *src_tab;    // S[n], n < src_nt (device); may be null
+    int src_nt, src_x, src_y;
+    long long t;             // time of the state being collided
+    int raw;                 // 1: `in` holds g(t) itself (set by lb_set_state / lb_init_pressure)
+    // receivers
+    const int2 *rec;
+    int nrec;
+    float *trace_row;        // pressure row for time t, or null
+    // 16-bit storage: value = stored * in_scale[i]; stored = value * out_inv[i]
+    float in_scale[9], out_inv[9];
+};
+
+// ---------------------------------------------------------------- storage --
+template <typename ST> struct Store;
+
+template <> struct Store<float> {
+    static constexpr int kBytes = 4;
+    __device__ static __forceinline__ float4 load4(const float *p) {
+        return *reinterpret_cast<const float4 *>(p);
+    }
+    __device__ static __forceinline__ float load1(const float *p) { return *p; }
+    __device__ static __forceinline__ void store1(float *p, float v) { *p = v; }
+    __device__ static __forceinline__ void store4(float *p, float4 v) {
+        *reinterpret_cast<float4 *>(p) = v;
+    }
+};
+
+template <> struct Store<__nv_bfloat16> {
+    static constexpr int kBytes = 2;
+    __device__ static __forceinline__ float4 load4(const __nv_bfloat16 *p) {
+        uint2 u = *reinterpret_cast<const uint2 *>(p);
+        __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x);
+        __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
+        float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    __device__ static __forceinline__ float load1(const __nv_bfloat16 *p) {
+        return __bfloat162float(*p);
+    }
+    __device__ static __forceinline__ void store1(__nv_bfloat16 *p, float v) {
+        *p = __float2bfloat16_rn(v);
+    }
+    __device__ static __forceinline__ void store4(__nv_bfloat16 *p, float4 v) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+        __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t *>(&a);
+        u.y = *reinterpret_cast<uint32_t *>(&b);
+        *reinterpret_cast<uint2 *>(p) = u;
+    }
+};
+
+template <> struct Store<__half> {
+    static constexpr int kBytes = 2;
+    __device__ static __forceinline__ float4 load4(const __half *p) {
+        uint2 u = *reinterpret_cast<const uint2 *>(p);
+        __half2 a = *reinterpret_cast<__half2 *>(&u.x);
+        __half2 b = *reinterpret_cast<__half2 *>(&u.y);
+        float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    __device__ static __forceinline__ float load1(const __half *p) { return __half2float(*p); }
+    __device__ static __forceinline__ void store1(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static __forceinline__ void store4(__half *p, float4 v) {
+        __half2 a = __floats2half2_rn(v.x, v.y);
+        __half2 b = __floats2half2_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t *>(&a);
+        u.y = *reinterpret_cast<uint32_t *>(&b);
+        *reinterpret_cast<uint2 *>(p) = u;
+    }
+};
+
+// ------------------------------------------------------------------ pulls --
+// Pull one population's 4 values for sites x0..x0+3 of this thread's row from
+// source row `row` (nullptr: the row lies outside a zero-ghost domain).  CX is
+// the population's x velocity: the value at site x comes from x - CX.
+// Must be called by all 32 lanes of the warp (shuffles).
+template <int CX, bool PERIODIC, typename ST>
+__device__ __forceinline__ void pull4(const ST *row, int x0, int lane, int nx, bool active,
+                                      float scale, float v[4]) {
+    if (row == nullptr) {  // warp-uniform
+        v[0] = v[1] = v[2] = v[3] = 0.f;
+        return;
+    }
+    float4 q = active ? Store<ST>::load4(row + x0) : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (CX == 0) {
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if (CX == 1) {  // value from x - 1
+        float left = __shfl_up_sync(0xffffffffu, q.w, 1);
+        if (lane == 0) left = (x0 > 0) ? Store<ST>::load1(row + x0 - 1) : 0.f;
+        v[0] = left; v[1] = q.x; v[2] = q.y; v[3] = q.z;
+        if (x0 == 0) v[0] = PERIODIC ? Store<ST>::load1(row + nx - 1) : 0.f;
+    } else {  // CX == -1: value from x + 1
+        float right = __shfl_down_sync(0xffffffffu, q.x, 1);
+        if (lane == 31) right = (x0 + 4 < nx) ? Store<ST>::load1(row + x0 + 4) : 0.f;
+        v[0] = q.y; v[1] = q.z; v[2] = q.w; v[3] = right;
+        const int k = nx - 1 - x0;  // local index of the last real site, if in this vector
+        if (k >= 0 && k < 4) {
+            const float b = PERIODIC ? Store<ST>::load1(row) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (j == k) v[j] = b;
+        }
+    }
+    if (scale != 1.f) {
+        v[0] *= scale; v[1] *= scale; v[2] *= scale; v[3] *= scale;
+    }
+}
+
+template <bool PERIODIC, typename ST>
+__device__ __forceinline__ const ST *src_row(const ST *base, int ys, int ny, int pitch) {
+    if (ys < 0 || ys >= ny) {
+        if (!PERIODIC) return nullptr;
+        ys = ys < 0 ? ys + ny : ys - ny;
+    }
+    return base + (long long)ys * pitch;
+}
+
+// ------------------------------------------------------------- collision --
+// D2Q5: w_0 = 1 - eta^2, w_1..4 = eta^2 / 4, c_s^2 = eta^2 / 2, so
+// g^eq_0 = w_0 rho, g^eq_{1,3} = w_1 rho +- j_x / 2, g^eq_{2,4} = w_1 rho +- j_y / 2.
+template <bool MRT>
+__device__ __forceinline__ void collide5(float g[5], float e2, const StepArgs &a) {
+    const float rho = g[0] + g[1] + g[2] + g[3] + g[4];
+    const float jx = g[1] - g[3], jy = g[2] - g[4];
+    const float w0 = 1.f - e2, w1 = 0.25f * e2;
+    if (!MRT) {
+        const float om = a.omega;
+        const float eq0 = w0 * rho, b = w1 * rho;
+        g[0] += om * (eq0 - g[0]);
+        g[1] += om * (b + 0.5f * jx - g[1]);
+        g[2] += om * (b + 0.5f * jy - g[2]);
+        g[3] += om * (b - 0.5f * jx - g[3]);
+        g[4] += om * (b - 0.5f * jy - g[4]);
+    } else {
+        // Only e and p_xx are not conserved.  e = -4 g0 + sum_{1..4} g = rho - 5 g0,
+        // e^eq = (-4 + 10 c_s^2) rho (Eq. higher moments e), p_xx^eq = 0.
+        // g* = g - M^-1 S (m - m^eq), M^-1 = M^T diag(1/5, 1/2, 1/2, 1/20, 1/4).
+        const float e_neq = (rho - 5.f * g[0]) - (-4.f + 5.f * e2) * rho;
+        const float pxx = g[1] - g[2] + g[3] - g[4];
+        const float de = a.s[3] * e_neq * (1.f / 20.f);
+        const float dp = a.s[4] * pxx * 0.25f;
+        g[0] += 4.f * de;
+        g[1] -= de + dp;
+        g[2] -= de - dp;
+        g[3] -= de + dp;
+        g[4] -= de - dp;
+    }
+}
+
+// D2Q9 with the eta^2-scaled weights: w_{1..4} = eta^2 w1r, w_{5..8} = eta^2 w5r,
+// c_s^2 = eta^2 c2r, so w_i / c_s^2 = a1 or a5 does not depend on eta.
+template <bool MRT>
+__device__ __forceinline__ void collide9(float g[9], float e2, const StepArgs &a) {
+    const float rho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+    const float jx = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
+    const float jy = g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
+    const float w1 = e2 * a.w1r, w5 = e2 * a.w5r;
+    const float w0 = 1.f - 4.f * (w1 + w5);
+    float eq[9];
+    eq[0] = w0 * rho;
+    const float b1 = w1 * rho, b5 = w5 * rho;
+    const float ux = a.a1 * jx, uy = a.a1 * jy;
+    eq[1] = b1 + ux; eq[3] = b1 - ux;
+    eq[2] = b1 + uy; eq[4] = b1 - uy;
+    const float dp = a.a5 * (jx + jy), dm = a.a5 * (jx - jy);
+    eq[5] = b5 + dp; eq[7] = b5 - dp;
+    eq[6] = b5 - dm; eq[8] = b5 + dm;
+    if (!MRT) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) g[i] += a.omega * (eq[i] - g[i]);
+        return;
+    }
+    float n[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) n[i] = g[i] - eq[i];
+    const float s14 = n[1] + n[2] + n[3] + n[4], s58 = n[5] + n[6] + n[7] + n[8];
+    // non-conserved moments of g - g^eq (rows 3..8 of M, App. A), scaled by s_k / |row_k|^2
+    const float d3 = a.s[3] * (-4.f * n[0] - s14 + 2.f * s58) * (1.f / 36.f);
+    const float d4 = a.s[4] * (n[1] - n[2] + n[3] - n[4]) * 0.25f;
+    const float d5 = a.s[5] * (4.f * n[0] - 2.f * s14 + s58) * (1.f / 36.f);
+    const float d6 = a.s[6] * (-2.f * n[1] + 2.f * n[3] + n[5] - n[6] - n[7] + n[8]) * (1.f / 12.f);
+    const float d7 = a.s[7] * (-2.f * n[2] + 2.f * n[4] + n[5] + n[6] - n[7] - n[8]) * (1.f / 12.f);
+    const float d8 = a.s[8] * (n[5] - n[6] + n[7] - n[8]) * 0.25f;
+    // g* = g - M^T (d3..d8)
+    g[0] -= -4.f * d3 + 4.f * d5;
+    g[1] -= -d3 + d4 - 2.f * d5 - 2.f * d6;
+    g[2] -= -d3 - d4 - 2.f * d5 - 2.f * d7;
+    g[3] -= -d3 + d4 - 2.f * d5 + 2.f * d6;
+    g[4] -= -d3 - d4 - 2.f * d5 + 2.f * d7;
+    const float c5 = 2.f * d3 + d5;
+    g[5] -= c5 + d6 + d7 + d8;
+    g[6] -= c5 - d6 + d7 - d8;
+    g[7] -= c5 - d6 - d7 + d8;
+    g[8] -= c5 + d6 - d7 - d8;
+}
+
+template <int Q>
+__device__ __forceinline__ float weight_i(int i, float e2, const StepArgs &a) {
+    if (Q == 5) return i == 0 ? 1.f - e2 : 0.25f * e2;
+    if (i == 0) return 1.f - 4.f * e2 * (a.w1r + a.w5r);
+    return i < 5 ? e2 * a.w1r : e2 * a.w5r;
+}
+
+template <int Q>
+__device__ __forceinline__ float cs2_of(float e2, const StepArgs &a) {
+    return Q == 5 ? 0.5f * e2 : e2 * a.c2r;
+}
+
+__device__ __forceinline__ float sponge_factor(int x, int y, const StepArgs &a) {
+    int d = min(min(x, a.nx - 1 - x), min(y, a.ny - 1 - y));
+    if (d >= a.sponge_w) return 1.f;
+    float r = (float)(a.sponge_w - d) * a.sponge_inv_w;
+    return 1.f - a.sponge_smax * r * r;
+}
+
+// --------------------------------------------------------------- receivers --
+template <int Q, bool PERIODIC, typename ST>
+__device__ __forceinline__ void gather_receivers(const StepArgs &a, int r) {
+    if (r >= a.nrec || a.trace_row == nullptr) return;
+    const int2 xy = a.rec[r];
+    const ST *in = static_cast<const ST *>(a.in);
+    float rho = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        int xs = xy.x - (a.raw ? 0 : Lat<Q>::cx(i)), ys = xy.y - (a.raw ? 0 : Lat<Q>::cy(i));
+        if (PERIODIC) {
+            xs = (xs + a.nx) % a.nx;
+            ys = (ys + a.ny) % a.ny;
+        } else if (xs < 0 || xs >= a.nx || ys < 0 || ys >= a.ny) {
+            continue;
+        }
+        rho += Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch + xs) * a.in_scale[i];
+    }
+    a.trace_row[r] = cs2_of<Q>(a.eta2[(long long)xy.y * a.pitch + xy.x], a) * rho;
+}
+
+// -------------------------------------------------------------------- step --
+template <int Q, bool MRT, bool PERIODIC, typename ST>
+__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
+    if ((int)blockIdx.x >= a.main_blocks) {
+        gather_receivers<Q, PERIODIC, ST>(a, ((int)blockIdx.x - a.main_blocks) * kThreads +
+                                                 (int)threadIdx.x);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int wid = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int y = wid / a.segs;
+    if (y >= a.ny) return;  // warp-uniform
+    const int x0 = (wid - y * a.segs) * kSitesPerWarp + lane * 4;
+    const bool active = x0 < a.nx;
+    const ST *in = static_cast<const ST *>(a.in);
+
+    float g[Q][4];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        if (a.raw) {  // warp-uniform: first step after lb_set_state, read g(t) in place
+            pull4<0, PERIODIC>(in + i * a.plane + (long long)y * a.pitch, x0, lane, a.nx, active,
+                               a.in_scale[i], g[i]);
+            continue;
+        }
+        const ST *row = src_row<PERIODIC>(in + i * a.plane, y - Lat<Q>::cy(i), a.ny, a.pitch);
+        const int cx = Lat<Q>::cx(i);
+        if (cx == 1)
+            pull4<1, PERIODIC>(row, x0, lane, a.nx, active, a.in_scale[i], g[i]);
+        else if (cx == -1)
+            pull4<-1, PERIODIC>(row, x0, lane, a.nx, active, a.in_scale[i], g[i]);
+        else
+            pull4<0, PERIODIC>(row, x0, lane, a.nx, active, a.in_scale[i], g[i]);
+    }
+    if (!active) return;  // no more shuffles below
+
+    float4 e2v = *reinterpret_cast<const float4 *>(a.eta2 + (long long)y * a.pitch + x0);
+    const float e2s[4] = {e2v.x, e2v.y, e2v.z, e2v.w};
+    const bool edge = a.sponge_w > 0 &&
+                      (y < a.sponge_w || y >= a.ny - a.sponge_w || x0 < a.sponge_w ||
+                       x0 + 3 >= a.nx - a.sponge_w);
+    const bool has_src = (y == a.src_y) && (a.src_x >= x0) && (a.src_x < x0 + 4) &&
+                         a.src_tab != nullptr && a.t < a.src_nt;
+    float out[Q][4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        float gs[Q];
+#pragma unroll
+        for (int i = 0; i < Q; i++) gs[i] = g[i][k];
+        if (Q == 5)
+            collide5<MRT>(gs, e2s[k], a);
+        else
+            collide9<MRT>(gs, e2s[k], a);
+        if (has_src && a.src_x == x0 + k) {
+            const float S = a.src_tab[a.t];
+#pragma unroll
+            for (int i = 0; i < Q; i++) gs[i] += weight_i<Q>(i, e2s[k], a) * S;
+        }
+        float f = 1.f;
+        if (edge) f = sponge_factor(x0 + k, y, a);
+        const bool real = x0 + k < a.nx;
+#pragma unroll
+        for (int i = 0; i < Q; i++) out[i][k] = real ? gs[i] * f : 0.f;
+    }
+    ST *o = static_cast<ST *>(a.out) + (long long)y * a.pitch + x0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        float sc = a.out_inv[i];
+        Store<ST>::store4(o + i * a.plane, make_float4(out[i][0] * sc, out[i][1] * sc,
+                                                       out[i][2] * sc, out[i][3] * sc));
+    }
+}
+
+// -------------------------------------------------------- state transforms --
+// Write the state g(t) in place ("raw", unshifted).  mode 0: g from pressure p
+// (g_i = (w_i / c_s^2) p, Eq. linear eqm dist with j = 0); mode 1: g given as
+// [Q][ny][nx] FP32; src == nullptr: all zero.
+template <int Q, bool PERIODIC, typename ST>
+__global__ void set_state_kernel(StepArgs a, const float *src, int mode) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = (long long)a.ny * a.pitch;
+    if (idx >= total) return;
+    int y = (int)(idx / a.pitch), x = (int)(idx - (long long)y * a.pitch);
+    ST *o = static_cast<ST *>(a.out);
+    for (int i = 0; i < Q; i++) {
+        float v = 0.f;
+        if (x < a.nx && src) {
+            if (mode == 0) {
+                float e2 = a.eta2[idx];
+                v = weight_i<Q>(i, e2, a) / cs2_of<Q>(e2, a) * src[(long long)y * a.nx + x];
+            } else {
+                v = src[(long long)i * a.nx * a.ny + (long long)y * a.nx + x];
+            }
+        }
+        Store<ST>::store1(o + i * a.plane + idx, v * a.out_inv[i]);
+    }
+}
+
+// mode 0: pressure [ny][nx]; mode 1: populations [Q][ny][nx] (pre-collision, current time)
+template <int Q, bool PERIODIC, typename ST>
+__global__ void get_state_kernel(StepArgs a, float *dst, int mode) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = (long long)a.ny * a.nx;
+    if (idx >= total) return;
+    int y = (int)(idx / a.nx), x = (int)(idx - (long long)y * a.nx);
+    const ST *in = static_cast<const ST *>(a.in);
+    float rho = 0.f;
+    for (int i = 0; i < Q; i++) {
+        int xs = x - (a.raw ? 0 : Lat<Q>::cx(i)), ys = y - (a.raw ? 0 : Lat<Q>::cy(i));
+        float v = 0.f;
+        bool ok = true;
+        if (PERIODIC) {
+            xs = (xs + a.nx) % a.nx;
+            ys = (ys + a.ny) % a.ny;
+        } else {
+            ok = xs >= 0 && xs < a.nx && ys >= 0 && ys < a.ny;
+        }
+        if (ok) v = Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch + xs) * a.in_scale[i];
+        if (mode == 1) dst[(long long)i * total + idx] = v;
+        rho += v;
+    }
+    if (mode == 0) dst[idx] = cs2_of<Q>(a.eta2[(long long)y * a.pitch + x], a) * rho;
+}
+
+// eta^2 = (c / c_ref)^2 per site (pads 0); flags: bit0 c <= 0 or non-finite, bit1 eta > 1.
+__global__ void medium_kernel(const float *c_map, float *eta2, int nx, int ny, int pitch,
+                              double inv_cref, unsigned *flags) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)ny * pitch) return;
+    int y = (int)(idx / pitch), x = (int)(idx - (long long)y * pitch);
+    float v = 0.f;
+    if (x < nx) {
+        float c = c_map[(long long)y * nx + x];
+        if (!(c > 0.f) || !isfinite(c)) atomicOr(flags, 1u);
+        double eta = (double)c * inv_cref;
+        if (eta > 1.0 + 1e-6) atomicOr(flags, 2u);
+        if (eta > 1.0) eta = 1.0;
+        v = (float)(eta * eta);
+    }
+    eta2[idx] = v;
+}
+
+}  // namespace lbk

@@ -1,0 +1,55 @@
+// lb_runtime.h -- internal context structure of the C ABI (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+#include "lbac.h"
+
+struct lb_refine;  // two-level grid refinement state (refine.cu)
+
+struct lb_ctx {
+    lb_config cfg;                  // copy; pointer members cleared
+    int Q = 5, nx = 0, ny = 0, pitch = 0, ebytes = 4;
+    void *pop[2] = {nullptr, nullptr};
+    int cur = 0;                    // pop[cur] holds the post-collision state of step t-1
+    bool raw = false;               // ... or, when raw, the state g(t) itself (unshifted)
+    float *eta2 = nullptr;          // [ny][pitch] (c / c_ref)^2
+    float *src_tab = nullptr;
+    int src_nt = 0, src_x = 0, src_y = 0;
+    int2 *rec = nullptr;
+    int nrec = 0;
+    float *trace = nullptr;         // [trace_cap][nrec]
+    int trace_cap = 0;
+    long long t_rec0 = 0;
+    long long t = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool refined = false;
+    bool fine_ready = false;
+    lb_refine *ref = nullptr;
+    void *(*alloc_fn)(size_t, void *) = nullptr;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *alloc_user = nullptr;
+    std::vector<void *> allocs;
+    std::string err;
+};
+
+namespace lbrt {
+lb_status fail(lb_ctx *ctx, lb_status st, const char *fmt, ...);
+lb_status cuda_fail(lb_ctx *ctx, cudaError_t e, const char *what);
+void *dev_alloc(lb_ctx *ctx, size_t bytes);
+void dev_free(lb_ctx *ctx, void *p);
+}  // namespace lbrt
+
+// grid refinement (refine.cu)
+lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev);
+void refine_destroy(lb_ctx *ctx);
+bool refine_contains(const lb_ctx *ctx, int x, int y);
+lb_status refine_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
+lb_status refine_after_set_state(lb_ctx *ctx);
+lb_status refine_step(lb_ctx *ctx, int n);
+lb_status refine_overlay_pressure(lb_ctx *ctx, float *p_dev);

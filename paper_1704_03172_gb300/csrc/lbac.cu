@@ -1,0 +1,574 @@
+// lbac.cu -- runtime behind the C ABI of include/lbac.h: context, device
+// memory, medium preprocessing and the launch loop of the fused LB step.
+//
+// The method is the linear lattice-Boltzmann scheme of arXiv:1704.03172; the
+// per-site arithmetic lives in lb_kernels.cuh.  Nothing here computes on the
+// host except parameter validation and launch bookkeeping.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbac.h"
+#include "lb_kernels.cuh"
+#include "lb_runtime.h"
+
+using namespace lbk;
+
+namespace lbrt {
+
+thread_local std::string g_create_error;
+
+lb_status fail(lb_ctx *ctx, lb_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx)
+        ctx->err = buf;
+    else
+        g_create_error = buf;
+    return st;
+}
+
+lb_status cuda_fail(lb_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, LB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void *dev_alloc(lb_ctx *ctx, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (ctx->alloc_fn) {
+        p = ctx->alloc_fn(bytes, ctx->alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) ctx->allocs.push_back(p);
+    return p;
+}
+
+void dev_free(lb_ctx *ctx, void *p) {
+    if (!p) return;
+    auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+    if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+    if (ctx->free_fn)
+        ctx->free_fn(p, ctx->alloc_user);
+    else
+        cudaFree(p);
+}
+
+int elem_bytes(int storage) { return storage == LB_F32 ? 4 : 2; }
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+StepArgs base_args(const lb_ctx *c) {
+    StepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.eta2 = c->eta2;
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.pitch = c->pitch;
+    a.plane = (long long)c->ny * c->pitch;
+    a.segs = (c->nx + kSitesPerWarp - 1) / kSitesPerWarp;
+    long long warps = (long long)a.segs * c->ny;
+    a.main_blocks = (int)((warps + kWarps - 1) / kWarps);
+    a.omega = (float)(1.0 / c->cfg.tau);
+    for (int k = 0; k < 9; k++) a.s[k] = (float)c->cfg.s[k];
+    a.w1r = (float)c->cfg.w_ref[1];
+    a.w5r = (float)c->cfg.w_ref[2];
+    double c2r = 2.0 * c->cfg.w_ref[1] + 4.0 * c->cfg.w_ref[2];
+    a.c2r = (float)c2r;
+    a.a1 = c2r > 0 ? (float)(c->cfg.w_ref[1] / c2r) : 0.f;
+    a.a5 = c2r > 0 ? (float)(c->cfg.w_ref[2] / c2r) : 0.f;
+    a.sponge_w = c->cfg.sponge_width;
+    a.sponge_smax = (float)c->cfg.sponge_sigma_max;
+    a.sponge_inv_w = c->cfg.sponge_width > 0 ? 1.f / (float)c->cfg.sponge_width : 0.f;
+    a.src_tab = c->src_tab;
+    a.src_nt = c->src_nt;
+    a.src_x = c->src_x;
+    a.src_y = c->src_y;
+    a.rec = c->rec;
+    a.nrec = c->nrec;
+    for (int i = 0; i < 9; i++) {
+        a.in_scale[i] = 1.f;
+        a.out_inv[i] = 1.f;
+    }
+    return a;
+}
+
+// ------------------------------------------------------- kernel dispatch --
+using StepFn = void (*)(const StepArgs);
+using SetFn = void (*)(StepArgs, const float *, int);
+using GetFn = void (*)(StepArgs, float *, int);
+
+template <int Q, bool MRT, bool PER, typename ST> StepFn step_fn() {
+    return step_kernel<Q, MRT, PER, ST>;
+}
+
+template <int Q, bool MRT, typename ST> StepFn step_fn_b(bool per) {
+    return per ? step_fn<Q, MRT, true, ST>() : step_fn<Q, MRT, false, ST>();
+}
+template <int Q, typename ST> StepFn step_fn_c(bool mrt, bool per) {
+    return mrt ? step_fn_b<Q, true, ST>(per) : step_fn_b<Q, false, ST>(per);
+}
+template <typename ST> StepFn step_fn_q(int Q, bool mrt, bool per) {
+    return Q == 9 ? step_fn_c<9, ST>(mrt, per) : step_fn_c<5, ST>(mrt, per);
+}
+
+StepFn pick_step(const lb_ctx *c) {
+    bool mrt = c->cfg.collision == LB_MRT, per = c->cfg.boundary == LB_PERIODIC;
+    switch (c->cfg.storage) {
+        case LB_BF16: return step_fn_q<__nv_bfloat16>(c->Q, mrt, per);
+        case LB_F16: return step_fn_q<__half>(c->Q, mrt, per);
+        default: return step_fn_q<float>(c->Q, mrt, per);
+    }
+}
+
+template <int Q, typename ST> SetFn set_fn_q(bool per) {
+    return per ? set_state_kernel<Q, true, ST> : set_state_kernel<Q, false, ST>;
+}
+template <typename ST> SetFn set_fn(int Q, bool per) {
+    return Q == 9 ? set_fn_q<9, ST>(per) : set_fn_q<5, ST>(per);
+}
+SetFn pick_set(const lb_ctx *c) {
+    bool per = c->cfg.boundary == LB_PERIODIC;
+    switch (c->cfg.storage) {
+        case LB_BF16: return set_fn<__nv_bfloat16>(c->Q, per);
+        case LB_F16: return set_fn<__half>(c->Q, per);
+        default: return set_fn<float>(c->Q, per);
+    }
+}
+template <int Q, typename ST> GetFn get_fn_q(bool per) {
+    return per ? get_state_kernel<Q, true, ST> : get_state_kernel<Q, false, ST>;
+}
+template <typename ST> GetFn get_fn(int Q, bool per) {
+    return Q == 9 ? get_fn_q<9, ST>(per) : get_fn_q<5, ST>(per);
+}
+GetFn pick_get(const lb_ctx *c) {
+    bool per = c->cfg.boundary == LB_PERIODIC;
+    switch (c->cfg.storage) {
+        case LB_BF16: return get_fn<__nv_bfloat16>(c->Q, per);
+        case LB_F16: return get_fn<__half>(c->Q, per);
+        default: return get_fn<float>(c->Q, per);
+    }
+}
+
+lb_status check_launch(lb_ctx *ctx, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    return LB_OK;
+}
+
+lb_status validate(const lb_config *cfg) {
+    if (!cfg) return fail(nullptr, LB_EINVAL, "cfg is NULL");
+    if (cfg->lattice != LB_D2Q5 && cfg->lattice != LB_D2Q9)
+        return fail(nullptr, LB_EINVAL, "lattice must be LB_D2Q5 or LB_D2Q9");
+    if (cfg->collision != LB_BGK && cfg->collision != LB_MRT)
+        return fail(nullptr, LB_EINVAL, "collision must be LB_BGK or LB_MRT");
+    if (cfg->storage != LB_F32 && cfg->storage != LB_BF16 && cfg->storage != LB_F16)
+        return fail(nullptr, LB_EINVAL, "storage must be LB_F32, LB_BF16 or LB_F16");
+    if (cfg->boundary != LB_ZERO_GHOST && cfg->boundary != LB_PERIODIC)
+        return fail(nullptr, LB_EINVAL, "boundary must be LB_ZERO_GHOST or LB_PERIODIC");
+    if (cfg->nx < 1 || cfg->ny < 1 || (long long)cfg->nx * cfg->ny > (1LL << 34))
+        return fail(nullptr, LB_EINVAL, "grid %d x %d out of range", cfg->nx, cfg->ny);
+    if (!cfg->c_map) return fail(nullptr, LB_EINVAL, "c_map is NULL");
+    if (cfg->collision == LB_BGK && !(cfg->tau >= 0.5 && std::isfinite(cfg->tau)))
+        return fail(nullptr, LB_EINVAL, "BGK needs tau >= 1/2 (got %g)", cfg->tau);
+    if (cfg->collision == LB_MRT) {
+        for (int k = 0; k < cfg->lattice; k++)
+            if (!(cfg->s[k] > 0.0 && cfg->s[k] <= 2.0))
+                return fail(nullptr, LB_EINVAL, "MRT rate s[%d] = %g outside (0, 2]", k, cfg->s[k]);
+    }
+    if (cfg->lattice == LB_D2Q9) {
+        const double *w = cfg->w_ref;
+        if (w[0] < 0 || w[1] < 0 || w[2] < 0 || std::fabs(w[0] + 4 * w[1] + 4 * w[2] - 1.0) > 1e-9)
+            return fail(nullptr, LB_EINVAL, "D2Q9 w_ref must be >= 0 with w0 + 4 w1 + 4 w5 = 1");
+        if (2 * w[1] + 4 * w[2] <= 0)
+            return fail(nullptr, LB_EINVAL, "D2Q9 w_ref gives c_s = 0");
+    }
+    if (cfg->sponge_width < 0 || cfg->sponge_sigma_max < 0 || cfg->sponge_sigma_max > 1)
+        return fail(nullptr, LB_EINVAL, "sponge_width >= 0 and sigma_max in [0, 1] required");
+    if (cfg->n_patches < 0 || cfg->n_patches > 1 || (cfg->n_patches > 0 && !cfg->patches))
+        return fail(nullptr, LB_EINVAL, "at most one patch is supported");
+    return LB_OK;
+}
+
+}  // namespace lbrt
+
+using namespace lbrt;
+
+extern "C" {
+
+lb_status lb_config_default(lb_config *cfg) {
+    if (!cfg) return LB_EINVAL;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->lattice = LB_D2Q5;
+    cfg->collision = LB_BGK;
+    cfg->storage = LB_F32;
+    cfg->boundary = LB_ZERO_GHOST;
+    cfg->tau = 0.5;
+    for (int k = 0; k < 9; k++) cfg->s[k] = 1.0;
+    cfg->w_ref[0] = 4.0 / 9.0;
+    cfg->w_ref[1] = 1.0 / 9.0;
+    cfg->w_ref[2] = 1.0 / 36.0;
+    cfg->time_block = 1;
+    return LB_OK;
+}
+
+lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint, size_t *bytes) {
+    if (!cfg || !bytes) return LB_EINVAL;
+    size_t pitch = (size_t)round_up(std::max(cfg->nx, 1), 32);
+    size_t plane = pitch * (size_t)std::max(cfg->ny, 1);
+    size_t q = cfg->lattice == LB_D2Q9 ? 9 : 5;
+    size_t b = 2 * q * plane * elem_bytes(cfg->storage) + plane * 4;
+    if (nrec > 0 && nt > 0) b += (size_t)nt * nrec * 4 + (size_t)nrec * 8;
+    if (nt > 0) b += (size_t)nt * 4;
+    if (want_adjoint) {
+        // adjoint state pair + gradient + checkpoints (see lb_adjoint)
+        b += 2 * q * plane * 4 + plane * 8;
+    }
+    *bytes = b;
+    return LB_OK;
+}
+
+lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
+    if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
+    *out = nullptr;
+    lb_status st = validate(cfg);
+    if (st != LB_OK) return st;
+    lb_ctx *c = new (std::nothrow) lb_ctx();
+    if (!c) return fail(nullptr, LB_ENOMEM, "host allocation failed");
+    c->cfg = *cfg;
+    c->cfg.c_map = nullptr;
+    c->cfg.patches = nullptr;
+    c->Q = cfg->lattice;
+    c->nx = cfg->nx;
+    c->ny = cfg->ny;
+    c->pitch = round_up(cfg->nx, 32);
+    c->ebytes = elem_bytes(cfg->storage);
+    c->alloc_fn = cfg->dev_alloc;
+    c->free_fn = cfg->dev_free;
+    c->alloc_user = cfg->alloc_user;
+    if (cfg->cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_fail(nullptr, e, "cudaStreamCreate");
+        }
+        c->own_stream = true;
+    }
+    auto bail = [&](lb_status s) {
+        std::string msg = c->err;
+        lb_destroy(c);
+        if (!msg.empty()) g_create_error = msg;
+        return s;
+    };
+    const size_t plane = (size_t)c->ny * c->pitch;
+    for (int b = 0; b < 2; b++) {
+        c->pop[b] = dev_alloc(c, (size_t)c->Q * plane * c->ebytes);
+        if (!c->pop[b]) return bail(fail(c, LB_ENOMEM, "population buffer (%zu bytes)",
+                                         (size_t)c->Q * plane * c->ebytes));
+        cudaError_t e = cudaMemsetAsync(c->pop[b], 0, (size_t)c->Q * plane * c->ebytes, c->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemsetAsync"));
+    }
+    c->eta2 = static_cast<float *>(dev_alloc(c, plane * 4));
+    unsigned *flags = static_cast<unsigned *>(dev_alloc(c, 256));
+    if (!c->eta2 || !flags) return bail(fail(c, LB_ENOMEM, "medium buffer"));
+    // medium: c_map -> eta^2 (Eq. 0th lattice weight), on the device
+    const float *cmap_dev = cfg->c_map;
+    float *staging = nullptr;
+    double cref = cfg->c_ref;
+    if (!cfg->c_map_on_device) {
+        if (!(cref > 0)) {
+            float mx = 0.f;
+            for (long long i = 0; i < (long long)c->nx * c->ny; i++) mx = std::max(mx, cfg->c_map[i]);
+            cref = mx;
+        }
+        staging = static_cast<float *>(dev_alloc(c, (size_t)c->nx * c->ny * 4));
+        if (!staging) return bail(fail(c, LB_ENOMEM, "c_map staging"));
+        cudaError_t e = cudaMemcpyAsync(staging, cfg->c_map, (size_t)c->nx * c->ny * 4,
+                                        cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "c_map upload"));
+        cmap_dev = staging;
+    } else if (!(cref > 0)) {
+        return bail(fail(c, LB_EINVAL, "c_ref must be given when c_map is on the device"));
+    }
+    c->cfg.c_ref = cref;
+    cudaMemsetAsync(flags, 0, 4, c->stream);
+    {
+        long long total = (long long)c->ny * c->pitch;
+        int blocks = (int)((total + 255) / 256);
+        medium_kernel<<<blocks, 256, 0, c->stream>>>(cmap_dev, c->eta2, c->nx, c->ny, c->pitch,
+                                                      1.0 / cref, flags);
+        if ((st = check_launch(c, "medium_kernel")) != LB_OK) return bail(st);
+    }
+    unsigned hflags = 0;
+    cudaError_t e = cudaMemcpyAsync(&hflags, flags, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "medium setup"));
+    dev_free(c, flags);
+    if (staging) dev_free(c, staging);
+    if (hflags & 1u) return bail(fail(c, LB_EINVAL, "c_map must be finite and > 0"));
+    if (hflags & 2u) return bail(fail(c, LB_EINVAL, "c_map exceeds c_ref (eta > 1)"));
+    if (cfg->n_patches > 0) {
+        if ((st = refine_setup(c, cfg, cmap_dev)) != LB_OK) return bail(st);
+    }
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_destroy(lb_ctx *ctx) {
+    if (!ctx) return LB_EINVAL;
+    cudaStreamSynchronize(ctx->stream);
+    refine_destroy(ctx);
+    std::vector<void *> all = ctx->allocs;
+    for (void *p : all) dev_free(ctx, p);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return LB_OK;
+}
+
+lb_status lb_set_source(lb_ctx *ctx, int x, int y, const double *wavelet, int nt) {
+    if (!ctx) return LB_EINVAL;
+    if (nt < 0 || (nt > 0 && !wavelet)) return fail(ctx, LB_EINVAL, "bad wavelet");
+    if (nt > 0 && (x < 0 || x >= ctx->nx || y < 0 || y >= ctx->ny))
+        return fail(ctx, LB_EINVAL, "source (%d, %d) outside the grid", x, y);
+    if (nt > 0 && ctx->refined && refine_contains(ctx, x, y))
+        return fail(ctx, LB_EINVAL, "the source must lie outside the refined patch");
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->src_tab) dev_free(ctx, ctx->src_tab);
+    ctx->src_tab = nullptr;
+    ctx->src_nt = 0;
+    if (nt == 0) return LB_OK;
+    std::vector<float> tab(wavelet, wavelet + nt);
+    ctx->src_tab = static_cast<float *>(dev_alloc(ctx, (size_t)nt * 4));
+    if (!ctx->src_tab) return fail(ctx, LB_ENOMEM, "source table");
+    cudaError_t e = cudaMemcpyAsync(ctx->src_tab, tab.data(), (size_t)nt * 4,
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "source upload");
+    ctx->src_nt = nt;
+    ctx->src_x = x;
+    ctx->src_y = y;
+    return LB_OK;
+}
+
+lb_status lb_set_receivers(lb_ctx *ctx, const int *xy, int nrec, int nt_capacity) {
+    if (!ctx) return LB_EINVAL;
+    if (nrec < 0 || (nrec > 0 && (!xy || nt_capacity < 0)))
+        return fail(ctx, LB_EINVAL, "bad receiver arguments");
+    for (int r = 0; r < nrec; r++)
+        if (xy[2 * r] < 0 || xy[2 * r] >= ctx->nx || xy[2 * r + 1] < 0 || xy[2 * r + 1] >= ctx->ny)
+            return fail(ctx, LB_EINVAL, "receiver %d (%d, %d) outside the grid", r, xy[2 * r],
+                        xy[2 * r + 1]);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->rec) dev_free(ctx, ctx->rec);
+    if (ctx->trace) dev_free(ctx, ctx->trace);
+    ctx->rec = nullptr;
+    ctx->trace = nullptr;
+    ctx->nrec = 0;
+    ctx->trace_cap = 0;
+    ctx->t_rec0 = ctx->t;
+    if (nrec == 0) return LB_OK;
+    ctx->rec = static_cast<int2 *>(dev_alloc(ctx, (size_t)nrec * 8));
+    ctx->trace = static_cast<float *>(dev_alloc(ctx, (size_t)std::max(nt_capacity, 1) * nrec * 4));
+    if (!ctx->rec || !ctx->trace) return fail(ctx, LB_ENOMEM, "receiver buffers");
+    cudaError_t e = cudaMemcpyAsync(ctx->rec, xy, (size_t)nrec * 8, cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ctx->trace, 0, (size_t)std::max(nt_capacity, 1) * nrec * 4,
+                            ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "receiver upload");
+    ctx->nrec = nrec;
+    ctx->trace_cap = nt_capacity;
+    if (ctx->refined) return refine_set_receivers(ctx, xy, nrec);
+    return LB_OK;
+}
+
+static lb_status upload_f32(lb_ctx *ctx, const float *src, size_t n, int on_device,
+                            const float **dev, float **tmp) {
+    *tmp = nullptr;
+    if (!src) {
+        *dev = nullptr;
+        return LB_OK;
+    }
+    if (on_device) {
+        *dev = src;
+        return LB_OK;
+    }
+    *tmp = static_cast<float *>(dev_alloc(ctx, n * 4));
+    if (!*tmp) return fail(ctx, LB_ENOMEM, "staging buffer");
+    cudaError_t e = cudaMemcpyAsync(*tmp, src, n * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
+    *dev = *tmp;
+    return LB_OK;
+}
+
+static lb_status set_state_common(lb_ctx *ctx, const float *src, int on_device, int mode) {
+    size_t n = (size_t)ctx->nx * ctx->ny * (mode == 0 ? 1 : ctx->Q);
+    const float *dev = nullptr;
+    float *tmp = nullptr;
+    lb_status st = upload_f32(ctx, src, n, on_device, &dev, &tmp);
+    if (st != LB_OK) return st;
+    StepArgs a = base_args(ctx);
+    a.out = ctx->pop[ctx->cur];
+    ctx->raw = true;
+    long long total = (long long)ctx->ny * ctx->pitch;
+    pick_set(ctx)<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(a, dev, mode);
+    st = check_launch(ctx, "set_state_kernel");
+    if (tmp) {
+        cudaStreamSynchronize(ctx->stream);
+        dev_free(ctx, tmp);
+    }
+    if (st == LB_OK && ctx->refined) st = refine_after_set_state(ctx);
+    return st;
+}
+
+lb_status lb_init_pressure(lb_ctx *ctx, const float *p0, int on_device) {
+    if (!ctx) return LB_EINVAL;
+    ctx->t = 0;
+    ctx->t_rec0 = 0;
+    ctx->fine_ready = false;
+    return set_state_common(ctx, p0, on_device, 0);
+}
+
+lb_status lb_set_state(lb_ctx *ctx, const float *in, int on_device) {
+    if (!ctx) return LB_EINVAL;
+    if (!in) return fail(ctx, LB_EINVAL, "state is NULL");
+    if (ctx->refined) return fail(ctx, LB_ESTATE, "lb_set_state is not available with a patch");
+    return set_state_common(ctx, in, on_device, 1);
+}
+
+static lb_status get_common(lb_ctx *ctx, float *out, int on_device, int mode) {
+    if (!out) return fail(ctx, LB_EINVAL, "out is NULL");
+    size_t n = (size_t)ctx->nx * ctx->ny * (mode == 0 ? 1 : ctx->Q);
+    float *dst = out;
+    if (!on_device) {
+        dst = static_cast<float *>(dev_alloc(ctx, n * 4));
+        if (!dst) return fail(ctx, LB_ENOMEM, "staging buffer");
+    }
+    StepArgs a = base_args(ctx);
+    a.in = ctx->pop[ctx->cur];
+    a.raw = ctx->raw ? 1 : 0;
+    long long total = (long long)ctx->ny * ctx->nx;
+    pick_get(ctx)<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(a, dst, mode);
+    lb_status st = check_launch(ctx, "get_state_kernel");
+    if (st == LB_OK && mode == 0 && ctx->refined) st = refine_overlay_pressure(ctx, dst);
+    cudaError_t e = cudaSuccess;
+    if (st == LB_OK && !on_device)
+        e = cudaMemcpyAsync(out, dst, n * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+    if (!on_device) dev_free(ctx, dst);
+    if (st != LB_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "download");
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "stream");
+    return LB_OK;
+}
+
+lb_status lb_get_pressure(lb_ctx *ctx, float *out, int on_device) {
+    if (!ctx) return LB_EINVAL;
+    return get_common(ctx, out, on_device, 0);
+}
+
+lb_status lb_get_state(lb_ctx *ctx, float *out, int on_device) {
+    if (!ctx) return LB_EINVAL;
+    if (ctx->refined) return fail(ctx, LB_ESTATE, "lb_get_state is not available with a patch");
+    return get_common(ctx, out, on_device, 1);
+}
+
+}  // extern "C"
+
+namespace lbrt {
+
+// One uniform-grid step: state h^{t-1} in pop[cur] -> h^t in pop[cur ^ 1].
+lb_status launch_step(lb_ctx *ctx, StepFn fn, StepArgs &a) {
+    a.in = ctx->pop[ctx->cur];
+    a.out = ctx->pop[ctx->cur ^ 1];
+    a.t = ctx->t;
+    a.raw = ctx->raw ? 1 : 0;
+    ctx->raw = false;
+    long long row = ctx->t - ctx->t_rec0;
+    a.trace_row = (ctx->trace && row >= 0 && row < ctx->trace_cap) ? ctx->trace + row * ctx->nrec
+                                                                  : nullptr;
+    int rec_blocks = a.trace_row ? (ctx->nrec + kThreads - 1) / kThreads : 0;
+    fn<<<a.main_blocks + rec_blocks, kThreads, 0, ctx->stream>>>(a);
+    ctx->cur ^= 1;
+    ctx->t += 1;
+    return LB_OK;
+}
+
+}  // namespace lbrt
+
+extern "C" {
+
+lb_status lb_step(lb_ctx *ctx, int n) {
+    if (!ctx) return LB_EINVAL;
+    if (n < 0) return fail(ctx, LB_EINVAL, "n < 0");
+    if (ctx->refined) return refine_step(ctx, n);
+    StepFn fn = pick_step(ctx);
+    StepArgs a = base_args(ctx);
+    for (int k = 0; k < n; k++) launch_step(ctx, fn, a);
+    return check_launch(ctx, "step_kernel");
+}
+
+lb_status lb_record_receivers(lb_ctx *ctx, float *out, int nt_max, int *nt_out, int on_device) {
+    if (!ctx) return LB_EINVAL;
+    long long rows = std::min<long long>(ctx->t - ctx->t_rec0, ctx->trace_cap);
+    rows = std::max<long long>(0, std::min<long long>(rows, nt_max));
+    if (nt_out) *nt_out = (int)rows;
+    cudaError_t e = cudaSuccess;
+    if (rows > 0 && ctx->nrec > 0) {
+        if (!out) return fail(ctx, LB_EINVAL, "out is NULL");
+        e = cudaMemcpyAsync(out, ctx->trace, (size_t)rows * ctx->nrec * 4,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "trace download");
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "stream");
+    return LB_OK;
+}
+
+lb_status lb_get_time(const lb_ctx *ctx, long long *t) {
+    if (!ctx || !t) return LB_EINVAL;
+    *t = ctx->t;
+    return LB_OK;
+}
+
+lb_status lb_sync(lb_ctx *ctx) {
+    if (!ctx) return LB_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device");
+    return LB_OK;
+}
+
+lb_status lb_info(const lb_ctx *ctx, double *info, int n_info) {
+    if (!ctx || !info) return LB_EINVAL;
+    double v[4];
+    v[0] = ctx->Q;
+    v[1] = ctx->pitch;
+    v[2] = ctx->ebytes;
+    double cs_ref = ctx->Q == 5 ? std::sqrt(0.5)
+                                : std::sqrt(2 * ctx->cfg.w_ref[1] + 4 * ctx->cfg.w_ref[2]);
+    v[3] = (ctx->cfg.dx > 0 && ctx->cfg.c_ref > 0) ? ctx->cfg.dx * cs_ref / ctx->cfg.c_ref : 0.0;
+    for (int k = 0; k < n_info && k < 4; k++) info[k] = v[k];
+    return LB_OK;
+}
+
+const char *lb_last_error(const lb_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+"""ctypes binding of the C ABI in ``include/lbac.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own.  Importing this module loads ``liblbac.so`` from the
+package directory and raises ``ImportError`` if it is missing: there is no
+CPU fallback.  Build it with ``paper_1704_03172_gb300.build.build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbac.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                      "(python -c 'import __graft_entry__ as g; g.build()')")
+_lib = ctypes.CDLL(LIB_PATH)
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE = 0, -1, -2, -3, -4, -5, -6
+LB_D2Q5, LB_D2Q9 = 5, 9
+LB_BGK, LB_MRT = 0, 1
+LB_F32, LB_BF16, LB_F16 = 0, 1, 2
+LB_ZERO_GHOST, LB_PERIODIC = 0, 1
+STATUS_NAMES = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOMEM", -3: "LB_ECUDA",
+                -4: "LB_EUNSTABLE", -5: "LB_ETIMEOUT", -6: "LB_ESTATE"}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class lb_patch(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_int), ("y0", ctypes.c_int), ("nx_c", ctypes.c_int),
+                ("ny_c", ctypes.c_int), ("ratio", ctypes.c_int)]
+
+
+class lb_config(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int), ("collision", ctypes.c_int), ("storage", ctypes.c_int),
+        ("boundary", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("sponge_width", ctypes.c_int), ("sponge_sigma_max", ctypes.c_double),
+        ("c_map", ctypes.POINTER(ctypes.c_float)), ("c_map_on_device", ctypes.c_int),
+        ("c_ref", ctypes.c_double), ("dx", ctypes.c_double), ("tau", ctypes.c_double),
+        ("s", ctypes.c_double * 9), ("w_ref", ctypes.c_double * 3),
+        ("patches", ctypes.POINTER(lb_patch)), ("n_patches", ctypes.c_int),
+        ("cuda_stream", ctypes.c_void_p), ("time_block", ctypes.c_int),
+        ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+    ]
+
+
+class LBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_ctx_p = ctypes.c_void_p
+_fp = ctypes.POINTER(ctypes.c_float)
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_cfgp = ctypes.POINTER(lb_config)
+
+_SIGS = {
+    "lb_config_default": [_cfgp],
+    "lb_create": [_cfgp, ctypes.POINTER(_ctx_p)],
+    "lb_destroy": [_ctx_p],
+    "lb_set_source": [_ctx_p, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int],
+    "lb_set_receivers": [_ctx_p, _ip, ctypes.c_int, ctypes.c_int],
+    "lb_init_pressure": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
+    "lb_step": [_ctx_p, ctypes.c_int],
+    "lb_record_receivers": [_ctx_p, ctypes.c_void_p, ctypes.c_int, _ip, ctypes.c_int],
+    "lb_get_pressure": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
+    "lb_get_state": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
+    "lb_set_state": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
+    "lb_get_time": [_ctx_p, ctypes.POINTER(ctypes.c_longlong)],
+    "lb_sync": [_ctx_p],
+    "lb_footprint": [_cfgp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                     ctypes.POINTER(ctypes.c_size_t)],
+    "lb_info": [_ctx_p, _dp, ctypes.c_int],
+}
+OPTIONAL = {
+    "lb_adjoint": [_ctx_p, _fp, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_int],
+}
+
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+for _name, _args in OPTIONAL.items():
+    if hasattr(_lib, _name):
+        _f = getattr(_lib, _name)
+        _f.argtypes = _args
+        _f.restype = ctypes.c_int
+_lib.lb_last_error.argtypes = [_ctx_p]
+_lib.lb_last_error.restype = ctypes.c_char_p
+
+EXPORTED = sorted(list(_SIGS) + ["lb_last_error"] + [n for n in OPTIONAL if hasattr(_lib, n)])
+
+
+def lb_last_error(ctx=None) -> str:
+    m = _lib.lb_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def _check(status, ctx=None):
+    if status != LB_OK:
+        raise LBError(status, lb_last_error(ctx))
+    return status
+
+
+def lb_config_default() -> lb_config:
+    cfg = lb_config()
+    _check(_lib.lb_config_default(ctypes.byref(cfg)))
+    return cfg
+
+
+def lb_create(cfg: lb_config):
+    ctx = _ctx_p()
+    _check(_lib.lb_create(ctypes.byref(cfg), ctypes.byref(ctx)))
+    return ctx
+
+
+def lb_destroy(ctx):
+    return _check(_lib.lb_destroy(ctx), ctx)
+
+
+def lb_set_source(ctx, x, y, wavelet_ptr, nt):
+    return _check(_lib.lb_set_source(ctx, int(x), int(y), wavelet_ptr, int(nt)), ctx)
+
+
+def lb_set_receivers(ctx, xy_ptr, nrec, nt_capacity):
+    return _check(_lib.lb_set_receivers(ctx, xy_ptr, int(nrec), int(nt_capacity)), ctx)
+
+
+def lb_init_pressure(ctx, p0_ptr, on_device):
+    return _check(_lib.lb_init_pressure(ctx, p0_ptr, int(on_device)), ctx)
+
+
+def lb_step(ctx, n):
+    return _check(_lib.lb_step(ctx, int(n)), ctx)
+
+
+def lb_record_receivers(ctx, out_ptr, nt_max, on_device):
+    nt = ctypes.c_int()
+    _check(_lib.lb_record_receivers(ctx, out_ptr, int(nt_max), ctypes.byref(nt), int(on_device)),
+           ctx)
+    return nt.value
+
+
+def lb_get_pressure(ctx, out_ptr, on_device):
+    return _check(_lib.lb_get_pressure(ctx, out_ptr, int(on_device)), ctx)
+
+
+def lb_get_state(ctx, out_ptr, on_device):
+    return _check(_lib.lb_get_state(ctx, out_ptr, int(on_device)), ctx)
+
+
+def lb_set_state(ctx, in_ptr, on_device):
+    return _check(_lib.lb_set_state(ctx, in_ptr, int(on_device)), ctx)
+
+
+def lb_get_time(ctx) -> int:
+    t = ctypes.c_longlong()
+    _check(_lib.lb_get_time(ctx, ctypes.byref(t)), ctx)
+    return t.value
+
+
+def lb_sync(ctx):
+    return _check(_lib.lb_sync(ctx), ctx)
+
+
+def lb_footprint(cfg: lb_config, nt, nrec, want_adjoint) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.lb_footprint(ctypes.byref(cfg), int(nt), int(nrec), int(want_adjoint),
+                             ctypes.byref(b)))
+    return b.value
+
+
+def lb_info(ctx):
+    v = (ctypes.c_double * 4)()
+    _check(_lib.lb_info(ctx, v, 4), ctx)
+    return list(v)
+
+
+def lb_adjoint(ctx, resid_ptr, nt, checkpoint_every, grad_c_ptr, grad_src_ptr, on_device):
+    return _check(_lib.lb_adjoint(ctx, resid_ptr, int(nt), int(checkpoint_every), grad_c_ptr,
+                                  grad_src_ptr, int(on_device)), ctx)
+
+
+def raw():
+    """The loaded CDLL (for symbol inspection)."""
+    return _lib

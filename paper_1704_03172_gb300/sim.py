@@ -1,0 +1,181 @@
+"""PyTorch-facing wrapper of the C ABI: device memory, streams, tensors in and out.
+
+``LBSim`` owns one ``lb_ctx``.  PyTorch supplies the CUDA stream the library
+runs on and (by default) its caching allocator for every device buffer the
+library allocates; all computation happens in the CUDA kernels of
+``liblbac.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import lbac
+
+_STORAGE = {"f32": lbac.LB_F32, "bf16": lbac.LB_BF16, "f16": lbac.LB_F16}
+_COLL = {"bgk": lbac.LB_BGK, "mrt": lbac.LB_MRT}
+_BOUND = {"zero": lbac.LB_ZERO_GHOST, "periodic": lbac.LB_PERIODIC}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class LBSim:
+    """One linear-LB acoustic simulation ("shot") on the current CUDA device."""
+
+    def __init__(self, c_map, *, lattice=5, collision="bgk", tau=0.5, s=None, storage="f32",
+                 boundary="zero", sponge_width=0, sponge_sigma_max=0.1, c_ref=None,
+                 w_ref=(4 / 9, 1 / 9, 1 / 36), patch=None, dx=0.0, time_block=1,
+                 device=None, stream=None, torch_allocator=True):
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        # A dedicated stream: the legacy default stream's handle is 0, which the C ABI
+        # reads as "create a private stream", so the default stream is never passed.
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        if self.stream.cuda_stream == 0:
+            raise ValueError("pass a non-default torch.cuda.Stream")
+        cfg = lbac.lb_config_default()
+        cfg.lattice = int(lattice)
+        cfg.collision = _COLL[collision] if isinstance(collision, str) else int(collision)
+        cfg.storage = _STORAGE[storage] if isinstance(storage, str) else int(storage)
+        cfg.boundary = _BOUND[boundary] if isinstance(boundary, str) else int(boundary)
+        if torch.is_tensor(c_map):
+            ny, nx = c_map.shape
+        else:
+            c_map = np.ascontiguousarray(c_map, dtype=np.float32)
+            ny, nx = c_map.shape
+        self.nx, self.ny, self.Q = int(nx), int(ny), int(lattice)
+        cfg.nx, cfg.ny = self.nx, self.ny
+        cfg.sponge_width = int(sponge_width)
+        cfg.sponge_sigma_max = float(sponge_sigma_max)
+        cfg.tau = float(tau)
+        if s is not None:
+            for k, v in enumerate(s):
+                cfg.s[k] = float(v)
+        for k in range(3):
+            cfg.w_ref[k] = float(w_ref[k])
+        cfg.dx = float(dx)
+        cfg.time_block = int(time_block)
+        cfg.c_ref = float(c_ref) if c_ref is not None else 0.0
+        if torch.is_tensor(c_map) and c_map.is_cuda:
+            self._cmap_keep = c_map.to(torch.float32).contiguous()
+            cfg.c_map = ctypes.cast(ctypes.c_void_p(self._cmap_keep.data_ptr()),
+                                    ctypes.POINTER(ctypes.c_float))
+            cfg.c_map_on_device = 1
+            if c_ref is None:
+                cfg.c_ref = float(self._cmap_keep.max())
+        else:
+            host = np.ascontiguousarray(c_map.cpu().numpy() if torch.is_tensor(c_map) else c_map,
+                                        dtype=np.float32)
+            self._cmap_keep = host
+            cfg.c_map = host.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        if patch is not None:
+            self._patch = lbac.lb_patch(*[int(v) for v in patch], 2) if len(patch) == 4 else \
+                lbac.lb_patch(*[int(v) for v in patch])
+            cfg.patches = ctypes.pointer(self._patch)
+            cfg.n_patches = 1
+        cfg.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
+        if torch_allocator:
+            dev, strm = self.device, self.stream
+
+            def _alloc(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=strm)
+                except Exception:
+                    return None
+
+            def _free(ptr, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_cb = lbac.ALLOC_FN(_alloc)
+            self._free_cb = lbac.FREE_FN(_free)
+            cfg.dev_alloc = self._alloc_cb
+            cfg.dev_free = self._free_cb
+        self.cfg = cfg
+        with torch.cuda.device(self.device):
+            self.ctx = lbac.lb_create(cfg)
+        self.nrec = 0
+
+    # -- inputs -----------------------------------------------------------------------
+    def set_source(self, x, y, wavelet):
+        w = np.ascontiguousarray(np.asarray(wavelet, dtype=np.float64))
+        lbac.lb_set_source(self.ctx, x, y, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           len(w))
+
+    def set_receivers(self, xy, nt_capacity):
+        xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
+        lbac.lb_set_receivers(self.ctx, xy.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(xy),
+                              nt_capacity)
+        self.nrec = len(xy)
+
+    def init_pressure(self, p0=None):
+        if p0 is None:
+            lbac.lb_init_pressure(self.ctx, None, 0)
+            return
+        t = torch.as_tensor(p0, dtype=torch.float32, device=self.device).contiguous()
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        lbac.lb_init_pressure(self.ctx, _ptr(t), 1)
+        self.stream.synchronize()
+
+    def set_state(self, g):
+        t = torch.as_tensor(g, dtype=torch.float32, device=self.device).contiguous()
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        lbac.lb_set_state(self.ctx, _ptr(t), 1)
+        self.stream.synchronize()
+
+    # -- stepping -----------------------------------------------------------------------
+    def step(self, n=1):
+        lbac.lb_step(self.ctx, n)
+
+    def sync(self):
+        lbac.lb_sync(self.ctx)
+
+    @property
+    def time(self):
+        return lbac.lb_get_time(self.ctx)
+
+    # -- outputs ------------------------------------------------------------------------
+    def _out(self, shape):
+        with torch.cuda.stream(self.stream):
+            return torch.zeros(shape, dtype=torch.float32, device=self.device)
+
+    def traces(self, nt_max=None):
+        """Receiver traces [rows, nrec] (row n = pressure at time n); synchronises."""
+        nt_max = self.time if nt_max is None else nt_max
+        out = self._out((max(nt_max, 0), max(self.nrec, 1)))
+        n = lbac.lb_record_receivers(self.ctx, _ptr(out), nt_max, 1)
+        return out[:n, :self.nrec]
+
+    def pressure(self):
+        out = self._out((self.ny, self.nx))
+        lbac.lb_get_pressure(self.ctx, _ptr(out), 1)
+        return out
+
+    def state(self):
+        out = self._out((self.Q, self.ny, self.nx))
+        lbac.lb_get_state(self.ctx, _ptr(out), 1)
+        return out
+
+    def info(self):
+        return lbac.lb_info(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbac.lb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,166 @@
+"""GPU parity of the fused LB step (CUDA, FP32 storage) against the FP64 oracle.
+
+Every case feeds the same seeded inputs to both sides through the C ABI
+(``LBSim`` -> ``liblbac.so``) and to ``oracle``.  Tolerance: relative L2
+<= 1e-5 on the state / pressure and on the receiver traces (FP32 arithmetic
+over the stated number of steps), plus an element-wise bound.
+"""
+import numpy as np
+import pytest
+
+from paper_1704_03172_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sim_cls():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_03172_gb300 import build
+    build.build()
+    from paper_1704_03172_gb300.sim import LBSim
+    return LBSim
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _pair(sim_cls, oracle, Q, nx, ny, c, *, collision="bgk", tau=0.5, s=None, periodic=False,
+          sponge=0, smax=0.1, w_ref=(4 / 9, 1 / 9, 1 / 36), source=None, rec=None, steps=1,
+          nt_cap=None, c_ref=1.0):
+    sim = sim_cls(c, lattice=Q, collision=collision, tau=tau, s=s, c_ref=c_ref,
+                  boundary="periodic" if periodic else "zero", sponge_width=sponge,
+                  sponge_sigma_max=smax, w_ref=w_ref)
+    P = oracle.Problem(Q, nx, ny, c, c_ref=c_ref, periodic=periodic, mrt=collision == "mrt",
+                       tau=tau, s=s, w_ref=w_ref, sponge_width=sponge, sponge_sigma_max=smax,
+                       source=source, receivers=rec)
+    if source is not None:
+        sim.set_source(*source)
+    if rec is not None:
+        sim.set_receivers(rec, nt_cap if nt_cap is not None else steps)
+    return sim, P
+
+
+CASES = [
+    # Q, collision, tau, periodic, nx, ny, steps
+    (5, "bgk", 0.5, True, 128, 128, 200),
+    (5, "bgk", 1.0, False, 37, 29, 120),
+    (5, "mrt", 0.5, False, 130, 7, 90),
+    (5, "mrt", 0.5, True, 1, 50, 40),
+    (5, "bgk", 0.7, False, 300, 1, 40),
+    (5, "bgk", 0.5, False, 257, 131, 150),
+    (9, "bgk", 0.5, False, 67, 45, 80),
+    (9, "mrt", 0.5, True, 64, 64, 100),
+    (9, "mrt", 0.5, False, 129, 33, 60),
+    (9, "bgk", 0.9, True, 5, 3, 30),
+]
+
+
+@pytest.mark.parametrize("Q,coll,tau,periodic,nx,ny,steps", CASES)
+def test_step_matches_oracle_small(sim_cls, oracle_mod, Q, coll, tau, periodic, nx, ny, steps):
+    rng = np.random.default_rng(nx * 1000 + ny + Q)
+    c = W.random_medium(nx, ny, rng.integers(1 << 30), 0.45, 1.0)
+    s = W.mrt_rates(Q, 7) if coll == "mrt" else None
+    if Q == 9 and coll == "mrt":
+        s = [1.0, 1.0, 1.0, 1.6, 1.3, 1.5, 1.2, 1.2, 1.3]
+    w_ref = (0.4, 0.11, 0.04) if Q == 9 else (4 / 9, 1 / 9, 1 / 36)
+    src = (int(rng.integers(nx)), int(rng.integers(ny)), rng.normal(size=steps // 2))
+    rec = np.stack([rng.integers(0, nx, 7), rng.integers(0, ny, 7)], 1).astype(np.int32)
+    sponge = 0 if periodic else min(4, max(0, min(nx, ny) // 3))
+    sim, P = _pair(sim_cls, oracle_mod, Q, nx, ny, c, collision=coll, tau=tau, s=s,
+                   periodic=periodic, sponge=sponge, w_ref=w_ref, source=src, rec=rec,
+                   steps=steps)
+    g0 = rng.normal(size=(Q, ny, nx)).astype(np.float32)
+    sim.set_state(g0)
+    sim.step(steps)
+    gs = sim.state().cpu().numpy()
+    tr = sim.traces().cpu().numpy()
+    ps = sim.pressure().cpu().numpy()
+    sim.close()
+    go, tro = oracle_mod.run(P, g0.astype(np.float64), steps)
+    assert rel(gs, go) < TOL
+    assert np.abs(gs - go).max() < 10 * TOL * np.abs(go).max()
+    assert rel(tr, tro) < TOL
+    assert rel(ps, oracle_mod.pressure(P, go)) < TOL
+
+
+def test_state_roundtrip_and_zero_steps(sim_cls, oracle_mod):
+    nx, ny = 45, 33
+    c = W.random_medium(nx, ny, 3, 0.5, 1.0)
+    sim = sim_cls(c, lattice=5, c_ref=1.0)
+    g0 = np.random.default_rng(1).normal(size=(5, ny, nx)).astype(np.float32)
+    sim.set_state(g0)
+    sim.step(0)
+    np.testing.assert_array_equal(sim.state().cpu().numpy(), g0)
+    sim.close()
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.5])
+def test_gaussian_pulse_128_periodic_500_steps(sim_cls, oracle_mod, tau):
+    n, steps = 128, 500
+    c = W.uniform_map(n, n, 1.0)
+    p0 = W.gaussian_pulse(n, n, 64, 64, 4.0, 1e-3).astype(np.float32)
+    rec = W.ring_receivers(64, 64, 32, [0, 15, 30, 45])
+    sim, P = _pair(sim_cls, oracle_mod, 5, n, n, c, tau=tau, periodic=True, rec=rec, steps=steps)
+    sim.init_pressure(p0)
+    sim.step(steps)
+    ps = sim.pressure().cpu().numpy()
+    tr = sim.traces().cpu().numpy()
+    sim.close()
+    g = oracle_mod.init_pressure(P, p0.astype(np.float64))
+    g, tro = oracle_mod.run(P, g, steps)
+    assert rel(ps, oracle_mod.pressure(P, g)) < TOL
+    assert rel(tr, tro) < TOL
+
+
+@pytest.mark.parametrize("Q,coll", [(5, "bgk"), (5, "mrt"), (9, "bgk"), (9, "mrt")])
+def test_two_layer_full_length_reduced_grid(sim_cls, oracle_mod, Q, coll):
+    # the two-layer workload (contrast 1:2, sponge, Ricker source, line of receivers)
+    # run for its full 5000 steps on a 256^2 version of the grid
+    wl = W.two_layer_workload(256, lattice=Q, collision=coll, nrec=64)
+    if Q == 9 and coll == "mrt":
+        wl["s"] = [1.0, 1.0, 1.0, 2.0, 2.0, 2.0, 1.0, 1.0, 2.0]
+    steps = wl["steps"]
+    sim, P = _pair(sim_cls, oracle_mod, Q, 256, 256, wl["c_map"], collision=coll,
+                   tau=wl["tau"], s=wl.get("s"), sponge=wl["sponge_width"],
+                   smax=wl["sponge_sigma_max"], w_ref=wl["w_ref"], source=wl["source"],
+                   rec=wl["receivers"], steps=steps, c_ref=wl["c_ref"])
+    snap = 300                 # the wavefront is inside the grid at this time
+    sim.init_pressure(None)
+    sim.step(snap)
+    ps = sim.pressure().cpu().numpy()
+    sim.step(steps - snap)
+    tr = sim.traces().cpu().numpy()
+    sim.close()
+    g, tro1 = oracle_mod.run(P, P.zeros(), snap)
+    assert rel(ps, oracle_mod.pressure(P, g)) < TOL
+    _, tro2 = oracle_mod.run(P, g, steps - snap, t0=snap)
+    assert rel(tr, np.concatenate([tro1, tro2])) < TOL
+
+
+@pytest.mark.parametrize("Q,coll,steps", [(5, "bgk", 30), (9, "mrt", 12)])
+def test_two_layer_4096_bench_configuration(sim_cls, oracle_mod, Q, coll, steps):
+    # full-size grid, same lb_step launch path the benchmark times; a random
+    # initial state so that every site carries signal from the first step
+    wl = W.two_layer_workload(4096, lattice=Q, collision=coll)
+    n = 4096
+    sim, P = _pair(sim_cls, oracle_mod, Q, n, n, wl["c_map"], collision=coll, tau=wl["tau"],
+                   s=wl.get("s"), sponge=wl["sponge_width"], smax=wl["sponge_sigma_max"],
+                   w_ref=wl["w_ref"], source=(wl["source"][0], wl["source"][1],
+                                               np.linspace(1, -1, steps)),
+                   rec=wl["receivers"], steps=steps, c_ref=wl["c_ref"])
+    rng = np.random.default_rng(5)
+    g0 = rng.normal(size=(Q, n, n)).astype(np.float32)
+    sim.set_state(g0)
+    sim.step(steps)
+    gs = sim.state().cpu().numpy()
+    tr = sim.traces().cpu().numpy()
+    sim.close()
+    go, tro = oracle_mod.run(P, g0.astype(np.float64), steps)
+    assert rel(gs, go) < TOL
+    assert rel(tr, tro) < TOL
