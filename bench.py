@@ -321,7 +321,8 @@ def run_ours(args):
     }
     if not args.no_variants:
         v = {}
-        for lat, st, coll in ((5, "f32", "mrt"), (9, "f32", "bgk"), (9, "f32", "mrt")):
+        for lat, st, coll in ((5, "bf16", "bgk"), (5, "f16", "bgk"), (5, "f32", "mrt"),
+                              (9, "f32", "bgk"), (9, "f32", "mrt"), (9, "bf16", "bgk")):
             try:
                 v[f"d2q{lat}_{coll}_{st}"] = _variant(torch, LBSim, lat, st, coll,
                                                        max(200, args.steps // 5), 10)

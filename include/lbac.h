@@ -141,6 +141,17 @@ lb_status lb_get_time(const lb_ctx *ctx, long long *t);
 /* Wait for all queued work; LB_ECUDA if any of it failed. */
 lb_status lb_sync(lb_ctx *ctx);
 
+/* FP64 invariants of the current state g(t), reduced on the device in a fixed
+ * order (bit-reproducible): out[0] = mass sum_x rho(x), out[1] = energy
+ * sum_x sum_i g_i^2 / w_i(x) over w_i > 0 (conserved by a tau = 1/2 step on a
+ * homogeneous periodic grid, because g^eq is the W^-1-orthogonal projection of g
+ * -- Eq. linear eqm dist -- and the collision reflects g about it),
+ * out[2] = max |g_i|, out[3] = number of non-finite values.  out: host [4].
+ * Returns LB_EUNSTABLE (with out filled) when out[3] > 0.  Uses a scratch
+ * array of 4 ny + 4 doubles that the context allocates on first use.
+ * Synchronises the stream. */
+lb_status lb_invariants(lb_ctx *ctx, double *out);
+
 /* Device bytes lb_create would allocate for cfg, plus the receiver trace for
  * nt steps when nrec > 0, plus adjoint checkpoints when want_adjoint. */
 lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint, size_t *bytes);

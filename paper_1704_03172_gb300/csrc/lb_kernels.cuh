@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace lbk {
 
@@ -72,9 +73,38 @@ struct StepArgs {
     const int2 *rec;
     int nrec;
     float *trace_row;        // pressure row for time t, or null
-    // 16-bit storage: value = stored * in_scale[i]; stored = value * out_inv[i]
-    float in_scale[9], out_inv[9];
+    // 16-bit storage (per-population power-of-two scale, value = stored * scale).
+    // Three device slots rotate: the input buffer's scale and max |value| are read,
+    // the output buffer's are written, and the third max slot is cleared for the
+    // next step.  All nullptr for FP32 storage.
+    const float *scale_in;    // [9]
+    float *scale_out;         // [9], written by block 0
+    const unsigned *max_in;   // [9][kMaxCopies] float bits of max |value| of `in`
+    unsigned *max_out;        // [9][kMaxCopies] accumulated max |value| of `out`
+    unsigned *max_clear;      // [9][kMaxCopies] zeroed for the next step
 };
+
+constexpr int kMaxCopies = 8;          // spread of the per-block atomicMax targets
+constexpr float kStoredTarget = 8192.f; // 16-bit: |stored| <= 2^13 for the predicted bound
+
+// smallest power of two >= r (r > 0, finite), clamped to normal floats
+__host__ __device__ inline float pow2_ceil(float r) {
+    if (!(r > 0.f)) return 1.f;
+    unsigned b;
+    memcpy(&b, &r, 4);
+    int e = (int)((b >> 23) & 0xffu);
+    if (b & 0x7fffffu) e += 1;
+    if (e < 1) e = 1;
+    if (e > 254) e = 254;
+    unsigned o = (unsigned)e << 23;
+    float f;
+    memcpy(&f, &o, 4);
+    return f;
+}
+
+__device__ __forceinline__ float scale_of(const float *scale, int i) {
+    return scale ? scale[i] : 1.f;
+}
 
 // ---------------------------------------------------------------- storage --
 template <typename ST> struct Store;
@@ -297,19 +327,42 @@ __device__ __forceinline__ void gather_receivers(const StepArgs &a, int r) {
         } else if (xs < 0 || xs >= a.nx || ys < 0 || ys >= a.ny) {
             continue;
         }
-        rho += Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch + xs) * a.in_scale[i];
+        rho += Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch + xs) *
+               scale_of(a.scale_in, i);
     }
     a.trace_row[r] = cs2_of<Q>(a.eta2[(long long)xy.y * a.pitch + xy.x], a) * rho;
 }
 
 // -------------------------------------------------------------------- step --
-template <int Q, bool MRT, bool PERIODIC, typename ST>
-__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
-    if ((int)blockIdx.x >= a.main_blocks) {
-        gather_receivers<Q, PERIODIC, ST>(a, ((int)blockIdx.x - a.main_blocks) * kThreads +
-                                                 (int)threadIdx.x);
-        return;
+// 16-bit prologue (thread i < Q): scale of the input buffer, and the output
+// scale predicted from its max: |out| <= 8 max|in| + |S[t]| is kept below
+// kStoredTarget (8x headroom again before FP16 overflows).
+template <int Q>
+__device__ __forceinline__ void scale_prologue(const StepArgs &a, int i, float *s_in,
+                                               float *s_oinv) {
+    const float sin_ = a.scale_in[i];
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < kMaxCopies; c++) m = fmaxf(m, __uint_as_float(a.max_in[i * kMaxCopies + c]));
+    const float S = (a.src_tab && a.t >= 0 && a.t < a.src_nt) ? fabsf(a.src_tab[a.t]) : 0.f;
+    const float bound = 8.f * m + S;
+    const float so = bound > 0.f ? pow2_ceil(bound * (1.f / kStoredTarget)) : sin_;
+    s_in[i] = sin_;
+    s_oinv[i] = 1.f / so;  // exact: so is a power of two
+    if (blockIdx.x == 0) {
+        a.scale_out[i] = so;
+#pragma unroll
+        for (int c = 0; c < kMaxCopies; c++) a.max_clear[i * kMaxCopies + c] = 0u;
     }
+}
+
+// The sites of one warp row-segment; tmax receives this thread's max |out_i|.
+template <int Q, bool MRT, bool PERIODIC, typename ST>
+__device__ __forceinline__ void step_sites(const StepArgs &a, const float *s_in,
+                                          const float *s_oinv, float tmax[Q]) {
+    constexpr bool LP = Store<ST>::kBytes == 2;
+#pragma unroll
+    for (int i = 0; i < Q; i++) tmax[i] = 0.f;
     const int lane = threadIdx.x & 31;
     const int wid = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int y = wid / a.segs;
@@ -321,21 +374,22 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     float g[Q][4];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
+        const float sc = LP ? s_in[i] : 1.f;
         if (a.raw) {  // warp-uniform: first step after lb_set_state, read g(t) in place
             pull4<0, PERIODIC>(in + i * a.plane + (long long)y * a.pitch, x0, lane, a.nx, active,
-                               a.in_scale[i], g[i]);
+                               sc, g[i]);
             continue;
         }
         const ST *row = src_row<PERIODIC>(in + i * a.plane, y - Lat<Q>::cy(i), a.ny, a.pitch);
         const int cx = Lat<Q>::cx(i);
         if (cx == 1)
-            pull4<1, PERIODIC>(row, x0, lane, a.nx, active, a.in_scale[i], g[i]);
+            pull4<1, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
         else if (cx == -1)
-            pull4<-1, PERIODIC>(row, x0, lane, a.nx, active, a.in_scale[i], g[i]);
+            pull4<-1, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
         else
-            pull4<0, PERIODIC>(row, x0, lane, a.nx, active, a.in_scale[i], g[i]);
+            pull4<0, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
     }
-    if (!active) return;  // no more shuffles below
+    if (!active) return;  // no shuffles below
 
     float4 e2v = *reinterpret_cast<const float4 *>(a.eta2 + (long long)y * a.pitch + x0);
     const float e2s[4] = {e2v.x, e2v.y, e2v.z, e2v.w};
@@ -368,9 +422,52 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     ST *o = static_cast<ST *>(a.out) + (long long)y * a.pitch + x0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        float sc = a.out_inv[i];
-        Store<ST>::store4(o + i * a.plane, make_float4(out[i][0] * sc, out[i][1] * sc,
-                                                       out[i][2] * sc, out[i][3] * sc));
+        if (LP) {
+            const float sc = s_oinv[i];
+            tmax[i] = fmaxf(fmaxf(fabsf(out[i][0]), fabsf(out[i][1])),
+                            fmaxf(fabsf(out[i][2]), fabsf(out[i][3])));
+            Store<ST>::store4(o + i * a.plane, make_float4(out[i][0] * sc, out[i][1] * sc,
+                                                           out[i][2] * sc, out[i][3] * sc));
+        } else {
+            Store<ST>::store4(o + i * a.plane,
+                              make_float4(out[i][0], out[i][1], out[i][2], out[i][3]));
+        }
+    }
+}
+
+template <int Q, bool MRT, bool PERIODIC, typename ST>
+__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
+    constexpr bool LP = Store<ST>::kBytes == 2;
+    __shared__ float s_in[9], s_oinv[9];
+    __shared__ float s_wmax[LP ? 9 : 1][kWarps];
+    if (LP) {
+        if ((int)threadIdx.x < Q) scale_prologue<Q>(a, threadIdx.x, s_in, s_oinv);
+        __syncthreads();
+    }
+    if ((int)blockIdx.x >= a.main_blocks) {  // block-uniform
+        gather_receivers<Q, PERIODIC, ST>(a, ((int)blockIdx.x - a.main_blocks) * kThreads +
+                                                 (int)threadIdx.x);
+        return;
+    }
+    float tmax[Q];
+    step_sites<Q, MRT, PERIODIC, ST>(a, s_in, s_oinv, tmax);
+    if (LP) {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            float m = tmax[i];
+            for (int off = 16; off > 0; off >>= 1)
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+            if (lane == 0) s_wmax[LP ? i : 0][w] = m;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < Q) {
+            float m = 0.f;
+#pragma unroll
+            for (int k = 0; k < kWarps; k++) m = fmaxf(m, s_wmax[LP ? threadIdx.x : 0][k]);
+            atomicMax(a.max_out + threadIdx.x * kMaxCopies + (blockIdx.x % kMaxCopies),
+                      __float_as_uint(m));
+        }
     }
 }
 
@@ -395,7 +492,7 @@ __global__ void set_state_kernel(StepArgs a, const float *src, int mode) {
                 v = src[(long long)i * a.nx * a.ny + (long long)y * a.nx + x];
             }
         }
-        Store<ST>::store1(o + i * a.plane + idx, v * a.out_inv[i]);
+        Store<ST>::store1(o + i * a.plane + idx, v / scale_of(a.scale_out, i));
     }
 }
 
@@ -418,15 +515,58 @@ __global__ void get_state_kernel(StepArgs a, float *dst, int mode) {
         } else {
             ok = xs >= 0 && xs < a.nx && ys >= 0 && ys < a.ny;
         }
-        if (ok) v = Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch + xs) * a.in_scale[i];
+        if (ok)
+            v = Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch + xs) *
+                scale_of(a.scale_in, i);
         if (mode == 1) dst[(long long)i * total + idx] = v;
         rho += v;
     }
     if (mode == 0) dst[idx] = cs2_of<Q>(a.eta2[(long long)y * a.pitch + x], a) * rho;
 }
 
+// 16-bit initial scale: max |g_i| of the state to be written (same value rule as
+// set_state_kernel) accumulated into max_out[i][*].
+template <int Q>
+__global__ void source_max_kernel(StepArgs a, const float *src, int mode) {
+    long long total = (long long)a.ny * a.nx;
+    float m[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) m[i] = 0.f;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int y = (int)(idx / a.nx), x = (int)(idx - (long long)y * a.nx);
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            float v;
+            if (mode == 0) {
+                float e2 = a.eta2[(long long)y * a.pitch + x];
+                v = weight_i<Q>(i, e2, a) / cs2_of<Q>(e2, a) * src[idx];
+            } else {
+                v = src[(long long)i * total + idx];
+            }
+            m[i] = fmaxf(m[i], fabsf(v));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        float v = m[i];
+        for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+        if ((threadIdx.x & 31) == 0)
+            atomicMax(a.max_out + i * kMaxCopies + (blockIdx.x % kMaxCopies), __float_as_uint(v));
+    }
+}
+
+// scale_out[i] = power of two keeping max |g_i| at or below kStoredTarget
+static __global__ void init_scale_kernel(StepArgs a, int Q) {
+    int i = threadIdx.x;
+    if (i >= Q) return;
+    float m = 0.f;
+    for (int c = 0; c < kMaxCopies; c++) m = fmaxf(m, __uint_as_float(a.max_out[i * kMaxCopies + c]));
+    a.scale_out[i] = m > 0.f ? pow2_ceil(m * (1.f / kStoredTarget)) : 1.f;
+}
+
 // eta^2 = (c / c_ref)^2 per site (pads 0); flags: bit0 c <= 0 or non-finite, bit1 eta > 1.
-__global__ void medium_kernel(const float *c_map, float *eta2, int nx, int ny, int pitch,
+static __global__ void medium_kernel(const float *c_map, float *eta2, int nx, int ny, int pitch,
                               double inv_cref, unsigned *flags) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)ny * pitch) return;

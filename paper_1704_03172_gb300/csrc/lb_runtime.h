@@ -18,6 +18,10 @@ struct lb_ctx {
     int cur = 0;                    // pop[cur] holds the post-collision state of step t-1
     bool raw = false;               // ... or, when raw, the state g(t) itself (unshifted)
     float *eta2 = nullptr;          // [ny][pitch] (c / c_ref)^2
+    float *lp_scale = nullptr;      // 16-bit storage: [3][9] per-population scales (slots)
+    unsigned *lp_max = nullptr;     // 16-bit storage: [3][9][kMaxCopies] max |value| (slots)
+    int lp_slot = 0;                // slot describing the current buffer
+    double *inv_scratch = nullptr;  // lb_invariants: [ny][4] row partials + [4] result
     float *src_tab = nullptr;
     int src_nt = 0, src_x = 0, src_y = 0;
     int2 *rec = nullptr;
@@ -39,6 +43,8 @@ struct lb_ctx {
 };
 
 namespace lbrt {
+// scale pointers of the current buffer (nullptr for FP32 storage)
+const float *current_scale(const lb_ctx *ctx);
 lb_status fail(lb_ctx *ctx, lb_status st, const char *fmt, ...);
 lb_status cuda_fail(lb_ctx *ctx, cudaError_t e, const char *what);
 void *dev_alloc(lb_ctx *ctx, size_t bytes);

@@ -95,11 +95,15 @@ StepArgs base_args(const lb_ctx *c) {
     a.src_y = c->src_y;
     a.rec = c->rec;
     a.nrec = c->nrec;
-    for (int i = 0; i < 9; i++) {
-        a.in_scale[i] = 1.f;
-        a.out_inv[i] = 1.f;
+    if (c->lp_scale) {
+        a.scale_in = c->lp_scale + c->lp_slot * 9;
+        a.max_in = c->lp_max + c->lp_slot * 9 * kMaxCopies;
     }
     return a;
+}
+
+const float *current_scale(const lb_ctx *ctx) {
+    return ctx->lp_scale ? ctx->lp_scale + ctx->lp_slot * 9 : nullptr;
 }
 
 // ------------------------------------------------------- kernel dispatch --
@@ -282,6 +286,15 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     c->eta2 = static_cast<float *>(dev_alloc(c, plane * 4));
     unsigned *flags = static_cast<unsigned *>(dev_alloc(c, 256));
     if (!c->eta2 || !flags) return bail(fail(c, LB_ENOMEM, "medium buffer"));
+    if (cfg->storage != LB_F32) {
+        c->lp_scale = static_cast<float *>(dev_alloc(c, 3 * 9 * sizeof(float)));
+        c->lp_max = static_cast<unsigned *>(dev_alloc(c, 3 * 9 * kMaxCopies * sizeof(unsigned)));
+        if (!c->lp_scale || !c->lp_max) return bail(fail(c, LB_ENOMEM, "scale buffers"));
+        std::vector<float> ones(27, 1.f);
+        cudaMemcpyAsync(c->lp_scale, ones.data(), 27 * sizeof(float), cudaMemcpyHostToDevice,
+                        c->stream);
+        cudaMemsetAsync(c->lp_max, 0, 3 * 9 * kMaxCopies * sizeof(unsigned), c->stream);
+    }
     // medium: c_map -> eta^2 (Eq. 0th lattice weight), on the device
     const float *cmap_dev = cfg->c_map;
     float *staging = nullptr;
@@ -422,6 +435,19 @@ static lb_status set_state_common(lb_ctx *ctx, const float *src, int on_device, 
     StepArgs a = base_args(ctx);
     a.out = ctx->pop[ctx->cur];
     ctx->raw = true;
+    if (ctx->lp_scale) {
+        // 16-bit: fresh slots; the scale of the written state comes from its own max
+        cudaMemsetAsync(ctx->lp_max, 0, 3 * 9 * kMaxCopies * sizeof(unsigned), ctx->stream);
+        a.scale_out = ctx->lp_scale + ctx->lp_slot * 9;
+        a.max_out = ctx->lp_max + ctx->lp_slot * 9 * kMaxCopies;
+        if (dev) {
+            if (ctx->Q == 9)
+                source_max_kernel<9><<<1024, 256, 0, ctx->stream>>>(a, dev, mode);
+            else
+                source_max_kernel<5><<<1024, 256, 0, ctx->stream>>>(a, dev, mode);
+        }
+        init_scale_kernel<<<1, 32, 0, ctx->stream>>>(a, ctx->Q);
+    }
     long long total = (long long)ctx->ny * ctx->pitch;
     pick_set(ctx)<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(a, dev, mode);
     st = check_launch(ctx, "set_state_kernel");
@@ -494,6 +520,15 @@ lb_status launch_step(lb_ctx *ctx, StepFn fn, StepArgs &a) {
     a.in = ctx->pop[ctx->cur];
     a.out = ctx->pop[ctx->cur ^ 1];
     a.t = ctx->t;
+    if (ctx->lp_scale) {
+        const int s0 = ctx->lp_slot, s1 = (s0 + 1) % 3, s2 = (s0 + 2) % 3;
+        a.scale_in = ctx->lp_scale + s0 * 9;
+        a.scale_out = ctx->lp_scale + s1 * 9;
+        a.max_in = ctx->lp_max + s0 * 9 * kMaxCopies;
+        a.max_out = ctx->lp_max + s1 * 9 * kMaxCopies;
+        a.max_clear = ctx->lp_max + s2 * 9 * kMaxCopies;
+        ctx->lp_slot = s1;
+    }
     a.raw = ctx->raw ? 1 : 0;
     ctx->raw = false;
     long long row = ctx->t - ctx->t_rec0;

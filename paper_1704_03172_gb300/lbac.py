@@ -78,6 +78,7 @@ _SIGS = {
     "lb_footprint": [_cfgp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                      ctypes.POINTER(ctypes.c_size_t)],
     "lb_info": [_ctx_p, _dp, ctypes.c_int],
+    "lb_invariants": [_ctx_p, _dp],
 }
 OPTIONAL = {
     "lb_adjoint": [_ctx_p, _fp, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_int],
@@ -181,6 +182,13 @@ def lb_info(ctx):
     v = (ctypes.c_double * 4)()
     _check(_lib.lb_info(ctx, v, 4), ctx)
     return list(v)
+
+
+def lb_invariants(ctx):
+    """(mass, energy, max |g|, non-finite count); raises LBError(LB_EUNSTABLE) on non-finite."""
+    v = (ctypes.c_double * 4)()
+    _check(_lib.lb_invariants(ctx, v), ctx)
+    return tuple(v)
 
 
 def lb_adjoint(ctx, resid_ptr, nt, checkpoint_every, grad_c_ptr, grad_src_ptr, on_device):

@@ -160,6 +160,10 @@ class LBSim:
         lbac.lb_get_state(self.ctx, _ptr(out), 1)
         return out
 
+    def invariants(self):
+        """(mass, energy, max |g|, non-finite count) of the current state, FP64."""
+        return lbac.lb_invariants(self.ctx)
+
     def info(self):
         return lbac.lb_info(self.ctx)
 
