@@ -152,6 +152,36 @@ lb_status lb_sync(lb_ctx *ctx);
  * Synchronises the stream. */
 lb_status lb_invariants(lb_ctx *ctx, double *out);
 
+/* lb_invariants without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at the
+ * point of the call -- code running under a fixed device-memory budget that
+ * another framework owns, real-time loops where an allocation (and the
+ * implicit synchronisation cudaMalloc/cudaFree may bring) is not allowed, or
+ * code that has no lb_ctx at all.  It computes the same four FP64 values as
+ * lb_invariants, with the same kernels and summation order, from caller
+ * buffers:
+ *   g       device, [Q][ny][nx] FP32 populations at one time (the layout
+ *           lb_get_state writes), Q = lattice
+ *   c_map   device, [ny][nx] FP32 sound speed; eta = c / c_ref
+ *   w_ref   host, D2Q9 reference weights (w0, w1, w5); ignored for D2Q5
+ *   out     device, 4 doubles: mass, energy, max |g|, non-finite count
+ *   cuda_stream  cudaStream_t to queue on (NULL: the legacy default stream)
+ * The work is queued asynchronously; nothing is copied to the host.  Zero-ghost
+ * (non-periodic) state only.
+ * Scratch: a file-scope static device array of 16384 x 4 + 4 doubles
+ * (512 KiB), held by every GPU that loads the library until the process exits.
+ * ny > 16384 (or nx * ny > 2^31) is rejected with LB_EINVAL and a message in
+ * lb_last_error(NULL).  No cudaMalloc, cudaFree or other allocating routine is
+ * called.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Every call on a device shares the
+ * same array and each call overwrites every part of it that it reads, so
+ * nothing needs clearing; calls that overlap on the GPU (other streams, or
+ * other host threads) race on the array and must be serialised by the caller. */
+lb_status lb_invariants_noalloc(const float *g, const float *c_map, int lattice, int nx,
+                                int ny, double c_ref, const double *w_ref, double *out,
+                                void *cuda_stream);
+
 /* Device bytes lb_create would allocate for cfg, plus the receiver trace for
  * nt steps when nrec > 0, plus adjoint checkpoints when want_adjoint. */
 lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint, size_t *bytes);

@@ -9,8 +9,10 @@
 // over rows); pass 2 reduces the row partials in one block.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <string>
 
 #include "lb_kernels.cuh"
 #include "lb_runtime.h"
@@ -152,6 +154,80 @@ cudaError_t launch(const InvArgs &a, int Q, int storage, double *partial, double
 }
 
 }  // namespace lbinv
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  Its scratch (the per-row partials of pass 1) is this
+// file-scope device array instead of memory from cudaMalloc: every GPU that
+// loads the library holds it (512 KiB) until the process exits.  Host code
+// must not pass the symbol itself to a kernel -- on the host it names a
+// stand-in, not device memory -- so its device address is looked up once per
+// device with cudaGetSymbolAddress and cached.
+#define LB_NOALLOC_MAX_ROWS 16384
+static __device__ __align__(256) double g_noalloc_partial[LB_NOALLOC_MAX_ROWS * 4 + 4];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::atomic<double *> g_noalloc_addr[kMaxDevices];
+
+lb_status noalloc_fail(lb_status st, const std::string &msg) {
+    lbrt::fail(nullptr, st, "%s", msg.c_str());  // reported by lb_last_error(NULL)
+    return st;
+}
+}  // namespace
+
+extern "C" lb_status lb_invariants_noalloc(const float *g, const float *c_map, int lattice,
+                                           int nx, int ny, double c_ref, const double *w_ref,
+                                           double *out, void *cuda_stream) {
+    if (!g || !c_map || !out) return noalloc_fail(LB_EINVAL, "g, c_map and out must be non-NULL");
+    if (lattice != LB_D2Q5 && lattice != LB_D2Q9)
+        return noalloc_fail(LB_EINVAL, "lattice must be LB_D2Q5 or LB_D2Q9");
+    if (nx < 1 || ny < 1) return noalloc_fail(LB_EINVAL, "nx and ny must be >= 1");
+    if (ny > LB_NOALLOC_MAX_ROWS)
+        return noalloc_fail(LB_EINVAL, "ny = " + std::to_string(ny) + " exceeds the " +
+                                           std::to_string(LB_NOALLOC_MAX_ROWS) +
+                                           "-row limit of the static scratch array");
+    if ((long long)nx * ny > (1LL << 31)) return noalloc_fail(LB_EINVAL, "nx * ny exceeds 2^31");
+    if (!(c_ref > 0.0)) return noalloc_fail(LB_EINVAL, "c_ref must be > 0");
+    if (lattice == LB_D2Q9 && !w_ref) return noalloc_fail(LB_EINVAL, "D2Q9 needs w_ref");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(LB_ECUDA, std::string("cudaGetDevice: ") +
+                                                            cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(LB_EINVAL, "device ordinal too large");
+    double *scratch = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!scratch) {  // set-up: once per device, with that device current
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+        if (e != cudaSuccess || !p)
+            return noalloc_fail(LB_ECUDA, std::string("cudaGetSymbolAddress: ") +
+                                              cudaGetErrorString(e));
+        scratch = static_cast<double *>(p);
+        g_noalloc_addr[dev].store(scratch, std::memory_order_release);
+    }
+    lbinv::InvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pop = g;
+    a.raw = 1;  // g holds the populations at their own sites
+    a.periodic = 0;
+    a.eta2 = nullptr;
+    a.c_map = c_map;
+    a.inv_cref = 1.0 / c_ref;
+    a.nx = nx;
+    a.ny = ny;
+    a.pitch = nx;
+    a.plane = (long long)nx * ny;
+    a.scale_in = nullptr;
+    if (lattice == LB_D2Q9) {
+        a.w1r = (float)w_ref[1];
+        a.w5r = (float)w_ref[2];
+    }
+    // every partial that pass 2 reads is written by pass 1 of the same call, so the
+    // array needs no clearing between calls
+    e = lbinv::launch(a, lattice, LB_F32, scratch, out, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return noalloc_fail(LB_ECUDA, std::string("launch: ") +
+                                                            cudaGetErrorString(e));
+    return LB_OK;
+}
 
 using namespace lbrt;
 

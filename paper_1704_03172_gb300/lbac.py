@@ -79,6 +79,9 @@ _SIGS = {
                      ctypes.POINTER(ctypes.c_size_t)],
     "lb_info": [_ctx_p, _dp, ctypes.c_int],
     "lb_invariants": [_ctx_p, _dp],
+    "lb_invariants_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_int, ctypes.c_double, _dp, ctypes.c_void_p,
+                              ctypes.c_void_p],
 }
 OPTIONAL = {
     "lb_adjoint": [_ctx_p, _fp, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_int],
@@ -189,6 +192,13 @@ def lb_invariants(ctx):
     v = (ctypes.c_double * 4)()
     _check(_lib.lb_invariants(ctx, v), ctx)
     return tuple(v)
+
+
+def lb_invariants_noalloc(g_ptr, c_map_ptr, lattice, nx, ny, c_ref, w_ref, out_ptr, stream):
+    """Allocation-free lb_invariants on caller device buffers (results stay on the device)."""
+    wr = (ctypes.c_double * 3)(*w_ref) if w_ref is not None else None
+    return _check(_lib.lb_invariants_noalloc(g_ptr, c_map_ptr, int(lattice), int(nx), int(ny),
+                                             float(c_ref), wr, out_ptr, stream))
 
 
 def lb_adjoint(ctx, resid_ptr, nt, checkpoint_every, grad_c_ptr, grad_src_ptr, on_device):

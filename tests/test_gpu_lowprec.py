@@ -148,9 +148,9 @@ def test_lowprec_two_layer_full_length(sim_cls, oracle_mod, storage, Q):
 
 
 def test_f16_scale_follows_a_large_source(sim_cls, oracle_mod):
-    # a source 1e6 times larger than usual: the per-population scale keeps FP16 finite
+    # a source 1e8 times larger than usual: the per-population scale keeps FP16 finite
     n, steps = 96, 400
-    wav = 1e6 * W.ricker(steps, 0.03)
+    wav = 1e8 * W.ricker(steps, 0.03)
     rec = np.array([[20, 48], [70, 48]], np.int32)
     sim = sim_cls(W.uniform_map(n, n, 1.0), lattice=5, tau=0.5, c_ref=1.0, storage="f16",
                   sponge_width=10)
