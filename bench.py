@@ -163,6 +163,27 @@ def _variant(torch, LBSim, lattice, storage, collision, steps, warmup):
             "achieved_gbs": round(glups * bps, 1), "ms_per_step": round(sec / steps * 1e3, 4)}
 
 
+def _refined_variant(torch, LBSim, steps, warmup):
+    """Slow-block workload: 2048^2 coarse grid + 1025^2-node fine patch (2x in space and
+    time).  One fine site-step counts as one update: 2048^2 + 2 * 1025^2 per coarse step."""
+    wl = W.refined_block_workload(2048)
+    sim = LBSim(wl["c_map"], lattice=5, collision="mrt", s=wl["s"], c_ref=wl["c_ref"],
+                sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"],
+                patch=wl["patch"])
+    sim.set_source(*wl["source"])
+    sim.set_receivers(wl["receivers"], steps + warmup)
+    sim.init_pressure(None)
+    try:
+        sec = _time_steps(torch, sim, steps, warmup)
+    finally:
+        sim.close()
+    nf = 2 * wl["patch"][2] + 1
+    updates = 2048 * 2048 + 2 * nf * nf
+    return {"glups": round(updates * steps / sec / 1e9, 2), "updates_per_coarse_step": updates,
+            "ms_per_coarse_step": round(sec / steps * 1e3, 4),
+            "launches_per_coarse_step": 7}
+
+
 def _e2e(torch, LBSim, steps_shot):
     """One full shot through the public API with host buffers (create .. traces .. destroy)."""
     from paper_1704_03172_gb300.sim import LBSim as _S  # noqa: F401
@@ -328,6 +349,10 @@ def run_ours(args):
                                                        max(200, args.steps // 5), 10)
             except Exception as ex:  # report, do not hide
                 v[f"d2q{lat}_{coll}_{st}"] = {"error": str(ex)[:200]}
+        try:
+            v["refined_block_2048_d2q5_mrt_f32"] = _refined_variant(torch, LBSim, 400, 10)
+        except Exception as ex:
+            v["refined_block_2048_d2q5_mrt_f32"] = {"error": str(ex)[:200]}
         line["variants"] = v
     if not args.no_e2e:
         line["e2e"] = _e2e(torch, LBSim, args.e2e_steps)

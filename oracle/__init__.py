@@ -94,8 +94,79 @@ def _declare(L):
         _declare_adjoint(L)
 
 
-def _declare_refine(L):  # filled in by the refinement oracle
-    pass
+def _declare_refine(L):
+    vp = ctypes.c_void_p
+    L.orc_ref_create.argtypes = [_pp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.orc_ref_create.restype = vp
+    L.orc_ref_destroy.argtypes = [vp]
+    L.orc_ref_destroy.restype = None
+    L.orc_ref_dims.argtypes = [vp, _ip, _ip]
+    L.orc_ref_fine_cmap.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    L.orc_ref_init_pressure.argtypes = [vp, _dp]
+    L.orc_ref_run.argtypes = [vp, ctypes.c_int, _dp]
+    L.orc_ref_pressure.argtypes = [vp, _dp]
+    L.orc_ref_fine_pressure.argtypes = [vp, _dp]
+    L.orc_ref_states.argtypes = [vp, _dp, _dp]
+    for n in ("orc_ref_dims", "orc_ref_fine_cmap", "orc_ref_init_pressure", "orc_ref_run",
+              "orc_ref_pressure", "orc_ref_fine_pressure", "orc_ref_states"):
+        getattr(L, n).restype = ctypes.c_int
+
+
+class Refined:
+    """Two-level refined run (Sec. 4): coarse Problem P plus a patch of coarse cells
+    [x0, x0 + nxp] x [y0, y0 + nyp] refined by 2 in space and time."""
+
+    def __init__(self, P: "Problem", x0, y0, nxp, nyp):
+        self.P = P
+        self._S = P._struct()
+        self.h = lib().orc_ref_create(ctypes.byref(self._S), int(x0), int(y0), int(nxp), int(nyp))
+        if not self.h:
+            raise ValueError("invalid patch")
+        nxf, nyf = ctypes.c_int(), ctypes.c_int()
+        self.nI = lib().orc_ref_dims(self.h, ctypes.byref(nxf), ctypes.byref(nyf))
+        self.nxf, self.nyf = nxf.value, nyf.value
+        self.t = 0
+
+    def fine_cmap(self):
+        cf = np.zeros((self.nyf, self.nxf), np.float32)
+        lib().orc_ref_fine_cmap(self.h, _ptr(cf, ctypes.c_float))
+        return cf
+
+    def init_pressure(self, p0=None):
+        p = None if p0 is None else np.ascontiguousarray(p0, np.float64).reshape(self.P.ny,
+                                                                                  self.P.nx)
+        lib().orc_ref_init_pressure(self.h, _ptr(p, ctypes.c_double) if p is not None else None)
+        self.t = 0
+
+    def run(self, nsteps):
+        trace = np.zeros((nsteps, len(self.P.receivers)))
+        lib().orc_ref_run(self.h, int(nsteps), _ptr(trace, ctypes.c_double))
+        self.t += nsteps
+        return trace
+
+    def pressure(self):
+        p = np.zeros((self.P.ny, self.P.nx))
+        lib().orc_ref_pressure(self.h, _ptr(p, ctypes.c_double))
+        return p
+
+    def fine_pressure(self):
+        p = np.zeros((self.nyf, self.nxf))
+        lib().orc_ref_fine_pressure(self.h, _ptr(p, ctypes.c_double))
+        return p
+
+    def states(self):
+        gc = np.zeros((self.P.Q, self.P.ny, self.P.nx))
+        gf = np.zeros((self.P.Q, self.nyf, self.nxf))
+        lib().orc_ref_states(self.h, _ptr(gc, ctypes.c_double), _ptr(gf, ctypes.c_double))
+        return gc, gf
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().orc_ref_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
 
 
 def _declare_adjoint(L):  # filled in by the adjoint oracle

@@ -315,3 +315,19 @@ int orc_max_threads(void) {
     return 1;
 #endif
 }
+
+/* Exported for the refinement and adjoint oracles (same library). */
+void orc_collide_site(int Q, int mrt, double tau, const double *s, const double *Minv,
+                      const double *w, double cs2, const double *g, double *gs) {
+    collide_with(Q, mrt, tau, s, Minv, w, cs2, g, gs);
+}
+
+void orc_step_grid(const orc_problem *P, const double *Minv, int t, const double *g, double *gn) {
+    step(P, Minv, t, g, gn);
+}
+
+void orc_record(const orc_problem *P, const double *g, double *row) { record(P, g, row); }
+
+void orc_site_weights(const orc_problem *P, size_t idx, double *w, double *cs2) {
+    site_weights(P, idx, w, cs2);
+}

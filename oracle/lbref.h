@@ -46,4 +46,22 @@ int orc_pressure(const orc_problem *P, const double *g, double *p);
 int orc_run(const orc_problem *P, double *g, int t0, int nsteps, double *trace);
 int orc_max_threads(void);
 
+/* building blocks shared by the oracle's own files (refinement, adjoint) */
+void orc_collide_site(int Q, int mrt, double tau, const double *s, const double *Minv,
+                      const double *w, double cs2, const double *g, double *gs);
+void orc_step_grid(const orc_problem *P, const double *Minv, int t, const double *g, double *gn);
+void orc_record(const orc_problem *P, const double *g, double *row);
+void orc_site_weights(const orc_problem *P, size_t idx, double *w, double *cs2);
+
+/* Two-level refinement (Sec. 4), lbrefine.c.  Opaque handle. */
+void *orc_ref_create(const orc_problem *coarse, int x0, int y0, int nxp, int nyp);
+void orc_ref_destroy(void *h);
+int orc_ref_dims(void *h, int *nxf, int *nyf);
+int orc_ref_fine_cmap(void *h, float *cf);
+int orc_ref_init_pressure(void *h, const double *p0);
+int orc_ref_run(void *h, int nsteps, double *trace);
+int orc_ref_pressure(void *h, double *p);
+int orc_ref_fine_pressure(void *h, double *pf);
+int orc_ref_states(void *h, double *gc, double *gf);
+
 #endif

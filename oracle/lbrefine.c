@@ -1,0 +1,348 @@
+/*
+ * lbrefine.c -- FP64 oracle of the two-level grid refinement of Sec. 4 of
+ * arXiv:1704.03172 (after Dupuis and Chopard).  TEST INFRASTRUCTURE: used only
+ * by the tests, the smoke check and the CPU-baseline leg of the benchmark.
+ *
+ * Geometry.  The coarse grid covers the whole domain.  A patch of coarse cells
+ * [x0, x0 + nxp] x [y0, y0 + nyp] (closed rectangle of coarse nodes) is covered
+ * by a fine grid with spacing and time step halved (n = 2): fine node (a, b),
+ * 0 <= a <= 2 nxp, 0 <= b <= 2 nyp, sits at coarse position
+ * (x0 + a/2, y0 + b/2).  The fine sound speed is the coarse c_map interpolated
+ * bilinearly to the fine nodes (rounded to float), so both grids share eta and
+ * hence the lattice sound speed; the physical speed is continuous.
+ * The interface I is the rectangle's boundary, a line of nodes of both grids.
+ *
+ * Coupling (Eq. grid refinement eqm dist, Eq. coarse-fine dist connect): the
+ * equilibrium part is shared and the non-equilibrium part is scaled,
+ *   fine   <- coarse:  g^f = g^eq + (g^c - g^eq) / n,
+ *   coarse <- fine:    g^c = g^eq + (g^f - g^eq) * n,
+ * with g^eq formed from the moments of the transferred vector and the
+ * receiving grid's weights.  "Specifying the direction of wave propagation"
+ * is read per population: at a fine node of I the populations whose upstream
+ * node x - c_i lies outside the fine grid come from the coarse grid; at a
+ * coarse node of I the populations whose upstream node lies strictly inside
+ * the patch come from the fine grid.  The coarse grid keeps evolving under the
+ * patch (its overlap with the fine domain), which supplies the full coarse
+ * vector at I for the coarse -> fine transfer.
+ *
+ * Time sequence per coarse step T -> T+1 (Sec. 4, itemised procedure):
+ *   record the pressure at time T;
+ *   coarse collide + stream -> coarse state at T+1 (provisional on I); keep its
+ *     values on I, U(T+1);
+ *   fine step 2T -> 2T+1, then set the coarse-side populations on I from the
+ *     spatial (linear along I) and temporal (midpoint) interpolation of U(T),
+ *     U(T+1);
+ *   fine step 2T+1 -> 2T+2, then the same from U(T+1);
+ *   correct the coarse populations on I from the fine state at 2T+2.
+ * The same coupling is applied once to the initial state (time 0).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lbref.h"
+
+typedef struct {
+    orc_problem C, F;
+    int x0, y0, nxp, nyp, nxf, nyf, nI;
+    float *cf;
+    double *gc, *gf, *tc, *tf, *Uprev, *Unext;
+    int *Ix, *Iy, *idxI;
+    double Minv[81];
+    long t;
+} ref_t;
+
+static const int V5[5][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+static const int V9[9][2] = {{0, 0},  {1, 0},  {0, 1},   {-1, 0}, {0, -1},
+                             {1, 1},  {-1, 1}, {-1, -1}, {1, -1}};
+
+static const int (*vel(int Q))[2] { return Q == 9 ? V9 : V5; }
+
+static int on_I(const ref_t *R, int X, int Y) {
+    if (X < R->x0 || X > R->x0 + R->nxp || Y < R->y0 || Y > R->y0 + R->nyp) return 0;
+    return X == R->x0 || X == R->x0 + R->nxp || Y == R->y0 || Y == R->y0 + R->nyp;
+}
+
+static int strictly_inside(const ref_t *R, int X, int Y) {
+    return X > R->x0 && X < R->x0 + R->nxp && Y > R->y0 && Y < R->y0 + R->nyp;
+}
+
+static int in_closed_patch(const ref_t *R, int X, int Y) {
+    return X >= R->x0 && X <= R->x0 + R->nxp && Y >= R->y0 && Y <= R->y0 + R->nyp;
+}
+
+static const double *U_at(const ref_t *R, const double *U, int X, int Y) {
+    int k = R->idxI[(Y - R->y0) * (R->nxp + 1) + (X - R->x0)];
+    return U + (size_t)k * R->C.Q;
+}
+
+static void snapshot(const ref_t *R, const double *gc, double *U) {
+    const int Q = R->C.Q;
+    const size_t N = (size_t)R->C.nx * R->C.ny;
+    for (int k = 0; k < R->nI; k++)
+        for (int i = 0; i < Q; i++)
+            U[(size_t)k * Q + i] = gc[(size_t)i * N + (size_t)R->Iy[k] * R->C.nx + R->Ix[k]];
+}
+
+/* coarse -> fine on I: ghat = (1 - alpha) Ua + alpha Ub, interpolated along I */
+static void c2f(const ref_t *R, double *gf, const double *Ua, const double *Ub, double alpha) {
+    const int Q = R->C.Q;
+    const int(*cv)[2] = vel(Q);
+    const size_t Nf = (size_t)R->nxf * R->nyf;
+    for (int b = 0; b < R->nyf; b++) {
+        for (int a = 0; a < R->nxf; a++) {
+            if (!(a == 0 || a == R->nxf - 1 || b == 0 || b == R->nyf - 1)) continue;
+            int X = R->x0 + a / 2, Y = R->y0 + b / 2;
+            const double *pa[2], *pb[2];
+            int np = 1;
+            pa[0] = U_at(R, Ua, X, Y);
+            pb[0] = U_at(R, Ub, X, Y);
+            if (a % 2 == 1) {
+                pa[1] = U_at(R, Ua, X + 1, Y);
+                pb[1] = U_at(R, Ub, X + 1, Y);
+                np = 2;
+            } else if (b % 2 == 1) {
+                pa[1] = U_at(R, Ua, X, Y + 1);
+                pb[1] = U_at(R, Ub, X, Y + 1);
+                np = 2;
+            }
+            double gh[9], rho = 0, jx = 0, jy = 0;
+            for (int i = 0; i < Q; i++) {
+                double s = 0;
+                for (int k = 0; k < np; k++) s += (1.0 - alpha) * pa[k][i] + alpha * pb[k][i];
+                gh[i] = s / np;
+                rho += gh[i];
+                jx += cv[i][0] * gh[i];
+                jy += cv[i][1] * gh[i];
+            }
+            double w[9], cs2, geq[9];
+            orc_site_weights(&R->F, (size_t)b * R->nxf + a, w, &cs2);
+            orc_equilibrium(Q, w, cs2, rho, jx, jy, geq);
+            for (int i = 0; i < Q; i++) {
+                int ua = a - cv[i][0], ub = b - cv[i][1];
+                if (ua >= 0 && ua < R->nxf && ub >= 0 && ub < R->nyf) continue;  /* from fine */
+                gf[(size_t)i * Nf + (size_t)b * R->nxf + a] = geq[i] + (gh[i] - geq[i]) / 2.0;
+            }
+        }
+    }
+}
+
+/* fine -> coarse on I */
+static void f2c(const ref_t *R, double *gc, const double *gf) {
+    const int Q = R->C.Q;
+    const int(*cv)[2] = vel(Q);
+    const size_t N = (size_t)R->C.nx * R->C.ny, Nf = (size_t)R->nxf * R->nyf;
+    for (int k = 0; k < R->nI; k++) {
+        int X = R->Ix[k], Y = R->Iy[k];
+        size_t fidx = (size_t)(2 * (Y - R->y0)) * R->nxf + 2 * (X - R->x0);
+        double G[9], rho = 0, jx = 0, jy = 0;
+        for (int i = 0; i < Q; i++) {
+            G[i] = gf[(size_t)i * Nf + fidx];
+            rho += G[i];
+            jx += cv[i][0] * G[i];
+            jy += cv[i][1] * G[i];
+        }
+        double w[9], cs2, geq[9];
+        size_t cidx = (size_t)Y * R->C.nx + X;
+        orc_site_weights(&R->C, cidx, w, &cs2);
+        orc_equilibrium(Q, w, cs2, rho, jx, jy, geq);
+        for (int i = 0; i < Q; i++)
+            if (strictly_inside(R, X - cv[i][0], Y - cv[i][1]))
+                gc[(size_t)i * N + cidx] = geq[i] + (G[i] - geq[i]) * 2.0;
+    }
+}
+
+void *orc_ref_create(const orc_problem *coarse, int x0, int y0, int nxp, int nyp) {
+    if (!coarse || nxp < 1 || nyp < 1 || x0 < 1 || y0 < 1 || x0 + nxp > coarse->nx - 2 ||
+        y0 + nyp > coarse->ny - 2)
+        return NULL;
+    ref_t *R = (ref_t *)calloc(1, sizeof(ref_t));
+    R->C = *coarse;
+    R->x0 = x0;
+    R->y0 = y0;
+    R->nxp = nxp;
+    R->nyp = nyp;
+    R->nxf = 2 * nxp + 1;
+    R->nyf = 2 * nyp + 1;
+    const int Q = coarse->Q, nx = coarse->nx;
+    const size_t N = (size_t)nx * coarse->ny, Nf = (size_t)R->nxf * R->nyf;
+    /* fine medium: bilinear interpolation of the coarse sound speed */
+    R->cf = (float *)malloc(sizeof(float) * Nf);
+    for (int b = 0; b < R->nyf; b++)
+        for (int a = 0; a < R->nxf; a++) {
+            int X = x0 + a / 2, Y = y0 + b / 2, ox = a % 2, oy = b % 2;
+            double s = 0;
+            int cnt = 0;
+            for (int dy = 0; dy <= oy; dy++)
+                for (int dx = 0; dx <= ox; dx++) {
+                    s += (double)coarse->c_map[(size_t)(Y + dy) * nx + X + dx];
+                    cnt++;
+                }
+            R->cf[(size_t)b * R->nxf + a] = (float)(s / cnt);
+        }
+    memset(&R->F, 0, sizeof(R->F));
+    R->F.Q = Q;
+    R->F.nx = R->nxf;
+    R->F.ny = R->nyf;
+    R->F.periodic = 0;
+    R->F.mrt = coarse->mrt;
+    R->F.tau = coarse->tau;
+    memcpy(R->F.s, coarse->s, sizeof(R->F.s));
+    memcpy(R->F.w_ref, coarse->w_ref, sizeof(R->F.w_ref));
+    R->F.c_map = R->cf;
+    R->F.c_ref = coarse->c_ref;
+    R->F.nthreads = coarse->nthreads;
+    /* interface nodes */
+    R->idxI = (int *)malloc(sizeof(int) * (nxp + 1) * (nyp + 1));
+    R->Ix = (int *)malloc(sizeof(int) * 2 * (nxp + nyp + 2));
+    R->Iy = (int *)malloc(sizeof(int) * 2 * (nxp + nyp + 2));
+    for (int Y = y0; Y <= y0 + nyp; Y++)
+        for (int X = x0; X <= x0 + nxp; X++) {
+            int *slot = &R->idxI[(Y - y0) * (nxp + 1) + (X - x0)];
+            *slot = -1;
+            if (on_I(R, X, Y)) {
+                *slot = R->nI;
+                R->Ix[R->nI] = X;
+                R->Iy[R->nI] = Y;
+                R->nI++;
+            }
+        }
+    R->gc = (double *)calloc((size_t)Q * N, sizeof(double));
+    R->tc = (double *)calloc((size_t)Q * N, sizeof(double));
+    R->gf = (double *)calloc((size_t)Q * Nf, sizeof(double));
+    R->tf = (double *)calloc((size_t)Q * Nf, sizeof(double));
+    R->Uprev = (double *)calloc((size_t)Q * R->nI, sizeof(double));
+    R->Unext = (double *)calloc((size_t)Q * R->nI, sizeof(double));
+    orc_moment_inverse(Q, R->Minv);
+    return R;
+}
+
+void orc_ref_destroy(void *h) {
+    ref_t *R = (ref_t *)h;
+    if (!R) return;
+    free(R->cf);
+    free(R->idxI);
+    free(R->Ix);
+    free(R->Iy);
+    free(R->gc);
+    free(R->tc);
+    free(R->gf);
+    free(R->tf);
+    free(R->Uprev);
+    free(R->Unext);
+    free(R);
+}
+
+int orc_ref_dims(void *h, int *nxf, int *nyf) {
+    ref_t *R = (ref_t *)h;
+    *nxf = R->nxf;
+    *nyf = R->nyf;
+    return R->nI;
+}
+
+int orc_ref_fine_cmap(void *h, float *cf) {
+    ref_t *R = (ref_t *)h;
+    memcpy(cf, R->cf, sizeof(float) * R->nxf * R->nyf);
+    return 0;
+}
+
+/* g = g^eq(p0 / c_s^2, 0) on both grids (p0 interpolated bilinearly to the fine
+ * nodes), then the coupling at time 0. */
+int orc_ref_init_pressure(void *h, const double *p0) {
+    ref_t *R = (ref_t *)h;
+    const int nx = R->C.nx;
+    const size_t Nf = (size_t)R->nxf * R->nyf;
+    orc_init_pressure(&R->C, p0, R->gc);
+    double *pf = NULL;
+    if (p0) {
+        pf = (double *)malloc(sizeof(double) * Nf);
+        for (int b = 0; b < R->nyf; b++)
+            for (int a = 0; a < R->nxf; a++) {
+                int X = R->x0 + a / 2, Y = R->y0 + b / 2, ox = a % 2, oy = b % 2, cnt = 0;
+                double s = 0;
+                for (int dy = 0; dy <= oy; dy++)
+                    for (int dx = 0; dx <= ox; dx++) {
+                        s += p0[(size_t)(Y + dy) * nx + X + dx];
+                        cnt++;
+                    }
+                pf[(size_t)b * R->nxf + a] = s / cnt;
+            }
+    }
+    orc_init_pressure(&R->F, pf, R->gf);
+    free(pf);
+    snapshot(R, R->gc, R->Uprev);
+    c2f(R, R->gf, R->Uprev, R->Uprev, 1.0);
+    f2c(R, R->gc, R->gf);
+    R->t = 0;
+    return 0;
+}
+
+static void record_all(const ref_t *R, double *row) {
+    const orc_problem *C = &R->C;
+    const size_t N = (size_t)C->nx * C->ny, Nf = (size_t)R->nxf * R->nyf;
+    for (int r = 0; r < C->nrec; r++) {
+        int X = C->rec_xy[2 * r], Y = C->rec_xy[2 * r + 1];
+        double w[9], cs2, rho = 0;
+        if (in_closed_patch(R, X, Y)) {
+            size_t fidx = (size_t)(2 * (Y - R->y0)) * R->nxf + 2 * (X - R->x0);
+            orc_site_weights(&R->F, fidx, w, &cs2);
+            for (int i = 0; i < C->Q; i++) rho += R->gf[(size_t)i * Nf + fidx];
+        } else {
+            size_t idx = (size_t)Y * C->nx + X;
+            orc_site_weights(C, idx, w, &cs2);
+            for (int i = 0; i < C->Q; i++) rho += R->gc[(size_t)i * N + idx];
+        }
+        row[r] = cs2 * rho;
+    }
+}
+
+int orc_ref_run(void *h, int nsteps, double *trace) {
+    ref_t *R = (ref_t *)h;
+    for (int k = 0; k < nsteps; k++) {
+        long T = R->t;
+        if (trace && R->C.nrec > 0) record_all(R, trace + (size_t)k * R->C.nrec);
+        orc_step_grid(&R->C, R->Minv, (int)T, R->gc, R->tc); /* provisional coarse T+1 */
+        snapshot(R, R->tc, R->Unext);
+        orc_step_grid(&R->F, R->Minv, 0, R->gf, R->tf); /* fine 2T -> 2T+1 */
+        c2f(R, R->tf, R->Uprev, R->Unext, 0.5);
+        orc_step_grid(&R->F, R->Minv, 0, R->tf, R->gf); /* fine 2T+1 -> 2T+2 */
+        c2f(R, R->gf, R->Uprev, R->Unext, 1.0);
+        f2c(R, R->tc, R->gf);
+        double *s = R->gc;
+        R->gc = R->tc;
+        R->tc = s;
+        s = R->Uprev;
+        R->Uprev = R->Unext;
+        R->Unext = s;
+        R->t++;
+    }
+    return 0;
+}
+
+/* pressure on the coarse grid; nodes of the closed patch from the fine grid */
+int orc_ref_pressure(void *h, double *p) {
+    ref_t *R = (ref_t *)h;
+    const size_t Nf = (size_t)R->nxf * R->nyf;
+    orc_pressure(&R->C, R->gc, p);
+    for (int Y = R->y0; Y <= R->y0 + R->nyp; Y++)
+        for (int X = R->x0; X <= R->x0 + R->nxp; X++) {
+            size_t fidx = (size_t)(2 * (Y - R->y0)) * R->nxf + 2 * (X - R->x0);
+            double w[9], cs2, rho = 0;
+            orc_site_weights(&R->F, fidx, w, &cs2);
+            for (int i = 0; i < R->C.Q; i++) rho += R->gf[(size_t)i * Nf + fidx];
+            p[(size_t)Y * R->C.nx + X] = cs2 * rho;
+        }
+    return 0;
+}
+
+int orc_ref_fine_pressure(void *h, double *pf) {
+    ref_t *R = (ref_t *)h;
+    return orc_pressure(&R->F, R->gf, pf);
+}
+
+int orc_ref_states(void *h, double *gc, double *gf) {
+    ref_t *R = (ref_t *)h;
+    if (gc) memcpy(gc, R->gc, sizeof(double) * R->C.Q * R->C.nx * R->C.ny);
+    if (gf) memcpy(gf, R->gf, sizeof(double) * R->C.Q * R->nxf * R->nyf);
+    return 0;
+}

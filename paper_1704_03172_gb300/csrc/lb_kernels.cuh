@@ -73,6 +73,7 @@ struct StepArgs {
     const int2 *rec;
     int nrec;
     float *trace_row;        // pressure row for time t, or null
+    const int *rec_col;      // column of receiver r in the trace row (nullptr: r)
     // 16-bit storage (per-population power-of-two scale, value = stored * scale).
     // Three device slots rotate: the input buffer's scale and max |value| are read,
     // the output buffer's are written, and the third max slot is cleared for the
@@ -330,7 +331,8 @@ __device__ __forceinline__ void gather_receivers(const StepArgs &a, int r) {
         rho += Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch + xs) *
                scale_of(a.scale_in, i);
     }
-    a.trace_row[r] = cs2_of<Q>(a.eta2[(long long)xy.y * a.pitch + xy.x], a) * rho;
+    a.trace_row[a.rec_col ? a.rec_col[r] : r] =
+        cs2_of<Q>(a.eta2[(long long)xy.y * a.pitch + xy.x], a) * rho;
 }
 
 // -------------------------------------------------------------------- step --

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "lbac.h"
+#include "lb_kernels.cuh"
 
 struct lb_refine;  // two-level grid refinement state (refine.cu)
 
@@ -43,6 +44,14 @@ struct lb_ctx {
 };
 
 namespace lbrt {
+using StepFn = void (*)(const lbk::StepArgs);
+using GetFn = void (*)(lbk::StepArgs, float *, int);
+lbk::StepArgs base_args(const lb_ctx *c);
+StepFn pick_step_for(int Q, bool mrt, bool periodic, int storage);
+StepFn pick_step(const lb_ctx *c);
+GetFn pick_get_for(int Q, bool periodic, int storage);
+lb_status check_launch(lb_ctx *ctx, const char *what);
+int round_up(int v, int m);
 // scale pointers of the current buffer (nullptr for FP32 storage)
 const float *current_scale(const lb_ctx *ctx);
 lb_status fail(lb_ctx *ctx, lb_status st, const char *fmt, ...);
@@ -56,6 +65,6 @@ lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev
 void refine_destroy(lb_ctx *ctx);
 bool refine_contains(const lb_ctx *ctx, int x, int y);
 lb_status refine_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
-lb_status refine_after_set_state(lb_ctx *ctx);
+lb_status refine_after_set_state(lb_ctx *ctx, const float *p0_dev);
 lb_status refine_step(lb_ctx *ctx, int n);
 lb_status refine_overlay_pressure(lb_ctx *ctx, float *p_dev);

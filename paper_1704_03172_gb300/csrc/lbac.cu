@@ -107,9 +107,7 @@ const float *current_scale(const lb_ctx *ctx) {
 }
 
 // ------------------------------------------------------- kernel dispatch --
-using StepFn = void (*)(const StepArgs);
 using SetFn = void (*)(StepArgs, const float *, int);
-using GetFn = void (*)(StepArgs, float *, int);
 
 template <int Q, bool MRT, bool PER, typename ST> StepFn step_fn() {
     return step_kernel<Q, MRT, PER, ST>;
@@ -125,13 +123,17 @@ template <typename ST> StepFn step_fn_q(int Q, bool mrt, bool per) {
     return Q == 9 ? step_fn_c<9, ST>(mrt, per) : step_fn_c<5, ST>(mrt, per);
 }
 
-StepFn pick_step(const lb_ctx *c) {
-    bool mrt = c->cfg.collision == LB_MRT, per = c->cfg.boundary == LB_PERIODIC;
-    switch (c->cfg.storage) {
-        case LB_BF16: return step_fn_q<__nv_bfloat16>(c->Q, mrt, per);
-        case LB_F16: return step_fn_q<__half>(c->Q, mrt, per);
-        default: return step_fn_q<float>(c->Q, mrt, per);
+StepFn pick_step_for(int Q, bool mrt, bool per, int storage) {
+    switch (storage) {
+        case LB_BF16: return step_fn_q<__nv_bfloat16>(Q, mrt, per);
+        case LB_F16: return step_fn_q<__half>(Q, mrt, per);
+        default: return step_fn_q<float>(Q, mrt, per);
     }
+}
+
+StepFn pick_step(const lb_ctx *c) {
+    return pick_step_for(c->Q, c->cfg.collision == LB_MRT, c->cfg.boundary == LB_PERIODIC,
+                         c->cfg.storage);
 }
 
 template <int Q, typename ST> SetFn set_fn_q(bool per) {
@@ -154,13 +156,16 @@ template <int Q, typename ST> GetFn get_fn_q(bool per) {
 template <typename ST> GetFn get_fn(int Q, bool per) {
     return Q == 9 ? get_fn_q<9, ST>(per) : get_fn_q<5, ST>(per);
 }
-GetFn pick_get(const lb_ctx *c) {
-    bool per = c->cfg.boundary == LB_PERIODIC;
-    switch (c->cfg.storage) {
-        case LB_BF16: return get_fn<__nv_bfloat16>(c->Q, per);
-        case LB_F16: return get_fn<__half>(c->Q, per);
-        default: return get_fn<float>(c->Q, per);
+GetFn pick_get_for(int Q, bool per, int storage) {
+    switch (storage) {
+        case LB_BF16: return get_fn<__nv_bfloat16>(Q, per);
+        case LB_F16: return get_fn<__half>(Q, per);
+        default: return get_fn<float>(Q, per);
     }
+}
+
+GetFn pick_get(const lb_ctx *c) {
+    return pick_get_for(c->Q, c->cfg.boundary == LB_PERIODIC, c->cfg.storage);
 }
 
 lb_status check_launch(lb_ctx *ctx, const char *what) {
@@ -328,12 +333,12 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "medium setup"));
     dev_free(c, flags);
-    if (staging) dev_free(c, staging);
     if (hflags & 1u) return bail(fail(c, LB_EINVAL, "c_map must be finite and > 0"));
     if (hflags & 2u) return bail(fail(c, LB_EINVAL, "c_map exceeds c_ref (eta > 1)"));
     if (cfg->n_patches > 0) {
         if ((st = refine_setup(c, cfg, cmap_dev)) != LB_OK) return bail(st);
     }
+    if (staging) dev_free(c, staging);
     *out = c;
     return LB_OK;
 }
@@ -451,11 +456,11 @@ static lb_status set_state_common(lb_ctx *ctx, const float *src, int on_device, 
     long long total = (long long)ctx->ny * ctx->pitch;
     pick_set(ctx)<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(a, dev, mode);
     st = check_launch(ctx, "set_state_kernel");
+    if (st == LB_OK && ctx->refined) st = refine_after_set_state(ctx, dev);
     if (tmp) {
         cudaStreamSynchronize(ctx->stream);
         dev_free(ctx, tmp);
     }
-    if (st == LB_OK && ctx->refined) st = refine_after_set_state(ctx);
     return st;
 }
 

@@ -142,3 +142,26 @@ def two_layer_workload(n=4096, lattice=5, collision="bgk", seed=DEFAULT_SEED + 2
     if collision == "mrt":
         d["s"] = mrt_rates(lattice, seed)
     return d
+
+
+def refined_block_workload(n=2048, nrec=256, steps=4000):
+    """Grid-refinement workload: coarse n^2 grid (eta = 1 background), a slow block
+    (c = c_ref / 3) of 448/2048 n coarse cells at the centre, covered by a refined
+    patch of n/4 coarse cells (= n/2 fine cells) with a margin of n/64 coarse cells;
+    Ricker source at (n/4, n/2); receivers on the line y = n/2 crossing the patch.
+    Central wavelength 32/2048 n coarse cells in the background."""
+    s = n / 2048.0
+    bw = int(round(448 * s))
+    b0 = (n - bw) // 2
+    margin = max(1, int(round(32 * s)))
+    nxp = bw + 2 * margin
+    x0 = b0 - margin
+    c = block_model(n, n, b0, b0, bw, bw, 1.0, 1.0 / 3.0)
+    fc = (0.5 ** 0.5) / (32.0 * s)
+    src = (n // 4, n // 2, ricker(steps, fc))
+    lo, hi = n // 8, n - n // 8
+    rec = line_receivers(nrec, n // 2, lo, hi - lo)
+    return dict(nx=n, ny=n, c_map=c, c_ref=1.0, source=src, receivers=rec, steps=steps,
+                patch=(x0, x0, nxp, nxp), lattice=5, collision="mrt",
+                s=[1.0, 1.0, 1.0, 2.0, 2.0], tau=0.5, sponge_width=max(2, int(round(40 * s))),
+                sponge_sigma_max=0.1, block=(b0, b0, bw, bw))

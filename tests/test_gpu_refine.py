@@ -1,0 +1,135 @@
+"""GPU parity of the two-level grid refinement (Sec. 4) against the FP64 refinement oracle.
+
+Same inputs on both sides; receivers outside the patch, inside it and on the
+interface; pressure fields at several times (nodes of the closed patch come
+from the fine grid).  Tolerance: relative L2 <= 1e-5 (FP32 GPU vs FP64).
+"""
+import numpy as np
+import pytest
+
+from paper_1704_03172_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sim_cls():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_03172_gb300 import build
+    build.build()
+    from paper_1704_03172_gb300.sim import LBSim
+    return LBSim
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+CASES = [
+    # Q, collision, s, periodic, heterogeneous
+    (5, "bgk", None, False, False),
+    (5, "mrt", [1.3, 0.8, 0.8, 2.0, 2.0], False, True),
+    (5, "mrt", [1.0, 1.0, 1.0, 1.4, 1.7], True, True),
+    (9, "bgk", None, False, False),
+    (9, "mrt", [1.0, 1.0, 1.0, 2.0, 2.0, 2.0, 1.0, 1.0, 2.0], False, True),
+]
+
+
+@pytest.mark.parametrize("Q,coll,s,periodic,hetero", CASES)
+def test_refined_matches_oracle(sim_cls, oracle_mod, Q, coll, s, periodic, hetero):
+    nx, ny, steps = 96, 80, 90
+    c = W.random_medium(nx, ny, 21, 0.6, 1.0) if hetero else W.uniform_map(nx, ny, 1.0)
+    patch = (40, 22, 30, 36)
+    wav = W.ricker(steps, 0.06)
+    rec = np.array([[20, 40], [40, 40], [52, 41], [70, 58], [69, 30], [85, 40], [55, 22]],
+                   np.int32)                     # outside / on I / inside / corner
+    w_ref = (0.4, 0.11, 0.04)
+    kw = dict(tau=0.5 if coll == "bgk" else 0.5, s=s, w_ref=w_ref, c_ref=1.0)
+    sponge = 0 if periodic else 8
+    sim = sim_cls(c, lattice=Q, collision=coll, boundary="periodic" if periodic else "zero",
+                  sponge_width=sponge, sponge_sigma_max=0.1, patch=patch, **kw)
+    sim.set_source(15, 40, wav)
+    sim.set_receivers(rec, steps)
+    p0 = W.gaussian_pulse(nx, ny, 30, 50, 3.0, 1e-2).astype(np.float32)
+    sim.init_pressure(p0)
+    P = oracle_mod.Problem(Q, nx, ny, c, periodic=periodic, mrt=coll == "mrt",
+                           sponge_width=sponge, sponge_sigma_max=0.1,
+                           source=(15, 40, wav), receivers=rec, **kw)
+    R = oracle_mod.Refined(P, *patch)
+    R.init_pressure(p0.astype(np.float64))
+    assert rel(sim.pressure().cpu().numpy(), R.pressure()) < TOL      # time 0
+    traces = []
+    for chunk in (1, 29, 60):
+        sim.step(chunk)
+        traces.append(R.run(chunk))
+        assert rel(sim.pressure().cpu().numpy(), R.pressure()) < TOL
+    tr = sim.traces().cpu().numpy()
+    sim.close()
+    assert rel(tr, np.concatenate(traces)) < TOL
+
+
+def test_refined_block_workload_reduced_full_length(sim_cls, oracle_mod):
+    # the slow-block refinement workload on a 256^2 coarse grid, all 4000 coarse steps
+    wl = W.refined_block_workload(256, nrec=64)
+    steps = wl["steps"]
+    sim = sim_cls(wl["c_map"], lattice=5, collision="mrt", s=wl["s"], c_ref=wl["c_ref"],
+                  sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"],
+                  patch=wl["patch"])
+    sim.set_source(*wl["source"])
+    sim.set_receivers(wl["receivers"], steps)
+    sim.init_pressure(None)
+    snap = 150
+    sim.step(snap)
+    ps = sim.pressure().cpu().numpy()
+    sim.step(steps - snap)
+    tr = sim.traces().cpu().numpy()
+    sim.close()
+    P = oracle_mod.Problem(5, 256, 256, wl["c_map"], c_ref=wl["c_ref"], mrt=True, s=wl["s"],
+                           sponge_width=wl["sponge_width"],
+                           sponge_sigma_max=wl["sponge_sigma_max"], source=wl["source"],
+                           receivers=wl["receivers"])
+    R = oracle_mod.Refined(P, *wl["patch"])
+    R.init_pressure(None)
+    t1 = R.run(snap)
+    assert rel(ps, R.pressure()) < TOL
+    t2 = R.run(steps - snap)
+    assert rel(tr, np.concatenate([t1, t2])) < TOL
+
+
+def test_refined_block_workload_full_size_truncated(sim_cls, oracle_mod):
+    # 2048^2 coarse grid with the 1025^2-node fine patch, the launch path the benchmark
+    # times, for 40 coarse steps from a smooth initial pulse that crosses the interface
+    wl = W.refined_block_workload(2048)
+    n, steps = 2048, 40
+    p0 = W.gaussian_pulse(n, n, wl["patch"][0], 1024, 12.0, 1e-2).astype(np.float32)
+    sim = sim_cls(wl["c_map"], lattice=5, collision="mrt", s=wl["s"], c_ref=wl["c_ref"],
+                  sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"],
+                  patch=wl["patch"])
+    sim.set_source(*wl["source"])
+    sim.set_receivers(wl["receivers"], steps)
+    sim.init_pressure(p0)
+    sim.step(steps)
+    ps = sim.pressure().cpu().numpy()
+    tr = sim.traces().cpu().numpy()
+    sim.close()
+    P = oracle_mod.Problem(5, n, n, wl["c_map"], c_ref=wl["c_ref"], mrt=True, s=wl["s"],
+                           sponge_width=wl["sponge_width"],
+                           sponge_sigma_max=wl["sponge_sigma_max"], source=wl["source"],
+                           receivers=wl["receivers"])
+    R = oracle_mod.Refined(P, *wl["patch"])
+    R.init_pressure(p0.astype(np.float64))
+    tro = R.run(steps)
+    assert rel(ps, R.pressure()) < TOL
+    assert rel(tr, tro) < TOL
+
+
+def test_source_inside_patch_is_rejected(sim_cls):
+    from paper_1704_03172_gb300 import lbac
+    c = W.uniform_map(64, 64, 1.0)
+    sim = sim_cls(c, lattice=5, c_ref=1.0, patch=(20, 20, 10, 10))
+    with pytest.raises(lbac.LBError):
+        sim.set_source(25, 25, [1.0, 2.0])
+    sim.close()
