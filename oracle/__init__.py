@@ -169,8 +169,25 @@ class Refined:
             pass
 
 
-def _declare_adjoint(L):  # filled in by the adjoint oracle
-    pass
+def _declare_adjoint(L):
+    L.orc_adjoint.argtypes = [_pp, _dp, ctypes.c_int, _dp, _dp, _dp, _dp]
+    L.orc_adjoint.restype = ctypes.c_int
+
+
+def adjoint(P: "Problem", g0, nt: int, resid):
+    """Discrete adjoint: (dJ/dc [ny, nx], dJ/dS [nt], dJ/dg0 [Q, ny, nx]) for
+    dJ/dp^t_r = resid[t, r] over nt steps from g0 (FP64, stores every state)."""
+    g0 = np.ascontiguousarray(g0, dtype=np.float64)
+    R = np.ascontiguousarray(resid, dtype=np.float64).reshape(nt, len(P.receivers))
+    gc = np.zeros((P.ny, P.nx))
+    gs = np.zeros(nt)
+    gg = np.zeros((P.Q, P.ny, P.nx))
+    S = P._struct()
+    rc = lib().orc_adjoint(ctypes.byref(S), _ptr(g0, ctypes.c_double), int(nt),
+                           _ptr(R, ctypes.c_double), _ptr(gc, ctypes.c_double),
+                           _ptr(gs, ctypes.c_double), _ptr(gg, ctypes.c_double))
+    assert rc == 0, rc
+    return gc, gs, gg
 
 
 def _ptr(a, ctype):

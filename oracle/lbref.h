@@ -64,4 +64,10 @@ int orc_ref_pressure(void *h, double *p);
 int orc_ref_fine_pressure(void *h, double *pf);
 int orc_ref_states(void *h, double *gc, double *gf);
 
+/* Discrete adjoint (lbadjoint.c): gradients of J with dJ/dp^t_r = resid[t][r]
+ * for nt steps from g0.  grad_c [ny][nx]; grad_src [nt] and grad_g0 [Q][ny][nx]
+ * may be NULL. */
+int orc_adjoint(const orc_problem *P, const double *g0, int nt, const double *resid,
+                double *grad_c, double *grad_src, double *grad_g0);
+
 #endif
