@@ -141,6 +141,25 @@ lb_status lb_get_time(const lb_ctx *ctx, long long *t);
 /* Wait for all queued work; LB_ECUDA if any of it failed. */
 lb_status lb_sync(lb_ctx *ctx);
 
+/* Keep adjoint checkpoints: from now on (time t0 = current time), lb_step copies
+ * the state into device memory before every step t with (t - t0) % every == 0.
+ * every = 0 stops.  lb_init_pressure and lb_set_state restart the run of
+ * checkpoints at their time.  Needs FP32 storage and no patch (LB_ESTATE). */
+lb_status lb_checkpoint_every(lb_ctx *ctx, int every);
+
+/* Discrete adjoint of the nt steps that followed the checkpointed start time
+ * t0 (the paper has no adjoint; the scheme is linear in g, so the adjoint step is
+ * the exact transpose: reverse streaming, K^T = (I - C (I - E))^T, receiver
+ * injection).  dJdp[n][r] is dJ/dp at receiver r, trace row n (time t0 + n),
+ * e.g. p - d for J = 1/2 sum (p - d)^2; the receivers must have been set at t0.
+ * Outputs (any may be NULL): grad_c [ny][nx] = dJ/dc_map (c_ref held fixed),
+ * grad_src [nt] = dJ/dS[t0 + n], grad_g0 [Q][ny][nx] = dJ/dg(t0).
+ * on_device applies to dJdp and all outputs.  Forward states are replayed
+ * from the checkpoints (two levels, ~2 sqrt(every) + 3 extra states of device
+ * memory).  The context's own state is left untouched.  Synchronises. */
+lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *grad_c, double *grad_src,
+                     float *grad_g0, int on_device);
+
 /* FP64 invariants of the current state g(t), reduced on the device in a fixed
  * order (bit-reproducible): out[0] = mass sum_x rho(x), out[1] = energy
  * sum_x sum_i g_i^2 / w_i(x) over w_i > 0 (conserved by a tau = 1/2 step on a

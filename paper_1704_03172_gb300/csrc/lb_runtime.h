@@ -23,6 +23,11 @@ struct lb_ctx {
     unsigned *lp_max = nullptr;     // 16-bit storage: [3][9][kMaxCopies] max |value| (slots)
     int lp_slot = 0;                // slot describing the current buffer
     double *inv_scratch = nullptr;  // lb_invariants: [ny][4] row partials + [4] result
+    int ckpt_every = 0;             // adjoint checkpoints: state copied every ckpt_every steps
+    std::vector<void *> ckpt;       // ckpt[k]: stored buffer at time k * ckpt_every
+    int ckpt_count = 0;             // valid checkpoints, from time ckpt_t0
+    long long ckpt_t0 = 0;
+    bool ckpt_raw0 = false;         // raw flag of the time-0 checkpoint
     float *src_tab = nullptr;
     int src_nt = 0, src_x = 0, src_y = 0;
     int2 *rec = nullptr;
@@ -59,6 +64,10 @@ lb_status cuda_fail(lb_ctx *ctx, cudaError_t e, const char *what);
 void *dev_alloc(lb_ctx *ctx, size_t bytes);
 void dev_free(lb_ctx *ctx, void *p);
 }  // namespace lbrt
+
+// adjoint checkpoints (adjoint.cu): copy the state before step t when t % every == 0
+lb_status ckpt_maybe_save(lb_ctx *ctx);
+void ckpt_reset(lb_ctx *ctx);
 
 // grid refinement (refine.cu)
 lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev);

@@ -469,6 +469,7 @@ lb_status lb_init_pressure(lb_ctx *ctx, const float *p0, int on_device) {
     ctx->t = 0;
     ctx->t_rec0 = 0;
     ctx->fine_ready = false;
+    ckpt_reset(ctx);
     return set_state_common(ctx, p0, on_device, 0);
 }
 
@@ -476,6 +477,7 @@ lb_status lb_set_state(lb_ctx *ctx, const float *in, int on_device) {
     if (!ctx) return LB_EINVAL;
     if (!in) return fail(ctx, LB_EINVAL, "state is NULL");
     if (ctx->refined) return fail(ctx, LB_ESTATE, "lb_set_state is not available with a patch");
+    ckpt_reset(ctx);  // checkpoints describe one trajectory; a new state starts another
     return set_state_common(ctx, in, on_device, 1);
 }
 
@@ -556,7 +558,13 @@ lb_status lb_step(lb_ctx *ctx, int n) {
     if (ctx->refined) return refine_step(ctx, n);
     StepFn fn = pick_step(ctx);
     StepArgs a = base_args(ctx);
-    for (int k = 0; k < n; k++) launch_step(ctx, fn, a);
+    for (int k = 0; k < n; k++) {
+        if (ctx->ckpt_every > 0) {
+            lb_status st = ckpt_maybe_save(ctx);
+            if (st != LB_OK) return st;
+        }
+        launch_step(ctx, fn, a);
+    }
     return check_launch(ctx, "step_kernel");
 }
 

@@ -83,9 +83,12 @@ _SIGS = {
                               ctypes.c_int, ctypes.c_double, _dp, ctypes.c_void_p,
                               ctypes.c_void_p],
 }
-OPTIONAL = {
-    "lb_adjoint": [_ctx_p, _fp, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_int],
-}
+_SIGS.update({
+    "lb_checkpoint_every": [_ctx_p, ctypes.c_int],
+    "lb_adjoint": [_ctx_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_int],
+})
+OPTIONAL = {}
 
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -201,9 +204,13 @@ def lb_invariants_noalloc(g_ptr, c_map_ptr, lattice, nx, ny, c_ref, w_ref, out_p
                                              float(c_ref), wr, out_ptr, stream))
 
 
-def lb_adjoint(ctx, resid_ptr, nt, checkpoint_every, grad_c_ptr, grad_src_ptr, on_device):
-    return _check(_lib.lb_adjoint(ctx, resid_ptr, int(nt), int(checkpoint_every), grad_c_ptr,
-                                  grad_src_ptr, int(on_device)), ctx)
+def lb_checkpoint_every(ctx, every):
+    return _check(_lib.lb_checkpoint_every(ctx, int(every)), ctx)
+
+
+def lb_adjoint(ctx, dJdp_ptr, nt, grad_c_ptr, grad_src_ptr, grad_g0_ptr, on_device):
+    return _check(_lib.lb_adjoint(ctx, dJdp_ptr, int(nt), grad_c_ptr, grad_src_ptr, grad_g0_ptr,
+                                  int(on_device)), ctx)
 
 
 def raw():

@@ -160,6 +160,25 @@ class LBSim:
         lbac.lb_get_state(self.ctx, _ptr(out), 1)
         return out
 
+    def checkpoint_every(self, every):
+        """Keep adjoint checkpoints every `every` steps from the current time."""
+        lbac.lb_checkpoint_every(self.ctx, every)
+
+    def adjoint(self, dJdp, nt=None, want_g0=False):
+        """Gradients of J given dJ/dp at the receivers (trace rows): returns
+        (dJ/dc_map [ny, nx] float32, dJ/dS [nt] float64, dJ/dg(t0) or None)."""
+        dJdp = torch.as_tensor(dJdp, dtype=torch.float32, device=self.device).contiguous()
+        nt = dJdp.shape[0] if nt is None else int(nt)
+        with torch.cuda.stream(self.stream):
+            gc = torch.zeros((self.ny, self.nx), dtype=torch.float32, device=self.device)
+            gs = torch.zeros(nt, dtype=torch.float64, device=self.device)
+            gg = (torch.zeros((self.Q, self.ny, self.nx), dtype=torch.float32, device=self.device)
+                  if want_g0 else None)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        lbac.lb_adjoint(self.ctx, _ptr(dJdp), nt, _ptr(gc), _ptr(gs),
+                        _ptr(gg) if gg is not None else None, 1)
+        return gc, gs, gg
+
     def invariants(self):
         """(mass, energy, max |g|, non-finite count) of the current state, FP64."""
         return lbac.lb_invariants(self.ctx)
@@ -183,3 +202,40 @@ class LBSim:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class LBForward(torch.autograd.Function):
+    """traces = LB(c_map, wavelet): receiver traces of one shot, differentiable with
+    respect to the sound-speed map and the source samples through the library's
+    discrete adjoint (lb_adjoint) rather than autograd tracing.
+
+    forward(c_map [ny, nx], wavelet [nt], spec) -> traces [nt, nrec], where spec is a
+    dict of LBSim keyword arguments plus "source_xy", "receivers", "nt" and
+    "checkpoint_every" (c_ref must be given: it is held fixed under differentiation).
+    """
+
+    @staticmethod
+    def forward(ctx, c_map, wavelet, spec):
+        spec = dict(spec)
+        nt = int(spec.pop("nt"))
+        sxy = spec.pop("source_xy")
+        rec = spec.pop("receivers")
+        every = int(spec.pop("checkpoint_every", 200))
+        if spec.get("c_ref") is None:
+            raise ValueError("spec['c_ref'] must be fixed for differentiation")
+        sim = LBSim(c_map.detach(), **spec)
+        sim.set_source(sxy[0], sxy[1], wavelet.detach().double().cpu().numpy())
+        sim.set_receivers(rec, nt)
+        sim.init_pressure(None)
+        sim.checkpoint_every(every)
+        sim.step(nt)
+        traces = sim.traces(nt).clone()
+        ctx.sim, ctx.nt = sim, nt
+        ctx.wdtype, ctx.wdevice = wavelet.dtype, wavelet.device
+        return traces
+
+    @staticmethod
+    def backward(ctx, grad_traces):
+        gc, gs, _ = ctx.sim.adjoint(grad_traces, ctx.nt)
+        ctx.sim.close()
+        return gc, gs.to(dtype=ctx.wdtype, device=ctx.wdevice), None
