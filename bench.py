@@ -128,7 +128,7 @@ def _make_sim(LBSim, wl, nt_cap):
     sim = LBSim(wl["c_map"], lattice=wl["lattice"], collision=wl["collision"], tau=wl["tau"],
                 s=wl.get("s"), storage=wl["storage"], c_ref=wl["c_ref"],
                 sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"],
-                w_ref=wl["w_ref"])
+                w_ref=wl["w_ref"], time_block=wl.get("time_block", 1))
     sx, sy, wav = wl["source"]
     sim.set_source(sx, sy, wav)
     sim.set_receivers(wl["receivers"], nt_cap)
@@ -149,8 +149,9 @@ def _time_steps(torch, sim, steps, warmup):
     return e0.elapsed_time(e1) / 1e3
 
 
-def _variant(torch, LBSim, lattice, storage, collision, steps, warmup):
+def _variant(torch, LBSim, lattice, storage, collision, steps, warmup, time_block=1):
     wl = _workload(lattice, storage, collision)
+    wl["time_block"] = time_block
     sim = _make_sim(LBSim, wl, steps + warmup)
     try:
         sec = _time_steps(torch, sim, steps, warmup)
@@ -349,6 +350,14 @@ def run_ours(args):
                                                        max(200, args.steps // 5), 10)
             except Exception as ex:  # report, do not hide
                 v[f"d2q{lat}_{coll}_{st}"] = {"error": str(ex)[:200]}
+        for K in (2, 4, 6, 8):
+            name = f"d2q5_bgk_f32_tb{K}"
+            try:
+                v[name] = _variant(torch, LBSim, 5, "f32", "bgk", max(400, args.steps // 5) // 24 * 24,
+                                   24, time_block=K)
+                v[name]["one_step_roofline_glups"] = round(_peaks()[0] / BYTES_PER_SITE[(5, "f32")], 1)
+            except Exception as ex:
+                v[name] = {"error": str(ex)[:200]}
         try:
             v["refined_block_2048_d2q5_mrt_f32"] = _refined_variant(torch, LBSim, 400, 10)
         except Exception as ex:

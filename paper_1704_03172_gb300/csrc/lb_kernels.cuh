@@ -110,26 +110,44 @@ __device__ __forceinline__ float scale_of(const float *scale, int i) {
 // ---------------------------------------------------------------- storage --
 template <typename ST> struct Store;
 
+// Every storage type moves one 16-byte vector per thread and population:
+// V = 4 FP32 sites or V = 8 sites of a 16-bit type.
 template <> struct Store<float> {
     static constexpr int kBytes = 4;
-    __device__ static __forceinline__ float4 load4(const float *p) {
-        return *reinterpret_cast<const float4 *>(p);
+    static constexpr int V = 4;
+    __device__ static __forceinline__ void loadV(const float *p, float (&v)[V]) {
+        float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    __device__ static __forceinline__ void storeV(float *p, const float (&v)[V]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
     __device__ static __forceinline__ float load1(const float *p) { return *p; }
     __device__ static __forceinline__ void store1(float *p, float v) { *p = v; }
-    __device__ static __forceinline__ void store4(float *p, float4 v) {
-        *reinterpret_cast<float4 *>(p) = v;
-    }
 };
 
 template <> struct Store<__nv_bfloat16> {
     static constexpr int kBytes = 2;
-    __device__ static __forceinline__ float4 load4(const __nv_bfloat16 *p) {
-        uint2 u = *reinterpret_cast<const uint2 *>(p);
-        __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x);
-        __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
-        float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    static constexpr int V = 8;
+    __device__ static __forceinline__ void loadV(const __nv_bfloat16 *p, float (&v)[V]) {
+        uint4 u = *reinterpret_cast<const uint4 *>(p);
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[k]);
+            float2 f = __bfloat1622float2(h);
+            v[2 * k] = f.x;
+            v[2 * k + 1] = f.y;
+        }
+    }
+    __device__ static __forceinline__ void storeV(__nv_bfloat16 *p, const float (&v)[V]) {
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+            w[k] = *reinterpret_cast<uint32_t *>(&h);
+        }
+        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     __device__ static __forceinline__ float load1(const __nv_bfloat16 *p) {
         return __bfloat162float(*p);
@@ -137,71 +155,83 @@ template <> struct Store<__nv_bfloat16> {
     __device__ static __forceinline__ void store1(__nv_bfloat16 *p, float v) {
         *p = __float2bfloat16_rn(v);
     }
-    __device__ static __forceinline__ void store4(__nv_bfloat16 *p, float4 v) {
-        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
-        __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
-        uint2 u;
-        u.x = *reinterpret_cast<uint32_t *>(&a);
-        u.y = *reinterpret_cast<uint32_t *>(&b);
-        *reinterpret_cast<uint2 *>(p) = u;
-    }
 };
 
 template <> struct Store<__half> {
     static constexpr int kBytes = 2;
-    __device__ static __forceinline__ float4 load4(const __half *p) {
-        uint2 u = *reinterpret_cast<const uint2 *>(p);
-        __half2 a = *reinterpret_cast<__half2 *>(&u.x);
-        __half2 b = *reinterpret_cast<__half2 *>(&u.y);
-        float2 fa = __half22float2(a), fb = __half22float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    static constexpr int V = 8;
+    __device__ static __forceinline__ void loadV(const __half *p, float (&v)[V]) {
+        uint4 u = *reinterpret_cast<const uint4 *>(p);
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            __half2 h = *reinterpret_cast<const __half2 *>(&w[k]);
+            float2 f = __half22float2(h);
+            v[2 * k] = f.x;
+            v[2 * k + 1] = f.y;
+        }
+    }
+    __device__ static __forceinline__ void storeV(__half *p, const float (&v)[V]) {
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            __half2 h = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
+            w[k] = *reinterpret_cast<uint32_t *>(&h);
+        }
+        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     __device__ static __forceinline__ float load1(const __half *p) { return __half2float(*p); }
     __device__ static __forceinline__ void store1(__half *p, float v) { *p = __float2half_rn(v); }
-    __device__ static __forceinline__ void store4(__half *p, float4 v) {
-        __half2 a = __floats2half2_rn(v.x, v.y);
-        __half2 b = __floats2half2_rn(v.z, v.w);
-        uint2 u;
-        u.x = *reinterpret_cast<uint32_t *>(&a);
-        u.y = *reinterpret_cast<uint32_t *>(&b);
-        *reinterpret_cast<uint2 *>(p) = u;
-    }
 };
 
 // ------------------------------------------------------------------ pulls --
-// Pull one population's 4 values for sites x0..x0+3 of this thread's row from
-// source row `row` (nullptr: the row lies outside a zero-ghost domain).  CX is
-// the population's x velocity: the value at site x comes from x - CX.
+// Pull one population's V values for sites x0..x0+V-1 of this thread's row
+// from source row `row` (nullptr: the row lies outside a zero-ghost domain).
+// CX is the population's x velocity: the value at site x comes from x - CX.
 // Must be called by all 32 lanes of the warp (shuffles).
 template <int CX, bool PERIODIC, typename ST>
-__device__ __forceinline__ void pull4(const ST *row, int x0, int lane, int nx, bool active,
-                                      float scale, float v[4]) {
+__device__ __forceinline__ void pullV(const ST *row, int x0, int lane, int nx, bool active,
+                                      float scale, float (&v)[Store<ST>::V]) {
+    constexpr int V = Store<ST>::V;
     if (row == nullptr) {  // warp-uniform
-        v[0] = v[1] = v[2] = v[3] = 0.f;
+#pragma unroll
+        for (int k = 0; k < V; k++) v[k] = 0.f;
         return;
     }
-    float4 q = active ? Store<ST>::load4(row + x0) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float q[V];
+    if (active) {
+        Store<ST>::loadV(row + x0, q);
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; k++) q[k] = 0.f;
+    }
     if (CX == 0) {
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+#pragma unroll
+        for (int k = 0; k < V; k++) v[k] = q[k];
     } else if (CX == 1) {  // value from x - 1
-        float left = __shfl_up_sync(0xffffffffu, q.w, 1);
+        float left = __shfl_up_sync(0xffffffffu, q[V - 1], 1);
         if (lane == 0) left = (x0 > 0) ? Store<ST>::load1(row + x0 - 1) : 0.f;
-        v[0] = left; v[1] = q.x; v[2] = q.y; v[3] = q.z;
+        v[0] = left;
+#pragma unroll
+        for (int k = 1; k < V; k++) v[k] = q[k - 1];
         if (x0 == 0) v[0] = PERIODIC ? Store<ST>::load1(row + nx - 1) : 0.f;
     } else {  // CX == -1: value from x + 1
-        float right = __shfl_down_sync(0xffffffffu, q.x, 1);
-        if (lane == 31) right = (x0 + 4 < nx) ? Store<ST>::load1(row + x0 + 4) : 0.f;
-        v[0] = q.y; v[1] = q.z; v[2] = q.w; v[3] = right;
-        const int k = nx - 1 - x0;  // local index of the last real site, if in this vector
-        if (k >= 0 && k < 4) {
+        float right = __shfl_down_sync(0xffffffffu, q[0], 1);
+        if (lane == 31) right = (x0 + V < nx) ? Store<ST>::load1(row + x0 + V) : 0.f;
+#pragma unroll
+        for (int k = 0; k + 1 < V; k++) v[k] = q[k + 1];
+        v[V - 1] = right;
+        const int last = nx - 1 - x0;  // local index of the last real site, if in this vector
+        if (last >= 0 && last < V) {
             const float b = PERIODIC ? Store<ST>::load1(row) : 0.f;
 #pragma unroll
-            for (int j = 0; j < 4; j++)
-                if (j == k) v[j] = b;
+            for (int j = 0; j < V; j++)
+                if (j == last) v[j] = b;
         }
     }
     if (scale != 1.f) {
-        v[0] *= scale; v[1] *= scale; v[2] *= scale; v[3] *= scale;
+#pragma unroll
+        for (int k = 0; k < V; k++) v[k] *= scale;
     }
 }
 
@@ -369,40 +399,45 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, const float *s_in,
     const int wid = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int y = wid / a.segs;
     if (y >= a.ny) return;  // warp-uniform
-    const int x0 = (wid - y * a.segs) * kSitesPerWarp + lane * 4;
+    constexpr int V = Store<ST>::V;
+    const int x0 = (wid - y * a.segs) * (32 * V) + lane * V;
     const bool active = x0 < a.nx;
     const ST *in = static_cast<const ST *>(a.in);
 
-    float g[Q][4];
+    float g[Q][V];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const float sc = LP ? s_in[i] : 1.f;
         if (a.raw) {  // warp-uniform: first step after lb_set_state, read g(t) in place
-            pull4<0, PERIODIC>(in + i * a.plane + (long long)y * a.pitch, x0, lane, a.nx, active,
+            pullV<0, PERIODIC>(in + i * a.plane + (long long)y * a.pitch, x0, lane, a.nx, active,
                                sc, g[i]);
             continue;
         }
         const ST *row = src_row<PERIODIC>(in + i * a.plane, y - Lat<Q>::cy(i), a.ny, a.pitch);
         const int cx = Lat<Q>::cx(i);
         if (cx == 1)
-            pull4<1, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
+            pullV<1, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
         else if (cx == -1)
-            pull4<-1, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
+            pullV<-1, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
         else
-            pull4<0, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
+            pullV<0, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
     }
     if (!active) return;  // no shuffles below
 
-    float4 e2v = *reinterpret_cast<const float4 *>(a.eta2 + (long long)y * a.pitch + x0);
-    const float e2s[4] = {e2v.x, e2v.y, e2v.z, e2v.w};
+    float e2s[V];
+#pragma unroll
+    for (int k = 0; k < V; k += 4) {
+        float4 e = *reinterpret_cast<const float4 *>(a.eta2 + (long long)y * a.pitch + x0 + k);
+        e2s[k] = e.x; e2s[k + 1] = e.y; e2s[k + 2] = e.z; e2s[k + 3] = e.w;
+    }
     const bool edge = a.sponge_w > 0 &&
                       (y < a.sponge_w || y >= a.ny - a.sponge_w || x0 < a.sponge_w ||
-                       x0 + 3 >= a.nx - a.sponge_w);
-    const bool has_src = (y == a.src_y) && (a.src_x >= x0) && (a.src_x < x0 + 4) &&
+                       x0 + V - 1 >= a.nx - a.sponge_w);
+    const bool has_src = (y == a.src_y) && (a.src_x >= x0) && (a.src_x < x0 + V) &&
                          a.src_tab != nullptr && a.t < a.src_nt;
-    float out[Q][4];
+    // collide site by site, in place: g[i][k] becomes the stored output
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < V; k++) {
         float gs[Q];
 #pragma unroll
         for (int i = 0; i < Q; i++) gs[i] = g[i][k];
@@ -419,21 +454,22 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, const float *s_in,
         if (edge) f = sponge_factor(x0 + k, y, a);
         const bool real = x0 + k < a.nx;
 #pragma unroll
-        for (int i = 0; i < Q; i++) out[i][k] = real ? gs[i] * f : 0.f;
+        for (int i = 0; i < Q; i++) g[i][k] = real ? gs[i] * f : 0.f;
     }
     ST *o = static_cast<ST *>(a.out) + (long long)y * a.pitch + x0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         if (LP) {
             const float sc = s_oinv[i];
-            tmax[i] = fmaxf(fmaxf(fabsf(out[i][0]), fabsf(out[i][1])),
-                            fmaxf(fabsf(out[i][2]), fabsf(out[i][3])));
-            Store<ST>::store4(o + i * a.plane, make_float4(out[i][0] * sc, out[i][1] * sc,
-                                                           out[i][2] * sc, out[i][3] * sc));
-        } else {
-            Store<ST>::store4(o + i * a.plane,
-                              make_float4(out[i][0], out[i][1], out[i][2], out[i][3]));
+            float m = 0.f;
+#pragma unroll
+            for (int k = 0; k < V; k++) {
+                m = fmaxf(m, fabsf(g[i][k]));
+                g[i][k] *= sc;
+            }
+            tmax[i] = m;
         }
+        Store<ST>::storeV(o + i * a.plane, g[i]);
     }
 }
 

@@ -27,6 +27,8 @@ struct lb_ctx {
     std::vector<void *> ckpt;       // ckpt[k]: stored buffer at time k * ckpt_every
     int ckpt_count = 0;             // valid checkpoints, from time ckpt_t0
     long long ckpt_t0 = 0;
+    int *tb_off = nullptr;          // temporal blocking: per-tile receiver list offsets
+    int *tb_rec = nullptr;          // receiver indices grouped by tile
     bool ckpt_raw0 = false;         // raw flag of the time-0 checkpoint
     float *src_tab = nullptr;
     int src_nt = 0, src_x = 0, src_y = 0;
@@ -68,6 +70,11 @@ void dev_free(lb_ctx *ctx, void *p);
 // adjoint checkpoints (adjoint.cu): copy the state before step t when t % every == 0
 lb_status ckpt_maybe_save(lb_ctx *ctx);
 void ckpt_reset(lb_ctx *ctx);
+
+// temporal blocking (tblock.cu)
+bool tb_supported(int Q, int K);
+lb_status tb_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
+lb_status tb_launch(lb_ctx *ctx, int K);
 
 // grid refinement (refine.cu)
 lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev);

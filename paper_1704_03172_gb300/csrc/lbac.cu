@@ -75,7 +75,8 @@ StepArgs base_args(const lb_ctx *c) {
     a.ny = c->ny;
     a.pitch = c->pitch;
     a.plane = (long long)c->ny * c->pitch;
-    a.segs = (c->nx + kSitesPerWarp - 1) / kSitesPerWarp;
+    const int sites_per_warp = 32 * (c->cfg.storage == LB_F32 ? 4 : 8);  // 16-byte vectors
+    a.segs = (c->nx + sites_per_warp - 1) / sites_per_warp;
     long long warps = (long long)a.segs * c->ny;
     a.main_blocks = (int)((warps + kWarps - 1) / kWarps);
     a.omega = (float)(1.0 / c->cfg.tau);
@@ -205,6 +206,13 @@ lb_status validate(const lb_config *cfg) {
         return fail(nullptr, LB_EINVAL, "sponge_width >= 0 and sigma_max in [0, 1] required");
     if (cfg->n_patches < 0 || cfg->n_patches > 1 || (cfg->n_patches > 0 && !cfg->patches))
         return fail(nullptr, LB_EINVAL, "at most one patch is supported");
+    if (cfg->time_block > 1) {
+        if (!tb_supported(cfg->lattice, cfg->time_block))
+            return fail(nullptr, LB_EINVAL, "time_block %d not supported for D2Q%d (D2Q5: 2, 4, 6, "
+                        "8; D2Q9: 2, 4)", cfg->time_block, cfg->lattice);
+        if (cfg->storage != LB_F32 || cfg->n_patches > 0)
+            return fail(nullptr, LB_EINVAL, "time_block needs FP32 storage and no patch");
+    }
     return LB_OK;
 }
 
@@ -409,6 +417,7 @@ lb_status lb_set_receivers(lb_ctx *ctx, const int *xy, int nrec, int nt_capacity
     ctx->nrec = nrec;
     ctx->trace_cap = nt_capacity;
     if (ctx->refined) return refine_set_receivers(ctx, xy, nrec);
+    if (ctx->cfg.time_block > 1) return tb_set_receivers(ctx, xy, nrec);
     return LB_OK;
 }
 
@@ -558,12 +567,29 @@ lb_status lb_step(lb_ctx *ctx, int n) {
     if (ctx->refined) return refine_step(ctx, n);
     StepFn fn = pick_step(ctx);
     StepArgs a = base_args(ctx);
-    for (int k = 0; k < n; k++) {
+    const int K = ctx->cfg.time_block;
+    for (int k = 0; k < n;) {
         if (ctx->ckpt_every > 0) {
             lb_status st = ckpt_maybe_save(ctx);
             if (st != LB_OK) return st;
         }
+        if (K > 1 && n - k >= K && !ctx->raw) {
+            // K fused steps, unless they would straddle a checkpoint time or the end
+            // of the trace capacity; then single steps keep both exact
+            const long long row = ctx->t - ctx->t_rec0;
+            const bool straddle_ckpt =
+                ctx->ckpt_every > 0 && (ctx->t - ctx->ckpt_t0) % ctx->ckpt_every + K > ctx->ckpt_every;
+            const bool straddle_trace =
+                ctx->trace && row < ctx->trace_cap && row + K > ctx->trace_cap;
+            if (!straddle_ckpt && !straddle_trace) {
+                lb_status st = tb_launch(ctx, K);
+                if (st != LB_OK) return st;
+                k += K;
+                continue;
+            }
+        }
         launch_step(ctx, fn, a);
+        k += 1;
     }
     return check_launch(ctx, "step_kernel");
 }
