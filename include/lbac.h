@@ -160,6 +160,64 @@ lb_status lb_checkpoint_every(lb_ctx *ctx, int every);
 lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *grad_c, double *grad_src,
                      float *grad_g0, int on_device);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of independent shots (one simulation each).
+ * The paper runs one simulation at a time; this layer serves many.  A
+ * scheduler thread admits submitted requests in arrival order whenever a slot
+ * and enough device memory (lb_footprint) are free, and advances every active
+ * FP32/BF16 shot by one step per scheduling round with a single batched launch
+ * per (lattice, collision, boundary, storage) group, so small shots share the
+ * GPU and requests that arrive while others run join the batch at the next
+ * round.  FP16 shots step on their own.  A request that asks for a gradient is
+ * checkpointed during its forward run and its adjoint (lb_adjoint, J = 1/2
+ * sum (p - d)^2 over its traces) runs on a worker thread on its own stream,
+ * overlapping the batched forward work.  Results do not depend on what else
+ * is in the batch: each shot runs the same kernels with the same arithmetic.
+ */
+typedef struct lb_server lb_server;
+
+typedef struct {
+    int max_active;          /* shots resident at once, >= 1 */
+    size_t hbm_budget;       /* device bytes the server may hold; 0: 80% of free memory */
+    int rounds_per_pass;     /* steps per scheduling pass between admission checks, >= 1 */
+    int adjoint_workers;     /* threads running gradient sweeps, >= 1 */
+} lb_server_config;
+
+typedef struct {
+    lb_config cfg;           /* shot configuration; c_map is a host array; cuda_stream,
+                                allocator and time_block are ignored */
+    int src_x, src_y;        /* source node */
+    const double *wavelet;   /* S[n], n < nt_wavelet, host */
+    int nt_wavelet;
+    const int *rec_xy;       /* [nrec][2] receivers, host */
+    int nrec;
+    int nt;                  /* steps to run; traces have nt rows */
+    const float *observed;   /* [nt][nrec] host data d (gradient requests only) */
+    int want_gradient;       /* 1: also dJ/dc_map and dJ/dS for J = 1/2 sum (p - d)^2 */
+    int checkpoint_every;    /* adjoint checkpoint interval, 0: 200 */
+} lb_request;
+
+lb_status lb_server_create(const lb_server_config *cfg, lb_server **out);
+/* Copies every input array; returns the request id.  LB_ENOMEM if the request
+ * can never fit the budget, LB_EINVAL for an invalid configuration. */
+lb_status lb_server_submit(lb_server *srv, const lb_request *req, long long *id);
+/* *done = 1 once results are ready (or the request failed). */
+lb_status lb_server_poll(lb_server *srv, long long id, int *done);
+/* Block until done; LB_ETIMEOUT after timeout_ms (< 0: no limit). */
+lb_status lb_server_wait(lb_server *srv, long long id, int timeout_ms);
+/* Copy the results of a finished request and release it.  traces [nt][nrec];
+ * grad_c [ny][nx] and grad_src [nt_wavelet] for gradient requests (any may be
+ * NULL); times[3] = submit, start (admission), done, in seconds on the
+ * server's monotonic clock.  Returns the request's own status (e.g. LB_ENOMEM). */
+lb_status lb_server_result(lb_server *srv, long long id, float *traces, float *grad_c,
+                           double *grad_src, double *times);
+/* Counters: out[0] requests done, out[1] active, out[2] pending, out[3] device
+ * bytes held, out[4] batched launches issued. */
+lb_status lb_server_stats(lb_server *srv, double *out, int n);
+/* Stop after finishing active and pending work; frees everything. */
+lb_status lb_server_destroy(lb_server *srv);
+const char *lb_server_last_error(const lb_server *srv);
+
 /* FP64 invariants of the current state g(t), reduced on the device in a fixed
  * order (bit-reproducible): out[0] = mass sum_x rho(x), out[1] = energy
  * sum_x sum_i g_i^2 / w_i(x) over w_i > 0 (conserved by a tau = 1/2 step on a
@@ -202,7 +260,8 @@ lb_status lb_invariants_noalloc(const float *g, const float *c_map, int lattice,
                                 void *cuda_stream);
 
 /* Device bytes lb_create would allocate for cfg, plus the receiver trace for
- * nt steps when nrec > 0, plus adjoint checkpoints when want_adjoint. */
+ * nt steps when nrec > 0, plus what lb_adjoint needs for nt steps when
+ * want_adjoint > 0 (the checkpoint interval; 1 means the default 200). */
 lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint, size_t *bytes);
 
 /* Sizes and derived constants: info[0] = Q, info[1] = row pitch in elements,

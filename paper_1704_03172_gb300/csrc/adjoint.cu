@@ -249,6 +249,25 @@ lb_status ckpt_maybe_save(lb_ctx *ctx) {
     return LB_OK;
 }
 
+bool ckpt_reserve(lb_ctx *ctx, void **dst, const void **src, size_t *bytes) {
+    const long long rel = ctx->t - ctx->ckpt_t0;
+    if (rel < 0 || rel % ctx->ckpt_every != 0) return false;
+    const long long k = rel / ctx->ckpt_every;
+    if (k != ctx->ckpt_count) return false;
+    const size_t b = (size_t)ctx->Q * ctx->ny * ctx->pitch * ctx->ebytes;
+    if ((size_t)k >= ctx->ckpt.size()) {
+        void *p = dev_alloc(ctx, b);
+        if (!p) return false;
+        ctx->ckpt.push_back(p);
+    }
+    *dst = ctx->ckpt[k];
+    *src = ctx->pop[ctx->cur];
+    *bytes = b;
+    if (k == 0) ctx->ckpt_raw0 = ctx->raw;
+    ctx->ckpt_count = (int)k + 1;
+    return true;
+}
+
 extern "C" lb_status lb_checkpoint_every(lb_ctx *ctx, int every) {
     if (!ctx) return LB_EINVAL;
     if (every < 0) return fail(ctx, LB_EINVAL, "every < 0");

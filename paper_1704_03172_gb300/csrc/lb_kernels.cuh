@@ -74,15 +74,19 @@ struct StepArgs {
     int nrec;
     float *trace_row;        // pressure row for time t, or null
     const int *rec_col;      // column of receiver r in the trace row (nullptr: r)
-    // 16-bit storage (per-population power-of-two scale, value = stored * scale).
-    // Three device slots rotate: the input buffer's scale and max |value| are read,
-    // the output buffer's are written, and the third max slot is cleared for the
-    // next step.  All nullptr for FP32 storage.
+    // FP16 storage: per-population power-of-two scale, value = stored * scale.
+    // Three device slots rotate.  The scale of the input buffer and the one chosen
+    // for the output buffer are ready before the launch; every block folds its
+    // max |output| into max_out, and the last block to finish derives the scale
+    // the next step will write with (scale_next, from 8 max|out| + |S[t+1]|) and
+    // clears max_next for it.  All nullptr for FP32 and BF16 storage (BF16 has
+    // the exponent range of FP32 and needs no range scale).
     const float *scale_in;    // [9]
-    float *scale_out;         // [9], written by block 0
-    const unsigned *max_in;   // [9][kMaxCopies] float bits of max |value| of `in`
-    unsigned *max_out;        // [9][kMaxCopies] accumulated max |value| of `out`
-    unsigned *max_clear;      // [9][kMaxCopies] zeroed for the next step
+    const float *scale_out;   // [9]
+    unsigned *max_out;        // [9][kMaxCopies] float bits of max |value| written
+    float *scale_next;        // [9]
+    unsigned *max_next;       // [9][kMaxCopies]
+    unsigned *done;           // block counter for the last-block hand-off
 };
 
 constexpr int kMaxCopies = 8;          // spread of the per-block atomicMax targets
@@ -366,37 +370,30 @@ __device__ __forceinline__ void gather_receivers(const StepArgs &a, int r) {
 }
 
 // -------------------------------------------------------------------- step --
-// 16-bit prologue (thread i < Q): scale of the input buffer, and the output
-// scale predicted from its max: |out| <= 8 max|in| + |S[t]| is kept below
-// kStoredTarget (8x headroom again before FP16 overflows).
-template <int Q>
-__device__ __forceinline__ void scale_prologue(const StepArgs &a, int i, float *s_in,
-                                               float *s_oinv) {
-    const float sin_ = a.scale_in[i];
-    float m = 0.f;
-#pragma unroll
-    for (int c = 0; c < kMaxCopies; c++) m = fmaxf(m, __uint_as_float(a.max_in[i * kMaxCopies + c]));
-    const float S = (a.src_tab && a.t >= 0 && a.t < a.src_nt) ? fabsf(a.src_tab[a.t]) : 0.f;
-    const float bound = 8.f * m + S;
-    const float so = bound > 0.f ? pow2_ceil(bound * (1.f / kStoredTarget)) : sin_;
-    s_in[i] = sin_;
-    s_oinv[i] = 1.f / so;  // exact: so is a power of two
-    if (blockIdx.x == 0) {
-        a.scale_out[i] = so;
-#pragma unroll
-        for (int c = 0; c < kMaxCopies; c++) a.max_clear[i * kMaxCopies + c] = 0u;
-    }
+// FP16 keeps a per-population scale; BF16 (FP32's exponent range) and FP32 do not.
+template <typename ST> struct Scaled {
+    static constexpr bool value = false;
+};
+template <> struct Scaled<__half> {
+    static constexpr bool value = true;
+};
+
+// Scale that keeps the predicted bound |out| <= 8 max|in| + |S| at or below
+// kStoredTarget (8x headroom again before FP16 overflows); `keep` if the bound is 0.
+__device__ __forceinline__ float next_scale(float maxval, float S, float keep) {
+    const float bound = 8.f * maxval + S;
+    return bound > 0.f ? pow2_ceil(bound * (1.f / kStoredTarget)) : keep;
 }
 
-// The sites of one warp row-segment; tmax receives this thread's max |out_i|.
+// The sites of one warp row-segment of block `blk`; tmax receives this
+// thread's max |out_i|.
 template <int Q, bool MRT, bool PERIODIC, typename ST>
-__device__ __forceinline__ void step_sites(const StepArgs &a, const float *s_in,
-                                          const float *s_oinv, float tmax[Q]) {
-    constexpr bool LP = Store<ST>::kBytes == 2;
+__device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tmax[Q]) {
+    constexpr bool SC = Scaled<ST>::value;
 #pragma unroll
     for (int i = 0; i < Q; i++) tmax[i] = 0.f;
     const int lane = threadIdx.x & 31;
-    const int wid = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int wid = blk * kWarps + (threadIdx.x >> 5);
     const int y = wid / a.segs;
     if (y >= a.ny) return;  // warp-uniform
     constexpr int V = Store<ST>::V;
@@ -407,22 +404,29 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, const float *s_in,
     float g[Q][V];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        const float sc = LP ? s_in[i] : 1.f;
         if (a.raw) {  // warp-uniform: first step after lb_set_state, read g(t) in place
             pullV<0, PERIODIC>(in + i * a.plane + (long long)y * a.pitch, x0, lane, a.nx, active,
-                               sc, g[i]);
+                               1.f, g[i]);
             continue;
         }
         const ST *row = src_row<PERIODIC>(in + i * a.plane, y - Lat<Q>::cy(i), a.ny, a.pitch);
         const int cx = Lat<Q>::cx(i);
         if (cx == 1)
-            pullV<1, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
+            pullV<1, PERIODIC>(row, x0, lane, a.nx, active, 1.f, g[i]);
         else if (cx == -1)
-            pullV<-1, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
+            pullV<-1, PERIODIC>(row, x0, lane, a.nx, active, 1.f, g[i]);
         else
-            pullV<0, PERIODIC>(row, x0, lane, a.nx, active, sc, g[i]);
+            pullV<0, PERIODIC>(row, x0, lane, a.nx, active, 1.f, g[i]);
     }
     if (!active) return;  // no shuffles below
+    if (SC) {  // one scale per population: applied after the shuffles
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const float sc = a.scale_in[i];
+#pragma unroll
+            for (int k = 0; k < V; k++) g[i][k] *= sc;
+        }
+    }
 
     float e2s[V];
 #pragma unroll
@@ -459,13 +463,13 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, const float *s_in,
     ST *o = static_cast<ST *>(a.out) + (long long)y * a.pitch + x0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        if (LP) {
-            const float sc = s_oinv[i];
+        if (SC) {
+            const float inv = 1.f / a.scale_out[i];  // exact: a power of two
             float m = 0.f;
 #pragma unroll
             for (int k = 0; k < V; k++) {
                 m = fmaxf(m, fabsf(g[i][k]));
-                g[i][k] *= sc;
+                g[i][k] *= inv;
             }
             tmax[i] = m;
         }
@@ -475,38 +479,86 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, const float *s_in,
 
 template <int Q, bool MRT, bool PERIODIC, typename ST>
 __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
-    constexpr bool LP = Store<ST>::kBytes == 2;
-    __shared__ float s_in[9], s_oinv[9];
-    __shared__ float s_wmax[LP ? 9 : 1][kWarps];
-    if (LP) {
-        if ((int)threadIdx.x < Q) scale_prologue<Q>(a, threadIdx.x, s_in, s_oinv);
-        __syncthreads();
-    }
+    constexpr bool SC = Scaled<ST>::value;
+    __shared__ float s_wmax[SC ? 9 : 1][kWarps];
+    __shared__ bool s_last;
     if ((int)blockIdx.x >= a.main_blocks) {  // block-uniform
         gather_receivers<Q, PERIODIC, ST>(a, ((int)blockIdx.x - a.main_blocks) * kThreads +
                                                  (int)threadIdx.x);
         return;
     }
     float tmax[Q];
-    step_sites<Q, MRT, PERIODIC, ST>(a, s_in, s_oinv, tmax);
-    if (LP) {
+    step_sites<Q, MRT, PERIODIC, ST>(a, blockIdx.x, tmax);
+    if (SC) {
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
             float m = tmax[i];
             for (int off = 16; off > 0; off >>= 1)
                 m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-            if (lane == 0) s_wmax[LP ? i : 0][w] = m;
+            if (lane == 0) s_wmax[SC ? i : 0][w] = m;
         }
         __syncthreads();
         if ((int)threadIdx.x < Q) {
             float m = 0.f;
 #pragma unroll
-            for (int k = 0; k < kWarps; k++) m = fmaxf(m, s_wmax[LP ? threadIdx.x : 0][k]);
+            for (int k = 0; k < kWarps; k++) m = fmaxf(m, s_wmax[SC ? threadIdx.x : 0][k]);
             atomicMax(a.max_out + threadIdx.x * kMaxCopies + (blockIdx.x % kMaxCopies),
                       __float_as_uint(m));
         }
+        // last block: derive the scale of the next step's output from this step's maxima
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_last = atomicAdd(a.done, 1u) == (unsigned)a.main_blocks - 1u;
+        __syncthreads();
+        if (s_last && (int)threadIdx.x < Q) {
+            __threadfence();
+            const int i = threadIdx.x;
+            float m = 0.f;
+#pragma unroll
+            for (int c = 0; c < kMaxCopies; c++)
+                m = fmaxf(m, __uint_as_float(atomicOr(a.max_out + i * kMaxCopies + c, 0u)));
+            const long long tn = a.t + 1;
+            const float S = (a.src_tab && tn < a.src_nt) ? fabsf(a.src_tab[tn]) : 0.f;
+            a.scale_next[i] = next_scale(m, S, a.scale_out[i]);
+#pragma unroll
+            for (int c = 0; c < kMaxCopies; c++) a.max_next[i * kMaxCopies + c] = 0u;
+            if (i == 0) *a.done = 0u;
+        }
     }
+}
+
+// ------------------------------------------------------------ batched step --
+// One launch advances several independent simulations ("shots") by one step
+// each: shot k owns blocks [first[k], first[k + 1]) of the grid (its site blocks
+// followed by its receiver blocks) and its own StepArgs descriptor.  Used by the
+// serving loop for FP32 and BF16 storage (no cross-block scale hand-off).
+template <int Q, bool MRT, bool PERIODIC, typename ST>
+__global__ void __launch_bounds__(kThreads)
+    batch_step_kernel(const StepArgs *__restrict__ args, const int *__restrict__ first, int nshots) {
+    __shared__ StepArgs sa;
+    __shared__ int s_blk;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nshots - 1;  // shot with first[k] <= blockIdx.x < first[k + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (first[mid] <= (int)blockIdx.x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        sa = args[lo];
+        s_blk = (int)blockIdx.x - first[lo];
+    }
+    __syncthreads();
+    const int blk = s_blk;
+    if (blk >= sa.main_blocks) {
+        gather_receivers<Q, PERIODIC, ST>(sa, (blk - sa.main_blocks) * kThreads + (int)threadIdx.x);
+        return;
+    }
+    float tmax[Q];
+    step_sites<Q, MRT, PERIODIC, ST>(sa, blk, tmax);
 }
 
 // -------------------------------------------------------- state transforms --
@@ -594,13 +646,21 @@ __global__ void source_max_kernel(StepArgs a, const float *src, int mode) {
     }
 }
 
-// scale_out[i] = power of two keeping max |g_i| at or below kStoredTarget
-static __global__ void init_scale_kernel(StepArgs a, int Q) {
+// FP16 initial scales from max |g_i| of the state being written (accumulated in
+// max_out): scale_next[i] for the written state itself, scale_out-style slot
+// `scale_first` for the first step's output (8x headroom plus |S[t]|), whose
+// max slot max_next is cleared, together with the block counter.
+static __global__ void init_scale_kernel(StepArgs a, int Q, float *scale_first) {
     int i = threadIdx.x;
     if (i >= Q) return;
     float m = 0.f;
     for (int c = 0; c < kMaxCopies; c++) m = fmaxf(m, __uint_as_float(a.max_out[i * kMaxCopies + c]));
-    a.scale_out[i] = m > 0.f ? pow2_ceil(m * (1.f / kStoredTarget)) : 1.f;
+    const float s0 = m > 0.f ? pow2_ceil(m * (1.f / kStoredTarget)) : 1.f;
+    a.scale_next[i] = s0;
+    const float S = (a.src_tab && a.t < a.src_nt) ? fabsf(a.src_tab[a.t]) : 0.f;
+    scale_first[i] = next_scale(m, S, s0);
+    for (int c = 0; c < kMaxCopies; c++) a.max_next[i * kMaxCopies + c] = 0u;
+    if (i == 0) *a.done = 0u;
 }
 
 // eta^2 = (c / c_ref)^2 per site (pads 0); flags: bit0 c <= 0 or non-finite, bit1 eta > 1.

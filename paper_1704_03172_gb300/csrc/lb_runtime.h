@@ -19,8 +19,8 @@ struct lb_ctx {
     int cur = 0;                    // pop[cur] holds the post-collision state of step t-1
     bool raw = false;               // ... or, when raw, the state g(t) itself (unshifted)
     float *eta2 = nullptr;          // [ny][pitch] (c / c_ref)^2
-    float *lp_scale = nullptr;      // 16-bit storage: [3][9] per-population scales (slots)
-    unsigned *lp_max = nullptr;     // 16-bit storage: [3][9][kMaxCopies] max |value| (slots)
+    float *lp_scale = nullptr;      // FP16 storage: [3][9] per-population scales (slots)
+    unsigned *lp_max = nullptr;     // FP16 storage: [3][9][kMaxCopies] max |value| + counter
     int lp_slot = 0;                // slot describing the current buffer
     double *inv_scratch = nullptr;  // lb_invariants: [ny][4] row partials + [4] result
     int ckpt_every = 0;             // adjoint checkpoints: state copied every ckpt_every steps
@@ -56,6 +56,7 @@ using GetFn = void (*)(lbk::StepArgs, float *, int);
 lbk::StepArgs base_args(const lb_ctx *c);
 StepFn pick_step_for(int Q, bool mrt, bool periodic, int storage);
 StepFn pick_step(const lb_ctx *c);
+lbk::StepArgs prepare_step(lb_ctx *ctx);  // FP32 / BF16 storage (no scale slots)
 GetFn pick_get_for(int Q, bool periodic, int storage);
 lb_status check_launch(lb_ctx *ctx, const char *what);
 int round_up(int v, int m);
@@ -69,6 +70,9 @@ void dev_free(lb_ctx *ctx, void *p);
 
 // adjoint checkpoints (adjoint.cu): copy the state before step t when t % every == 0
 lb_status ckpt_maybe_save(lb_ctx *ctx);
+// the same, for callers that queue the copy themselves: reserves checkpoint slot
+// k if one is due before the next step and returns the copy to make
+bool ckpt_reserve(lb_ctx *ctx, void **dst, const void **src, size_t *bytes);
 void ckpt_reset(lb_ctx *ctx);
 
 // temporal blocking (tblock.cu)

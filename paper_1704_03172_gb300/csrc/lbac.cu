@@ -96,10 +96,7 @@ StepArgs base_args(const lb_ctx *c) {
     a.src_y = c->src_y;
     a.rec = c->rec;
     a.nrec = c->nrec;
-    if (c->lp_scale) {
-        a.scale_in = c->lp_scale + c->lp_slot * 9;
-        a.max_in = c->lp_max + c->lp_slot * 9 * kMaxCopies;
-    }
+    if (c->lp_scale) a.scale_in = c->lp_scale + c->lp_slot * 9;
     return a;
 }
 
@@ -247,8 +244,12 @@ lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint,
     if (nrec > 0 && nt > 0) b += (size_t)nt * nrec * 4 + (size_t)nrec * 8;
     if (nt > 0) b += (size_t)nt * 4;
     if (want_adjoint) {
-        // adjoint state pair + gradient + checkpoints (see lb_adjoint)
-        b += 2 * q * plane * 4 + plane * 8;
+        // lb_adjoint: checkpoints every C steps, the replay states (ceil(sqrt(C)) + 1),
+        // the sub-checkpoints, the adjoint pair, the FP64 gradient and dJ/dS
+        const size_t C = want_adjoint > 1 ? (size_t)want_adjoint : 200;
+        const size_t C2 = (size_t)std::ceil(std::sqrt((double)C));
+        const size_t states = (nt > 0 ? ((size_t)nt + C - 1) / C : 1) + (C2 + 1) + (C + C2 - 1) / C2 + 2;
+        b += states * q * plane * 4 + plane * 8 + (size_t)std::max(nt, 0) * 8;
     }
     *bytes = b;
     return LB_OK;
@@ -299,14 +300,14 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     c->eta2 = static_cast<float *>(dev_alloc(c, plane * 4));
     unsigned *flags = static_cast<unsigned *>(dev_alloc(c, 256));
     if (!c->eta2 || !flags) return bail(fail(c, LB_ENOMEM, "medium buffer"));
-    if (cfg->storage != LB_F32) {
+    if (cfg->storage == LB_F16) {  // FP16 range scales (BF16 has FP32's range and needs none)
         c->lp_scale = static_cast<float *>(dev_alloc(c, 3 * 9 * sizeof(float)));
-        c->lp_max = static_cast<unsigned *>(dev_alloc(c, 3 * 9 * kMaxCopies * sizeof(unsigned)));
+        c->lp_max = static_cast<unsigned *>(dev_alloc(c, (3 * 9 * kMaxCopies + 1) * sizeof(unsigned)));
         if (!c->lp_scale || !c->lp_max) return bail(fail(c, LB_ENOMEM, "scale buffers"));
         std::vector<float> ones(27, 1.f);
         cudaMemcpyAsync(c->lp_scale, ones.data(), 27 * sizeof(float), cudaMemcpyHostToDevice,
                         c->stream);
-        cudaMemsetAsync(c->lp_max, 0, 3 * 9 * kMaxCopies * sizeof(unsigned), c->stream);
+        cudaMemsetAsync(c->lp_max, 0, (3 * 9 * kMaxCopies + 1) * sizeof(unsigned), c->stream);
     }
     // medium: c_map -> eta^2 (Eq. 0th lattice weight), on the device
     const float *cmap_dev = cfg->c_map;
@@ -450,17 +451,23 @@ static lb_status set_state_common(lb_ctx *ctx, const float *src, int on_device, 
     a.out = ctx->pop[ctx->cur];
     ctx->raw = true;
     if (ctx->lp_scale) {
-        // 16-bit: fresh slots; the scale of the written state comes from its own max
-        cudaMemsetAsync(ctx->lp_max, 0, 3 * 9 * kMaxCopies * sizeof(unsigned), ctx->stream);
-        a.scale_out = ctx->lp_scale + ctx->lp_slot * 9;
-        a.max_out = ctx->lp_max + ctx->lp_slot * 9 * kMaxCopies;
+        // FP16: the written state's scale from its own max (slot s0), and the scale
+        // the first step will write with (slot s1), whose max slot starts cleared
+        const int s0 = ctx->lp_slot, s1 = (s0 + 1) % 3;
+        cudaMemsetAsync(ctx->lp_max, 0, (3 * 9 * kMaxCopies + 1) * sizeof(unsigned), ctx->stream);
+        a.t = ctx->t;
+        a.max_out = ctx->lp_max + s0 * 9 * kMaxCopies;
+        a.scale_next = ctx->lp_scale + s0 * 9;
+        a.max_next = ctx->lp_max + s1 * 9 * kMaxCopies;
+        a.done = ctx->lp_max + 3 * 9 * kMaxCopies;
         if (dev) {
             if (ctx->Q == 9)
                 source_max_kernel<9><<<1024, 256, 0, ctx->stream>>>(a, dev, mode);
             else
                 source_max_kernel<5><<<1024, 256, 0, ctx->stream>>>(a, dev, mode);
         }
-        init_scale_kernel<<<1, 32, 0, ctx->stream>>>(a, ctx->Q);
+        init_scale_kernel<<<1, 32, 0, ctx->stream>>>(a, ctx->Q, ctx->lp_scale + s1 * 9);
+        a.scale_out = ctx->lp_scale + s0 * 9;  // set_state_kernel writes with it
     }
     long long total = (long long)ctx->ny * ctx->pitch;
     pick_set(ctx)<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(a, dev, mode);
@@ -531,6 +538,23 @@ lb_status lb_get_state(lb_ctx *ctx, float *out, int on_device) {
 
 namespace lbrt {
 
+// Arguments of the next uniform-grid step (h^{t-1} in pop[cur] -> h^t in
+// pop[cur ^ 1]); advances the context's bookkeeping as if the step ran.
+StepArgs prepare_step(lb_ctx *ctx) {
+    StepArgs a = base_args(ctx);
+    a.in = ctx->pop[ctx->cur];
+    a.out = ctx->pop[ctx->cur ^ 1];
+    a.t = ctx->t;
+    a.raw = ctx->raw ? 1 : 0;
+    ctx->raw = false;
+    long long row = ctx->t - ctx->t_rec0;
+    a.trace_row = (ctx->trace && row >= 0 && row < ctx->trace_cap) ? ctx->trace + row * ctx->nrec
+                                                                  : nullptr;
+    ctx->cur ^= 1;
+    ctx->t += 1;
+    return a;
+}
+
 // One uniform-grid step: state h^{t-1} in pop[cur] -> h^t in pop[cur ^ 1].
 lb_status launch_step(lb_ctx *ctx, StepFn fn, StepArgs &a) {
     a.in = ctx->pop[ctx->cur];
@@ -540,9 +564,10 @@ lb_status launch_step(lb_ctx *ctx, StepFn fn, StepArgs &a) {
         const int s0 = ctx->lp_slot, s1 = (s0 + 1) % 3, s2 = (s0 + 2) % 3;
         a.scale_in = ctx->lp_scale + s0 * 9;
         a.scale_out = ctx->lp_scale + s1 * 9;
-        a.max_in = ctx->lp_max + s0 * 9 * kMaxCopies;
         a.max_out = ctx->lp_max + s1 * 9 * kMaxCopies;
-        a.max_clear = ctx->lp_max + s2 * 9 * kMaxCopies;
+        a.scale_next = ctx->lp_scale + s2 * 9;
+        a.max_next = ctx->lp_max + s2 * 9 * kMaxCopies;
+        a.done = ctx->lp_max + 3 * 9 * kMaxCopies;
         ctx->lp_slot = s1;
     }
     a.raw = ctx->raw ? 1 : 0;

@@ -1,0 +1,557 @@
+// serve.cu -- continuous batching of independent shots (the serving layer).
+//
+// A scheduler thread owns the device work.  Requests wait in arrival order;
+// whenever a slot and enough of the device-memory budget are free, the first
+// requests that fit are admitted (their lb_ctx is created on the server
+// stream).  Each scheduling pass then advances every active shot by up to
+// `rounds_per_pass` steps: in every round one batch_step_kernel launch per
+// (lattice, collision, boundary, storage) group steps all the group's shots
+// once, each shot reading its own StepArgs descriptor (uploaded once per pass),
+// so many small shots share one launch and fill the GPU together.  Shots that
+// finish leave the batch (their traces are copied to pinned host memory), new
+// ones join at the next pass.  Gradient requests hand their context to an
+// adjoint worker thread, which waits for the forward work on its own stream
+// and runs lb_adjoint there, overlapping the batched forward work of others.
+// FP16 shots, whose per-step scale hand-off is per launch, step on their own.
+//
+// All waits are bounded: the scheduler sleeps at most 5 ms when idle, workers
+// poll their queue with a timeout, and lb_server_wait takes a timeout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "lb_kernels.cuh"
+#include "lb_runtime.h"
+
+using namespace lbk;
+using namespace lbrt;
+
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+enum class RS { Pending, Active, Draining, Adjoint, Done };
+
+struct Req {
+    long long id = 0;
+    lb_config cfg;
+    std::vector<float> cmap, obs;
+    std::vector<double> wav;
+    std::vector<int> rec;
+    int src_x = 0, src_y = 0, nt = 0, want_grad = 0, ckpt = 200;
+    size_t fp = 0;
+    RS state = RS::Pending;
+    lb_ctx *ctx = nullptr;
+    int steps = 0;
+    float *h_traces = nullptr;  // pinned [nt][nrec]
+    std::vector<float> grad_c;
+    std::vector<double> grad_src;
+    cudaEvent_t ev = nullptr;   // forward work and trace copy complete
+    double t_submit = 0, t_start = 0, t_done = 0;
+    lb_status status = LB_OK;
+    std::string err;
+};
+
+__global__ void residual_kernel(const float *p, const float *d, float *r, long long n) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < n) r[k] = p[k] - d[k];
+}
+
+using BatchFn = void (*)(const StepArgs *, const int *, int);
+
+template <typename ST> BatchFn batch_fn(int Q, bool mrt, bool per) {
+    if (Q == 9) {
+        if (mrt) return per ? batch_step_kernel<9, true, true, ST> : batch_step_kernel<9, true, false, ST>;
+        return per ? batch_step_kernel<9, false, true, ST> : batch_step_kernel<9, false, false, ST>;
+    }
+    if (mrt) return per ? batch_step_kernel<5, true, true, ST> : batch_step_kernel<5, true, false, ST>;
+    return per ? batch_step_kernel<5, false, true, ST> : batch_step_kernel<5, false, false, ST>;
+}
+
+BatchFn pick_batch(const lb_config &c) {
+    const bool mrt = c.collision == LB_MRT, per = c.boundary == LB_PERIODIC;
+    return c.storage == LB_BF16 ? batch_fn<__nv_bfloat16>(c.lattice, mrt, per)
+                                : batch_fn<float>(c.lattice, mrt, per);
+}
+
+}  // namespace
+
+struct lb_server {
+    lb_server_config cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done, cv_adj;
+    std::deque<Req *> pending, adj_queue;
+    std::vector<Req *> active;  // stepping or draining; touched only by the scheduler
+    std::map<long long, Req *> reqs;
+    size_t budget = 0, used = 0;
+    long long next_id = 1;
+    bool stop = false;
+    std::thread sched;
+    std::vector<std::thread> workers;
+    StepArgs *d_args = nullptr, *h_args = nullptr;
+    int *d_first = nullptr, *h_first = nullptr;
+    size_t cap = 0;
+    cudaEvent_t staged = nullptr;
+    std::atomic<long long> n_done{0}, n_launch{0};
+    std::string err;
+};
+
+namespace {
+
+void finish(lb_server *S, Req *r, lb_status st, const std::string &msg) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (st != LB_OK && r->status == LB_OK) {
+        r->status = st;
+        r->err = msg;
+    }
+    r->t_done = now_s();
+    r->state = RS::Done;
+    S->used -= std::min(S->used, r->fp);
+    S->n_done++;
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+}
+
+void admit(lb_server *S, Req *r) {
+    lb_config c = r->cfg;
+    c.c_map = r->cmap.data();
+    c.c_map_on_device = 0;
+    c.cuda_stream = S->stream;
+    c.time_block = 1;
+    c.dev_alloc = nullptr;
+    c.dev_free = nullptr;
+    lb_ctx *ctx = nullptr;
+    lb_status st = lb_create(&c, &ctx);
+    if (st == LB_OK && !r->wav.empty())
+        st = lb_set_source(ctx, r->src_x, r->src_y, r->wav.data(), (int)r->wav.size());
+    if (st == LB_OK) st = lb_set_receivers(ctx, r->rec.data(), (int)r->rec.size() / 2, r->nt);
+    if (st == LB_OK) st = lb_init_pressure(ctx, nullptr, 0);
+    if (st == LB_OK && r->want_grad) st = lb_checkpoint_every(ctx, r->ckpt);
+    if (st == LB_OK && cudaMallocHost(&r->h_traces, std::max<size_t>(1, (size_t)r->nt * r->rec.size() / 2) * 4) != cudaSuccess)
+        st = LB_ENOMEM;
+    if (st == LB_OK && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
+        st = LB_ECUDA;
+    if (st != LB_OK) {
+        std::string msg = ctx ? lb_last_error(ctx) : lb_last_error(nullptr);
+        if (ctx) lb_destroy(ctx);
+        finish(S, r, st, msg);
+        return;
+    }
+    r->ctx = ctx;
+    r->t_start = now_s();
+    r->state = RS::Active;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->active.push_back(r);
+}
+
+bool ensure_capacity(lb_server *S, size_t n) {
+    if (n <= S->cap) return true;
+    size_t cap = std::max(n, 2 * S->cap);
+    if (S->d_args) cudaFree(S->d_args);
+    if (S->d_first) cudaFree(S->d_first);
+    if (S->h_args) cudaFreeHost(S->h_args);
+    if (S->h_first) cudaFreeHost(S->h_first);
+    S->d_args = nullptr;
+    S->d_first = nullptr;
+    S->h_args = nullptr;
+    S->h_first = nullptr;
+    S->cap = 0;
+    if (cudaMalloc(&S->d_args, cap * sizeof(StepArgs)) != cudaSuccess ||
+        cudaMalloc(&S->d_first, 2 * cap * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&S->h_args, cap * sizeof(StepArgs)) != cudaSuccess ||
+        cudaMallocHost(&S->h_first, 2 * cap * sizeof(int)) != cudaSuccess)
+        return false;
+    S->cap = cap;
+    return true;
+}
+
+// One pass: up to R rounds of one step for every stepping shot.
+void pass(lb_server *S) {
+    const int R = std::max(1, S->cfg.rounds_per_pass);
+    std::vector<Req *> shots;
+    for (Req *r : S->active)
+        if (r->state == RS::Active && r->steps < r->nt) shots.push_back(r);
+    if (shots.empty()) return;
+    // FP16 shots step on their own (their scale hand-off is per launch)
+    std::vector<Req *> batched;
+    for (Req *r : shots) {
+        if (r->cfg.storage == LB_F16) {
+            int n = std::min(R, r->nt - r->steps);
+            lb_step(r->ctx, n);
+            r->steps += n;
+        } else {
+            batched.push_back(r);
+        }
+    }
+    if (batched.empty()) return;
+    // build every round's descriptors: groups of identical kernels, shots sorted by group
+    using Key = std::tuple<int, int, int, int>;
+    auto key = [](const Req *r) {
+        return Key(r->cfg.lattice, r->cfg.collision, r->cfg.boundary, r->cfg.storage);
+    };
+    std::stable_sort(batched.begin(), batched.end(),
+                     [&](const Req *a, const Req *b) { return key(a) < key(b); });
+    struct Launch {
+        BatchFn fn;
+        size_t arg0, first0;
+        int n, blocks, round;
+    };
+    struct Copy {  // adjoint checkpoint, queued just before its round's launches
+        int round;
+        void *dst;
+        const void *src;
+        size_t bytes;
+    };
+    std::vector<Launch> launches;
+    std::vector<Copy> copies;
+    size_t need = (size_t)R * batched.size();
+    // wait until the previous pass has consumed the staging buffers
+    if (S->staged) cudaEventSynchronize(S->staged);
+    if (!ensure_capacity(S, need + 1)) {
+        S->err = "descriptor buffers";
+        return;
+    }
+    size_t na = 0, nf = 0;
+    for (int k = 0; k < R; k++) {
+        size_t g0 = 0;
+        while (g0 < batched.size()) {
+            size_t g1 = g0;
+            while (g1 < batched.size() && key(batched[g1]) == key(batched[g0])) g1++;
+            Launch L{pick_batch(batched[g0]->cfg), na, nf, 0, 0, k};
+            for (size_t q = g0; q < g1; q++) {
+                Req *r = batched[q];
+                if (r->steps >= r->nt) continue;
+                Copy c{k, nullptr, nullptr, 0};
+                if (r->ctx->ckpt_every > 0 && ckpt_reserve(r->ctx, &c.dst, &c.src, &c.bytes))
+                    copies.push_back(c);
+                StepArgs a = prepare_step(r->ctx);
+                const int blocks =
+                    a.main_blocks + (a.trace_row ? (a.nrec + kThreads - 1) / kThreads : 0);
+                S->h_args[na++] = a;
+                S->h_first[nf++] = L.blocks;
+                L.blocks += blocks;
+                L.n++;
+                r->steps++;
+            }
+            if (L.n > 0) {
+                S->h_first[nf++] = L.blocks;  // closing prefix entry
+                launches.push_back(L);
+            }
+            g0 = g1;
+        }
+    }
+    cudaMemcpyAsync(S->d_args, S->h_args, na * sizeof(StepArgs), cudaMemcpyHostToDevice, S->stream);
+    cudaMemcpyAsync(S->d_first, S->h_first, nf * sizeof(int), cudaMemcpyHostToDevice, S->stream);
+    if (!S->staged) cudaEventCreateWithFlags(&S->staged, cudaEventDisableTiming);
+    cudaEventRecord(S->staged, S->stream);
+    // rounds in order; a checkpoint copy reads the state its round starts from
+    size_t ci = 0;
+    for (const Launch &L : launches) {
+        for (; ci < copies.size() && copies[ci].round <= L.round; ci++)
+            cudaMemcpyAsync(copies[ci].dst, copies[ci].src, copies[ci].bytes,
+                            cudaMemcpyDeviceToDevice, S->stream);
+        L.fn<<<L.blocks, kThreads, 0, S->stream>>>(S->d_args + L.arg0, S->d_first + L.first0, L.n);
+        S->n_launch++;
+    }
+}
+
+// Shots that ran all their steps: copy traces out, then finish or hand to an adjoint worker.
+void retire(lb_server *S) {
+    std::vector<Req *> keep;
+    for (Req *r : S->active) {
+        if (r->state == RS::Active && r->steps >= r->nt) {
+            const size_t bytes = (size_t)r->nt * (r->rec.size() / 2) * 4;
+            if (bytes) cudaMemcpyAsync(r->h_traces, r->ctx->trace, bytes, cudaMemcpyDeviceToHost, S->stream);
+            cudaEventRecord(r->ev, S->stream);
+            if (r->want_grad) {
+                r->state = RS::Adjoint;
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->adj_queue.push_back(r);
+                S->cv_adj.notify_one();
+                continue;  // leaves the active list; memory stays accounted
+            }
+            r->state = RS::Draining;
+        }
+        if (r->state == RS::Draining && cudaEventQuery(r->ev) == cudaSuccess) {
+            lb_destroy(r->ctx);
+            r->ctx = nullptr;
+            finish(S, r, LB_OK, "");
+            continue;
+        }
+        keep.push_back(r);
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->active.swap(keep);
+}
+
+void scheduler(lb_server *S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<Req *> admit_now;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->stop && S->pending.empty() && S->active.empty()) break;
+            if (S->active.empty() && S->pending.empty()) {
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+                continue;
+            }
+            size_t slots = S->active.size();
+            for (auto it = S->pending.begin();
+                 it != S->pending.end() && slots + admit_now.size() < (size_t)S->cfg.max_active;) {
+                if (S->used + (*it)->fp <= S->budget) {
+                    S->used += (*it)->fp;
+                    admit_now.push_back(*it);
+                    it = S->pending.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        for (Req *r : admit_now) admit(S, r);
+        pass(S);
+        retire(S);
+        bool idle;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            idle = true;
+            for (Req *r : S->active)
+                if (r->state == RS::Active) idle = false;
+        }
+        if (idle) std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    cudaStreamSynchronize(S->stream);
+}
+
+void adjoint_worker(lb_server *S) {
+    cudaSetDevice(S->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    for (;;) {
+        Req *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            while (S->adj_queue.empty()) {
+                if (S->stop && S->pending.empty() && S->active.empty()) {
+                    cudaStreamDestroy(st);
+                    return;
+                }
+                S->cv_adj.wait_for(lk, std::chrono::milliseconds(10));
+            }
+            r = S->adj_queue.front();
+            S->adj_queue.pop_front();
+        }
+        cudaStreamWaitEvent(st, r->ev, 0);
+        lb_ctx *ctx = r->ctx;
+        ctx->stream = st;  // the scheduler no longer touches this context
+        const int nrec = (int)r->rec.size() / 2;
+        const long long n = (long long)r->nt * nrec;
+        float *d_obs = nullptr, *d_res = nullptr;
+        lb_status status = LB_OK;
+        if (n > 0 && (cudaMalloc(&d_obs, n * 4) != cudaSuccess || cudaMalloc(&d_res, n * 4) != cudaSuccess))
+            status = LB_ENOMEM;
+        if (status == LB_OK && n > 0) {
+            cudaMemcpyAsync(d_obs, r->obs.data(), n * 4, cudaMemcpyHostToDevice, st);
+            residual_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctx->trace, d_obs, d_res, n);
+        }
+        r->grad_c.assign((size_t)ctx->nx * ctx->ny, 0.f);
+        std::vector<double> gs(r->nt, 0.0);
+        if (status == LB_OK) {  // dJ/dp and the gradients stay on the device, then one copy out
+            float *d_gc = nullptr;
+            double *d_gs = nullptr;
+            if (cudaMalloc(&d_gc, r->grad_c.size() * 4) != cudaSuccess ||
+                cudaMalloc(&d_gs, gs.size() * 8) != cudaSuccess) {
+                status = LB_ENOMEM;
+            } else {
+                status = lb_adjoint(ctx, d_res, r->nt, d_gc, d_gs, nullptr, 1);
+                if (status == LB_OK) {
+                    cudaMemcpyAsync(r->grad_c.data(), d_gc, r->grad_c.size() * 4, cudaMemcpyDeviceToHost, st);
+                    cudaMemcpyAsync(gs.data(), d_gs, gs.size() * 8, cudaMemcpyDeviceToHost, st);
+                    if (cudaStreamSynchronize(st) != cudaSuccess) status = LB_ECUDA;
+                }
+            }
+            if (d_gc) cudaFree(d_gc);
+            if (d_gs) cudaFree(d_gs);
+        }
+        std::string msg = status == LB_OK ? "" : lb_last_error(ctx);
+        r->grad_src.assign(r->wav.size(), 0.0);
+        for (size_t k = 0; k < r->grad_src.size() && k < gs.size(); k++) r->grad_src[k] = gs[k];
+        if (d_obs) cudaFree(d_obs);
+        if (d_res) cudaFree(d_res);
+        lb_destroy(ctx);
+        r->ctx = nullptr;
+        finish(S, r, status, msg);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_server_create(const lb_server_config *cfg, lb_server **out) {
+    if (!cfg || !out) return LB_EINVAL;
+    *out = nullptr;
+    if (cfg->max_active < 1 || cfg->rounds_per_pass < 1 || cfg->adjoint_workers < 1)
+        return fail(nullptr, LB_EINVAL, "max_active, rounds_per_pass and adjoint_workers must be >= 1");
+    lb_server *S = new lb_server();
+    S->cfg = *cfg;
+    cudaGetDevice(&S->device);
+    if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete S;
+        return fail(nullptr, LB_ECUDA, "server stream");
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    S->budget = cfg->hbm_budget ? cfg->hbm_budget : (size_t)(0.8 * (double)free_b);
+    S->sched = std::thread(scheduler, S);
+    for (int k = 0; k < cfg->adjoint_workers; k++) S->workers.emplace_back(adjoint_worker, S);
+    *out = S;
+    return LB_OK;
+}
+
+lb_status lb_server_submit(lb_server *S, const lb_request *q, long long *id) {
+    if (!S || !q || !id) return LB_EINVAL;
+    if (q->nt < 1 || q->nrec < 0 || (q->nrec > 0 && !q->rec_xy) || !q->cfg.c_map ||
+        (q->nt_wavelet > 0 && !q->wavelet) || (q->want_gradient && q->nrec > 0 && !q->observed))
+        return fail(nullptr, LB_EINVAL, "incomplete request");
+    if (q->cfg.n_patches > 0) return fail(nullptr, LB_EINVAL, "served shots have no patch");
+    if (q->want_gradient && q->cfg.storage != LB_F32)
+        return fail(nullptr, LB_EINVAL, "gradient requests need FP32 storage");
+    Req *r = new Req();
+    r->cfg = q->cfg;
+    r->cmap.assign(q->cfg.c_map, q->cfg.c_map + (size_t)q->cfg.nx * q->cfg.ny);
+    r->cfg.c_map = nullptr;
+    if (q->nt_wavelet > 0) r->wav.assign(q->wavelet, q->wavelet + q->nt_wavelet);
+    r->rec.assign(q->rec_xy, q->rec_xy + 2 * q->nrec);
+    if (q->want_gradient && q->nrec > 0) r->obs.assign(q->observed, q->observed + (size_t)q->nt * q->nrec);
+    r->src_x = q->src_x;
+    r->src_y = q->src_y;
+    r->nt = q->nt;
+    r->want_grad = q->want_gradient ? 1 : 0;
+    r->ckpt = q->checkpoint_every > 0 ? q->checkpoint_every : 200;
+    lb_footprint(&q->cfg, q->nt, q->nrec, r->want_grad ? r->ckpt : 0, &r->fp);
+    r->fp += (size_t)q->nt * q->nrec * 4 * (r->want_grad ? 2 : 0);  // observed + residual
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (r->fp > S->budget) {
+        delete r;
+        S->err = "request needs more device memory than the budget";
+        return fail(nullptr, LB_ENOMEM, "request needs more device memory than the budget");
+    }
+    r->id = S->next_id++;
+    r->t_submit = now_s();
+    S->reqs[r->id] = r;
+    S->pending.push_back(r);
+    S->cv_work.notify_all();
+    *id = r->id;
+    return LB_OK;
+}
+
+lb_status lb_server_poll(lb_server *S, long long id, int *done) {
+    if (!S || !done) return LB_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return LB_EINVAL;
+    *done = it->second->state == RS::Done;
+    return LB_OK;
+}
+
+lb_status lb_server_wait(lb_server *S, long long id, int timeout_ms) {
+    if (!S) return LB_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return LB_EINVAL;
+    Req *r = it->second;
+    auto pred = [&] { return r->state == RS::Done; };
+    if (timeout_ms < 0) {
+        S->cv_done.wait(lk, pred);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) {
+        return LB_ETIMEOUT;
+    }
+    return LB_OK;
+}
+
+lb_status lb_server_result(lb_server *S, long long id, float *traces, float *grad_c,
+                           double *grad_src, double *times) {
+    if (!S) return LB_EINVAL;
+    Req *r = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(id);
+        if (it == S->reqs.end()) return LB_EINVAL;
+        r = it->second;
+        if (r->state != RS::Done) return LB_ESTATE;
+        S->reqs.erase(it);
+    }
+    const size_t nrec = r->rec.size() / 2;
+    if (traces && r->h_traces && r->status == LB_OK)
+        memcpy(traces, r->h_traces, (size_t)r->nt * nrec * 4);
+    if (grad_c && !r->grad_c.empty()) memcpy(grad_c, r->grad_c.data(), r->grad_c.size() * 4);
+    if (grad_src && !r->grad_src.empty()) memcpy(grad_src, r->grad_src.data(), r->grad_src.size() * 8);
+    if (times) {
+        times[0] = r->t_submit;
+        times[1] = r->t_start;
+        times[2] = r->t_done;
+    }
+    lb_status st = r->status;
+    if (st != LB_OK) S->err = r->err;
+    if (r->h_traces) cudaFreeHost(r->h_traces);
+    if (r->ev) cudaEventDestroy(r->ev);
+    delete r;
+    return st;
+}
+
+lb_status lb_server_stats(lb_server *S, double *out, int n) {
+    if (!S || !out) return LB_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    double v[5] = {(double)S->n_done.load(), (double)S->active.size(), (double)S->pending.size(),
+                   (double)S->used, (double)S->n_launch.load()};
+    for (int k = 0; k < n && k < 5; k++) out[k] = v[k];
+    return LB_OK;
+}
+
+lb_status lb_server_destroy(lb_server *S) {
+    if (!S) return LB_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv_work.notify_all();
+        S->cv_adj.notify_all();
+    }
+    if (S->sched.joinable()) S->sched.join();
+    for (auto &w : S->workers)
+        if (w.joinable()) w.join();
+    for (auto &kv : S->reqs) {
+        Req *r = kv.second;
+        if (r->h_traces) cudaFreeHost(r->h_traces);
+        if (r->ev) cudaEventDestroy(r->ev);
+        delete r;
+    }
+    if (S->d_args) cudaFree(S->d_args);
+    if (S->d_first) cudaFree(S->d_first);
+    if (S->h_args) cudaFreeHost(S->h_args);
+    if (S->h_first) cudaFreeHost(S->h_first);
+    if (S->staged) cudaEventDestroy(S->staged);
+    cudaStreamDestroy(S->stream);
+    delete S;
+    return LB_OK;
+}
+
+const char *lb_server_last_error(const lb_server *S) { return S ? S->err.c_str() : ""; }
+
+}  // extern "C"

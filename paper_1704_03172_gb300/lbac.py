@@ -49,6 +49,21 @@ class lb_config(ctypes.Structure):
     ]
 
 
+class lb_server_config(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
+                ("rounds_per_pass", ctypes.c_int), ("adjoint_workers", ctypes.c_int)]
+
+
+class lb_request(ctypes.Structure):
+    _fields_ = [
+        ("cfg", lb_config), ("src_x", ctypes.c_int), ("src_y", ctypes.c_int),
+        ("wavelet", ctypes.POINTER(ctypes.c_double)), ("nt_wavelet", ctypes.c_int),
+        ("rec_xy", ctypes.POINTER(ctypes.c_int)), ("nrec", ctypes.c_int), ("nt", ctypes.c_int),
+        ("observed", ctypes.POINTER(ctypes.c_float)), ("want_gradient", ctypes.c_int),
+        ("checkpoint_every", ctypes.c_int),
+    ]
+
+
 class LBError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -83,7 +98,16 @@ _SIGS = {
                               ctypes.c_int, ctypes.c_double, _dp, ctypes.c_void_p,
                               ctypes.c_void_p],
 }
+_srv_p = ctypes.c_void_p
 _SIGS.update({
+    "lb_server_create": [ctypes.POINTER(lb_server_config), ctypes.POINTER(_srv_p)],
+    "lb_server_submit": [_srv_p, ctypes.POINTER(lb_request), ctypes.POINTER(ctypes.c_longlong)],
+    "lb_server_poll": [_srv_p, ctypes.c_longlong, _ip],
+    "lb_server_wait": [_srv_p, ctypes.c_longlong, ctypes.c_int],
+    "lb_server_result": [_srv_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.c_void_p, _dp],
+    "lb_server_stats": [_srv_p, _dp, ctypes.c_int],
+    "lb_server_destroy": [_srv_p],
     "lb_checkpoint_every": [_ctx_p, ctypes.c_int],
     "lb_adjoint": [_ctx_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                    ctypes.c_void_p, ctypes.c_int],
@@ -101,8 +125,55 @@ for _name, _args in OPTIONAL.items():
         _f.restype = ctypes.c_int
 _lib.lb_last_error.argtypes = [_ctx_p]
 _lib.lb_last_error.restype = ctypes.c_char_p
+_lib.lb_server_last_error.argtypes = [_srv_p]
+_lib.lb_server_last_error.restype = ctypes.c_char_p
 
-EXPORTED = sorted(list(_SIGS) + ["lb_last_error"] + [n for n in OPTIONAL if hasattr(_lib, n)])
+EXPORTED = sorted(list(_SIGS) + ["lb_last_error", "lb_server_last_error"] +
+                  [n for n in OPTIONAL if hasattr(_lib, n)])
+
+
+def lb_server_create(cfg: lb_server_config):
+    srv = _srv_p()
+    _check(_lib.lb_server_create(ctypes.byref(cfg), ctypes.byref(srv)))
+    return srv
+
+
+def lb_server_submit(srv, req: lb_request) -> int:
+    rid = ctypes.c_longlong()
+    _check(_lib.lb_server_submit(srv, ctypes.byref(req), ctypes.byref(rid)))
+    return rid.value
+
+
+def lb_server_poll(srv, rid) -> bool:
+    d = ctypes.c_int()
+    _check(_lib.lb_server_poll(srv, int(rid), ctypes.byref(d)))
+    return bool(d.value)
+
+
+def lb_server_wait(srv, rid, timeout_ms=-1):
+    return _check(_lib.lb_server_wait(srv, int(rid), int(timeout_ms)))
+
+
+def lb_server_result(srv, rid, traces_ptr, grad_c_ptr, grad_src_ptr):
+    """Returns (status, times[3]); the caller checks status (the request's own)."""
+    t = (ctypes.c_double * 3)()
+    st = _lib.lb_server_result(srv, int(rid), traces_ptr, grad_c_ptr, grad_src_ptr, t)
+    return st, list(t)
+
+
+def lb_server_stats(srv):
+    v = (ctypes.c_double * 5)()
+    _check(_lib.lb_server_stats(srv, v, 5))
+    return list(v)
+
+
+def lb_server_destroy(srv):
+    return _check(_lib.lb_server_destroy(srv))
+
+
+def lb_server_last_error(srv) -> str:
+    m = _lib.lb_server_last_error(srv)
+    return m.decode() if m else ""
 
 
 def lb_last_error(ctx=None) -> str:

@@ -239,3 +239,89 @@ class LBForward(torch.autograd.Function):
         gc, gs, _ = ctx.sim.adjoint(grad_traces, ctx.nt)
         ctx.sim.close()
         return gc, gs.to(dtype=ctx.wdtype, device=ctx.wdevice), None
+
+
+class LBServer:
+    """Continuous-batching shot server (lb_server_* of the C ABI)."""
+
+    def __init__(self, max_active=64, hbm_budget=0, rounds_per_pass=16, adjoint_workers=2):
+        cfg = lbac.lb_server_config(int(max_active), int(hbm_budget), int(rounds_per_pass),
+                                    int(adjoint_workers))
+        self.srv = lbac.lb_server_create(cfg)
+        self._meta = {}
+
+    def submit(self, c_map, *, nt, source, receivers, observed=None, want_gradient=False,
+               checkpoint_every=200, lattice=5, collision="bgk", tau=0.5, s=None,
+               storage="f32", boundary="zero", sponge_width=0, sponge_sigma_max=0.1, c_ref=None,
+               w_ref=(4 / 9, 1 / 9, 1 / 36)):
+        c = np.ascontiguousarray(c_map, dtype=np.float32)
+        ny, nx = c.shape
+        cfg = lbac.lb_config_default()
+        cfg.lattice, cfg.nx, cfg.ny = int(lattice), nx, ny
+        cfg.collision = _COLL[collision] if isinstance(collision, str) else int(collision)
+        cfg.storage = _STORAGE[storage] if isinstance(storage, str) else int(storage)
+        cfg.boundary = _BOUND[boundary] if isinstance(boundary, str) else int(boundary)
+        cfg.tau = float(tau)
+        if s is not None:
+            for k, v in enumerate(s):
+                cfg.s[k] = float(v)
+        for k in range(3):
+            cfg.w_ref[k] = float(w_ref[k])
+        cfg.sponge_width, cfg.sponge_sigma_max = int(sponge_width), float(sponge_sigma_max)
+        cfg.c_ref = float(c_ref) if c_ref is not None else 0.0
+        cfg.c_map = c.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        sx, sy, wav = source
+        wav = np.ascontiguousarray(wav, dtype=np.float64)
+        rec = np.ascontiguousarray(np.asarray(receivers, dtype=np.int32).reshape(-1, 2))
+        req = lbac.lb_request()
+        req.cfg = cfg
+        req.src_x, req.src_y = int(sx), int(sy)
+        req.wavelet = wav.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        req.nt_wavelet = len(wav)
+        req.rec_xy = rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        req.nrec = len(rec)
+        req.nt = int(nt)
+        obs = None
+        if want_gradient:
+            obs = np.ascontiguousarray(observed, dtype=np.float32).reshape(int(nt), len(rec))
+            req.observed = obs.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        req.want_gradient = int(bool(want_gradient))
+        req.checkpoint_every = int(checkpoint_every)
+        rid = lbac.lb_server_submit(self.srv, req)   # copies every array
+        self._meta[rid] = (int(nt), len(rec), nx, ny, len(wav), bool(want_gradient))
+        return rid
+
+    def poll(self, rid):
+        return lbac.lb_server_poll(self.srv, rid)
+
+    def wait(self, rid, timeout_ms=-1):
+        lbac.lb_server_wait(self.srv, rid, timeout_ms)
+
+    def result(self, rid):
+        nt, nrec, nx, ny, nw, grad = self._meta.pop(rid)
+        tr = np.zeros((nt, max(nrec, 1)), np.float32)
+        gc = np.zeros((ny, nx), np.float32) if grad else None
+        gs = np.zeros(max(nw, 1), np.float64) if grad else None
+        st, times = lbac.lb_server_result(
+            self.srv, rid, ctypes.c_void_p(tr.ctypes.data),
+            ctypes.c_void_p(gc.ctypes.data) if grad else None,
+            ctypes.c_void_p(gs.ctypes.data) if grad else None)
+        if st != lbac.LB_OK:
+            raise lbac.LBError(st, lbac.lb_server_last_error(self.srv))
+        return {"traces": tr[:, :nrec], "grad_c": gc, "grad_src": gs[:nw] if grad else None,
+                "submit": times[0], "start": times[1], "done": times[2]}
+
+    def stats(self):
+        v = lbac.lb_server_stats(self.srv)
+        return {"done": v[0], "active": v[1], "pending": v[2], "bytes": v[3], "launches": v[4]}
+
+    def close(self):
+        if getattr(self, "srv", None):
+            lbac.lb_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

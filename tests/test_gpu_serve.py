@@ -1,0 +1,142 @@
+"""GPU tests of the continuous-batching shot server (lb_server_*).
+
+Each served result must be the same alone and in a mix of other requests of
+different sizes, storage types and kinds (the batched launch runs the same
+per-shot arithmetic), must match the FP64 oracle to FP32 tolerance, and
+gradient requests must match the direct adjoint.  Admission respects the
+device-memory budget.
+"""
+import numpy as np
+import pytest
+
+from paper_1704_03172_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_03172_gb300 import build
+    build.build()
+    from paper_1704_03172_gb300 import lbac
+    from paper_1704_03172_gb300.sim import LBServer, LBSim
+    return LBServer, LBSim, lbac
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def _shot(n, seed, nt, storage="f32", grad=False, lattice=5):
+    c = W.layered_fault_model(n, n, seed, n_layers=6, throw=(2.0, n / 16))
+    src = (n // 2, 6, W.ricker(nt, 0.05))
+    rec = W.line_receivers(16, 6, 4, n - 8)
+    spec = dict(nt=nt, source=src, receivers=rec, lattice=lattice, tau=0.5, storage=storage,
+                sponge_width=6, c_ref=5500.0)
+    if grad:
+        spec.update(want_gradient=True, observed=np.zeros((nt, len(rec)), np.float32),
+                    checkpoint_every=32)
+    return c, spec
+
+
+def test_result_is_identical_alone_and_in_the_mix(mods, oracle_mod):
+    LBServer, _, _ = mods
+    cA, sA = _shot(96, 1, 300)
+    srv = LBServer(max_active=1, rounds_per_pass=8)
+    a = srv.submit(cA, **sA)
+    srv.wait(a, 60000)
+    alone = srv.result(a)["traces"]
+    srv.close()
+    # a mix: different sizes, storage types, a gradient request, staggered arrivals
+    srv = LBServer(max_active=6, rounds_per_pass=8)
+    ids = []
+    for k, (n, st, g) in enumerate([(128, "f32", False), (64, "bf16", False), (160, "f32", True),
+                                     (80, "f16", False), (200, "bf16", False)]):
+        c, s = _shot(n, 10 + k, 200 + 37 * k, st, g)
+        ids.append(srv.submit(c, **s))
+    a2 = srv.submit(cA, **sA)
+    c, s = _shot(112, 30, 250)
+    ids.append(srv.submit(c, **s))
+    srv.wait(a2, 120000)
+    mixed = srv.result(a2)["traces"]
+    for i in ids:
+        srv.wait(i, 120000)
+        srv.result(i)
+    st = srv.stats()
+    srv.close()
+    np.testing.assert_array_equal(mixed, alone)
+    assert st["launches"] > 0
+    P = oracle_mod.Problem(5, 96, 96, cA, c_ref=5500.0, tau=0.5, sponge_width=6,
+                           sponge_sigma_max=0.1, source=sA["source"], receivers=sA["receivers"])
+    _, tro = oracle_mod.run(P, P.zeros(), sA["nt"])
+    assert rel(alone, tro) < 1e-5
+
+
+def test_gradient_request_matches_direct_adjoint(mods, oracle_mod):
+    LBServer, LBSim, _ = mods
+    n, nt = 72, 120
+    c, s = _shot(n, 4, nt, grad=True)
+    rng = np.random.default_rng(2)
+    d = rng.normal(size=(nt, 16)).astype(np.float32) * 1e-3
+    s["observed"] = d
+    srv = LBServer(max_active=4, rounds_per_pass=16)
+    rid = srv.submit(c, **s)
+    c2, s2 = _shot(90, 9, 180)
+    rid2 = srv.submit(c2, **s2)
+    srv.wait(rid, 120000)
+    res = srv.result(rid)
+    srv.wait(rid2, 120000)
+    srv.result(rid2)
+    srv.close()
+    P = oracle_mod.Problem(5, n, n, c, c_ref=5500.0, tau=0.5, sponge_width=6,
+                           sponge_sigma_max=0.1, source=s["source"], receivers=s["receivers"])
+    _, tro = oracle_mod.run(P, P.zeros(), nt)
+    assert rel(res["traces"], tro) < 1e-5
+    oc, os_, _ = oracle_mod.adjoint(P, P.zeros(), nt, (res["traces"] - d).astype(np.float64))
+    assert rel(res["grad_c"], oc) < 1e-4
+    assert rel(res["grad_src"], os_) < 1e-4
+
+
+def test_admission_respects_the_memory_budget(mods):
+    LBServer, _, lbac = mods
+    c, s = _shot(256, 3, 100)
+    cfg = lbac.lb_config_default()
+    cfg.nx = cfg.ny = 256
+    one = lbac.lb_footprint(cfg, 100, 16, 0)
+    srv = LBServer(max_active=8, hbm_budget=int(2.5 * one) + (1 << 20), rounds_per_pass=4)
+    ids = [srv.submit(c, **s) for _ in range(5)]
+    peak = 0
+    import time
+    t0 = time.time()
+    while not all(srv.poll(i) for i in ids) and time.time() - t0 < 120:
+        peak = max(peak, srv.stats()["active"])
+        time.sleep(0.002)
+    outs = [srv.result(i)["traces"] for i in ids]
+    srv.close()
+    assert peak <= 2                                   # at most two fit the budget at once
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+    big_c, big_s = _shot(512, 3, 100)
+    srv = LBServer(max_active=8, hbm_budget=int(2.5 * one), rounds_per_pass=4)
+    with pytest.raises(lbac.LBError) as e:
+        srv.submit(big_c, **big_s)
+    assert e.value.status == lbac.LB_ENOMEM
+    srv.close()
+
+
+def test_wait_times_out_and_then_completes(mods):
+    LBServer, _, lbac = mods
+    c, s = _shot(512, 5, 3000)
+    srv = LBServer(max_active=2, rounds_per_pass=4)
+    rid = srv.submit(c, **s)
+    with pytest.raises(lbac.LBError) as e:
+        srv.wait(rid, 0)
+    assert e.value.status == lbac.LB_ETIMEOUT
+    srv.wait(rid, 120000)
+    r = srv.result(rid)
+    srv.close()
+    assert r["done"] >= r["start"] >= r["submit"]
+    assert np.isfinite(r["traces"]).all()
