@@ -77,16 +77,15 @@ struct StepArgs {
     // FP16 storage: per-population power-of-two scale, value = stored * scale.
     // Three device slots rotate.  The scale of the input buffer and the one chosen
     // for the output buffer are ready before the launch; every block folds its
-    // max |output| into max_out, and the last block to finish derives the scale
-    // the next step will write with (scale_next, from 8 max|out| + |S[t+1]|) and
-    // clears max_next for it.  All nullptr for FP32 and BF16 storage (BF16 has
+    // max |output| into max_out, and a one-block kernel after the step derives the
+    // scale the next step will write with (scale_next, from 8 max|out| + |S[t+1]|)
+    // and clears max_next for it.  All nullptr for FP32 and BF16 storage (BF16 has
     // the exponent range of FP32 and needs no range scale).
     const float *scale_in;    // [9]
     const float *scale_out;   // [9]
     unsigned *max_out;        // [9][kMaxCopies] float bits of max |value| written
     float *scale_next;        // [9]
     unsigned *max_next;       // [9][kMaxCopies]
-    unsigned *done;           // block counter for the last-block hand-off
 };
 
 constexpr int kMaxCopies = 8;          // spread of the per-block atomicMax targets
@@ -478,10 +477,15 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
 }
 
 template <int Q, bool MRT, bool PERIODIC, typename ST>
-__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
+// Minimum resident blocks per SM: enough warps to keep ~100 KB of loads in
+// flight per SM (FP32 D2Q5 fits 5 blocks at <= 48 registers; the 8-site 16-bit
+// and the 9-population FP32 forms are held to 64 registers for 4 blocks; the
+// 9-population 16-bit form holds 72 values per thread and gets 80 registers).
+__global__ void __launch_bounds__(kThreads, Q == 5 ? (sizeof(ST) == 4 ? 5 : 4)
+                                                     : (sizeof(ST) == 4 ? 4 : 2))
+    step_kernel(const StepArgs a) {
     constexpr bool SC = Scaled<ST>::value;
     __shared__ float s_wmax[SC ? 9 : 1][kWarps];
-    __shared__ bool s_last;
     if ((int)blockIdx.x >= a.main_blocks) {  // block-uniform
         gather_receivers<Q, PERIODIC, ST>(a, ((int)blockIdx.x - a.main_blocks) * kThreads +
                                                  (int)threadIdx.x);
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     }
     float tmax[Q];
     step_sites<Q, MRT, PERIODIC, ST>(a, blockIdx.x, tmax);
-    if (SC) {
+    if (SC) {  // fold this block's max |output| per population into max_out
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
@@ -506,27 +510,21 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
             atomicMax(a.max_out + threadIdx.x * kMaxCopies + (blockIdx.x % kMaxCopies),
                       __float_as_uint(m));
         }
-        // last block: derive the scale of the next step's output from this step's maxima
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0)
-            s_last = atomicAdd(a.done, 1u) == (unsigned)a.main_blocks - 1u;
-        __syncthreads();
-        if (s_last && (int)threadIdx.x < Q) {
-            __threadfence();
-            const int i = threadIdx.x;
-            float m = 0.f;
-#pragma unroll
-            for (int c = 0; c < kMaxCopies; c++)
-                m = fmaxf(m, __uint_as_float(atomicOr(a.max_out + i * kMaxCopies + c, 0u)));
-            const long long tn = a.t + 1;
-            const float S = (a.src_tab && tn < a.src_nt) ? fabsf(a.src_tab[tn]) : 0.f;
-            a.scale_next[i] = next_scale(m, S, a.scale_out[i]);
-#pragma unroll
-            for (int c = 0; c < kMaxCopies; c++) a.max_next[i * kMaxCopies + c] = 0u;
-            if (i == 0) *a.done = 0u;
-        }
     }
+}
+
+// FP16, after each step (one block): the scale the next step writes with, from
+// this step's maxima (8 max|out| + |S[t+1]| at or below kStoredTarget), and a
+// cleared max slot for the next step.
+static __global__ void scale_update_kernel(StepArgs a, int Q) {
+    const int i = threadIdx.x;
+    if (i >= Q) return;
+    float m = 0.f;
+    for (int c = 0; c < kMaxCopies; c++) m = fmaxf(m, __uint_as_float(a.max_out[i * kMaxCopies + c]));
+    const long long tn = a.t + 1;
+    const float S = (a.src_tab && tn < a.src_nt) ? fabsf(a.src_tab[tn]) : 0.f;
+    a.scale_next[i] = next_scale(m, S, a.scale_out[i]);
+    for (int c = 0; c < kMaxCopies; c++) a.max_next[i * kMaxCopies + c] = 0u;
 }
 
 // ------------------------------------------------------------ batched step --
@@ -660,7 +658,6 @@ static __global__ void init_scale_kernel(StepArgs a, int Q, float *scale_first) 
     const float S = (a.src_tab && a.t < a.src_nt) ? fabsf(a.src_tab[a.t]) : 0.f;
     scale_first[i] = next_scale(m, S, s0);
     for (int c = 0; c < kMaxCopies; c++) a.max_next[i * kMaxCopies + c] = 0u;
-    if (i == 0) *a.done = 0u;
 }
 
 // eta^2 = (c / c_ref)^2 per site (pads 0); flags: bit0 c <= 0 or non-finite, bit1 eta > 1.

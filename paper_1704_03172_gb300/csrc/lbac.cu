@@ -459,7 +459,6 @@ static lb_status set_state_common(lb_ctx *ctx, const float *src, int on_device, 
         a.max_out = ctx->lp_max + s0 * 9 * kMaxCopies;
         a.scale_next = ctx->lp_scale + s0 * 9;
         a.max_next = ctx->lp_max + s1 * 9 * kMaxCopies;
-        a.done = ctx->lp_max + 3 * 9 * kMaxCopies;
         if (dev) {
             if (ctx->Q == 9)
                 source_max_kernel<9><<<1024, 256, 0, ctx->stream>>>(a, dev, mode);
@@ -567,7 +566,6 @@ lb_status launch_step(lb_ctx *ctx, StepFn fn, StepArgs &a) {
         a.max_out = ctx->lp_max + s1 * 9 * kMaxCopies;
         a.scale_next = ctx->lp_scale + s2 * 9;
         a.max_next = ctx->lp_max + s2 * 9 * kMaxCopies;
-        a.done = ctx->lp_max + 3 * 9 * kMaxCopies;
         ctx->lp_slot = s1;
     }
     a.raw = ctx->raw ? 1 : 0;
@@ -577,6 +575,7 @@ lb_status launch_step(lb_ctx *ctx, StepFn fn, StepArgs &a) {
                                                                   : nullptr;
     int rec_blocks = a.trace_row ? (ctx->nrec + kThreads - 1) / kThreads : 0;
     fn<<<a.main_blocks + rec_blocks, kThreads, 0, ctx->stream>>>(a);
+    if (ctx->lp_scale) scale_update_kernel<<<1, 32, 0, ctx->stream>>>(a, ctx->Q);
     ctx->cur ^= 1;
     ctx->t += 1;
     return LB_OK;
