@@ -185,6 +185,47 @@ def _refined_variant(torch, LBSim, steps, warmup):
             "launches_per_coarse_step": 7}
 
 
+def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32"):
+    """Gradient of J = 1/2 sum p^2 over 512 receiver traces w.r.t. the sound-speed map and
+    the source, for a 20-layer faulted model: forward run with checkpoints, then lb_adjoint
+    (replay + reverse sweep).  Rates count n^2 * nt site-steps of the gradient call."""
+    c = W.layered_fault_model(n, n, W.DEFAULT_SEED + 4, n_layers=20,
+                              throw=(20.0 * n / 8192, 200.0 * n / 8192))
+    sim = LBSim(c, lattice=5, tau=0.5, c_ref=W.SERVED_C_REF, sponge_width=40, storage=storage)
+    try:
+        sim.set_source(n // 2, 48, W.ricker(nt, W.SERVED_FC))
+        sim.set_receivers(W.line_receivers(512, 48, 40, n - 80), nt)
+        sim.init_pressure(None)
+        sim.checkpoint_every(every)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(nt)
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+        R = sim.traces(nt).clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gc, gs, _ = sim.adjoint(R, nt)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        finite = bool(torch.isfinite(gc).all().item())
+    finally:
+        sim.close()
+    T = min(every, (16 << 30) // (n * n * 4))
+    levels = 1 if T >= every else 2
+    bps_fwd = BYTES_PER_SITE[(5, storage)]
+    # per adjoint site-step: `levels` replays (+4 B rho store on the recorded one) and the
+    # adjoint step (lambda pull + store 2*5*4, rho 4, eta^2 4, FP64 gradient RMW 16)
+    bps = levels * bps_fwd + 4 + 2 * 5 * 4 + 4 + 4 + 16
+    upd = n * n * nt
+    return {"gradient_glups": round(upd / t_adj / 1e9, 2),
+            "forward_with_checkpoints_glups": round(upd / t_fwd / 1e9, 2),
+            "bytes_per_site_step": bps, "achieved_gbs": round(upd * bps / t_adj / 1e9, 1),
+            "replay_levels": levels, "seconds": round(t_adj, 4), "finite": finite,
+            "workload": f"{n}x{n} 20-layer faulted model, D2Q5 BGK {storage.upper()}, {nt} steps, "
+                        f"checkpoint every {every}, 512 receivers, wall time of lb_adjoint"}
+
+
 def _e2e(torch, LBSim, steps_shot):
     """One full shot through the public API with host buffers (create .. traces .. destroy)."""
     from paper_1704_03172_gb300.sim import LBSim as _S  # noqa: F401
@@ -209,9 +250,95 @@ def _e2e(torch, LBSim, steps_shot):
     assert n == steps_shot
     h2d = c_host.nbytes + len(wav) * 8 + rec.nbytes
     return {"value": round(N_GRID * N_GRID * steps_shot / sec / 1e9, 2), "unit": UNIT,
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes),
+            "h2d_bytes_per_step": round(h2d / steps_shot, 1),
+            "d2h_bytes_per_step": round(out.nbytes / steps_shot, 1),
+            "h2d_bytes_per_shot": int(h2d), "d2h_bytes_per_shot": int(out.nbytes),
             "step": f"one {steps_shot}-step shot: lb_create(host c_map) .. lb_step .. "
                     "lb_record_receivers(host) .. lb_destroy", "seconds": round(sec, 4)}
+
+
+def _served(n_req, n_cal, seed=W.DEFAULT_SEED + 5, load=0.7, max_active=64):
+    """Served shot stream through lb_server_*: ``n_req`` shots with Poisson arrivals at
+    ``load`` x the closed-loop capacity measured on ``n_cal`` calibration shots.
+
+    Each shot: grid side from {256, 512, 1024, 2048}, 2000-8000 steps, its own seeded
+    layered-fault model (4-12 layers), FP32 or BF16 storage with p = 1/2, and with
+    p = 1/4 an adjoint gradient of J = 1/2 sum p^2 (zero observed data, checkpoint every
+    200 steps).  Latency = result ready - submit (the arrival).  GLUPS counts forward
+    site updates only."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1704_03172_gb300.sim import LBServer
+
+    descs = W.served_requests(n_req, seed)
+    cal = W.served_requests(n_cal, seed + 1, id0=1_000_000)
+    t_gen = time.perf_counter()
+    with ThreadPoolExecutor(8) as ex:
+        shots = list(ex.map(W.served_shot, descs))
+        cal_shots = list(ex.map(W.served_shot, cal))
+    t_gen = time.perf_counter() - t_gen
+
+    def submit(srv, s):
+        kw = dict(s)
+        c = kw.pop("c_map")
+        if kw["want_gradient"]:
+            kw["observed"] = np.zeros((kw["nt"], len(kw["receivers"])), np.float32)
+            kw["checkpoint_every"] = 200
+        return srv.submit(c, **kw)
+
+    def collect(srv, ids, out):
+        for i in ids:
+            srv.wait(i)
+            out.append(srv.result(i))
+
+    srv = LBServer(max_active=max_active, rounds_per_pass=16, adjoint_workers=4)
+    try:
+        t0 = time.monotonic()
+        ids = [submit(srv, s) for s in cal_shots]
+        done = []
+        collect(srv, ids, done)
+        cal_s = time.monotonic() - t0
+        capacity = n_cal / cal_s
+        lam = load * capacity
+        arrivals = np.cumsum(np.random.default_rng(seed + 2).exponential(1.0 / lam, n_req))
+        launches0 = srv.stats()["launches"]
+        ids, res = [], []
+        import queue
+        q = queue.Queue()
+        th = threading.Thread(target=lambda: collect(srv, iter(q.get, None), res), daemon=True)
+        th.start()
+        t0 = time.monotonic()
+        for k, s in enumerate(shots):
+            dt = t0 + arrivals[k] - time.monotonic()
+            if dt > 0:
+                time.sleep(dt)
+            rid = submit(srv, s)
+            ids.append(rid)
+            q.put(rid)
+        q.put(None)
+        th.join()
+        launches = srv.stats()["launches"] - launches0
+    finally:
+        srv.close()
+    lat = np.array([r["done"] - r["submit"] for r in res])
+    span = max(r["done"] for r in res) - min(r["submit"] for r in res)
+    fwd = sum(d["n"] ** 2 * d["nt"] for d in descs)
+    finite = all(np.isfinite(r["traces"]).all() for r in res)
+    return {"requests": n_req, "shots_per_s": round(n_req / span, 3),
+            "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+            "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
+            "mean_latency_s": round(float(lat.mean()), 4),
+            "forward_glups": round(fwd / span / 1e9, 2), "span_s": round(span, 2),
+            "offered_rate_per_s": round(lam, 3), "load": load,
+            "calibrated_capacity_per_s": round(capacity, 3),
+            "calibration": f"{n_cal} shots of the same distribution submitted at once, "
+                           f"{cal_s:.2f} s", "launches": int(launches),
+            "gradients": sum(d["grad"] for d in descs),
+            "bf16": sum(d["storage"] == "bf16" for d in descs),
+            "forward_updates": fwd, "finite": bool(finite), "max_active": max_active,
+            "input_generation_s": round(t_gen, 2),
+            "shot": "D2Q5 BGK tau=1/2, layered-fault model (4-12 layers, c 1500-5500 m/s), "
+                    "Ricker 10 ppw at 1500 m/s, 40-cell sponge, 128 receivers; side from "
+                    "{256,512,1024,2048}, 2000-8000 steps"}
 
 
 def _cpu_sample(target_s=12.0, lattice=5):
@@ -371,9 +498,19 @@ def run_ours(args):
             v["refined_block_2048_d2q5_mrt_f32"] = _refined_variant(torch, LBSim, 400, 10)
         except Exception as ex:
             v["refined_block_2048_d2q5_mrt_f32"] = {"error": str(ex)[:200]}
+        for st in ("f32", "bf16"):
+            try:
+                v[f"adjoint_4096_d2q5_{st}"] = _adjoint_variant(torch, LBSim, storage=st)
+            except Exception as ex:
+                v[f"adjoint_4096_d2q5_{st}"] = {"error": str(ex)[:200]}
         line["variants"] = v
     if not args.no_e2e:
         line["e2e"] = _e2e(torch, LBSim, args.e2e_steps)
+    if args.served_requests > 0:
+        try:
+            line["served"] = _served(args.served_requests, args.served_calibration)
+        except Exception as ex:  # report, do not hide
+            line["served"] = {"error": str(ex)[:300]}
     if not args.no_cpu:
         line["cpu_baseline"] = _cpu_sample(args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -393,6 +530,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--served-requests", type=int, default=512,
+                    help="shots in the served stream (0 skips it)")
+    ap.add_argument("--served-calibration", type=int, default=64,
+                    help="closed-loop shots that set the Poisson arrival rate")
     ap.add_argument("--lattice", type=int, choices=[5, 9], default=5,
                     help="main line's lattice (D2Q5 is the paper's recommended scheme)")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")

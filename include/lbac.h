@@ -144,7 +144,8 @@ lb_status lb_sync(lb_ctx *ctx);
 /* Keep adjoint checkpoints: from now on (time t0 = current time), lb_step copies
  * the state into device memory before every step t with (t - t0) % every == 0.
  * every = 0 stops.  lb_init_pressure and lb_set_state restart the run of
- * checkpoints at their time.  Needs FP32 storage and no patch (LB_ESTATE). */
+ * checkpoints at their time.  Needs FP32 or BF16 storage and no patch
+ * (LB_ESTATE); BF16 checkpoints are BF16 states (half the memory). */
 lb_status lb_checkpoint_every(lb_ctx *ctx, int every);
 
 /* Discrete adjoint of the nt steps that followed the checkpointed start time
@@ -156,7 +157,10 @@ lb_status lb_checkpoint_every(lb_ctx *ctx, int every);
  * grad_src [nt] = dJ/dS[t0 + n], grad_g0 [Q][ny][nx] = dJ/dg(t0).
  * on_device applies to dJdp and all outputs.  Forward states are replayed
  * from the checkpoints (two levels, ~2 sqrt(every) + 3 extra states of device
- * memory).  The context's own state is left untouched.  Synchronises. */
+ * memory).  The context's own state is left untouched.  Synchronises.
+ * With BF16 storage the replayed forward states are the stored BF16 ones and the
+ * adjoint runs in FP32: the gradient of the exact scheme along that trajectory,
+ * which differs from the FP32 run's by about the forward's BF16 error. */
 lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *grad_c, double *grad_src,
                      float *grad_g0, int on_device);
 

@@ -21,6 +21,14 @@
 // sub-segment is replayed again keeping all its states, then swept backwards.
 // Device memory: the checkpoints, ~2 sqrt(C) + 3 states, the adjoint pair and
 // an FP64 gradient.
+//
+// BF16 storage: the checkpoints and replayed states are the BF16 states the
+// forward run produced (the replay runs the same kernel on the same inputs, so
+// it reproduces them bit for bit); the adjoint state stays FP32.  The result is
+// the transpose of the exact linear step taken along the stored trajectory, so
+// its distance from the FP32 gradient is of the order of the forward's BF16
+// error.  FP16 storage is not supported (its per-step range scales would have
+// to be replayed as well).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,146 +60,147 @@ __device__ __forceinline__ float dcs2(const StepArgs &a) {
 struct AdjArgs {
     const float *lam_in;   // lambda^{t+1} [Q][ny][pitch]
     float *lam_out;        // lambda^t
-    const float *fwd;      // forward buffer whose pull gives g^t (raw: g^t itself)
-    int fwd_raw;
+    const float *rho;      // rho(x, t) of the forward state g^t, [ny][pitch] (replay tape)
     double *grad;          // dJ/d(eta^2), [ny][pitch]
     double *grad_src;      // [nt] (indexed by t - t0) or nullptr
     long long t0;
     const float *resid;    // dJ/dp, [nt][nrec] (row t - t0)
     int nrec;
+    int segs;              // warps per row: ceil(nx / 128)
 };
 
+// One adjoint step for 4 consecutive x-sites per thread (16-byte FP32 vectors;
+// the +-1 x-shift of the reverse pull is a warp shuffle, as in the forward step).
 template <int Q, bool MRT, bool PERIODIC>
-__global__ void __launch_bounds__(256) adjoint_kernel(const StepArgs a, const AdjArgs d) {
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= (long long)a.ny * a.pitch) return;
-    const int y = (int)(idx / a.pitch), x = (int)(idx - (long long)y * a.pitch);
-    if (x >= a.nx) return;
-    const float e2 = a.eta2[idx];
-    const float f = a.sponge_w > 0 ? sponge_factor(x, y, a) : 1.f;
-    float mu[Q], rho = 0.f;
+__global__ void __launch_bounds__(kThreads, Q == 5 ? 4 : 3) adjoint_kernel(const StepArgs a, const AdjArgs d) {
+    constexpr int V = 4;
+    const int lane = threadIdx.x & 31;
+    const int wid = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int y = wid / d.segs;
+    if (y >= a.ny) return;  // warp-uniform
+    const int x0 = (wid - y * d.segs) * (32 * V) + lane * V;
+    const bool active = x0 < a.nx;
+    // mu_i(x) = (1 - sigma(x)) lambda_i^{t+1}(x + c_i): P^T pulls from x + c_i
+    float mu[Q][V];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        int xd = x + Lat<Q>::cx(i), yd = y + Lat<Q>::cy(i);
-        float v = 0.f;
-        bool ok = true;
-        if (PERIODIC) {
-            xd = (xd + a.nx) % a.nx;
-            yd = (yd + a.ny) % a.ny;
+        const float *row = src_row<PERIODIC>(d.lam_in + i * a.plane, y + Lat<Q>::cy(i), a.ny, a.pitch);
+        const int cx = Lat<Q>::cx(i);
+        if (cx == 1)
+            pullV<-1, PERIODIC>(row, x0, lane, a.nx, active, 1.f, mu[i]);
+        else if (cx == -1)
+            pullV<1, PERIODIC>(row, x0, lane, a.nx, active, 1.f, mu[i]);
+        else
+            pullV<0, PERIODIC>(row, x0, lane, a.nx, active, 1.f, mu[i]);
+    }
+    if (!active) return;  // no shuffles below
+    const long long base = (long long)y * a.pitch + x0;
+    const float4 e4 = *reinterpret_cast<const float4 *>(a.eta2 + base);
+    const float4 r4 = *reinterpret_cast<const float4 *>(d.rho + base);
+    const float e2s[V] = {e4.x, e4.y, e4.z, e4.w}, rhos[V] = {r4.x, r4.y, r4.z, r4.w};
+    const bool edge = a.sponge_w > 0 &&
+                      (y < a.sponge_w || y >= a.ny - a.sponge_w || x0 < a.sponge_w ||
+                       x0 + V - 1 >= a.nx - a.sponge_w);
+    const bool has_src = (y == a.src_y) && (a.src_x >= x0) && (a.src_x < x0 + V) && a.src_tab;
+    double gadd[V];
+#pragma unroll
+    for (int k = 0; k < V; k++) {
+        const float f = edge ? sponge_factor(x0 + k, y, a) : 1.f;
+        float m[Q];
+#pragma unroll
+        for (int i = 0; i < Q; i++) m[i] = f * mu[i][k];
+        // w_j and w_j / c_s^2 (eta-independent for j > 0)
+        float w[Q], wc[Q];
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            w[i] = weight_i<Q>(i, e2s[k], a);
+            wc[i] = i == 0 ? 0.f : (Q == 5 ? 0.5f : (i < 5 ? a.a1 : a.a5));
+        }
+        // v = C^T mu (non-conserved part for MRT; all of it for BGK)
+        float v[Q];
+        if (!MRT) {
+#pragma unroll
+            for (int i = 0; i < Q; i++) v[i] = a.omega * m[i];
+        } else if (Q == 5) {
+            // rows 3 (e) and 4 (p_xx) of M, norms 20 and 4
+            const float me = (-4.f * m[0] + m[1] + m[2] + m[3] + m[4]) * a.s[3] * (1.f / 20.f);
+            const float mp = (m[1] - m[2] + m[3] - m[4]) * a.s[4] * 0.25f;
+            v[0] = -4.f * me;
+            v[1] = me + mp;
+            v[2] = me - mp;
+            v[3] = me + mp;
+            v[4] = me - mp;
         } else {
-            ok = xd >= 0 && xd < a.nx && yd >= 0 && yd < a.ny;
+            const float s14 = m[1] + m[2] + m[3] + m[4], s58 = m[5] + m[6] + m[7] + m[8];
+            const float d3 = a.s[3] * (-4.f * m[0] - s14 + 2.f * s58) * (1.f / 36.f);
+            const float d4 = a.s[4] * (m[1] - m[2] + m[3] - m[4]) * 0.25f;
+            const float d5 = a.s[5] * (4.f * m[0] - 2.f * s14 + s58) * (1.f / 36.f);
+            const float d6 = a.s[6] * (-2.f * m[1] + 2.f * m[3] + m[5] - m[6] - m[7] + m[8]) *
+                             (1.f / 12.f);
+            const float d7 = a.s[7] * (-2.f * m[2] + 2.f * m[4] + m[5] + m[6] - m[7] - m[8]) *
+                             (1.f / 12.f);
+            const float d8 = a.s[8] * (m[5] - m[6] + m[7] - m[8]) * 0.25f;
+            v[0] = -4.f * d3 + 4.f * d5;
+            v[1] = -d3 + d4 - 2.f * d5 - 2.f * d6;
+            v[2] = -d3 - d4 - 2.f * d5 - 2.f * d7;
+            v[3] = -d3 + d4 - 2.f * d5 + 2.f * d6;
+            v[4] = -d3 - d4 - 2.f * d5 + 2.f * d7;
+            const float c5 = 2.f * d3 + d5;
+            v[5] = c5 + d6 + d7 + d8;
+            v[6] = c5 - d6 + d7 - d8;
+            v[7] = c5 - d6 - d7 + d8;
+            v[8] = c5 + d6 - d7 - d8;
         }
-        if (ok) v = d.lam_in[i * a.plane + (long long)yd * a.pitch + xd];
-        mu[i] = f * v;
-        // forward population g^t_i(x)
-        int xs = x, ys = y;
-        if (!d.fwd_raw) {
-            xs -= Lat<Q>::cx(i);
-            ys -= Lat<Q>::cy(i);
+        // K^T mu = mu - (I - E^T) v, (E^T v)_i = sum_j w_j v_j + c_i . sum_j (w_j / c_s^2) c_j v_j
+        float A = 0.f, Bx = 0.f, By = 0.f;
+#pragma unroll
+        for (int j = 0; j < Q; j++) {
+            A += w[j] * v[j];
+            Bx += wc[j] * Lat<Q>::cx(j) * v[j];
+            By += wc[j] * Lat<Q>::cy(j) * v[j];
         }
-        bool okf = true;
-        if (PERIODIC) {
-            xs = (xs + a.nx) % a.nx;
-            ys = (ys + a.ny) % a.ny;
-        } else {
-            okf = xs >= 0 && xs < a.nx && ys >= 0 && ys < a.ny;
+        float gsum = 0.f, src_w = 0.f, src_dw = 0.f;
+        const bool real = x0 + k < a.nx;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const float et = A + Lat<Q>::cx(i) * Bx + Lat<Q>::cy(i) * By;
+            const float dw = dweight<Q>(i, a);
+            gsum += v[i] * dw;
+            src_w += w[i] * m[i];
+            src_dw += dw * m[i];
+            mu[i][k] = real ? m[i] - v[i] + et : 0.f;  // becomes lambda^t
         }
-        if (okf) rho += d.fwd[i * a.plane + (long long)ys * a.pitch + xs];
+        gadd[k] = (double)rhos[k] * (double)gsum;
+        if (has_src && a.src_x == x0 + k) {
+            if (d.grad_src) d.grad_src[a.t - d.t0] = (double)src_w;
+            if (a.t < a.src_nt) gadd[k] += (double)a.src_tab[a.t] * (double)src_dw;
+        }
     }
-    // w_j and w_j / c_s^2 (eta-independent for j > 0)
-    float w[Q], wc[Q];
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-        w[i] = weight_i<Q>(i, e2, a);
-        wc[i] = i == 0 ? 0.f : (Q == 5 ? 0.5f : (i < 5 ? a.a1 : a.a5));
-    }
-    // v = C^T mu (non-conserved part for MRT; all of it for BGK)
-    float v[Q];
-    if (!MRT) {
-#pragma unroll
-        for (int i = 0; i < Q; i++) v[i] = a.omega * mu[i];
-    } else if (Q == 5) {
-        // rows 3 (e) and 4 (p_xx) of M, norms 20 and 4
-        const float me = (-4.f * mu[0] + mu[1] + mu[2] + mu[3] + mu[4]) * a.s[3] * (1.f / 20.f);
-        const float mp = (mu[1] - mu[2] + mu[3] - mu[4]) * a.s[4] * 0.25f;
-        v[0] = -4.f * me;
-        v[1] = me + mp;
-        v[2] = me - mp;
-        v[3] = me + mp;
-        v[4] = me - mp;
-    } else {
-        const float s14 = mu[1] + mu[2] + mu[3] + mu[4], s58 = mu[5] + mu[6] + mu[7] + mu[8];
-        const float d3 = a.s[3] * (-4.f * mu[0] - s14 + 2.f * s58) * (1.f / 36.f);
-        const float d4 = a.s[4] * (mu[1] - mu[2] + mu[3] - mu[4]) * 0.25f;
-        const float d5 = a.s[5] * (4.f * mu[0] - 2.f * s14 + s58) * (1.f / 36.f);
-        const float d6 = a.s[6] * (-2.f * mu[1] + 2.f * mu[3] + mu[5] - mu[6] - mu[7] + mu[8]) *
-                         (1.f / 12.f);
-        const float d7 = a.s[7] * (-2.f * mu[2] + 2.f * mu[4] + mu[5] + mu[6] - mu[7] - mu[8]) *
-                         (1.f / 12.f);
-        const float d8 = a.s[8] * (mu[5] - mu[6] + mu[7] - mu[8]) * 0.25f;
-        v[0] = -4.f * d3 + 4.f * d5;
-        v[1] = -d3 + d4 - 2.f * d5 - 2.f * d6;
-        v[2] = -d3 - d4 - 2.f * d5 - 2.f * d7;
-        v[3] = -d3 + d4 - 2.f * d5 + 2.f * d6;
-        v[4] = -d3 - d4 - 2.f * d5 + 2.f * d7;
-        const float c5 = 2.f * d3 + d5;
-        v[5] = c5 + d6 + d7 + d8;
-        v[6] = c5 - d6 + d7 - d8;
-        v[7] = c5 - d6 - d7 + d8;
-        v[8] = c5 + d6 - d7 - d8;
-    }
-    // K^T mu = mu - (I - E^T) v, (E^T v)_i = sum_j w_j v_j + c_i . sum_j (w_j / c_s^2) c_j v_j
-    float A = 0.f, Bx = 0.f, By = 0.f;
-#pragma unroll
-    for (int j = 0; j < Q; j++) {
-        A += w[j] * v[j];
-        Bx += wc[j] * Lat<Q>::cx(j) * v[j];
-        By += wc[j] * Lat<Q>::cy(j) * v[j];
-    }
-    float gsum = 0.f, src_w = 0.f, src_dw = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const float et = A + Lat<Q>::cx(i) * Bx + Lat<Q>::cy(i) * By;
-        d.lam_out[i * a.plane + idx] = mu[i] - v[i] + et;
-        const float dw = dweight<Q>(i, a);
-        gsum += v[i] * dw;
-        src_w += w[i] * mu[i];
-        src_dw += dw * mu[i];
-    }
-    double gadd = (double)rho * (double)gsum;
-    if (x == a.src_x && y == a.src_y && a.src_tab) {
-        if (d.grad_src) d.grad_src[a.t - d.t0] = (double)src_w;
-        if (a.t < a.src_nt) gadd += (double)a.src_tab[a.t] * (double)src_dw;
-    }
-    d.grad[idx] += gadd;
+    for (int i = 0; i < Q; i++)
+        *reinterpret_cast<float4 *>(d.lam_out + i * a.plane + base) =
+            make_float4(mu[i][0], mu[i][1], mu[i][2], mu[i][3]);
+    double2 *gp = reinterpret_cast<double2 *>(d.grad + base);
+    double2 g01 = gp[0], g23 = gp[1];
+    g01.x += gadd[0];
+    g01.y += gadd[1];
+    g23.x += gadd[2];
+    g23.y += gadd[3];
+    gp[0] = g01;
+    gp[1] = g23;
 }
 
 // receivers: lambda^t += R^t_r c_s^2(x_r) (every population), dJ/d(eta^2) += R dc_s^2 rho^t
-template <int Q, bool PERIODIC>
+template <int Q>
 __global__ void adjoint_receivers(const StepArgs a, const AdjArgs d) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d.nrec) return;
     const int2 xy = a.rec[r];
     const long long idx = (long long)xy.y * a.pitch + xy.x;
     const float R = d.resid[(a.t - d.t0) * d.nrec + r];
-    float rho = 0.f;
-    for (int i = 0; i < Q; i++) {
-        int xs = xy.x, ys = xy.y;
-        if (!d.fwd_raw) {
-            xs -= Lat<Q>::cx(i);
-            ys -= Lat<Q>::cy(i);
-        }
-        if (PERIODIC) {
-            xs = (xs + a.nx) % a.nx;
-            ys = (ys + a.ny) % a.ny;
-        } else if (xs < 0 || xs >= a.nx || ys < 0 || ys >= a.ny) {
-            continue;
-        }
-        rho += d.fwd[i * a.plane + (long long)ys * a.pitch + xs];
-    }
     const float c2 = cs2_of<Q>(a.eta2[idx], a);
     for (int i = 0; i < Q; i++) atomicAdd(d.lam_out + i * a.plane + idx, R * c2);
-    atomicAdd(d.grad + idx, (double)R * (double)dcs2<Q>(a) * (double)rho);
+    atomicAdd(d.grad + idx, (double)R * (double)dcs2<Q>(a) * (double)d.rho[idx]);
 }
 
 // dJ/dc = dJ/d(eta^2) * 2 eta / c_ref, and lambda^0 unpadded
@@ -218,10 +227,7 @@ AdjFn pick_adj(int Q, bool mrt, bool per) {
     return mrt ? adj_fn<5, true>(per) : adj_fn<5, false>(per);
 }
 
-AdjFn pick_adj_rec(int Q, bool per) {
-    if (Q == 9) return per ? adjoint_receivers<9, true> : adjoint_receivers<9, false>;
-    return per ? adjoint_receivers<5, true> : adjoint_receivers<5, false>;
-}
+AdjFn pick_adj_rec(int Q) { return Q == 9 ? adjoint_receivers<9> : adjoint_receivers<5>; }
 
 }  // namespace
 
@@ -271,8 +277,8 @@ bool ckpt_reserve(lb_ctx *ctx, void **dst, const void **src, size_t *bytes) {
 extern "C" lb_status lb_checkpoint_every(lb_ctx *ctx, int every) {
     if (!ctx) return LB_EINVAL;
     if (every < 0) return fail(ctx, LB_EINVAL, "every < 0");
-    if (every > 0 && (ctx->refined || ctx->cfg.storage != LB_F32))
-        return fail(ctx, LB_ESTATE, "the adjoint needs an FP32 context without a patch");
+    if (every > 0 && (ctx->refined || (ctx->cfg.storage != LB_F32 && ctx->cfg.storage != LB_BF16)))
+        return fail(ctx, LB_ESTATE, "the adjoint needs an FP32 or BF16 context without a patch");
     ctx->ckpt_every = every;
     ckpt_reset(ctx);
     return LB_OK;
@@ -291,9 +297,12 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
     if (ctx->nrec > 0 && ctx->ckpt_t0 != ctx->t_rec0)
         return fail(ctx, LB_ESTATE, "receivers must be set at the checkpointed start time");
     const int Q = ctx->Q;
-    const size_t plane = (size_t)ctx->ny * ctx->pitch, sbytes = (size_t)Q * plane * 4;
-    const int C2 = std::max(1, (int)std::ceil(std::sqrt((double)C)));
-    const int nsub = (C + C2 - 1) / C2;
+    // forward states (checkpoints, replays) in the storage type; adjoint states FP32
+    const size_t plane = (size_t)ctx->ny * ctx->pitch, sbytes = (size_t)Q * plane * ctx->ebytes,
+                 lbytes = (size_t)Q * plane * 4;
+    // replay plan: the rho tape holds T steps; sub-checkpoints every T steps when T < C
+    const int T = adj_tape_steps(plane * 4, C);
+    const int nsub = (C + T - 1) / T;
     std::vector<void *> mine;
     auto grab = [&](size_t b) {
         void *p = dev_alloc(ctx, b);
@@ -305,14 +314,17 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
         for (void *p : mine) dev_free(ctx, p);
         return st;
     };
-    std::vector<float *> X(C2 + 1), SC(nsub);
+    void *X[2];
     for (auto &p : X)
-        if (!(p = static_cast<float *>(grab(sbytes)))) return release(fail(ctx, LB_ENOMEM, "replay states"));
-    for (auto &p : SC)
-        if (!(p = static_cast<float *>(grab(sbytes)))) return release(fail(ctx, LB_ENOMEM, "sub-checkpoints"));
+        if (!(p = grab(sbytes))) return release(fail(ctx, LB_ENOMEM, "replay states"));
+    std::vector<void *> SC(nsub, nullptr);  // SC[0] is the segment's checkpoint itself
+    for (int j = 1; j < nsub; j++)
+        if (!(SC[j] = grab(sbytes))) return release(fail(ctx, LB_ENOMEM, "sub-checkpoints"));
+    float *tape = static_cast<float *>(grab((size_t)T * plane * 4));
+    if (!tape) return release(fail(ctx, LB_ENOMEM, "rho tape (%d steps)", T));
     float *L[2];
     for (auto &p : L)
-        if (!(p = static_cast<float *>(grab(sbytes)))) return release(fail(ctx, LB_ENOMEM, "adjoint state"));
+        if (!(p = static_cast<float *>(grab(lbytes)))) return release(fail(ctx, LB_ENOMEM, "adjoint state"));
     double *grad = static_cast<double *>(grab(plane * 8));
     double *gsrc = static_cast<double *>(grab((size_t)nt * 8));
     float *resid = nullptr;
@@ -327,67 +339,63 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
                             ctx->stream);
         }
     }
-    cudaMemsetAsync(L[0], 0, sbytes, ctx->stream);
-    cudaMemsetAsync(L[1], 0, sbytes, ctx->stream);
+    cudaMemsetAsync(L[0], 0, lbytes, ctx->stream);
+    cudaMemsetAsync(L[1], 0, lbytes, ctx->stream);
     cudaMemsetAsync(grad, 0, plane * 8, ctx->stream);
     cudaMemsetAsync(gsrc, 0, (size_t)nt * 8, ctx->stream);
 
     const bool mrt = ctx->cfg.collision == LB_MRT, per = ctx->cfg.boundary == LB_PERIODIC;
     StepFn fwd = pick_step(ctx);
-    AdjFn adj = pick_adj(Q, mrt, per), adj_rec = pick_adj_rec(Q, per);
+    AdjFn adj = pick_adj(Q, mrt, per), adj_rec = pick_adj_rec(Q);
     StepArgs base = base_args(ctx);
     base.trace_row = nullptr;  // replays record nothing
     const long long t0 = ctx->ckpt_t0;
-    const int grid_sites = (int)((plane + 255) / 256);
-    // one forward step of the replay: in -> out at absolute time t
-    auto replay = [&](const float *in, bool raw, float *out, long long t) {
-        StepArgs a = base;
-        a.in = in;
-        a.out = out;
-        a.raw = raw ? 1 : 0;
-        a.t = t;
-        fwd<<<a.main_blocks, kThreads, 0, ctx->stream>>>(a);
+    const int segs4 = (ctx->nx + 127) / 128;
+    const int adj_blocks = (int)(((long long)ctx->ny * segs4 + kWarps - 1) / kWarps);
+    // replay steps t = from .. from + n - 1 starting at state `in`; the state after the
+    // last one goes to `last` (when given); rho(t) goes to tape[t - from] (when given)
+    auto replay = [&](const void *in, bool raw, long long from, int n, void *last, bool record) {
+        int x = 0;
+        for (int m = 0; m < n; m++) {
+            StepArgs a = base;
+            a.in = in;
+            a.out = (m == n - 1 && last) ? last : X[x];
+            a.raw = (raw && m == 0) ? 1 : 0;
+            a.t = from + m;
+            a.rho_out = record ? tape + (size_t)m * plane : nullptr;
+            fwd<<<a.main_blocks, kThreads, 0, ctx->stream>>>(a);
+            in = a.out;
+            x ^= 1;
+        }
     };
     int li = 0;  // L[li] holds lambda^{t+1}
     const int nseg = (nt + C - 1) / C;
     for (int k = nseg - 1; k >= 0; k--) {
         const long long ta = t0 + (long long)k * C, tb = std::min<long long>(ta + C, t0 + nt);
         const bool raw_a = (k == 0) && ctx->ckpt_raw0;
-        // place sub-checkpoints
-        cudaMemcpyAsync(SC[0], ctx->ckpt[k], sbytes, cudaMemcpyDeviceToDevice, ctx->stream);
-        const int nsc = (int)((tb - ta + C2 - 1) / C2);
-        for (int j = 1; j < nsc; j++) {
-            const float *cur = SC[j - 1];
-            bool raw = raw_a && j == 1;
-            for (int m = 0; m < C2; m++) {
-                long long t = ta + (long long)(j - 1) * C2 + m;
-                float *out = (m == C2 - 1) ? SC[j] : X[m & 1];
-                replay(cur, raw, out, t);
-                cur = out;
-                raw = false;
-            }
-        }
-        // sweep the sub-segments backwards
+        const int nsc = (int)((tb - ta + T - 1) / T);
+        SC[0] = ctx->ckpt[k];
+        for (int j = 1; j < nsc; j++)  // place the sub-checkpoints
+            replay(SC[j - 1], raw_a && j == 1, ta + (long long)(j - 1) * T, T, SC[j], false);
+        // sweep the sub-segments backwards: replay recording rho, then the adjoint steps
         for (int j = nsc - 1; j >= 0; j--) {
-            const long long sa = ta + (long long)j * C2, sb = std::min<long long>(sa + C2, tb);
+            const long long sa = ta + (long long)j * T, sb = std::min<long long>(sa + T, tb);
             const int len = (int)(sb - sa);
-            const bool raw0 = raw_a && j == 0;
-            cudaMemcpyAsync(X[0], SC[j], sbytes, cudaMemcpyDeviceToDevice, ctx->stream);
-            for (int m = 0; m + 1 < len; m++) replay(X[m], raw0 && m == 0, X[m + 1], sa + m);
+            replay(SC[j], raw_a && j == 0, sa, len, nullptr, true);
             for (int m = len - 1; m >= 0; m--) {
                 StepArgs a = base;
                 a.t = sa + m;
                 AdjArgs d;
                 d.lam_in = L[li];
                 d.lam_out = L[li ^ 1];
-                d.fwd = X[m];
-                d.fwd_raw = (raw0 && m == 0) ? 1 : 0;
+                d.rho = tape + (size_t)m * plane;
                 d.grad = grad;
                 d.grad_src = gsrc;
                 d.t0 = t0;
                 d.resid = resid;
                 d.nrec = ctx->nrec;
-                adj<<<grid_sites, 256, 0, ctx->stream>>>(a, d);
+                d.segs = segs4;
+                adj<<<adj_blocks, kThreads, 0, ctx->stream>>>(a, d);
                 if (ctx->nrec > 0)
                     adj_rec<<<(ctx->nrec + 255) / 256, 256, 0, ctx->stream>>>(a, d);
                 li ^= 1;

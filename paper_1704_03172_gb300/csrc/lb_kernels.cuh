@@ -86,6 +86,9 @@ struct StepArgs {
     unsigned *max_out;        // [9][kMaxCopies] float bits of max |value| written
     float *scale_next;        // [9]
     unsigned *max_next;       // [9][kMaxCopies]
+    // Adjoint replays only: rho(x, t) of the pulled state g(t), [ny][pitch] FP32
+    // (nullptr otherwise).
+    float *rho_out;
 };
 
 constexpr int kMaxCopies = 8;          // spread of the per-block atomicMax targets
@@ -427,6 +430,20 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
         }
     }
 
+    if (a.rho_out) {  // warp-uniform: adjoint replay records rho(t)
+#pragma unroll
+        for (int k = 0; k < V; k += 4) {
+            float r[4];
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                r[m] = 0.f;
+#pragma unroll
+                for (int i = 0; i < Q; i++) r[m] += g[i][k + m];
+            }
+            *reinterpret_cast<float4 *>(a.rho_out + (long long)y * a.pitch + x0 + k) =
+                make_float4(r[0], r[1], r[2], r[3]);
+        }
+    }
     float e2s[V];
 #pragma unroll
     for (int k = 0; k < V; k += 4) {

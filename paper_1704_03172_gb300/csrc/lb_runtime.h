@@ -66,6 +66,16 @@ lb_status fail(lb_ctx *ctx, lb_status st, const char *fmt, ...);
 lb_status cuda_fail(lb_ctx *ctx, cudaError_t e, const char *what);
 void *dev_alloc(lb_ctx *ctx, size_t bytes);
 void dev_free(lb_ctx *ctx, void *p);
+
+// Adjoint replay plan: the rho tape of lb_adjoint holds T = min(C, kAdjTapeBytes /
+// plane_bytes) steps (at least 1) of one FP32 plane each; when T < C every
+// checkpoint segment is first replayed once to place sub-checkpoints every T steps.
+constexpr size_t kAdjTapeBytes = size_t(16) << 30;
+inline int adj_tape_steps(size_t plane_bytes, int C) {
+    size_t t = plane_bytes ? kAdjTapeBytes / plane_bytes : (size_t)C;
+    if (t < 1) t = 1;
+    return (int)(t < (size_t)C ? t : (size_t)C);
+}
 }  // namespace lbrt
 
 // adjoint checkpoints (adjoint.cu): copy the state before step t when t % every == 0

@@ -244,12 +244,15 @@ lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint,
     if (nrec > 0 && nt > 0) b += (size_t)nt * nrec * 4 + (size_t)nrec * 8;
     if (nt > 0) b += (size_t)nt * 4;
     if (want_adjoint) {
-        // lb_adjoint: checkpoints every C steps, the replay states (ceil(sqrt(C)) + 1),
-        // the sub-checkpoints, the adjoint pair, the FP64 gradient and dJ/dS
-        const size_t C = want_adjoint > 1 ? (size_t)want_adjoint : 200;
-        const size_t C2 = (size_t)std::ceil(std::sqrt((double)C));
-        const size_t states = (nt > 0 ? ((size_t)nt + C - 1) / C : 1) + (C2 + 1) + (C + C2 - 1) / C2 + 2;
-        b += states * q * plane * 4 + plane * 8 + (size_t)std::max(nt, 0) * 8;
+        // lb_adjoint: checkpoints every C steps and, in the storage type, the two replay
+        // states and the sub-checkpoints; the FP32 rho tape (T planes), the FP32 adjoint
+        // pair, the FP64 gradient and dJ/dS
+        const int C = want_adjoint > 1 ? want_adjoint : 200;
+        const int T = adj_tape_steps(plane * 4, C);
+        const size_t nsub = (size_t)((C + T - 1) / T);
+        const size_t states = (nt > 0 ? ((size_t)nt + C - 1) / C : 1) + 2 + (nsub - 1);
+        b += states * q * plane * elem_bytes(cfg->storage) + (size_t)T * plane * 4 +
+             2 * q * plane * 4 + plane * 8 + (size_t)std::max(nt, 0) * 8;
     }
     *bytes = b;
     return LB_OK;

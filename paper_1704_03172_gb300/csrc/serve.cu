@@ -1,21 +1,29 @@
 // serve.cu -- continuous batching of independent shots (the serving layer).
 //
-// A scheduler thread owns the device work.  Requests wait in arrival order;
-// whenever a slot and enough of the device-memory budget are free, the first
-// requests that fit are admitted (their lb_ctx is created on the server
-// stream).  Each scheduling pass then advances every active shot by up to
-// `rounds_per_pass` steps: in every round one batch_step_kernel launch per
-// (lattice, collision, boundary, storage) group steps all the group's shots
-// once, each shot reading its own StepArgs descriptor (uploaded once per pass),
-// so many small shots share one launch and fill the GPU together.  Shots that
-// finish leave the batch (their traces are copied to pinned host memory), new
-// ones join at the next pass.  Gradient requests hand their context to an
-// adjoint worker thread, which waits for the forward work on its own stream
-// and runs lb_adjoint there, overlapping the batched forward work of others.
+// Threads and streams:
+//   admitter   creates each admitted shot's lb_ctx (medium, source, receivers,
+//              initial state) on the server's setup stream, so admission never
+//              drains the batch stream;
+//   scheduler  owns the batch stream.  Each scheduling pass advances every
+//              active shot by up to `rounds_per_pass` steps: in every round one
+//              batch_step_kernel launch per (lattice, collision, boundary,
+//              storage) group steps all the group's shots once, each shot
+//              reading its own StepArgs descriptor (uploaded once per pass), so
+//              many small shots share one launch and fill the GPU together.
+//              Shots that finish leave the batch (their traces are copied to
+//              pinned host memory), shots that are ready join at the next pass;
+//   workers    run the adjoint of gradient requests (lb_adjoint) on their own
+//              streams, overlapping the batched forward work of others.
 // FP16 shots, whose per-step scale hand-off is per launch, step on their own.
 //
-// All waits are bounded: the scheduler sleeps at most 5 ms when idle, workers
-// poll their queue with a timeout, and lb_server_wait takes a timeout.
+// Memory: every device buffer of a served shot comes from one stream-ordered
+// pool owned by the server (cudaMallocFromPoolAsync / cudaFreeAsync on the
+// stream that uses the shot at that moment), so creating and retiring shots
+// never synchronises the device; pinned trace buffers are recycled.  Admission
+// is by lb_footprint against the budget, so the pool stays within it.
+//
+// All waits are bounded: the scheduler sleeps at most 5 ms when idle, the other
+// threads poll their queues with a timeout, and lb_server_wait takes a timeout.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,9 +53,11 @@ double now_s() {
     return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
-enum class RS { Pending, Active, Draining, Adjoint, Done };
+enum class RS { Pending, Admitting, Ready, Active, Draining, Adjoint, Done };
 
 struct Req {
+    lb_server *srv = nullptr;
+    std::atomic<cudaStream_t> astream{nullptr};  // stream the shot's memory is ordered on
     long long id = 0;
     lb_config cfg;
     std::vector<float> cmap, obs;
@@ -58,7 +68,8 @@ struct Req {
     RS state = RS::Pending;
     lb_ctx *ctx = nullptr;
     int steps = 0;
-    float *h_traces = nullptr;  // pinned [nt][nrec]
+    float *h_traces = nullptr;  // pinned [nt][nrec], from the server's recycled buffers
+    size_t h_cap = 0;
     std::vector<float> grad_c;
     std::vector<double> grad_src;
     cudaEvent_t ev = nullptr;   // forward work and trace copy complete
@@ -94,26 +105,76 @@ BatchFn pick_batch(const lb_config &c) {
 struct lb_server {
     lb_server_config cfg;
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // batch stream (scheduler)
+    cudaStream_t setup = nullptr;    // admission (admitter)
+    cudaStream_t idle = nullptr;     // retirement of finished shots: nothing else runs on it
+    cudaMemPool_t pool = nullptr;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done, cv_adj;
-    std::deque<Req *> pending, adj_queue;
+    std::condition_variable cv_work, cv_done, cv_adj, cv_admit;
+    std::deque<Req *> pending, adj_queue, admit_queue, ready;
+    int admitting = 0;
     std::vector<Req *> active;  // stepping or draining; touched only by the scheduler
     std::map<long long, Req *> reqs;
     size_t budget = 0, used = 0;
     long long next_id = 1;
-    bool stop = false;
-    std::thread sched;
+    bool stop = false, stop_helpers = false;
+    std::thread sched, admitter;
     std::vector<std::thread> workers;
     StepArgs *d_args = nullptr, *h_args = nullptr;
     int *d_first = nullptr, *h_first = nullptr;
     size_t cap = 0;
     cudaEvent_t staged = nullptr;
+    std::mutex pin_mu;
+    std::multimap<size_t, void *> pinned;  // free pinned trace buffers by size
     std::atomic<long long> n_done{0}, n_launch{0};
     std::string err;
 };
 
 namespace {
+
+// device memory of a served shot: the server's pool, ordered on the stream that
+// currently runs the shot
+void *pool_alloc(size_t bytes, void *user) {
+    Req *r = static_cast<Req *>(user);
+    void *p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, bytes, r->srv->pool, r->astream.load()) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void pool_free(void *p, void *user) {
+    Req *r = static_cast<Req *>(user);
+    cudaFreeAsync(p, r->astream.load());
+}
+
+void *pin_get(lb_server *S, size_t bytes, size_t *cap) {
+    bytes = std::max<size_t>(bytes, 256);
+    {
+        std::lock_guard<std::mutex> lk(S->pin_mu);
+        auto it = S->pinned.lower_bound(bytes);
+        if (it != S->pinned.end() && it->first <= 2 * bytes) {
+            void *p = it->second;
+            *cap = it->first;
+            S->pinned.erase(it);
+            return p;
+        }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    *cap = bytes;
+    return p;
+}
+
+void pin_put(lb_server *S, void *p, size_t cap) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(S->pin_mu);
+    S->pinned.emplace(cap, p);
+}
 
 void finish(lb_server *S, Req *r, lb_status st, const std::string &msg) {
     std::lock_guard<std::mutex> lk(S->mu);
@@ -129,14 +190,20 @@ void finish(lb_server *S, Req *r, lb_status st, const std::string &msg) {
     S->cv_work.notify_all();
 }
 
+// Runs on the admitter thread: build the shot's context on the setup stream.
+// Every call below that touches the device synchronises the setup stream, so
+// the context is complete when it is handed to the scheduler.
 void admit(lb_server *S, Req *r) {
+    r->srv = S;
+    r->astream.store(S->setup);
     lb_config c = r->cfg;
     c.c_map = r->cmap.data();
     c.c_map_on_device = 0;
-    c.cuda_stream = S->stream;
+    c.cuda_stream = S->setup;
     c.time_block = 1;
-    c.dev_alloc = nullptr;
-    c.dev_free = nullptr;
+    c.dev_alloc = pool_alloc;
+    c.dev_free = pool_free;
+    c.alloc_user = r;
     lb_ctx *ctx = nullptr;
     lb_status st = lb_create(&c, &ctx);
     if (st == LB_OK && !r->wav.empty())
@@ -144,23 +211,49 @@ void admit(lb_server *S, Req *r) {
     if (st == LB_OK) st = lb_set_receivers(ctx, r->rec.data(), (int)r->rec.size() / 2, r->nt);
     if (st == LB_OK) st = lb_init_pressure(ctx, nullptr, 0);
     if (st == LB_OK && r->want_grad) st = lb_checkpoint_every(ctx, r->ckpt);
-    if (st == LB_OK && cudaMallocHost(&r->h_traces, std::max<size_t>(1, (size_t)r->nt * r->rec.size() / 2) * 4) != cudaSuccess)
+    if (st == LB_OK &&
+        !(r->h_traces = static_cast<float *>(pin_get(S, (size_t)r->nt * (r->rec.size() / 2) * 4, &r->h_cap))))
         st = LB_ENOMEM;
     if (st == LB_OK && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
         st = LB_ECUDA;
+    if (st == LB_OK && cudaStreamSynchronize(S->setup) != cudaSuccess) st = LB_ECUDA;
     if (st != LB_OK) {
         std::string msg = ctx ? lb_last_error(ctx) : lb_last_error(nullptr);
         if (ctx) lb_destroy(ctx);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->admitting--;
+        }
         finish(S, r, st, msg);
         return;
     }
+    ctx->stream = S->stream;  // from here on the scheduler runs it
     r->ctx = ctx;
-    r->t_start = now_s();
-    r->state = RS::Active;
     std::lock_guard<std::mutex> lk(S->mu);
-    S->active.push_back(r);
+    r->astream.store(S->stream);
+    r->state = RS::Ready;
+    S->admitting--;
+    S->ready.push_back(r);
+    S->cv_work.notify_all();
 }
 
+void admitter(lb_server *S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        Req *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            while (S->admit_queue.empty()) {
+                if (S->stop_helpers) return;
+                S->cv_admit.wait_for(lk, std::chrono::milliseconds(10));
+            }
+            r = S->admit_queue.front();
+            S->admit_queue.pop_front();
+            S->admitting++;
+        }
+        admit(S, r);
+    }
+}
 bool ensure_capacity(lb_server *S, size_t n) {
     if (n <= S->cap) return true;
     size_t cap = std::max(n, 2 * S->cap);
@@ -290,6 +383,10 @@ void retire(lb_server *S) {
             r->state = RS::Draining;
         }
         if (r->state == RS::Draining && cudaEventQuery(r->ev) == cudaSuccess) {
+            // all of the shot's work is complete: free on a stream with nothing queued,
+            // so neither lb_destroy's wait nor the frees hold up the batch stream
+            r->ctx->stream = S->idle;
+            r->astream.store(S->idle);
             lb_destroy(r->ctx);
             r->ctx = nullptr;
             finish(S, r, LB_OK, "");
@@ -297,43 +394,50 @@ void retire(lb_server *S) {
         }
         keep.push_back(r);
     }
-    std::lock_guard<std::mutex> lk(S->mu);
+    std::lock_guard<std::mutex> lk(S->mu);  // lb_server_stats reads the size
     S->active.swap(keep);
 }
 
 void scheduler(lb_server *S) {
     cudaSetDevice(S->device);
     for (;;) {
-        std::vector<Req *> admit_now;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            if (S->stop && S->pending.empty() && S->active.empty()) break;
-            if (S->active.empty() && S->pending.empty()) {
-                S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
-                continue;
+            const bool busy = !S->pending.empty() || !S->admit_queue.empty() || !S->ready.empty() ||
+                              S->admitting > 0;
+            if (S->stop && !busy && S->active.empty()) break;
+            // shots whose context is built join the batch
+            for (Req *r : S->ready) {
+                r->state = RS::Active;
+                r->t_start = now_s();
+                S->active.push_back(r);
             }
-            size_t slots = S->active.size();
+            S->ready.clear();
+            // admission in arrival order, by slot and device-memory budget
+            size_t slots = S->active.size() + S->admit_queue.size() + (size_t)S->admitting;
             for (auto it = S->pending.begin();
-                 it != S->pending.end() && slots + admit_now.size() < (size_t)S->cfg.max_active;) {
+                 it != S->pending.end() && slots < (size_t)S->cfg.max_active;) {
                 if (S->used + (*it)->fp <= S->budget) {
                     S->used += (*it)->fp;
-                    admit_now.push_back(*it);
+                    (*it)->state = RS::Admitting;
+                    S->admit_queue.push_back(*it);
                     it = S->pending.erase(it);
+                    slots++;
                 } else {
                     ++it;
                 }
             }
+            if (!S->admit_queue.empty()) S->cv_admit.notify_one();
+            if (S->active.empty()) {
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+                continue;
+            }
         }
-        for (Req *r : admit_now) admit(S, r);
         pass(S);
         retire(S);
-        bool idle;
-        {
-            std::lock_guard<std::mutex> lk(S->mu);
-            idle = true;
-            for (Req *r : S->active)
-                if (r->state == RS::Active) idle = false;
-        }
+        bool idle = true;
+        for (Req *r : S->active)
+            if (r->state == RS::Active) idle = false;
         if (idle) std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     cudaStreamSynchronize(S->stream);
@@ -348,7 +452,8 @@ void adjoint_worker(lb_server *S) {
         {
             std::unique_lock<std::mutex> lk(S->mu);
             while (S->adj_queue.empty()) {
-                if (S->stop && S->pending.empty() && S->active.empty()) {
+                if (S->stop_helpers) {
+                    lk.unlock();
                     cudaStreamDestroy(st);
                     return;
                 }
@@ -360,11 +465,15 @@ void adjoint_worker(lb_server *S) {
         cudaStreamWaitEvent(st, r->ev, 0);
         lb_ctx *ctx = r->ctx;
         ctx->stream = st;  // the scheduler no longer touches this context
+        r->astream.store(st);
         const int nrec = (int)r->rec.size() / 2;
         const long long n = (long long)r->nt * nrec;
-        float *d_obs = nullptr, *d_res = nullptr;
+        float *d_obs = nullptr, *d_res = nullptr, *d_gc = nullptr;
+        double *d_gs = nullptr;
+        auto grab = [&](size_t b) { return pool_alloc(b, r); };
         lb_status status = LB_OK;
-        if (n > 0 && (cudaMalloc(&d_obs, n * 4) != cudaSuccess || cudaMalloc(&d_res, n * 4) != cudaSuccess))
+        if (n > 0 && (!(d_obs = static_cast<float *>(grab(n * 4))) ||
+                      !(d_res = static_cast<float *>(grab(n * 4)))))
             status = LB_ENOMEM;
         if (status == LB_OK && n > 0) {
             cudaMemcpyAsync(d_obs, r->obs.data(), n * 4, cudaMemcpyHostToDevice, st);
@@ -373,10 +482,8 @@ void adjoint_worker(lb_server *S) {
         r->grad_c.assign((size_t)ctx->nx * ctx->ny, 0.f);
         std::vector<double> gs(r->nt, 0.0);
         if (status == LB_OK) {  // dJ/dp and the gradients stay on the device, then one copy out
-            float *d_gc = nullptr;
-            double *d_gs = nullptr;
-            if (cudaMalloc(&d_gc, r->grad_c.size() * 4) != cudaSuccess ||
-                cudaMalloc(&d_gs, gs.size() * 8) != cudaSuccess) {
+            if (!(d_gc = static_cast<float *>(grab(r->grad_c.size() * 4))) ||
+                !(d_gs = static_cast<double *>(grab(gs.size() * 8)))) {
                 status = LB_ENOMEM;
             } else {
                 status = lb_adjoint(ctx, d_res, r->nt, d_gc, d_gs, nullptr, 1);
@@ -386,14 +493,12 @@ void adjoint_worker(lb_server *S) {
                     if (cudaStreamSynchronize(st) != cudaSuccess) status = LB_ECUDA;
                 }
             }
-            if (d_gc) cudaFree(d_gc);
-            if (d_gs) cudaFree(d_gs);
         }
         std::string msg = status == LB_OK ? "" : lb_last_error(ctx);
         r->grad_src.assign(r->wav.size(), 0.0);
         for (size_t k = 0; k < r->grad_src.size() && k < gs.size(); k++) r->grad_src[k] = gs[k];
-        if (d_obs) cudaFree(d_obs);
-        if (d_res) cudaFree(d_res);
+        for (void *p : {(void *)d_obs, (void *)d_res, (void *)d_gc, (void *)d_gs})
+            if (p) pool_free(p, r);
         lb_destroy(ctx);
         r->ctx = nullptr;
         finish(S, r, status, msg);
@@ -412,14 +517,28 @@ lb_status lb_server_create(const lb_server_config *cfg, lb_server **out) {
     lb_server *S = new lb_server();
     S->cfg = *cfg;
     cudaGetDevice(&S->device);
-    if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = S->device;
+    if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->setup, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->idle, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMemPoolCreate(&S->pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        for (cudaStream_t s : {S->stream, S->setup, S->idle})
+            if (s) cudaStreamDestroy(s);
         delete S;
-        return fail(nullptr, LB_ECUDA, "server stream");
+        return fail(nullptr, LB_ECUDA, "server streams or memory pool");
     }
+    // keep freed memory in the pool for the next shots (bounded by the admission budget)
+    unsigned long long keep = ~0ull;
+    cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     S->budget = cfg->hbm_budget ? cfg->hbm_budget : (size_t)(0.8 * (double)free_b);
     S->sched = std::thread(scheduler, S);
+    S->admitter = std::thread(admitter, S);
     for (int k = 0; k < cfg->adjoint_workers; k++) S->workers.emplace_back(adjoint_worker, S);
     *out = S;
     return LB_OK;
@@ -431,8 +550,8 @@ lb_status lb_server_submit(lb_server *S, const lb_request *q, long long *id) {
         (q->nt_wavelet > 0 && !q->wavelet) || (q->want_gradient && q->nrec > 0 && !q->observed))
         return fail(nullptr, LB_EINVAL, "incomplete request");
     if (q->cfg.n_patches > 0) return fail(nullptr, LB_EINVAL, "served shots have no patch");
-    if (q->want_gradient && q->cfg.storage != LB_F32)
-        return fail(nullptr, LB_EINVAL, "gradient requests need FP32 storage");
+    if (q->want_gradient && q->cfg.storage != LB_F32 && q->cfg.storage != LB_BF16)
+        return fail(nullptr, LB_EINVAL, "gradient requests need FP32 or BF16 storage");
     Req *r = new Req();
     r->cfg = q->cfg;
     r->cmap.assign(q->cfg.c_map, q->cfg.c_map + (size_t)q->cfg.nx * q->cfg.ny);
@@ -510,7 +629,7 @@ lb_status lb_server_result(lb_server *S, long long id, float *traces, float *gra
     }
     lb_status st = r->status;
     if (st != LB_OK) S->err = r->err;
-    if (r->h_traces) cudaFreeHost(r->h_traces);
+    pin_put(S, r->h_traces, r->h_cap);
     if (r->ev) cudaEventDestroy(r->ev);
     delete r;
     return st;
@@ -531,14 +650,20 @@ lb_status lb_server_destroy(lb_server *S) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->stop = true;
         S->cv_work.notify_all();
-        S->cv_adj.notify_all();
     }
-    if (S->sched.joinable()) S->sched.join();
+    if (S->sched.joinable()) S->sched.join();  // returns once nothing is pending, admitting or stepping
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop_helpers = true;  // workers drain their queue first
+        S->cv_adj.notify_all();
+        S->cv_admit.notify_all();
+    }
+    if (S->admitter.joinable()) S->admitter.join();
     for (auto &w : S->workers)
         if (w.joinable()) w.join();
     for (auto &kv : S->reqs) {
         Req *r = kv.second;
-        if (r->h_traces) cudaFreeHost(r->h_traces);
+        pin_put(S, r->h_traces, r->h_cap);
         if (r->ev) cudaEventDestroy(r->ev);
         delete r;
     }
@@ -546,8 +671,13 @@ lb_status lb_server_destroy(lb_server *S) {
     if (S->d_first) cudaFree(S->d_first);
     if (S->h_args) cudaFreeHost(S->h_args);
     if (S->h_first) cudaFreeHost(S->h_first);
+    for (auto &kv : S->pinned) cudaFreeHost(kv.second);
     if (S->staged) cudaEventDestroy(S->staged);
-    cudaStreamDestroy(S->stream);
+    for (cudaStream_t s : {S->stream, S->setup, S->idle}) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+    cudaMemPoolDestroy(S->pool);
     delete S;
     return LB_OK;
 }

@@ -75,14 +75,15 @@ def layered_fault_model(nx, ny, seed, n_layers=20, c_lo=1500.0, c_hi=5500.0, n_f
     fx = rng.uniform(0, nx, size=n_faults)
     fdip = np.deg2rad(rng.uniform(dip_deg[0], dip_deg[1], size=n_faults))
     fthrow = rng.uniform(throw[0], throw[1], size=n_faults)
-    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
-    ye = y.copy()
+    y = np.arange(ny, dtype=np.float64)[:, None]
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    ye = np.repeat(y, nx, axis=1)
     for k in range(n_faults):
         hanging = x > fx[k] + y / np.tan(fdip[k])
-        ye = np.where(hanging, ye - fthrow[k], ye)
-    layer = np.zeros((ny, nx), dtype=np.int64)
+        np.subtract(ye, fthrow[k], out=ye, where=hanging)
+    layer = np.zeros((ny, nx), dtype=np.int16)
     for k in range(n_layers - 1):
-        layer += (ye > depths[k] + slopes[k] * (x - nx / 2.0)).astype(np.int64)
+        layer += ye > depths[k] + slopes[k] * (x - nx / 2.0)
     return speeds[layer].astype(np.float32)
 
 
@@ -165,3 +166,46 @@ def refined_block_workload(n=2048, nrec=256, steps=4000):
                 patch=(x0, x0, nxp, nxp), lattice=5, collision="mrt",
                 s=[1.0, 1.0, 1.0, 2.0, 2.0], tau=0.5, sponge_width=max(2, int(round(40 * s))),
                 sponge_sigma_max=0.1, block=(b0, b0, bw, bw))
+
+
+# --- served shot stream ---------------------------------------------------------------
+
+SERVED_SIZES = (256, 512, 1024, 2048)
+SERVED_C_REF = 5500.0
+# 10 points per wavelength at the slowest layer speed (1500 m/s): the D2Q5 lattice
+# sound speed there is (1500 / 5500) / sqrt(2) cells per step.
+SERVED_FC = (1500.0 / SERVED_C_REF) / math.sqrt(2.0) / 10.0
+
+
+def served_requests(n_req, seed, sizes=SERVED_SIZES, steps=(2000, 8000), p_bf16=0.5,
+                    p_grad=0.25, layers=(4, 12), id0=0):
+    """Descriptors of a stream of independent seismic shots (no arrays yet).
+
+    Grid side uniform in ``sizes``, step count uniform integer in ``steps``
+    (inclusive), storage BF16 with probability ``p_bf16`` else FP32, an adjoint
+    gradient with probability ``p_grad``, and a layered-fault model of
+    ``layers`` (inclusive) layers seeded by the request id."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_req):
+        out.append(dict(id=id0 + k, n=int(rng.choice(sizes)),
+                        nt=int(rng.integers(steps[0], steps[1] + 1)),
+                        storage="bf16" if rng.random() < p_bf16 else "f32",
+                        grad=bool(rng.random() < p_grad),
+                        layers=int(rng.integers(layers[0], layers[1] + 1))))
+    return out
+
+
+def served_shot(desc, nrec=128, sponge=40):
+    """Inputs of one served shot: layered-fault model (throws scaled from 20-200
+    cells at 8192 to the grid side), Ricker source at (n/2, sponge + 8), ``nrec``
+    receivers on the source row between the sponges, D2Q5 BGK tau = 1/2."""
+    n = desc["n"]
+    f = n / 8192.0
+    c = layered_fault_model(n, n, desc["id"], n_layers=desc["layers"],
+                            throw=(20.0 * f, 200.0 * f))
+    y = sponge + 8
+    return dict(c_map=c, nt=desc["nt"], source=(n // 2, y, ricker(desc["nt"], SERVED_FC)),
+                receivers=line_receivers(nrec, y, sponge, n - 2 * sponge), lattice=5,
+                collision="bgk", tau=0.5, storage=desc["storage"], sponge_width=sponge,
+                sponge_sigma_max=0.1, c_ref=SERVED_C_REF, want_gradient=desc["grad"])

@@ -46,12 +46,12 @@ def _setup(seed, nx=70, ny=45, nt=40):
     return rng, c, src, rec
 
 
-def _both(sim_cls, oracle, case, c, src, rec, nt):
+def _both(sim_cls, oracle, case, c, src, rec, nt, storage="f32"):
     Q, coll, tau, s, per, sponge, every = case
     ny, nx = c.shape
     kw = dict(tau=tau, s=s, w_ref=(0.4, 0.11, 0.04), c_ref=1.0)
     sim = sim_cls(c, lattice=Q, collision=coll, boundary="periodic" if per else "zero",
-                  sponge_width=sponge, sponge_sigma_max=0.15, **kw)
+                  sponge_width=sponge, sponge_sigma_max=0.15, storage=storage, **kw)
     sim.set_source(*src)
     sim.set_receivers(rec, nt)
     P = oracle.Problem(Q, nx, ny, c, periodic=per, mrt=coll == "mrt", sponge_width=sponge,
@@ -79,6 +79,49 @@ def test_adjoint_matches_oracle(sim_cls, oracle_mod, case):
     assert rel(gc, oc) < TOL
     assert rel(gs, os_) < TOL
     assert rel(gg, og) < TOL
+
+
+# BF16 storage: the adjoint state is FP32 and only the replayed forward states are
+# BF16.  dJ/dS depends on the adjoint state alone, so it keeps the FP32 bound;
+# dJ/dc also weighs the BF16 densities rho^t and carries their rounding error
+# (bounded here like the BF16 forward fields, 4e-2 relative).
+BF16_GRAD_C_TOL = 4e-2
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[3]])
+def test_bf16_storage_adjoint(sim_cls, oracle_mod, case):
+    Q, every = case[0], case[-1]
+    rng, c, src, rec = _setup(15, nt=60)
+    nt = 60
+    _, P = _both(sim_cls, oracle_mod, case, c, src, rec, nt)
+    _, tro = oracle_mod.run(P, P.zeros(), nt)
+    R = (tro - rng.normal(size=tro.shape) * 1e-3).astype(np.float32)
+    oc, os_, _ = oracle_mod.adjoint(P, P.zeros(), nt, R.astype(np.float64))
+    out = {}
+    for st in ("f32", "bf16"):
+        sim, _ = _both(sim_cls, oracle_mod, case, c, src, rec, nt, storage=st)
+        sim.init_pressure(None)
+        sim.checkpoint_every(every)
+        sim.step(nt)
+        gc, gs, _ = sim.adjoint(R, nt)
+        out[st] = (gc.cpu().numpy(), gs.cpu().numpy())
+        sim.close()
+    assert rel(out["f32"][0], oc) < TOL
+    assert rel(out["bf16"][1], os_) < TOL
+    e = rel(out["bf16"][0], oc)
+    print(f"BF16-storage dJ/dc vs FP64 oracle: rel L2 {e:.2e} (D2Q{Q} {case[1]})")
+    assert e < BF16_GRAD_C_TOL
+    assert rel(out["bf16"][0], out["f32"][0]) < BF16_GRAD_C_TOL
+
+
+def test_fp16_storage_adjoint_is_refused(sim_cls):
+    from paper_1704_03172_gb300 import lbac
+    c = W.uniform_map(64, 64)
+    sim = sim_cls(c, lattice=5, storage="f16", c_ref=1.0)
+    with pytest.raises(lbac.LBError) as e:
+        sim.checkpoint_every(10)
+    assert e.value.status == lbac.LB_ESTATE
+    sim.close()
 
 
 def test_adjoint_dot_product_on_gpu(sim_cls, oracle_mod):

@@ -54,7 +54,7 @@ def test_result_is_identical_alone_and_in_the_mix(mods, oracle_mod):
     srv = LBServer(max_active=6, rounds_per_pass=8)
     ids = []
     for k, (n, st, g) in enumerate([(128, "f32", False), (64, "bf16", False), (160, "f32", True),
-                                     (80, "f16", False), (200, "bf16", False)]):
+                                     (80, "f16", False), (200, "bf16", False), (96, "bf16", True)]):
         c, s = _shot(n, 10 + k, 200 + 37 * k, st, g)
         ids.append(srv.submit(c, **s))
     a2 = srv.submit(cA, **sA)
@@ -98,6 +98,38 @@ def test_gradient_request_matches_direct_adjoint(mods, oracle_mod):
     oc, os_, _ = oracle_mod.adjoint(P, P.zeros(), nt, (res["traces"] - d).astype(np.float64))
     assert rel(res["grad_c"], oc) < 1e-4
     assert rel(res["grad_src"], os_) < 1e-4
+
+
+def test_bf16_gradient_request_matches_direct_bf16_adjoint(mods, oracle_mod):
+    # a served BF16 shot runs the same kernels as a direct BF16 context, so its traces
+    # and its gradient (FP32 adjoint over the replayed BF16 states) match the direct ones
+    LBServer, LBSim, _ = mods
+    n, nt = 80, 150
+    c, s = _shot(n, 6, nt, storage="bf16", grad=True)
+    rng = np.random.default_rng(5)
+    d = rng.normal(size=(nt, 16)).astype(np.float32) * 1e-3
+    s["observed"] = d
+    srv = LBServer(max_active=4, rounds_per_pass=8)
+    rid = srv.submit(c, **s)
+    c2, s2 = _shot(128, 8, 120, storage="f32", grad=True)
+    rid2 = srv.submit(c2, **s2)
+    srv.wait(rid, 120000)
+    res = srv.result(rid)
+    srv.wait(rid2, 120000)
+    srv.result(rid2)
+    srv.close()
+    sim = LBSim(c, lattice=5, tau=0.5, storage="bf16", sponge_width=6, c_ref=5500.0)
+    sim.set_source(*s["source"])
+    sim.set_receivers(s["receivers"], nt)
+    sim.init_pressure(None)
+    sim.checkpoint_every(32)
+    sim.step(nt)
+    tr = sim.traces(nt).cpu().numpy()
+    gc, gs, _ = sim.adjoint((tr - d).astype(np.float32), nt)
+    sim.close()
+    np.testing.assert_array_equal(res["traces"], tr)
+    np.testing.assert_allclose(res["grad_c"], gc.cpu().numpy(), rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(res["grad_src"], gs.cpu().numpy(), rtol=1e-6, atol=1e-15)
 
 
 def test_admission_respects_the_memory_budget(mods):
