@@ -33,11 +33,17 @@ METRIC = "GLUPS & % of HBM roofline (D2Q5 step, FP32 vs BF16); served shots/s, p
 UNIT = "GLUPS"
 N_GRID = 4096
 FALLBACK_HBM_GBS = 6800.0
-BYTES_PER_SITE = {  # algorithmic HBM bytes per site update: read + write every population + eta^2
-    (5, "f32"): 2 * 5 * 4 + 4, (9, "f32"): 2 * 9 * 4 + 4,
-    (5, "bf16"): 2 * 5 * 2 + 4, (5, "f16"): 2 * 5 * 2 + 4,
-    (9, "bf16"): 2 * 9 * 2 + 4, (9, "f16"): 2 * 9 * 2 + 4,
-}
+ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
+
+
+def bytes_per_site(Q, storage, indexed):
+    """Algorithmic HBM bytes of one site update: read and write every population once,
+    plus the medium read (a 1-byte medium index, or 4-byte eta^2 per site)."""
+    return 2 * Q * ELEM_BYTES[storage] + (1 if indexed else 4)
+
+
+def _indexed(sim):
+    return sim.info()[4] > 0      # distinct speeds behind the 1-byte medium index (0: none)
 
 
 def _peaks():
@@ -154,12 +160,13 @@ def _variant(torch, LBSim, lattice, storage, collision, steps, warmup, time_bloc
     wl["time_block"] = time_block
     sim = _make_sim(LBSim, wl, steps + warmup)
     try:
+        indexed = _indexed(sim) and time_block <= 1   # the time-blocked kernel reads eta^2
         sec = _time_steps(torch, sim, steps, warmup)
     finally:
         sim.close()
     sites = N_GRID * N_GRID
     glups = sites * steps / sec / 1e9
-    bps = BYTES_PER_SITE[(lattice, storage)]
+    bps = bytes_per_site(lattice, storage, indexed)
     return {"glups": round(glups, 2), "bytes_per_site": bps,
             "achieved_gbs": round(glups * bps, 1), "ms_per_step": round(sec / steps * 1e3, 4)}
 
@@ -209,11 +216,12 @@ def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32"):
         torch.cuda.synchronize()
         t_adj = time.perf_counter() - t0
         finite = bool(torch.isfinite(gc).all().item())
+        indexed = _indexed(sim)
     finally:
         sim.close()
     T = min(every, (16 << 30) // (n * n * 4))
     levels = 1 if T >= every else 2
-    bps_fwd = BYTES_PER_SITE[(5, storage)]
+    bps_fwd = bytes_per_site(5, storage, indexed)
     # per adjoint site-step: `levels` replays (+4 B rho store on the recorded one) and the
     # adjoint step (lambda pull + store 2*5*4, rho 4, eta^2 4, FP64 gradient RMW 16)
     bps = levels * bps_fwd + 4 + 2 * 5 * 4 + 4 + 4 + 16
@@ -290,6 +298,30 @@ def _served(n_req, n_cal, seed=W.DEFAULT_SEED + 5, load=0.7, max_active=64):
             srv.wait(i)
             out.append(srv.result(i))
 
+    def one_by_one(shots_):
+        """The same shots through the plain per-shot API (LBSim), one after another."""
+        import torch
+        from paper_1704_03172_gb300.sim import LBSim
+        t0 = time.monotonic()
+        for s in shots_:
+            sim = LBSim(s["c_map"], lattice=5, tau=s["tau"], storage=s["storage"],
+                        sponge_width=s["sponge_width"], sponge_sigma_max=s["sponge_sigma_max"],
+                        c_ref=s["c_ref"])
+            sim.set_source(*s["source"])
+            sim.set_receivers(s["receivers"], s["nt"])
+            sim.init_pressure(None)
+            if s["want_gradient"]:
+                sim.checkpoint_every(200)
+            sim.step(s["nt"])
+            tr = sim.traces(s["nt"])
+            tr.cpu()
+            if s["want_gradient"]:
+                gc, gs, _ = sim.adjoint(tr, s["nt"])
+                gc.cpu()
+            sim.close()
+        torch.cuda.synchronize()
+        return time.monotonic() - t0
+
     srv = LBServer(max_active=max_active, rounds_per_pass=16, adjoint_workers=4)
     try:
         t0 = time.monotonic()
@@ -319,6 +351,7 @@ def _served(n_req, n_cal, seed=W.DEFAULT_SEED + 5, load=0.7, max_active=64):
         launches = srv.stats()["launches"] - launches0
     finally:
         srv.close()
+    plain_s = one_by_one(cal_shots)
     lat = np.array([r["done"] - r["submit"] for r in res])
     span = max(r["done"] for r in res) - min(r["submit"] for r in res)
     fwd = sum(d["n"] ** 2 * d["nt"] for d in descs)
@@ -332,6 +365,10 @@ def _served(n_req, n_cal, seed=W.DEFAULT_SEED + 5, load=0.7, max_active=64):
             "calibrated_capacity_per_s": round(capacity, 3),
             "calibration": f"{n_cal} shots of the same distribution submitted at once, "
                            f"{cal_s:.2f} s", "launches": int(launches),
+            "one_by_one_capacity_per_s": round(n_cal / plain_s, 3),
+            "batching_gain": round(plain_s / cal_s, 3),
+            "one_by_one": f"the {n_cal} calibration shots run one after another through the "
+                          f"per-shot API (LBSim: create, step, traces, adjoint), {plain_s:.2f} s",
             "gradients": sum(d["grad"] for d in descs),
             "bf16": sum(d["storage"] == "bf16" for d in descs),
             "forward_updates": fwd, "finite": bool(finite), "max_active": max_active,
@@ -412,6 +449,21 @@ def run_ours(args):
     build.build()
     from paper_1704_03172_gb300.sim import LBSim
 
+    if args.variant:  # one variant alone (profiling runs)
+        name = args.variant
+        if name.startswith("adjoint_"):
+            out = _adjoint_variant(torch, LBSim, n=args.adj_n, nt=args.adj_nt,
+                                   every=args.adj_every, storage=name.rsplit("_", 1)[1])
+        elif name.startswith("refined"):
+            out = _refined_variant(torch, LBSim, args.steps, args.warmup)
+        elif name == "served":
+            out = _served(args.served_requests, args.served_calibration)
+        else:
+            raise SystemExit(f"unknown variant {name}")
+        if rank == 0:
+            print(json.dumps({"variant": name, **out}), flush=True)
+        return 0
+
     wl = _workload(args.lattice, args.storage, "bgk")
     wl["time_block"] = args.time_block
     sim = _make_sim(LBSim, wl, args.steps + args.warmup)
@@ -439,6 +491,7 @@ def run_ours(args):
         sec = float(t.item())
     tr = sim.traces(args.steps + args.warmup)
     finite = bool(torch.isfinite(tr).all().item())
+    indexed = _indexed(sim)
     sim.close()
     sites = N_GRID * N_GRID
     value = ws * sites * args.steps / sec / 1e9
@@ -447,8 +500,8 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
     peak, peak_kind = _peaks()
-    bps = BYTES_PER_SITE[(args.lattice, args.storage)]
     K = max(1, args.time_block)
+    bps = bytes_per_site(args.lattice, args.storage, indexed and K == 1)
     launches = (args.steps + K - 1) // K
     per_launch_s = sec / launches
     achieved = bps * sites * K / per_launch_s / 1e9   # algorithmic one-step bytes per update
@@ -465,7 +518,9 @@ def run_ours(args):
                                "40-cell sponge, Ricker source, 512 receivers; one bench step = "
                                "one LB time step" + (f" ({K} steps fused per launch)" if K > 1 else ""),
                    "parallelism": f"replicas x{ws} (independent shots)",
-                   "l2": "inputs larger than L2 (population state >= 335 MB + 67 MB medium)"},
+                   "l2": "inputs larger than L2 (each population buffer >= 168 MB; 129 MB L2)",
+                   "medium": "1-byte medium index + eta^2 table" if indexed and K == 1
+                             else "eta^2 per site (FP32)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": None, "kernel": kname,
@@ -491,7 +546,8 @@ def run_ours(args):
             try:
                 v[name] = _variant(torch, LBSim, 5, "f32", "bgk", max(400, args.steps // 5) // 24 * 24,
                                    24, time_block=K)
-                v[name]["one_step_roofline_glups"] = round(_peaks()[0] / BYTES_PER_SITE[(5, "f32")], 1)
+                v[name]["one_step_roofline_glups"] = round(
+                    _peaks()[0] / bytes_per_site(5, "f32", True), 1)
             except Exception as ex:
                 v[name] = {"error": str(ex)[:200]}
         try:
@@ -530,6 +586,11 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--variant", default="",
+                    help="run one variant alone: adjoint_f32, adjoint_bf16, refined, served")
+    ap.add_argument("--adj-n", type=int, default=4096, help="adjoint variant grid side")
+    ap.add_argument("--adj-nt", type=int, default=1000, help="adjoint variant steps")
+    ap.add_argument("--adj-every", type=int, default=200, help="adjoint checkpoint interval")
     ap.add_argument("--served-requests", type=int, default=512,
                     help="shots in the served stream (0 skips it)")
     ap.add_argument("--served-calibration", type=int, default=64,

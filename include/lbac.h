@@ -270,7 +270,9 @@ lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint,
 
 /* Sizes and derived constants: info[0] = Q, info[1] = row pitch in elements,
  * info[2] = bytes per stored population value, info[3] = physical time step
- * dt = dx c_s(eta=1) / c_ref (seconds; 0 when dx or c_ref is 0). */
+ * dt = dx c_s(eta=1) / c_ref (seconds; 0 when dx or c_ref is 0), info[4] = number
+ * of distinct speeds when the step reads a 1-byte medium index (host c_map with at
+ * most 256 distinct values), 0 when it reads eta^2 per site. */
 lb_status lb_info(const lb_ctx *ctx, double *info, int n_info);
 
 const char *lb_last_error(const lb_ctx *ctx);

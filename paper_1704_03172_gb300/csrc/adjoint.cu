@@ -81,17 +81,32 @@ __global__ void __launch_bounds__(kThreads, Q == 5 ? 4 : 3) adjoint_kernel(const
     const int x0 = (wid - y * d.segs) * (32 * V) + lane * V;
     const bool active = x0 < a.nx;
     // mu_i(x) = (1 - sigma(x)) lambda_i^{t+1}(x + c_i): P^T pulls from x + c_i
-    float mu[Q][V];
+    // (two phases: every population's loads in flight together, then the shifts)
+    uint4 q[Q];
+    uint32_t e[Q];
+    bool absent[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const float *row = src_row<PERIODIC>(d.lam_in + i * a.plane, y + Lat<Q>::cy(i), a.ny, a.pitch);
+        absent[i] = row == nullptr;
         const int cx = Lat<Q>::cx(i);
         if (cx == 1)
-            pullV<-1, PERIODIC>(row, x0, lane, a.nx, active, 1.f, mu[i]);
+            pull_issue<-1, PERIODIC>(row, x0, lane, a.nx, active, q[i], e[i]);
         else if (cx == -1)
-            pullV<1, PERIODIC>(row, x0, lane, a.nx, active, 1.f, mu[i]);
+            pull_issue<1, PERIODIC>(row, x0, lane, a.nx, active, q[i], e[i]);
         else
-            pullV<0, PERIODIC>(row, x0, lane, a.nx, active, 1.f, mu[i]);
+            pull_issue<0, PERIODIC>(row, x0, lane, a.nx, active, q[i], e[i]);
+    }
+    float mu[Q][V];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int cx = Lat<Q>::cx(i);
+        if (cx == 1)
+            pull_finish<-1, PERIODIC, float>(absent[i], x0, lane, a.nx, q[i], e[i], mu[i]);
+        else if (cx == -1)
+            pull_finish<1, PERIODIC, float>(absent[i], x0, lane, a.nx, q[i], e[i], mu[i]);
+        else
+            pull_finish<0, PERIODIC, float>(absent[i], x0, lane, a.nx, q[i], e[i], mu[i]);
     }
     if (!active) return;  // no shuffles below
     const long long base = (long long)y * a.pitch + x0;

@@ -32,6 +32,7 @@ namespace lbk {
 constexpr int kThreads = 256;            // threads per block (8 warps)
 constexpr int kWarps = kThreads / 32;
 constexpr int kSitesPerWarp = 128;       // 32 lanes x 4 sites
+static_assert(kThreads == 256, "one medium-table entry per thread");
 
 template <int Q> struct Lat;
 template <> struct Lat<5> {
@@ -52,6 +53,11 @@ struct StepArgs {
     const void *in;          // h^{t-1}  [Q][ny][pitch]
     void *out;               // h^{t}
     const float *eta2;       // [ny][pitch] (c / c_ref)^2
+    // Optional medium index (nullptr: read eta2): when the map holds at most 256
+    // distinct speeds, mid[y][x] selects eta^2 = mid_tab[mid] (1 byte per site
+    // instead of 4); the step kernels stage mid_tab in shared memory.
+    const uint8_t *mid;      // [ny][pitch]
+    const float *mid_tab;    // [256]
     int nx, ny, pitch;
     long long plane;         // ny * pitch
     int segs;                // warps per row = ceil(nx / 128)
@@ -130,6 +136,15 @@ template <> struct Store<float> {
     }
     __device__ static __forceinline__ float load1(const float *p) { return *p; }
     __device__ static __forceinline__ void store1(float *p, float v) { *p = v; }
+    // raw forms for the two-phase pull: 16-byte vector and one element as bits
+    __device__ static __forceinline__ uint32_t bits1(const float *p) {
+        return __float_as_uint(*p);
+    }
+    __device__ static __forceinline__ float unbits1(uint32_t b) { return __uint_as_float(b); }
+    __device__ static __forceinline__ void unpackV(const uint4 &u, float (&v)[V]) {
+        v[0] = __uint_as_float(u.x); v[1] = __uint_as_float(u.y);
+        v[2] = __uint_as_float(u.z); v[3] = __uint_as_float(u.w);
+    }
 };
 
 template <> struct Store<__nv_bfloat16> {
@@ -161,6 +176,20 @@ template <> struct Store<__nv_bfloat16> {
     __device__ static __forceinline__ void store1(__nv_bfloat16 *p, float v) {
         *p = __float2bfloat16_rn(v);
     }
+    __device__ static __forceinline__ uint32_t bits1(const __nv_bfloat16 *p) {
+        return *reinterpret_cast<const unsigned short *>(p);
+    }
+    __device__ static __forceinline__ float unbits1(uint32_t b) {
+        return __uint_as_float(b << 16);  // BF16 is the upper half of an FP32
+    }
+    __device__ static __forceinline__ void unpackV(const uint4 &u, float (&v)[V]) {
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            v[2 * k] = __uint_as_float(w[k] << 16);
+            v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+    }
 };
 
 template <> struct Store<__half> {
@@ -188,6 +217,21 @@ template <> struct Store<__half> {
     }
     __device__ static __forceinline__ float load1(const __half *p) { return __half2float(*p); }
     __device__ static __forceinline__ void store1(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static __forceinline__ uint32_t bits1(const __half *p) {
+        return *reinterpret_cast<const unsigned short *>(p);
+    }
+    __device__ static __forceinline__ float unbits1(uint32_t b) {
+        return __half2float(__ushort_as_half((unsigned short)b));
+    }
+    __device__ static __forceinline__ void unpackV(const uint4 &u, float (&v)[V]) {
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
+            v[2 * k] = f.x;
+            v[2 * k + 1] = f.y;
+        }
+    }
 };
 
 // ------------------------------------------------------------------ pulls --
@@ -238,6 +282,67 @@ __device__ __forceinline__ void pullV(const ST *row, int x0, int lane, int nx, b
     if (scale != 1.f) {
 #pragma unroll
         for (int k = 0; k < V; k++) v[k] *= scale;
+    }
+}
+
+// Two-phase form of pullV for kernels that pull several populations: phase 1
+// issues, for every population, the 16-byte vector load and ONE unconditional
+// scalar load (lane 0 / 31: the neighbouring warp's edge element, or the
+// periodic wrap element; every other lane: the row's first element, a
+// broadcast), so that all of a thread's loads are in flight together; phase 2
+// shuffles and assembles.  Same values as pullV.
+template <int CX, bool PERIODIC, typename ST>
+__device__ __forceinline__ void pull_issue(const ST *row, int x0, int lane, int nx, bool active,
+                                           uint4 &q, uint32_t &e) {
+    constexpr int V = Store<ST>::V;
+    q = make_uint4(0u, 0u, 0u, 0u);
+    e = 0u;
+    if (row == nullptr) return;  // warp-uniform
+    if (active) q = *reinterpret_cast<const uint4 *>(row + x0);
+    if (CX == 1) {  // lane 0 needs x0 - 1 (or, at x0 == 0, the periodic image nx - 1)
+        const ST *ep = row;
+        if (lane == 0 && x0 > 0) ep = row + x0 - 1;
+        if (PERIODIC && lane == 0 && x0 == 0) ep = row + nx - 1;
+        e = Store<ST>::bits1(ep);
+    } else if (CX == -1) {  // lane 31 needs x0 + V; the last real site's periodic image is row[0]
+        const ST *ep = row;
+        if (lane == 31 && x0 + V < nx) ep = row + x0 + V;
+        e = Store<ST>::bits1(ep);
+    }
+}
+
+template <int CX, bool PERIODIC, typename ST>
+__device__ __forceinline__ void pull_finish(bool row_null, int x0, int lane, int nx,
+                                            const uint4 &q, uint32_t e,
+                                            float (&v)[Store<ST>::V]) {
+    constexpr int V = Store<ST>::V;
+    float f[V];
+    Store<ST>::unpackV(q, f);  // zeros for an absent row or an inactive lane
+    if (CX == 0) {
+#pragma unroll
+        for (int k = 0; k < V; k++) v[k] = f[k];
+        return;
+    }
+    const float eb = row_null ? 0.f : Store<ST>::unbits1(e);
+    if (CX == 1) {  // value from x - 1
+        float left = __shfl_up_sync(0xffffffffu, f[V - 1], 1);
+        if (lane == 0) left = (x0 > 0 || PERIODIC) ? eb : 0.f;
+        v[0] = left;
+#pragma unroll
+        for (int k = 1; k < V; k++) v[k] = f[k - 1];
+    } else {  // CX == -1: value from x + 1
+        float right = __shfl_down_sync(0xffffffffu, f[0], 1);
+        if (lane == 31) right = (x0 + V < nx) ? eb : 0.f;
+#pragma unroll
+        for (int k = 0; k + 1 < V; k++) v[k] = f[k + 1];
+        v[V - 1] = right;
+        const int last = nx - 1 - x0;  // local index of the last real site, if in this vector
+        if (last >= 0 && last < V) {
+            const float b = PERIODIC ? eb : 0.f;
+#pragma unroll
+            for (int j = 0; j < V; j++)
+                if (j == last) v[j] = b;
+        }
     }
 }
 
@@ -390,7 +495,8 @@ __device__ __forceinline__ float next_scale(float maxval, float S, float keep) {
 // The sites of one warp row-segment of block `blk`; tmax receives this
 // thread's max |out_i|.
 template <int Q, bool MRT, bool PERIODIC, typename ST>
-__device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tmax[Q]) {
+__device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tmax[Q],
+                                           const float *tab) {
     constexpr bool SC = Scaled<ST>::value;
 #pragma unroll
     for (int i = 0; i < Q; i++) tmax[i] = 0.f;
@@ -403,22 +509,34 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
     const bool active = x0 < a.nx;
     const ST *in = static_cast<const ST *>(a.in);
 
+    // phase 1: every population's loads in flight together
+    uint4 q[Q];
+    uint32_t e[Q];
+    bool absent[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int cx = a.raw ? 0 : Lat<Q>::cx(i);  // raw: read g(t) in place (warp-uniform)
+        const ST *row = a.raw ? in + i * a.plane + (long long)y * a.pitch
+                              : src_row<PERIODIC>(in + i * a.plane, y - Lat<Q>::cy(i), a.ny, a.pitch);
+        absent[i] = row == nullptr;
+        if (cx == 1)
+            pull_issue<1, PERIODIC>(row, x0, lane, a.nx, active, q[i], e[i]);
+        else if (cx == -1)
+            pull_issue<-1, PERIODIC>(row, x0, lane, a.nx, active, q[i], e[i]);
+        else
+            pull_issue<0, PERIODIC>(row, x0, lane, a.nx, active, q[i], e[i]);
+    }
+    // phase 2: shifts and assembly
     float g[Q][V];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        if (a.raw) {  // warp-uniform: first step after lb_set_state, read g(t) in place
-            pullV<0, PERIODIC>(in + i * a.plane + (long long)y * a.pitch, x0, lane, a.nx, active,
-                               1.f, g[i]);
-            continue;
-        }
-        const ST *row = src_row<PERIODIC>(in + i * a.plane, y - Lat<Q>::cy(i), a.ny, a.pitch);
-        const int cx = Lat<Q>::cx(i);
+        const int cx = a.raw ? 0 : Lat<Q>::cx(i);
         if (cx == 1)
-            pullV<1, PERIODIC>(row, x0, lane, a.nx, active, 1.f, g[i]);
+            pull_finish<1, PERIODIC, ST>(absent[i], x0, lane, a.nx, q[i], e[i], g[i]);
         else if (cx == -1)
-            pullV<-1, PERIODIC>(row, x0, lane, a.nx, active, 1.f, g[i]);
+            pull_finish<-1, PERIODIC, ST>(absent[i], x0, lane, a.nx, q[i], e[i], g[i]);
         else
-            pullV<0, PERIODIC>(row, x0, lane, a.nx, active, 1.f, g[i]);
+            pull_finish<0, PERIODIC, ST>(absent[i], x0, lane, a.nx, q[i], e[i], g[i]);
     }
     if (!active) return;  // no shuffles below
     if (SC) {  // one scale per population: applied after the shuffles
@@ -445,10 +563,24 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
         }
     }
     float e2s[V];
+    if (a.mid) {  // warp-uniform: 1-byte medium index, eta^2 from the shared table
+        const uint8_t *mp = a.mid + (long long)y * a.pitch + x0;
+        uint32_t w[V / 4];
+        if (V == 4) {
+            w[0] = *reinterpret_cast<const uint32_t *>(mp);
+        } else {
+            const uint2 u = *reinterpret_cast<const uint2 *>(mp);
+            w[0] = u.x;
+            w[V / 4 - 1] = u.y;
+        }
 #pragma unroll
-    for (int k = 0; k < V; k += 4) {
-        float4 e = *reinterpret_cast<const float4 *>(a.eta2 + (long long)y * a.pitch + x0 + k);
-        e2s[k] = e.x; e2s[k + 1] = e.y; e2s[k + 2] = e.z; e2s[k + 3] = e.w;
+        for (int k = 0; k < V; k++) e2s[k] = tab[(w[k >> 2] >> (8 * (k & 3))) & 0xffu];
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; k += 4) {
+            float4 e = *reinterpret_cast<const float4 *>(a.eta2 + (long long)y * a.pitch + x0 + k);
+            e2s[k] = e.x; e2s[k + 1] = e.y; e2s[k + 2] = e.z; e2s[k + 3] = e.w;
+        }
     }
     const bool edge = a.sponge_w > 0 &&
                       (y < a.sponge_w || y >= a.ny - a.sponge_w || x0 < a.sponge_w ||
@@ -508,8 +640,13 @@ __global__ void __launch_bounds__(kThreads, Q == 5 ? (sizeof(ST) == 4 ? 5 : 4)
                                                  (int)threadIdx.x);
         return;
     }
+    __shared__ float s_tab[kThreads];
+    if (a.mid) {  // block-uniform
+        s_tab[threadIdx.x] = a.mid_tab[threadIdx.x];
+        __syncthreads();
+    }
     float tmax[Q];
-    step_sites<Q, MRT, PERIODIC, ST>(a, blockIdx.x, tmax);
+    step_sites<Q, MRT, PERIODIC, ST>(a, blockIdx.x, tmax, s_tab);
     if (SC) {  // fold this block's max |output| per population into max_out
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -572,8 +709,13 @@ __global__ void __launch_bounds__(kThreads)
         gather_receivers<Q, PERIODIC, ST>(sa, (blk - sa.main_blocks) * kThreads + (int)threadIdx.x);
         return;
     }
+    __shared__ float s_tab[kThreads];
+    if (sa.mid) {  // block-uniform
+        s_tab[threadIdx.x] = sa.mid_tab[threadIdx.x];
+        __syncthreads();
+    }
     float tmax[Q];
-    step_sites<Q, MRT, PERIODIC, ST>(sa, blk, tmax);
+    step_sites<Q, MRT, PERIODIC, ST>(sa, blk, tmax, s_tab);
 }
 
 // -------------------------------------------------------- state transforms --

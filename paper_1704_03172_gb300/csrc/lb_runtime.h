@@ -18,7 +18,10 @@ struct lb_ctx {
     void *pop[2] = {nullptr, nullptr};
     int cur = 0;                    // pop[cur] holds the post-collision state of step t-1
     bool raw = false;               // ... or, when raw, the state g(t) itself (unshifted)
-    float *eta2 = nullptr;          // [ny][pitch] (c / c_ref)^2
+    float *eta2 = nullptr;
+    uint8_t *mid = nullptr;      // medium index (<= 256 distinct speeds), or nullptr
+    float *mid_tab = nullptr;    // [256] eta^2 per index
+    int n_mid = 0;          // [ny][pitch] (c / c_ref)^2
     float *lp_scale = nullptr;      // FP16 storage: [3][9] per-population scales (slots)
     unsigned *lp_max = nullptr;     // FP16 storage: [3][9][kMaxCopies] max |value| + counter
     int lp_slot = 0;                // slot describing the current buffer

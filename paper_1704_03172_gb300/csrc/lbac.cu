@@ -67,10 +67,63 @@ int elem_bytes(int storage) { return storage == LB_F32 ? 4 : 2; }
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+namespace {
+
+// Medium index: when the host map holds at most 256 distinct speeds, map[y][x]
+// (row pitch `pitch`) indexes tab, whose entries are eta^2 formed exactly as
+// medium_kernel forms them (so both forms give bit-identical steps).  Returns
+// false as soon as a 257th value appears.
+bool medium_index(const float *c, int nx, int ny, int pitch, double inv_cref,
+                  std::vector<uint8_t> &map, std::vector<float> &tab) {
+    constexpr unsigned kSlots = 512;  // open addressing, linear probing
+    uint32_t key[kSlots];
+    int val[kSlots];
+    bool used[kSlots] = {};
+    std::vector<uint32_t> distinct;
+    map.assign((size_t)ny * pitch, 0);
+    uint32_t last = 0;
+    int last_i = -1;
+    for (int y = 0; y < ny; y++) {
+        const float *row = c + (size_t)y * nx;
+        uint8_t *mrow = map.data() + (size_t)y * pitch;
+        for (int x = 0; x < nx; x++) {
+            uint32_t b;
+            memcpy(&b, row + x, 4);
+            if (b != last || last_i < 0) {  // runs of equal speeds skip the table
+                unsigned h = (b * 2654435761u) >> 23;
+                while (used[h] && key[h] != b) h = (h + 1) & (kSlots - 1);
+                if (!used[h]) {
+                    if (distinct.size() == 256) return false;
+                    used[h] = true;
+                    key[h] = b;
+                    val[h] = (int)distinct.size();
+                    distinct.push_back(b);
+                }
+                last = b;
+                last_i = val[h];
+            }
+            mrow[x] = (uint8_t)last_i;
+        }
+    }
+    tab.assign(256, 0.f);
+    for (size_t i = 0; i < distinct.size(); i++) {
+        float cv;
+        memcpy(&cv, &distinct[i], 4);
+        double eta = (double)cv * inv_cref;
+        if (eta > 1.0) eta = 1.0;
+        tab[i] = (float)(eta * eta);
+    }
+    return true;
+}
+
+}  // namespace
+
 StepArgs base_args(const lb_ctx *c) {
     StepArgs a;
     memset(&a, 0, sizeof(a));
     a.eta2 = c->eta2;
+    a.mid = c->mid;
+    a.mid_tab = c->mid_tab;
     a.nx = c->nx;
     a.ny = c->ny;
     a.pitch = c->pitch;
@@ -240,7 +293,8 @@ lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint,
     size_t pitch = (size_t)round_up(std::max(cfg->nx, 1), 32);
     size_t plane = pitch * (size_t)std::max(cfg->ny, 1);
     size_t q = cfg->lattice == LB_D2Q9 ? 9 : 5;
-    size_t b = 2 * q * plane * elem_bytes(cfg->storage) + plane * 4;
+    // populations (two buffers), eta^2 and, for piecewise-constant media, the medium index
+    size_t b = 2 * q * plane * elem_bytes(cfg->storage) + plane * 4 + plane + 1024;
     if (nrec > 0 && nt > 0) b += (size_t)nt * nrec * 4 + (size_t)nrec * 8;
     if (nt > 0) b += (size_t)nt * 4;
     if (want_adjoint) {
@@ -347,6 +401,23 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     dev_free(c, flags);
     if (hflags & 1u) return bail(fail(c, LB_EINVAL, "c_map must be finite and > 0"));
     if (hflags & 2u) return bail(fail(c, LB_EINVAL, "c_map exceeds c_ref (eta > 1)"));
+    if (!cfg->c_map_on_device) {  // piecewise-constant media: 1-byte medium index
+        std::vector<uint8_t> map;
+        std::vector<float> tab;
+        if (medium_index(cfg->c_map, c->nx, c->ny, c->pitch, 1.0 / cref, map, tab)) {
+            c->mid = static_cast<uint8_t *>(dev_alloc(c, map.size()));
+            c->mid_tab = static_cast<float *>(dev_alloc(c, 256 * sizeof(float)));
+            if (!c->mid || !c->mid_tab) return bail(fail(c, LB_ENOMEM, "medium index"));
+            cudaMemcpyAsync(c->mid, map.data(), map.size(), cudaMemcpyHostToDevice, c->stream);
+            cudaMemcpyAsync(c->mid_tab, tab.data(), 256 * sizeof(float), cudaMemcpyHostToDevice,
+                            c->stream);
+            e = cudaStreamSynchronize(c->stream);  // the host vectors go out of scope
+            if (e != cudaSuccess) return bail(cuda_fail(c, e, "medium index upload"));
+            int n = 0;
+            for (size_t i = 0; i < 256; i++) n += tab[i] > 0.f;
+            c->n_mid = n;
+        }
+    }
     if (cfg->n_patches > 0) {
         if ((st = refine_setup(c, cfg, cmap_dev)) != LB_OK) return bail(st);
     }
@@ -656,14 +727,15 @@ lb_status lb_sync(lb_ctx *ctx) {
 
 lb_status lb_info(const lb_ctx *ctx, double *info, int n_info) {
     if (!ctx || !info) return LB_EINVAL;
-    double v[4];
+    double v[5];
     v[0] = ctx->Q;
     v[1] = ctx->pitch;
     v[2] = ctx->ebytes;
     double cs_ref = ctx->Q == 5 ? std::sqrt(0.5)
                                 : std::sqrt(2 * ctx->cfg.w_ref[1] + 4 * ctx->cfg.w_ref[2]);
     v[3] = (ctx->cfg.dx > 0 && ctx->cfg.c_ref > 0) ? ctx->cfg.dx * cs_ref / ctx->cfg.c_ref : 0.0;
-    for (int k = 0; k < n_info && k < 4; k++) info[k] = v[k];
+    v[4] = ctx->n_mid;
+    for (int k = 0; k < n_info && k < 5; k++) info[k] = v[k];
     return LB_OK;
 }
 

@@ -247,6 +247,8 @@ StepArgs fine_args(const lb_ctx *ctx) {
     const lb_refine *R = ctx->ref;
     StepArgs a = base_args(ctx);
     a.eta2 = R->eta2;
+    a.mid = nullptr;  // the fine grid reads its own eta^2 plane
+    a.mid_tab = nullptr;
     a.nx = R->gx;
     a.ny = R->gy;
     a.pitch = R->pitch;

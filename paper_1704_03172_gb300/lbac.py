@@ -256,8 +256,8 @@ def lb_footprint(cfg: lb_config, nt, nrec, want_adjoint) -> int:
 
 
 def lb_info(ctx):
-    v = (ctypes.c_double * 4)()
-    _check(_lib.lb_info(ctx, v, 4), ctx)
+    v = (ctypes.c_double * 5)()
+    _check(_lib.lb_info(ctx, v, 5), ctx)
     return list(v)
 
 

@@ -43,7 +43,8 @@ def test_config_default_and_footprint_without_gpu(lib):
     assert cfg.lattice == 5 and cfg.tau == 0.5 and cfg.storage == lib.LB_F32
     cfg.nx, cfg.ny = 4096, 4096
     b = lib.lb_footprint(cfg, 0, 0, 0)
-    assert b == 2 * 5 * 4096 * 4096 * 4 + 4096 * 4096 * 4   # two population buffers + eta^2
+    # two population buffers + eta^2 + the 1-byte medium index and its 256-entry table
+    assert b == 2 * 5 * 4096 * 4096 * 4 + 4096 * 4096 * 4 + 4096 * 4096 + 1024
 
 
 def test_create_rejects_bad_config_without_touching_gpu(lib):

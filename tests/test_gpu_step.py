@@ -164,3 +164,47 @@ def test_two_layer_4096_bench_configuration(sim_cls, oracle_mod, Q, coll, steps)
     go, tro = oracle_mod.run(P, g0.astype(np.float64), steps)
     assert rel(gs, go) < TOL
     assert rel(tr, tro) < TOL
+
+
+@pytest.mark.parametrize("Q,storage,periodic,n", [(5, "f32", False, 200), (5, "bf16", False, 333),
+                                                  (9, "f32", True, 96), (9, "bf16", False, 130),
+                                                  (5, "f16", False, 150)])
+def test_medium_index_matches_per_site_eta2_bitwise(sim_cls, Q, storage, periodic, n):
+    # A layered model has few distinct speeds: with a host c_map the step reads a
+    # 1-byte medium index and a table; with the same map on the device it reads
+    # eta^2 per site.  Both must give bit-identical states and traces.
+    import torch
+    c = W.layered_fault_model(n, n + 13, 11, n_layers=9, throw=(2.0, n / 10))
+    rec = W.line_receivers(24, 20, 4, n - 8)
+    src = (n // 3, 20, W.ricker(120, 0.04))
+    out = []
+    for cm in (c, torch.tensor(c, device="cuda")):
+        sim = sim_cls(cm, lattice=Q, storage=storage, c_ref=5500.0, sponge_width=8,
+                      boundary="periodic" if periodic else "zero",
+                      w_ref=(0.0, 0.01, 0.24) if Q == 9 else (4 / 9, 1 / 9, 1 / 36))
+        sim.set_source(*src)
+        sim.set_receivers(rec, 120)
+        sim.init_pressure(None)
+        sim.step(120)
+        out.append((sim.info()[4], sim.state().cpu().numpy(), sim.traces(120).cpu().numpy()))
+        sim.close()
+    (n_idx, g_idx, t_idx), (n_site, g_site, t_site) = out
+    assert n_idx == len(np.unique(c)) and n_site == 0
+    np.testing.assert_array_equal(g_idx, g_site)
+    np.testing.assert_array_equal(t_idx, t_site)
+    assert np.abs(t_idx).max() > 0
+
+
+def test_medium_index_not_used_beyond_256_speeds(sim_cls):
+    c = W.random_medium(64, 40, 3, 0.5, 1.0)            # every site its own speed
+    sim = sim_cls(c, lattice=5, c_ref=1.0)
+    assert sim.info()[4] == 0
+    sim.close()
+    c2 = np.repeat(np.linspace(0.5, 1.0, 256, dtype=np.float32)[None, :], 3, axis=0)
+    sim = sim_cls(c2, lattice=5, c_ref=1.0)             # exactly 256 speeds: indexed
+    assert sim.info()[4] == 256
+    sim.close()
+    c3 = np.repeat(np.linspace(0.5, 1.0, 257, dtype=np.float32)[None, :], 3, axis=0)
+    sim = sim_cls(c3, lattice=5, c_ref=1.0)             # 257: per-site eta^2
+    assert sim.info()[4] == 0
+    sim.close()
