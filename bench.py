@@ -134,7 +134,8 @@ def _make_sim(LBSim, wl, nt_cap):
     sim = LBSim(wl["c_map"], lattice=wl["lattice"], collision=wl["collision"], tau=wl["tau"],
                 s=wl.get("s"), storage=wl["storage"], c_ref=wl["c_ref"],
                 sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"],
-                w_ref=wl["w_ref"], time_block=wl.get("time_block", 1))
+                w_ref=wl["w_ref"], time_block=wl.get("time_block", 1),
+                step_kernel=wl.get("step_kernel", "auto"))
     sx, sy, wav = wl["source"]
     sim.set_source(sx, sy, wav)
     sim.set_receivers(wl["receivers"], nt_cap)
@@ -466,6 +467,7 @@ def run_ours(args):
 
     wl = _workload(args.lattice, args.storage, "bgk")
     wl["time_block"] = args.time_block
+    wl["step_kernel"] = args.step_kernel
     sim = _make_sim(LBSim, wl, args.steps + args.warmup)
     sim.step(args.warmup)
     torch.cuda.synchronize()
@@ -598,6 +600,8 @@ def main():
     ap.add_argument("--lattice", type=int, choices=[5, 9], default=5,
                     help="main line's lattice (D2Q5 is the paper's recommended scheme)")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")
+    ap.add_argument("--step-kernel", choices=["auto", "direct"], default="auto",
+                    help="auto: TMA-staged persistent step; direct: register-streaming step")
     ap.add_argument("--time-block", type=int, default=1,
                     help="steps fused per launch for the main line (temporal blocking)")
     args = ap.parse_args()

@@ -89,7 +89,13 @@ typedef struct {
     void *(*dev_alloc)(size_t bytes, void *user);
     void (*dev_free)(void *ptr, void *user);
     void *alloc_user;
+    int step_kernel;          /* LB_STEP_AUTO (0): the TMA-staged persistent step for 16-bit
+                                 storage without a patch, the register-streaming step otherwise;
+                                 LB_STEP_DIRECT (1): always the register-streaming step.  Both
+                                 give bit-identical results. */
 } lb_config;
+
+enum { LB_STEP_AUTO = 0, LB_STEP_DIRECT = 1 };
 
 /* Fill *cfg with defaults: D2Q5, BGK tau = 1/2, F32, zero ghost, no sponge,
  * conventional D2Q9 weights (4/9, 1/9, 1/36), c_ref = max(c_map). */

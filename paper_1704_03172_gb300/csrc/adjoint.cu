@@ -378,7 +378,10 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
             a.raw = (raw && m == 0) ? 1 : 0;
             a.t = from + m;
             a.rho_out = record ? tape + (size_t)m * plane : nullptr;
-            fwd<<<a.main_blocks, kThreads, 0, ctx->stream>>>(a);
+            if (ctx->staged)
+                stream_launch(ctx, a, 0);  // cannot fail once the forward run has stepped
+            else
+                fwd<<<a.main_blocks, kThreads, 0, ctx->stream>>>(a);
             in = a.out;
             x ^= 1;
         }

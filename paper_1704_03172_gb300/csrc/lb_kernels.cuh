@@ -492,12 +492,103 @@ __device__ __forceinline__ float next_scale(float maxval, float S, float keep) {
     return bound > 0.f ? pow2_ceil(bound * (1.f / kStoredTarget)) : keep;
 }
 
+// Collision, source and sponge for a thread's V sites, in place.  EDGE: some site
+// lies in the sponge or beyond the last column (damped / zeroed per site).
+template <int Q, bool MRT, int V, bool EDGE>
+__device__ __forceinline__ void collide_sites(float (&g)[Q][V], const float (&e2s)[V],
+                                              const StepArgs &a, int x0, int y, bool has_src) {
+#pragma unroll
+    for (int k = 0; k < V; k++) {
+        float gs[Q];
+#pragma unroll
+        for (int i = 0; i < Q; i++) gs[i] = g[i][k];
+        if (Q == 5)
+            collide5<MRT>(gs, e2s[k], a);
+        else
+            collide9<MRT>(gs, e2s[k], a);
+        if (has_src && a.src_x == x0 + k) {
+            const float S = a.src_tab[a.t];
+#pragma unroll
+            for (int i = 0; i < Q; i++) gs[i] += weight_i<Q>(i, e2s[k], a) * S;
+        }
+        if (EDGE) {
+            const float f = a.sponge_w > 0 ? sponge_factor(x0 + k, y, a) : 1.f;
+            const bool real = x0 + k < a.nx;
+#pragma unroll
+            for (int i = 0; i < Q; i++) g[i][k] = real ? gs[i] * f : 0.f;
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; i++) g[i][k] = gs[i];
+        }
+    }
+}
+
+// Everything after the pulls, for a thread's V sites at (x0..x0+V-1, y): FP16
+// input scale, the adjoint replay's rho record, collision + source + sponge, and
+// the vector store of h(t) (FP16: scaled, with this thread's max |h_i| folded
+// into tmax).  Shared by the register-streaming and the TMA-staged kernels.
+template <int Q, bool MRT, typename ST>
+__device__ __forceinline__ void finish_sites(const StepArgs &a, float (&g)[Q][Store<ST>::V],
+                                             const float (&e2s)[Store<ST>::V], int x0, int y,
+                                             float tmax[Q]) {
+    constexpr bool SC = Scaled<ST>::value;
+    constexpr int V = Store<ST>::V;
+    if (SC) {  // one scale per population: applied after the shuffles
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const float sc = a.scale_in[i];
+#pragma unroll
+            for (int k = 0; k < V; k++) g[i][k] *= sc;
+        }
+    }
+
+    if (a.rho_out) {  // warp-uniform: adjoint replay records rho(t)
+#pragma unroll
+        for (int k = 0; k < V; k += 4) {
+            float r[4];
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                r[m] = 0.f;
+#pragma unroll
+                for (int i = 0; i < Q; i++) r[m] += g[i][k + m];
+            }
+            *reinterpret_cast<float4 *>(a.rho_out + (long long)y * a.pitch + x0 + k) =
+                make_float4(r[0], r[1], r[2], r[3]);
+        }
+    }
+    const bool edge = a.sponge_w > 0 &&
+                      (y < a.sponge_w || y >= a.ny - a.sponge_w || x0 < a.sponge_w ||
+                       x0 + V - 1 >= a.nx - a.sponge_w);
+    const bool has_src = (y == a.src_y) && (a.src_x >= x0) && (a.src_x < x0 + V) &&
+                         a.src_tab != nullptr && a.t < a.src_nt;
+    // collide site by site, in place: g[i][k] becomes the stored output.  Threads whose
+    // sites are all real and outside the sponge (almost all) skip damping and masking.
+    if (!edge && x0 + V <= a.nx)
+        collide_sites<Q, MRT, V, false>(g, e2s, a, x0, y, has_src);
+    else
+        collide_sites<Q, MRT, V, true>(g, e2s, a, x0, y, has_src);
+    ST *o = static_cast<ST *>(a.out) + (long long)y * a.pitch + x0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        if (SC) {
+            const float inv = 1.f / a.scale_out[i];  // exact: a power of two
+            float m = 0.f;
+#pragma unroll
+            for (int k = 0; k < V; k++) {
+                m = fmaxf(m, fabsf(g[i][k]));
+                g[i][k] *= inv;
+            }
+            tmax[i] = fmaxf(tmax[i], m);
+        }
+        Store<ST>::storeV(o + i * a.plane, g[i]);
+    }
+}
+
 // The sites of one warp row-segment of block `blk`; tmax receives this
 // thread's max |out_i|.
 template <int Q, bool MRT, bool PERIODIC, typename ST>
 __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tmax[Q],
                                            const float *tab) {
-    constexpr bool SC = Scaled<ST>::value;
 #pragma unroll
     for (int i = 0; i < Q; i++) tmax[i] = 0.f;
     const int lane = threadIdx.x & 31;
@@ -539,29 +630,6 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
             pull_finish<0, PERIODIC, ST>(absent[i], x0, lane, a.nx, q[i], e[i], g[i]);
     }
     if (!active) return;  // no shuffles below
-    if (SC) {  // one scale per population: applied after the shuffles
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            const float sc = a.scale_in[i];
-#pragma unroll
-            for (int k = 0; k < V; k++) g[i][k] *= sc;
-        }
-    }
-
-    if (a.rho_out) {  // warp-uniform: adjoint replay records rho(t)
-#pragma unroll
-        for (int k = 0; k < V; k += 4) {
-            float r[4];
-#pragma unroll
-            for (int m = 0; m < 4; m++) {
-                r[m] = 0.f;
-#pragma unroll
-                for (int i = 0; i < Q; i++) r[m] += g[i][k + m];
-            }
-            *reinterpret_cast<float4 *>(a.rho_out + (long long)y * a.pitch + x0 + k) =
-                make_float4(r[0], r[1], r[2], r[3]);
-        }
-    }
     float e2s[V];
     if (a.mid) {  // warp-uniform: 1-byte medium index, eta^2 from the shared table
         const uint8_t *mp = a.mid + (long long)y * a.pitch + x0;
@@ -582,47 +650,7 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
             e2s[k] = e.x; e2s[k + 1] = e.y; e2s[k + 2] = e.z; e2s[k + 3] = e.w;
         }
     }
-    const bool edge = a.sponge_w > 0 &&
-                      (y < a.sponge_w || y >= a.ny - a.sponge_w || x0 < a.sponge_w ||
-                       x0 + V - 1 >= a.nx - a.sponge_w);
-    const bool has_src = (y == a.src_y) && (a.src_x >= x0) && (a.src_x < x0 + V) &&
-                         a.src_tab != nullptr && a.t < a.src_nt;
-    // collide site by site, in place: g[i][k] becomes the stored output
-#pragma unroll
-    for (int k = 0; k < V; k++) {
-        float gs[Q];
-#pragma unroll
-        for (int i = 0; i < Q; i++) gs[i] = g[i][k];
-        if (Q == 5)
-            collide5<MRT>(gs, e2s[k], a);
-        else
-            collide9<MRT>(gs, e2s[k], a);
-        if (has_src && a.src_x == x0 + k) {
-            const float S = a.src_tab[a.t];
-#pragma unroll
-            for (int i = 0; i < Q; i++) gs[i] += weight_i<Q>(i, e2s[k], a) * S;
-        }
-        float f = 1.f;
-        if (edge) f = sponge_factor(x0 + k, y, a);
-        const bool real = x0 + k < a.nx;
-#pragma unroll
-        for (int i = 0; i < Q; i++) g[i][k] = real ? gs[i] * f : 0.f;
-    }
-    ST *o = static_cast<ST *>(a.out) + (long long)y * a.pitch + x0;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        if (SC) {
-            const float inv = 1.f / a.scale_out[i];  // exact: a power of two
-            float m = 0.f;
-#pragma unroll
-            for (int k = 0; k < V; k++) {
-                m = fmaxf(m, fabsf(g[i][k]));
-                g[i][k] *= inv;
-            }
-            tmax[i] = m;
-        }
-        Store<ST>::storeV(o + i * a.plane, g[i]);
-    }
+    finish_sites<Q, MRT, ST>(a, g, e2s, x0, y, tmax);
 }
 
 template <int Q, bool MRT, bool PERIODIC, typename ST>

@@ -19,9 +19,11 @@ struct lb_ctx {
     int cur = 0;                    // pop[cur] holds the post-collision state of step t-1
     bool raw = false;               // ... or, when raw, the state g(t) itself (unshifted)
     float *eta2 = nullptr;
-    uint8_t *mid = nullptr;      // medium index (<= 256 distinct speeds), or nullptr
-    float *mid_tab = nullptr;    // [256] eta^2 per index
-    int n_mid = 0;          // [ny][pitch] (c / c_ref)^2
+    uint8_t *mid = nullptr;         // medium index (<= 256 distinct speeds), or nullptr
+    float *mid_tab = nullptr;       // [256] eta^2 per index
+    int n_mid = 0;
+    bool staged = false;            // steps run the TMA-staged persistent kernel
+    unsigned *fault = nullptr;      // device flag: a bounded wait in a kernel gave up
     float *lp_scale = nullptr;      // FP16 storage: [3][9] per-population scales (slots)
     unsigned *lp_max = nullptr;     // FP16 storage: [3][9][kMaxCopies] max |value| + counter
     int lp_slot = 0;                // slot describing the current buffer
@@ -90,6 +92,8 @@ void ckpt_reset(lb_ctx *ctx);
 
 // temporal blocking (tblock.cu)
 bool tb_supported(int Q, int K);
+// TMA-staged persistent step (stream_step.cu): one LB step of the context's grid
+lb_status stream_launch(lb_ctx *ctx, const lbk::StepArgs &a, int rec_blocks);
 lb_status tb_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
 lb_status tb_launch(lb_ctx *ctx, int K);
 

@@ -263,6 +263,8 @@ lb_status validate(const lb_config *cfg) {
         if (cfg->storage != LB_F32 || cfg->n_patches > 0)
             return fail(nullptr, LB_EINVAL, "time_block needs FP32 storage and no patch");
     }
+    if (cfg->step_kernel != LB_STEP_AUTO && cfg->step_kernel != LB_STEP_DIRECT)
+        return fail(nullptr, LB_EINVAL, "step_kernel must be LB_STEP_AUTO or LB_STEP_DIRECT");
     return LB_OK;
 }
 
@@ -356,7 +358,11 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     }
     c->eta2 = static_cast<float *>(dev_alloc(c, plane * 4));
     unsigned *flags = static_cast<unsigned *>(dev_alloc(c, 256));
-    if (!c->eta2 || !flags) return bail(fail(c, LB_ENOMEM, "medium buffer"));
+    c->fault = static_cast<unsigned *>(dev_alloc(c, 256));
+    if (!c->eta2 || !flags || !c->fault) return bail(fail(c, LB_ENOMEM, "medium buffer"));
+    cudaMemsetAsync(c->fault, 0, 4, c->stream);
+    // 16-bit storage: the TMA-staged persistent step (faster there); FP32: register-streaming
+    c->staged = cfg->step_kernel == LB_STEP_AUTO && cfg->n_patches == 0 && cfg->storage != LB_F32;
     if (cfg->storage == LB_F16) {  // FP16 range scales (BF16 has FP32's range and needs none)
         c->lp_scale = static_cast<float *>(dev_alloc(c, 3 * 9 * sizeof(float)));
         c->lp_max = static_cast<unsigned *>(dev_alloc(c, (3 * 9 * kMaxCopies + 1) * sizeof(unsigned)));
@@ -648,7 +654,12 @@ lb_status launch_step(lb_ctx *ctx, StepFn fn, StepArgs &a) {
     a.trace_row = (ctx->trace && row >= 0 && row < ctx->trace_cap) ? ctx->trace + row * ctx->nrec
                                                                   : nullptr;
     int rec_blocks = a.trace_row ? (ctx->nrec + kThreads - 1) / kThreads : 0;
-    fn<<<a.main_blocks + rec_blocks, kThreads, 0, ctx->stream>>>(a);
+    if (ctx->staged) {
+        lb_status st = stream_launch(ctx, a, rec_blocks);
+        if (st != LB_OK) return st;
+    } else {
+        fn<<<a.main_blocks + rec_blocks, kThreads, 0, ctx->stream>>>(a);
+    }
     if (ctx->lp_scale) scale_update_kernel<<<1, 32, 0, ctx->stream>>>(a, ctx->Q);
     ctx->cur ^= 1;
     ctx->t += 1;
@@ -686,7 +697,8 @@ lb_status lb_step(lb_ctx *ctx, int n) {
                 continue;
             }
         }
-        launch_step(ctx, fn, a);
+        lb_status st = launch_step(ctx, fn, a);
+        if (st != LB_OK) return st;
         k += 1;
     }
     return check_launch(ctx, "step_kernel");
@@ -722,6 +734,10 @@ lb_status lb_sync(lb_ctx *ctx) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stream");
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "device");
+    unsigned fault = 0;
+    e = cudaMemcpy(&fault, ctx->fault, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fault flag");
+    if (fault) return fail(ctx, LB_ETIMEOUT, "a bounded wait in a step kernel gave up");
     return LB_OK;
 }
 

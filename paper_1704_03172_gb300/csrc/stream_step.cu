@@ -1,0 +1,415 @@
+// stream_step.cu -- TMA-staged persistent form of the fused LB step.
+//
+// Same per-site arithmetic as step_kernel (finish_sites / collide_sites in
+// lb_kernels.cuh), different data movement.  A persistent grid (resident CTAs
+// x SM count) walks the row segments ("tasks") of the grid: task = W = 256 V
+// consecutive sites of one row.  For every task one thread issues, per
+// population, a bulk copy (cp.async.bulk, the untiled TMA form) of the source
+// row segment with a 16-byte halo on each side, plus the segment's medium
+// (1-byte index or FP32 eta^2), into a shared-memory stage, completing on that
+// stage's mbarrier.  While a CTA computes task k from stage k mod S, the copies
+// of the next S - 1 tasks are in flight, so the loads are decoupled from the
+// arithmetic and no register holds data waiting on DRAM.  Outputs go straight
+// from registers to HBM with 16-byte stores.
+//
+// Addresses and sizes of every bulk copy are multiples of 16 bytes: rows are
+// pitch elements apart (pitch a multiple of 32 elements), a task starts at a
+// multiple of W elements (W * element size = 4096 bytes) and the halo is 16
+// bytes; copies are clipped to [0, pitch) of the row.
+//
+// Used for 16-bit storage, where it beats the register-streaming kernel (GB300,
+// 4096^2: BF16 D2Q5 206 -> 261 GLUPS, FP16 195 -> 214, BF16 D2Q9 82 -> 128); for
+// FP32 the register-streaming kernel is faster (159 vs 135 GLUPS) and stays.
+//
+// Every wait on an mbarrier is bounded (one second of %globaltimer).  On a
+// timeout the block votes to stop, raises the context's fault flag (read by
+// lb_sync), waits (bounded again) for the copies it still has in flight and
+// returns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "lb_kernels.cuh"
+#include "lb_runtime.h"
+
+using namespace lbk;
+using namespace lbrt;
+
+namespace {
+
+constexpr int kSThreads = 256;                       // threads per CTA
+constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of every mbarrier wait
+
+template <typename ST> struct Geom {
+    static constexpr int V = Store<ST>::V;             // sites per thread
+    static constexpr int W = kSThreads * V;            // sites per task
+    static constexpr int H = 16 / (int)sizeof(ST);     // halo elements (16 bytes)
+    static constexpr int ROWB = (W + 2 * H) * (int)sizeof(ST);  // staged bytes per population
+};
+
+// A stage: Q staged population rows, then the medium (W bytes of index or 4W of eta^2).
+template <int Q, typename ST> struct Stage {
+    static constexpr int kPops = Q * Geom<ST>::ROWB;
+    static_assert(kPops % 16 == 0, "16-byte aligned stage layout");
+    static constexpr int bytes(bool indexed) { return kPops + Geom<ST>::W * (indexed ? 1 : 4); }
+};
+constexpr int kMaxStages = 4;
+
+struct SArgs {
+    int tasks_per_row;
+    int ntasks;
+    int ncta;          // persistent CTAs; blocks beyond them gather receivers
+    int stages;        // shared-memory stages per CTA (2 .. kMaxStages)
+    int stage_bytes;   // bytes per stage (a multiple of 16)
+    unsigned *fault;   // raised when a bounded wait gives up
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase `parity` of *bar; false after kWaitNs without completion.
+__device__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitNs) return false;
+    return true;
+}
+
+// Bulk copy global -> shared (TMA, untiled), completing `bytes` on *bar.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+}  // namespace
+
+namespace {
+
+// Source row of population i for output row y; -1: outside a zero-ghost domain.
+template <int Q, bool PERIODIC>
+__device__ __forceinline__ int source_row(const StepArgs &a, int i, int y) {
+    if (a.raw) return y;  // first step after lb_set_state: g(t) is read in place
+    int ys = y - Lat<Q>::cy(i);
+    if (ys < 0 || ys >= a.ny) {
+        if (!PERIODIC) return -1;
+        ys = ys < 0 ? ys + a.ny : ys - a.ny;
+    }
+    return ys;
+}
+
+// Thread 0: queue the bulk copies of task `task` into `stage`, completing on *bar.
+template <int Q, bool PERIODIC, typename ST>
+__device__ void issue_task(const StepArgs &a, const SArgs &s, int task, unsigned char *stage,
+                           uint64_t *bar) {
+    using G = Geom<ST>;
+    const int y = task / s.tasks_per_row, xs = (task - y * s.tasks_per_row) * G::W;
+    const int lo = max(xs - G::H, 0), hi = min(xs + G::W + G::H, a.pitch);
+    const unsigned rowb = (unsigned)(hi - lo) * (unsigned)sizeof(ST);
+    const unsigned dst = (unsigned)(lo - (xs - G::H)) * (unsigned)sizeof(ST);
+    const unsigned medb = (unsigned)min(G::W, a.pitch - xs) * (a.mid ? 1u : 4u);
+    int ys[Q];
+    unsigned total = medb;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        ys[i] = source_row<Q, PERIODIC>(a, i, y);
+        if (ys[i] >= 0) total += rowb;
+    }
+    mbar_expect_tx(bar, total);
+    const ST *in = static_cast<const ST *>(a.in);
+#pragma unroll
+    for (int i = 0; i < Q; i++)
+        if (ys[i] >= 0)
+            bulk_g2s(stage + i * G::ROWB + dst, in + i * a.plane + (long long)ys[i] * a.pitch + lo,
+                     rowb, bar);
+    const long long m0 = (long long)y * a.pitch + xs;
+    const void *msrc = a.mid ? static_cast<const void *>(a.mid + m0)
+                             : static_cast<const void *>(a.eta2 + m0);
+    bulk_g2s(stage + Stage<Q, ST>::kPops, msrc, medb, bar);  // medb <= W or 4W by form
+}
+
+// All threads: one task from its stage.  Thread t owns sites x0 = xs + t V .. + V - 1;
+// the +-1 x-shifts come from the neighbouring lane (shuffle) or, at lanes 0 / 31, from
+// the staged neighbour element (the 16-byte halo at the task's ends).
+template <int Q, bool MRT, bool PERIODIC, typename ST>
+__device__ __forceinline__ void compute_task(const StepArgs &a, const SArgs &s, int task,
+                                             const unsigned char *stage, const float *tab,
+                                             float tmax[Q]) {
+    using G = Geom<ST>;
+    constexpr int V = G::V;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int y = task / s.tasks_per_row, xs = (task - y * s.tasks_per_row) * G::W;
+    const int x0 = xs + tid * V;
+    const bool active = x0 < a.nx;
+    const ST *in = static_cast<const ST *>(a.in);
+    float g[Q][V];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int cx = a.raw ? 0 : Lat<Q>::cx(i);
+        const int ys = source_row<Q, PERIODIC>(a, i, y);
+        const ST *sp = reinterpret_cast<const ST *>(stage + i * G::ROWB) + G::H + tid * V;
+        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+        if (ys >= 0 && active) q = *reinterpret_cast<const uint4 *>(sp);
+        float f[V];
+        Store<ST>::unpackV(q, f);
+        if (cx == 0) {
+#pragma unroll
+            for (int k = 0; k < V; k++) g[i][k] = f[k];
+        } else if (cx == 1) {  // value from x - 1
+            float left = __shfl_up_sync(0xffffffffu, f[V - 1], 1);
+            if (lane == 0) {
+                if (ys < 0)
+                    left = 0.f;
+                else if (x0 > 0)
+                    left = Store<ST>::load1(sp - 1);
+                else
+                    left = PERIODIC ? Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch +
+                                                       a.nx - 1)
+                                    : 0.f;
+            }
+            g[i][0] = left;
+#pragma unroll
+            for (int k = 1; k < V; k++) g[i][k] = f[k - 1];
+        } else {  // cx == -1: value from x + 1
+            float right = __shfl_down_sync(0xffffffffu, f[0], 1);
+            if (lane == 31) right = (ys >= 0 && x0 + V < a.nx) ? Store<ST>::load1(sp + V) : 0.f;
+#pragma unroll
+            for (int k = 0; k + 1 < V; k++) g[i][k] = f[k + 1];
+            g[i][V - 1] = right;
+            const int last = a.nx - 1 - x0;  // the last real site's image: periodic row[0]
+            if (last >= 0 && last < V) {
+                const float b = (PERIODIC && ys >= 0)
+                                    ? Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch)
+                                    : 0.f;
+#pragma unroll
+                for (int j = 0; j < V; j++)
+                    if (j == last) g[i][j] = b;
+            }
+        }
+    }
+    if (!active) return;  // no shuffles below
+    float e2s[V];
+    const unsigned char *mp = stage + Stage<Q, ST>::kPops;
+    if (a.mid) {
+        uint32_t w[V / 4];
+        if (V == 4) {
+            w[0] = *reinterpret_cast<const uint32_t *>(mp + tid * V);
+        } else {
+            const uint2 u = *reinterpret_cast<const uint2 *>(mp + tid * V);
+            w[0] = u.x;
+            w[V / 4 - 1] = u.y;
+        }
+#pragma unroll
+        for (int k = 0; k < V; k++) e2s[k] = tab[(w[k >> 2] >> (8 * (k & 3))) & 0xffu];
+    } else {
+        const float *ep = reinterpret_cast<const float *>(mp) + tid * V;
+#pragma unroll
+        for (int k = 0; k < V; k += 4) {
+            const float4 e = *reinterpret_cast<const float4 *>(ep + k);
+            e2s[k] = e.x; e2s[k + 1] = e.y; e2s[k + 2] = e.z; e2s[k + 3] = e.w;
+        }
+    }
+    finish_sites<Q, MRT, ST>(a, g, e2s, x0, y, tmax);
+}
+
+}  // namespace
+
+namespace {
+
+// Resident CTAs per SM the register budget is held to (8 warps each).
+template <int Q, typename ST> constexpr int stream_min_ctas() {
+    return Q == 5 ? (sizeof(ST) == 4 ? 5 : (Scaled<ST>::value ? 3 : 4)) : (sizeof(ST) == 4 ? 3 : 2);
+}
+
+template <int Q, bool MRT, bool PERIODIC, typename ST>
+__global__ void __launch_bounds__(kSThreads, (stream_min_ctas<Q, ST>()))
+    stream_step_kernel(const StepArgs a, const SArgs s) {
+    constexpr bool SC = Scaled<ST>::value;
+    const int S = s.stages, SB = s.stage_bytes;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kMaxStages];
+    __shared__ float s_tab[kSThreads];
+    __shared__ float s_wmax[SC ? 9 : 1][kSThreads / 32];
+    if ((int)blockIdx.x >= s.ncta) {  // block-uniform: receiver gather blocks
+        gather_receivers<Q, PERIODIC, ST>(a, ((int)blockIdx.x - s.ncta) * kSThreads +
+                                                 (int)threadIdx.x);
+        return;
+    }
+    const int tid = threadIdx.x;
+    if (a.mid) s_tab[tid] = a.mid_tab[tid];
+    if (tid == 0) {
+        for (int st = 0; st < S; st++) mbar_init(&full[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int st = 0; st < S; st++) {  // prologue: the first S tasks in flight
+            const int task = (int)blockIdx.x + st * s.ncta;
+            if (task < s.ntasks) issue_task<Q, PERIODIC, ST>(a, s, task, smem + st * SB, &full[st]);
+        }
+    }
+    __syncthreads();
+    float tmax[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) tmax[i] = 0.f;
+    int k = 0;
+    bool failed = false;
+    for (int task = blockIdx.x; task < s.ntasks; task += s.ncta, k++) {
+        const int st = k % S;
+        // warp-uniform outcome: compute_task shuffles with all 32 lanes
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[st], (unsigned)(k / S) & 1u));
+        if (ok) compute_task<Q, MRT, PERIODIC, ST>(a, s, task, smem + st * SB, s_tab, tmax);
+        // every thread is done with stage st (and every wait succeeded) before it is refilled
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0) {
+            const int next = task + S * s.ncta;
+            if (next < s.ntasks) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_task<Q, PERIODIC, ST>(a, s, next, smem + st * SB, &full[st]);
+            }
+        }
+    }
+    if (failed) {  // record, then wait (bounded) for this block's copies still in flight
+        if (tid == 0) {
+            atomicExch(s.fault, 1u);
+            for (int j = 0; j < S; j++) {
+                const int kk = k + j;
+                if ((int)blockIdx.x + kk * s.ncta >= s.ntasks) break;
+                mbar_wait(&full[kk % S], (unsigned)(kk / S) & 1u);
+            }
+        }
+        return;
+    }
+    if (SC) {  // fold this block's max |output| per population into max_out
+        const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            float m = tmax[i];
+            for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+            if (lane == 0) s_wmax[SC ? i : 0][w] = m;
+        }
+        __syncthreads();
+        if (tid < Q) {
+            float m = 0.f;
+            for (int j = 0; j < kSThreads / 32; j++) m = fmaxf(m, s_wmax[SC ? tid : 0][j]);
+            atomicMax(a.max_out + tid * kMaxCopies + (blockIdx.x % kMaxCopies), __float_as_uint(m));
+        }
+    }
+}
+
+using SFn = void (*)(const StepArgs, const SArgs);
+
+// Two stages per CTA: while one task is computed, the next task's copies are in
+// flight.  Measured on GB300 (4096^2 two-layer): deeper pipelines cost more
+// shared memory (fewer resident CTAs) than they gain.
+constexpr int kStages = 2;
+
+struct SInfo {
+    SFn fn = nullptr;
+    int stages = 0;
+    int stage_bytes = 0;
+    int smem = 0;   // dynamic shared memory per CTA
+    int ctas = 0;   // resident CTAs on the device
+    int W = 0;      // sites per task
+};
+
+template <int Q, bool MRT, bool PER, typename ST> SInfo make_info(bool indexed) {
+    SInfo in;
+    in.fn = stream_step_kernel<Q, MRT, PER, ST>;
+    in.stages = kStages;
+    in.stage_bytes = Stage<Q, ST>::bytes(indexed);
+    in.smem = in.stage_bytes * in.stages;
+    in.W = Geom<ST>::W;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // the attribute belongs to the kernel, shared by both medium forms: allow the larger
+    const int smem_max = Stage<Q, ST>::bytes(false) * kStages;
+    if (cudaFuncSetAttribute(in.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, in.fn, kSThreads, in.smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+    }
+    in.ctas = per_sm * sms;
+    return in;
+}
+
+template <int Q, bool MRT, typename ST> SInfo info_p(bool per, bool ix) {
+    return per ? make_info<Q, MRT, true, ST>(ix) : make_info<Q, MRT, false, ST>(ix);
+}
+
+template <typename ST> SInfo info_st(int Q, bool mrt, bool per, bool ix) {
+    if (Q == 9) return mrt ? info_p<9, true, ST>(per, ix) : info_p<9, false, ST>(per, ix);
+    return mrt ? info_p<5, true, ST>(per, ix) : info_p<5, false, ST>(per, ix);
+}
+
+// Kernel, shared memory and resident CTA count per (Q, MRT, PERIODIC, storage), measured
+// once per process (one device).
+const SInfo &stream_info(int Q, bool mrt, bool per, int storage, bool ix) {
+    static std::mutex mu;
+    static SInfo cache[2][2][2][3][2];
+    static bool ready[2][2][2][3][2] = {};
+    const int q = Q == 9, m = mrt, p = per, st = storage == LB_BF16 ? 1 : storage == LB_F16 ? 2 : 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready[q][m][p][st][ix]) {
+        cache[q][m][p][st][ix] = st == 1   ? info_st<__nv_bfloat16>(Q, mrt, per, ix)
+                                 : st == 2 ? info_st<__half>(Q, mrt, per, ix)
+                                           : info_st<float>(Q, mrt, per, ix);
+        ready[q][m][p][st][ix] = true;
+    }
+    return cache[q][m][p][st][ix];
+}
+
+}  // namespace
+
+lb_status stream_launch(lb_ctx *ctx, const StepArgs &a, int rec_blocks) {
+    const SInfo &in = stream_info(ctx->Q, ctx->cfg.collision == LB_MRT,
+                                  ctx->cfg.boundary == LB_PERIODIC, ctx->cfg.storage,
+                                  a.mid != nullptr);
+    if (in.ctas < 1) return fail(ctx, LB_ECUDA, "TMA-staged step: no resident CTA fits");
+    SArgs s;
+    s.tasks_per_row = (ctx->nx + in.W - 1) / in.W;
+    s.ntasks = s.tasks_per_row * ctx->ny;
+    s.ncta = std::min(s.ntasks, in.ctas);
+    s.stages = in.stages;
+    s.stage_bytes = in.stage_bytes;
+    s.fault = ctx->fault;
+    in.fn<<<s.ncta + rec_blocks, kSThreads, in.smem, ctx->stream>>>(a, s);
+    return LB_OK;
+}

@@ -22,6 +22,7 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE = 0,
 LB_D2Q5, LB_D2Q9 = 5, 9
 LB_BGK, LB_MRT = 0, 1
 LB_F32, LB_BF16, LB_F16 = 0, 1, 2
+LB_STEP_AUTO, LB_STEP_DIRECT = 0, 1
 LB_ZERO_GHOST, LB_PERIODIC = 0, 1
 STATUS_NAMES = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOMEM", -3: "LB_ECUDA",
                 -4: "LB_EUNSTABLE", -5: "LB_ETIMEOUT", -6: "LB_ESTATE"}
@@ -46,6 +47,7 @@ class lb_config(ctypes.Structure):
         ("patches", ctypes.POINTER(lb_patch)), ("n_patches", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p), ("time_block", ctypes.c_int),
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+        ("step_kernel", ctypes.c_int),
     ]
 
 

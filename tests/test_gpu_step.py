@@ -208,3 +208,44 @@ def test_medium_index_not_used_beyond_256_speeds(sim_cls):
     sim = sim_cls(c3, lattice=5, c_ref=1.0)             # 257: per-site eta^2
     assert sim.info()[4] == 0
     sim.close()
+
+
+@pytest.mark.parametrize("Q,storage,coll,periodic,nx,ny,layered", [
+    (5, "bf16", "bgk", False, 3000, 37, True),    # two tasks per row, ragged second task
+    (5, "bf16", "mrt", True, 2056, 21, False),
+    (5, "bf16", "bgk", False, 2050, 19, True),
+    (5, "f16", "bgk", False, 700, 33, False),
+    (5, "f16", "mrt", True, 4100, 9, True),
+    (9, "bf16", "mrt", False, 2100, 17, True),
+    (9, "bf16", "bgk", True, 300, 40, False),
+    (9, "f16", "bgk", False, 64, 12, False),
+    (5, "bf16", "bgk", True, 33, 5, False),
+])
+def test_staged_step_matches_direct_step_bitwise(sim_cls, Q, storage, coll, periodic, nx, ny,
+                                                 layered):
+    # For 16-bit storage the default step is the TMA-staged persistent kernel; it runs
+    # the register-streaming step's per-site arithmetic: states and traces must agree bit for bit, including the
+    # first step from an arbitrary state (read in place), the sponge, the source and
+    # both medium forms.
+    rng = np.random.default_rng(nx + ny)
+    c = (W.layered_fault_model(nx, ny, 5, n_layers=7, throw=(1.0, 4.0)) if layered
+         else W.random_medium(nx, ny, 6, 0.5, 1.0))
+    g0 = (rng.normal(size=(Q, ny, nx)) * 0.1).astype(np.float32)
+    rec = np.stack([rng.integers(0, nx, 12), rng.integers(0, ny, 12)], 1).astype(np.int32)
+    src = (nx // 3, ny // 2, W.ricker(30, 0.05))
+    s = ([1.0, 1.0, 1.0, 1.6, 1.3] if Q == 5 else [1.0, 1.0, 1.0, 1.7, 1.4, 1.6, 1.2, 1.2, 1.4])
+    out = []
+    for kernel in ("auto", "direct"):
+        sim = sim_cls(c, lattice=Q, collision=coll, s=s if coll == "mrt" else None, tau=0.6,
+                      storage=storage, c_ref=float(c.max()), sponge_width=0 if periodic else 4,
+                      boundary="periodic" if periodic else "zero", step_kernel=kernel,
+                      w_ref=(0.0, 0.01, 0.24) if Q == 9 else (4 / 9, 1 / 9, 1 / 36))
+        sim.set_source(*src)
+        sim.set_receivers(rec, 30)
+        sim.set_state(g0)
+        sim.step(30)
+        out.append((sim.state().cpu().numpy(), sim.traces(30).cpu().numpy()))
+        sim.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert np.isfinite(out[0][0]).all() and np.abs(out[0][1]).max() > 0
