@@ -36,6 +36,17 @@ FALLBACK_HBM_GBS = 6800.0
 ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel on the
+# 4096^2 two-layer workload, from one ncu capture of the current kernel (the summaries under
+# profiles/ give the commands); keyed by (kernel, medium index).  A kernel without an entry,
+# or one changed since its capture, reports null.
+NCU_TRAFFIC = {
+    ("lbk::step_kernel<5,false,false,float>", True): 639.9e6,
+    ("stream_step_kernel<5,false,false,__nv_bfloat16>", True): 302.2e6,
+    ("tb_kernel<5,false,false,8>", False): 705.5e6,
+}
+
+
 def bytes_per_site(Q, storage, indexed):
     """Algorithmic HBM bytes of one site update: read and write every population once,
     plus the medium read (a 1-byte medium index, or 4-byte eta^2 per site)."""
@@ -507,9 +518,12 @@ def run_ours(args):
     launches = (args.steps + K - 1) // K
     per_launch_s = sec / launches
     achieved = bps * sites * K / per_launch_s / 1e9   # algorithmic one-step bytes per update
+    staged = K == 1 and args.step_kernel == "auto" and args.storage != "f32"
+    st_name = dict(f32='float', bf16='__nv_bfloat16', f16='__half')[args.storage]
     kname = (f"tb_kernel<{args.lattice},false,false,{K}>" if K > 1 else
-             f"lbk::step_kernel<{args.lattice},false,false,"
-             f"{dict(f32='float', bf16='__nv_bfloat16', f16='__half')[args.storage]}>")
+             f"stream_step_kernel<{args.lattice},false,false,{st_name}>" if staged else
+             f"lbk::step_kernel<{args.lattice},false,false,{st_name}>")
+    traffic = NCU_TRAFFIC.get((kname, bool(indexed and K == 1)))
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
@@ -525,7 +539,7 @@ def run_ours(args):
                              else "eta^2 per site (FP32)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "kernel": kname,
+                     "traffic": traffic, "kernel": kname,
                      "algorithmic_bytes_per_launch": bps * sites * K,
                      "note": "achieved counts the one-step algorithmic bytes of every fused step"
                      if K > 1 else "one launch per step"},

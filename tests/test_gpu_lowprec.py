@@ -168,3 +168,34 @@ def test_f16_scale_follows_a_large_source(sim_cls, oracle_mod):
     _, tro = oracle_mod.run(P, P.zeros(), steps)
     assert bad == 0 and gmax > 65504          # values beyond the FP16 range, stored scaled
     assert rel(tr, tro) < LOWPREC_BOUND["f16"]
+
+
+def test_layered_model_error_per_receiver_trace(sim_cls, oracle_mod):
+    # The faulted layered workload (20 layers, c in [1500, 5500] m/s, throws scaled to the grid),
+    # reduced to 512^2 and 2000 steps so the oracle finishes in seconds: the error of every
+    # receiver trace against the FP64 oracle, per storage form.
+    n, nt = 512, 2000
+    c = W.layered_fault_model(n, n, W.DEFAULT_SEED + 4, n_layers=20,
+                              throw=(20.0 * n / 8192, 200.0 * n / 8192))
+    src = (n // 2, 48, W.ricker(nt, W.SERVED_FC))
+    rec = W.line_receivers(64, 48, 40, n - 80)
+    P = oracle_mod.Problem(5, n, n, c, c_ref=W.SERVED_C_REF, tau=0.5, sponge_width=40,
+                           sponge_sigma_max=0.1, source=src, receivers=rec)
+    _, tro = oracle_mod.run(P, P.zeros(), nt)
+    per = {}
+    for storage in ("f32", "bf16", "f16"):
+        sim = sim_cls(c, lattice=5, tau=0.5, c_ref=W.SERVED_C_REF, storage=storage,
+                      sponge_width=40, sponge_sigma_max=0.1)
+        sim.set_source(*src)
+        sim.set_receivers(rec, nt)
+        sim.init_pressure(None)
+        sim.step(nt)
+        tr = sim.traces(nt).cpu().numpy().astype(np.float64)
+        sim.close()
+        e = np.linalg.norm(tr - tro, axis=0) / np.linalg.norm(tro, axis=0)
+        per[storage] = e
+        _record(f"layered_512_d2q5_{storage}_per_trace",
+                {"max": float(e.max()), "median": float(np.median(e)), "all": rel(tr, tro)})
+    assert per["f32"].max() < 1e-5
+    assert per["f16"].max() < LOWPREC_BOUND["f16"]
+    assert per["bf16"].max() < LOWPREC_BOUND["bf16"]
