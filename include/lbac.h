@@ -274,6 +274,15 @@ lb_status lb_invariants_noalloc(const float *g, const float *c_map, int lattice,
  * want_adjoint > 0 (the checkpoint interval; 1 means the default 200). */
 lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint, size_t *bytes);
 
+/* Fourier projections of the pressure for dispersion diagnostics (the
+ * single-mode analysis of Sec. 3, Eq. MRT-LB dispersion; Fig. 3 / Fig. 4):
+ * for m < n_modes, with integer wave numbers (mx, my) = modes[2m], modes[2m+1]
+ * and k = 2 pi (mx / nx, my / ny),
+ *   out[2m] + i out[2m+1] = sum_x p(x) exp(-i k . x),  p = c_s^2 rho (Eq. state),
+ * of the state at the current time, summed in FP64 on the device in a fixed
+ * order.  Host arrays.  LB_ESTATE for a refined context.  Synchronises. */
+lb_status lb_mode_projection(lb_ctx *ctx, const int *modes, int n_modes, double *out);
+
 /* Sizes and derived constants: info[0] = Q, info[1] = row pitch in elements,
  * info[2] = bytes per stored population value, info[3] = physical time step
  * dt = dx c_s(eta=1) / c_ref (seconds; 0 when dx or c_ref is 0), info[4] = number

@@ -96,6 +96,7 @@ _SIGS = {
                      ctypes.POINTER(ctypes.c_size_t)],
     "lb_info": [_ctx_p, _dp, ctypes.c_int],
     "lb_invariants": [_ctx_p, _dp],
+    "lb_mode_projection": [_ctx_p, _ip, ctypes.c_int, _dp],
     "lb_invariants_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                               ctypes.c_int, ctypes.c_double, _dp, ctypes.c_void_p,
                               ctypes.c_void_p],
@@ -275,6 +276,15 @@ def lb_invariants_noalloc(g_ptr, c_map_ptr, lattice, nx, ny, c_ref, w_ref, out_p
     wr = (ctypes.c_double * 3)(*w_ref) if w_ref is not None else None
     return _check(_lib.lb_invariants_noalloc(g_ptr, c_map_ptr, int(lattice), int(nx), int(ny),
                                              float(c_ref), wr, out_ptr, stream))
+
+
+def lb_mode_projection(ctx, modes):
+    """[(mx, my), ...] integer wave numbers -> list of complex sum_x p(x) exp(-i k.x)."""
+    n = len(modes)
+    m = (ctypes.c_int * (2 * n))(*[int(v) for pair in modes for v in pair])
+    out = (ctypes.c_double * (2 * n))()
+    _check(_lib.lb_mode_projection(ctx, m, n, out), ctx)
+    return [complex(out[2 * j], out[2 * j + 1]) for j in range(n)]
 
 
 def lb_checkpoint_every(ctx, every):
