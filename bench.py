@@ -246,6 +246,23 @@ def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32"):
                         f"checkpoint every {every}, 512 receivers, wall time of lb_adjoint"}
 
 
+def _dispersion_variant(n=128, steps=256):
+    """Fig. 3 / Fig. 4 style: phase speed / c_s of the acoustic branch, measured on the GPU
+    (single-mode runs batched in one periodic grid, FP64 projections, matrix pencil fit),
+    at theta = 0 and 45 degrees, for D2Q5 and two D2Q9 weight sets, BGK tau = 1/2."""
+    from paper_1704_03172_gb300 import dispersion as D
+    modes = [(32, 0), (16, 0), (8, 0), (4, 0), (16, 16), (8, 8), (4, 4)]
+    out = {}
+    for name, kw in (("d2q5", dict(lattice=5)),
+                     ("d2q9_conventional_weights", dict(lattice=9, w_ref=(4 / 9, 1 / 9, 1 / 36))),
+                     ("d2q9_w0_0.01_0.24", dict(lattice=9, w_ref=(0.0, 0.01, 0.24)))):
+        rows = D.phase_speed(modes, n, steps, **kw)
+        out[name] = [{"ppw": round(r["ppw"], 2), "theta_deg": round(r["theta_deg"], 1),
+                      "phase_speed_ratio": round(r["phase_speed_ratio"], 6),
+                      "damping": round(r["damping"], 8)} for r in rows]
+    return out
+
+
 def _e2e(torch, LBSim, steps_shot):
     """One full shot through the public API with host buffers (create .. traces .. destroy)."""
     from paper_1704_03172_gb300.sim import LBSim as _S  # noqa: F401
@@ -468,6 +485,8 @@ def run_ours(args):
                                    every=args.adj_every, storage=name.rsplit("_", 1)[1])
         elif name.startswith("refined"):
             out = _refined_variant(torch, LBSim, args.steps, args.warmup)
+        elif name == "dispersion":
+            out = _dispersion_variant()
         elif name == "served":
             out = _served(args.served_requests, args.served_calibration)
         else:
@@ -575,6 +594,10 @@ def run_ours(args):
                 v[f"adjoint_4096_d2q5_{st}"] = _adjoint_variant(torch, LBSim, storage=st)
             except Exception as ex:
                 v[f"adjoint_4096_d2q5_{st}"] = {"error": str(ex)[:200]}
+        try:
+            v["dispersion_bgk_tau0.5"] = _dispersion_variant()
+        except Exception as ex:
+            v["dispersion_bgk_tau0.5"] = {"error": str(ex)[:200]}
         line["variants"] = v
     if not args.no_e2e:
         line["e2e"] = _e2e(torch, LBSim, args.e2e_steps)
