@@ -96,7 +96,8 @@ def _declare(L):
 
 def _declare_refine(L):
     vp = ctypes.c_void_p
-    L.orc_ref_create.argtypes = [_pp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.orc_ref_create.argtypes = [_pp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int]
     L.orc_ref_create.restype = vp
     L.orc_ref_destroy.argtypes = [vp]
     L.orc_ref_destroy.restype = None
@@ -116,10 +117,14 @@ class Refined:
     """Two-level refined run (Sec. 4): coarse Problem P plus a patch of coarse cells
     [x0, x0 + nxp] x [y0, y0 + nyp] refined by 2 in space and time."""
 
-    def __init__(self, P: "Problem", x0, y0, nxp, nyp):
+    def __init__(self, P: "Problem", x0, y0, nxp, nyp, rule="viscous"):
+        """rule "viscous" (R6): fine rates with tau_f - 1/2 = 2 (tau_c - 1/2) and factors
+        tau_f / (2 tau_c), 2 tau_c / tau_f per relaxed moment; "paper": the printed factors
+        1/2 and 2 with the coarse rates on both grids (they coincide at tau = 1/2)."""
         self.P = P
         self._S = P._struct()
-        self.h = lib().orc_ref_create(ctypes.byref(self._S), int(x0), int(y0), int(nxp), int(nyp))
+        self.h = lib().orc_ref_create(ctypes.byref(self._S), int(x0), int(y0), int(nxp), int(nyp),
+                                      {"viscous": 0, "paper": 1}[rule])
         if not self.h:
             raise ValueError("invalid patch")
         nxf, nyf = ctypes.c_int(), ctypes.c_int()

@@ -54,7 +54,10 @@ void orc_record(const orc_problem *P, const double *g, double *row);
 void orc_site_weights(const orc_problem *P, size_t idx, double *w, double *cs2);
 
 /* Two-level refinement (Sec. 4), lbrefine.c.  Opaque handle. */
-void *orc_ref_create(const orc_problem *coarse, int x0, int y0, int nxp, int nyp);
+/* rule 0: viscosity-continuous fine rates and non-equilibrium factors (reading R6);
+ * rule 1: the paper's printed factors 1/2 and 2 with the coarse rates on both grids.
+ * Both coincide at tau = 1/2 (MRT: s = 2 for every relaxed moment). */
+void *orc_ref_create(const orc_problem *coarse, int x0, int y0, int nxp, int nyp, int rule);
 void orc_ref_destroy(void *h);
 int orc_ref_dims(void *h, int *nxf, int *nyf);
 int orc_ref_fine_cmap(void *h, float *cf);

@@ -48,9 +48,41 @@ typedef struct {
     float *cf;
     double *gc, *gf, *tc, *tf, *Uprev, *Unext;
     int *Ix, *Iy, *idxI;
-    double Minv[81];
+    double M[81], Minv[81];
+    /* non-equilibrium factors per moment (MRT) or for all populations (BGK, entry 0):
+     * coarse -> fine and fine -> coarse */
+    double fc2f[9], ff2c[9];
     long t;
 } ref_t;
+
+/* Relaxation time of a rate and its fine-grid counterpart.  With dx and dt halved, the
+ * physical viscosity c_s^2 (tau - 1/2) dx^2 / dt is the same on both grids when
+ * tau_f - 1/2 = n (tau_c - 1/2) (reading R6); the non-equilibrium parts then scale
+ * as g_neq_f = tau_f / (n tau_c) g_neq_c (Chapman-Enskog: g_neq ~ tau dt times
+ * gradients that are n times smaller per fine cell).  At tau = 1/2 (s = 2, the
+ * paper's lossless setting) this is the paper's factor 1/n, and tau_f = tau_c. */
+static double fine_tau(double tau_c) { return 0.5 + 2.0 * (tau_c - 0.5); }
+
+/* n_k(g - geq): the non-equilibrium part rescaled by fac (per moment for MRT) */
+static void rescale_neq(const ref_t *R, const double *fac, const double *g, const double *geq,
+                        double *out) {
+    const int Q = R->C.Q;
+    if (!R->C.mrt) {
+        for (int i = 0; i < Q; i++) out[i] = geq[i] + fac[0] * (g[i] - geq[i]);
+        return;
+    }
+    double m[9];
+    for (int k = 0; k < Q; k++) {
+        double v = 0;
+        for (int i = 0; i < Q; i++) v += R->M[k * Q + i] * (g[i] - geq[i]);
+        m[k] = fac[k] * v;
+    }
+    for (int i = 0; i < Q; i++) {
+        double v = 0;
+        for (int k = 0; k < Q; k++) v += R->Minv[i * Q + k] * m[k];
+        out[i] = geq[i] + v;
+    }
+}
 
 static const int V5[5][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1}};
 static const int V9[9][2] = {{0, 0},  {1, 0},  {0, 1},   {-1, 0}, {0, -1},
@@ -115,13 +147,14 @@ static void c2f(const ref_t *R, double *gf, const double *Ua, const double *Ub, 
                 jx += cv[i][0] * gh[i];
                 jy += cv[i][1] * gh[i];
             }
-            double w[9], cs2, geq[9];
+            double w[9], cs2, geq[9], gr[9];
             orc_site_weights(&R->F, (size_t)b * R->nxf + a, w, &cs2);
             orc_equilibrium(Q, w, cs2, rho, jx, jy, geq);
+            rescale_neq(R, R->fc2f, gh, geq, gr);
             for (int i = 0; i < Q; i++) {
                 int ua = a - cv[i][0], ub = b - cv[i][1];
                 if (ua >= 0 && ua < R->nxf && ub >= 0 && ub < R->nyf) continue;  /* from fine */
-                gf[(size_t)i * Nf + (size_t)b * R->nxf + a] = geq[i] + (gh[i] - geq[i]) / 2.0;
+                gf[(size_t)i * Nf + (size_t)b * R->nxf + a] = gr[i];
             }
         }
     }
@@ -142,17 +175,17 @@ static void f2c(const ref_t *R, double *gc, const double *gf) {
             jx += cv[i][0] * G[i];
             jy += cv[i][1] * G[i];
         }
-        double w[9], cs2, geq[9];
+        double w[9], cs2, geq[9], gr[9];
         size_t cidx = (size_t)Y * R->C.nx + X;
         orc_site_weights(&R->C, cidx, w, &cs2);
         orc_equilibrium(Q, w, cs2, rho, jx, jy, geq);
+        rescale_neq(R, R->ff2c, G, geq, gr);
         for (int i = 0; i < Q; i++)
-            if (strictly_inside(R, X - cv[i][0], Y - cv[i][1]))
-                gc[(size_t)i * N + cidx] = geq[i] + (G[i] - geq[i]) * 2.0;
+            if (strictly_inside(R, X - cv[i][0], Y - cv[i][1])) gc[(size_t)i * N + cidx] = gr[i];
     }
 }
 
-void *orc_ref_create(const orc_problem *coarse, int x0, int y0, int nxp, int nyp) {
+void *orc_ref_create(const orc_problem *coarse, int x0, int y0, int nxp, int nyp, int rule) {
     if (!coarse || nxp < 1 || nyp < 1 || x0 < 1 || y0 < 1 || x0 + nxp > coarse->nx - 2 ||
         y0 + nyp > coarse->ny - 2)
         return NULL;
@@ -213,7 +246,21 @@ void *orc_ref_create(const orc_problem *coarse, int x0, int y0, int nxp, int nyp
     R->tf = (double *)calloc((size_t)Q * Nf, sizeof(double));
     R->Uprev = (double *)calloc((size_t)Q * R->nI, sizeof(double));
     R->Unext = (double *)calloc((size_t)Q * R->nI, sizeof(double));
+    orc_moment_matrix(Q, R->M);
     orc_moment_inverse(Q, R->Minv);
+    /* rule 0 (R6): viscosity-continuous fine rates and per-moment factors; rule 1: the
+     * paper's printed factors 1/2 and 2 with the coarse rates on both grids (exact for
+     * tau = 1/2 / s = 2, where both rules coincide) */
+    if (rule == 0) {
+        R->F.tau = fine_tau(coarse->tau);
+        for (int k = 0; k < Q; k++) R->F.s[k] = 1.0 / fine_tau(1.0 / coarse->s[k]);
+    }
+    for (int k = 0; k < 9; k++) {
+        double tc = coarse->mrt ? (k < Q ? 1.0 / coarse->s[k] : 1.0) : coarse->tau;
+        double tf = rule == 0 ? fine_tau(tc) : tc;
+        R->fc2f[k] = rule == 0 ? tf / (2.0 * tc) : 0.5;
+        R->ff2c[k] = rule == 0 ? 2.0 * tc / tf : 2.0;
+    }
     return R;
 }
 

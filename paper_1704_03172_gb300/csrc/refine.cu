@@ -19,7 +19,12 @@
 // whose upstream node lies strictly inside the patch,
 //   g^c_i = g^eq_i + 2 (g^f_i - g^eq_i),
 // g^eq being formed from the transferred vector's moments with the receiving
-// grid's weights.  The coarse grid keeps running under the patch, which gives
+// grid's weights.  The factors 1/2 and 2 are those of the paper's lossless
+// setting (tau = 1/2, s = 2).  For other rates the fine grid relaxes with
+// tau_f - 1/2 = 2 (tau_c - 1/2) per relaxed moment, which keeps the physical
+// viscosity continuous, and the non-equilibrium parts scale by tau_f / (2 tau_c)
+// (coarse -> fine) and 2 tau_c / tau_f (fine -> coarse), moment by moment;
+// at tau = 1/2 these are the paper's factors.  The coarse grid keeps running under the patch, which gives
 // the full coarse vector on I (U, kept for two coarse times).
 //
 // One coarse step T (fused kernels, all on the context stream):
@@ -56,6 +61,10 @@ struct lb_refine {
     int2 *rec_c = nullptr, *rec_f = nullptr;
     int *col_c = nullptr, *col_f = nullptr;
     int nrec_c = 0, nrec_f = 0;
+    // relaxation on the fine grid, and the non-equilibrium rescales written as collisions:
+    // g' = geq + F (g - geq) per non-conserved moment is a collision with rates 1 - F
+    float omega_f = 2.f, s_f[9] = {};
+    float c2f_omega = 0.5f, c2f_s[9] = {}, f2c_omega = -1.f, f2c_s[9] = {};
 };
 
 namespace {
@@ -137,29 +146,10 @@ __global__ void ref_snapshot_kernel(StepArgs ac, const int2 *Ic, int nI, float *
                                            ac.plane);
 }
 
-// equilibrium of a population vector with the weights of eta^2 = e2
-template <int Q>
-__device__ __forceinline__ void equilibrium(const float g[Q], float e2, const StepArgs &a,
-                                            float geq[Q]) {
-    float rho = 0.f, jx = 0.f, jy = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        rho += g[i];
-        jx += Lat<Q>::cx(i) * g[i];
-        jy += Lat<Q>::cy(i) * g[i];
-    }
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const float w = weight_i<Q>(i, e2, a);
-        const float wc = Q == 5 ? (i == 0 ? 0.f : 0.5f) : (i == 0 ? 0.f : (i < 5 ? a.a1 : a.a5));
-        geq[i] = w * rho + wc * (Lat<Q>::cx(i) * jx + Lat<Q>::cy(i) * jy);
-    }
-}
-
 // coarse -> fine: write the entering populations of the fine nodes of I into
 // the fine input buffer (at the upstream ghost node, or in place when raw).
-template <int Q>
-__global__ void ref_c2f_kernel(StepArgs af, const int4 *If, int nIf, const float *Ua,
+template <int Q, bool MRT>
+__global__ void ref_c2f_kernel(StepArgs af, StepArgs rs, const int4 *If, int nIf, const float *Ua,
                                const float *Ub, float alpha, int nxf, int nyf) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nIf) return;
@@ -176,8 +166,11 @@ __global__ void ref_c2f_kernel(StepArgs af, const int4 *If, int nIf, const float
         gh[i] = v;
     }
     const long long node = (long long)(b + 1) * af.pitch + (a + 1);
-    float geq[Q];
-    equilibrium<Q>(gh, af.eta2[node], af, geq);
+    // g^eq (fine weights) + factor (g - g^eq): a collision with the rescale rates rs
+    if (Q == 5)
+        collide5<MRT>(gh, af.eta2[node], rs);
+    else
+        collide9<MRT>(gh, af.eta2[node], rs);
     float *in = static_cast<float *>(const_cast<void *>(af.in));
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -185,13 +178,13 @@ __global__ void ref_c2f_kernel(StepArgs af, const int4 *If, int nIf, const float
         if (ua >= 0 && ua < nxf && ub >= 0 && ub < nyf) continue;  // comes from the fine grid
         const long long pos =
             af.raw ? node : (long long)(ub + 1) * af.pitch + (ua + 1);
-        in[i * af.plane + pos] = geq[i] + (gh[i] - geq[i]) * 0.5f;
+        in[i * af.plane + pos] = gh[i];
     }
 }
 
 // fine -> coarse on I, then collide (+ sponge) and overwrite the coarse output
 template <int Q, bool MRT, bool PERIODIC>
-__global__ void ref_f2c_kernel(StepArgs ac, const float *fin, int fraw, int fpitch,
+__global__ void ref_f2c_kernel(StepArgs ac, StepArgs rs, const float *fin, int fraw, int fpitch,
                                long long fplane, const int2 *Ic, int nI, int x0, int y0, int nxp,
                                int nyp) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -206,13 +199,15 @@ __global__ void ref_f2c_kernel(StepArgs ac, const float *fin, int fraw, int fpit
         G[i] = pull1<Q>(fin, fraw, 0, fa, fb, i, 1 << 30, 1 << 30, fpitch, fplane);
     }
     const float e2 = ac.eta2[(long long)X.y * ac.pitch + X.x];
-    float geq[Q];
-    equilibrium<Q>(G, e2, ac, geq);
+    // g^eq (coarse weights) + factor (G - g^eq): a collision with the rescale rates rs
+    if (Q == 5)
+        collide5<MRT>(G, e2, rs);
+    else
+        collide9<MRT>(G, e2, rs);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int ux = X.x - Lat<Q>::cx(i), uy = X.y - Lat<Q>::cy(i);
-        if (ux > x0 && ux < x0 + nxp && uy > y0 && uy < y0 + nyp)
-            g[i] = geq[i] + (G[i] - geq[i]) * 2.f;
+        if (ux > x0 && ux < x0 + nxp && uy > y0 && uy < y0 + nyp) g[i] = G[i];
     }
     if (Q == 5)
         collide5<MRT>(g, e2, ac);
@@ -249,6 +244,8 @@ StepArgs fine_args(const lb_ctx *ctx) {
     a.eta2 = R->eta2;
     a.mid = nullptr;  // the fine grid reads its own eta^2 plane
     a.mid_tab = nullptr;
+    a.omega = R->omega_f;  // viscosity-continuous fine relaxation
+    for (int k = 0; k < 9; k++) a.s[k] = R->s_f[k];
     a.nx = R->gx;
     a.ny = R->gy;
     a.pitch = R->pitch;
@@ -266,17 +263,31 @@ StepArgs fine_args(const lb_ctx *ctx) {
     return a;
 }
 
+// rates whose collision is the non-equilibrium rescale g^eq + F (g - g^eq)
+StepArgs rescale_args(StepArgs a, float omega, const float *s) {
+    a.omega = omega;
+    for (int k = 0; k < 9; k++) a.s[k] = s[k];
+    return a;
+}
+
+template <int Q, bool MRT>
+void c2f_q(lb_ctx *ctx, const StepArgs &af, const float *Ua, const float *Ub, float alpha) {
+    lb_refine *R = ctx->ref;
+    ref_c2f_kernel<Q, MRT><<<blocks_for(R->nIf), 256, 0, ctx->stream>>>(
+        af, rescale_args(af, R->c2f_omega, R->c2f_s), R->If, R->nIf, Ua, Ub, alpha, R->nxf, R->nyf);
+}
+
 void launch_c2f(lb_ctx *ctx, const float *Ua, const float *Ub, float alpha) {
     lb_refine *R = ctx->ref;
     StepArgs af = fine_args(ctx);
     af.in = R->pop[R->cur];
     af.raw = R->raw ? 1 : 0;
-    if (ctx->Q == 9)
-        ref_c2f_kernel<9><<<blocks_for(R->nIf), 256, 0, ctx->stream>>>(af, R->If, R->nIf, Ua, Ub,
-                                                                       alpha, R->nxf, R->nyf);
-    else
-        ref_c2f_kernel<5><<<blocks_for(R->nIf), 256, 0, ctx->stream>>>(af, R->If, R->nIf, Ua, Ub,
-                                                                       alpha, R->nxf, R->nyf);
+    const bool mrt = ctx->cfg.collision == LB_MRT;
+    if (ctx->Q == 9) {
+        if (mrt) c2f_q<9, true>(ctx, af, Ua, Ub, alpha); else c2f_q<9, false>(ctx, af, Ua, Ub, alpha);
+    } else {
+        if (mrt) c2f_q<5, true>(ctx, af, Ua, Ub, alpha); else c2f_q<5, false>(ctx, af, Ua, Ub, alpha);
+    }
 }
 
 // one fine step (pull from pop[cur], store into pop[cur ^ 1]); receivers at trace row `row`
@@ -317,10 +328,12 @@ void f2c_q(lb_ctx *ctx, const StepArgs &ac, const float *fin, int fraw) {
     long long fplane = (long long)R->gy * R->pitch;
     if (ctx->cfg.boundary == LB_PERIODIC)
         ref_f2c_kernel<Q, MRT, true><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(
-            ac, fin, fraw, R->pitch, fplane, R->Ic, R->nI, R->x0, R->y0, R->nxp, R->nyp);
+            ac, rescale_args(ac, R->f2c_omega, R->f2c_s), fin, fraw, R->pitch, fplane, R->Ic,
+            R->nI, R->x0, R->y0, R->nxp, R->nyp);
     else
         ref_f2c_kernel<Q, MRT, false><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(
-            ac, fin, fraw, R->pitch, fplane, R->Ic, R->nI, R->x0, R->y0, R->nxp, R->nyp);
+            ac, rescale_args(ac, R->f2c_omega, R->f2c_s), fin, fraw, R->pitch, fplane, R->Ic,
+            R->nI, R->x0, R->y0, R->nxp, R->nyp);
 }
 
 void launch_f2c(lb_ctx *ctx, const StepArgs &ac, const float *fin, int fraw) {
@@ -343,6 +356,19 @@ lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev
         return fail(ctx, LB_EINVAL, "patch must lie inside the grid with a 1-node margin");
     lb_refine *R = new lb_refine();
     ctx->ref = R;
+    {  // fine rates and rescale factors (tau_f - 1/2 = 2 (tau_c - 1/2), per relaxed moment)
+        auto fine_tau = [](double tc) { return 0.5 + 2.0 * (tc - 0.5); };
+        const double tc = cfg->tau, tf = fine_tau(tc);
+        R->omega_f = (float)(1.0 / tf);
+        R->c2f_omega = (float)(1.0 - tf / (2.0 * tc));
+        R->f2c_omega = (float)(1.0 - 2.0 * tc / tf);
+        for (int k = 0; k < 9; k++) {
+            const double tck = 1.0 / cfg->s[k], tfk = fine_tau(tck);
+            R->s_f[k] = (float)(1.0 / tfk);
+            R->c2f_s[k] = (float)(1.0 - tfk / (2.0 * tck));
+            R->f2c_s[k] = (float)(1.0 - 2.0 * tck / tfk);
+        }
+    }
     R->x0 = P.x0;
     R->y0 = P.y0;
     R->nxp = P.nx_c;

@@ -29,17 +29,19 @@ def rel(a, b):
 
 
 CASES = [
-    # Q, collision, s, periodic, heterogeneous
-    (5, "bgk", None, False, False),
-    (5, "mrt", [1.3, 0.8, 0.8, 2.0, 2.0], False, True),
-    (5, "mrt", [1.0, 1.0, 1.0, 1.4, 1.7], True, True),
-    (9, "bgk", None, False, False),
-    (9, "mrt", [1.0, 1.0, 1.0, 2.0, 2.0, 2.0, 1.0, 1.0, 2.0], False, True),
+    # Q, collision, tau, s, periodic, heterogeneous
+    (5, "bgk", 0.5, None, False, False),
+    (5, "mrt", 0.5, [1.3, 0.8, 0.8, 2.0, 2.0], False, True),
+    (5, "mrt", 0.5, [1.0, 1.0, 1.0, 1.4, 1.7], True, True),     # s != 2: viscosity-continuous
+    (5, "bgk", 0.8, None, False, True),                         # tau != 1/2: fine tau = 1.1
+    (9, "bgk", 0.5, None, False, False),
+    (9, "bgk", 0.7, None, True, True),
+    (9, "mrt", 0.5, [1.0, 1.0, 1.0, 2.0, 2.0, 2.0, 1.0, 1.0, 2.0], False, True),
 ]
 
 
-@pytest.mark.parametrize("Q,coll,s,periodic,hetero", CASES)
-def test_refined_matches_oracle(sim_cls, oracle_mod, Q, coll, s, periodic, hetero):
+@pytest.mark.parametrize("Q,coll,tau,s,periodic,hetero", CASES)
+def test_refined_matches_oracle(sim_cls, oracle_mod, Q, coll, tau, s, periodic, hetero):
     nx, ny, steps = 96, 80, 90
     c = W.random_medium(nx, ny, 21, 0.6, 1.0) if hetero else W.uniform_map(nx, ny, 1.0)
     patch = (40, 22, 30, 36)
@@ -47,7 +49,7 @@ def test_refined_matches_oracle(sim_cls, oracle_mod, Q, coll, s, periodic, heter
     rec = np.array([[20, 40], [40, 40], [52, 41], [70, 58], [69, 30], [85, 40], [55, 22]],
                    np.int32)                     # outside / on I / inside / corner
     w_ref = (0.4, 0.11, 0.04)
-    kw = dict(tau=0.5 if coll == "bgk" else 0.5, s=s, w_ref=w_ref, c_ref=1.0)
+    kw = dict(tau=tau, s=s, w_ref=w_ref, c_ref=1.0)
     sponge = 0 if periodic else 8
     sim = sim_cls(c, lattice=Q, collision=coll, boundary="periodic" if periodic else "zero",
                   sponge_width=sponge, sponge_sigma_max=0.1, patch=patch, **kw)
