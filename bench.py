@@ -246,6 +246,29 @@ def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32"):
                         f"checkpoint every {every}, 512 receivers, wall time of lb_adjoint"}
 
 
+def _d3q7_variant(torch, LBSim, storage, n=256, steps=300, warmup=10):
+    """The 3-D (D3Q7) step on a two-layer n^3 medium (contrast 1:2 at mid-depth along z),
+    BGK tau = 1/2, 16-cell sponge, Ricker source, 64 receivers on a line."""
+    c = np.ones((n, n, n), np.float32)
+    c[n // 2:] = 2.0
+    sim = LBSim(c, lattice=7, tau=0.5, storage=storage, c_ref=2.0, sponge_width=16)
+    try:
+        fc = 0.5 / math.sqrt(3.0) / (n / 30.0)
+        sim.set_source(n // 2, n // 2, n // 4, W.ricker(steps + warmup, fc))
+        rec = np.stack([np.arange(16, n - 16, (n - 32) // 64)[:64], np.full(64, n // 2),
+                        np.full(64, n // 4)], 1)
+        sim.set_receivers(rec, steps + warmup)
+        sim.init_pressure(None)
+        indexed = _indexed(sim)
+        sec = _time_steps(torch, sim, steps, warmup)
+    finally:
+        sim.close()
+    glups = n ** 3 * steps / sec / 1e9
+    bps = 2 * 7 * ELEM_BYTES[storage] + (1 if indexed else 4)
+    return {"glups": round(glups, 2), "bytes_per_site": bps, "achieved_gbs": round(glups * bps, 1),
+            "ms_per_step": round(sec / steps * 1e3, 4), "grid": f"{n}^3"}
+
+
 def _dispersion_variant(n=128, steps=256):
     """Fig. 3 / Fig. 4 style: phase speed / c_s of the acoustic branch, measured on the GPU
     (single-mode runs batched in one periodic grid, FP64 projections, matrix pencil fit),
@@ -487,6 +510,8 @@ def run_ours(args):
             out = _refined_variant(torch, LBSim, args.steps, args.warmup)
         elif name == "dispersion":
             out = _dispersion_variant()
+        elif name.startswith("d3q7"):
+            out = _d3q7_variant(torch, LBSim, name.rsplit("_", 1)[1])
         elif name == "served":
             out = _served(args.served_requests, args.served_calibration)
         else:
@@ -594,6 +619,11 @@ def run_ours(args):
                 v[f"adjoint_4096_d2q5_{st}"] = _adjoint_variant(torch, LBSim, storage=st)
             except Exception as ex:
                 v[f"adjoint_4096_d2q5_{st}"] = {"error": str(ex)[:200]}
+        for st in ("f32", "bf16"):
+            try:
+                v[f"d3q7_bgk_{st}_256"] = _d3q7_variant(torch, LBSim, st)
+            except Exception as ex:
+                v[f"d3q7_bgk_{st}_256"] = {"error": str(ex)[:200]}
         try:
             v["dispersion_bgk_tau0.5"] = _dispersion_variant()
         except Exception as ex:

@@ -49,7 +49,9 @@ typedef enum {
     LB_ESTATE = -6      /* call not valid in the context's current state */
 } lb_status;
 
-enum { LB_D2Q5 = 5, LB_D2Q9 = 9 };                 /* lattice (Table I) */
+enum { LB_D2Q5 = 5, LB_D2Q9 = 9, LB_D3Q7 = 7 };   /* lattice (Table I; D3Q7: the 3-D
+                                                      extension of D2Q5, w_0 = 1 - eta^2,
+                                                      w_1..6 = eta^2 / 6, c_s^2 = eta^2 / 3) */
 enum { LB_BGK = 0, LB_MRT = 1 };                   /* collision operator */
 enum { LB_F32 = 0, LB_BF16 = 1, LB_F16 = 2 };      /* population storage in HBM */
 enum { LB_ZERO_GHOST = 0, LB_PERIODIC = 1 };       /* outer boundary */
@@ -93,6 +95,9 @@ typedef struct {
                                  storage without a patch, the register-streaming step otherwise;
                                  LB_STEP_DIRECT (1): always the register-streaming step.  Both
                                  give bit-identical results. */
+    int nz;                   /* planes of a 3-D grid (LB_D3Q7 only, BGK, no patch, no time
+                                 blocking); <= 1: 2-D.  3-D arrays are [nz][ny][nx] (c_map,
+                                 pressure) and [Q][nz][ny][nx] (state). */
 } lb_config;
 
 enum { LB_STEP_AUTO = 0, LB_STEP_DIRECT = 1 };
@@ -114,6 +119,12 @@ lb_status lb_destroy(lb_ctx *ctx);
  * nothing.  The populations receive w_i(x, y) S[t] (Eq. MRT-LB linear
  * acoustic).  nt = 0 removes the source.  Host pointer, FP64 samples. */
 lb_status lb_set_source(lb_ctx *ctx, int x, int y, const double *wavelet, int nt);
+
+/* 3-D grids (nz > 1): the source at node (x, y, z) and receivers at xyz[r] =
+ * (x, y, z), otherwise as lb_set_source / lb_set_receivers (which a 3-D context
+ * refuses with LB_EINVAL).  Host pointers. */
+lb_status lb_set_source_3d(lb_ctx *ctx, int x, int y, int z, const double *wavelet, int nt);
+lb_status lb_set_receivers_3d(lb_ctx *ctx, const int *xyz, int nrec, int nt_capacity);
 
 /* Receivers at nodes xy[r] = (x, y).  Row n of the trace is the pressure
  * p = c_s^2 rho (Eq. state) at time t0 + n, where t0 is the context time when

@@ -19,7 +19,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["lbref.c", "lbrefine.c", "lbadjoint.c"]
+_SOURCES = ["lbref.c", "lbrefine.c", "lbadjoint.c", "lbref3d.c"]
 _SO = os.path.join(_HERE, "liblbref.so")
 _lock = threading.Lock()
 _lib = None
@@ -339,3 +339,98 @@ def sponge_sigma(x, y, nx, ny, W, smax):
 
 def max_threads() -> int:
     return lib().orc_max_threads()
+
+
+# --- three dimensions (D3Q7, lbref3d.c) ------------------------------------------------
+
+class _Problem3(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("periodic", ctypes.c_int), ("tau", ctypes.c_double),
+        ("c_map", ctypes.POINTER(ctypes.c_float)), ("c_ref", ctypes.c_double),
+        ("sponge_width", ctypes.c_int), ("sponge_sigma_max", ctypes.c_double),
+        ("src_x", ctypes.c_int), ("src_y", ctypes.c_int), ("src_z", ctypes.c_int),
+        ("src", ctypes.POINTER(ctypes.c_double)), ("nt_src", ctypes.c_int),
+        ("rec_xyz", ctypes.POINTER(ctypes.c_int)), ("nrec", ctypes.c_int),
+        ("nthreads", ctypes.c_int),
+    ]
+
+
+def _declare3(L):
+    pp = ctypes.POINTER(_Problem3)
+    L.orc3_init_pressure.argtypes = [pp, _dp, _dp]
+    L.orc3_pressure.argtypes = [pp, _dp, _dp]
+    L.orc3_run.argtypes = [pp, _dp, ctypes.c_int, ctypes.c_int, _dp]
+    for n in ("orc3_init_pressure", "orc3_pressure", "orc3_run"):
+        getattr(L, n).restype = ctypes.c_int
+
+
+class Problem3:
+    """A D3Q7 BGK problem: c_map [nz, ny, nx] float32; source (x, y, z, wavelet) or None;
+    receivers [nrec, 3] int (x, y, z)."""
+
+    def __init__(self, nx, ny, nz, c_map, c_ref=None, periodic=False, tau=0.5, sponge_width=0,
+                 sponge_sigma_max=0.0, source=None, receivers=None, nthreads=0):
+        self.Q, self.nx, self.ny, self.nz = 7, int(nx), int(ny), int(nz)
+        self.c_map = np.ascontiguousarray(c_map, dtype=np.float32).reshape(nz, ny, nx)
+        self.c_ref = float(c_ref if c_ref is not None else self.c_map.max())
+        self.periodic, self.tau = bool(periodic), float(tau)
+        self.sponge_width, self.sponge_sigma_max = int(sponge_width), float(sponge_sigma_max)
+        self.source = None
+        if source is not None:
+            sx, sy, sz, wav = source
+            self.source = (int(sx), int(sy), int(sz), np.ascontiguousarray(wav, dtype=np.float64))
+        self.receivers = (np.ascontiguousarray(receivers, dtype=np.int32).reshape(-1, 3)
+                          if receivers is not None else np.zeros((0, 3), np.int32))
+        self.nthreads = int(nthreads)
+
+    def _struct(self):
+        L = lib()
+        if not hasattr(L, "_d3"):
+            _declare3(L)
+            L._d3 = True
+        P = _Problem3()
+        P.nx, P.ny, P.nz = self.nx, self.ny, self.nz
+        P.periodic, P.tau = int(self.periodic), self.tau
+        P.c_map = _ptr(self.c_map, ctypes.c_float)
+        P.c_ref = self.c_ref
+        P.sponge_width, P.sponge_sigma_max = self.sponge_width, self.sponge_sigma_max
+        if self.source is not None:
+            P.src_x, P.src_y, P.src_z = self.source[:3]
+            P.src = _ptr(self.source[3], ctypes.c_double)
+            P.nt_src = len(self.source[3])
+        P.rec_xyz = _ptr(self.receivers, ctypes.c_int)
+        P.nrec = len(self.receivers)
+        P.nthreads = self.nthreads
+        return P
+
+    def zeros(self):
+        return np.zeros((7, self.nz, self.ny, self.nx), dtype=np.float64)
+
+
+def init_pressure3(P: Problem3, p0=None) -> np.ndarray:
+    g = P.zeros()
+    S = P._struct()
+    p = None if p0 is None else np.ascontiguousarray(p0, np.float64).reshape(P.nz, P.ny, P.nx)
+    assert lib().orc3_init_pressure(ctypes.byref(S), _ptr(p, ctypes.c_double) if p is not None
+                                    else None, _ptr(g, ctypes.c_double)) == 0
+    return g
+
+
+def pressure3(P: Problem3, g) -> np.ndarray:
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    p = np.zeros((P.nz, P.ny, P.nx))
+    S = P._struct()
+    assert lib().orc3_pressure(ctypes.byref(S), _ptr(g, ctypes.c_double),
+                               _ptr(p, ctypes.c_double)) == 0
+    return p
+
+
+def run3(P: Problem3, g, nsteps: int, t0: int = 0):
+    """Advance a D3Q7 state by nsteps; returns (g, trace[nsteps, nrec])."""
+    g = np.ascontiguousarray(g, dtype=np.float64).copy()
+    trace = np.zeros((nsteps, len(P.receivers)))
+    S = P._struct()
+    assert lib().orc3_run(ctypes.byref(S), _ptr(g, ctypes.c_double), int(t0), int(nsteps),
+                          _ptr(trace, ctypes.c_double)) == 0
+    return g, trace

@@ -73,4 +73,25 @@ int orc_ref_states(void *h, double *gc, double *gf);
 int orc_adjoint(const orc_problem *P, const double *g0, int nt, const double *resid,
                 double *grad_c, double *grad_src, double *grad_g0);
 
+/* Three-dimensional D3Q7 BGK (lbref3d.c): arrays [nz][ny][nx], populations [7][nz][ny][nx]. */
+typedef struct {
+    int nx, ny, nz;
+    int periodic;
+    double tau;
+    const float *c_map;    /* [nz][ny][nx] */
+    double c_ref;
+    int sponge_width;
+    double sponge_sigma_max;
+    int src_x, src_y, src_z;
+    const double *src;
+    int nt_src;
+    const int *rec_xyz;    /* [nrec][3] */
+    int nrec;
+    int nthreads;
+} orc3_problem;
+
+int orc3_init_pressure(const orc3_problem *P, const double *p0, double *g);
+int orc3_pressure(const orc3_problem *P, const double *g, double *p);
+int orc3_run(const orc3_problem *P, double *g, int t0, int nsteps, double *trace);
+
 #endif

@@ -291,6 +291,7 @@ bool ckpt_reserve(lb_ctx *ctx, void **dst, const void **src, size_t *bytes) {
 
 extern "C" lb_status lb_checkpoint_every(lb_ctx *ctx, int every) {
     if (!ctx) return LB_EINVAL;
+    if (every > 0 && ctx->Q == 7) return fail(ctx, LB_ESTATE, "the adjoint is 2-D (D2Q5 / D2Q9)");
     if (every < 0) return fail(ctx, LB_EINVAL, "every < 0");
     if (every > 0 && (ctx->refined || (ctx->cfg.storage != LB_F32 && ctx->cfg.storage != LB_BF16)))
         return fail(ctx, LB_ESTATE, "the adjoint needs an FP32 or BF16 context without a patch");

@@ -232,6 +232,7 @@ extern "C" lb_status lb_invariants_noalloc(const float *g, const float *c_map, i
 using namespace lbrt;
 
 extern "C" lb_status lb_invariants(lb_ctx *ctx, double *out) {
+    if (ctx && ctx->Q == 7) return fail(ctx, LB_ESTATE, "invariants are 2-D (D2Q5 / D2Q9)");
     if (!ctx) return LB_EINVAL;
     if (!out) return fail(ctx, LB_EINVAL, "out is NULL");
     if (!ctx->inv_scratch) {

@@ -38,6 +38,7 @@ template <int Q> struct Lat;
 template <> struct Lat<5> {
     __host__ __device__ static constexpr int cx(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
     __host__ __device__ static constexpr int cy(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
 };
 template <> struct Lat<9> {
     __host__ __device__ static constexpr int cx(int i) {
@@ -46,6 +47,13 @@ template <> struct Lat<9> {
     __host__ __device__ static constexpr int cy(int i) {
         return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
     }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+};
+// D3Q7, the 3-D extension of D2Q5: c_0 = 0, c_1,3 = +-e_x, c_2,4 = +-e_y, c_5,6 = +-e_z
+template <> struct Lat<7> {
+    __host__ __device__ static constexpr int cx(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
+    __host__ __device__ static constexpr int cy(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
+    __host__ __device__ static constexpr int cz(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
 };
 
 // Arguments of one step launch (passed by value).
@@ -53,6 +61,9 @@ struct StepArgs {
     const void *in;          // h^{t-1}  [Q][ny][pitch]
     void *out;               // h^{t}
     const float *eta2;       // [ny][pitch] (c / c_ref)^2
+    // 3-D grids (D3Q7): ny counts the rows of all z-planes (ny3 rows per plane, nz planes,
+    // row r = z ny3 + y); 2-D grids have ny3 = ny and nz = 1
+    int ny3, nz;
     // Optional medium index (nullptr: read eta2): when the map holds at most 256
     // distinct speeds, mid[y][x] selects eta^2 = mid_tab[mid] (1 byte per site
     // instead of 4); the step kernels stage mid_tab in shared memory.
@@ -355,6 +366,31 @@ __device__ __forceinline__ const ST *src_row(const ST *base, int ys, int ny, int
     return base + (long long)ys * pitch;
 }
 
+// Source row of population i for output row r: the pull's y shift (2-D, row = y) or its
+// y and z shifts (D3Q7, r = z ny3 + y); -1 outside a zero-ghost domain.
+template <int Q, bool PERIODIC>
+__device__ __forceinline__ int pull_row(const StepArgs &a, int r, int i) {
+    if (Q != 7) {
+        int ys = r - Lat<Q>::cy(i);
+        if (ys < 0 || ys >= a.ny) {
+            if (!PERIODIC) return -1;
+            ys = ys < 0 ? ys + a.ny : ys - a.ny;
+        }
+        return ys;
+    }
+    const int y = r % a.ny3, z = r / a.ny3;
+    int ys = y - Lat<Q>::cy(i), zs = z - Lat<Q>::cz(i);
+    if (ys < 0 || ys >= a.ny3) {
+        if (!PERIODIC) return -1;
+        ys = ys < 0 ? ys + a.ny3 : ys - a.ny3;
+    }
+    if (zs < 0 || zs >= a.nz) {
+        if (!PERIODIC) return -1;
+        zs = zs < 0 ? zs + a.nz : zs - a.nz;
+    }
+    return zs * a.ny3 + ys;
+}
+
 // ------------------------------------------------------------- collision --
 // D2Q5: w_0 = 1 - eta^2, w_1..4 = eta^2 / 4, c_s^2 = eta^2 / 2, so
 // g^eq_0 = w_0 rho, g^eq_{1,3} = w_1 rho +- j_x / 2, g^eq_{2,4} = w_1 rho +- j_y / 2.
@@ -434,16 +470,33 @@ __device__ __forceinline__ void collide9(float g[9], float e2, const StepArgs &a
     g[8] -= c5 + d6 - d7 - d8;
 }
 
+// D3Q7 BGK with w_0 = 1 - eta^2, w_1..6 = eta^2 / 6, c_s^2 = eta^2 / 3 (the D2Q5 rule of
+// Eq. 0th lattice weight carried to three dimensions), so w_i / c_s^2 = 1/2 and
+// g^eq_{1,3} = w_1 rho +- j_x / 2, g^eq_{2,4} = w_1 rho +- j_y / 2, g^eq_{5,6} = w_1 rho +- j_z / 2.
+__device__ __forceinline__ void collide7(float g[7], float e2, const StepArgs &a) {
+    const float rho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+    const float jx = g[1] - g[3], jy = g[2] - g[4], jz = g[5] - g[6];
+    const float om = a.omega, eq0 = (1.f - e2) * rho, b = e2 * (1.f / 6.f) * rho;
+    g[0] += om * (eq0 - g[0]);
+    g[1] += om * (b + 0.5f * jx - g[1]);
+    g[2] += om * (b + 0.5f * jy - g[2]);
+    g[3] += om * (b - 0.5f * jx - g[3]);
+    g[4] += om * (b - 0.5f * jy - g[4]);
+    g[5] += om * (b + 0.5f * jz - g[5]);
+    g[6] += om * (b - 0.5f * jz - g[6]);
+}
+
 template <int Q>
 __device__ __forceinline__ float weight_i(int i, float e2, const StepArgs &a) {
     if (Q == 5) return i == 0 ? 1.f - e2 : 0.25f * e2;
+    if (Q == 7) return i == 0 ? 1.f - e2 : e2 * (1.f / 6.f);  // D3Q7: w_0 = 1 - eta^2
     if (i == 0) return 1.f - 4.f * e2 * (a.w1r + a.w5r);
     return i < 5 ? e2 * a.w1r : e2 * a.w5r;
 }
 
 template <int Q>
 __device__ __forceinline__ float cs2_of(float e2, const StepArgs &a) {
-    return Q == 5 ? 0.5f * e2 : e2 * a.c2r;
+    return Q == 5 ? 0.5f * e2 : (Q == 7 ? e2 * (1.f / 3.f) : e2 * a.c2r);
 }
 
 __device__ __forceinline__ float sponge_factor(int x, int y, const StepArgs &a) {
@@ -451,6 +504,17 @@ __device__ __forceinline__ float sponge_factor(int x, int y, const StepArgs &a) 
     if (d >= a.sponge_w) return 1.f;
     float r = (float)(a.sponge_w - d) * a.sponge_inv_w;
     return 1.f - a.sponge_smax * r * r;
+}
+
+// sponge factor at row r (D3Q7: distance to the nearest of the six faces)
+template <int Q>
+__device__ __forceinline__ float sponge_at(int x, int r, const StepArgs &a) {
+    if (Q != 7) return sponge_factor(x, r, a);
+    const int y = r % a.ny3, z = r / a.ny3;
+    const int d = min(min(min(x, a.nx - 1 - x), min(y, a.ny3 - 1 - y)), min(z, a.nz - 1 - z));
+    if (d >= a.sponge_w) return 1.f;
+    const float q = (float)(a.sponge_w - d) * a.sponge_inv_w;
+    return 1.f - a.sponge_smax * q * q;
 }
 
 // --------------------------------------------------------------- receivers --
@@ -462,11 +526,11 @@ __device__ __forceinline__ void gather_receivers(const StepArgs &a, int r) {
     float rho = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        int xs = xy.x - (a.raw ? 0 : Lat<Q>::cx(i)), ys = xy.y - (a.raw ? 0 : Lat<Q>::cy(i));
+        int xs = xy.x - (a.raw ? 0 : Lat<Q>::cx(i));
+        const int ys = a.raw ? xy.y : pull_row<Q, PERIODIC>(a, xy.y, i);  // xy.y: row
         if (PERIODIC) {
             xs = (xs + a.nx) % a.nx;
-            ys = (ys + a.ny) % a.ny;
-        } else if (xs < 0 || xs >= a.nx || ys < 0 || ys >= a.ny) {
+        } else if (xs < 0 || xs >= a.nx || ys < 0) {
             continue;
         }
         rho += Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch + xs) *
@@ -504,15 +568,17 @@ __device__ __forceinline__ void collide_sites(float (&g)[Q][V], const float (&e2
         for (int i = 0; i < Q; i++) gs[i] = g[i][k];
         if (Q == 5)
             collide5<MRT>(gs, e2s[k], a);
-        else
+        else if (Q == 9)
             collide9<MRT>(gs, e2s[k], a);
+        else
+            collide7(gs, e2s[k], a);
         if (has_src && a.src_x == x0 + k) {
             const float S = a.src_tab[a.t];
 #pragma unroll
             for (int i = 0; i < Q; i++) gs[i] += weight_i<Q>(i, e2s[k], a) * S;
         }
         if (EDGE) {
-            const float f = a.sponge_w > 0 ? sponge_factor(x0 + k, y, a) : 1.f;
+            const float f = a.sponge_w > 0 ? sponge_at<Q>(x0 + k, y, a) : 1.f;
             const bool real = x0 + k < a.nx;
 #pragma unroll
             for (int i = 0; i < Q; i++) g[i][k] = real ? gs[i] * f : 0.f;
@@ -556,9 +622,16 @@ __device__ __forceinline__ void finish_sites(const StepArgs &a, float (&g)[Q][St
                 make_float4(r[0], r[1], r[2], r[3]);
         }
     }
-    const bool edge = a.sponge_w > 0 &&
-                      (y < a.sponge_w || y >= a.ny - a.sponge_w || x0 < a.sponge_w ||
-                       x0 + V - 1 >= a.nx - a.sponge_w);
+    bool edge;
+    if (Q == 7) {  // row y = z ny3 + y3
+        const int y3 = y % a.ny3, z = y / a.ny3;
+        edge = a.sponge_w > 0 && (y3 < a.sponge_w || y3 >= a.ny3 - a.sponge_w || z < a.sponge_w ||
+                                  z >= a.nz - a.sponge_w || x0 < a.sponge_w ||
+                                  x0 + V - 1 >= a.nx - a.sponge_w);
+    } else {
+        edge = a.sponge_w > 0 && (y < a.sponge_w || y >= a.ny - a.sponge_w || x0 < a.sponge_w ||
+                                  x0 + V - 1 >= a.nx - a.sponge_w);
+    }
     const bool has_src = (y == a.src_y) && (a.src_x >= x0) && (a.src_x < x0 + V) &&
                          a.src_tab != nullptr && a.t < a.src_nt;
     // collide site by site, in place: g[i][k] becomes the stored output.  Threads whose
@@ -607,8 +680,8 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int cx = a.raw ? 0 : Lat<Q>::cx(i);  // raw: read g(t) in place (warp-uniform)
-        const ST *row = a.raw ? in + i * a.plane + (long long)y * a.pitch
-                              : src_row<PERIODIC>(in + i * a.plane, y - Lat<Q>::cy(i), a.ny, a.pitch);
+        const int rs = a.raw ? y : pull_row<Q, PERIODIC>(a, y, i);
+        const ST *row = rs < 0 ? nullptr : in + i * a.plane + (long long)rs * a.pitch;
         absent[i] = row == nullptr;
         if (cx == 1)
             pull_issue<1, PERIODIC>(row, x0, lane, a.nx, active, q[i], e[i]);
@@ -658,8 +731,9 @@ template <int Q, bool MRT, bool PERIODIC, typename ST>
 // flight per SM (FP32 D2Q5 fits 5 blocks at <= 48 registers; the 8-site 16-bit
 // and the 9-population FP32 forms are held to 64 registers for 4 blocks; the
 // 9-population 16-bit form holds 72 values per thread and gets 80 registers).
-__global__ void __launch_bounds__(kThreads, Q == 5 ? (sizeof(ST) == 4 ? 5 : 4)
-                                                     : (sizeof(ST) == 4 ? 4 : 2))
+__global__ void __launch_bounds__(kThreads, Q == 5   ? (sizeof(ST) == 4 ? 5 : 4)
+                                           : Q == 7 ? (sizeof(ST) == 4 ? 4 : 3)
+                                                    : (sizeof(ST) == 4 ? 4 : 2))
     step_kernel(const StepArgs a) {
     constexpr bool SC = Scaled<ST>::value;
     __shared__ float s_wmax[SC ? 9 : 1][kWarps];
@@ -781,14 +855,14 @@ __global__ void get_state_kernel(StepArgs a, float *dst, int mode) {
     const ST *in = static_cast<const ST *>(a.in);
     float rho = 0.f;
     for (int i = 0; i < Q; i++) {
-        int xs = x - (a.raw ? 0 : Lat<Q>::cx(i)), ys = y - (a.raw ? 0 : Lat<Q>::cy(i));
+        int xs = x - (a.raw ? 0 : Lat<Q>::cx(i));
+        const int ys = a.raw ? y : pull_row<Q, PERIODIC>(a, y, i);  // y: row (z ny3 + y in 3-D)
         float v = 0.f;
         bool ok = true;
         if (PERIODIC) {
             xs = (xs + a.nx) % a.nx;
-            ys = (ys + a.ny) % a.ny;
         } else {
-            ok = xs >= 0 && xs < a.nx && ys >= 0 && ys < a.ny;
+            ok = xs >= 0 && xs < a.nx && ys >= 0;
         }
         if (ok)
             v = Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch + xs) *

@@ -15,6 +15,7 @@ struct lb_refine;  // two-level grid refinement state (refine.cu)
 struct lb_ctx {
     lb_config cfg;                  // copy; pointer members cleared
     int Q = 5, nx = 0, ny = 0, pitch = 0, ebytes = 4;
+    int ny3 = 0, nz = 1;            // 3-D (D3Q7): ny = ny3 * nz rows, row r = z ny3 + y
     void *pop[2] = {nullptr, nullptr};
     int cur = 0;                    // pop[cur] holds the post-collision state of step t-1
     bool raw = false;               // ... or, when raw, the state g(t) itself (unshifted)

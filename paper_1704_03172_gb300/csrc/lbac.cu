@@ -124,6 +124,8 @@ StepArgs base_args(const lb_ctx *c) {
     a.eta2 = c->eta2;
     a.mid = c->mid;
     a.mid_tab = c->mid_tab;
+    a.ny3 = c->ny3;
+    a.nz = c->nz;
     a.nx = c->nx;
     a.ny = c->ny;
     a.pitch = c->pitch;
@@ -171,6 +173,7 @@ template <int Q, typename ST> StepFn step_fn_c(bool mrt, bool per) {
     return mrt ? step_fn_b<Q, true, ST>(per) : step_fn_b<Q, false, ST>(per);
 }
 template <typename ST> StepFn step_fn_q(int Q, bool mrt, bool per) {
+    if (Q == 7) return step_fn_b<7, false, ST>(per);  // D3Q7: BGK only
     return Q == 9 ? step_fn_c<9, ST>(mrt, per) : step_fn_c<5, ST>(mrt, per);
 }
 
@@ -191,7 +194,7 @@ template <int Q, typename ST> SetFn set_fn_q(bool per) {
     return per ? set_state_kernel<Q, true, ST> : set_state_kernel<Q, false, ST>;
 }
 template <typename ST> SetFn set_fn(int Q, bool per) {
-    return Q == 9 ? set_fn_q<9, ST>(per) : set_fn_q<5, ST>(per);
+    return Q == 9 ? set_fn_q<9, ST>(per) : Q == 7 ? set_fn_q<7, ST>(per) : set_fn_q<5, ST>(per);
 }
 SetFn pick_set(const lb_ctx *c) {
     bool per = c->cfg.boundary == LB_PERIODIC;
@@ -205,7 +208,7 @@ template <int Q, typename ST> GetFn get_fn_q(bool per) {
     return per ? get_state_kernel<Q, true, ST> : get_state_kernel<Q, false, ST>;
 }
 template <typename ST> GetFn get_fn(int Q, bool per) {
-    return Q == 9 ? get_fn_q<9, ST>(per) : get_fn_q<5, ST>(per);
+    return Q == 9 ? get_fn_q<9, ST>(per) : Q == 7 ? get_fn_q<7, ST>(per) : get_fn_q<5, ST>(per);
 }
 GetFn pick_get_for(int Q, bool per, int storage) {
     switch (storage) {
@@ -227,16 +230,26 @@ lb_status check_launch(lb_ctx *ctx, const char *what) {
 
 lb_status validate(const lb_config *cfg) {
     if (!cfg) return fail(nullptr, LB_EINVAL, "cfg is NULL");
-    if (cfg->lattice != LB_D2Q5 && cfg->lattice != LB_D2Q9)
-        return fail(nullptr, LB_EINVAL, "lattice must be LB_D2Q5 or LB_D2Q9");
+    if (cfg->lattice != LB_D2Q5 && cfg->lattice != LB_D2Q9 && cfg->lattice != LB_D3Q7)
+        return fail(nullptr, LB_EINVAL, "lattice must be LB_D2Q5, LB_D2Q9 or LB_D3Q7");
+    const int nz = std::max(cfg->nz, 1);
+    if (nz > 1 && cfg->lattice != LB_D3Q7)
+        return fail(nullptr, LB_EINVAL, "nz > 1 needs the LB_D3Q7 lattice");
+    if (cfg->lattice == LB_D3Q7) {
+        if (cfg->collision != LB_BGK)
+            return fail(nullptr, LB_EINVAL, "LB_D3Q7 supports BGK collision only");
+        if (cfg->n_patches > 0 || cfg->time_block > 1)
+            return fail(nullptr, LB_EINVAL, "LB_D3Q7: no refinement patch or time blocking");
+    }
     if (cfg->collision != LB_BGK && cfg->collision != LB_MRT)
         return fail(nullptr, LB_EINVAL, "collision must be LB_BGK or LB_MRT");
     if (cfg->storage != LB_F32 && cfg->storage != LB_BF16 && cfg->storage != LB_F16)
         return fail(nullptr, LB_EINVAL, "storage must be LB_F32, LB_BF16 or LB_F16");
     if (cfg->boundary != LB_ZERO_GHOST && cfg->boundary != LB_PERIODIC)
         return fail(nullptr, LB_EINVAL, "boundary must be LB_ZERO_GHOST or LB_PERIODIC");
-    if (cfg->nx < 1 || cfg->ny < 1 || (long long)cfg->nx * cfg->ny > (1LL << 34))
-        return fail(nullptr, LB_EINVAL, "grid %d x %d out of range", cfg->nx, cfg->ny);
+    if (cfg->nx < 1 || cfg->ny < 1 || (long long)cfg->nx * cfg->ny * nz > (1LL << 34) ||
+        (long long)cfg->ny * nz > (1LL << 30))
+        return fail(nullptr, LB_EINVAL, "grid %d x %d x %d out of range", cfg->nx, cfg->ny, nz);
     if (!cfg->c_map) return fail(nullptr, LB_EINVAL, "c_map is NULL");
     if (cfg->collision == LB_BGK && !(cfg->tau >= 0.5 && std::isfinite(cfg->tau)))
         return fail(nullptr, LB_EINVAL, "BGK needs tau >= 1/2 (got %g)", cfg->tau);
@@ -293,8 +306,8 @@ lb_status lb_config_default(lb_config *cfg) {
 lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint, size_t *bytes) {
     if (!cfg || !bytes) return LB_EINVAL;
     size_t pitch = (size_t)round_up(std::max(cfg->nx, 1), 32);
-    size_t plane = pitch * (size_t)std::max(cfg->ny, 1);
-    size_t q = cfg->lattice == LB_D2Q9 ? 9 : 5;
+    size_t plane = pitch * (size_t)std::max(cfg->ny, 1) * (size_t)std::max(cfg->nz, 1);
+    size_t q = cfg->lattice == LB_D2Q9 ? 9 : cfg->lattice == LB_D3Q7 ? 7 : 5;
     // populations (two buffers), eta^2 and, for piecewise-constant media, the medium index
     size_t b = 2 * q * plane * elem_bytes(cfg->storage) + plane * 4 + plane + 1024;
     if (nrec > 0 && nt > 0) b += (size_t)nt * nrec * 4 + (size_t)nrec * 8;
@@ -326,7 +339,9 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     c->cfg.patches = nullptr;
     c->Q = cfg->lattice;
     c->nx = cfg->nx;
-    c->ny = cfg->ny;
+    c->nz = std::max(cfg->nz, 1);
+    c->ny3 = cfg->ny;
+    c->ny = cfg->ny * c->nz;  // rows of all z-planes
     c->pitch = round_up(cfg->nx, 32);
     c->ebytes = elem_bytes(cfg->storage);
     c->alloc_fn = cfg->dev_alloc;
@@ -362,7 +377,8 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     if (!c->eta2 || !flags || !c->fault) return bail(fail(c, LB_ENOMEM, "medium buffer"));
     cudaMemsetAsync(c->fault, 0, 4, c->stream);
     // 16-bit storage: the TMA-staged persistent step (faster there); FP32: register-streaming
-    c->staged = cfg->step_kernel == LB_STEP_AUTO && cfg->n_patches == 0 && cfg->storage != LB_F32;
+    c->staged = cfg->step_kernel == LB_STEP_AUTO && cfg->n_patches == 0 &&
+                cfg->storage != LB_F32 && c->Q != 7;  // the staged step is 2-D
     if (cfg->storage == LB_F16) {  // FP16 range scales (BF16 has FP32's range and needs none)
         c->lp_scale = static_cast<float *>(dev_alloc(c, 3 * 9 * sizeof(float)));
         c->lp_max = static_cast<unsigned *>(dev_alloc(c, (3 * 9 * kMaxCopies + 1) * sizeof(unsigned)));
@@ -443,8 +459,23 @@ lb_status lb_destroy(lb_ctx *ctx) {
     return LB_OK;
 }
 
+static lb_status set_source_row(lb_ctx *ctx, int x, int y, const double *wavelet, int nt);
+
 lb_status lb_set_source(lb_ctx *ctx, int x, int y, const double *wavelet, int nt) {
     if (!ctx) return LB_EINVAL;
+    if (ctx->nz > 1) return fail(ctx, LB_EINVAL, "3-D context: use lb_set_source_3d");
+    return set_source_row(ctx, x, y, wavelet, nt);
+}
+
+lb_status lb_set_source_3d(lb_ctx *ctx, int x, int y, int z, const double *wavelet, int nt) {
+    if (!ctx) return LB_EINVAL;
+    if (nt > 0 && (y < 0 || y >= ctx->ny3 || z < 0 || z >= ctx->nz))
+        return fail(ctx, LB_EINVAL, "source (%d, %d, %d) outside the grid", x, y, z);
+    return set_source_row(ctx, x, z * ctx->ny3 + y, wavelet, nt);
+}
+
+// y: row index (z ny3 + y for 3-D grids)
+static lb_status set_source_row(lb_ctx *ctx, int x, int y, const double *wavelet, int nt) {
     if (nt < 0 || (nt > 0 && !wavelet)) return fail(ctx, LB_EINVAL, "bad wavelet");
     if (nt > 0 && (x < 0 || x >= ctx->nx || y < 0 || y >= ctx->ny))
         return fail(ctx, LB_EINVAL, "source (%d, %d) outside the grid", x, y);
@@ -468,8 +499,30 @@ lb_status lb_set_source(lb_ctx *ctx, int x, int y, const double *wavelet, int nt
     return LB_OK;
 }
 
+static lb_status set_receivers_rows(lb_ctx *ctx, const int *xy, int nrec, int nt_capacity);
+
 lb_status lb_set_receivers(lb_ctx *ctx, const int *xy, int nrec, int nt_capacity) {
     if (!ctx) return LB_EINVAL;
+    if (ctx->nz > 1) return fail(ctx, LB_EINVAL, "3-D context: use lb_set_receivers_3d");
+    return set_receivers_rows(ctx, xy, nrec, nt_capacity);
+}
+
+lb_status lb_set_receivers_3d(lb_ctx *ctx, const int *xyz, int nrec, int nt_capacity) {
+    if (!ctx) return LB_EINVAL;
+    if (nrec < 0 || (nrec > 0 && !xyz)) return fail(ctx, LB_EINVAL, "bad receiver arguments");
+    std::vector<int> xy(2 * (size_t)std::max(nrec, 0));
+    for (int r = 0; r < nrec; r++) {
+        const int x = xyz[3 * r], y = xyz[3 * r + 1], z = xyz[3 * r + 2];
+        if (y < 0 || y >= ctx->ny3 || z < 0 || z >= ctx->nz)
+            return fail(ctx, LB_EINVAL, "receiver %d (%d, %d, %d) outside the grid", r, x, y, z);
+        xy[2 * r] = x;
+        xy[2 * r + 1] = z * ctx->ny3 + y;
+    }
+    return set_receivers_rows(ctx, xy.data(), nrec, nt_capacity);
+}
+
+// xy[r] = (x, row), row = z ny3 + y for 3-D grids
+static lb_status set_receivers_rows(lb_ctx *ctx, const int *xy, int nrec, int nt_capacity) {
     if (nrec < 0 || (nrec > 0 && (!xy || nt_capacity < 0)))
         return fail(ctx, LB_EINVAL, "bad receiver arguments");
     for (int r = 0; r < nrec; r++)
@@ -542,6 +595,8 @@ static lb_status set_state_common(lb_ctx *ctx, const float *src, int on_device, 
         if (dev) {
             if (ctx->Q == 9)
                 source_max_kernel<9><<<1024, 256, 0, ctx->stream>>>(a, dev, mode);
+            else if (ctx->Q == 7)
+                source_max_kernel<7><<<1024, 256, 0, ctx->stream>>>(a, dev, mode);
             else
                 source_max_kernel<5><<<1024, 256, 0, ctx->stream>>>(a, dev, mode);
         }
@@ -747,7 +802,7 @@ lb_status lb_info(const lb_ctx *ctx, double *info, int n_info) {
     v[0] = ctx->Q;
     v[1] = ctx->pitch;
     v[2] = ctx->ebytes;
-    double cs_ref = ctx->Q == 5 ? std::sqrt(0.5)
+    double cs_ref = ctx->Q == 7 ? std::sqrt(1.0 / 3.0) : ctx->Q == 5 ? std::sqrt(0.5)
                                 : std::sqrt(2 * ctx->cfg.w_ref[1] + 4 * ctx->cfg.w_ref[2]);
     v[3] = (ctx->cfg.dx > 0 && ctx->cfg.c_ref > 0) ? ctx->cfg.dx * cs_ref / ctx->cfg.c_ref : 0.0;
     v[4] = ctx->n_mid;

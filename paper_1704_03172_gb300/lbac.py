@@ -19,7 +19,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE = 0, -1, -2, -3, -4, -5, -6
-LB_D2Q5, LB_D2Q9 = 5, 9
+LB_D2Q5, LB_D2Q9, LB_D3Q7 = 5, 9, 7
 LB_BGK, LB_MRT = 0, 1
 LB_F32, LB_BF16, LB_F16 = 0, 1, 2
 LB_STEP_AUTO, LB_STEP_DIRECT = 0, 1
@@ -47,7 +47,7 @@ class lb_config(ctypes.Structure):
         ("patches", ctypes.POINTER(lb_patch)), ("n_patches", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p), ("time_block", ctypes.c_int),
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", ctypes.c_void_p),
-        ("step_kernel", ctypes.c_int),
+        ("step_kernel", ctypes.c_int), ("nz", ctypes.c_int),
     ]
 
 
@@ -84,6 +84,8 @@ _SIGS = {
     "lb_destroy": [_ctx_p],
     "lb_set_source": [_ctx_p, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int],
     "lb_set_receivers": [_ctx_p, _ip, ctypes.c_int, ctypes.c_int],
+    "lb_set_source_3d": [_ctx_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int],
+    "lb_set_receivers_3d": [_ctx_p, _ip, ctypes.c_int, ctypes.c_int],
     "lb_init_pressure": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
     "lb_step": [_ctx_p, ctypes.c_int],
     "lb_record_receivers": [_ctx_p, ctypes.c_void_p, ctypes.c_int, _ip, ctypes.c_int],
@@ -212,6 +214,14 @@ def lb_set_source(ctx, x, y, wavelet_ptr, nt):
 
 def lb_set_receivers(ctx, xy_ptr, nrec, nt_capacity):
     return _check(_lib.lb_set_receivers(ctx, xy_ptr, int(nrec), int(nt_capacity)), ctx)
+
+
+def lb_set_source_3d(ctx, x, y, z, wavelet_ptr, nt):
+    return _check(_lib.lb_set_source_3d(ctx, int(x), int(y), int(z), wavelet_ptr, int(nt)), ctx)
+
+
+def lb_set_receivers_3d(ctx, xyz_ptr, nrec, nt_capacity):
+    return _check(_lib.lb_set_receivers_3d(ctx, xyz_ptr, int(nrec), int(nt_capacity)), ctx)
 
 
 def lb_init_pressure(ctx, p0_ptr, on_device):

@@ -43,13 +43,13 @@ class LBSim:
         cfg.collision = _COLL[collision] if isinstance(collision, str) else int(collision)
         cfg.storage = _STORAGE[storage] if isinstance(storage, str) else int(storage)
         cfg.boundary = _BOUND[boundary] if isinstance(boundary, str) else int(boundary)
-        if torch.is_tensor(c_map):
-            ny, nx = c_map.shape
-        else:
+        if not torch.is_tensor(c_map):
             c_map = np.ascontiguousarray(c_map, dtype=np.float32)
-            ny, nx = c_map.shape
-        self.nx, self.ny, self.Q = int(nx), int(ny), int(lattice)
-        cfg.nx, cfg.ny = self.nx, self.ny
+        # [ny][nx], or [nz][ny][nx] for the 3-D lattice (D3Q7)
+        nz, ny, nx = (1,) + tuple(c_map.shape) if len(c_map.shape) == 2 else tuple(c_map.shape)
+        self.nx, self.ny, self.nz, self.Q = int(nx), int(ny), int(nz), int(lattice)
+        cfg.nx, cfg.ny, cfg.nz = self.nx, self.ny, self.nz
+        self._grid = (self.ny, self.nx) if len(c_map.shape) == 2 else (self.nz, self.ny, self.nx)
         cfg.sponge_width = int(sponge_width)
         cfg.sponge_sigma_max = float(sponge_sigma_max)
         cfg.tau = float(tau)
@@ -102,15 +102,22 @@ class LBSim:
         self.nrec = 0
 
     # -- inputs -----------------------------------------------------------------------
-    def set_source(self, x, y, wavelet):
+    def set_source(self, *args):
+        """set_source(x, y, wavelet), or set_source(x, y, z, wavelet) on a 3-D grid."""
+        *xyz, wavelet = args
         w = np.ascontiguousarray(np.asarray(wavelet, dtype=np.float64))
-        lbac.lb_set_source(self.ctx, x, y, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                           len(w))
+        wp = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if len(xyz) == 3:
+            lbac.lb_set_source_3d(self.ctx, *xyz, wp, len(w))
+        else:
+            lbac.lb_set_source(self.ctx, *xyz, wp, len(w))
 
     def set_receivers(self, xy, nt_capacity):
-        xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
-        lbac.lb_set_receivers(self.ctx, xy.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(xy),
-                              nt_capacity)
+        """Receivers [n][2] = (x, y), or [n][3] = (x, y, z) on a 3-D grid."""
+        d = 3 if len(self._grid) == 3 else 2
+        xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, d))
+        fn = lbac.lb_set_receivers_3d if d == 3 else lbac.lb_set_receivers
+        fn(self.ctx, xy.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(xy), nt_capacity)
         self.nrec = len(xy)
 
     def init_pressure(self, p0=None):
@@ -152,12 +159,12 @@ class LBSim:
         return out[:n, :self.nrec]
 
     def pressure(self):
-        out = self._out((self.ny, self.nx))
+        out = self._out(self._grid)
         lbac.lb_get_pressure(self.ctx, _ptr(out), 1)
         return out
 
     def state(self):
-        out = self._out((self.Q, self.ny, self.nx))
+        out = self._out((self.Q,) + self._grid)
         lbac.lb_get_state(self.ctx, _ptr(out), 1)
         return out
 
