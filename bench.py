@@ -562,7 +562,8 @@ def run_ours(args):
     launches = (args.steps + K - 1) // K
     per_launch_s = sec / launches
     achieved = bps * sites * K / per_launch_s / 1e9   # algorithmic one-step bytes per update
-    staged = K == 1 and args.step_kernel == "auto" and args.storage != "f32"
+    staged = K == 1 and (args.step_kernel == "staged" or
+                         (args.step_kernel == "auto" and args.storage != "f32"))
     st_name = dict(f32='float', bf16='__nv_bfloat16', f16='__half')[args.storage]
     kname = (f"tb_kernel<{args.lattice},false,false,{K}>" if K > 1 else
              f"stream_step_kernel<{args.lattice},false,false,{st_name}>" if staged else
@@ -667,8 +668,9 @@ def main():
     ap.add_argument("--lattice", type=int, choices=[5, 9], default=5,
                     help="main line's lattice (D2Q5 is the paper's recommended scheme)")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")
-    ap.add_argument("--step-kernel", choices=["auto", "direct"], default="auto",
-                    help="auto: TMA-staged persistent step; direct: register-streaming step")
+    ap.add_argument("--step-kernel", choices=["auto", "direct", "staged"], default="auto",
+                    help="auto (TMA-staged for wide 16-bit rows), direct (register-streaming) "
+                         "or staged (TMA-staged persistent)")
     ap.add_argument("--time-block", type=int, default=1,
                     help="steps fused per launch for the main line (temporal blocking)")
     args = ap.parse_args()

@@ -92,15 +92,15 @@ typedef struct {
     void (*dev_free)(void *ptr, void *user);
     void *alloc_user;
     int step_kernel;          /* LB_STEP_AUTO (0): the TMA-staged persistent step for 16-bit
-                                 storage without a patch, the register-streaming step otherwise;
-                                 LB_STEP_DIRECT (1): always the register-streaming step.  Both
-                                 give bit-identical results. */
+                                 storage on rows of >= 1024 sites without a patch, the
+                                 register-streaming step otherwise; LB_STEP_DIRECT (1) / LB_STEP_STAGED
+                                 (2, no patch): always that step.  All give bit-identical results. */
     int nz;                   /* planes of a 3-D grid (LB_D3Q7 only, BGK, no patch, no time
                                  blocking); <= 1: 2-D.  3-D arrays are [nz][ny][nx] (c_map,
                                  pressure) and [Q][nz][ny][nx] (state). */
 } lb_config;
 
-enum { LB_STEP_AUTO = 0, LB_STEP_DIRECT = 1 };
+enum { LB_STEP_AUTO = 0, LB_STEP_DIRECT = 1, LB_STEP_STAGED = 2 };
 
 /* Fill *cfg with defaults: D2Q5, BGK tau = 1/2, F32, zero ghost, no sponge,
  * conventional D2Q9 weights (4/9, 1/9, 1/36), c_ref = max(c_map). */

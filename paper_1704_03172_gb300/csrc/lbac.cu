@@ -276,8 +276,9 @@ lb_status validate(const lb_config *cfg) {
         if (cfg->storage != LB_F32 || cfg->n_patches > 0)
             return fail(nullptr, LB_EINVAL, "time_block needs FP32 storage and no patch");
     }
-    if (cfg->step_kernel != LB_STEP_AUTO && cfg->step_kernel != LB_STEP_DIRECT)
-        return fail(nullptr, LB_EINVAL, "step_kernel must be LB_STEP_AUTO or LB_STEP_DIRECT");
+    if (cfg->step_kernel != LB_STEP_AUTO && cfg->step_kernel != LB_STEP_DIRECT &&
+        cfg->step_kernel != LB_STEP_STAGED)
+        return fail(nullptr, LB_EINVAL, "step_kernel must be LB_STEP_AUTO, _DIRECT or _STAGED");
     return LB_OK;
 }
 
@@ -377,8 +378,12 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     if (!c->eta2 || !flags || !c->fault) return bail(fail(c, LB_ENOMEM, "medium buffer"));
     cudaMemsetAsync(c->fault, 0, 4, c->stream);
     // 16-bit storage: the TMA-staged persistent step (faster there); FP32: register-streaming
-    c->staged = cfg->step_kernel == LB_STEP_AUTO && cfg->n_patches == 0 &&
-                cfg->storage != LB_F32 && c->Q != 7;  // the staged step is 2-D
+    // TMA-staged persistent step: forced, or automatic for 16-bit storage on rows of at least
+    // 1024 sites (a task is one row segment of 2048 16-bit sites: narrower rows idle most
+    // threads, and for FP32 the register-streaming step is faster)
+    c->staged = cfg->n_patches == 0 &&
+                (cfg->step_kernel == LB_STEP_STAGED ||
+                 (cfg->step_kernel == LB_STEP_AUTO && cfg->storage != LB_F32 && cfg->nx >= 1024));
     if (cfg->storage == LB_F16) {  // FP16 range scales (BF16 has FP32's range and needs none)
         c->lp_scale = static_cast<float *>(dev_alloc(c, 3 * 9 * sizeof(float)));
         c->lp_max = static_cast<unsigned *>(dev_alloc(c, (3 * 9 * kMaxCopies + 1) * sizeof(unsigned)));

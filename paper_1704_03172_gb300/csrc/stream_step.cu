@@ -17,9 +17,11 @@
 // multiple of W elements (W * element size = 4096 bytes) and the halo is 16
 // bytes; copies are clipped to [0, pitch) of the row.
 //
-// Used for 16-bit storage, where it beats the register-streaming kernel (GB300,
-// 4096^2: BF16 D2Q5 206 -> 261 GLUPS, FP16 195 -> 214, BF16 D2Q9 82 -> 128); for
-// FP32 the register-streaming kernel is faster (159 vs 135 GLUPS) and stays.
+// Chosen automatically for 16-bit storage on rows of >= 1024 sites, where it beats
+// the register-streaming kernel (GB300, 4096^2: BF16 D2Q5 206 -> 258 GLUPS, FP16
+// 195 -> 214, BF16 D2Q9 82 -> 128).  For FP32 the register-streaming kernel is
+// faster (159 vs 135 GLUPS), and on narrow rows (e.g. a 256^3 D3Q7 grid) most of a
+// task's threads would idle.  Any lattice (D2Q5, D2Q9, D3Q7) can force it.
 //
 // Every wait on an mbarrier is bounded (one second of %globaltimer).  On a
 // timeout the block votes to stop, raises the context's fault flag (read by
@@ -124,12 +126,7 @@ namespace {
 template <int Q, bool PERIODIC>
 __device__ __forceinline__ int source_row(const StepArgs &a, int i, int y) {
     if (a.raw) return y;  // first step after lb_set_state: g(t) is read in place
-    int ys = y - Lat<Q>::cy(i);
-    if (ys < 0 || ys >= a.ny) {
-        if (!PERIODIC) return -1;
-        ys = ys < 0 ? ys + a.ny : ys - a.ny;
-    }
-    return ys;
+    return pull_row<Q, PERIODIC>(a, y, i);  // y (and, for D3Q7, z) shift of the row
 }
 
 // Thread 0: queue the bulk copies of task `task` into `stage`, completing on *bar.
@@ -252,7 +249,9 @@ namespace {
 
 // Resident CTAs per SM the register budget is held to (8 warps each).
 template <int Q, typename ST> constexpr int stream_min_ctas() {
-    return Q == 5 ? (sizeof(ST) == 4 ? 5 : (Scaled<ST>::value ? 3 : 4)) : (sizeof(ST) == 4 ? 3 : 2);
+    return Q == 5   ? (sizeof(ST) == 4 ? 5 : (Scaled<ST>::value ? 3 : 4))
+           : Q == 7 ? (sizeof(ST) == 4 ? 4 : 2)
+                    : (sizeof(ST) == 4 ? 3 : 2);
 }
 
 template <int Q, bool MRT, bool PERIODIC, typename ST>
@@ -375,6 +374,7 @@ template <int Q, bool MRT, typename ST> SInfo info_p(bool per, bool ix) {
 }
 
 template <typename ST> SInfo info_st(int Q, bool mrt, bool per, bool ix) {
+    if (Q == 7) return info_p<7, false, ST>(per, ix);  // D3Q7: BGK only
     if (Q == 9) return mrt ? info_p<9, true, ST>(per, ix) : info_p<9, false, ST>(per, ix);
     return mrt ? info_p<5, true, ST>(per, ix) : info_p<5, false, ST>(per, ix);
 }
@@ -383,9 +383,10 @@ template <typename ST> SInfo info_st(int Q, bool mrt, bool per, bool ix) {
 // once per process (one device).
 const SInfo &stream_info(int Q, bool mrt, bool per, int storage, bool ix) {
     static std::mutex mu;
-    static SInfo cache[2][2][2][3][2];
-    static bool ready[2][2][2][3][2] = {};
-    const int q = Q == 9, m = mrt, p = per, st = storage == LB_BF16 ? 1 : storage == LB_F16 ? 2 : 0;
+    static SInfo cache[3][2][2][3][2];
+    static bool ready[3][2][2][3][2] = {};
+    const int q = Q == 9 ? 1 : Q == 7 ? 2 : 0, m = mrt, p = per;
+    const int st = storage == LB_BF16 ? 1 : storage == LB_F16 ? 2 : 0;
     std::lock_guard<std::mutex> lk(mu);
     if (!ready[q][m][p][st][ix]) {
         cache[q][m][p][st][ix] = st == 1   ? info_st<__nv_bfloat16>(Q, mrt, per, ix)

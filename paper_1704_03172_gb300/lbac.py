@@ -22,7 +22,7 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE = 0,
 LB_D2Q5, LB_D2Q9, LB_D3Q7 = 5, 9, 7
 LB_BGK, LB_MRT = 0, 1
 LB_F32, LB_BF16, LB_F16 = 0, 1, 2
-LB_STEP_AUTO, LB_STEP_DIRECT = 0, 1
+LB_STEP_AUTO, LB_STEP_DIRECT, LB_STEP_STAGED = 0, 1, 2
 LB_ZERO_GHOST, LB_PERIODIC = 0, 1
 STATUS_NAMES = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOMEM", -3: "LB_ECUDA",
                 -4: "LB_EUNSTABLE", -5: "LB_ETIMEOUT", -6: "LB_ESTATE"}

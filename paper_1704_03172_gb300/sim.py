@@ -60,7 +60,8 @@ class LBSim:
             cfg.w_ref[k] = float(w_ref[k])
         cfg.dx = float(dx)
         cfg.time_block = int(time_block)
-        cfg.step_kernel = {"auto": lbac.LB_STEP_AUTO, "direct": lbac.LB_STEP_DIRECT}[step_kernel]
+        cfg.step_kernel = {"auto": lbac.LB_STEP_AUTO, "direct": lbac.LB_STEP_DIRECT,
+                           "staged": lbac.LB_STEP_STAGED}[step_kernel]
         cfg.c_ref = float(c_ref) if c_ref is not None else 0.0
         if torch.is_tensor(c_map) and c_map.is_cuda:
             self._cmap_keep = c_map.to(torch.float32).contiguous()
