@@ -369,22 +369,33 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
     const int segs4 = (ctx->nx + 127) / 128;
     const int adj_blocks = (int)(((long long)ctx->ny * segs4 + kWarps - 1) / kWarps);
     // replay steps t = from .. from + n - 1 starting at state `in`; the state after the
-    // last one goes to `last` (when given); rho(t) goes to tape[t - from] (when given)
+    // last one goes to `last` (when given); rho(t) goes to tape[t - from] (when given).
+    // FP32 contexts replay K steps per launch with the time-blocked kernel wherever a whole
+    // block of K fits (not from a raw state); other steps run one per launch.
+    const int K = ctx->cfg.storage == LB_F32 ? (ctx->Q == 5 ? 8 : ctx->Q == 9 ? 4 : 0) : 0;
+    lb_status rst = LB_OK;
     auto replay = [&](const void *in, bool raw, long long from, int n, void *last, bool record) {
         int x = 0;
-        for (int m = 0; m < n; m++) {
+        for (int m = 0; m < n;) {
+            const bool first_raw = raw && m == 0;
+            const int len = (K > 0 && !first_raw && n - m >= K) ? K : 1;
             StepArgs a = base;
             a.in = in;
-            a.out = (m == n - 1 && last) ? last : X[x];
-            a.raw = (raw && m == 0) ? 1 : 0;
+            a.out = (m + len == n && last) ? last : X[x];
+            a.raw = first_raw ? 1 : 0;
             a.t = from + m;
             a.rho_out = record ? tape + (size_t)m * plane : nullptr;
-            if (ctx->staged)
+            a.rho_stride = (long long)plane;
+            if (len > 1) {
+                if (rst == LB_OK) rst = tb_launch_args(ctx, a, len);
+            } else if (ctx->staged) {
                 stream_launch(ctx, a, 0);  // cannot fail once the forward run has stepped
-            else
+            } else {
                 fwd<<<a.main_blocks, kThreads, 0, ctx->stream>>>(a);
+            }
             in = a.out;
             x ^= 1;
+            m += len;
         }
     };
     int li = 0;  // L[li] holds lambda^{t+1}
@@ -421,7 +432,7 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
             }
         }
     }
-    lb_status st = check_launch(ctx, "adjoint");
+    lb_status st = rst != LB_OK ? rst : check_launch(ctx, "adjoint");
     if (st != LB_OK) return release(st);
     // outputs
     const size_t N = (size_t)ctx->nx * ctx->ny;

@@ -104,8 +104,10 @@ struct StepArgs {
     float *scale_next;        // [9]
     unsigned *max_next;       // [9][kMaxCopies]
     // Adjoint replays only: rho(x, t) of the pulled state g(t), [ny][pitch] FP32
-    // (nullptr otherwise).
+    // (nullptr otherwise); a time-blocked launch writes step j of its K at
+    // rho_out + j rho_stride.
     float *rho_out;
+    long long rho_stride;
 };
 
 constexpr int kMaxCopies = 8;          // spread of the per-block atomicMax targets

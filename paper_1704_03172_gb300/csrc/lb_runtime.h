@@ -97,6 +97,7 @@ bool tb_supported(int Q, int K);
 lb_status stream_launch(lb_ctx *ctx, const lbk::StepArgs &a, int rec_blocks);
 lb_status tb_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
 lb_status tb_launch(lb_ctx *ctx, int K);
+lb_status tb_launch_args(lb_ctx *ctx, const lbk::StepArgs &a, int K);
 
 // grid refinement (refine.cu)
 lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev);

@@ -51,7 +51,8 @@ __device__ __forceinline__ int wrap(int v, int n) {
     return v < 0 ? v + n : v;
 }
 
-template <int Q, bool MRT, bool PERIODIC, int K>
+// REC: also record rho of every level of the own tile (adjoint replays only)
+template <int Q, bool MRT, bool PERIODIC, int K, bool REC>
 __global__ void __launch_bounds__(kTbThreads) tb_kernel(const StepArgs a, const TbArgs tb) {
     constexpr int W = kW, NS = kNS, OUT = W - 2 * K;
     extern __shared__ float smem[];  // two copies of [Q][NS]
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kTbThreads) tb_kernel(const StepArgs a, const 
     // ---- per-thread sites: ring distance (-1: outside the domain), medium, sponge, source
     int ring[kPer];
     float e2[kPer], sf[kPer];
-    unsigned srcmask = 0u;
+    unsigned srcmask = 0u, ownmask = 0u;  // ownmask: sites of this block's output tile
 #pragma unroll
     for (int m = 0; m < kPer; m++) {
         const int s = tid + m * kTbThreads, r = s / W, c = s - r * W;
@@ -103,6 +104,11 @@ __global__ void __launch_bounds__(kTbThreads) tb_kernel(const StepArgs a, const 
         e2[m] = live ? a.eta2[(long long)gy * a.pitch + gx] : 0.f;
         sf[m] = (live && a.sponge_w > 0) ? sponge_factor(gx, gy, a) : 1.f;
         if (live && gx == a.src_x && gy == a.src_y) srcmask |= 1u << m;
+        // own output sites, unwrapped coordinates inside the grid (the last tile row / column
+        // may extend past nx / ny)
+        if (live && r >= K && r < K + OUT && c >= K && c < K + OUT && X0 + c < a.nx &&
+            Y0 + r < a.ny)
+            ownmask |= 1u << m;
         if (!live)
 #pragma unroll
             for (int i = 0; i < Q; i++) bufB[i * NS + s] = 0.f;  // copy A is already 0 there
@@ -139,6 +145,13 @@ __global__ void __launch_bounds__(kTbThreads) tb_kernel(const StepArgs a, const 
             float g[Q];
 #pragma unroll
             for (int i = 0; i < Q; i++) g[i] = src[i * NS + s - Lat<Q>::cy(i) * W - Lat<Q>::cx(i)];
+            if (REC && (ownmask & (1u << m))) {  // adjoint replay: rho of level j
+                const int r = s / W, c = s - r * W;
+                float rho = 0.f;
+#pragma unroll
+                for (int i = 0; i < Q; i++) rho += g[i];
+                a.rho_out[j * a.rho_stride + (long long)(Y0 + r) * a.pitch + X0 + c] = rho;
+            }
             if (Q == 5)
                 collide5<MRT>(g, e2[m], a);
             else
@@ -177,15 +190,16 @@ __global__ void __launch_bounds__(kTbThreads) tb_kernel(const StepArgs a, const 
 
 using TbFn = void (*)(const StepArgs, const TbArgs);
 
-template <int Q, bool MRT, int K> TbFn tb_fn_p(bool per) {
-    return per ? tb_kernel<Q, MRT, true, K> : tb_kernel<Q, MRT, false, K>;
+template <int Q, bool MRT, int K> TbFn tb_fn_p(bool per, bool rec) {
+    if (rec) return per ? tb_kernel<Q, MRT, true, K, true> : tb_kernel<Q, MRT, false, K, true>;
+    return per ? tb_kernel<Q, MRT, true, K, false> : tb_kernel<Q, MRT, false, K, false>;
 }
-template <int K> TbFn tb_fn(int Q, bool mrt, bool per) {
+template <int K> TbFn tb_fn(int Q, bool mrt, bool per, bool rec) {
     if constexpr (K <= 4) {
-        if (Q == 9) return mrt ? tb_fn_p<9, true, K>(per) : tb_fn_p<9, false, K>(per);
+        if (Q == 9) return mrt ? tb_fn_p<9, true, K>(per, rec) : tb_fn_p<9, false, K>(per, rec);
     }
     if (Q == 9) return nullptr;  // not offered: see tb_supported
-    return mrt ? tb_fn_p<5, true, K>(per) : tb_fn_p<5, false, K>(per);
+    return mrt ? tb_fn_p<5, true, K>(per, rec) : tb_fn_p<5, false, K>(per, rec);
 }
 
 int tile_out(int K) { return kW - 2 * K; }
@@ -217,20 +231,38 @@ lb_status tb_set_receivers(lb_ctx *ctx, const int *xy, int nrec) {
     return LB_OK;
 }
 
-// K fused steps from a non-raw FP32 state; traces for times t .. t+K-1 go to
-// consecutive rows, so the caller only uses this while all K rows fit.
-lb_status tb_launch(lb_ctx *ctx, int K) {
+// Launch K fused steps with the caller's arguments (a.in / a.out / a.t / a.trace_row /
+// a.rho_out; a.in must not be raw).  Receivers only when a.trace_row is set and the
+// tile lists exist.
+lb_status tb_launch_args(lb_ctx *ctx, const StepArgs &a, int K) {
     if (!tb_supported(ctx->Q, K)) return fail(ctx, LB_EINVAL, "time_block %d not supported", K);
     const bool mrt = ctx->cfg.collision == LB_MRT, per = ctx->cfg.boundary == LB_PERIODIC;
+    const bool rec = a.rho_out != nullptr;
     TbFn fn = nullptr;
     switch (K) {
-        case 2: fn = tb_fn<2>(ctx->Q, mrt, per); break;
-        case 4: fn = tb_fn<4>(ctx->Q, mrt, per); break;
-        case 6: fn = tb_fn<6>(ctx->Q, mrt, per); break;
-        case 8: fn = tb_fn<8>(ctx->Q, mrt, per); break;
+        case 2: fn = tb_fn<2>(ctx->Q, mrt, per, rec); break;
+        case 4: fn = tb_fn<4>(ctx->Q, mrt, per, rec); break;
+        case 6: fn = tb_fn<6>(ctx->Q, mrt, per, rec); break;
+        case 8: fn = tb_fn<8>(ctx->Q, mrt, per, rec); break;
         default: break;
     }
     if (!fn) return fail(ctx, LB_EINVAL, "time_block %d not supported", K);
+    const int T = tile_out(K);
+    TbArgs tb;
+    tb.tile_off = a.trace_row ? ctx->tb_off : nullptr;
+    tb.tile_rec = a.trace_row ? ctx->tb_rec : nullptr;
+    tb.tiles_x = (ctx->nx + T - 1) / T;
+    dim3 grid(tb.tiles_x, (ctx->ny + T - 1) / T);
+    const size_t smem = 2 * (size_t)ctx->Q * kNS * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "temporal-blocking shared memory");
+    fn<<<grid, kTbThreads, smem, ctx->stream>>>(a, tb);
+    return LB_OK;
+}
+
+// K fused steps of the context from a non-raw FP32 state; traces for times t .. t+K-1 go
+// to consecutive rows, so the caller only uses this while all K rows fit.
+lb_status tb_launch(lb_ctx *ctx, int K) {
     StepArgs a = base_args(ctx);
     a.in = ctx->pop[ctx->cur];
     a.out = ctx->pop[ctx->cur ^ 1];
@@ -239,16 +271,8 @@ lb_status tb_launch(lb_ctx *ctx, int K) {
     long long row = ctx->t - ctx->t_rec0;
     a.trace_row = (ctx->trace && ctx->tb_off && row >= 0 && row + K <= ctx->trace_cap)
                       ? ctx->trace + row * ctx->nrec : nullptr;
-    const int T = tile_out(K);
-    TbArgs tb;
-    tb.tile_off = ctx->tb_off;
-    tb.tile_rec = ctx->tb_rec;
-    tb.tiles_x = (ctx->nx + T - 1) / T;
-    dim3 grid(tb.tiles_x, (ctx->ny + T - 1) / T);
-    const size_t smem = 2 * (size_t)ctx->Q * kNS * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "temporal-blocking shared memory");
-    fn<<<grid, kTbThreads, smem, ctx->stream>>>(a, tb);
+    lb_status st = tb_launch_args(ctx, a, K);
+    if (st != LB_OK) return st;
     ctx->cur ^= 1;
     ctx->t += K;
     return LB_OK;
