@@ -43,7 +43,7 @@ ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 NCU_TRAFFIC = {
     ("lbk::step_kernel<5,false,false,float>", True): 639.9e6,
     ("stream_step_kernel<5,false,false,__nv_bfloat16>", True): 302.2e6,
-    ("tb_kernel<5,false,false,8>", False): 705.5e6,
+    ("tb_kernel<5,false,false,8>", False): 703.5e6,
 }
 
 
@@ -238,8 +238,11 @@ def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32"):
     else:
         bps_fwd = bytes_per_site(5, storage, indexed)
     # per adjoint site-step: `levels` replays (+4 B rho store on the recorded one) and the
-    # adjoint step (lambda pull + store 2*5*4, rho 4, eta^2 4, FP64 gradient RMW 16)
-    bps = round(levels * bps_fwd + 4 + 2 * 5 * 4 + 4 + 4 + 16, 2)
+    # blocked reverse sweep, 8 levels per launch on 32^2 tiles of 48^2 regions: lambda and
+    # eta^2 loads over the region, lambda store and FP64 gradient RMW over the tile once per
+    # 8 levels, and the rho tape read at every level
+    bps_adj = ((48 / 32) ** 2 * (5 * 4 + 4) + 5 * 4 + 16) / 8 + 4
+    bps = round(levels * bps_fwd + 4 + bps_adj, 2)
     upd = n * n * nt
     return {"gradient_glups": round(upd / t_adj / 1e9, 2),
             "forward_with_checkpoints_glups": round(upd / t_fwd / 1e9, 2),

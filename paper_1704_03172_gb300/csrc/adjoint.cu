@@ -34,6 +34,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "lb_kernels.cuh"
@@ -55,6 +57,107 @@ __device__ __forceinline__ float dweight(int i, const StepArgs &a) {
 template <int Q>
 __device__ __forceinline__ float dcs2(const StepArgs &a) {
     return Q == 5 ? 0.5f : a.c2r;
+}
+
+// Source terms of one site's adjoint, from m = sigma(x) mu(x) before adj_site: src_w = w . m
+// (dJ/dS^t at the source) and src_dw = dw/d(eta^2) . m (times S^t: the source's medium
+// gradient).
+template <int Q>
+__device__ __forceinline__ void adj_src(const float (&m)[Q], float e2, const StepArgs &a,
+                                        float &src_w, float &src_dw) {
+    src_w = 0.f;
+    src_dw = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        src_w += weight_i<Q>(i, e2, a) * m[i];
+        src_dw += dweight<Q>(i, a) * m[i];
+    }
+}
+
+// Adjoint of one site's collision.  In: m = sigma(x) mu(x), the pulled adjoint populations
+// times the sponge factor.  Out: m = K^T m = m - (I - E^T) v with v = C^T m, the site's
+// lambda^t before receiver terms; returns gsum = v . dw/d(eta^2) (times rho^t: the medium
+// gradient).  (E^T v)_i = A + c_i . B with A = sum_j w_j v_j, B = sum_j (w_j / c_s^2) c_j v_j.
+template <int Q, bool MRT>
+__device__ __forceinline__ float adj_site(float (&m)[Q], float e2, const StepArgs &a) {
+    if constexpr (Q == 5) {
+        // D2Q5: w_0 = 1 - eta^2, w_i = eta^2 / 4, w_i / c_s^2 = 1/2, dw = (-1, 1/4, 1/4, 1/4, 1/4)
+        const float w0 = 1.f - e2, w1 = 0.25f * e2;
+        const float s14 = m[1] + m[2] + m[3] + m[4];
+        if (!MRT) {
+            // v = omega m: A = omega (w . m), B = omega / 2 (m1 - m3, m2 - m4), and
+            // m - v + E^T v = (1 - omega) m + A + c . B
+            const float om = a.omega, A = om * (w0 * m[0] + w1 * s14);
+            const float hb = 0.5f * om, Bx = hb * (m[1] - m[3]), By = hb * (m[2] - m[4]);
+            const float keep = 1.f - om;
+            const float gsum = om * (0.25f * s14 - m[0]);
+            m[0] = keep * m[0] + A;
+            m[1] = keep * m[1] + (A + Bx);
+            m[2] = keep * m[2] + (A + By);
+            m[3] = keep * m[3] + (A - Bx);
+            m[4] = keep * m[4] + (A - By);
+            return gsum;
+        }
+        // MRT: only e (row 3 of M, norm 20) and p_xx (row 4, norm 4) relax; both are even
+        // in c, so B = 0, and v = (-4 e', e' + p', e' - p', e' + p', e' - p')
+        const float me = (-4.f * m[0] + s14) * a.s[3] * (1.f / 20.f);
+        const float mp = (m[1] - m[2] + m[3] - m[4]) * a.s[4] * 0.25f;
+        const float v13 = me + mp, v24 = me - mp;
+        const float A = 4.f * me * (w1 - w0);  // w0 v0 + w1 (2 v13 + 2 v24)
+        m[0] = m[0] + 4.f * me + A;
+        m[1] = m[1] - v13 + A;
+        m[2] = m[2] - v24 + A;
+        m[3] = m[3] - v13 + A;
+        m[4] = m[4] - v24 + A;
+        return 5.f * me;  // v . dw = 4 e' + e'
+    } else {
+        // D2Q9: w_j and w_j / c_s^2 (eta-independent for j > 0)
+        float w[Q], wc[Q];
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            w[i] = weight_i<Q>(i, e2, a);
+            wc[i] = i == 0 ? 0.f : (i < 5 ? a.a1 : a.a5);
+        }
+        float v[Q];
+        if (!MRT) {
+#pragma unroll
+            for (int i = 0; i < Q; i++) v[i] = a.omega * m[i];
+        } else {
+            const float s14 = m[1] + m[2] + m[3] + m[4], s58 = m[5] + m[6] + m[7] + m[8];
+            const float d3 = a.s[3] * (-4.f * m[0] - s14 + 2.f * s58) * (1.f / 36.f);
+            const float d4 = a.s[4] * (m[1] - m[2] + m[3] - m[4]) * 0.25f;
+            const float d5 = a.s[5] * (4.f * m[0] - 2.f * s14 + s58) * (1.f / 36.f);
+            const float d6 = a.s[6] * (-2.f * m[1] + 2.f * m[3] + m[5] - m[6] - m[7] + m[8]) *
+                             (1.f / 12.f);
+            const float d7 = a.s[7] * (-2.f * m[2] + 2.f * m[4] + m[5] + m[6] - m[7] - m[8]) *
+                             (1.f / 12.f);
+            const float d8 = a.s[8] * (m[5] - m[6] + m[7] - m[8]) * 0.25f;
+            v[0] = -4.f * d3 + 4.f * d5;
+            v[1] = -d3 + d4 - 2.f * d5 - 2.f * d6;
+            v[2] = -d3 - d4 - 2.f * d5 - 2.f * d7;
+            v[3] = -d3 + d4 - 2.f * d5 + 2.f * d6;
+            v[4] = -d3 - d4 - 2.f * d5 + 2.f * d7;
+            const float c5 = 2.f * d3 + d5;
+            v[5] = c5 + d6 + d7 + d8;
+            v[6] = c5 - d6 + d7 - d8;
+            v[7] = c5 - d6 - d7 + d8;
+            v[8] = c5 + d6 - d7 - d8;
+        }
+        float A = 0.f, Bx = 0.f, By = 0.f;
+#pragma unroll
+        for (int j = 0; j < Q; j++) {
+            A += w[j] * v[j];
+            Bx += wc[j] * Lat<Q>::cx(j) * v[j];
+            By += wc[j] * Lat<Q>::cy(j) * v[j];
+        }
+        float gsum = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            gsum += v[i] * dweight<Q>(i, a);
+            m[i] = m[i] - v[i] + (A + Lat<Q>::cx(i) * Bx + Lat<Q>::cy(i) * By);
+        }
+        return gsum;
+    }
 }
 
 struct AdjArgs {
@@ -124,69 +227,15 @@ __global__ void __launch_bounds__(kThreads, Q == 5 ? 4 : 3) adjoint_kernel(const
         float m[Q];
 #pragma unroll
         for (int i = 0; i < Q; i++) m[i] = f * mu[i][k];
-        // w_j and w_j / c_s^2 (eta-independent for j > 0)
-        float w[Q], wc[Q];
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            w[i] = weight_i<Q>(i, e2s[k], a);
-            wc[i] = i == 0 ? 0.f : (Q == 5 ? 0.5f : (i < 5 ? a.a1 : a.a5));
-        }
-        // v = C^T mu (non-conserved part for MRT; all of it for BGK)
-        float v[Q];
-        if (!MRT) {
-#pragma unroll
-            for (int i = 0; i < Q; i++) v[i] = a.omega * m[i];
-        } else if (Q == 5) {
-            // rows 3 (e) and 4 (p_xx) of M, norms 20 and 4
-            const float me = (-4.f * m[0] + m[1] + m[2] + m[3] + m[4]) * a.s[3] * (1.f / 20.f);
-            const float mp = (m[1] - m[2] + m[3] - m[4]) * a.s[4] * 0.25f;
-            v[0] = -4.f * me;
-            v[1] = me + mp;
-            v[2] = me - mp;
-            v[3] = me + mp;
-            v[4] = me - mp;
-        } else {
-            const float s14 = m[1] + m[2] + m[3] + m[4], s58 = m[5] + m[6] + m[7] + m[8];
-            const float d3 = a.s[3] * (-4.f * m[0] - s14 + 2.f * s58) * (1.f / 36.f);
-            const float d4 = a.s[4] * (m[1] - m[2] + m[3] - m[4]) * 0.25f;
-            const float d5 = a.s[5] * (4.f * m[0] - 2.f * s14 + s58) * (1.f / 36.f);
-            const float d6 = a.s[6] * (-2.f * m[1] + 2.f * m[3] + m[5] - m[6] - m[7] + m[8]) *
-                             (1.f / 12.f);
-            const float d7 = a.s[7] * (-2.f * m[2] + 2.f * m[4] + m[5] + m[6] - m[7] - m[8]) *
-                             (1.f / 12.f);
-            const float d8 = a.s[8] * (m[5] - m[6] + m[7] - m[8]) * 0.25f;
-            v[0] = -4.f * d3 + 4.f * d5;
-            v[1] = -d3 + d4 - 2.f * d5 - 2.f * d6;
-            v[2] = -d3 - d4 - 2.f * d5 - 2.f * d7;
-            v[3] = -d3 + d4 - 2.f * d5 + 2.f * d6;
-            v[4] = -d3 - d4 - 2.f * d5 + 2.f * d7;
-            const float c5 = 2.f * d3 + d5;
-            v[5] = c5 + d6 + d7 + d8;
-            v[6] = c5 - d6 + d7 - d8;
-            v[7] = c5 - d6 - d7 + d8;
-            v[8] = c5 + d6 - d7 - d8;
-        }
-        // K^T mu = mu - (I - E^T) v, (E^T v)_i = sum_j w_j v_j + c_i . sum_j (w_j / c_s^2) c_j v_j
-        float A = 0.f, Bx = 0.f, By = 0.f;
-#pragma unroll
-        for (int j = 0; j < Q; j++) {
-            A += w[j] * v[j];
-            Bx += wc[j] * Lat<Q>::cx(j) * v[j];
-            By += wc[j] * Lat<Q>::cy(j) * v[j];
-        }
-        float gsum = 0.f, src_w = 0.f, src_dw = 0.f;
+        float src_w = 0.f, src_dw = 0.f;
+        const bool at_src = has_src && a.src_x == x0 + k;
+        if (at_src) adj_src<Q>(m, e2s[k], a, src_w, src_dw);
+        const float gsum = adj_site<Q, MRT>(m, e2s[k], a);
         const bool real = x0 + k < a.nx;
 #pragma unroll
-        for (int i = 0; i < Q; i++) {
-            const float et = A + Lat<Q>::cx(i) * Bx + Lat<Q>::cy(i) * By;
-            const float dw = dweight<Q>(i, a);
-            gsum += v[i] * dw;
-            src_w += w[i] * m[i];
-            src_dw += dw * m[i];
-            mu[i][k] = real ? m[i] - v[i] + et : 0.f;  // becomes lambda^t
-        }
+        for (int i = 0; i < Q; i++) mu[i][k] = real ? m[i] : 0.f;  // becomes lambda^t
         gadd[k] = (double)rhos[k] * (double)gsum;
-        if (has_src && a.src_x == x0 + k) {
+        if (at_src) {
             if (d.grad_src) d.grad_src[a.t - d.t0] = (double)src_w;
             if (a.t < a.src_nt) gadd[k] += (double)a.src_tab[a.t] * (double)src_dw;
         }
@@ -218,6 +267,197 @@ __global__ void adjoint_receivers(const StepArgs a, const AdjArgs d) {
     atomicAdd(d.grad + idx, (double)R * (double)dcs2<Q>(a) * (double)d.rho[idx]);
 }
 
+// ---- time-blocked reverse sweep: K adjoint levels per launch
+//
+// The transpose of the overlapped tiling of tblock.cu.  A CTA owns an OUT x OUT tile
+// (OUT = 48 - 2K) and loads lambda^{t_hi+1} on the 48 x 48 region made of the tile and a
+// K-site halo; level j (time t = t_hi - j) turns lambda^{t+1} into lambda^t in shared
+// memory for every site whose distance to the region edge exceeds j (its pull from
+// x + c_i is still valid), adds the receiver terms R^t c_s^2 of the receivers inside the
+// region (per-region lists, so that the halo sees them too), and one barrier closes the
+// level.  The own tile's medium and source gradients are summed over the K levels in
+// registers and added to dJ/d(eta^2) once; rho^t comes from the replay tape at
+// rho_hi - j plane.  HBM traffic per site falls from 2Q + 2 FP32 words and an FP64
+// read-modify-write per level to (48 / OUT)^2 Q + Q + 1 words, K tape words and one
+// FP64 read-modify-write per K levels.
+struct AdjTbArgs {
+    const float *rho_hi;   // rho(x, t_hi) on the tape; level j reads rho_hi - j plane
+    long long t_hi;        // time of level 0; the launch covers t_hi .. t_hi - K + 1
+    const int *reg_off;    // [regions + 1] offsets into reg_rec (nullptr: no receivers)
+    const int2 *reg_rec;   // {receiver r, region site} for every receiver position in a region
+    int tiles_x;
+};
+
+template <int Q, bool MRT, bool PERIODIC, int K>
+__global__ void __launch_bounds__(kTbThreads) adjoint_tb_kernel(const StepArgs a, const AdjArgs d,
+                                                                const AdjTbArgs b) {
+    constexpr int W = kTbW, NS = kTbNS, OUT = W - 2 * K, PER = kTbPer;
+    extern __shared__ float smem[];  // two copies of [Q][NS]
+    float *bufA = smem, *bufB = smem + Q * NS;
+    const int X0 = blockIdx.x * OUT - K, Y0 = blockIdx.y * OUT - K;
+    const int tid = threadIdx.x;
+
+    // ---- lambda^{t_hi + 1} on the region into copy A (zero outside a zero-ghost domain)
+    const bool interior = (K % 4 == 0) && (OUT % 4 == 0) && X0 >= 0 && Y0 >= 0 &&
+                          X0 + W <= a.nx && Y0 + W <= a.ny;
+    if (interior) {  // 16-byte loads: X0 = OUT bx - K is a multiple of 4
+        constexpr int CH = W / 4;
+        for (int e = tid; e < Q * W * CH; e += kTbThreads) {
+            const int i = e / (W * CH), rem = e - i * (W * CH), r = rem / CH, c = rem - r * CH;
+            const float4 v = *reinterpret_cast<const float4 *>(
+                d.lam_in + i * a.plane + (long long)(Y0 + r) * a.pitch + X0 + 4 * c);
+            *reinterpret_cast<float4 *>(bufA + i * NS + r * W + 4 * c) = v;
+        }
+    } else {
+        for (int e = tid; e < Q * NS; e += kTbThreads) {
+            const int i = e / NS, s = e - i * NS, r = s / W, c = s - r * W;
+            const int gx = X0 + c, gy = Y0 + r;
+            float v = 0.f;
+            if (PERIODIC)
+                v = d.lam_in[i * a.plane + (long long)wrap_mod(gy, a.ny) * a.pitch + wrap_mod(gx, a.nx)];
+            else if (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny)
+                v = d.lam_in[i * a.plane + (long long)gy * a.pitch + gx];
+            bufA[i * NS + s] = v;
+        }
+    }
+    // ---- per-thread sites: column c = tid mod 48 and rows r0 + 8 m (384 = 8 x 48); ring
+    // distance (-1: outside the domain), medium, sponge, source and own-tile flags
+    static_assert(kTbThreads % W == 0, "a thread's sites share one column");
+    constexpr int RS = kTbThreads / W;  // row step between a thread's sites
+    const int c = tid % W, r0 = tid / W;
+    int ring[PER];
+    float e2[PER], sf[PER];
+    unsigned srcmask = 0u, ownmask = 0u;
+#pragma unroll
+    for (int m = 0; m < PER; m++) {
+        const int s = tid + m * kTbThreads, r = r0 + RS * m;
+        int gx = X0 + c, gy = Y0 + r;
+        bool live = true;
+        if (PERIODIC) {
+            gx = wrap_mod(gx, a.nx);
+            gy = wrap_mod(gy, a.ny);
+        } else {
+            live = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
+        }
+        ring[m] = live ? min(min(r, c), min(W - 1 - r, W - 1 - c)) : -1;
+        e2[m] = live ? a.eta2[(long long)gy * a.pitch + gx] : 0.f;
+        sf[m] = (live && a.sponge_w > 0) ? sponge_factor(gx, gy, a) : 1.f;
+        // own sites: inside the tile and, unwrapped, inside the grid (the last tile row or
+        // column may reach past nx / ny); each grid site is owned by exactly one CTA
+        if (live && r >= K && r < K + OUT && c >= K && c < K + OUT && X0 + c < a.nx &&
+            Y0 + r < a.ny) {
+            ownmask |= 1u << m;
+            if (gx == a.src_x && gy == a.src_y && a.src_tab) srcmask |= 1u << m;
+        }
+        if (!live)
+#pragma unroll
+            for (int i = 0; i < Q; i++) bufB[i * NS + s] = 0.f;  // copy A is already 0 there
+    }
+    // grid index of own site m: own0 + m RS pitch (own sites are unwrapped and in the grid)
+    const long long own0 = (long long)(Y0 + r0) * a.pitch + X0 + c;
+    bool damp = false;
+#pragma unroll
+    for (int m = 0; m < PER; m++) damp |= sf[m] != 1.f;
+    const bool sp_block = __syncthreads_or(damp);
+
+    // The own sites' gradient terms of the K levels are summed in FP32 (the terms are FP32
+    // products of FP32 adjoint quantities) and added to the FP64 gradient once: GB300's
+    // FP64 rate would otherwise bound the sweep.  rho of the next level is loaded while
+    // the current one computes.
+    float acc[PER], rho_n[PER];
+#pragma unroll
+    for (int m = 0; m < PER; m++) {
+        acc[m] = 0.f;
+        rho_n[m] = (ownmask & (1u << m)) ? b.rho_hi[own0 + (long long)(m * RS) * a.pitch] : 0.f;
+    }
+    const int reg = blockIdx.y * b.tiles_x + blockIdx.x;
+    const int q0 = b.reg_off ? b.reg_off[reg] : 0, q1 = b.reg_off ? b.reg_off[reg + 1] : 0;
+#pragma unroll 1
+    for (int j = 0; j < K; j++) {
+        const float *src = (j & 1) ? bufB : bufA;
+        float *dst = (j & 1) ? bufA : bufB;
+        const long long t = b.t_hi - j;
+        const float *rho = b.rho_hi - (long long)j * a.plane;
+        float rho_j[PER];
+#pragma unroll
+        for (int m = 0; m < PER; m++) {
+            rho_j[m] = rho_n[m];
+            if (j + 1 < K && (ownmask & (1u << m)))
+                rho_n[m] = rho[own0 + (long long)(m * RS) * a.pitch - a.plane];
+        }
+        // the sites of one level; SPONGE: the region meets the sponge (block-uniform)
+        auto level = [&](auto sponge) {
+#pragma unroll
+            for (int m = 0; m < PER; m++) {
+                if (ring[m] <= j) continue;
+                const int s = tid + m * kTbThreads;
+                // mu_i(x) = sigma(x) lambda_i^{t+1}(x + c_i)
+                float mm[Q];
+#pragma unroll
+                for (int i = 0; i < Q; i++) {
+                    mm[i] = src[i * NS + s + Lat<Q>::cy(i) * W + Lat<Q>::cx(i)];
+                    if (decltype(sponge)::value) mm[i] *= sf[m];
+                }
+                if (srcmask & (1u << m)) {  // own source site
+                    float src_w, src_dw;
+                    adj_src<Q>(mm, e2[m], a, src_w, src_dw);
+                    if (d.grad_src) d.grad_src[t - d.t0] = (double)src_w;
+                    if (t < a.src_nt) acc[m] += a.src_tab[t] * src_dw;
+                }
+                const float gsum = adj_site<Q, MRT>(mm, e2[m], a);
+#pragma unroll
+                for (int i = 0; i < Q; i++) dst[i * NS + s] = mm[i];
+                if (ownmask & (1u << m)) acc[m] += rho_j[m] * gsum;
+            }
+        };
+        if (sp_block)
+            level(std::true_type{});
+        else
+            level(std::false_type{});
+        if (q1 > q0) {  // block-uniform: receivers inside the region, at time t
+            __syncthreads();
+            for (int q = q0 + tid; q < q1; q += kTbThreads) {
+                const int2 rs = b.reg_rec[q];
+                const int2 xy = a.rec[rs.x];
+                const long long idx = (long long)xy.y * a.pitch + xy.x;
+                const float R = d.resid[(t - d.t0) * d.nrec + rs.x];
+                const float c2 = cs2_of<Q>(a.eta2[idx], a);
+#pragma unroll
+                for (int i = 0; i < Q; i++) atomicAdd(dst + i * NS + rs.y, R * c2);
+                const int r = rs.y / W, c = rs.y - r * W;
+                if (r >= K && r < K + OUT && c >= K && c < K + OUT && X0 + c == xy.x &&
+                    Y0 + r == xy.y)
+                    atomicAdd(d.grad + idx, (double)R * (double)dcs2<Q>(a) * (double)rho[idx]);
+            }
+        }
+        __syncthreads();
+    }
+    // ---- lambda^{t_hi - K + 1} of the own tile, and the summed gradient
+#pragma unroll
+    for (int m = 0; m < PER; m++)
+        if (ownmask & (1u << m)) d.grad[own0 + (long long)(m * RS) * a.pitch] += (double)acc[m];
+    const float *fin = (K % 2 == 0) ? bufA : bufB;
+    const int OX = blockIdx.x * OUT, OY = blockIdx.y * OUT;
+    const bool full = (K % 4 == 0) && (OUT % 4 == 0) && OX + OUT <= a.nx && OY + OUT <= a.ny;
+    if (full) {
+        constexpr int CH = OUT / 4;
+        for (int e = tid; e < Q * OUT * CH; e += kTbThreads) {
+            const int i = e / (OUT * CH), rem = e - i * (OUT * CH), r = rem / CH, c = rem - r * CH;
+            const float4 v = *reinterpret_cast<const float4 *>(fin + i * NS + (r + K) * W + K + 4 * c);
+            *reinterpret_cast<float4 *>(d.lam_out + i * a.plane + (long long)(OY + r) * a.pitch +
+                                        OX + 4 * c) = v;
+        }
+    } else {
+        for (int e = tid; e < Q * OUT * OUT; e += kTbThreads) {
+            const int i = e / (OUT * OUT), s = e - i * (OUT * OUT), r = s / OUT, c = s - r * OUT;
+            const int gx = OX + c, gy = OY + r;
+            if (gy < a.ny && gx < a.pitch)
+                d.lam_out[i * a.plane + (long long)gy * a.pitch + gx] =
+                    gx < a.nx ? fin[i * NS + (r + K) * W + c + K] : 0.f;
+        }
+    }
+}
+
 // dJ/dc = dJ/d(eta^2) * 2 eta / c_ref, and lambda^0 unpadded
 __global__ void adjoint_finish(const StepArgs a, const double *grad, float *grad_c, double inv_cref,
                                const float *lam, float *grad_g0, int Q) {
@@ -243,6 +483,64 @@ AdjFn pick_adj(int Q, bool mrt, bool per) {
 }
 
 AdjFn pick_adj_rec(int Q) { return Q == 9 ? adjoint_receivers<9> : adjoint_receivers<5>; }
+
+using AdjTbFn = void (*)(const StepArgs, const AdjArgs, const AdjTbArgs);
+
+// levels per blocked launch: D2Q5 8 (32 x 32 tiles; two copies of 5 x 48^2 floats, 92 KB of
+// shared memory, two CTAs per SM), D2Q9 4 (40 x 40 tiles; 166 KB, one CTA per SM)
+int adj_tb_levels(int Q) { return Q == 5 ? 8 : 4; }
+
+template <int Q, bool MRT, int K> AdjTbFn adj_tb_fn(bool per) {
+    return per ? adjoint_tb_kernel<Q, MRT, true, K> : adjoint_tb_kernel<Q, MRT, false, K>;
+}
+
+AdjTbFn pick_adj_tb(int Q, bool mrt, bool per) {
+    if (Q == 9) return mrt ? adj_tb_fn<9, true, 4>(per) : adj_tb_fn<9, false, 4>(per);
+    return mrt ? adj_tb_fn<5, true, 8>(per) : adj_tb_fn<5, false, 8>(per);
+}
+
+// Every (region, local coordinate) along one axis at which grid coordinate x appears:
+// region b covers the unwrapped coordinates b OUT - K .. b OUT - K + 47; a periodic axis
+// also places the images x + k n of x.
+void axis_hits(int x, int n, int tiles, int K, bool per, std::vector<std::pair<int, int>> &hits) {
+    const int OUT = kTbW - 2 * K, lo = -K, hi = tiles * OUT - K + kTbW;
+    hits.clear();
+    int xs = x;
+    if (per)
+        while (xs - n >= lo) xs -= n;
+    for (; xs < hi; xs += n) {
+        if (xs >= lo) {
+            const int num = xs + K - (kTbW - 1);
+            const int b0 = num <= 0 ? 0 : (num + OUT - 1) / OUT;
+            const int b1 = std::min((xs + K) / OUT, tiles - 1);
+            for (int bb = b0; bb <= b1; bb++) hits.emplace_back(bb, xs - (bb * OUT - K));
+        }
+        if (!per) break;
+    }
+}
+
+// receivers inside each region of the blocked sweep: offsets [regions + 1] and
+// {receiver, region site} entries, grouped by region
+void region_lists(const lb_ctx *ctx, int K, bool per, std::vector<int> &off,
+                  std::vector<int2> &ent) {
+    const int OUT = kTbW - 2 * K;
+    const int tx = (ctx->nx + OUT - 1) / OUT, ty = (ctx->ny + OUT - 1) / OUT;
+    std::vector<std::pair<int, int>> hx, hy;
+    std::vector<std::pair<int, int2>> all;  // (region, entry)
+    for (int r = 0; r < ctx->nrec; r++) {
+        axis_hits(ctx->rec_xy[2 * r], ctx->nx, tx, K, per, hx);
+        axis_hits(ctx->rec_xy[2 * r + 1], ctx->ny, ty, K, per, hy);
+        for (const auto &py : hy)
+            for (const auto &px : hx)
+                all.push_back({py.first * tx + px.first, make_int2(r, py.second * kTbW + px.second)});
+    }
+    off.assign((size_t)tx * ty + 1, 0);
+    for (const auto &e : all) off[e.first + 1]++;
+    for (size_t k = 1; k < off.size(); k++) off[k] += off[k - 1];
+    std::vector<int> pos(off.begin(), off.end() - 1);
+    ent.resize(std::max<size_t>(all.size(), 1));
+    for (const auto &e : all) ent[pos[e.first]++] = e.second;
+}
 
 }  // namespace
 
@@ -363,6 +661,34 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
     const bool mrt = ctx->cfg.collision == LB_MRT, per = ctx->cfg.boundary == LB_PERIODIC;
     StepFn fwd = pick_step(ctx);
     AdjFn adj = pick_adj(Q, mrt, per), adj_rec = pick_adj_rec(Q);
+    // blocked reverse sweep: Ka levels per launch wherever Ka levels of a sub-segment remain
+    const int Ka = adj_tb_levels(Q), OUTa = kTbW - 2 * Ka;
+    AdjTbFn adj_tb = pick_adj_tb(Q, mrt, per);
+    AdjTbArgs tbb;
+    tbb.tiles_x = (ctx->nx + OUTa - 1) / OUTa;
+    tbb.reg_off = nullptr;
+    tbb.reg_rec = nullptr;
+    const dim3 tb_grid(tbb.tiles_x, (ctx->ny + OUTa - 1) / OUTa);
+    const size_t tb_smem = 2 * (size_t)Q * kTbNS * sizeof(float);
+    {
+        cudaError_t e = cudaFuncSetAttribute(adj_tb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tb_smem);
+        if (e != cudaSuccess) return release(cuda_fail(ctx, e, "blocked adjoint shared memory"));
+    }
+    std::vector<int> reg_off;
+    std::vector<int2> reg_ent;
+    if (ctx->nrec > 0) {
+        region_lists(ctx, Ka, per, reg_off, reg_ent);
+        int *o = static_cast<int *>(grab(reg_off.size() * sizeof(int)));
+        int2 *en = static_cast<int2 *>(grab(reg_ent.size() * sizeof(int2)));
+        if (!o || !en) return release(fail(ctx, LB_ENOMEM, "region receiver lists"));
+        cudaMemcpyAsync(o, reg_off.data(), reg_off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        ctx->stream);
+        cudaMemcpyAsync(en, reg_ent.data(), reg_ent.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                        ctx->stream);
+        tbb.reg_off = o;
+        tbb.reg_rec = en;
+    }
     StepArgs base = base_args(ctx);
     base.trace_row = nullptr;  // replays record nothing
     const long long t0 = ctx->ckpt_t0;
@@ -412,7 +738,7 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
             const long long sa = ta + (long long)j * T, sb = std::min<long long>(sa + T, tb);
             const int len = (int)(sb - sa);
             replay(SC[j], raw_a && j == 0, sa, len, nullptr, true);
-            for (int m = len - 1; m >= 0; m--) {
+            for (int m = len - 1; m >= 0;) {
                 StepArgs a = base;
                 a.t = sa + m;
                 AdjArgs d;
@@ -425,9 +751,17 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
                 d.resid = resid;
                 d.nrec = ctx->nrec;
                 d.segs = segs4;
-                adj<<<adj_blocks, kThreads, 0, ctx->stream>>>(a, d);
-                if (ctx->nrec > 0)
-                    adj_rec<<<(ctx->nrec + 255) / 256, 256, 0, ctx->stream>>>(a, d);
+                if (m + 1 >= Ka) {  // levels sa + m .. sa + m - Ka + 1 in one launch
+                    tbb.rho_hi = d.rho;
+                    tbb.t_hi = a.t;
+                    adj_tb<<<tb_grid, kTbThreads, tb_smem, ctx->stream>>>(a, d, tbb);
+                    m -= Ka;
+                } else {
+                    adj<<<adj_blocks, kThreads, 0, ctx->stream>>>(a, d);
+                    if (ctx->nrec > 0)
+                        adj_rec<<<(ctx->nrec + 255) / 256, 256, 0, ctx->stream>>>(a, d);
+                    m -= 1;
+                }
                 li ^= 1;
             }
         }

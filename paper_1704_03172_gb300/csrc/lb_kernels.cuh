@@ -34,6 +34,20 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kSitesPerWarp = 128;       // 32 lanes x 4 sites
 static_assert(kThreads == 256, "one medium-table entry per thread");
 
+// Time-blocked kernels (tblock.cu forward, adjoint.cu reverse): one CTA of kTbThreads
+// threads per kTbW x kTbW region (an output tile plus a K-site halo), each thread
+// holding the same kTbPer sites of the region for every level.
+constexpr int kTbW = 48;
+constexpr int kTbNS = kTbW * kTbW;
+constexpr int kTbThreads = 384;
+constexpr int kTbPer = kTbNS / kTbThreads;
+static_assert(kTbPer * kTbThreads == kTbNS, "region must split evenly over the threads");
+
+__host__ __device__ __forceinline__ int wrap_mod(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
 template <int Q> struct Lat;
 template <> struct Lat<5> {
     __host__ __device__ static constexpr int cx(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }

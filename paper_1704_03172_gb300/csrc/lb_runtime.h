@@ -40,6 +40,7 @@ struct lb_ctx {
     int src_nt = 0, src_x = 0, src_y = 0;
     int2 *rec = nullptr;
     int nrec = 0;
+    std::vector<int> rec_xy;        // host copy of rec: (x, row) pairs
     float *trace = nullptr;         // [trace_cap][nrec]
     int trace_cap = 0;
     long long t_rec0 = 0;

@@ -316,13 +316,17 @@ lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint,
     if (want_adjoint) {
         // lb_adjoint: checkpoints every C steps and, in the storage type, the two replay
         // states and the sub-checkpoints; the FP32 rho tape (T planes), the FP32 adjoint
-        // pair, the FP64 gradient and dJ/dS
+        // pair, the FP64 gradient and dJ/dS; the receiver lists of the blocked reverse
+        // sweep (one offset per 32 x 32 tile or larger, up to four entries per receiver)
         const int C = want_adjoint > 1 ? want_adjoint : 200;
         const int T = adj_tape_steps(plane * 4, C);
         const size_t nsub = (size_t)((C + T - 1) / T);
         const size_t states = (nt > 0 ? ((size_t)nt + C - 1) / C : 1) + 2 + (nsub - 1);
         b += states * q * plane * elem_bytes(cfg->storage) + (size_t)T * plane * 4 +
              2 * q * plane * 4 + plane * 8 + (size_t)std::max(nt, 0) * 8;
+        const size_t tiles = ((size_t)std::max(cfg->nx, 1) + 31) / 32 *
+                             (((size_t)std::max(cfg->ny, 1) + 31) / 32);
+        b += (tiles + 1) * 4 + (size_t)std::max(nrec, 0) * 4 * 8;
     }
     *bytes = b;
     return LB_OK;
@@ -540,6 +544,7 @@ static lb_status set_receivers_rows(lb_ctx *ctx, const int *xy, int nrec, int nt
     ctx->rec = nullptr;
     ctx->trace = nullptr;
     ctx->nrec = 0;
+    ctx->rec_xy.clear();
     ctx->trace_cap = 0;
     ctx->t_rec0 = ctx->t;
     if (nrec == 0) return LB_OK;
@@ -554,6 +559,7 @@ static lb_status set_receivers_rows(lb_ctx *ctx, const int *xy, int nrec, int nt
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "receiver upload");
     ctx->nrec = nrec;
+    ctx->rec_xy.assign(xy, xy + 2 * (size_t)nrec);
     ctx->trace_cap = nt_capacity;
     if (ctx->refined) return refine_set_receivers(ctx, xy, nrec);
     if (ctx->cfg.time_block > 1) return tb_set_receivers(ctx, xy, nrec);

@@ -34,11 +34,9 @@ using namespace lbrt;
 
 namespace {
 
-constexpr int kW = 48;                      // region width (tile + 2K halo)
-constexpr int kNS = kW * kW;                // sites in the region
-constexpr int kTbThreads = 384;
-constexpr int kPer = kNS / kTbThreads;      // 6 sites per thread
-static_assert(kPer * kTbThreads == kNS, "region must split evenly over the threads");
+constexpr int kW = kTbW;      // region width (tile + 2K halo)
+constexpr int kNS = kTbNS;    // sites in the region
+constexpr int kPer = kTbPer;  // 6 sites per thread
 
 struct TbArgs {
     const int *tile_off;  // [ntiles + 1] receiver list offsets per tile
@@ -46,10 +44,6 @@ struct TbArgs {
     int tiles_x;
 };
 
-__device__ __forceinline__ int wrap(int v, int n) {
-    v %= n;
-    return v < 0 ? v + n : v;
-}
 
 // REC: also record rho of every level of the own tile (adjoint replays only)
 template <int Q, bool MRT, bool PERIODIC, int K, bool REC>
@@ -78,7 +72,7 @@ __global__ void __launch_bounds__(kTbThreads) tb_kernel(const StepArgs a, const 
             int gx = X0 + c, gy = Y0 + r;
             float v = 0.f;
             if (PERIODIC) {
-                v = in[i * a.plane + (long long)wrap(gy, a.ny) * a.pitch + wrap(gx, a.nx)];
+                v = in[i * a.plane + (long long)wrap_mod(gy, a.ny) * a.pitch + wrap_mod(gx, a.nx)];
             } else if (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny) {
                 v = in[i * a.plane + (long long)gy * a.pitch + gx];
             }
@@ -95,8 +89,8 @@ __global__ void __launch_bounds__(kTbThreads) tb_kernel(const StepArgs a, const 
         int gx = X0 + c, gy = Y0 + r;
         bool live = true;
         if (PERIODIC) {
-            gx = wrap(gx, a.nx);
-            gy = wrap(gy, a.ny);
+            gx = wrap_mod(gx, a.nx);
+            gy = wrap_mod(gy, a.ny);
         } else {
             live = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
         }
