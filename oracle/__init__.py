@@ -108,14 +108,20 @@ def _declare_refine(L):
     L.orc_ref_pressure.argtypes = [vp, _dp]
     L.orc_ref_fine_pressure.argtypes = [vp, _dp]
     L.orc_ref_states.argtypes = [vp, _dp, _dp]
+    L.orc_ref_nest.argtypes = [vp] + [ctypes.c_int] * 4
+    L.orc_ref_level_dims.argtypes = [vp, ctypes.c_int, _ip, _ip]
+    L.orc_ref_level_pressure.argtypes = [vp, ctypes.c_int, _dp]
+    L.orc_ref_level_cmap.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     for n in ("orc_ref_dims", "orc_ref_fine_cmap", "orc_ref_init_pressure", "orc_ref_run",
-              "orc_ref_pressure", "orc_ref_fine_pressure", "orc_ref_states"):
+              "orc_ref_pressure", "orc_ref_fine_pressure", "orc_ref_states", "orc_ref_nest",
+              "orc_ref_level_dims", "orc_ref_level_pressure", "orc_ref_level_cmap"):
         getattr(L, n).restype = ctypes.c_int
 
 
 class Refined:
-    """Two-level refined run (Sec. 4): coarse Problem P plus a patch of coarse cells
-    [x0, x0 + nxp] x [y0, y0 + nyp] refined by 2 in space and time."""
+    """Refined run (Sec. 4): coarse Problem P plus a patch of coarse cells
+    [x0, x0 + nxp] x [y0, y0 + nyp] refined by 2 in space and time; nest() adds patches
+    refined by 2 again inside the innermost fine grid."""
 
     def __init__(self, P: "Problem", x0, y0, nxp, nyp, rule="viscous"):
         """rule "viscous" (R6): fine rates with tau_f - 1/2 = 2 (tau_c - 1/2) and factors
@@ -136,6 +142,32 @@ class Refined:
         cf = np.zeros((self.nyf, self.nxf), np.float32)
         lib().orc_ref_fine_cmap(self.h, _ptr(cf, ctypes.c_float))
         return cf
+
+    def nest(self, x0, y0, nxp, nyp):
+        """A patch of nodes [x0, x0 + nxp] x [y0, y0 + nyp] of the innermost fine grid (its
+        node coordinates), refined by 2 again ("multiples of 2", Sec. 4).  Before
+        init_pressure.  Returns the new level's index (2 for the first nested patch)."""
+        level = lib().orc_ref_nest(self.h, int(x0), int(y0), int(nxp), int(nyp))
+        if level < 0:
+            raise ValueError("invalid nested patch")
+        return level
+
+    def level_dims(self, level):
+        nx, ny = ctypes.c_int(), ctypes.c_int()
+        if lib().orc_ref_level_dims(self.h, int(level), ctypes.byref(nx), ctypes.byref(ny)):
+            raise ValueError("no such level")
+        return ny.value, nx.value
+
+    def level_pressure(self, level):
+        """pressure of refined level >= 1 on all of its own nodes"""
+        p = np.zeros(self.level_dims(level))
+        lib().orc_ref_level_pressure(self.h, int(level), _ptr(p, ctypes.c_double))
+        return p
+
+    def level_cmap(self, level):
+        c = np.zeros(self.level_dims(level), np.float32)
+        lib().orc_ref_level_cmap(self.h, int(level), _ptr(c, ctypes.c_float))
+        return c
 
     def init_pressure(self, p0=None):
         p = None if p0 is None else np.ascontiguousarray(p0, np.float64).reshape(self.P.ny,

@@ -53,7 +53,8 @@ void orc_step_grid(const orc_problem *P, const double *Minv, int t, const double
 void orc_record(const orc_problem *P, const double *g, double *row);
 void orc_site_weights(const orc_problem *P, size_t idx, double *w, double *cs2);
 
-/* Two-level refinement (Sec. 4), lbrefine.c.  Opaque handle. */
+/* Grid refinement (Sec. 4), lbrefine.c: two levels, or more with nested patches.  Opaque
+ * handle. */
 /* rule 0: viscosity-continuous fine rates and non-equilibrium factors (reading R6);
  * rule 1: the paper's printed factors 1/2 and 2 with the coarse rates on both grids.
  * Both coincide at tau = 1/2 (MRT: s = 2 for every relaxed moment). */
@@ -66,6 +67,11 @@ int orc_ref_run(void *h, int nsteps, double *trace);
 int orc_ref_pressure(void *h, double *p);
 int orc_ref_fine_pressure(void *h, double *pf);
 int orc_ref_states(void *h, double *gc, double *gf);
+/* nested patches: a patch of the innermost fine grid (its node coordinates), refined by 2 */
+int orc_ref_nest(void *h, int x0, int y0, int nxp, int nyp);
+int orc_ref_level_dims(void *h, int level, int *nx, int *ny);
+int orc_ref_level_pressure(void *h, int level, double *p);
+int orc_ref_level_cmap(void *h, int level, float *c);
 
 /* Discrete adjoint (lbadjoint.c): gradients of J with dJ/dp^t_r = resid[t][r]
  * for nt steps from g0.  grad_c [ny][nx]; grad_src [nt] and grad_g0 [Q][ny][nx]

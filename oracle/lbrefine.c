@@ -35,6 +35,14 @@
  *   fine step 2T+1 -> 2T+2, then the same from U(T+1);
  *   correct the coarse populations on I from the fine state at 2T+2.
  * The same coupling is applied once to the initial state (time 0).
+ *
+ * Nested patches ("multiples of 2", Sec. 4): orc_ref_nest places a further patch inside the
+ * innermost fine grid, in that grid's node coordinates, refined by 2 again (ratio 4, 8, ...
+ * to the coarse grid).  Each pair of adjacent levels is coupled exactly as above; a "fine
+ * step" of a level that holds a patch is the whole procedure for that level and its patch
+ * (two steps of the next level per step, recursively).  The fine rates follow reading R6 level
+ * by level: tau_{l+1} - 1/2 = 2 (tau_l - 1/2).  Receivers and pressures come from the deepest
+ * level whose closed patch holds the node.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -42,8 +50,10 @@
 
 #include "lbref.h"
 
-typedef struct {
+typedef struct ref_s {
     orc_problem C, F;
+    struct ref_s *sub; /* nested patch inside F, or NULL */
+    int rule;
     int x0, y0, nxp, nyp, nxf, nyf, nI;
     float *cf;
     double *gc, *gf, *tc, *tf, *Uprev, *Unext;
@@ -197,6 +207,7 @@ void *orc_ref_create(const orc_problem *coarse, int x0, int y0, int nxp, int nyp
     R->nyp = nyp;
     R->nxf = 2 * nxp + 1;
     R->nyf = 2 * nyp + 1;
+    R->rule = rule;
     const int Q = coarse->Q, nx = coarse->nx;
     const size_t N = (size_t)nx * coarse->ny, Nf = (size_t)R->nxf * R->nyf;
     /* fine medium: bilinear interpolation of the coarse sound speed */
@@ -267,6 +278,7 @@ void *orc_ref_create(const orc_problem *coarse, int x0, int y0, int nxp, int nyp
 void orc_ref_destroy(void *h) {
     ref_t *R = (ref_t *)h;
     if (!R) return;
+    orc_ref_destroy(R->sub);
     free(R->cf);
     free(R->idxI);
     free(R->Ix);
@@ -293,15 +305,15 @@ int orc_ref_fine_cmap(void *h, float *cf) {
     return 0;
 }
 
-/* g = g^eq(p0 / c_s^2, 0) on both grids (p0 interpolated bilinearly to the fine
- * nodes), then the coupling at time 0. */
-int orc_ref_init_pressure(void *h, const double *p0) {
-    ref_t *R = (ref_t *)h;
+/* Fine grid of R from the pressure pc on R's coarse grid (NULL: zero): g = g^eq(p / c_s^2, 0)
+ * with p interpolated bilinearly, the same for every nested level, then the coupling at
+ * time 0 of each pair (the couplings of different pairs touch different nodes when every
+ * patch keeps a margin of at least one node, so their order is immaterial). */
+static void init_level(ref_t *R, const double *pc, double *gcs) {
     const int nx = R->C.nx;
     const size_t Nf = (size_t)R->nxf * R->nyf;
-    orc_init_pressure(&R->C, p0, R->gc);
     double *pf = NULL;
-    if (p0) {
+    if (pc) {
         pf = (double *)malloc(sizeof(double) * Nf);
         for (int b = 0; b < R->nyf; b++)
             for (int a = 0; a < R->nxf; a++) {
@@ -309,76 +321,102 @@ int orc_ref_init_pressure(void *h, const double *p0) {
                 double s = 0;
                 for (int dy = 0; dy <= oy; dy++)
                     for (int dx = 0; dx <= ox; dx++) {
-                        s += p0[(size_t)(Y + dy) * nx + X + dx];
+                        s += pc[(size_t)(Y + dy) * nx + X + dx];
                         cnt++;
                     }
                 pf[(size_t)b * R->nxf + a] = s / cnt;
             }
     }
     orc_init_pressure(&R->F, pf, R->gf);
+    if (R->sub) init_level(R->sub, pf, R->gf);
     free(pf);
-    snapshot(R, R->gc, R->Uprev);
+    snapshot(R, gcs, R->Uprev);
     c2f(R, R->gf, R->Uprev, R->Uprev, 1.0);
-    f2c(R, R->gc, R->gf);
+    f2c(R, gcs, R->gf);
+}
+
+/* g = g^eq(p0 / c_s^2, 0) on every grid (p0 interpolated bilinearly to the fine
+ * nodes, level by level), then the coupling at time 0. */
+int orc_ref_init_pressure(void *h, const double *p0) {
+    ref_t *R = (ref_t *)h;
+    orc_init_pressure(&R->C, p0, R->gc);
+    init_level(R, p0, R->gc);
     R->t = 0;
     return 0;
 }
 
+/* pressure at node (a, b) of R's fine grid, from the deepest level holding it */
+static double fine_p(const ref_t *R, int a, int b) {
+    if (R->sub && in_closed_patch(R->sub, a, b))
+        return fine_p(R->sub, 2 * (a - R->sub->x0), 2 * (b - R->sub->y0));
+    const size_t Nf = (size_t)R->nxf * R->nyf, fidx = (size_t)b * R->nxf + a;
+    double w[9], cs2, rho = 0;
+    orc_site_weights(&R->F, fidx, w, &cs2);
+    for (int i = 0; i < R->C.Q; i++) rho += R->gf[(size_t)i * Nf + fidx];
+    return cs2 * rho;
+}
+
 static void record_all(const ref_t *R, double *row) {
     const orc_problem *C = &R->C;
-    const size_t N = (size_t)C->nx * C->ny, Nf = (size_t)R->nxf * R->nyf;
+    const size_t N = (size_t)C->nx * C->ny;
     for (int r = 0; r < C->nrec; r++) {
         int X = C->rec_xy[2 * r], Y = C->rec_xy[2 * r + 1];
-        double w[9], cs2, rho = 0;
         if (in_closed_patch(R, X, Y)) {
-            size_t fidx = (size_t)(2 * (Y - R->y0)) * R->nxf + 2 * (X - R->x0);
-            orc_site_weights(&R->F, fidx, w, &cs2);
-            for (int i = 0; i < C->Q; i++) rho += R->gf[(size_t)i * Nf + fidx];
+            row[r] = fine_p(R, 2 * (X - R->x0), 2 * (Y - R->y0));
         } else {
+            double w[9], cs2, rho = 0;
             size_t idx = (size_t)Y * C->nx + X;
             orc_site_weights(C, idx, w, &cs2);
             for (int i = 0; i < C->Q; i++) rho += R->gc[(size_t)i * N + idx];
+            row[r] = cs2 * rho;
         }
-        row[r] = cs2 * rho;
     }
+}
+
+static void pair_advance(ref_t *R, double *gin, double *gout, long T);
+
+/* one step of R's fine grid from fin to fout, with every level nested in it */
+static void fine_advance(ref_t *R, double *fin, double *fout, long t) {
+    if (R->sub)
+        pair_advance(R->sub, fin, fout, t);
+    else
+        orc_step_grid(&R->F, R->Minv, 0, fin, fout);
+}
+
+/* R's coarse grid from time T (gin) to T+1 (gout), its fine grid from 2T to 2T+2 */
+static void pair_advance(ref_t *R, double *gin, double *gout, long T) {
+    orc_step_grid(&R->C, R->Minv, (int)T, gin, gout); /* provisional coarse T+1 */
+    snapshot(R, gout, R->Unext);
+    fine_advance(R, R->gf, R->tf, 2 * T); /* fine 2T -> 2T+1 */
+    c2f(R, R->tf, R->Uprev, R->Unext, 0.5);
+    fine_advance(R, R->tf, R->gf, 2 * T + 1); /* fine 2T+1 -> 2T+2 */
+    c2f(R, R->gf, R->Uprev, R->Unext, 1.0);
+    f2c(R, gout, R->gf);
+    double *s = R->Uprev;
+    R->Uprev = R->Unext;
+    R->Unext = s;
 }
 
 int orc_ref_run(void *h, int nsteps, double *trace) {
     ref_t *R = (ref_t *)h;
     for (int k = 0; k < nsteps; k++) {
-        long T = R->t;
         if (trace && R->C.nrec > 0) record_all(R, trace + (size_t)k * R->C.nrec);
-        orc_step_grid(&R->C, R->Minv, (int)T, R->gc, R->tc); /* provisional coarse T+1 */
-        snapshot(R, R->tc, R->Unext);
-        orc_step_grid(&R->F, R->Minv, 0, R->gf, R->tf); /* fine 2T -> 2T+1 */
-        c2f(R, R->tf, R->Uprev, R->Unext, 0.5);
-        orc_step_grid(&R->F, R->Minv, 0, R->tf, R->gf); /* fine 2T+1 -> 2T+2 */
-        c2f(R, R->gf, R->Uprev, R->Unext, 1.0);
-        f2c(R, R->tc, R->gf);
+        pair_advance(R, R->gc, R->tc, R->t);
         double *s = R->gc;
         R->gc = R->tc;
         R->tc = s;
-        s = R->Uprev;
-        R->Uprev = R->Unext;
-        R->Unext = s;
         R->t++;
     }
     return 0;
 }
 
-/* pressure on the coarse grid; nodes of the closed patch from the fine grid */
+/* pressure on the coarse grid; nodes of the closed patch from the finest level holding them */
 int orc_ref_pressure(void *h, double *p) {
     ref_t *R = (ref_t *)h;
-    const size_t Nf = (size_t)R->nxf * R->nyf;
     orc_pressure(&R->C, R->gc, p);
     for (int Y = R->y0; Y <= R->y0 + R->nyp; Y++)
-        for (int X = R->x0; X <= R->x0 + R->nxp; X++) {
-            size_t fidx = (size_t)(2 * (Y - R->y0)) * R->nxf + 2 * (X - R->x0);
-            double w[9], cs2, rho = 0;
-            orc_site_weights(&R->F, fidx, w, &cs2);
-            for (int i = 0; i < R->C.Q; i++) rho += R->gf[(size_t)i * Nf + fidx];
-            p[(size_t)Y * R->C.nx + X] = cs2 * rho;
-        }
+        for (int X = R->x0; X <= R->x0 + R->nxp; X++)
+            p[(size_t)Y * R->C.nx + X] = fine_p(R, 2 * (X - R->x0), 2 * (Y - R->y0));
     return 0;
 }
 
@@ -391,5 +429,49 @@ int orc_ref_states(void *h, double *gc, double *gf) {
     ref_t *R = (ref_t *)h;
     if (gc) memcpy(gc, R->gc, sizeof(double) * R->C.Q * R->C.nx * R->C.ny);
     if (gf) memcpy(gf, R->gf, sizeof(double) * R->C.Q * R->nxf * R->nyf);
+    return 0;
+}
+
+/* A patch of nodes [x0, x0 + nxp] x [y0, y0 + nyp] of the innermost fine grid, refined by 2
+ * again (same rule).  Call before orc_ref_init_pressure.  Returns the new level's index
+ * (2 for the first nested patch), or -1 for a patch without a one-node margin. */
+int orc_ref_nest(void *h, int x0, int y0, int nxp, int nyp) {
+    ref_t *R = (ref_t *)h;
+    int level = 1;
+    while (R->sub) {
+        R = R->sub;
+        level++;
+    }
+    ref_t *S = (ref_t *)orc_ref_create(&R->F, x0, y0, nxp, nyp, R->rule);
+    if (!S) return -1;
+    R->sub = S;
+    return level + 1;
+}
+
+static const ref_t *level_of(const ref_t *R, int level) {
+    for (int l = 1; l < level && R; l++) R = R->sub;
+    return R;
+}
+
+/* node counts of level >= 1 (level 1 is the first patch's fine grid) */
+int orc_ref_level_dims(void *h, int level, int *nx, int *ny) {
+    const ref_t *R = level_of((const ref_t *)h, level);
+    if (!R || level < 1) return -1;
+    *nx = R->nxf;
+    *ny = R->nyf;
+    return 0;
+}
+
+/* pressure of level >= 1 on its own nodes [ny][nx] */
+int orc_ref_level_pressure(void *h, int level, double *p) {
+    const ref_t *R = level_of((const ref_t *)h, level);
+    if (!R || level < 1) return -1;
+    return orc_pressure(&R->F, R->gf, p);
+}
+
+int orc_ref_level_cmap(void *h, int level, float *c) {
+    const ref_t *R = level_of((const ref_t *)h, level);
+    if (!R || level < 1) return -1;
+    memcpy(c, R->cf, sizeof(float) * R->nxf * R->nyf);
     return 0;
 }

@@ -123,3 +123,99 @@ def test_viscous_rule_mrt_general_rates(oracle_mod):
     ref = _standing_wave(oracle_mod, 0.5, True, s, 200, None)
     vis = _standing_wave(oracle_mod, 0.5, True, s, 200, "viscous")
     assert abs(vis / ref - 1) < 5e-3
+
+
+# ---- nested patches ("multiples of 2", Sec. 4): a patch refined by 2 inside the fine grid
+
+def test_nested_medium_is_bilinear_interpolation_of_the_fine_medium(oracle_mod):
+    n = 24
+    c = W.random_medium(n, n, 8, 0.4, 1.0)
+    R = oracle_mod.Refined(oracle_mod.Problem(5, n, n, c, c_ref=1.0), 4, 5, 12, 10)
+    assert R.nest(3, 4, 6, 5) == 2
+    c1, c2 = R.level_cmap(1), R.level_cmap(2)
+    assert c1.shape == (21, 25) and c2.shape == (11, 13)
+    np.testing.assert_array_equal(c1, R.fine_cmap())
+    a = c1.astype(np.float64)
+    assert c2[4, 6] == c1[4 // 2 + 4, 6 // 2 + 3]
+    assert c2[4, 7] == np.float32((a[6, 6] + a[6, 7]) / 2)
+    assert c2[5, 7] == np.float32((a[6, 6] + a[6, 7] + a[7, 6] + a[7, 7]) / 4)
+
+
+@pytest.mark.parametrize("Q", [5, 9])
+def test_nested_uniform_state_is_preserved(oracle_mod, Q):
+    n = 48
+    P = oracle_mod.Problem(Q, n, n, W.uniform_map(n, n, 1.0), c_ref=1.0, periodic=True,
+                           mrt=True, s=[1.0] * 3 + [1.5, 1.7] + [1.2] * 4, w_ref=(0.4, 0.11, 0.04))
+    R = oracle_mod.Refined(P, 15, 12, 18, 20)
+    R.nest(6, 8, 20, 16)
+    R.init_pressure(np.full((n, n), 2e-3))
+    R.run(20)
+    assert np.abs(R.pressure() - 2e-3).max() < 1e-15
+    for level in (1, 2):
+        assert np.abs(R.level_pressure(level) - 2e-3).max() < 1e-15
+
+
+def test_nested_patch_reflection_and_accuracy(oracle_mod):
+    # a pulse from a coarse-grid source crosses the first interface, then the nested one
+    # (ratio 4 to the coarse grid); compared with the same problem on a uniformly 4x finer
+    # grid (source density per unit time kept: S_4(tau) = 4 S(tau / 4))
+    nx, ny, steps = 160, 96, 200
+    fc = 0.5 ** 0.5 / 16
+    wav = W.ricker(steps, fc)
+    xs = np.array([30, 60, 75, 85, 95, 105, 120, 140])
+    rec = np.stack([xs, np.full(len(xs), 48)], 1).astype(np.int32)
+    P = oracle_mod.Problem(5, nx, ny, W.uniform_map(nx, ny, 1.0), c_ref=1.0, tau=0.5,
+                           source=(20, 48, wav), receivers=rec, sponge_width=16,
+                           sponge_sigma_max=0.1)
+    two = oracle_mod.Refined(P, 50, 18, 80, 60)       # level 1: coarse x 50..130
+    two.init_pressure(None)
+    tr2 = two.run(steps)
+    nest = oracle_mod.Refined(P, 50, 18, 80, 60)
+    nest.nest(40, 30, 80, 60)                         # level 2: coarse x 70..110, y 33..63
+    nest.init_pressure(None)
+    tr3 = nest.run(steps)
+    _, tru = oracle_mod.run(P, P.zeros(), steps)
+    k = 4
+    Pf = oracle_mod.Problem(5, k * nx, k * ny, W.uniform_map(k * nx, k * ny, 1.0), c_ref=1.0,
+                            tau=0.5, source=(k * 20, k * 48, k * W.ricker(k * steps, fc / k)),
+                            receivers=k * rec, sponge_width=16 * k, sponge_sigma_max=0.1 / k)
+    _, trf = oracle_mod.run(Pf, Pf.zeros(), k * steps)
+    trf = trf[::k]
+    amp = np.abs(tru).max(axis=0)
+    # upstream: neither interface reflects (Sec. 5.2); the nested one adds less than 1e-3
+    assert np.abs(tr3 - tru).max(axis=0)[0] / amp[0] < 5e-3
+    assert np.abs(tr3 - tr2).max(axis=0)[0] / amp[0] < 1e-3
+    err = {name: np.linalg.norm(tr - trf, axis=0) / np.linalg.norm(trf, axis=0)
+           for name, tr in (("coarse", tru), ("two", tr2), ("nest", tr3))}
+    inner = (xs >= 85)
+    # across the ratio-4 patch the error against the 4x run does not grow, while the
+    # two-level run's does; beyond it the nested run stays the closer one
+    assert err["nest"][5] - err["nest"][2] < 0.2 * (err["two"][5] - err["two"][2])
+    assert (err["nest"][inner] < 0.95 * err["two"][inner]).all()
+    assert (err["two"][1:] < 0.85 * err["coarse"][1:]).all()
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.0])
+def test_nested_viscous_rule_keeps_the_damping(oracle_mod, tau):
+    # Reading R6 level by level (tau_2 - 1/2 = 2 (tau_1 - 1/2) = 4 (tau_0 - 1/2)): a decaying
+    # standing wave loses amplitude at the unrefined rate with two nested patches as well
+    n, T = 64, 200
+    P = oracle_mod.Problem(5, n, n, np.ones((n, n), np.float32), c_ref=1.0, periodic=True,
+                           tau=tau)
+    x = np.arange(n)
+    p0 = 1e-3 * np.repeat(np.cos(2 * np.pi * x / n)[None, :], n, axis=0)
+
+    def amp(p):
+        return float((p * np.cos(2 * np.pi * x / n)[None, :]).mean() * 2)
+
+    g, _ = oracle_mod.run(P, oracle_mod.init_pressure(P, p0), T)
+    ref = amp(oracle_mod.pressure(P, g))
+    out = {}
+    for rule in ("viscous", "paper"):
+        R = oracle_mod.Refined(P, 16, 16, 32, 32, rule=rule)
+        R.nest(16, 16, 32, 32)
+        R.init_pressure(p0)
+        R.run(T)
+        out[rule] = amp(R.pressure()) / ref - 1
+    assert abs(out["viscous"]) < 5e-3
+    assert out["paper"] > 2 * abs(out["viscous"])    # coarse rates on every level damp less
