@@ -204,6 +204,29 @@ def _refined_variant(torch, LBSim, steps, warmup):
             "launches_per_coarse_step": 7}
 
 
+def _nested_variant(torch, LBSim, steps, warmup):
+    """The slow-block workload with a nested patch: 2048^2 coarse grid, a 1025^2-node patch
+    (2x) and inside it a 1025^2-node nested patch (4x to the coarse grid).  One site-step of
+    any level counts as one update: 2048^2 + 2 * 1025^2 + 4 * 1025^2 per coarse step."""
+    wl = W.refined_nested_workload(2048)
+    sim = LBSim(wl["c_map"], lattice=5, collision="mrt", s=wl["s"], c_ref=wl["c_ref"],
+                sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"],
+                patch=wl["patches"])
+    sim.set_source(*wl["source"])
+    sim.set_receivers(wl["receivers"], steps + warmup)
+    sim.init_pressure(None)
+    try:
+        sec = _time_steps(torch, sim, steps, warmup)
+    finally:
+        sim.close()
+    n1 = 2 * wl["patches"][0][2] + 1
+    n2 = 2 * wl["patches"][1][2] + 1
+    updates = 2048 * 2048 + 2 * n1 * n1 + 4 * n2 * n2
+    return {"glups": round(updates * steps / sec / 1e9, 2), "updates_per_coarse_step": updates,
+            "ms_per_coarse_step": round(sec / steps * 1e3, 4),
+            "launches_per_coarse_step": 19}
+
+
 def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32"):
     """Gradient of J = 1/2 sum p^2 over 512 receiver traces w.r.t. the sound-speed map and
     the source, for a 20-layer faulted model: forward run with checkpoints, then lb_adjoint
@@ -514,6 +537,8 @@ def run_ours(args):
         if name.startswith("adjoint_"):
             out = _adjoint_variant(torch, LBSim, n=args.adj_n, nt=args.adj_nt,
                                    every=args.adj_every, storage=name.rsplit("_", 1)[1])
+        elif name.startswith("refined_nested"):
+            out = _nested_variant(torch, LBSim, args.steps, args.warmup)
         elif name.startswith("refined"):
             out = _refined_variant(torch, LBSim, args.steps, args.warmup)
         elif name == "dispersion":
@@ -623,6 +648,10 @@ def run_ours(args):
             v["refined_block_2048_d2q5_mrt_f32"] = _refined_variant(torch, LBSim, 400, 10)
         except Exception as ex:
             v["refined_block_2048_d2q5_mrt_f32"] = {"error": str(ex)[:200]}
+        try:
+            v["refined_nested_2048_d2q5_mrt_f32"] = _nested_variant(torch, LBSim, 400, 10)
+        except Exception as ex:
+            v["refined_nested_2048_d2q5_mrt_f32"] = {"error": str(ex)[:200]}
         for st in ("f32", "bf16"):
             try:
                 v[f"adjoint_4096_d2q5_{st}"] = _adjoint_variant(torch, LBSim, storage=st)
@@ -665,7 +694,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--variant", default="",
-                    help="run one variant alone: adjoint_f32, adjoint_bf16, refined, served")
+                    help="run one variant alone: adjoint_f32, adjoint_bf16, refined, refined_nested, served")
     ap.add_argument("--adj-n", type=int, default=4096, help="adjoint variant grid side")
     ap.add_argument("--adj-nt", type=int, default=1000, help="adjoint variant steps")
     ap.add_argument("--adj-every", type=int, default=200, help="adjoint checkpoint interval")

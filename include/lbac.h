@@ -59,7 +59,10 @@ enum { LB_ZERO_GHOST = 0, LB_PERIODIC = 1 };       /* outer boundary */
 /* One refined patch (Sec. 4).  The fine grid covers the coarse rectangle of
  * nodes [x0, x0 + nx_c] x [y0, y0 + ny_c] with (2 nx_c + 1) x (2 ny_c + 1) fine
  * nodes; fine node (2a, 2b) coincides with coarse node (x0 + a, y0 + b).
- * ratio must be 2 (the paper's n; "multiples of 2", Sec. 4). */
+ * ratio must be 2 (the paper's n).  Larger ratios ("multiples of 2", Sec. 4)
+ * are nested patches: patches[k], k >= 1, lies inside the fine grid of
+ * patches[k - 1], in that grid's node coordinates, and refines it by 2 again;
+ * each patch keeps a margin of at least one node inside the grid above it. */
 typedef struct {
     int x0, y0;
     int nx_c, ny_c;
@@ -81,8 +84,8 @@ typedef struct {
     double tau;               /* BGK relaxation time, tau >= 1/2 (Eq. BGK-LB) */
     double s[9];              /* MRT: diagonal of S in the moment order of App. A, 0 < s <= 2 */
     double w_ref[3];          /* D2Q9 weights (w0, w1, w5) at eta = 1; ignored for D2Q5 */
-    const lb_patch *patches;  /* refinement patches (at most 1), or NULL */
-    int n_patches;
+    const lb_patch *patches;  /* refinement patches, nested (see lb_patch), or NULL */
+    int n_patches;            /* 0 .. LB_MAX_PATCHES */
     void *cuda_stream;        /* cudaStream_t to run on; NULL: the context creates its own
                                  non-blocking stream (pass cudaStreamLegacy for the legacy
                                  default stream, whose handle is NULL) */
@@ -101,6 +104,7 @@ typedef struct {
 } lb_config;
 
 enum { LB_STEP_AUTO = 0, LB_STEP_DIRECT = 1, LB_STEP_STAGED = 2 };
+enum { LB_MAX_PATCHES = 3 };  /* nesting depth: ratio up to 8 to the coarse grid */
 
 /* Fill *cfg with defaults: D2Q5, BGK tau = 1/2, F32, zero ghost, no sponge,
  * conventional D2Q9 weights (4/9, 1/9, 1/36), c_ref = max(c_map). */
@@ -144,7 +148,8 @@ lb_status lb_step(lb_ctx *ctx, int n);
 lb_status lb_record_receivers(lb_ctx *ctx, float *out, int nt_max, int *nt_out, int on_device);
 
 /* Pressure p = c_s^2 sum_i g_i at the current time, [ny][nx] FP32.
- * With a refined patch, nodes inside the patch come from the fine grid. */
+ * With refined patches, nodes inside a patch come from the finest level that
+ * holds them (as do receiver traces). */
 lb_status lb_get_pressure(lb_ctx *ctx, float *out, int on_device);
 
 /* Populations g_i(x) at the current time (before its collision), as

@@ -267,8 +267,9 @@ lb_status validate(const lb_config *cfg) {
     }
     if (cfg->sponge_width < 0 || cfg->sponge_sigma_max < 0 || cfg->sponge_sigma_max > 1)
         return fail(nullptr, LB_EINVAL, "sponge_width >= 0 and sigma_max in [0, 1] required");
-    if (cfg->n_patches < 0 || cfg->n_patches > 1 || (cfg->n_patches > 0 && !cfg->patches))
-        return fail(nullptr, LB_EINVAL, "at most one patch is supported");
+    if (cfg->n_patches < 0 || cfg->n_patches > LB_MAX_PATCHES ||
+        (cfg->n_patches > 0 && !cfg->patches))
+        return fail(nullptr, LB_EINVAL, "n_patches must be 0 .. %d (nested)", LB_MAX_PATCHES);
     if (cfg->time_block > 1) {
         if (!tb_supported(cfg->lattice, cfg->time_block))
             return fail(nullptr, LB_EINVAL, "time_block %d not supported for D2Q%d (D2Q5: 2, 4, 6, "

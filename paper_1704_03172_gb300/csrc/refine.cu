@@ -1,14 +1,17 @@
-// refine.cu -- two-level grid refinement of Sec. 4 (ratio n = 2 in space and
-// time) on the GPU.
+// refine.cu -- grid refinement of Sec. 4 (ratio n = 2 in space and time per
+// level) on the GPU: one patch of the context's grid, and optionally patches
+// nested inside it ("multiples of 2": ratio 4, 8 to the coarse grid).
 //
 // The coarse grid is the context's grid; a patch of coarse cells
 // [x0, x0 + nxp] x [y0, y0 + nyp] is covered by a fine grid of
 // (2 nxp + 1) x (2 nyp + 1) nodes, fine node (a, b) at coarse position
-// (x0 + a/2, y0 + b/2), whose sound speed is the coarse c_map interpolated
-// bilinearly.  The fine grid is stored with a one-node ghost ring: the
-// populations that enter the fine grid across the interface I (the patch
+// (x0 + a/2, y0 + b/2), whose sound speed is the coarse sound speed
+// interpolated bilinearly.  Every fine grid is stored with a one-node ghost
+// ring: the populations that enter it across its interface I (the patch
 // boundary) are written into the ghost ring, so the ordinary fused step kernel
-// pulls them in.
+// pulls them in.  A nested patch lies inside the fine grid of the level above
+// it, in that grid's node coordinates, and is coupled to it exactly as the
+// first patch is coupled to the coarse grid.
 //
 // Coupling (Eq. grid refinement eqm dist, Eq. coarse-fine dist connect), read
 // per population: a fine node of I takes from the coarse grid exactly the
@@ -20,20 +23,24 @@
 //   g^c_i = g^eq_i + 2 (g^f_i - g^eq_i),
 // g^eq being formed from the transferred vector's moments with the receiving
 // grid's weights.  The factors 1/2 and 2 are those of the paper's lossless
-// setting (tau = 1/2, s = 2).  For other rates the fine grid relaxes with
+// setting (tau = 1/2, s = 2).  For other rates each level relaxes with
 // tau_f - 1/2 = 2 (tau_c - 1/2) per relaxed moment, which keeps the physical
 // viscosity continuous, and the non-equilibrium parts scale by tau_f / (2 tau_c)
 // (coarse -> fine) and 2 tau_c / tau_f (fine -> coarse), moment by moment;
-// at tau = 1/2 these are the paper's factors.  The coarse grid keeps running under the patch, which gives
-// the full coarse vector on I (U, kept for two coarse times).
+// at tau = 1/2 these are the paper's factors.  The coarser grid keeps running
+// under its patch, which gives the full coarse vector on I (U, kept for two
+// coarse times).
 //
-// One coarse step T (fused kernels, all on the context stream):
-//   coarse step T (pull, collide, store; receivers outside the patch)
-//   snapshot U(T) = coarse populations on I at time T (before correction)
-//   [T >= 1] c2f into the fine ghost ring from (U(T-1) + U(T)) / 2, fine step 2T-1
-//   c2f from U(T), fine step 2T (receivers inside the closed patch)
-//   f2c: coarse nodes of I re-pulled, corrected from the fine state at 2T,
-//        re-collided and stored over the coarse step's output.
+// One step T of a grid that holds a patch (fused kernels, all on the context
+// stream):
+//   the grid's step T (pull, collide, store; its own receivers)
+//   snapshot U(T) = the grid's populations on I at time T (before correction)
+//   [T >= 1] c2f into the patch's ghost ring from (U(T-1) + U(T)) / 2, patch step 2T-1
+//   c2f from U(T), patch step 2T (receivers inside the closed patch)
+//   f2c: the grid's nodes of I re-pulled, corrected from the patch state at 2T,
+//        re-collided and stored over the grid's step output.
+// A "patch step" of a level that holds a nested patch is this same procedure one level
+// down, so a coarse step of a two-patch hierarchy runs 1 + 2 + 4 step launches.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,31 +53,48 @@
 using namespace lbk;
 using namespace lbrt;
 
+// One refined level: the fine grid of a patch and its coupling to the grid above it.
 struct lb_refine {
-    int x0, y0, nxp, nyp, nxf, nyf;  // patch (coarse cells) and fine node counts
-    int gx, gy, pitch;               // fine grid with its ghost ring
+    int depth = 1;                   // 1: patch of the context's grid; k: patch of level k - 1
+    int x0n = 0, y0n = 0;            // patch origin, parent grid node coordinates
+    int x0 = 0, y0 = 0;              // patch origin, parent grid storage coordinates
+    int nxp = 0, nyp = 0, nxf = 0, nyf = 0;  // patch (parent cells) and fine node counts
+    int gx = 0, gy = 0, pitch = 0;   // fine grid with its ghost ring
     void *pop[2] = {nullptr, nullptr};
     int cur = 0;
     bool raw = false;
     float *eta2 = nullptr;
+    float *cf = nullptr;             // [nyf][nxf] fine sound speed (medium of a nested patch)
+    float *pf = nullptr;             // [nyf][nxf] initial fine pressure (for a nested patch)
     int nI = 0;
-    int2 *Ic = nullptr;              // coarse nodes of I
+    int2 *Ic = nullptr;              // parent nodes of I (storage coordinates)
     float *U[3] = {nullptr, nullptr, nullptr};  // [nI][Q]: slots T % 2, plus one for peeks
     int nIf = 0;
     int4 *If = nullptr;              // fine nodes of I: (a, b, k1, k2), k2 < 0 when single
-    int2 *rec_c = nullptr, *rec_f = nullptr;
+    int2 *rec_c = nullptr, *rec_f = nullptr;  // rec_c: the context grid's (depth 1 only)
     int *col_c = nullptr, *col_f = nullptr;
     int nrec_c = 0, nrec_f = 0;
-    // relaxation on the fine grid, and the non-equilibrium rescales written as collisions:
+    // relaxation on this level, and the non-equilibrium rescales written as collisions:
     // g' = geq + F (g - geq) per non-conserved moment is a collision with rates 1 - F
+    double tau_f = 0.5, stau_f[9] = {};
     float omega_f = 2.f, s_f[9] = {};
     float c2f_omega = 0.5f, c2f_s[9] = {}, f2c_omega = -1.f, f2c_s[9] = {};
+    // coarse node (X, Y), X in [ox0, ox0 + onx), Y in [oy0, oy0 + ony), is this level's
+    // node (oA X + obx, oA Y + oby): the context-grid pressure taken from this level
+    int oA = 2, obx = 0, oby = 0, ox0 = 0, oy0 = 0, onx = 0, ony = 0;
+    lb_refine *sub = nullptr;        // nested patch inside this level's grid
+    void *bak = nullptr;             // depth >= 2: input buffer saved around pressure peeks
+    float *Ubak[2] = {nullptr, nullptr};
+    ~lb_refine() { delete sub; }
 };
 
 namespace {
 
-__global__ void ref_medium_kernel(const float *c_map, int nx, int x0, int y0, int nxf, int nyf,
-                                  int gx, int gy, int pitch, double inv_cref, float *eta2) {
+// fine sound speed and eta^2 (with the ghost ring: nearest real node) from the parent's
+// sound speed pc [..][pnx] (node coordinates), bilinearly; cf gets the real nodes' speeds
+__global__ void ref_medium_kernel(const float *pc, int pnx, int x0n, int y0n, int nxf, int nyf,
+                                  int gx, int gy, int pitch, double inv_cref, float *eta2,
+                                  float *cf) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)gy * pitch) return;
     int pb = (int)(idx / pitch), pa = (int)(idx - (long long)pb * pitch);
@@ -79,39 +103,42 @@ __global__ void ref_medium_kernel(const float *c_map, int nx, int x0, int y0, in
         return;
     }
     int a = min(max(pa - 1, 0), nxf - 1), b = min(max(pb - 1, 0), nyf - 1);
-    int X = x0 + a / 2, Y = y0 + b / 2, ox = a & 1, oy = b & 1, cnt = 0;
+    int X = x0n + a / 2, Y = y0n + b / 2, ox = a & 1, oy = b & 1, cnt = 0;
     double s = 0.0;
     for (int dy = 0; dy <= oy; dy++)
         for (int dx = 0; dx <= ox; dx++) {
-            s += (double)c_map[(long long)(Y + dy) * nx + X + dx];
+            s += (double)pc[(long long)(Y + dy) * pnx + X + dx];
             cnt++;
         }
-    float cf = (float)(s / cnt);
-    double eta = (double)cf * inv_cref;
+    float c = (float)(s / cnt);
+    double eta = (double)c * inv_cref;
     if (eta > 1.0) eta = 1.0;
     eta2[idx] = (float)(eta * eta);
+    if (cf && pa == a + 1 && pb == b + 1) cf[(long long)b * nxf + a] = c;
 }
 
-// raw fine state g = g^eq(p / c_s^2, 0), p = bilinear interpolation of the coarse p0
+// raw fine state g = g^eq(p / c_s^2, 0), p = bilinear interpolation of the parent's
+// pressure pp [..][pnx] (node coordinates; nullptr: zero); pf gets p at the real nodes
 template <int Q>
-__global__ void ref_init_fine_kernel(StepArgs af, const float *p0, int nx, int x0, int y0,
-                                     int nxf, int nyf) {
+__global__ void ref_init_fine_kernel(StepArgs af, const float *pp, int pnx, int x0n, int y0n,
+                                     int nxf, int nyf, float *pf) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= af.plane) return;
     int pb = (int)(idx / af.pitch), pa = (int)(idx - (long long)pb * af.pitch);
     int a = pa - 1, b = pb - 1;
     float p = 0.f;
     bool inside = a >= 0 && a < nxf && b >= 0 && b < nyf;
-    if (inside && p0) {
-        int X = x0 + a / 2, Y = y0 + b / 2, ox = a & 1, oy = b & 1, cnt = 0;
+    if (inside && pp) {
+        int X = x0n + a / 2, Y = y0n + b / 2, ox = a & 1, oy = b & 1, cnt = 0;
         double s = 0.0;
         for (int dy = 0; dy <= oy; dy++)
             for (int dx = 0; dx <= ox; dx++) {
-                s += (double)p0[(long long)(Y + dy) * nx + X + dx];
+                s += (double)pp[(long long)(Y + dy) * pnx + X + dx];
                 cnt++;
             }
         p = (float)(s / cnt);
     }
+    if (inside && pf) pf[(long long)b * nxf + a] = p;
     float *o = static_cast<float *>(af.out);
     const float e2 = af.eta2[idx];
     for (int i = 0; i < Q; i++)
@@ -140,7 +167,7 @@ __global__ void ref_snapshot_kernel(StepArgs ac, const int2 *Ic, int nI, float *
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nI) return;
     const float *in = static_cast<const float *>(ac.in);
-    int2 X = Ic[k];  // at least one node from the coarse edges: no wrap needed
+    int2 X = Ic[k];  // at least one node from the parent's edges: no wrap needed
     for (int i = 0; i < Q; i++)
         U[(long long)k * Q + i] = pull1<Q>(in, ac.raw, 0, X.x, X.y, i, ac.nx, ac.ny, ac.pitch,
                                            ac.plane);
@@ -182,7 +209,7 @@ __global__ void ref_c2f_kernel(StepArgs af, StepArgs rs, const int4 *If, int nIf
     }
 }
 
-// fine -> coarse on I, then collide (+ sponge) and overwrite the coarse output
+// fine -> coarse on I, then collide (+ sponge) and overwrite the parent's step output
 template <int Q, bool MRT, bool PERIODIC>
 __global__ void ref_f2c_kernel(StepArgs ac, StepArgs rs, const float *fin, int fraw, int fpitch,
                                long long fplane, const int2 *Ic, int nI, int x0, int y0, int nxp,
@@ -219,35 +246,37 @@ __global__ void ref_f2c_kernel(StepArgs ac, StepArgs rs, const float *fin, int f
     for (int i = 0; i < Q; i++) out[i * ac.plane + (long long)X.y * ac.pitch + X.x] = g[i] * f;
 }
 
-// pressure at the nodes of the closed patch from the coincident fine nodes
+// context-grid pressure at the coarse nodes covered by a level, from its coincident nodes:
+// coarse (X, Y) -> level node (A X + bx, A Y + by), stored at (+1, +1)
 template <int Q>
-__global__ void ref_overlay_kernel(StepArgs af, float *p, int nx, int x0, int y0, int nxp,
-                                   int nyp) {
+__global__ void ref_overlay_kernel(StepArgs af, float *p, int nx, int X0, int Y0, int w, int h,
+                                   int A, int bx, int by) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    int w = nxp + 1;
-    if (k >= w * (nyp + 1)) return;
-    int ca = k % w, cb = k / w;
-    int fa = 1 + 2 * ca, fb = 1 + 2 * cb;
+    if (k >= w * h) return;
+    const int X = X0 + k % w, Y = Y0 + k / w;
+    const int fa = 1 + A * X + bx, fb = 1 + A * Y + by;
     const float *in = static_cast<const float *>(af.in);
     float rho = 0.f;
     for (int i = 0; i < Q; i++)
         rho += pull1<Q>(in, af.raw, 0, fa, fb, i, 1 << 30, 1 << 30, af.pitch, af.plane);
-    p[(long long)(y0 + cb) * nx + (x0 + ca)] =
-        cs2_of<Q>(af.eta2[(long long)fb * af.pitch + fa], af) * rho;
+    p[(long long)Y * nx + X] = cs2_of<Q>(af.eta2[(long long)fb * af.pitch + fa], af) * rho;
 }
 
 int blocks_for(long long n) { return (int)((n + 255) / 256); }
 
-StepArgs fine_args(const lb_ctx *ctx) {
-    const lb_refine *R = ctx->ref;
+// step arguments of refined level R: its own eta^2 plane and rates; no sponge, source or
+// receivers (the caller adds receivers)
+StepArgs level_args(const lb_ctx *ctx, const lb_refine *R) {
     StepArgs a = base_args(ctx);
     a.eta2 = R->eta2;
-    a.mid = nullptr;  // the fine grid reads its own eta^2 plane
+    a.mid = nullptr;  // refined levels read their own eta^2 plane
     a.mid_tab = nullptr;
-    a.omega = R->omega_f;  // viscosity-continuous fine relaxation
+    a.omega = R->omega_f;  // viscosity-continuous relaxation of this level
     for (int k = 0; k < 9; k++) a.s[k] = R->s_f[k];
     a.nx = R->gx;
     a.ny = R->gy;
+    a.ny3 = R->gy;
+    a.nz = 1;
     a.pitch = R->pitch;
     a.plane = (long long)R->gy * R->pitch;
     a.segs = (R->gx + kSitesPerWarp - 1) / kSitesPerWarp;
@@ -271,32 +300,68 @@ StepArgs rescale_args(StepArgs a, float omega, const float *s) {
 }
 
 template <int Q, bool MRT>
-void c2f_q(lb_ctx *ctx, const StepArgs &af, const float *Ua, const float *Ub, float alpha) {
-    lb_refine *R = ctx->ref;
+void c2f_q(lb_ctx *ctx, lb_refine *R, const StepArgs &af, const float *Ua, const float *Ub,
+           float alpha) {
     ref_c2f_kernel<Q, MRT><<<blocks_for(R->nIf), 256, 0, ctx->stream>>>(
         af, rescale_args(af, R->c2f_omega, R->c2f_s), R->If, R->nIf, Ua, Ub, alpha, R->nxf, R->nyf);
 }
 
-void launch_c2f(lb_ctx *ctx, const float *Ua, const float *Ub, float alpha) {
-    lb_refine *R = ctx->ref;
-    StepArgs af = fine_args(ctx);
+void launch_c2f(lb_ctx *ctx, lb_refine *R, const float *Ua, const float *Ub, float alpha) {
+    StepArgs af = level_args(ctx, R);
     af.in = R->pop[R->cur];
     af.raw = R->raw ? 1 : 0;
     const bool mrt = ctx->cfg.collision == LB_MRT;
     if (ctx->Q == 9) {
-        if (mrt) c2f_q<9, true>(ctx, af, Ua, Ub, alpha); else c2f_q<9, false>(ctx, af, Ua, Ub, alpha);
+        if (mrt) c2f_q<9, true>(ctx, R, af, Ua, Ub, alpha); else c2f_q<9, false>(ctx, R, af, Ua, Ub, alpha);
     } else {
-        if (mrt) c2f_q<5, true>(ctx, af, Ua, Ub, alpha); else c2f_q<5, false>(ctx, af, Ua, Ub, alpha);
+        if (mrt) c2f_q<5, true>(ctx, R, af, Ua, Ub, alpha); else c2f_q<5, false>(ctx, R, af, Ua, Ub, alpha);
     }
 }
 
-// one fine step (pull from pop[cur], store into pop[cur ^ 1]); receivers at trace row `row`
-void launch_fine_step(lb_ctx *ctx, float *trace_row) {
-    lb_refine *R = ctx->ref;
-    StepArgs af = fine_args(ctx);
+// snapshot of the parent's populations on R's interface, from the parent's step input
+void launch_snapshot(lb_ctx *ctx, const StepArgs &ap, lb_refine *R, float *U) {
+    if (ctx->Q == 9)
+        ref_snapshot_kernel<9><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(ap, R->Ic, R->nI, U);
+    else
+        ref_snapshot_kernel<5><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(ap, R->Ic, R->nI, U);
+}
+
+template <int Q, bool MRT>
+void f2c_q(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, const float *fin,
+           int fraw) {
+    long long fplane = (long long)R->gy * R->pitch;
+    if (periodic)
+        ref_f2c_kernel<Q, MRT, true><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(
+            ap, rescale_args(ap, R->f2c_omega, R->f2c_s), fin, fraw, R->pitch, fplane, R->Ic,
+            R->nI, R->x0, R->y0, R->nxp, R->nyp);
+    else
+        ref_f2c_kernel<Q, MRT, false><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(
+            ap, rescale_args(ap, R->f2c_omega, R->f2c_s), fin, fraw, R->pitch, fplane, R->Ic,
+            R->nI, R->x0, R->y0, R->nxp, R->nyp);
+}
+
+// correction of the parent's step output on R's interface from R's state fin
+void launch_f2c(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, const float *fin,
+                int fraw) {
+    const bool mrt = ctx->cfg.collision == LB_MRT;
+    if (ctx->Q == 9) {
+        if (mrt) f2c_q<9, true>(ctx, ap, periodic, R, fin, fraw); else f2c_q<9, false>(ctx, ap, periodic, R, fin, fraw);
+    } else {
+        if (mrt) f2c_q<5, true>(ctx, ap, periodic, R, fin, fraw); else f2c_q<5, false>(ctx, ap, periodic, R, fin, fraw);
+    }
+}
+
+void child_steps(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, float *trace_row,
+                 long long T);
+
+// one step t of refined level R (pull from pop[cur], store into pop[cur ^ 1]), with every
+// level nested in it; receivers of R at trace row `trace_row`
+void level_step(lb_ctx *ctx, lb_refine *R, float *trace_row, long long t) {
+    StepArgs af = level_args(ctx, R);
     af.in = R->pop[R->cur];
     af.out = R->pop[R->cur ^ 1];
     af.raw = R->raw ? 1 : 0;
+    af.t = t;
     int rec_blocks = 0;
     if (trace_row && R->nrec_f > 0) {
         af.rec = R->rec_f;
@@ -307,70 +372,103 @@ void launch_fine_step(lb_ctx *ctx, float *trace_row) {
     }
     StepFn fn = pick_step_for(ctx->Q, ctx->cfg.collision == LB_MRT, false, LB_F32);
     fn<<<af.main_blocks + rec_blocks, kThreads, 0, ctx->stream>>>(af);
+    if (R->sub) child_steps(ctx, af, false, R->sub, trace_row, t);
     R->cur ^= 1;
     R->raw = false;
 }
 
-void launch_snapshot(lb_ctx *ctx, const void *coarse_in, bool raw, float *U) {
-    lb_refine *R = ctx->ref;
-    StepArgs ac = base_args(ctx);
-    ac.in = coarse_in;
-    ac.raw = raw ? 1 : 0;
+// The part of the parent's step T that advances its patch R from 2T - 1 to 2T + 1: snapshot
+// U(T), two steps of R with the coarse-to-fine transfers, and the correction of the parent's
+// step output (ap: the parent's step arguments, in / out / raw of step T).
+void child_steps(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, float *trace_row,
+                 long long T) {
+    float *Ucur = R->U[T & 1], *Uprev = R->U[(T + 1) & 1];
+    launch_snapshot(ctx, ap, R, Ucur);
+    if (T >= 1) {
+        launch_c2f(ctx, R, Uprev, Ucur, 0.5f);
+        level_step(ctx, R, nullptr, 2 * T - 1);
+    }
+    launch_c2f(ctx, R, Ucur, Ucur, 1.0f);
+    const float *fin_last = static_cast<const float *>(R->pop[R->cur]);
+    const int fraw = R->raw ? 1 : 0;
+    level_step(ctx, R, trace_row, 2 * T);
+    launch_f2c(ctx, ap, periodic, R, fin_last, fraw);
+}
+
+void launch_overlay(lb_ctx *ctx, lb_refine *R, float *p) {
+    if (R->onx <= 0 || R->ony <= 0) return;
+    StepArgs af = level_args(ctx, R);
+    af.in = R->pop[R->cur];
+    af.raw = R->raw ? 1 : 0;
+    const int cnt = R->onx * R->ony;
     if (ctx->Q == 9)
-        ref_snapshot_kernel<9><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(ac, R->Ic, R->nI, U);
+        ref_overlay_kernel<9><<<blocks_for(cnt), 256, 0, ctx->stream>>>(
+            af, p, ctx->nx, R->ox0, R->oy0, R->onx, R->ony, R->oA, R->obx, R->oby);
     else
-        ref_snapshot_kernel<5><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(ac, R->Ic, R->nI, U);
+        ref_overlay_kernel<5><<<blocks_for(cnt), 256, 0, ctx->stream>>>(
+            af, p, ctx->nx, R->ox0, R->oy0, R->onx, R->ony, R->oA, R->obx, R->oby);
 }
 
-template <int Q, bool MRT>
-void f2c_q(lb_ctx *ctx, const StepArgs &ac, const float *fin, int fraw) {
-    lb_refine *R = ctx->ref;
-    long long fplane = (long long)R->gy * R->pitch;
-    if (ctx->cfg.boundary == LB_PERIODIC)
-        ref_f2c_kernel<Q, MRT, true><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(
-            ac, rescale_args(ac, R->f2c_omega, R->f2c_s), fin, fraw, R->pitch, fplane, R->Ic,
-            R->nI, R->x0, R->y0, R->nxp, R->nyp);
-    else
-        ref_f2c_kernel<Q, MRT, false><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(
-            ac, rescale_args(ac, R->f2c_omega, R->f2c_s), fin, fraw, R->pitch, fplane, R->Ic,
-            R->nI, R->x0, R->y0, R->nxp, R->nyp);
-}
-
-void launch_f2c(lb_ctx *ctx, const StepArgs &ac, const float *fin, int fraw) {
-    bool mrt = ctx->cfg.collision == LB_MRT;
-    if (ctx->Q == 9) {
-        if (mrt) f2c_q<9, true>(ctx, ac, fin, fraw); else f2c_q<9, false>(ctx, ac, fin, fraw);
-    } else {
-        if (mrt) f2c_q<5, true>(ctx, ac, fin, fraw); else f2c_q<5, false>(ctx, ac, fin, fraw);
+// Bring patch R (of a parent at time T, step arguments ap: in / raw) to time 2T without
+// committing, write the context-grid pressure of the nodes it covers, then recurse.
+void peek_level(lb_ctx *ctx, const StepArgs &ap, lb_refine *R, long long T, float *p) {
+    float *Ucur = R->U[2], *Uprev = R->U[(T + 1) & 1];
+    launch_snapshot(ctx, ap, R, Ucur);
+    if (T >= 1) {
+        launch_c2f(ctx, R, Uprev, Ucur, 0.5f);
+        level_step(ctx, R, nullptr, 2 * T - 1);
+    }
+    launch_c2f(ctx, R, Ucur, Ucur, 1.0f);
+    launch_overlay(ctx, R, p);
+    if (R->sub) {
+        StepArgs af = level_args(ctx, R);
+        af.in = R->pop[R->cur];
+        af.raw = R->raw ? 1 : 0;
+        peek_level(ctx, af, R->sub, 2 * T, p);
     }
 }
 
+// floor(a / b) for b > 0
+int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
 }  // namespace
 
-lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev) {
-    const lb_patch P = cfg->patches[0];
+// Sets up one refined level: patch P of the parent grid (the context grid when parent is
+// null).  Parent speeds pc [..][pnx] in the parent's node coordinates.
+static lb_status setup_level(lb_ctx *ctx, const lb_config *cfg, lb_refine *parent,
+                             const lb_patch &P, const float *pc, int pnx, bool has_sub,
+                             lb_refine **out) {
+    const int pn_x = parent ? parent->nxf : ctx->nx, pn_y = parent ? parent->nyf : ctx->ny;
     if (P.ratio != 2) return fail(ctx, LB_EINVAL, "patch ratio must be 2");
-    if (cfg->storage != LB_F32) return fail(ctx, LB_EINVAL, "refinement needs FP32 storage");
-    if (P.nx_c < 1 || P.ny_c < 1 || P.x0 < 1 || P.y0 < 1 || P.x0 + P.nx_c > ctx->nx - 2 ||
-        P.y0 + P.ny_c > ctx->ny - 2)
-        return fail(ctx, LB_EINVAL, "patch must lie inside the grid with a 1-node margin");
+    if (P.nx_c < 1 || P.ny_c < 1 || P.x0 < 1 || P.y0 < 1 || P.x0 + P.nx_c > pn_x - 2 ||
+        P.y0 + P.ny_c > pn_y - 2)
+        return fail(ctx, LB_EINVAL,
+                    parent ? "a nested patch must lie inside the fine grid above it with a "
+                             "1-node margin"
+                           : "patch must lie inside the grid with a 1-node margin");
     lb_refine *R = new lb_refine();
-    ctx->ref = R;
-    {  // fine rates and rescale factors (tau_f - 1/2 = 2 (tau_c - 1/2), per relaxed moment)
+    *out = R;
+    R->depth = parent ? parent->depth + 1 : 1;
+    {  // rates of this level (tau_f - 1/2 = 2 (tau_c - 1/2) per relaxed moment) and rescales
         auto fine_tau = [](double tc) { return 0.5 + 2.0 * (tc - 0.5); };
-        const double tc = cfg->tau, tf = fine_tau(tc);
+        const double tc = parent ? parent->tau_f : cfg->tau, tf = fine_tau(tc);
+        R->tau_f = tf;
         R->omega_f = (float)(1.0 / tf);
         R->c2f_omega = (float)(1.0 - tf / (2.0 * tc));
         R->f2c_omega = (float)(1.0 - 2.0 * tc / tf);
         for (int k = 0; k < 9; k++) {
-            const double tck = 1.0 / cfg->s[k], tfk = fine_tau(tck);
+            const double tck = parent ? parent->stau_f[k] : 1.0 / cfg->s[k], tfk = fine_tau(tck);
+            R->stau_f[k] = tfk;
             R->s_f[k] = (float)(1.0 / tfk);
             R->c2f_s[k] = (float)(1.0 - tfk / (2.0 * tck));
             R->f2c_s[k] = (float)(1.0 - 2.0 * tck / tfk);
         }
     }
-    R->x0 = P.x0;
-    R->y0 = P.y0;
+    const int off = parent ? 1 : 0;  // parent storage = parent node + off
+    R->x0n = P.x0;
+    R->y0n = P.y0;
+    R->x0 = P.x0 + off;
+    R->y0 = P.y0 + off;
     R->nxp = P.nx_c;
     R->nyp = P.ny_c;
     R->nxf = 2 * P.nx_c + 1;
@@ -378,6 +476,21 @@ lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev
     R->gx = R->nxf + 2;
     R->gy = R->nyf + 2;
     R->pitch = round_up(R->gx, 32);
+    // the coarse nodes this level covers: parent node a_p = A_p X + b_p, own node
+    // a = 2 (a_p - x0n)
+    {
+        const int Ap = parent ? parent->oA : 1, bxp = parent ? parent->obx : 0,
+                  byp = parent ? parent->oby : 0;
+        R->oA = 2 * Ap;
+        R->obx = 2 * (bxp - P.x0);
+        R->oby = 2 * (byp - P.y0);
+        const int xl = -floordiv(-(P.x0 - bxp), Ap), xh = floordiv(P.x0 + P.nx_c - bxp, Ap);
+        const int yl = -floordiv(-(P.y0 - byp), Ap), yh = floordiv(P.y0 + P.ny_c - byp, Ap);
+        R->ox0 = xl;
+        R->oy0 = yl;
+        R->onx = std::max(0, xh - xl + 1);
+        R->ony = std::max(0, yh - yl + 1);
+    }
     const size_t plane = (size_t)R->gy * R->pitch;
     const int Q = ctx->Q;
     for (int b = 0; b < 2; b++) {
@@ -387,10 +500,19 @@ lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev
     }
     R->eta2 = static_cast<float *>(dev_alloc(ctx, plane * 4));
     if (!R->eta2) return fail(ctx, LB_ENOMEM, "fine medium");
+    if (has_sub) {
+        R->cf = static_cast<float *>(dev_alloc(ctx, (size_t)R->nxf * R->nyf * 4));
+        R->pf = static_cast<float *>(dev_alloc(ctx, (size_t)R->nxf * R->nyf * 4));
+        if (!R->cf || !R->pf) return fail(ctx, LB_ENOMEM, "nested patch medium");
+    }
+    if (R->depth >= 2) {
+        R->bak = dev_alloc(ctx, (size_t)Q * plane * 4);
+        if (!R->bak) return fail(ctx, LB_ENOMEM, "nested patch peek buffer");
+    }
     ref_medium_kernel<<<blocks_for((long long)plane), 256, 0, ctx->stream>>>(
-        c_map_dev, ctx->nx, R->x0, R->y0, R->nxf, R->nyf, R->gx, R->gy, R->pitch,
-        1.0 / ctx->cfg.c_ref, R->eta2);
-    // interface node lists
+        pc, pnx, R->x0n, R->y0n, R->nxf, R->nyf, R->gx, R->gy, R->pitch, 1.0 / ctx->cfg.c_ref,
+        R->eta2, R->cf);
+    // interface node lists (parent storage coordinates)
     std::vector<int2> Ic;
     std::vector<int> idx((size_t)(R->nxp + 1) * (R->nyp + 1), -1);
     for (int Y = R->y0; Y <= R->y0 + R->nyp; Y++)
@@ -419,12 +541,39 @@ lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev
     for (int s = 0; s < 3; s++) R->U[s] = static_cast<float *>(dev_alloc(ctx, (size_t)R->nI * Q * 4));
     if (!R->Ic || !R->If || !R->U[0] || !R->U[1] || !R->U[2])
         return fail(ctx, LB_ENOMEM, "interface buffers");
+    if (R->depth >= 2) {
+        for (int s = 0; s < 2; s++) {
+            R->Ubak[s] = static_cast<float *>(dev_alloc(ctx, (size_t)R->nI * Q * 4));
+            if (!R->Ubak[s]) return fail(ctx, LB_ENOMEM, "nested patch peek buffer");
+        }
+    }
     cudaMemcpyAsync(R->Ic, Ic.data(), Ic.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(R->If, If.data(), If.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream);
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);  // the host vectors go out of scope
     if (e != cudaSuccess) return cuda_fail(ctx, e, "refinement setup");
-    ctx->refined = true;
     return check_launch(ctx, "refinement setup");
+}
+
+lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev) {
+    if (cfg->storage != LB_F32) return fail(ctx, LB_EINVAL, "refinement needs FP32 storage");
+    lb_refine *parent = nullptr;
+    const float *pc = c_map_dev;
+    int pnx = ctx->nx;
+    for (int k = 0; k < cfg->n_patches; k++) {
+        lb_refine *R = nullptr;
+        lb_status st = setup_level(ctx, cfg, parent, cfg->patches[k], pc, pnx,
+                                   k + 1 < cfg->n_patches, &R);
+        if (parent)
+            parent->sub = R;
+        else
+            ctx->ref = R;
+        if (st != LB_OK) return st;
+        parent = R;
+        pc = R->cf;
+        pnx = R->nxf;
+    }
+    ctx->refined = true;
+    return LB_OK;
 }
 
 void refine_destroy(lb_ctx *ctx) {
@@ -437,66 +586,77 @@ bool refine_contains(const lb_ctx *ctx, int x, int y) {
     return R && x >= R->x0 && x <= R->x0 + R->nxp && y >= R->y0 && y <= R->y0 + R->nyp;
 }
 
+static lb_status upload_list(lb_ctx *ctx, const std::vector<int2> &v, const std::vector<int> &c,
+                             int2 **dv, int **dc) {
+    *dv = static_cast<int2 *>(dev_alloc(ctx, std::max<size_t>(1, v.size()) * sizeof(int2)));
+    *dc = static_cast<int *>(dev_alloc(ctx, std::max<size_t>(1, c.size()) * sizeof(int)));
+    if (!*dv || !*dc) return fail(ctx, LB_ENOMEM, "receiver lists");
+    if (!v.empty()) {
+        cudaMemcpyAsync(*dv, v.data(), v.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemcpyAsync(*dc, c.data(), c.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+    }
+    return LB_OK;
+}
+
+// each receiver is recorded on the deepest level whose closed patch holds its node
 lb_status refine_set_receivers(lb_ctx *ctx, const int *xy, int nrec) {
-    lb_refine *R = ctx->ref;
-    std::vector<int2> rc, rf;
-    std::vector<int> cc, cf;
+    std::vector<lb_refine *> lv;
+    for (lb_refine *R = ctx->ref; R; R = R->sub) lv.push_back(R);
+    std::vector<std::vector<int2>> pos(lv.size() + 1);
+    std::vector<std::vector<int>> col(lv.size() + 1);
     for (int r = 0; r < nrec; r++) {
-        int x = xy[2 * r], y = xy[2 * r + 1];
-        if (refine_contains(ctx, x, y)) {
-            rf.push_back(make_int2(1 + 2 * (x - R->x0), 1 + 2 * (y - R->y0)));
-            cf.push_back(r);
-        } else {
-            rc.push_back(make_int2(x, y));
-            cc.push_back(r);
+        int a = xy[2 * r], b = xy[2 * r + 1];  // node coordinates of the current level
+        size_t L = 0;
+        while (L < lv.size()) {
+            const lb_refine *R = lv[L];
+            if (a < R->x0n || a > R->x0n + R->nxp || b < R->y0n || b > R->y0n + R->nyp) break;
+            a = 2 * (a - R->x0n);
+            b = 2 * (b - R->y0n);
+            L++;
         }
+        pos[L].push_back(L == 0 ? make_int2(a, b) : make_int2(a + 1, b + 1));
+        col[L].push_back(r);
     }
-    R->nrec_c = (int)rc.size();
-    R->nrec_f = (int)rf.size();
-    R->rec_c = static_cast<int2 *>(dev_alloc(ctx, std::max<size_t>(1, rc.size()) * sizeof(int2)));
-    R->rec_f = static_cast<int2 *>(dev_alloc(ctx, std::max<size_t>(1, rf.size()) * sizeof(int2)));
-    R->col_c = static_cast<int *>(dev_alloc(ctx, std::max<size_t>(1, cc.size()) * sizeof(int)));
-    R->col_f = static_cast<int *>(dev_alloc(ctx, std::max<size_t>(1, cf.size()) * sizeof(int)));
-    if (!R->rec_c || !R->rec_f || !R->col_c || !R->col_f)
-        return fail(ctx, LB_ENOMEM, "receiver lists");
-    if (!rc.empty()) {
-        cudaMemcpyAsync(R->rec_c, rc.data(), rc.size() * sizeof(int2), cudaMemcpyHostToDevice,
-                        ctx->stream);
-        cudaMemcpyAsync(R->col_c, cc.data(), cc.size() * sizeof(int), cudaMemcpyHostToDevice,
-                        ctx->stream);
+    lb_refine *R1 = lv[0];
+    R1->nrec_c = (int)pos[0].size();
+    lb_status st = upload_list(ctx, pos[0], col[0], &R1->rec_c, &R1->col_c);
+    for (size_t L = 1; st == LB_OK && L <= lv.size(); L++) {
+        lv[L - 1]->nrec_f = (int)pos[L].size();
+        st = upload_list(ctx, pos[L], col[L], &lv[L - 1]->rec_f, &lv[L - 1]->col_f);
     }
-    if (!rf.empty()) {
-        cudaMemcpyAsync(R->rec_f, rf.data(), rf.size() * sizeof(int2), cudaMemcpyHostToDevice,
-                        ctx->stream);
-        cudaMemcpyAsync(R->col_f, cf.data(), cf.size() * sizeof(int), cudaMemcpyHostToDevice,
-                        ctx->stream);
-    }
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);  // the host vectors go out of scope
+    if (st != LB_OK) return st;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "receiver upload");
     return LB_OK;
 }
 
 lb_status refine_after_set_state(lb_ctx *ctx, const float *p0_dev) {
-    lb_refine *R = ctx->ref;
-    StepArgs af = fine_args(ctx);
-    R->cur = 0;
-    af.out = R->pop[0];
-    if (ctx->Q == 9)
-        ref_init_fine_kernel<9><<<blocks_for(af.plane), 256, 0, ctx->stream>>>(
-            af, p0_dev, ctx->nx, R->x0, R->y0, R->nxf, R->nyf);
-    else
-        ref_init_fine_kernel<5><<<blocks_for(af.plane), 256, 0, ctx->stream>>>(
-            af, p0_dev, ctx->nx, R->x0, R->y0, R->nxf, R->nyf);
-    R->raw = true;
+    const float *pp = p0_dev;
+    int pnx = ctx->nx;
+    for (lb_refine *R = ctx->ref; R; R = R->sub) {
+        StepArgs af = level_args(ctx, R);
+        R->cur = 0;
+        af.out = R->pop[0];
+        float *pf = (R->sub && pp) ? R->pf : nullptr;
+        if (ctx->Q == 9)
+            ref_init_fine_kernel<9><<<blocks_for(af.plane), 256, 0, ctx->stream>>>(
+                af, pp, pnx, R->x0n, R->y0n, R->nxf, R->nyf, pf);
+        else
+            ref_init_fine_kernel<5><<<blocks_for(af.plane), 256, 0, ctx->stream>>>(
+                af, pp, pnx, R->x0n, R->y0n, R->nxf, R->nyf, pf);
+        R->raw = true;
+        pp = pf;
+        pnx = R->nxf;
+    }
     return check_launch(ctx, "refined initial state");
 }
 
 lb_status refine_step(lb_ctx *ctx, int n) {
     lb_refine *R = ctx->ref;
     StepFn coarse_fn = pick_step(ctx);
+    const bool periodic = ctx->cfg.boundary == LB_PERIODIC;
     for (int k = 0; k < n; k++) {
         const long long T = ctx->t;
-        float *Ucur = R->U[T & 1], *Uprev = R->U[(T + 1) & 1];
         long long row = T - ctx->t_rec0;
         float *trace_row = (ctx->trace && row >= 0 && row < ctx->trace_cap)
                                ? ctx->trace + row * ctx->nrec : nullptr;
@@ -512,16 +672,7 @@ lb_status refine_step(lb_ctx *ctx, int n) {
         ac.trace_row = R->nrec_c > 0 ? trace_row : nullptr;
         int rec_blocks = ac.trace_row ? (R->nrec_c + kThreads - 1) / kThreads : 0;
         coarse_fn<<<ac.main_blocks + rec_blocks, kThreads, 0, ctx->stream>>>(ac);
-        launch_snapshot(ctx, ac.in, ctx->raw, Ucur);
-        if (T >= 1) {
-            launch_c2f(ctx, Uprev, Ucur, 0.5f);
-            launch_fine_step(ctx, nullptr);
-        }
-        launch_c2f(ctx, Ucur, Ucur, 1.0f);
-        const float *fin_last = static_cast<const float *>(R->pop[R->cur]);
-        const int fraw = R->raw ? 1 : 0;
-        launch_fine_step(ctx, trace_row);
-        launch_f2c(ctx, ac, fin_last, fraw);
+        child_steps(ctx, ac, periodic, R, trace_row, T);
         ctx->cur ^= 1;
         ctx->raw = false;
         ctx->t += 1;
@@ -529,33 +680,44 @@ lb_status refine_step(lb_ctx *ctx, int n) {
     return check_launch(ctx, "refined step");
 }
 
-// Pressure at the current time inside the closed patch.  The fine state at
-// fine time 2t does not exist yet between steps, so the coupling and the fine
-// sub-steps of step t are replayed into the buffers they will overwrite
-// anyway (the spare fine buffer, its ghost ring, and the third U slot).
+// Pressure at the current time inside the closed patches.  The fine states at the
+// current time do not exist yet between steps, so the coupling and the patch sub-steps of
+// step t are replayed into the buffers they will overwrite anyway (the spare buffer of
+// each level, its ghost ring, and the third U slot).  A nested level also runs its own
+// sub-steps during the replay, which overwrite its input buffer and interface snapshots:
+// those are saved before and restored after.
 lb_status refine_overlay_pressure(lb_ctx *ctx, float *p_dev) {
-    lb_refine *R = ctx->ref;
-    const long long T = ctx->t;
-    float *Ucur = R->U[2], *Uprev = R->U[(T + 1) & 1];
-    launch_snapshot(ctx, ctx->pop[ctx->cur], ctx->raw, Ucur);
-    const int cur0 = R->cur;
-    const bool raw0 = R->raw;
-    if (T >= 1) {
-        launch_c2f(ctx, Uprev, Ucur, 0.5f);
-        launch_fine_step(ctx, nullptr);
+    std::vector<lb_refine *> lv;
+    for (lb_refine *R = ctx->ref; R; R = R->sub) lv.push_back(R);
+    std::vector<int> cur0(lv.size());
+    std::vector<char> raw0(lv.size());
+    const int Q = ctx->Q;
+    cudaError_t e = cudaSuccess;
+    for (size_t L = 0; L < lv.size(); L++) {
+        lb_refine *R = lv[L];
+        cur0[L] = R->cur;
+        raw0[L] = R->raw ? 1 : 0;
+        if (R->depth < 2 || e != cudaSuccess) continue;
+        const size_t bytes = (size_t)Q * R->gy * R->pitch * 4, ub = (size_t)R->nI * Q * 4;
+        e = cudaMemcpyAsync(R->bak, R->pop[R->cur], bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        for (int s = 0; s < 2 && e == cudaSuccess; s++)
+            e = cudaMemcpyAsync(R->Ubak[s], R->U[s], ub, cudaMemcpyDeviceToDevice, ctx->stream);
     }
-    launch_c2f(ctx, Ucur, Ucur, 1.0f);
-    StepArgs af = fine_args(ctx);
-    af.in = R->pop[R->cur];
-    af.raw = R->raw ? 1 : 0;
-    int cnt = (R->nxp + 1) * (R->nyp + 1);
-    if (ctx->Q == 9)
-        ref_overlay_kernel<9><<<blocks_for(cnt), 256, 0, ctx->stream>>>(af, p_dev, ctx->nx, R->x0,
-                                                                      R->y0, R->nxp, R->nyp);
-    else
-        ref_overlay_kernel<5><<<blocks_for(cnt), 256, 0, ctx->stream>>>(af, p_dev, ctx->nx, R->x0,
-                                                                      R->y0, R->nxp, R->nyp);
-    R->cur = cur0;  // the replay committed nothing
-    R->raw = raw0;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refined pressure: save");
+    StepArgs ac = base_args(ctx);
+    ac.in = ctx->pop[ctx->cur];
+    ac.raw = ctx->raw ? 1 : 0;
+    peek_level(ctx, ac, ctx->ref, ctx->t, p_dev);
+    for (size_t L = 0; L < lv.size(); L++) {  // the replay committed nothing
+        lb_refine *R = lv[L];
+        R->cur = cur0[L];
+        R->raw = raw0[L] != 0;
+        if (R->depth < 2 || e != cudaSuccess) continue;
+        const size_t bytes = (size_t)Q * R->gy * R->pitch * 4, ub = (size_t)R->nI * Q * 4;
+        e = cudaMemcpyAsync(R->pop[R->cur], R->bak, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        for (int s = 0; s < 2 && e == cudaSuccess; s++)
+            e = cudaMemcpyAsync(R->U[s], R->Ubak[s], ub, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refined pressure: restore");
     return check_launch(ctx, "refined pressure");
 }

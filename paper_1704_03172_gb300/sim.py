@@ -76,10 +76,13 @@ class LBSim:
             self._cmap_keep = host
             cfg.c_map = host.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         if patch is not None:
-            self._patch = lbac.lb_patch(*[int(v) for v in patch], 2) if len(patch) == 4 else \
-                lbac.lb_patch(*[int(v) for v in patch])
-            cfg.patches = ctypes.pointer(self._patch)
-            cfg.n_patches = 1
+            # one patch (x0, y0, nx_c, ny_c[, ratio]) or a list of nested patches, each in the
+            # node coordinates of the fine grid of the one before it
+            plist = list(patch) if len(patch) and hasattr(patch[0], "__len__") else [patch]
+            self._patch = (lbac.lb_patch * len(plist))(
+                *[lbac.lb_patch(*[int(v) for v in q], *([2] if len(q) == 4 else [])) for q in plist])
+            cfg.patches = ctypes.cast(self._patch, ctypes.POINTER(lbac.lb_patch))
+            cfg.n_patches = len(plist)
         cfg.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
         if torch_allocator:
             dev, strm = self.device, self.stream

@@ -168,6 +168,18 @@ def refined_block_workload(n=2048, nrec=256, steps=4000):
                 sponge_sigma_max=0.1, block=(b0, b0, bw, bw))
 
 
+def refined_nested_workload(n=2048, nrec=256, steps=4000):
+    """The grid-refinement workload with a second, nested patch (ratio 4 to the coarse grid,
+    "multiples of 2", Sec. 4): the central half of the first patch's fine grid, inside the
+    slow block, refined by 2 again.  The nested patch is given in the first fine grid's node
+    coordinates."""
+    wl = refined_block_workload(n, nrec, steps)
+    nxf = 2 * wl["patch"][2] + 1
+    q = (nxf - 1) // 4
+    wl["patches"] = [wl["patch"], (q, q, 2 * q, 2 * q)]
+    return wl
+
+
 # --- served shot stream ---------------------------------------------------------------
 
 SERVED_SIZES = (256, 512, 1024, 2048)

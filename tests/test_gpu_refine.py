@@ -135,3 +135,99 @@ def test_source_inside_patch_is_rejected(sim_cls):
     with pytest.raises(lbac.LBError):
         sim.set_source(25, 25, [1.0, 2.0])
     sim.close()
+
+
+# ---- nested patches (ratio 4 and 8 through levels of 2; "multiples of 2", Sec. 4)
+
+NESTED = [
+    # Q, collision, tau, s, periodic, heterogeneous, nested patches after the first
+    (5, "bgk", 0.5, None, False, False, [(12, 14, 30, 36)]),
+    (5, "mrt", 0.5, [1.0, 1.0, 1.0, 1.4, 1.7], False, True, [(12, 14, 30, 36)]),
+    (5, "bgk", 0.8, None, True, True, [(12, 14, 30, 36)]),
+    (9, "bgk", 0.7, None, False, True, [(12, 14, 30, 36)]),
+    (9, "mrt", 0.5, [1.0, 1.0, 1.0, 2.0, 2.0, 2.0, 1.0, 1.0, 2.0], True, False, [(12, 14, 30, 36)]),
+    (5, "mrt", 0.5, [1.3, 0.8, 0.8, 2.0, 2.0], False, True, [(12, 14, 30, 36), (10, 12, 20, 24)]),
+]
+
+
+@pytest.mark.parametrize("Q,coll,tau,s,periodic,hetero,inner", NESTED)
+def test_nested_refined_matches_oracle(sim_cls, oracle_mod, Q, coll, tau, s, periodic, hetero,
+                                       inner):
+    nx, ny, steps = 96, 80, 60
+    c = W.random_medium(nx, ny, 23, 0.6, 1.0) if hetero else W.uniform_map(nx, ny, 1.0)
+    patch = (40, 22, 30, 36)
+    wav = W.ricker(steps, 0.06)
+    # outside / on the first interface / level 1 only / on the nested interface / inside the
+    # nested patch / its corner / bottom edge of the first patch
+    rec = np.array([[20, 40], [40, 40], [43, 41], [46, 35], [52, 38], [61, 47], [69, 30],
+                    [85, 40], [55, 22], [50, 33]], np.int32)
+    kw = dict(tau=tau, s=s, w_ref=(0.4, 0.11, 0.04), c_ref=1.0)
+    sponge = 0 if periodic else 8
+    sim = sim_cls(c, lattice=Q, collision=coll, boundary="periodic" if periodic else "zero",
+                  sponge_width=sponge, sponge_sigma_max=0.1, patch=[patch] + inner, **kw)
+    sim.set_source(15, 40, wav)
+    sim.set_receivers(rec, steps)
+    p0 = W.gaussian_pulse(nx, ny, 30, 50, 3.0, 1e-2).astype(np.float32)
+    p0 += W.gaussian_pulse(nx, ny, 52, 40, 2.0, 5e-3).astype(np.float32)  # inside the nest
+    sim.init_pressure(p0)
+    P = oracle_mod.Problem(Q, nx, ny, c, periodic=periodic, mrt=coll == "mrt",
+                           sponge_width=sponge, sponge_sigma_max=0.1,
+                           source=(15, 40, wav), receivers=rec, **kw)
+    R = oracle_mod.Refined(P, *patch)
+    for q in inner:
+        R.nest(*q)
+    R.init_pressure(p0.astype(np.float64))
+    assert rel(sim.pressure().cpu().numpy(), R.pressure()) < TOL      # time 0
+    traces = []
+    for chunk in (1, 1, 18, 40):
+        sim.step(chunk)
+        traces.append(R.run(chunk))
+        assert rel(sim.pressure().cpu().numpy(), R.pressure()) < TOL
+    tr = sim.traces().cpu().numpy()
+    sim.close()
+    ref = np.concatenate(traces)
+    assert rel(tr, ref) < TOL
+    for j in range(len(rec)):                    # every receiver, each from its own level
+        assert np.linalg.norm(tr[:, j] - ref[:, j]) <= 1e-4 * np.linalg.norm(ref[:, j]) + 1e-9
+
+
+def test_nested_patch_placement_is_checked(sim_cls):
+    c = W.uniform_map(64, 48, 1.0)
+    with pytest.raises(Exception):     # touches the edge of the level-1 grid
+        sim_cls(c, patch=[(20, 10, 16, 20), (0, 4, 10, 10)])
+    with pytest.raises(Exception):     # reaches past it
+        sim_cls(c, patch=[(20, 10, 16, 20), (20, 4, 12, 10)])
+    with pytest.raises(Exception):     # more than LB_MAX_PATCHES
+        sim_cls(c, patch=[(20, 10, 16, 20)] + [(4, 4, 8, 8)] * 3)
+    sim = sim_cls(c, patch=[(20, 10, 16, 20), (4, 4, 20, 30)])
+    sim.close()
+
+
+def test_nested_block_workload_reduced_full_length(sim_cls, oracle_mod):
+    # the nested slow-block workload on a 256^2 coarse grid, all 4000 coarse steps
+    # (16000 steps of the nested level)
+    wl = W.refined_nested_workload(256, nrec=64)
+    steps = wl["steps"]
+    sim = sim_cls(wl["c_map"], lattice=5, collision="mrt", s=wl["s"], c_ref=wl["c_ref"],
+                  sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"],
+                  patch=wl["patches"])
+    sim.set_source(*wl["source"])
+    sim.set_receivers(wl["receivers"], steps)
+    sim.init_pressure(None)
+    snap = 150
+    sim.step(snap)
+    ps = sim.pressure().cpu().numpy()
+    sim.step(steps - snap)
+    tr = sim.traces().cpu().numpy()
+    sim.close()
+    P = oracle_mod.Problem(5, 256, 256, wl["c_map"], c_ref=wl["c_ref"], mrt=True, s=wl["s"],
+                           sponge_width=wl["sponge_width"],
+                           sponge_sigma_max=wl["sponge_sigma_max"], source=wl["source"],
+                           receivers=wl["receivers"])
+    R = oracle_mod.Refined(P, *wl["patches"][0])
+    R.nest(*wl["patches"][1])
+    R.init_pressure(None)
+    t1 = R.run(snap)
+    assert rel(ps, R.pressure()) < TOL
+    t2 = R.run(steps - snap)
+    assert rel(tr, np.concatenate([t1, t2])) < TOL
