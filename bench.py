@@ -42,7 +42,7 @@ ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 # or one changed since its capture, reports null.
 NCU_TRAFFIC = {
     ("lbk::step_kernel<5,false,false,float>", True): 639.9e6,
-    ("stream_step_kernel<5,false,false,__nv_bfloat16>", True): 302.2e6,
+    ("stream_step_kernel<5,false,false,__nv_bfloat16>", True): 302.6e6,
     ("tb_kernel<5,false,false,8>", False): 703.5e6,
 }
 

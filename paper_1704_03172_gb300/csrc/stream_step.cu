@@ -10,7 +10,9 @@
 // stage's mbarrier.  While a CTA computes task k from stage k mod S, the copies
 // of the next S - 1 tasks are in flight, so the loads are decoupled from the
 // arithmetic and no register holds data waiting on DRAM.  Outputs go straight
-// from registers to HBM with 16-byte stores.
+// from registers to HBM with 16-byte stores.  For D2Q5 a dedicated producer
+// warp issues the copies and each compute warp releases a stage on its own (an
+// "empty" mbarrier per stage), so no block-wide barrier paces the loop.
 //
 // Addresses and sizes of every bulk copy are multiples of 16 bytes: rows are
 // pitch elements apart (pitch a multiple of 32 elements), a task starts at a
@@ -18,8 +20,8 @@
 // bytes; copies are clipped to [0, pitch) of the row.
 //
 // Chosen automatically for 16-bit storage on rows of >= 1024 sites, where it beats
-// the register-streaming kernel (GB300, 4096^2: BF16 D2Q5 206 -> 258 GLUPS, FP16
-// 195 -> 214, BF16 D2Q9 82 -> 128).  For FP32 the register-streaming kernel is
+// the register-streaming kernel (GB300, 4096^2: BF16 D2Q5 206 -> 271 GLUPS, FP16
+// 195 -> 214, BF16 D2Q9 82 -> 134).  For FP32 the register-streaming kernel is
 // faster (159 vs 135 GLUPS), and on narrow rows (e.g. a 256^3 D3Q7 grid) most of a
 // task's threads would idle.  Any lattice (D2Q5, D2Q9, D3Q7) can force it.
 //
@@ -247,95 +249,198 @@ __device__ __forceinline__ void compute_task(const StepArgs &a, const SArgs &s, 
 
 namespace {
 
-// Resident CTAs per SM the register budget is held to (8 warps each).
+// D2Q5 without range scales runs a dedicated producer warp next to the eight compute warps
+// (288 threads; GB300, 4096^2 BF16: 271 GLUPS against 261 with the block barrier).  The
+// register-heavier forms (D2Q9, D3Q7, FP16 with its per-population scales) keep all 64 K
+// registers for compute warps (256 threads): with a producer warp they lost 10-35 %.
+template <int Q, typename ST> constexpr bool stream_dedicated() {
+    return Q == 5 && !Scaled<ST>::value;
+}
+template <int Q, typename ST> constexpr int stream_threads() {
+    return kSThreads + (stream_dedicated<Q, ST>() ? 32 : 0);
+}
+
+// Resident CTAs per SM the register budget is held to.
 template <int Q, typename ST> constexpr int stream_min_ctas() {
-    return Q == 5   ? (sizeof(ST) == 4 ? 5 : (Scaled<ST>::value ? 3 : 4))
+    return Q == 5   ? 3
            : Q == 7 ? (sizeof(ST) == 4 ? 4 : 2)
                     : (sizeof(ST) == 4 ? 3 : 2);
 }
 
+// register cap that lets stream_min_ctas CTAs share the 64 K registers of an SM
+template <int Q, typename ST> constexpr int stream_max_regs() {
+    return (65536 / (stream_min_ctas<Q, ST>() * stream_threads<Q, ST>())) / 8 * 8;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Bounded wait for phase `parity` of *bar that also gives up once *abort is raised.
+__device__ bool mbar_wait_or_abort(uint64_t *bar, unsigned parity, volatile int *abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+    return true;
+}
+
+// fold a warp's max |output| per population into max_out (FP16 storage)
+template <int Q>
+__device__ __forceinline__ void fold_max(const StepArgs &a, const float (&tmax)[Q], int slot) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        float m = tmax[i];
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (lane == 0) atomicMax(a.max_out + i * kMaxCopies + slot % kMaxCopies, __float_as_uint(m));
+    }
+}
+
+// Two pipelines over the same stages and per-site code.
+//
+// Dedicated producer (D2Q5, FP32 / BF16): warps 0-7 compute (thread t owns sites t V .. t V + V - 1 of a
+// task); warp 8 lane 0 issues every copy.  Stage st carries two mbarriers: full[st]
+// completes when the bulk copies of the task placed there have landed, empty[st] when all
+// eight compute warps have finished reading it.  The producer refills a stage as soon as its
+// empty phase completes, so the compute warps never wait for one another.
+//
+// Block barrier (D2Q9, D3Q7, FP16): thread 0 refills stage st after a block-wide barrier that
+// follows every task; all 64 K registers stay with the compute warps.
+//
+// Every wait is bounded (one second); whoever gives up raises the context's fault flag (and,
+// with a producer warp, the block's abort flag), the warps leave, and the issuing thread
+// waits (bounded) for the copies still in flight before it returns.
 template <int Q, bool MRT, bool PERIODIC, typename ST>
-__global__ void __launch_bounds__(kSThreads, (stream_min_ctas<Q, ST>()))
+__global__ void __launch_bounds__((stream_threads<Q, ST>())) __maxnreg__((stream_max_regs<Q, ST>()))
     stream_step_kernel(const StepArgs a, const SArgs s) {
     constexpr bool SC = Scaled<ST>::value;
+    constexpr int kWarpsPerCta = kSThreads / 32;  // compute warps
     const int S = s.stages, SB = s.stage_bytes;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kMaxStages];
+    __shared__ __align__(8) uint64_t empty[kMaxStages];
     __shared__ float s_tab[kSThreads];
-    __shared__ float s_wmax[SC ? 9 : 1][kSThreads / 32];
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31;
     if ((int)blockIdx.x >= s.ncta) {  // block-uniform: receiver gather blocks
-        gather_receivers<Q, PERIODIC, ST>(a, ((int)blockIdx.x - s.ncta) * kSThreads +
-                                                 (int)threadIdx.x);
+        if (tid < kSThreads)
+            gather_receivers<Q, PERIODIC, ST>(a, ((int)blockIdx.x - s.ncta) * kSThreads + tid);
         return;
     }
-    const int tid = threadIdx.x;
-    if (a.mid) s_tab[tid] = a.mid_tab[tid];
-    if (tid == 0) {
-        for (int st = 0; st < S; st++) mbar_init(&full[st], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int st = 0; st < S; st++) {  // prologue: the first S tasks in flight
-            const int task = (int)blockIdx.x + st * s.ncta;
-            if (task < s.ntasks) issue_task<Q, PERIODIC, ST>(a, s, task, smem + st * SB, &full[st]);
-        }
-    }
-    __syncthreads();
+    if (tid < kSThreads && a.mid) s_tab[tid] = a.mid_tab[tid];
     float tmax[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) tmax[i] = 0.f;
-    int k = 0;
-    bool failed = false;
-    for (int task = blockIdx.x; task < s.ntasks; task += s.ncta, k++) {
-        const int st = k % S;
-        // warp-uniform outcome: compute_task shuffles with all 32 lanes
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[st], (unsigned)(k / S) & 1u));
-        if (ok) compute_task<Q, MRT, PERIODIC, ST>(a, s, task, smem + st * SB, s_tab, tmax);
-        // every thread is done with stage st (and every wait succeeded) before it is refilled
-        if (!__syncthreads_and(ok)) {
-            failed = true;
-            break;
-        }
-        if (tid == 0) {
-            const int next = task + S * s.ncta;
-            if (next < s.ntasks) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_task<Q, PERIODIC, ST>(a, s, next, smem + st * SB, &full[st]);
+
+    if constexpr (stream_dedicated<Q, ST>()) {
+        if (tid == kSThreads) {
+            abort_flag = 0;
+            for (int st = 0; st < S; st++) {
+                mbar_init(&full[st], 1);
+                mbar_init(&empty[st], kWarpsPerCta);
             }
-        }
-    }
-    if (failed) {  // record, then wait (bounded) for this block's copies still in flight
-        if (tid == 0) {
-            atomicExch(s.fault, 1u);
-            for (int j = 0; j < S; j++) {
-                const int kk = k + j;
-                if ((int)blockIdx.x + kk * s.ncta >= s.ntasks) break;
-                mbar_wait(&full[kk % S], (unsigned)(kk / S) & 1u);
-            }
-        }
-        return;
-    }
-    if (SC) {  // fold this block's max |output| per population into max_out
-        const int lane = tid & 31, w = tid >> 5;
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            float m = tmax[i];
-            for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-            if (lane == 0) s_wmax[SC ? i : 0][w] = m;
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         __syncthreads();
-        if (tid < Q) {
-            float m = 0.f;
-            for (int j = 0; j < kSThreads / 32; j++) m = fmaxf(m, s_wmax[SC ? tid : 0][j]);
-            atomicMax(a.max_out + tid * kMaxCopies + (blockIdx.x % kMaxCopies), __float_as_uint(m));
+        if (tid >= kSThreads) {  // producer warp: lane 0 issues every copy of this block
+            if (tid != kSThreads) return;
+            int k = 0;
+            for (int task = blockIdx.x; task < s.ntasks; task += s.ncta, k++) {
+                const int st = k % S;
+                if (k >= S &&
+                    !mbar_wait_or_abort(&empty[st], (unsigned)(k / S - 1) & 1u, &abort_flag)) {
+                    if (!abort_flag) {
+                        abort_flag = 1;
+                        atomicExch(s.fault, 1u);
+                    }
+                    break;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_task<Q, PERIODIC, ST>(a, s, task, smem + st * SB, &full[st]);
+            }
+            // the block must not retire with copies landing in its shared memory: wait
+            // (bounded) for the last (at most S) issued tasks' copies, which the compute
+            // warps also await
+            for (int j = max(k - S, 0); j < k; j++) mbar_wait(&full[j % S], (unsigned)(j / S) & 1u);
+            return;
+        }
+        int k = 0;
+        for (int task = blockIdx.x; task < s.ntasks; task += s.ncta, k++) {
+            const int st = k % S;
+            // warp-uniform outcome: compute_task shuffles with all 32 lanes
+            const bool ok = __all_sync(
+                0xffffffffu, mbar_wait_or_abort(&full[st], (unsigned)(k / S) & 1u, &abort_flag));
+            if (!ok) {
+                if (lane == 0 && !abort_flag) {
+                    abort_flag = 1;
+                    atomicExch(s.fault, 1u);
+                }
+                return;
+            }
+            compute_task<Q, MRT, PERIODIC, ST>(a, s, task, smem + st * SB, s_tab, tmax);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+    } else {
+        if (tid == 0) {
+            for (int st = 0; st < S; st++) mbar_init(&full[st], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            for (int st = 0; st < S; st++) {  // prologue: the first S tasks in flight
+                const int task = (int)blockIdx.x + st * s.ncta;
+                if (task < s.ntasks) issue_task<Q, PERIODIC, ST>(a, s, task, smem + st * SB, &full[st]);
+            }
+        }
+        __syncthreads();
+        int k = 0;
+        bool failed = false;
+        for (int task = blockIdx.x; task < s.ntasks; task += s.ncta, k++) {
+            const int st = k % S;
+            // warp-uniform outcome: compute_task shuffles with all 32 lanes
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[st], (unsigned)(k / S) & 1u));
+            if (ok) compute_task<Q, MRT, PERIODIC, ST>(a, s, task, smem + st * SB, s_tab, tmax);
+            // every thread is done with stage st (and every wait succeeded) before it is refilled
+            if (!__syncthreads_and(ok)) {
+                failed = true;
+                break;
+            }
+            if (tid == 0) {
+                const int next = task + S * s.ncta;
+                if (next < s.ntasks) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue_task<Q, PERIODIC, ST>(a, s, next, smem + st * SB, &full[st]);
+                }
+            }
+        }
+        if (failed) {  // record, then wait (bounded) for this block's copies still in flight
+            if (tid == 0) {
+                atomicExch(s.fault, 1u);
+                for (int j = 0; j < S; j++) {
+                    const int kk = k + j;
+                    if ((int)blockIdx.x + kk * s.ncta >= s.ntasks) break;
+                    mbar_wait(&full[kk % S], (unsigned)(kk / S) & 1u);
+                }
+            }
+            return;
         }
     }
+    if (SC) fold_max<Q>(a, tmax, blockIdx.x * kWarpsPerCta + (tid >> 5));
 }
 
 using SFn = void (*)(const StepArgs, const SArgs);
 
-// Two stages per CTA: while one task is computed, the next task's copies are in
-// flight.  Measured on GB300 (4096^2 two-layer): deeper pipelines cost more
-// shared memory (fewer resident CTAs) than they gain.
-constexpr int kStages = 2;
+// Stages per CTA: as many as the shared memory of the resident CTAs allows (2 .. kMaxStages).
+int stages_for(int stage_bytes, int ctas_per_sm) {
+    int dev = 0, per_sm = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    const int statics = 2048;  // barriers, medium table, abort flag (with room to spare)
+    const int fit = (per_sm / ctas_per_sm - reserved - statics) / stage_bytes;
+    return std::max(2, std::min(kMaxStages, fit));
+}
 
 struct SInfo {
     SFn fn = nullptr;
@@ -344,23 +449,30 @@ struct SInfo {
     int smem = 0;   // dynamic shared memory per CTA
     int ctas = 0;   // resident CTAs on the device
     int W = 0;      // sites per task
+    int threads = 0;  // per CTA
 };
 
 template <int Q, bool MRT, bool PER, typename ST> SInfo make_info(bool indexed) {
     SInfo in;
     in.fn = stream_step_kernel<Q, MRT, PER, ST>;
-    in.stages = kStages;
+    constexpr int kCtas = stream_min_ctas<Q, ST>();
     in.stage_bytes = Stage<Q, ST>::bytes(indexed);
+    in.stages = stages_for(in.stage_bytes, kCtas);
     in.smem = in.stage_bytes * in.stages;
     in.W = Geom<ST>::W;
-    int dev = 0, sms = 0, per_sm = 0;
+    in.threads = stream_threads<Q, ST>();
+    int dev = 0, sms = 0, per_sm = 0, smem_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     // the attribute belongs to the kernel, shared by both medium forms: allow the larger
-    const int smem_max = Stage<Q, ST>::bytes(false) * kStages;
-    if (cudaFuncSetAttribute(in.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) !=
+    const int b1 = Stage<Q, ST>::bytes(true), b4 = Stage<Q, ST>::bytes(false);
+    const int smem_max =
+        std::min(smem_optin, std::max(b1 * stages_for(b1, kCtas), b4 * stages_for(b4, kCtas)));
+    if (in.smem > smem_max ||
+        cudaFuncSetAttribute(in.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, in.fn, kSThreads, in.smem) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, in.fn, in.threads, in.smem) !=
             cudaSuccess) {
         cudaGetLastError();
         per_sm = 0;
@@ -411,6 +523,6 @@ lb_status stream_launch(lb_ctx *ctx, const StepArgs &a, int rec_blocks) {
     s.stages = in.stages;
     s.stage_bytes = in.stage_bytes;
     s.fault = ctx->fault;
-    in.fn<<<s.ncta + rec_blocks, kSThreads, in.smem, ctx->stream>>>(a, s);
+    in.fn<<<s.ncta + rec_blocks, in.threads, in.smem, ctx->stream>>>(a, s);
     return LB_OK;
 }
