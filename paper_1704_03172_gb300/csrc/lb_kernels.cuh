@@ -383,9 +383,10 @@ __device__ __forceinline__ const ST *src_row(const ST *base, int ys, int ny, int
 }
 
 // Source row of population i for output row r: the pull's y shift (2-D, row = y) or its
-// y and z shifts (D3Q7, r = z ny3 + y); -1 outside a zero-ghost domain.
+// y and z shifts (D3Q7, r = z ny3 + y3, with y3 and z given); -1 outside a zero-ghost
+// domain.
 template <int Q, bool PERIODIC>
-__device__ __forceinline__ int pull_row(const StepArgs &a, int r, int i) {
+__device__ __forceinline__ int pull_row_yz(const StepArgs &a, int r, int y, int z, int i) {
     if (Q != 7) {
         int ys = r - Lat<Q>::cy(i);
         if (ys < 0 || ys >= a.ny) {
@@ -394,7 +395,6 @@ __device__ __forceinline__ int pull_row(const StepArgs &a, int r, int i) {
         }
         return ys;
     }
-    const int y = r % a.ny3, z = r / a.ny3;
     int ys = y - Lat<Q>::cy(i), zs = z - Lat<Q>::cz(i);
     if (ys < 0 || ys >= a.ny3) {
         if (!PERIODIC) return -1;
@@ -405,6 +405,25 @@ __device__ __forceinline__ int pull_row(const StepArgs &a, int r, int i) {
         zs = zs < 0 ? zs + a.nz : zs - a.nz;
     }
     return zs * a.ny3 + ys;
+}
+
+// (y3, z) of row r of a D3Q7 grid (r itself and 0 for 2-D grids)
+template <int Q>
+__device__ __forceinline__ void row_yz(const StepArgs &a, int r, int &y, int &z) {
+    if (Q != 7) {
+        y = r;
+        z = 0;
+        return;
+    }
+    z = r / a.ny3;
+    y = r - z * a.ny3;
+}
+
+template <int Q, bool PERIODIC>
+__device__ __forceinline__ int pull_row(const StepArgs &a, int r, int i) {
+    int y, z;
+    row_yz<Q>(a, r, y, z);
+    return pull_row_yz<Q, PERIODIC>(a, r, y, z, i);
 }
 
 // ------------------------------------------------------------- collision --
@@ -522,15 +541,26 @@ __device__ __forceinline__ float sponge_factor(int x, int y, const StepArgs &a) 
     return 1.f - a.sponge_smax * r * r;
 }
 
-// sponge factor at row r (D3Q7: distance to the nearest of the six faces)
-template <int Q>
-__device__ __forceinline__ float sponge_at(int x, int r, const StepArgs &a) {
-    if (Q != 7) return sponge_factor(x, r, a);
-    const int y = r % a.ny3, z = r / a.ny3;
-    const int d = min(min(min(x, a.nx - 1 - x), min(y, a.ny3 - 1 - y)), min(z, a.nz - 1 - z));
+// sponge factor at distance d from the nearest face
+__device__ __forceinline__ float sponge_of_dist(int d, const StepArgs &a) {
     if (d >= a.sponge_w) return 1.f;
     const float q = (float)(a.sponge_w - d) * a.sponge_inv_w;
     return 1.f - a.sponge_smax * q * q;
+}
+
+// distance from row r to the nearest y face (D3Q7: y or z face)
+template <int Q>
+__device__ __forceinline__ int row_face_dist(int r, const StepArgs &a) {
+    if (Q != 7) return min(r, a.ny - 1 - r);
+    int y, z;
+    row_yz<Q>(a, r, y, z);
+    return min(min(y, a.ny3 - 1 - y), min(z, a.nz - 1 - z));
+}
+
+// sponge factor at row r (D3Q7: distance to the nearest of the six faces)
+template <int Q>
+__device__ __forceinline__ float sponge_at(int x, int r, const StepArgs &a) {
+    return sponge_of_dist(min(min(x, a.nx - 1 - x), row_face_dist<Q>(r, a)), a);
 }
 
 // --------------------------------------------------------------- receivers --
@@ -572,11 +602,12 @@ __device__ __forceinline__ float next_scale(float maxval, float S, float keep) {
     return bound > 0.f ? pow2_ceil(bound * (1.f / kStoredTarget)) : keep;
 }
 
-// Collision, source and sponge for a thread's V sites, in place.  EDGE: some site
-// lies in the sponge or beyond the last column (damped / zeroed per site).
+// Collision, source and sponge for a thread's V sites, in place.  EDGE: some site of
+// the warp lies in the sponge or beyond the last column (damped / zeroed per site; dyz is
+// the row's distance to the nearest y / z face).
 template <int Q, bool MRT, int V, bool EDGE>
 __device__ __forceinline__ void collide_sites(float (&g)[Q][V], const float (&e2s)[V],
-                                              const StepArgs &a, int x0, int y, bool has_src) {
+                                              const StepArgs &a, int x0, int dyz, bool has_src) {
 #pragma unroll
     for (int k = 0; k < V; k++) {
         float gs[Q];
@@ -594,7 +625,9 @@ __device__ __forceinline__ void collide_sites(float (&g)[Q][V], const float (&e2
             for (int i = 0; i < Q; i++) gs[i] += weight_i<Q>(i, e2s[k], a) * S;
         }
         if (EDGE) {
-            const float f = a.sponge_w > 0 ? sponge_at<Q>(x0 + k, y, a) : 1.f;
+            const int x = x0 + k;
+            const float f =
+                a.sponge_w > 0 ? sponge_of_dist(min(min(x, a.nx - 1 - x), dyz), a) : 1.f;
             const bool real = x0 + k < a.nx;
 #pragma unroll
             for (int i = 0; i < Q; i++) g[i][k] = real ? gs[i] * f : 0.f;
@@ -638,24 +671,23 @@ __device__ __forceinline__ void finish_sites(const StepArgs &a, float (&g)[Q][St
                 make_float4(r[0], r[1], r[2], r[3]);
         }
     }
-    bool edge;
-    if (Q == 7) {  // row y = z ny3 + y3
-        const int y3 = y % a.ny3, z = y / a.ny3;
-        edge = a.sponge_w > 0 && (y3 < a.sponge_w || y3 >= a.ny3 - a.sponge_w || z < a.sponge_w ||
-                                  z >= a.nz - a.sponge_w || x0 < a.sponge_w ||
-                                  x0 + V - 1 >= a.nx - a.sponge_w);
-    } else {
-        edge = a.sponge_w > 0 && (y < a.sponge_w || y >= a.ny - a.sponge_w || x0 < a.sponge_w ||
-                                  x0 + V - 1 >= a.nx - a.sponge_w);
-    }
+    // row y (D3Q7: z ny3 + y3): its distance to the nearest y / z face
+    const int dyz = row_face_dist<Q>(y, a);
+    bool edge = (a.sponge_w > 0 && (dyz < a.sponge_w || x0 < a.sponge_w ||
+                                    x0 + V - 1 >= a.nx - a.sponge_w)) ||
+                x0 + V > a.nx;
+    // one path per warp: on narrow rows (a 256-wide 3-D grid) every warp holds sponge
+    // columns, and per-lane paths would run both variants; for sites outside the sponge
+    // the EDGE variant gives the same values
+    edge = __any_sync(__activemask(), edge);
     const bool has_src = (y == a.src_y) && (a.src_x >= x0) && (a.src_x < x0 + V) &&
                          a.src_tab != nullptr && a.t < a.src_nt;
-    // collide site by site, in place: g[i][k] becomes the stored output.  Threads whose
+    // collide site by site, in place: g[i][k] becomes the stored output.  Warps whose
     // sites are all real and outside the sponge (almost all) skip damping and masking.
-    if (!edge && x0 + V <= a.nx)
-        collide_sites<Q, MRT, V, false>(g, e2s, a, x0, y, has_src);
+    if (!edge)
+        collide_sites<Q, MRT, V, false>(g, e2s, a, x0, dyz, has_src);
     else
-        collide_sites<Q, MRT, V, true>(g, e2s, a, x0, y, has_src);
+        collide_sites<Q, MRT, V, true>(g, e2s, a, x0, dyz, has_src);
     ST *o = static_cast<ST *>(a.out) + (long long)y * a.pitch + x0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -693,10 +725,12 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
     uint4 q[Q];
     uint32_t e[Q];
     bool absent[Q];
+    int y3, z3;
+    row_yz<Q>(a, y, y3, z3);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int cx = a.raw ? 0 : Lat<Q>::cx(i);  // raw: read g(t) in place (warp-uniform)
-        const int rs = a.raw ? y : pull_row<Q, PERIODIC>(a, y, i);
+        const int rs = a.raw ? y : pull_row_yz<Q, PERIODIC>(a, y, y3, z3, i);
         const ST *row = rs < 0 ? nullptr : in + i * a.plane + (long long)rs * a.pitch;
         absent[i] = row == nullptr;
         if (cx == 1)

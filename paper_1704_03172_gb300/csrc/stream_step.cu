@@ -124,11 +124,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 
 namespace {
 
-// Source row of population i for output row y; -1: outside a zero-ghost domain.
+// Source row of population i for output row y (D3Q7: (y3, z) of that row given); -1:
+// outside a zero-ghost domain.
 template <int Q, bool PERIODIC>
-__device__ __forceinline__ int source_row(const StepArgs &a, int i, int y) {
+__device__ __forceinline__ int source_row(const StepArgs &a, int i, int y, int y3, int z3) {
     if (a.raw) return y;  // first step after lb_set_state: g(t) is read in place
-    return pull_row<Q, PERIODIC>(a, y, i);  // y (and, for D3Q7, z) shift of the row
+    return pull_row_yz<Q, PERIODIC>(a, y, y3, z3, i);  // y (and, for D3Q7, z) shift of the row
 }
 
 // Thread 0: queue the bulk copies of task `task` into `stage`, completing on *bar.
@@ -143,9 +144,11 @@ __device__ void issue_task(const StepArgs &a, const SArgs &s, int task, unsigned
     const unsigned medb = (unsigned)min(G::W, a.pitch - xs) * (a.mid ? 1u : 4u);
     int ys[Q];
     unsigned total = medb;
+    int y3, z3;
+    row_yz<Q>(a, y, y3, z3);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        ys[i] = source_row<Q, PERIODIC>(a, i, y);
+        ys[i] = source_row<Q, PERIODIC>(a, i, y, y3, z3);
         if (ys[i] >= 0) total += rowb;
     }
     mbar_expect_tx(bar, total);
@@ -176,10 +179,12 @@ __device__ __forceinline__ void compute_task(const StepArgs &a, const SArgs &s, 
     const bool active = x0 < a.nx;
     const ST *in = static_cast<const ST *>(a.in);
     float g[Q][V];
+    int y3, z3;
+    row_yz<Q>(a, y, y3, z3);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int cx = a.raw ? 0 : Lat<Q>::cx(i);
-        const int ys = source_row<Q, PERIODIC>(a, i, y);
+        const int ys = source_row<Q, PERIODIC>(a, i, y, y3, z3);
         const ST *sp = reinterpret_cast<const ST *>(stage + i * G::ROWB) + G::H + tid * V;
         uint4 q = make_uint4(0u, 0u, 0u, 0u);
         if (ys >= 0 && active) q = *reinterpret_cast<const uint4 *>(sp);
