@@ -201,7 +201,7 @@ def _refined_variant(torch, LBSim, steps, warmup):
     updates = 2048 * 2048 + 2 * nf * nf
     return {"glups": round(updates * steps / sec / 1e9, 2), "updates_per_coarse_step": updates,
             "ms_per_coarse_step": round(sec / steps * 1e3, 4),
-            "launches_per_coarse_step": 7}
+            "launches_per_coarse_step": 6}
 
 
 def _nested_variant(torch, LBSim, steps, warmup):
@@ -224,7 +224,7 @@ def _nested_variant(torch, LBSim, steps, warmup):
     updates = 2048 * 2048 + 2 * n1 * n1 + 4 * n2 * n2
     return {"glups": round(updates * steps / sec / 1e9, 2), "updates_per_coarse_step": updates,
             "ms_per_coarse_step": round(sec / steps * 1e3, 4),
-            "launches_per_coarse_step": 19}
+            "launches_per_coarse_step": 16}
 
 
 def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32"):

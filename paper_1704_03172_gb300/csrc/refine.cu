@@ -34,13 +34,15 @@
 // One step T of a grid that holds a patch (fused kernels, all on the context
 // stream):
 //   the grid's step T (pull, collide, store; its own receivers)
-//   snapshot U(T) = the grid's populations on I at time T (before correction)
+//   snapshot U(T) = the grid's populations on I at time T (before correction), fused
+//     into the first transfer below
 //   [T >= 1] c2f into the patch's ghost ring from (U(T-1) + U(T)) / 2, patch step 2T-1
 //   c2f from U(T), patch step 2T (receivers inside the closed patch)
 //   f2c: the grid's nodes of I re-pulled, corrected from the patch state at 2T,
 //        re-collided and stored over the grid's step output.
 // A "patch step" of a level that holds a nested patch is this same procedure one level
-// down, so a coarse step of a two-patch hierarchy runs 1 + 2 + 4 step launches.
+// down, so a coarse step of a two-patch hierarchy runs 1 + 2 + 4 step launches and
+// 3 + 2 x 3 coupling launches.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -209,6 +211,61 @@ __global__ void ref_c2f_kernel(StepArgs af, StepArgs rs, const int4 *If, int nIf
     }
 }
 
+// The first coarse -> fine transfer of the parent's step T with the snapshot fused in: the
+// parent's populations on I at time T are pulled here from its step input (ap), each coarse
+// node's vector is stored to Ucur by the fine node that coincides with it, and the transfer
+// interpolates them with Ua = U(T - 1) (alpha = 1/2) or takes them alone (alpha = 1, T = 0).
+// Same values as the snapshot kernel followed by ref_c2f_kernel.
+template <int Q, bool MRT>
+__global__ void ref_snap_c2f_kernel(StepArgs ap, StepArgs af, StepArgs rs, const int4 *If, int nIf,
+                                    const int2 *Ic, const float *Ua, float *Ucur, float alpha,
+                                    int nxf, int nyf) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nIf) return;
+    const int4 e = If[j];
+    const int a = e.x, b = e.y;
+    const float *pin = static_cast<const float *>(ap.in);
+    float u1[Q], u2[Q];
+    const int2 X1 = Ic[e.z];
+#pragma unroll
+    for (int i = 0; i < Q; i++)
+        u1[i] = pull1<Q>(pin, ap.raw, 0, X1.x, X1.y, i, ap.nx, ap.ny, ap.pitch, ap.plane);
+    if (e.w >= 0) {
+        const int2 X2 = Ic[e.w];
+#pragma unroll
+        for (int i = 0; i < Q; i++)
+            u2[i] = pull1<Q>(pin, ap.raw, 0, X2.x, X2.y, i, ap.nx, ap.ny, ap.pitch, ap.plane);
+    }
+    if (!(a & 1) && !(b & 1)) {  // the fine node that coincides with coarse node e.z
+#pragma unroll
+        for (int i = 0; i < Q; i++) Ucur[(long long)e.z * Q + i] = u1[i];
+    }
+    float gh[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        float v = alpha < 1.f ? (1.f - alpha) * Ua[(long long)e.z * Q + i] + alpha * u1[i] : u1[i];
+        if (e.w >= 0) {
+            v += alpha < 1.f ? (1.f - alpha) * Ua[(long long)e.w * Q + i] + alpha * u2[i] : u2[i];
+            v *= 0.5f;
+        }
+        gh[i] = v;
+    }
+    const long long node = (long long)(b + 1) * af.pitch + (a + 1);
+    if (Q == 5)
+        collide5<MRT>(gh, af.eta2[node], rs);
+    else
+        collide9<MRT>(gh, af.eta2[node], rs);
+    float *in = static_cast<float *>(const_cast<void *>(af.in));
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int ua = a - Lat<Q>::cx(i), ub = b - Lat<Q>::cy(i);
+        if (ua >= 0 && ua < nxf && ub >= 0 && ub < nyf) continue;  // comes from the fine grid
+        const long long pos =
+            af.raw ? node : (long long)(ub + 1) * af.pitch + (ua + 1);
+        in[i * af.plane + pos] = gh[i];
+    }
+}
+
 // fine -> coarse on I, then collide (+ sponge) and overwrite the parent's step output
 template <int Q, bool MRT, bool PERIODIC>
 __global__ void ref_f2c_kernel(StepArgs ac, StepArgs rs, const float *fin, int fraw, int fpitch,
@@ -318,6 +375,29 @@ void launch_c2f(lb_ctx *ctx, lb_refine *R, const float *Ua, const float *Ub, flo
     }
 }
 
+template <int Q, bool MRT>
+void snap_c2f_q(lb_ctx *ctx, const StepArgs &ap, lb_refine *R, const StepArgs &af, const float *Ua,
+                float *Ucur, float alpha) {
+    ref_snap_c2f_kernel<Q, MRT><<<blocks_for(R->nIf), 256, 0, ctx->stream>>>(
+        ap, af, rescale_args(af, R->c2f_omega, R->c2f_s), R->If, R->nIf, R->Ic, Ua, Ucur, alpha,
+        R->nxf, R->nyf);
+}
+
+// snapshot U(T) of the parent's interface into Ucur fused with the first coarse -> fine
+// transfer of step T (alpha = 1/2 with Ua = U(T - 1), or alpha = 1)
+void launch_snap_c2f(lb_ctx *ctx, const StepArgs &ap, lb_refine *R, const float *Ua, float *Ucur,
+                     float alpha) {
+    StepArgs af = level_args(ctx, R);
+    af.in = R->pop[R->cur];
+    af.raw = R->raw ? 1 : 0;
+    const bool mrt = ctx->cfg.collision == LB_MRT;
+    if (ctx->Q == 9) {
+        if (mrt) snap_c2f_q<9, true>(ctx, ap, R, af, Ua, Ucur, alpha); else snap_c2f_q<9, false>(ctx, ap, R, af, Ua, Ucur, alpha);
+    } else {
+        if (mrt) snap_c2f_q<5, true>(ctx, ap, R, af, Ua, Ucur, alpha); else snap_c2f_q<5, false>(ctx, ap, R, af, Ua, Ucur, alpha);
+    }
+}
+
 // snapshot of the parent's populations on R's interface, from the parent's step input
 void launch_snapshot(lb_ctx *ctx, const StepArgs &ap, lb_refine *R, float *U) {
     if (ctx->Q == 9)
@@ -383,12 +463,13 @@ void level_step(lb_ctx *ctx, lb_refine *R, float *trace_row, long long t) {
 void child_steps(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, float *trace_row,
                  long long T) {
     float *Ucur = R->U[T & 1], *Uprev = R->U[(T + 1) & 1];
-    launch_snapshot(ctx, ap, R, Ucur);
-    if (T >= 1) {
-        launch_c2f(ctx, R, Uprev, Ucur, 0.5f);
+    if (T >= 1) {  // snapshot U(T) fused with the midpoint transfer
+        launch_snap_c2f(ctx, ap, R, Uprev, Ucur, 0.5f);
         level_step(ctx, R, nullptr, 2 * T - 1);
+        launch_c2f(ctx, R, Ucur, Ucur, 1.0f);
+    } else {  // snapshot U(0) fused with the transfer at time 0
+        launch_snap_c2f(ctx, ap, R, nullptr, Ucur, 1.0f);
     }
-    launch_c2f(ctx, R, Ucur, Ucur, 1.0f);
     const float *fin_last = static_cast<const float *>(R->pop[R->cur]);
     const int fraw = R->raw ? 1 : 0;
     level_step(ctx, R, trace_row, 2 * T);

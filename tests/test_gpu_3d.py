@@ -93,10 +93,18 @@ def test_d3q7_rejects_2d_only_features(sim_cls):
     sim.close()
 
 
-@pytest.mark.parametrize("storage,periodic", [("bf16", False), ("f32", True), ("f16", False)])
-def test_d3q7_staged_step_matches_direct_bitwise(sim_cls, storage, periodic):
+@pytest.mark.parametrize("storage,periodic,nx,ny,nz", [
+    ("bf16", False, 2100, 6, 5),      # two row segments per row, the second ragged
+    ("f32", True, 2100, 6, 5),
+    ("f16", False, 2100, 6, 5),
+    ("bf16", False, 256, 20, 9),      # narrow rows: one segment covers a whole row
+    ("bf16", True, 200, 13, 7),       # pitch 224, periodic wraps in y and z
+    ("f16", True, 96, 10, 6),
+    ("f32", False, 160, 11, 5),
+])
+def test_d3q7_staged_step_matches_direct_bitwise(sim_cls, storage, periodic, nx, ny, nz):
     rng = np.random.default_rng(5)
-    nx, ny, nz, steps = 2100, 6, 5, 12
+    steps = 12
     c = rng.uniform(0.45, 1.0, size=(nz, ny, nx)).astype(np.float32)
     g0 = (np.round(rng.normal(size=(7, nz, ny, nx)) * 0.05 * 256) / 256).astype(np.float32)
     rec = np.stack([rng.integers(0, nx, 8), rng.integers(0, ny, 8), rng.integers(0, nz, 8)],
