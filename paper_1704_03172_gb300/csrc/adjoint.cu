@@ -488,15 +488,17 @@ using AdjTbFn = void (*)(const StepArgs, const AdjArgs, const AdjTbArgs);
 
 // levels per blocked launch: D2Q5 8 (32 x 32 tiles; two copies of 5 x 48^2 floats, 92 KB of
 // shared memory, two CTAs per SM), D2Q9 4 (40 x 40 tiles; 166 KB, one CTA per SM)
-int adj_tb_levels(int Q) { return Q == 5 ? 8 : 4; }
+constexpr int kAdjLevels5 = 8, kAdjLevels9 = 4;
+int adj_tb_levels(int Q) { return Q == 5 ? kAdjLevels5 : kAdjLevels9; }
 
 template <int Q, bool MRT, int K> AdjTbFn adj_tb_fn(bool per) {
     return per ? adjoint_tb_kernel<Q, MRT, true, K> : adjoint_tb_kernel<Q, MRT, false, K>;
 }
 
 AdjTbFn pick_adj_tb(int Q, bool mrt, bool per) {
-    if (Q == 9) return mrt ? adj_tb_fn<9, true, 4>(per) : adj_tb_fn<9, false, 4>(per);
-    return mrt ? adj_tb_fn<5, true, 8>(per) : adj_tb_fn<5, false, 8>(per);
+    if (Q == 9)
+        return mrt ? adj_tb_fn<9, true, kAdjLevels9>(per) : adj_tb_fn<9, false, kAdjLevels9>(per);
+    return mrt ? adj_tb_fn<5, true, kAdjLevels5>(per) : adj_tb_fn<5, false, kAdjLevels5>(per);
 }
 
 // Every (region, local coordinate) along one axis at which grid coordinate x appears:
