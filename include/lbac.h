@@ -285,9 +285,10 @@ lb_status lb_invariants_noalloc(const float *g, const float *c_map, int lattice,
                                 int ny, double c_ref, const double *w_ref, double *out,
                                 void *cuda_stream);
 
-/* Device bytes lb_create would allocate for cfg, plus the receiver trace for
- * nt steps when nrec > 0, plus what lb_adjoint needs for nt steps when
- * want_adjoint > 0 (the checkpoint interval; 1 means the default 200). */
+/* Device bytes lb_create would allocate for cfg (refinement patches included),
+ * plus the receiver trace for nt steps when nrec > 0, plus what lb_adjoint needs
+ * for nt steps when want_adjoint > 0 (the checkpoint interval; 1 means the
+ * default 200). */
 lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint, size_t *bytes);
 
 /* Fourier projections of the pressure for dispersion diagnostics (the

@@ -314,6 +314,20 @@ lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint,
     size_t b = 2 * q * plane * elem_bytes(cfg->storage) + plane * 4 + plane + 1024;
     if (nrec > 0 && nt > 0) b += (size_t)nt * nrec * 4 + (size_t)nrec * 8;
     if (nt > 0) b += (size_t)nt * 4;
+    // refinement levels (refine.cu): per patch, two population buffers with a ghost ring and
+    // its eta^2 plane, the interface lists and three snapshot slots, the nested patch's
+    // medium and initial pressure when one follows, and the peek copies of a nested level
+    for (int k = 0; cfg->patches && k < cfg->n_patches && k < LB_MAX_PATCHES; k++) {
+        const size_t nxf = 2 * (size_t)std::max(cfg->patches[k].nx_c, 0) + 1;
+        const size_t nyf = 2 * (size_t)std::max(cfg->patches[k].ny_c, 0) + 1;
+        const size_t fplane = (nyf + 2) * (size_t)round_up((int)nxf + 2, 32);
+        const size_t nI = 2 * ((size_t)cfg->patches[k].nx_c + cfg->patches[k].ny_c);
+        const size_t nIf = 2 * (nxf + nyf);
+        b += 2 * q * fplane * 4 + fplane * 4 + nI * 8 + nIf * 16 + 3 * nI * q * 4 + 4096;
+        if (k + 1 < cfg->n_patches) b += 2 * nxf * nyf * 4;
+        if (k >= 1) b += q * fplane * 4 + 2 * nI * q * 4;
+        if (nrec > 0) b += (size_t)nrec * 12 + 1024;
+    }
     if (want_adjoint) {
         // lb_adjoint: checkpoints every C steps and, in the storage type, the two replay
         // states and the sub-checkpoints; the FP32 rho tape (T planes), the FP32 adjoint

@@ -231,3 +231,35 @@ def test_nested_block_workload_reduced_full_length(sim_cls, oracle_mod):
     assert rel(ps, R.pressure()) < TOL
     t2 = R.run(steps - snap)
     assert rel(tr, np.concatenate([t1, t2])) < TOL
+
+
+def test_footprint_covers_refined_levels(sim_cls):
+    # lb_footprint counts the patch levels: it bounds what lb_create and lb_set_receivers
+    # take from the (PyTorch) allocator, without overstating it by much
+    import torch
+    from paper_1704_03172_gb300 import lbac
+    nx, ny = 400, 300
+    c = W.uniform_map(nx, ny, 1.0)
+    patches = [(100, 80, 150, 120), (40, 30, 200, 150)]
+    rec = np.array([[20, 20], [150, 140], [180, 150]], np.int32)
+    for plist in (patches[:1], patches):
+        cfg = lbac.lb_config_default()
+        cfg.nx, cfg.ny = nx, ny
+        arr = (lbac.lb_patch * len(plist))(*[lbac.lb_patch(*q, 2) for q in plist])
+        cfg.patches = ctypes_cast(arr, lbac)
+        cfg.n_patches = len(plist)
+        est = lbac.lb_footprint(cfg, 50, len(rec), 0)
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        sim = sim_cls(c, patch=plist)
+        sim.set_receivers(rec, 50)
+        torch.cuda.synchronize()
+        used = torch.cuda.memory_allocated() - before
+        sim.close()
+        # (the allocator rounds each small buffer up to 512 bytes)
+        assert used <= est + (64 << 10) and est <= 1.3 * used + (4 << 20), (len(plist), used, est)
+
+
+def ctypes_cast(arr, lbac):
+    import ctypes
+    return ctypes.cast(arr, ctypes.POINTER(lbac.lb_patch))
