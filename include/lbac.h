@@ -160,8 +160,19 @@ lb_status lb_set_state(lb_ctx *ctx, const float *in, int on_device);
 /* Current time (steps taken since lb_init_pressure / lb_create). */
 lb_status lb_get_time(const lb_ctx *ctx, long long *t);
 
-/* Wait for all queued work; LB_ECUDA if any of it failed. */
+/* Wait for all queued work; LB_ECUDA if any of it failed.  LB_ETIMEOUT if a
+ * bounded device wait gave up since the last lb_sync (the TMA-staged step waits
+ * at most one second for each of its bulk copies); the flag is then cleared,
+ * so the status is reported once.  After LB_ETIMEOUT the state is undefined
+ * until lb_init_pressure or lb_set_state; the context stays usable. */
 lb_status lb_sync(lb_ctx *ctx);
+
+/* Self-test of the bounded-wait failure path, for tests: queues one block
+ * that waits on a shared-memory mbarrier phase that nothing completes, with
+ * the staged step's polling, gives up after timeout_us microseconds
+ * (1 .. 1000000) and raises the fault flag exactly as the step does.  The
+ * state is not touched; the next lb_sync returns LB_ETIMEOUT. */
+lb_status lb_wait_selftest(lb_ctx *ctx, int timeout_us);
 
 /* Keep adjoint checkpoints: from now on (time t0 = current time), lb_step copies
  * the state into device memory before every step t with (t - t0) % every == 0.

@@ -818,7 +818,11 @@ lb_status lb_sync(lb_ctx *ctx) {
     unsigned fault = 0;
     e = cudaMemcpy(&fault, ctx->fault, 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fault flag");
-    if (fault) return fail(ctx, LB_ETIMEOUT, "a bounded wait in a step kernel gave up");
+    if (fault) {  // reported once: the flag is cleared for what follows
+        e = cudaMemset(ctx->fault, 0, 4);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "fault flag");
+        return fail(ctx, LB_ETIMEOUT, "a bounded wait in a kernel gave up");
+    }
     return LB_OK;
 }
 

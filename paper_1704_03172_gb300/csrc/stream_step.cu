@@ -101,14 +101,16 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Bounded wait for phase `parity` of *bar; false after kWaitNs without completion.
-__device__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// Bounded wait for phase `parity` of *bar; false after `ns` without completion.
+__device__ bool mbar_wait_for(uint64_t *bar, unsigned parity, unsigned long long ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > ns) return false;
     return true;
 }
+
+__device__ bool mbar_wait(uint64_t *bar, unsigned parity) { return mbar_wait_for(bar, parity, kWaitNs); }
 
 // Bulk copy global -> shared (TMA, untiled), completing `bytes` on *bar.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
@@ -515,6 +517,33 @@ const SInfo &stream_info(int Q, bool mrt, bool per, int storage, bool ix) {
 }
 
 }  // namespace
+
+namespace {
+
+// Self-test of the bounded-wait failure path: one block waits for the first phase of a
+// shared-memory mbarrier on which nothing arrives, with the staged step's polling, gives up
+// after `ns` and raises the fault flag as the step does.
+__global__ void wait_selftest_kernel(unsigned *fault, unsigned long long ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_for(&bar, 0u, ns));
+    if (!ok && threadIdx.x == 0) atomicExch(fault, 1u);
+}
+
+}  // namespace
+
+extern "C" lb_status lb_wait_selftest(lb_ctx *ctx, int timeout_us) {
+    if (!ctx) return LB_EINVAL;
+    if (timeout_us < 1 || timeout_us > 1000000)
+        return fail(ctx, LB_EINVAL, "timeout_us must be 1 .. 1000000");
+    wait_selftest_kernel<<<1, 32, 0, ctx->stream>>>(ctx->fault,
+                                                    (unsigned long long)timeout_us * 1000ull);
+    return check_launch(ctx, "wait self-test");
+}
 
 lb_status stream_launch(lb_ctx *ctx, const StepArgs &a, int rec_blocks) {
     const SInfo &in = stream_info(ctx->Q, ctx->cfg.collision == LB_MRT,

@@ -94,6 +94,7 @@ _SIGS = {
     "lb_set_state": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
     "lb_get_time": [_ctx_p, ctypes.POINTER(ctypes.c_longlong)],
     "lb_sync": [_ctx_p],
+    "lb_wait_selftest": [_ctx_p, ctypes.c_int],
     "lb_footprint": [_cfgp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                      ctypes.POINTER(ctypes.c_size_t)],
     "lb_info": [_ctx_p, _dp, ctypes.c_int],
@@ -259,6 +260,10 @@ def lb_get_time(ctx) -> int:
 
 def lb_sync(ctx):
     return _check(_lib.lb_sync(ctx), ctx)
+
+
+def lb_wait_selftest(ctx, timeout_us):
+    return _check(_lib.lb_wait_selftest(ctx, int(timeout_us)), ctx)
 
 
 def lb_footprint(cfg: lb_config, nt, nrec, want_adjoint) -> int:

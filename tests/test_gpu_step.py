@@ -249,3 +249,31 @@ def test_staged_step_matches_direct_step_bitwise(sim_cls, Q, storage, coll, peri
     np.testing.assert_array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
     assert np.isfinite(out[0][0]).all() and np.abs(out[0][1]).max() > 0
+
+
+def test_bounded_wait_gives_up_reports_once_and_leaves_the_context_usable(sim_cls):
+    # The failure path of the TMA-staged step's bounded waits, driven without any fault: a
+    # one-block self-test waits on an mbarrier phase that nothing completes, gives up after
+    # 2 ms and raises the fault flag.  lb_sync reports LB_ETIMEOUT once; the context keeps
+    # stepping, and the state it produces equals a run without the self-test bit for bit.
+    from paper_1704_03172_gb300 import lbac
+    nx, ny = 2100, 16
+    c = W.random_medium(nx, ny, 12, 0.5, 1.0)
+    g0 = (np.random.default_rng(1).normal(size=(5, ny, nx)) * 0.1).astype(np.float32)
+    out = []
+    for probe in (False, True):
+        sim = sim_cls(c, storage="bf16", c_ref=1.0, sponge_width=4, step_kernel="staged")
+        sim.set_state(g0)
+        sim.step(5)
+        lbac.lb_sync(sim.ctx)
+        if probe:
+            lbac.lb_wait_selftest(sim.ctx, 2000)
+            with pytest.raises(lbac.LBError) as e:
+                lbac.lb_sync(sim.ctx)
+            assert e.value.status == lbac.LB_ETIMEOUT
+            lbac.lb_sync(sim.ctx)                      # reported once
+        sim.step(5)
+        lbac.lb_sync(sim.ctx)
+        out.append(sim.state().cpu().numpy())
+        sim.close()
+    np.testing.assert_array_equal(out[0], out[1])
