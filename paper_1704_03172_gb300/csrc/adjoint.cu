@@ -176,6 +176,7 @@ struct AdjArgs {
 // the +-1 x-shift of the reverse pull is a warp shuffle, as in the forward step).
 template <int Q, bool MRT, bool PERIODIC>
 __global__ void __launch_bounds__(kThreads, Q == 5 ? 4 : 3) adjoint_kernel(const StepArgs a, const AdjArgs d) {
+    pdl_trigger_and_wait();
     constexpr int V = 4;
     const int lane = threadIdx.x & 31;
     const int wid = blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -257,6 +258,7 @@ __global__ void __launch_bounds__(kThreads, Q == 5 ? 4 : 3) adjoint_kernel(const
 // receivers: lambda^t += R^t_r c_s^2(x_r) (every population), dJ/d(eta^2) += R dc_s^2 rho^t
 template <int Q>
 __global__ void adjoint_receivers(const StepArgs a, const AdjArgs d) {
+    pdl_trigger_and_wait();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d.nrec) return;
     const int2 xy = a.rec[r];
@@ -291,6 +293,7 @@ struct AdjTbArgs {
 template <int Q, bool MRT, bool PERIODIC, int K>
 __global__ void __launch_bounds__(kTbThreads) adjoint_tb_kernel(const StepArgs a, const AdjArgs d,
                                                                 const AdjTbArgs b) {
+    pdl_trigger_and_wait();
     constexpr int W = kTbW, NS = kTbNS, OUT = W - 2 * K, PER = kTbPer;
     extern __shared__ float smem[];  // two copies of [Q][NS]
     float *bufA = smem, *bufB = smem + Q * NS;
@@ -719,7 +722,7 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
             } else if (ctx->staged) {
                 stream_launch(ctx, a, 0);  // cannot fail once the forward run has stepped
             } else {
-                fwd<<<a.main_blocks, kThreads, 0, ctx->stream>>>(a);
+                launch_pdl(fwd, dim3(a.main_blocks), dim3(kThreads), 0, ctx->stream, a);
             }
             in = a.out;
             x ^= 1;
@@ -756,12 +759,13 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
                 if (m + 1 >= Ka) {  // levels sa + m .. sa + m - Ka + 1 in one launch
                     tbb.rho_hi = d.rho;
                     tbb.t_hi = a.t;
-                    adj_tb<<<tb_grid, kTbThreads, tb_smem, ctx->stream>>>(a, d, tbb);
+                    launch_pdl(adj_tb, tb_grid, dim3(kTbThreads), tb_smem, ctx->stream, a, d, tbb);
                     m -= Ka;
                 } else {
-                    adj<<<adj_blocks, kThreads, 0, ctx->stream>>>(a, d);
+                    launch_pdl(adj, dim3(adj_blocks), dim3(kThreads), 0, ctx->stream, a, d);
                     if (ctx->nrec > 0)
-                        adj_rec<<<(ctx->nrec + 255) / 256, 256, 0, ctx->stream>>>(a, d);
+                        launch_pdl(adj_rec, dim3((ctx->nrec + 255) / 256), dim3(256), 0,
+                                   ctx->stream, a, d);
                     m -= 1;
                 }
                 li ^= 1;

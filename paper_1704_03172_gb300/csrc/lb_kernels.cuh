@@ -48,6 +48,15 @@ __host__ __device__ __forceinline__ int wrap_mod(int v, int n) {
     return v < 0 ? v + n : v;
 }
 
+// Programmatic dependent launch: a step kernel lets the next step's blocks launch at once
+// (they become resident as this grid's blocks retire) and, before touching global memory,
+// waits until the grid it depends on has completed and its writes are visible.  Without the
+// launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger_and_wait() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <int Q> struct Lat;
 template <> struct Lat<5> {
     __host__ __device__ static constexpr int cx(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
@@ -787,6 +796,7 @@ __global__ void __launch_bounds__(kThreads, Q == 5   ? (sizeof(ST) == 4 ? 5 : 4)
     step_kernel(const StepArgs a) {
     constexpr bool SC = Scaled<ST>::value;
     __shared__ float s_wmax[SC ? 9 : 1][kWarps];
+    pdl_trigger_and_wait();
     if ((int)blockIdx.x >= a.main_blocks) {  // block-uniform
         gather_receivers<Q, PERIODIC, ST>(a, ((int)blockIdx.x - a.main_blocks) * kThreads +
                                                  (int)threadIdx.x);
@@ -843,6 +853,7 @@ __global__ void __launch_bounds__(kThreads)
     batch_step_kernel(const StepArgs *__restrict__ args, const int *__restrict__ first, int nshots) {
     __shared__ StepArgs sa;
     __shared__ int s_blk;
+    pdl_trigger_and_wait();
     if (threadIdx.x == 0) {
         int lo = 0, hi = nshots - 1;  // shot with first[k] <= blockIdx.x < first[k + 1]
         while (lo < hi) {

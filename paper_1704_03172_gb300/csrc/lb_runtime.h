@@ -5,6 +5,7 @@
 
 #include <cstdarg>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "lbac.h"
@@ -58,6 +59,25 @@ struct lb_ctx {
 };
 
 namespace lbrt {
+// Launch with programmatic stream serialization: the kernel may start while the previous
+// kernel in the stream is finishing, and must call lbk::pdl_trigger_and_wait() before it
+// touches global memory.
+template <typename... ExpTypes, typename... ActTypes>
+inline cudaError_t launch_pdl(void (*kernel)(ExpTypes...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, ActTypes &&...args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = stream;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, kernel, std::forward<ActTypes>(args)...);
+}
+
 using StepFn = void (*)(const lbk::StepArgs);
 using GetFn = void (*)(lbk::StepArgs, float *, int);
 lbk::StepArgs base_args(const lb_ctx *c);

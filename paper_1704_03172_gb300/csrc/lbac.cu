@@ -738,8 +738,10 @@ lb_status launch_step(lb_ctx *ctx, StepFn fn, StepArgs &a) {
     if (ctx->staged) {
         lb_status st = stream_launch(ctx, a, rec_blocks);
         if (st != LB_OK) return st;
-    } else {
-        fn<<<a.main_blocks + rec_blocks, kThreads, 0, ctx->stream>>>(a);
+    } else {  // programmatic dependent launch: the step waits for the grid before it
+        cudaError_t e = launch_pdl(fn, dim3(a.main_blocks + rec_blocks), dim3(kThreads), 0,
+                                   ctx->stream, a);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
     }
     if (ctx->lp_scale) scale_update_kernel<<<1, 32, 0, ctx->stream>>>(a, ctx->Q);
     ctx->cur ^= 1;

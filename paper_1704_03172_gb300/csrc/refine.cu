@@ -180,6 +180,7 @@ __global__ void ref_snapshot_kernel(StepArgs ac, const int2 *Ic, int nI, float *
 template <int Q, bool MRT>
 __global__ void ref_c2f_kernel(StepArgs af, StepArgs rs, const int4 *If, int nIf, const float *Ua,
                                const float *Ub, float alpha, int nxf, int nyf) {
+    pdl_trigger_and_wait();  // launched with launch_pdl
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nIf) return;
     const int4 e = If[j];
@@ -220,6 +221,7 @@ template <int Q, bool MRT>
 __global__ void ref_snap_c2f_kernel(StepArgs ap, StepArgs af, StepArgs rs, const int4 *If, int nIf,
                                     const int2 *Ic, const float *Ua, float *Ucur, float alpha,
                                     int nxf, int nyf) {
+    pdl_trigger_and_wait();  // launched with launch_pdl
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nIf) return;
     const int4 e = If[j];
@@ -271,6 +273,7 @@ template <int Q, bool MRT, bool PERIODIC>
 __global__ void ref_f2c_kernel(StepArgs ac, StepArgs rs, const float *fin, int fraw, int fpitch,
                                long long fplane, const int2 *Ic, int nI, int x0, int y0, int nxp,
                                int nyp) {
+    pdl_trigger_and_wait();  // launched with launch_pdl
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nI) return;
     const int2 X = Ic[k];
@@ -359,8 +362,9 @@ StepArgs rescale_args(StepArgs a, float omega, const float *s) {
 template <int Q, bool MRT>
 void c2f_q(lb_ctx *ctx, lb_refine *R, const StepArgs &af, const float *Ua, const float *Ub,
            float alpha) {
-    ref_c2f_kernel<Q, MRT><<<blocks_for(R->nIf), 256, 0, ctx->stream>>>(
-        af, rescale_args(af, R->c2f_omega, R->c2f_s), R->If, R->nIf, Ua, Ub, alpha, R->nxf, R->nyf);
+    launch_pdl(ref_c2f_kernel<Q, MRT>, dim3(blocks_for(R->nIf)), dim3(256), 0, ctx->stream, af,
+               rescale_args(af, R->c2f_omega, R->c2f_s), R->If, R->nIf, Ua, Ub, alpha, R->nxf,
+               R->nyf);
 }
 
 void launch_c2f(lb_ctx *ctx, lb_refine *R, const float *Ua, const float *Ub, float alpha) {
@@ -378,9 +382,9 @@ void launch_c2f(lb_ctx *ctx, lb_refine *R, const float *Ua, const float *Ub, flo
 template <int Q, bool MRT>
 void snap_c2f_q(lb_ctx *ctx, const StepArgs &ap, lb_refine *R, const StepArgs &af, const float *Ua,
                 float *Ucur, float alpha) {
-    ref_snap_c2f_kernel<Q, MRT><<<blocks_for(R->nIf), 256, 0, ctx->stream>>>(
-        ap, af, rescale_args(af, R->c2f_omega, R->c2f_s), R->If, R->nIf, R->Ic, Ua, Ucur, alpha,
-        R->nxf, R->nyf);
+    launch_pdl(ref_snap_c2f_kernel<Q, MRT>, dim3(blocks_for(R->nIf)), dim3(256), 0, ctx->stream,
+               ap, af, rescale_args(af, R->c2f_omega, R->c2f_s), R->If, R->nIf, R->Ic, Ua, Ucur,
+               alpha, R->nxf, R->nyf);
 }
 
 // snapshot U(T) of the parent's interface into Ucur fused with the first coarse -> fine
@@ -410,14 +414,10 @@ template <int Q, bool MRT>
 void f2c_q(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, const float *fin,
            int fraw) {
     long long fplane = (long long)R->gy * R->pitch;
-    if (periodic)
-        ref_f2c_kernel<Q, MRT, true><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(
-            ap, rescale_args(ap, R->f2c_omega, R->f2c_s), fin, fraw, R->pitch, fplane, R->Ic,
-            R->nI, R->x0, R->y0, R->nxp, R->nyp);
-    else
-        ref_f2c_kernel<Q, MRT, false><<<blocks_for(R->nI), 256, 0, ctx->stream>>>(
-            ap, rescale_args(ap, R->f2c_omega, R->f2c_s), fin, fraw, R->pitch, fplane, R->Ic,
-            R->nI, R->x0, R->y0, R->nxp, R->nyp);
+    launch_pdl(periodic ? ref_f2c_kernel<Q, MRT, true> : ref_f2c_kernel<Q, MRT, false>,
+               dim3(blocks_for(R->nI)), dim3(256), 0, ctx->stream, ap,
+               rescale_args(ap, R->f2c_omega, R->f2c_s), fin, fraw, R->pitch, fplane, R->Ic, R->nI,
+               R->x0, R->y0, R->nxp, R->nyp);
 }
 
 // correction of the parent's step output on R's interface from R's state fin
@@ -451,7 +451,7 @@ void level_step(lb_ctx *ctx, lb_refine *R, float *trace_row, long long t) {
         rec_blocks = (R->nrec_f + kThreads - 1) / kThreads;
     }
     StepFn fn = pick_step_for(ctx->Q, ctx->cfg.collision == LB_MRT, false, LB_F32);
-    fn<<<af.main_blocks + rec_blocks, kThreads, 0, ctx->stream>>>(af);
+    launch_pdl(fn, dim3(af.main_blocks + rec_blocks), dim3(kThreads), 0, ctx->stream, af);
     if (R->sub) child_steps(ctx, af, false, R->sub, trace_row, t);
     R->cur ^= 1;
     R->raw = false;
@@ -752,7 +752,8 @@ lb_status refine_step(lb_ctx *ctx, int n) {
         ac.rec_col = R->col_c;
         ac.trace_row = R->nrec_c > 0 ? trace_row : nullptr;
         int rec_blocks = ac.trace_row ? (R->nrec_c + kThreads - 1) / kThreads : 0;
-        coarse_fn<<<ac.main_blocks + rec_blocks, kThreads, 0, ctx->stream>>>(ac);
+        launch_pdl(coarse_fn, dim3(ac.main_blocks + rec_blocks), dim3(kThreads), 0, ctx->stream,
+                   ac);
         child_steps(ctx, ac, periodic, R, trace_row, T);
         ctx->cur ^= 1;
         ctx->raw = false;

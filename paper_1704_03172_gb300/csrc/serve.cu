@@ -360,7 +360,8 @@ void pass(lb_server *S) {
         for (; ci < copies.size() && copies[ci].round <= L.round; ci++)
             cudaMemcpyAsync(copies[ci].dst, copies[ci].src, copies[ci].bytes,
                             cudaMemcpyDeviceToDevice, S->stream);
-        L.fn<<<L.blocks, kThreads, 0, S->stream>>>(S->d_args + L.arg0, S->d_first + L.first0, L.n);
+        launch_pdl(L.fn, dim3(L.blocks), dim3(kThreads), 0, S->stream,
+                   (const StepArgs *)(S->d_args + L.arg0), (const int *)(S->d_first + L.first0), L.n);
         S->n_launch++;
     }
 }

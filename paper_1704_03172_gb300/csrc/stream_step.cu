@@ -332,6 +332,7 @@ __global__ void __launch_bounds__((stream_threads<Q, ST>())) __maxnreg__((stream
     __shared__ float s_tab[kSThreads];
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, lane = tid & 31;
+    pdl_trigger_and_wait();
     if ((int)blockIdx.x >= s.ncta) {  // block-uniform: receiver gather blocks
         if (tid < kSThreads)
             gather_receivers<Q, PERIODIC, ST>(a, ((int)blockIdx.x - s.ncta) * kSThreads + tid);
@@ -557,6 +558,8 @@ lb_status stream_launch(lb_ctx *ctx, const StepArgs &a, int rec_blocks) {
     s.stages = in.stages;
     s.stage_bytes = in.stage_bytes;
     s.fault = ctx->fault;
-    in.fn<<<s.ncta + rec_blocks, in.threads, in.smem, ctx->stream>>>(a, s);
+    cudaError_t e = launch_pdl(in.fn, dim3(s.ncta + rec_blocks), dim3(in.threads),
+                               (size_t)in.smem, ctx->stream, a, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "TMA-staged step launch");
     return LB_OK;
 }

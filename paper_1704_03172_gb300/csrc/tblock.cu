@@ -48,6 +48,7 @@ struct TbArgs {
 // REC: also record rho of every level of the own tile (adjoint replays only)
 template <int Q, bool MRT, bool PERIODIC, int K, bool REC>
 __global__ void __launch_bounds__(kTbThreads) tb_kernel(const StepArgs a, const TbArgs tb) {
+    pdl_trigger_and_wait();
     constexpr int W = kW, NS = kNS, OUT = W - 2 * K;
     extern __shared__ float smem[];  // two copies of [Q][NS]
     float *bufA = smem, *bufB = smem + Q * NS;
@@ -250,7 +251,8 @@ lb_status tb_launch_args(lb_ctx *ctx, const StepArgs &a, int K) {
     const size_t smem = 2 * (size_t)ctx->Q * kNS * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "temporal-blocking shared memory");
-    fn<<<grid, kTbThreads, smem, ctx->stream>>>(a, tb);
+    e = launch_pdl(fn, grid, dim3(kTbThreads), smem, ctx->stream, a, tb);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "temporal-blocking launch");
     return LB_OK;
 }
 
