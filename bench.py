@@ -227,10 +227,12 @@ def _nested_variant(torch, LBSim, steps, warmup):
             "launches_per_coarse_step": 16}
 
 
-def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32"):
+def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32", mode="ckpt"):
     """Gradient of J = 1/2 sum p^2 over 512 receiver traces w.r.t. the sound-speed map and
     the source, for a 20-layer faulted model: forward run with checkpoints, then lb_adjoint
-    (replay + reverse sweep).  Rates count n^2 * nt site-steps of the gradient call."""
+    (replay + reverse sweep); mode "tape": the forward run records rho (n^2 nt 4 bytes) and
+    lb_adjoint is the reverse sweep alone.  Rates count n^2 * nt site-steps of the gradient
+    call."""
     c = W.layered_fault_model(n, n, W.DEFAULT_SEED + 4, n_layers=20,
                               throw=(20.0 * n / 8192, 200.0 * n / 8192))
     sim = LBSim(c, lattice=5, tau=0.5, c_ref=W.SERVED_C_REF, sponge_width=40, storage=storage)
@@ -238,7 +240,10 @@ def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32"):
         sim.set_source(n // 2, 48, W.ricker(nt, W.SERVED_FC))
         sim.set_receivers(W.line_receivers(512, 48, 40, n - 80), nt)
         sim.init_pressure(None)
-        sim.checkpoint_every(every)
+        if mode == "tape":
+            sim.record_rho(nt)
+        else:
+            sim.checkpoint_every(every)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim.step(nt)
@@ -265,14 +270,20 @@ def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32"):
     # eta^2 loads over the region, lambda store and FP64 gradient RMW over the tile once per
     # 8 levels, and the rho tape read at every level
     bps_adj = ((48 / 32) ** 2 * (5 * 4 + 4) + 5 * 4 + 16) / 8 + 4
-    bps = round(levels * bps_fwd + 4 + bps_adj, 2)
+    bps = round(bps_adj if mode == "tape" else levels * bps_fwd + 4 + bps_adj, 2)
     upd = n * n * nt
-    return {"gradient_glups": round(upd / t_adj / 1e9, 2),
-            "forward_with_checkpoints_glups": round(upd / t_fwd / 1e9, 2),
-            "bytes_per_site_step": bps, "achieved_gbs": round(upd * bps / t_adj / 1e9, 1),
-            "replay_levels": levels, "seconds": round(t_adj, 4), "finite": finite,
-            "workload": f"{n}x{n} 20-layer faulted model, D2Q5 BGK {storage.upper()}, {nt} steps, "
-                        f"checkpoint every {every}, 512 receivers, wall time of lb_adjoint"}
+    out = {"gradient_glups": round(upd / t_adj / 1e9, 2),
+           "forward_with_checkpoints_glups" if mode != "tape" else "forward_with_rho_tape_glups":
+               round(upd / t_fwd / 1e9, 2),
+           "bytes_per_site_step": bps, "achieved_gbs": round(upd * bps / t_adj / 1e9, 1),
+           "seconds": round(t_adj, 4), "finite": finite,
+           "workload": f"{n}x{n} 20-layer faulted model, D2Q5 BGK {storage.upper()}, {nt} steps, "
+                       + (f"forward rho tape ({n * n * nt * 4 / 1e9:.0f} GB), no replay"
+                          if mode == "tape" else f"checkpoint every {every}")
+                       + ", 512 receivers, wall time of lb_adjoint"}
+    if mode != "tape":
+        out["replay_levels"] = levels
+    return out
 
 
 def _d3q7_variant(torch, LBSim, storage, n=256, steps=300, warmup=10):
@@ -371,7 +382,7 @@ def _served(n_req, n_cal, seed=W.DEFAULT_SEED + 5, load=0.7, max_active=64):
         c = kw.pop("c_map")
         if kw["want_gradient"]:
             kw["observed"] = np.zeros((kw["nt"], len(kw["receivers"])), np.float32)
-            kw["checkpoint_every"] = 200
+            kw["checkpoint_every"] = 0  # the forward rho tape when it is small, else 200
         return srv.submit(c, **kw)
 
     def collect(srv, ids, out):
@@ -383,6 +394,7 @@ def _served(n_req, n_cal, seed=W.DEFAULT_SEED + 5, load=0.7, max_active=64):
         """The same shots through the plain per-shot API (LBSim), one after another."""
         import torch
         from paper_1704_03172_gb300.sim import LBSim
+        tape_limit = 0.2 * torch.cuda.mem_get_info()[0]  # the server's rule: budget / 4
         t0 = time.monotonic()
         for s in shots_:
             sim = LBSim(s["c_map"], lattice=5, tau=s["tau"], storage=s["storage"],
@@ -392,7 +404,11 @@ def _served(n_req, n_cal, seed=W.DEFAULT_SEED + 5, load=0.7, max_active=64):
             sim.set_receivers(s["receivers"], s["nt"])
             sim.init_pressure(None)
             if s["want_gradient"]:
-                sim.checkpoint_every(200)
+                n = s["c_map"].shape[0]
+                if s["nt"] * n * (-(-n // 32) * 32) * 4 <= tape_limit:
+                    sim.record_rho(s["nt"])
+                else:
+                    sim.checkpoint_every(200)
             sim.step(s["nt"])
             tr = sim.traces(s["nt"])
             tr.cpu()
@@ -534,9 +550,10 @@ def run_ours(args):
 
     if args.variant:  # one variant alone (profiling runs)
         name = args.variant
-        if name.startswith("adjoint_"):
+        if name.startswith("adjoint_"):  # adjoint_f32, adjoint_bf16, adjoint_tape_f32, ...
             out = _adjoint_variant(torch, LBSim, n=args.adj_n, nt=args.adj_nt,
-                                   every=args.adj_every, storage=name.rsplit("_", 1)[1])
+                                   every=args.adj_every, storage=name.rsplit("_", 1)[1],
+                                   mode="tape" if "_tape_" in name else "ckpt")
         elif name.startswith("refined_nested"):
             out = _nested_variant(torch, LBSim, args.steps, args.warmup)
         elif name.startswith("refined"):
@@ -654,6 +671,12 @@ def run_ours(args):
             v["refined_nested_2048_d2q5_mrt_f32"] = {"error": str(ex)[:200]}
         for st in ("f32", "bf16"):
             try:
+                v[f"adjoint_tape_4096_d2q5_{st}"] = _adjoint_variant(torch, LBSim, storage=st,
+                                                                     mode="tape")
+            except Exception as ex:
+                v[f"adjoint_tape_4096_d2q5_{st}"] = {"error": str(ex)[:200]}
+        for st in ("f32", "bf16"):
+            try:
                 v[f"adjoint_4096_d2q5_{st}"] = _adjoint_variant(torch, LBSim, storage=st)
             except Exception as ex:
                 v[f"adjoint_4096_d2q5_{st}"] = {"error": str(ex)[:200]}
@@ -694,7 +717,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--variant", default="",
-                    help="run one variant alone: adjoint_f32, adjoint_bf16, refined, refined_nested, served")
+                    help="run one variant alone: adjoint_f32, adjoint_bf16, adjoint_tape_f32, adjoint_tape_bf16, refined, refined_nested, served")
     ap.add_argument("--adj-n", type=int, default=4096, help="adjoint variant grid side")
     ap.add_argument("--adj-nt", type=int, default=1000, help="adjoint variant steps")
     ap.add_argument("--adj-every", type=int, default=200, help="adjoint checkpoint interval")

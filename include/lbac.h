@@ -181,6 +181,17 @@ lb_status lb_wait_selftest(lb_ctx *ctx, int timeout_us);
  * (LB_ESTATE); BF16 checkpoints are BF16 states (half the memory). */
 lb_status lb_checkpoint_every(lb_ctx *ctx, int every);
 
+/* Record the forward density tape for lb_adjoint: from now on (time t0 =
+ * current time) every step t < t0 + nt_capacity also writes rho(x, t) =
+ * sum_i g_i(x, t) of the state it pulls, FP32, nt_capacity x ny x pitch x 4
+ * bytes of device memory (a 4096^2 run of 1000 steps: 67 GB).  lb_adjoint
+ * then needs neither checkpoints nor replays when the tape covers its nt steps
+ * and the receivers were set at t0.  nt_capacity = 0 frees the tape.
+ * lb_init_pressure and lb_set_state restart it at their time.  Any storage
+ * (FP16 included: the adjoint needs only rho), 2-D, no patch (LB_ESTATE);
+ * LB_ENOMEM when the tape does not fit.  Synchronises. */
+lb_status lb_record_rho(lb_ctx *ctx, int nt_capacity);
+
 /* Discrete adjoint of the nt steps that followed the checkpointed start time
  * t0 (the paper has no adjoint; the scheme is linear in g, so the adjoint step is
  * the exact transpose: reverse streaming, K^T = (I - C (I - E))^T, receiver
@@ -188,9 +199,11 @@ lb_status lb_checkpoint_every(lb_ctx *ctx, int every);
  * e.g. p - d for J = 1/2 sum (p - d)^2; the receivers must have been set at t0.
  * Outputs (any may be NULL): grad_c [ny][nx] = dJ/dc_map (c_ref held fixed),
  * grad_src [nt] = dJ/dS[t0 + n], grad_g0 [Q][ny][nx] = dJ/dg(t0).
- * on_device applies to dJdp and all outputs.  Forward states are replayed
- * from the checkpoints (two levels, ~2 sqrt(every) + 3 extra states of device
- * memory).  The context's own state is left untouched.  Synchronises.
+ * on_device applies to dJdp and all outputs.  With a rho tape covering the nt
+ * steps (lb_record_rho; t0 is then the tape's start) the sweep reads rho from
+ * it; otherwise forward states are replayed from the checkpoints (two levels,
+ * ~2 sqrt(every) + 3 extra states of device memory).  The context's own state
+ * is left untouched.  Synchronises.
  * With BF16 storage the replayed forward states are the stored BF16 ones and the
  * adjoint runs in FP32: the gradient of the exact scheme along that trajectory,
  * which differs from the FP32 run's by about the forward's BF16 error. */
@@ -205,8 +218,9 @@ lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *grad_c, doub
  * FP32/BF16 shot by one step per scheduling round with a single batched launch
  * per (lattice, collision, boundary, storage) group, so small shots share the
  * GPU and requests that arrive while others run join the batch at the next
- * round.  FP16 shots step on their own.  A request that asks for a gradient is
- * checkpointed during its forward run and its adjoint (lb_adjoint, J = 1/2
+ * round.  FP16 shots step on their own.  A request that asks for a gradient
+ * records the forward rho tape or keeps checkpoints during its forward run
+ * (lb_request.checkpoint_every) and its adjoint (lb_adjoint, J = 1/2
  * sum (p - d)^2 over its traces) runs on a worker thread on its own stream,
  * overlapping the batched forward work.  Results do not depend on what else
  * is in the batch: each shot runs the same kernels with the same arithmetic.
@@ -231,7 +245,10 @@ typedef struct {
     int nt;                  /* steps to run; traces have nt rows */
     const float *observed;   /* [nt][nrec] host data d (gradient requests only) */
     int want_gradient;       /* 1: also dJ/dc_map and dJ/dS for J = 1/2 sum (p - d)^2 */
-    int checkpoint_every;    /* adjoint checkpoint interval, 0: 200 */
+    int checkpoint_every;    /* gradient requests: > 0 checkpoints every that many steps
+                                (FP32 / BF16); < 0 the forward rho tape (lb_record_rho, any
+                                storage); 0: the tape when it needs at most a quarter of the
+                                server's budget, else checkpoints every 200 steps */
 } lb_request;
 
 lb_status lb_server_create(const lb_server_config *cfg, lb_server **out);
@@ -299,7 +316,8 @@ lb_status lb_invariants_noalloc(const float *g, const float *c_map, int lattice,
 /* Device bytes lb_create would allocate for cfg (refinement patches included),
  * plus the receiver trace for nt steps when nrec > 0, plus what lb_adjoint needs
  * for nt steps when want_adjoint > 0 (the checkpoint interval; 1 means the
- * default 200). */
+ * default 200) or, for want_adjoint = -1, the rho tape of nt steps
+ * (lb_record_rho) and what lb_adjoint needs beside it. */
 lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint, size_t *bytes);
 
 /* Fourier projections of the pressure for dispersion diagnostics (the

@@ -592,6 +592,33 @@ bool ckpt_reserve(lb_ctx *ctx, void **dst, const void **src, size_t *bytes) {
     return true;
 }
 
+void tape_reset(lb_ctx *ctx) { ctx->tape_t0 = ctx->t; }
+
+float *tape_row(const lb_ctx *ctx, long long t) {
+    const long long r = t - ctx->tape_t0;
+    if (!ctx->rho_tape || r < 0 || r >= ctx->tape_cap) return nullptr;
+    return ctx->rho_tape + r * (long long)ctx->ny * ctx->pitch;
+}
+
+extern "C" lb_status lb_record_rho(lb_ctx *ctx, int nt_capacity) {
+    if (!ctx) return LB_EINVAL;
+    if (nt_capacity < 0) return fail(ctx, LB_EINVAL, "nt_capacity < 0");
+    if (nt_capacity > 0 && (ctx->Q == 7 || ctx->refined))
+        return fail(ctx, LB_ESTATE, "the rho tape serves the 2-D adjoint without a patch");
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);  // steps may still write the old tape
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rho tape");
+    if (ctx->rho_tape) dev_free(ctx, ctx->rho_tape);
+    ctx->rho_tape = nullptr;
+    ctx->tape_cap = 0;
+    if (nt_capacity == 0) return LB_OK;
+    const size_t bytes = (size_t)nt_capacity * ctx->ny * ctx->pitch * 4;
+    ctx->rho_tape = static_cast<float *>(dev_alloc(ctx, bytes));
+    if (!ctx->rho_tape) return fail(ctx, LB_ENOMEM, "rho tape of %d steps (%zu bytes)", nt_capacity, bytes);
+    ctx->tape_cap = nt_capacity;
+    tape_reset(ctx);
+    return LB_OK;
+}
+
 extern "C" lb_status lb_checkpoint_every(lb_ctx *ctx, int every) {
     if (!ctx) return LB_EINVAL;
     if (every > 0 && ctx->Q == 7) return fail(ctx, LB_ESTATE, "the adjoint is 2-D (D2Q5 / D2Q9)");
@@ -606,22 +633,31 @@ extern "C" lb_status lb_checkpoint_every(lb_ctx *ctx, int every) {
 extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *grad_c,
                                 double *grad_src, float *grad_g0, int on_device) {
     if (!ctx) return LB_EINVAL;
-    const int C = ctx->ckpt_every;
-    if (C <= 0) return fail(ctx, LB_ESTATE, "call lb_checkpoint_every before stepping");
     if (nt < 1) return fail(ctx, LB_EINVAL, "nt < 1");
     if (ctx->nrec > 0 && !dJdp) return fail(ctx, LB_EINVAL, "dJdp is NULL");
-    if (ctx->t - ctx->ckpt_t0 < nt || (long long)ctx->ckpt_count * C < nt)
-        return fail(ctx, LB_ESTATE, "checkpoints cover %lld steps, %d requested",
-                    std::min<long long>(ctx->t - ctx->ckpt_t0, (long long)ctx->ckpt_count * C), nt);
-    if (ctx->nrec > 0 && ctx->ckpt_t0 != ctx->t_rec0)
-        return fail(ctx, LB_ESTATE, "receivers must be set at the checkpointed start time");
+    // The forward rho tape (lb_record_rho) covers the nt steps: no checkpoints, no replays.
+    const bool taped = ctx->rho_tape && nt <= ctx->tape_cap && ctx->t - ctx->tape_t0 >= nt &&
+                       (ctx->nrec == 0 || ctx->tape_t0 == ctx->t_rec0);
+    const int C = taped ? 0 : ctx->ckpt_every;
+    if (!taped) {
+        if (C <= 0)
+            return fail(ctx, LB_ESTATE,
+                        "call lb_checkpoint_every or lb_record_rho (at the receivers' start time) "
+                        "before stepping");
+        if (ctx->t - ctx->ckpt_t0 < nt || (long long)ctx->ckpt_count * C < nt)
+            return fail(ctx, LB_ESTATE, "checkpoints cover %lld steps, %d requested",
+                        std::min<long long>(ctx->t - ctx->ckpt_t0, (long long)ctx->ckpt_count * C),
+                        nt);
+        if (ctx->nrec > 0 && ctx->ckpt_t0 != ctx->t_rec0)
+            return fail(ctx, LB_ESTATE, "receivers must be set at the checkpointed start time");
+    }
     const int Q = ctx->Q;
     // forward states (checkpoints, replays) in the storage type; adjoint states FP32
     const size_t plane = (size_t)ctx->ny * ctx->pitch, sbytes = (size_t)Q * plane * ctx->ebytes,
                  lbytes = (size_t)Q * plane * 4;
     // replay plan: the rho tape holds T steps; sub-checkpoints every T steps when T < C
-    const int T = adj_tape_steps(plane * 4, C);
-    const int nsub = (C + T - 1) / T;
+    const int T = taped ? 0 : adj_tape_steps(plane * 4, C);
+    const int nsub = taped ? 0 : (C + T - 1) / T;
     std::vector<void *> mine;
     auto grab = [&](size_t b) {
         void *p = dev_alloc(ctx, b);
@@ -633,14 +669,17 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
         for (void *p : mine) dev_free(ctx, p);
         return st;
     };
-    void *X[2];
-    for (auto &p : X)
-        if (!(p = grab(sbytes))) return release(fail(ctx, LB_ENOMEM, "replay states"));
-    std::vector<void *> SC(nsub, nullptr);  // SC[0] is the segment's checkpoint itself
-    for (int j = 1; j < nsub; j++)
-        if (!(SC[j] = grab(sbytes))) return release(fail(ctx, LB_ENOMEM, "sub-checkpoints"));
-    float *tape = static_cast<float *>(grab((size_t)T * plane * 4));
-    if (!tape) return release(fail(ctx, LB_ENOMEM, "rho tape (%d steps)", T));
+    void *X[2] = {nullptr, nullptr};
+    std::vector<void *> SC(std::max(nsub, 1), nullptr);  // SC[0] is the segment's checkpoint
+    float *tape = ctx->rho_tape;
+    if (!taped) {
+        for (auto &p : X)
+            if (!(p = grab(sbytes))) return release(fail(ctx, LB_ENOMEM, "replay states"));
+        for (int j = 1; j < nsub; j++)
+            if (!(SC[j] = grab(sbytes))) return release(fail(ctx, LB_ENOMEM, "sub-checkpoints"));
+        tape = static_cast<float *>(grab((size_t)T * plane * 4));
+        if (!tape) return release(fail(ctx, LB_ENOMEM, "rho tape (%d steps)", T));
+    }
     float *L[2];
     for (auto &p : L)
         if (!(p = static_cast<float *>(grab(lbytes)))) return release(fail(ctx, LB_ENOMEM, "adjoint state"));
@@ -696,7 +735,7 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
     }
     StepArgs base = base_args(ctx);
     base.trace_row = nullptr;  // replays record nothing
-    const long long t0 = ctx->ckpt_t0;
+    const long long t0 = taped ? ctx->tape_t0 : ctx->ckpt_t0;
     const int segs4 = (ctx->nx + 127) / 128;
     const int adj_blocks = (int)(((long long)ctx->ny * segs4 + kWarps - 1) / kWarps);
     // replay steps t = from .. from + n - 1 starting at state `in`; the state after the
@@ -730,45 +769,53 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
         }
     };
     int li = 0;  // L[li] holds lambda^{t+1}
-    const int nseg = (nt + C - 1) / C;
-    for (int k = nseg - 1; k >= 0; k--) {
-        const long long ta = t0 + (long long)k * C, tb = std::min<long long>(ta + C, t0 + nt);
-        const bool raw_a = (k == 0) && ctx->ckpt_raw0;
-        const int nsc = (int)((tb - ta + T - 1) / T);
-        SC[0] = ctx->ckpt[k];
-        for (int j = 1; j < nsc; j++)  // place the sub-checkpoints
-            replay(SC[j - 1], raw_a && j == 1, ta + (long long)(j - 1) * T, T, SC[j], false);
-        // sweep the sub-segments backwards: replay recording rho, then the adjoint steps
-        for (int j = nsc - 1; j >= 0; j--) {
-            const long long sa = ta + (long long)j * T, sb = std::min<long long>(sa + T, tb);
-            const int len = (int)(sb - sa);
-            replay(SC[j], raw_a && j == 0, sa, len, nullptr, true);
-            for (int m = len - 1; m >= 0;) {
-                StepArgs a = base;
-                a.t = sa + m;
-                AdjArgs d;
-                d.lam_in = L[li];
-                d.lam_out = L[li ^ 1];
-                d.rho = tape + (size_t)m * plane;
-                d.grad = grad;
-                d.grad_src = gsrc;
-                d.t0 = t0;
-                d.resid = resid;
-                d.nrec = ctx->nrec;
-                d.segs = segs4;
-                if (m + 1 >= Ka) {  // levels sa + m .. sa + m - Ka + 1 in one launch
-                    tbb.rho_hi = d.rho;
-                    tbb.t_hi = a.t;
-                    launch_pdl(adj_tb, tb_grid, dim3(kTbThreads), tb_smem, ctx->stream, a, d, tbb);
-                    m -= Ka;
-                } else {
-                    launch_pdl(adj, dim3(adj_blocks), dim3(kThreads), 0, ctx->stream, a, d);
-                    if (ctx->nrec > 0)
-                        launch_pdl(adj_rec, dim3((ctx->nrec + 255) / 256), dim3(256), 0,
-                                   ctx->stream, a, d);
-                    m -= 1;
-                }
-                li ^= 1;
+    // the adjoint steps of times sa + len - 1 .. sa; rho(sa + m) at rho0 + m plane
+    auto sweep = [&](long long sa, int len, const float *rho0) {
+        for (int m = len - 1; m >= 0;) {
+            StepArgs a = base;
+            a.t = sa + m;
+            AdjArgs d;
+            d.lam_in = L[li];
+            d.lam_out = L[li ^ 1];
+            d.rho = rho0 + (size_t)m * plane;
+            d.grad = grad;
+            d.grad_src = gsrc;
+            d.t0 = t0;
+            d.resid = resid;
+            d.nrec = ctx->nrec;
+            d.segs = segs4;
+            if (m + 1 >= Ka) {  // levels sa + m .. sa + m - Ka + 1 in one launch
+                tbb.rho_hi = d.rho;
+                tbb.t_hi = a.t;
+                launch_pdl(adj_tb, tb_grid, dim3(kTbThreads), tb_smem, ctx->stream, a, d, tbb);
+                m -= Ka;
+            } else {
+                launch_pdl(adj, dim3(adj_blocks), dim3(kThreads), 0, ctx->stream, a, d);
+                if (ctx->nrec > 0)
+                    launch_pdl(adj_rec, dim3((ctx->nrec + 255) / 256), dim3(256), 0,
+                               ctx->stream, a, d);
+                m -= 1;
+            }
+            li ^= 1;
+        }
+    };
+    if (taped) {
+        sweep(t0, nt, ctx->rho_tape);
+    } else {
+        const int nseg = (nt + C - 1) / C;
+        for (int k = nseg - 1; k >= 0; k--) {
+            const long long ta = t0 + (long long)k * C, tb = std::min<long long>(ta + C, t0 + nt);
+            const bool raw_a = (k == 0) && ctx->ckpt_raw0;
+            const int nsc = (int)((tb - ta + T - 1) / T);
+            SC[0] = ctx->ckpt[k];
+            for (int j = 1; j < nsc; j++)  // place the sub-checkpoints
+                replay(SC[j - 1], raw_a && j == 1, ta + (long long)(j - 1) * T, T, SC[j], false);
+            // sweep the sub-segments backwards: replay recording rho, then the adjoint steps
+            for (int j = nsc - 1; j >= 0; j--) {
+                const long long sa = ta + (long long)j * T, sb = std::min<long long>(sa + T, tb);
+                const int len = (int)(sb - sa);
+                replay(SC[j], raw_a && j == 0, sa, len, nullptr, true);
+                sweep(sa, len, tape);
             }
         }
     }

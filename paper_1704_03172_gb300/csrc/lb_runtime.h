@@ -34,6 +34,9 @@ struct lb_ctx {
     std::vector<void *> ckpt;       // ckpt[k]: stored buffer at time k * ckpt_every
     int ckpt_count = 0;             // valid checkpoints, from time ckpt_t0
     long long ckpt_t0 = 0;
+    float *rho_tape = nullptr;      // lb_record_rho: rho(t) [tape_cap][ny][pitch] from tape_t0
+    long long tape_t0 = 0;
+    int tape_cap = 0;
     int *tb_off = nullptr;          // temporal blocking: per-tile receiver list offsets
     int *tb_rec = nullptr;          // receiver indices grouped by tile
     bool ckpt_raw0 = false;         // raw flag of the time-0 checkpoint
@@ -111,6 +114,10 @@ lb_status ckpt_maybe_save(lb_ctx *ctx);
 // k if one is due before the next step and returns the copy to make
 bool ckpt_reserve(lb_ctx *ctx, void **dst, const void **src, size_t *bytes);
 void ckpt_reset(lb_ctx *ctx);
+// the forward rho tape (adjoint.cu): restart it at the current time; its row for step t
+// (nullptr outside the tape)
+void tape_reset(lb_ctx *ctx);
+float *tape_row(const lb_ctx *ctx, long long t);
 
 // temporal blocking (tblock.cu)
 bool tb_supported(int Q, int K);

@@ -328,7 +328,13 @@ lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint,
         if (k >= 1) b += q * fplane * 4 + 2 * nI * q * 4;
         if (nrec > 0) b += (size_t)nrec * 12 + 1024;
     }
-    if (want_adjoint) {
+    if (want_adjoint < 0) {  // the forward rho tape, the adjoint pair, the FP64 gradient,
+                             // dJ/dS and the region receiver lists
+        const size_t tiles = ((size_t)std::max(cfg->nx, 1) + 31) / 32 *
+                             (((size_t)std::max(cfg->ny, 1) + 31) / 32);
+        b += (size_t)std::max(nt, 0) * plane * 4 + 2 * q * plane * 4 + plane * 8 +
+             (size_t)std::max(nt, 0) * 8 + (tiles + 1) * 4 + (size_t)std::max(nrec, 0) * 4 * 8;
+    } else if (want_adjoint) {
         // lb_adjoint: checkpoints every C steps and, in the storage type, the two replay
         // states and the sub-checkpoints; the FP32 rho tape (T planes), the FP32 adjoint
         // pair, the FP64 gradient and dJ/dS; the receiver lists of the blocked reverse
@@ -646,6 +652,7 @@ lb_status lb_init_pressure(lb_ctx *ctx, const float *p0, int on_device) {
     ctx->t_rec0 = 0;
     ctx->fine_ready = false;
     ckpt_reset(ctx);
+    tape_reset(ctx);
     return set_state_common(ctx, p0, on_device, 0);
 }
 
@@ -654,6 +661,7 @@ lb_status lb_set_state(lb_ctx *ctx, const float *in, int on_device) {
     if (!in) return fail(ctx, LB_EINVAL, "state is NULL");
     if (ctx->refined) return fail(ctx, LB_ESTATE, "lb_set_state is not available with a patch");
     ckpt_reset(ctx);  // checkpoints describe one trajectory; a new state starts another
+    tape_reset(ctx);
     return set_state_common(ctx, in, on_device, 1);
 }
 
@@ -707,6 +715,8 @@ StepArgs prepare_step(lb_ctx *ctx) {
     a.t = ctx->t;
     a.raw = ctx->raw ? 1 : 0;
     ctx->raw = false;
+    a.rho_out = tape_row(ctx, ctx->t);  // forward rho tape for lb_adjoint, if recording
+    a.rho_stride = (long long)ctx->ny * ctx->pitch;
     long long row = ctx->t - ctx->t_rec0;
     a.trace_row = (ctx->trace && row >= 0 && row < ctx->trace_cap) ? ctx->trace + row * ctx->nrec
                                                                   : nullptr;
@@ -731,6 +741,8 @@ lb_status launch_step(lb_ctx *ctx, StepFn fn, StepArgs &a) {
     }
     a.raw = ctx->raw ? 1 : 0;
     ctx->raw = false;
+    a.rho_out = tape_row(ctx, ctx->t);  // forward rho tape for lb_adjoint, if recording
+    a.rho_stride = (long long)ctx->ny * ctx->pitch;
     long long row = ctx->t - ctx->t_rec0;
     a.trace_row = (ctx->trace && row >= 0 && row < ctx->trace_cap) ? ctx->trace + row * ctx->nrec
                                                                   : nullptr;
@@ -773,7 +785,10 @@ lb_status lb_step(lb_ctx *ctx, int n) {
                 ctx->ckpt_every > 0 && (ctx->t - ctx->ckpt_t0) % ctx->ckpt_every + K > ctx->ckpt_every;
             const bool straddle_trace =
                 ctx->trace && row < ctx->trace_cap && row + K > ctx->trace_cap;
-            if (!straddle_ckpt && !straddle_trace) {
+            const long long trow = ctx->t - ctx->tape_t0;
+            const bool straddle_tape =
+                ctx->rho_tape && trow < ctx->tape_cap && trow + K > ctx->tape_cap;
+            if (!straddle_ckpt && !straddle_trace && !straddle_tape) {
                 lb_status st = tb_launch(ctx, K);
                 if (st != LB_OK) return st;
                 k += K;

@@ -64,6 +64,7 @@ struct Req {
     std::vector<double> wav;
     std::vector<int> rec;
     int src_x = 0, src_y = 0, nt = 0, want_grad = 0, ckpt = 200;
+    bool tape = false;  // gradient from the forward rho tape (no checkpoints, no replays)
     size_t fp = 0;
     RS state = RS::Pending;
     lb_ctx *ctx = nullptr;
@@ -210,7 +211,8 @@ void admit(lb_server *S, Req *r) {
         st = lb_set_source(ctx, r->src_x, r->src_y, r->wav.data(), (int)r->wav.size());
     if (st == LB_OK) st = lb_set_receivers(ctx, r->rec.data(), (int)r->rec.size() / 2, r->nt);
     if (st == LB_OK) st = lb_init_pressure(ctx, nullptr, 0);
-    if (st == LB_OK && r->want_grad) st = lb_checkpoint_every(ctx, r->ckpt);
+    if (st == LB_OK && r->want_grad)
+        st = r->tape ? lb_record_rho(ctx, r->nt) : lb_checkpoint_every(ctx, r->ckpt);
     if (st == LB_OK &&
         !(r->h_traces = static_cast<float *>(pin_get(S, (size_t)r->nt * (r->rec.size() / 2) * 4, &r->h_cap))))
         st = LB_ENOMEM;
@@ -553,8 +555,6 @@ lb_status lb_server_submit(lb_server *S, const lb_request *q, long long *id) {
     if (q->cfg.n_patches > 0) return fail(nullptr, LB_EINVAL, "served shots have no patch");
     if (q->cfg.lattice == LB_D3Q7 || q->cfg.nz > 1)
         return fail(nullptr, LB_EINVAL, "served shots are 2-D (D2Q5 / D2Q9)");
-    if (q->want_gradient && q->cfg.storage != LB_F32 && q->cfg.storage != LB_BF16)
-        return fail(nullptr, LB_EINVAL, "gradient requests need FP32 or BF16 storage");
     Req *r = new Req();
     r->cfg = q->cfg;
     r->cmap.assign(q->cfg.c_map, q->cfg.c_map + (size_t)q->cfg.nx * q->cfg.ny);
@@ -567,7 +567,17 @@ lb_status lb_server_submit(lb_server *S, const lb_request *q, long long *id) {
     r->nt = q->nt;
     r->want_grad = q->want_gradient ? 1 : 0;
     r->ckpt = q->checkpoint_every > 0 ? q->checkpoint_every : 200;
-    lb_footprint(&q->cfg, q->nt, q->nrec, r->want_grad ? r->ckpt : 0, &r->fp);
+    if (r->want_grad) {  // the forward rho tape when asked for, or (0) when it is small
+        size_t tape_fp = 0;
+        lb_footprint(&q->cfg, q->nt, q->nrec, -1, &tape_fp);
+        r->tape = q->checkpoint_every < 0 || (q->checkpoint_every == 0 && tape_fp <= S->budget / 4);
+    }
+    if (r->want_grad && !r->tape && q->cfg.storage != LB_F32 && q->cfg.storage != LB_BF16) {
+        delete r;
+        return fail(nullptr, LB_EINVAL,
+                    "checkpointed gradients need FP32 or BF16 storage (FP16: the rho tape)");
+    }
+    lb_footprint(&q->cfg, q->nt, q->nrec, r->want_grad ? (r->tape ? -1 : r->ckpt) : 0, &r->fp);
     r->fp += (size_t)q->nt * q->nrec * 4 * (r->want_grad ? 2 : 0);  // observed + residual
     std::lock_guard<std::mutex> lk(S->mu);
     if (r->fp > S->budget) {

@@ -267,6 +267,9 @@ lb_status tb_launch(lb_ctx *ctx, int K) {
     long long row = ctx->t - ctx->t_rec0;
     a.trace_row = (ctx->trace && ctx->tb_off && row >= 0 && row + K <= ctx->trace_cap)
                       ? ctx->trace + row * ctx->nrec : nullptr;
+    // forward rho tape (the caller keeps K steps inside it): level j at rho_out + j plane
+    a.rho_out = tape_row(ctx, ctx->t);
+    a.rho_stride = (long long)ctx->ny * ctx->pitch;
     lb_status st = tb_launch_args(ctx, a, K);
     if (st != LB_OK) return st;
     ctx->cur ^= 1;

@@ -95,6 +95,7 @@ _SIGS = {
     "lb_get_time": [_ctx_p, ctypes.POINTER(ctypes.c_longlong)],
     "lb_sync": [_ctx_p],
     "lb_wait_selftest": [_ctx_p, ctypes.c_int],
+    "lb_record_rho": [_ctx_p, ctypes.c_int],
     "lb_footprint": [_cfgp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                      ctypes.POINTER(ctypes.c_size_t)],
     "lb_info": [_ctx_p, _dp, ctypes.c_int],
@@ -260,6 +261,10 @@ def lb_get_time(ctx) -> int:
 
 def lb_sync(ctx):
     return _check(_lib.lb_sync(ctx), ctx)
+
+
+def lb_record_rho(ctx, nt_capacity):
+    return _check(_lib.lb_record_rho(ctx, int(nt_capacity)), ctx)
 
 
 def lb_wait_selftest(ctx, timeout_us):

@@ -176,6 +176,11 @@ class LBSim:
         """Keep adjoint checkpoints every `every` steps from the current time."""
         lbac.lb_checkpoint_every(self.ctx, every)
 
+    def record_rho(self, nt):
+        """Record the forward density tape for the next `nt` steps (no checkpoints or replays
+        needed by adjoint(); nt * ny * pitch * 4 bytes of device memory; 0 frees it)."""
+        lbac.lb_record_rho(self.ctx, nt)
+
     def adjoint(self, dJdp, nt=None, want_g0=False):
         """Gradients of J given dJ/dp at the receivers (trace rows): returns
         (dJ/dc_map [ny, nx] float32, dJ/dS [nt] float64, dJ/dg(t0) or None)."""
@@ -223,7 +228,9 @@ class LBForward(torch.autograd.Function):
 
     forward(c_map [ny, nx], wavelet [nt], spec) -> traces [nt, nrec], where spec is a
     dict of LBSim keyword arguments plus "source_xy", "receivers", "nt" and
-    "checkpoint_every" (c_ref must be given: it is held fixed under differentiation).
+    "checkpoint_every" (> 0: checkpoints; < 0: the forward rho tape; 0 or absent: the tape
+    when it takes at most a quarter of the free device memory, else checkpoints every 200
+    steps).  c_ref must be given: it is held fixed under differentiation.
     """
 
     @staticmethod
@@ -232,14 +239,20 @@ class LBForward(torch.autograd.Function):
         nt = int(spec.pop("nt"))
         sxy = spec.pop("source_xy")
         rec = spec.pop("receivers")
-        every = int(spec.pop("checkpoint_every", 200))
+        every = int(spec.pop("checkpoint_every", 0))
         if spec.get("c_ref") is None:
             raise ValueError("spec['c_ref'] must be fixed for differentiation")
         sim = LBSim(c_map.detach(), **spec)
         sim.set_source(sxy[0], sxy[1], wavelet.detach().double().cpu().numpy())
         sim.set_receivers(rec, nt)
         sim.init_pressure(None)
-        sim.checkpoint_every(every)
+        if every == 0:
+            tape_bytes = nt * sim.ny * (-(-sim.nx // 32) * 32) * 4
+            every = -1 if tape_bytes <= torch.cuda.mem_get_info(sim.device)[0] // 4 else 200
+        if every < 0:
+            sim.record_rho(nt)
+        else:
+            sim.checkpoint_every(every)
         sim.step(nt)
         traces = sim.traces(nt).clone()
         ctx.sim, ctx.nt = sim, nt
@@ -263,7 +276,7 @@ class LBServer:
         self._meta = {}
 
     def submit(self, c_map, *, nt, source, receivers, observed=None, want_gradient=False,
-               checkpoint_every=200, lattice=5, collision="bgk", tau=0.5, s=None,
+               checkpoint_every=0, lattice=5, collision="bgk", tau=0.5, s=None,
                storage="f32", boundary="zero", sponge_width=0, sponge_sigma_max=0.1, c_ref=None,
                w_ref=(4 / 9, 1 / 9, 1 / 36)):
         c = np.ascontiguousarray(c_map, dtype=np.float32)

@@ -53,8 +53,11 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("mode", ["ckpt", "tape"])
 @pytest.mark.parametrize("case", CASES)
-def test_blocked_adjoint_matches_oracle(sim_cls, oracle_mod, case):
+def test_blocked_adjoint_matches_oracle(sim_cls, oracle_mod, case, mode):
+    # ckpt: checkpoints every `every` steps, replays; tape: the forward run records rho
+    # (lb_record_rho) and the sweep reads it, no replay
     Q, coll, tau, s, per, sponge, nx, ny, every, nt = case
     out = 48 - 2 * (8 if Q == 5 else 4)
     rng = np.random.default_rng(nx * 1000 + ny)
@@ -68,7 +71,10 @@ def test_blocked_adjoint_matches_oracle(sim_cls, oracle_mod, case):
     sim.set_receivers(rec, nt)
     g0 = (rng.normal(size=(Q, ny, nx)) * 0.1).astype(np.float32)
     sim.set_state(g0)
-    sim.checkpoint_every(every)
+    if mode == "ckpt":
+        sim.checkpoint_every(every)
+    else:
+        sim.record_rho(nt)
     sim.step(nt)
     tr = sim.traces(nt).cpu().numpy()
     R = tr - rng.normal(size=tr.shape).astype(np.float32)
@@ -115,3 +121,90 @@ def test_blocked_adjoint_bf16_storage(sim_cls, oracle_mod):
     assert rel(gs, os_) < TOL
     assert rel(gg, og) < TOL
     assert rel(gc, oc) < 4e-2
+
+
+def _tape_run(sim_cls, c, Q, nt, rec, src, storage="f32", mode="tape", time_block=1, seed=7):
+    rng = np.random.default_rng(seed)
+    ny, nx = c.shape
+    kw = dict(tau=0.5, s=[1.2, 0.9, 0.9, 1.6, 1.3] if Q == 5 else None, c_ref=1.0,
+              w_ref=(0.4, 0.11, 0.04))
+    sim = sim_cls(c, lattice=Q, collision="mrt" if Q == 5 else "bgk", sponge_width=6,
+                  sponge_sigma_max=0.15, storage=storage, time_block=time_block, **kw)
+    sim.set_source(*src)
+    sim.set_receivers(rec, nt)
+    sim.init_pressure(None)
+    if mode == "tape":
+        sim.record_rho(nt)
+    else:
+        sim.checkpoint_every(12)
+    sim.step(nt)
+    R = (sim.traces(nt).cpu().numpy() - rng.normal(size=(nt, len(rec))) * 1e-3).astype(np.float32)
+    gc, gs, gg = sim.adjoint(R, nt, want_g0=True)
+    out = (gc.cpu().numpy(), gs.cpu().numpy(), gg.cpu().numpy(), R)
+    sim.close()
+    return out, kw
+
+
+def test_tape_and_checkpoint_gradients_agree(sim_cls):
+    nx, ny, nt = 150, 110, 45
+    c = W.random_medium(nx, ny, 11, 0.5, 1.0)
+    rec = _receivers(np.random.default_rng(2), nx, ny, 32)
+    src = (75, 55, W.ricker(nt, 0.06))
+    a, _ = _tape_run(sim_cls, c, 5, nt, rec, src, mode="tape")
+    b, _ = _tape_run(sim_cls, c, 5, nt, rec, src, mode="ckpt")
+    for x, y in zip(a[:3], b[:3]):
+        assert rel(x, y) < 1e-6
+
+
+@pytest.mark.parametrize("storage,tol_c", [("f16", 2e-2), ("bf16", 4e-2)])
+def test_tape_adjoint_low_precision_storage(sim_cls, oracle_mod, storage, tol_c):
+    # with the tape the adjoint needs only rho, so FP16 storage (whose range scales are not
+    # replayed) works too; dJ/dS and dJ/dg0 depend on the adjoint state alone and keep the
+    # FP32 bound, dJ/dc carries the stored densities' rounding
+    Q, nx, ny, nt = 5, 140, 100, 40
+    c = W.random_medium(nx, ny, 3, 0.5, 1.0)
+    rec = _receivers(np.random.default_rng(5), nx, ny, 32)
+    src = (70, 50, W.ricker(nt, 0.06))
+    (gc, gs, gg, R), kw = _tape_run(sim_cls, c, Q, nt, rec, src, storage=storage)
+    P = oracle_mod.Problem(Q, nx, ny, c, mrt=True, sponge_width=6, sponge_sigma_max=0.15,
+                           source=src, receivers=rec, **kw)
+    oc, os_, og = oracle_mod.adjoint(P, P.zeros(), nt, R.astype(np.float64))
+    assert rel(gs, os_) < TOL
+    assert rel(gg, og) < TOL
+    assert rel(gc, oc) < tol_c
+
+
+def test_tape_with_time_blocked_forward(sim_cls, oracle_mod):
+    # an FP32 forward with 8 fused steps per launch records rho through the time-blocked
+    # kernel's per-level output; steps that would leave the tape run singly
+    Q, nx, ny, nt = 5, 150, 110, 43
+    c = W.random_medium(nx, ny, 4, 0.5, 1.0)
+    rec = _receivers(np.random.default_rng(6), nx, ny, 32)
+    src = (75, 55, W.ricker(nt, 0.06))
+    (gc, gs, gg, R), kw = _tape_run(sim_cls, c, Q, nt, rec, src, time_block=8)
+    P = oracle_mod.Problem(Q, nx, ny, c, mrt=True, sponge_width=6, sponge_sigma_max=0.15,
+                           source=src, receivers=rec, **kw)
+    oc, os_, og = oracle_mod.adjoint(P, P.zeros(), nt, R.astype(np.float64))
+    assert rel(gc, oc) < TOL
+    assert rel(gs, os_) < TOL
+    assert rel(gg, og) < TOL
+
+
+def test_tape_lifecycle(sim_cls):
+    from paper_1704_03172_gb300 import lbac
+    nx, ny = 64, 48
+    c = W.random_medium(nx, ny, 8, 0.5, 1.0)
+    sim = sim_cls(c, sponge_width=4)
+    sim.set_receivers(np.array([[30, 20]], np.int32), 30)
+    sim.init_pressure(None)
+    sim.record_rho(10)
+    sim.step(20)                                   # the tape covers the first 10 steps only
+    with pytest.raises(lbac.LBError) as e:         # no checkpoints, tape too short for 20
+        sim.adjoint(np.ones((20, 1), np.float32), 20)
+    assert e.value.status == lbac.LB_ESTATE
+    gc, gs, _ = sim.adjoint(np.ones((10, 1), np.float32), 10)
+    assert np.isfinite(gc.cpu().numpy()).all()
+    sim.record_rho(0)                              # freed
+    with pytest.raises(lbac.LBError):
+        sim.adjoint(np.ones((10, 1), np.float32), 10)
+    sim.close()

@@ -172,3 +172,44 @@ def test_wait_times_out_and_then_completes(mods):
     srv.close()
     assert r["done"] >= r["start"] >= r["submit"]
     assert np.isfinite(r["traces"]).all()
+
+
+@pytest.mark.parametrize("every,storage", [(-1, "f32"), (0, "bf16"), (-1, "f16")])
+def test_tape_gradient_request_matches_direct_tape_adjoint(mods, oracle_mod, every, storage):
+    # gradient requests that record the forward rho tape (checkpoint_every < 0, or 0 with a
+    # small tape) run no replay; FP16 storage works there.  The served shot runs the same
+    # kernels as a direct context with lb_record_rho: identical traces, the same gradient
+    LBServer, LBSim, _ = mods
+    n, nt = 80, 150
+    c, s = _shot(n, 6, nt, storage=storage, grad=True)
+    s["checkpoint_every"] = every
+    rng = np.random.default_rng(5)
+    d = rng.normal(size=(nt, 16)).astype(np.float32) * 1e-3
+    s["observed"] = d
+    srv = LBServer(max_active=4, rounds_per_pass=8)
+    rid = srv.submit(c, **s)
+    c2, s2 = _shot(128, 8, 120, storage="f32", grad=True)
+    rid2 = srv.submit(c2, **s2)
+    srv.wait(rid, 120000)
+    res = srv.result(rid)
+    srv.wait(rid2, 120000)
+    srv.result(rid2)
+    srv.close()
+    sim = LBSim(c, lattice=5, tau=0.5, storage=storage, sponge_width=6, c_ref=5500.0)
+    sim.set_source(*s["source"])
+    sim.set_receivers(s["receivers"], nt)
+    sim.init_pressure(None)
+    sim.record_rho(nt)
+    sim.step(nt)
+    tr = sim.traces(nt).cpu().numpy()
+    gc, gs, _ = sim.adjoint((tr - d).astype(np.float32), nt)
+    sim.close()
+    np.testing.assert_array_equal(res["traces"], tr)
+    np.testing.assert_allclose(res["grad_c"], gc.cpu().numpy(), rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(res["grad_src"], gs.cpu().numpy(), rtol=1e-6, atol=1e-15)
+    if storage == "f32":  # and the FP64 oracle
+        P = oracle_mod.Problem(5, n, n, c, c_ref=5500.0, tau=0.5, sponge_width=6,
+                               sponge_sigma_max=0.1, source=s["source"], receivers=s["receivers"])
+        oc, os_, _ = oracle_mod.adjoint(P, P.zeros(), nt, (res["traces"] - d).astype(np.float64))
+        assert rel(res["grad_c"], oc) < 1e-4
+        assert rel(res["grad_src"], os_) < 1e-4
