@@ -479,6 +479,7 @@ def _cpu_sample(target_s=12.0, lattice=5):
     """Time the FP64 oracle on a bounded sample of the workload (rows of the 4096^2 grid)."""
     import oracle
     oracle.build()
+    cores = oracle.max_threads()
     wl = _workload(lattice)
     rows = 256
     c = wl["c_map"][: rows]
@@ -496,10 +497,26 @@ def _cpu_sample(target_s=12.0, lattice=5):
         steps += chunk
     sec = time.perf_counter() - t0
     glups = N_GRID * rows * steps / sec / 1e9
-    return {"value": round(glups, 4), "unit": UNIT, "cores": oracle.max_threads(),
+    # one thread, on a shorter sample of the same band (the oracle's thread count is a
+    # process setting: restored to all cores afterwards)
+    def band(nthreads):
+        return oracle.Problem(lattice, N_GRID, rows, c, c_ref=wl["c_ref"], tau=wl["tau"],
+                              sponge_width=wl["sponge_width"],
+                              sponge_sigma_max=wl["sponge_sigma_max"], w_ref=wl["w_ref"],
+                              nthreads=nthreads)
+    P1 = band(1)
+    steps1, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < target_s / 4:
+        oracle.run(P1, g, 1)
+        steps1 += 1
+    sec1 = time.perf_counter() - t1
+    oracle.run(band(cores), g, 1)
+    return {"value": round(glups, 4), "unit": UNIT, "cores": cores,
             "kind": "oracle",
+            "single_thread_value": round(N_GRID * rows * steps1 / sec1 / 1e9, 5),
             "sample": f"{steps} steps of a {N_GRID}x{rows} band of the two-layer workload "
-                      f"(FP64 C, OpenMP over rows), {sec:.1f} s"}
+                      f"(FP64 C, OpenMP over rows), {sec:.1f} s; single thread: {steps1} steps, "
+                      f"{sec1:.1f} s"}
 
 
 def run_reference(args):
