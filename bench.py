@@ -43,7 +43,7 @@ ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 NCU_TRAFFIC = {
     ("lbk::step_kernel<5,false,false,float>", True): 640.35e6,
     ("stream_step_kernel<5,false,false,__nv_bfloat16>", True): 301.9e6,
-    ("tb_kernel<5,false,false,8>", False): 703.5e6,
+    ("tb_kernel<5,false,false,8>", False): 703.2e6,
 }
 
 
