@@ -485,33 +485,33 @@ __device__ __forceinline__ void collide9(float g[9], float e2, const StepArgs &a
     const float dp = a.a5 * (jx + jy), dm = a.a5 * (jx - jy);
     eq[5] = b5 + dp; eq[7] = b5 - dp;
     eq[6] = b5 - dm; eq[8] = b5 + dm;
-    if (!MRT) {
+    if constexpr (!MRT) {
 #pragma unroll
         for (int i = 0; i < 9; i++) g[i] += a.omega * (eq[i] - g[i]);
-        return;
-    }
-    float n[9];
+    } else {
+        float n[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) n[i] = g[i] - eq[i];
-    const float s14 = n[1] + n[2] + n[3] + n[4], s58 = n[5] + n[6] + n[7] + n[8];
-    // non-conserved moments of g - g^eq (rows 3..8 of M, App. A), scaled by s_k / |row_k|^2
-    const float d3 = a.s[3] * (-4.f * n[0] - s14 + 2.f * s58) * (1.f / 36.f);
-    const float d4 = a.s[4] * (n[1] - n[2] + n[3] - n[4]) * 0.25f;
-    const float d5 = a.s[5] * (4.f * n[0] - 2.f * s14 + s58) * (1.f / 36.f);
-    const float d6 = a.s[6] * (-2.f * n[1] + 2.f * n[3] + n[5] - n[6] - n[7] + n[8]) * (1.f / 12.f);
-    const float d7 = a.s[7] * (-2.f * n[2] + 2.f * n[4] + n[5] + n[6] - n[7] - n[8]) * (1.f / 12.f);
-    const float d8 = a.s[8] * (n[5] - n[6] + n[7] - n[8]) * 0.25f;
-    // g* = g - M^T (d3..d8)
-    g[0] -= -4.f * d3 + 4.f * d5;
-    g[1] -= -d3 + d4 - 2.f * d5 - 2.f * d6;
-    g[2] -= -d3 - d4 - 2.f * d5 - 2.f * d7;
-    g[3] -= -d3 + d4 - 2.f * d5 + 2.f * d6;
-    g[4] -= -d3 - d4 - 2.f * d5 + 2.f * d7;
-    const float c5 = 2.f * d3 + d5;
-    g[5] -= c5 + d6 + d7 + d8;
-    g[6] -= c5 - d6 + d7 - d8;
-    g[7] -= c5 - d6 - d7 + d8;
-    g[8] -= c5 + d6 - d7 - d8;
+        for (int i = 0; i < 9; i++) n[i] = g[i] - eq[i];
+        const float s14 = n[1] + n[2] + n[3] + n[4], s58 = n[5] + n[6] + n[7] + n[8];
+        // non-conserved moments of g - g^eq (rows 3..8 of M, App. A), scaled by s_k / |row_k|^2
+        const float d3 = a.s[3] * (-4.f * n[0] - s14 + 2.f * s58) * (1.f / 36.f);
+        const float d4 = a.s[4] * (n[1] - n[2] + n[3] - n[4]) * 0.25f;
+        const float d5 = a.s[5] * (4.f * n[0] - 2.f * s14 + s58) * (1.f / 36.f);
+        const float d6 = a.s[6] * (-2.f * n[1] + 2.f * n[3] + n[5] - n[6] - n[7] + n[8]) * (1.f / 12.f);
+        const float d7 = a.s[7] * (-2.f * n[2] + 2.f * n[4] + n[5] + n[6] - n[7] - n[8]) * (1.f / 12.f);
+        const float d8 = a.s[8] * (n[5] - n[6] + n[7] - n[8]) * 0.25f;
+        // g* = g - M^T (d3..d8)
+        g[0] -= -4.f * d3 + 4.f * d5;
+        g[1] -= -d3 + d4 - 2.f * d5 - 2.f * d6;
+        g[2] -= -d3 - d4 - 2.f * d5 - 2.f * d7;
+        g[3] -= -d3 + d4 - 2.f * d5 + 2.f * d6;
+        g[4] -= -d3 - d4 - 2.f * d5 + 2.f * d7;
+        const float c5 = 2.f * d3 + d5;
+        g[5] -= c5 + d6 + d7 + d8;
+        g[6] -= c5 - d6 + d7 - d8;
+        g[7] -= c5 - d6 - d7 + d8;
+        g[8] -= c5 + d6 - d7 - d8;
+    }
 }
 
 // D3Q7 BGK with w_0 = 1 - eta^2, w_1..6 = eta^2 / 6, c_s^2 = eta^2 / 3 (the D2Q5 rule of
