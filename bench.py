@@ -394,7 +394,7 @@ def _served(n_req, n_cal, seed=W.DEFAULT_SEED + 5, load=0.7, max_active=64):
         """The same shots through the plain per-shot API (LBSim), one after another."""
         import torch
         from paper_1704_03172_gb300.sim import LBSim
-        tape_limit = 0.2 * torch.cuda.mem_get_info()[0]  # the server's rule: budget / 4
+        tape_limit = 0.4 * torch.cuda.mem_get_info()[0]  # the server's rule: budget / 2
         t0 = time.monotonic()
         for s in shots_:
             sim = LBSim(s["c_map"], lattice=5, tau=s["tau"], storage=s["storage"],

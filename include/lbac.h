@@ -247,7 +247,7 @@ typedef struct {
     int want_gradient;       /* 1: also dJ/dc_map and dJ/dS for J = 1/2 sum (p - d)^2 */
     int checkpoint_every;    /* gradient requests: > 0 checkpoints every that many steps
                                 (FP32 / BF16); < 0 the forward rho tape (lb_record_rho, any
-                                storage); 0: the tape when it needs at most a quarter of the
+                                storage); 0: the tape when it needs at most half of the
                                 server's budget, else checkpoints every 200 steps */
 } lb_request;
 

@@ -570,7 +570,7 @@ lb_status lb_server_submit(lb_server *S, const lb_request *q, long long *id) {
     if (r->want_grad) {  // the forward rho tape when asked for, or (0) when it is small
         size_t tape_fp = 0;
         lb_footprint(&q->cfg, q->nt, q->nrec, -1, &tape_fp);
-        r->tape = q->checkpoint_every < 0 || (q->checkpoint_every == 0 && tape_fp <= S->budget / 4);
+        r->tape = q->checkpoint_every < 0 || (q->checkpoint_every == 0 && tape_fp <= S->budget / 2);
     }
     if (r->want_grad && !r->tape && q->cfg.storage != LB_F32 && q->cfg.storage != LB_BF16) {
         delete r;

@@ -229,8 +229,9 @@ class LBForward(torch.autograd.Function):
     forward(c_map [ny, nx], wavelet [nt], spec) -> traces [nt, nrec], where spec is a
     dict of LBSim keyword arguments plus "source_xy", "receivers", "nt" and
     "checkpoint_every" (> 0: checkpoints; < 0: the forward rho tape; 0 or absent: the tape
-    when it takes at most a quarter of the free device memory, else checkpoints every 200
-    steps).  c_ref must be given: it is held fixed under differentiation.
+    when it takes at most 40 % of the free device memory, as the server decides, else
+    checkpoints every 200 steps).  c_ref must be given: it is held fixed under
+    differentiation.
     """
 
     @staticmethod
@@ -248,7 +249,7 @@ class LBForward(torch.autograd.Function):
         sim.init_pressure(None)
         if every == 0:
             tape_bytes = nt * sim.ny * (-(-sim.nx // 32) * 32) * 4
-            every = -1 if tape_bytes <= torch.cuda.mem_get_info(sim.device)[0] // 4 else 200
+            every = -1 if tape_bytes <= 0.4 * torch.cuda.mem_get_info(sim.device)[0] else 200
         if every < 0:
             sim.record_rho(nt)
         else:
