@@ -208,3 +208,33 @@ def test_tape_lifecycle(sim_cls):
     with pytest.raises(lbac.LBError):
         sim.adjoint(np.ones((10, 1), np.float32), 10)
     sim.close()
+
+
+@pytest.mark.parametrize("Q", [5, 9])
+def test_tape_from_the_staged_step(sim_cls, oracle_mod, Q):
+    # BF16 on rows of >= 1024 sites runs the TMA-staged step, which writes the tape through
+    # the same per-site code; dJ/dS and dJ/dg0 keep the FP32 bound, dJ/dc the BF16 one
+    nx, ny, nt = 1100, 40, 30
+    rng = np.random.default_rng(Q)
+    c = W.random_medium(nx, ny, 9, 0.5, 1.0)
+    # receivers within reach of the source in nt steps (c_s <= 0.7 cells per step)
+    rec = np.stack([rng.integers(535, 566, 10), rng.integers(8, 33, 10)], 1).astype(np.int32)
+    src = (550, 20, W.ricker(nt, 0.06))
+    kw = dict(tau=0.5, c_ref=1.0, w_ref=(0.4, 0.11, 0.04))
+    sim = sim_cls(c, lattice=Q, sponge_width=4, sponge_sigma_max=0.15, storage="bf16", **kw)
+    assert sim.info()[2] == 2                       # 16-bit storage: the staged step
+    sim.set_source(*src)
+    sim.set_receivers(rec, nt)
+    sim.init_pressure(None)
+    sim.record_rho(nt)
+    sim.step(nt)
+    R = (sim.traces(nt).cpu().numpy() - rng.normal(size=(nt, len(rec))) * 1e-3).astype(np.float32)
+    gc, gs, gg = sim.adjoint(R, nt, want_g0=True)
+    gc, gs, gg = gc.cpu().numpy(), gs.cpu().numpy(), gg.cpu().numpy()
+    sim.close()
+    P = oracle_mod.Problem(Q, nx, ny, c, sponge_width=4, sponge_sigma_max=0.15, source=src,
+                           receivers=rec, **kw)
+    oc, os_, og = oracle_mod.adjoint(P, P.zeros(), nt, R.astype(np.float64))
+    assert rel(gs, os_) < TOL
+    assert rel(gg, og) < TOL
+    assert rel(gc, oc) < 4e-2
