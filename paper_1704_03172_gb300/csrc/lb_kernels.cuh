@@ -789,9 +789,12 @@ template <int Q, bool MRT, bool PERIODIC, typename ST>
 // Minimum resident blocks per SM: enough warps to keep ~100 KB of loads in
 // flight per SM (FP32 D2Q5 fits 5 blocks at <= 48 registers; the 8-site 16-bit
 // and the 9-population FP32 forms are held to 64 registers for 4 blocks; the
-// 9-population 16-bit form holds 72 values per thread and gets 80 registers).
+// 9-population 16-bit form holds 72 values per thread and gets 128 registers).
+// The 7-population 16-bit form (56 values) spills ~330 bytes at 64 registers and
+// still runs faster with 4 blocks than with 3 at 80 registers (GB300, 256^3 BF16:
+// 144 against 136 GLUPS; 5 blocks: 110).
 __global__ void __launch_bounds__(kThreads, Q == 5   ? (sizeof(ST) == 4 ? 5 : 4)
-                                           : Q == 7 ? (sizeof(ST) == 4 ? 4 : 3)
+                                           : Q == 7 ? 4
                                                     : (sizeof(ST) == 4 ? 4 : 2))
     step_kernel(const StepArgs a) {
     constexpr bool SC = Scaled<ST>::value;
