@@ -204,6 +204,26 @@ def _refined_variant(torch, LBSim, steps, warmup):
             "launches_per_coarse_step": 6}
 
 
+def _l2_variant(torch, LBSim, n, storage, steps, warmup=50, time_block=1):
+    """The two-layer workload scaled to n^2 (64 receivers), small enough that both state
+    buffers stay in the 129 MB L2: reported apart from the HBM-bound lines, against no
+    roofline.  time_block 8 takes 8 steps per launch, which matters where a step lasts
+    only a few microseconds."""
+    wl = W.two_layer_workload(n, nrec=64)
+    wl["storage"] = storage
+    wl["time_block"] = time_block
+    sim = _make_sim(LBSim, wl, steps + warmup)
+    try:
+        sec = _time_steps(torch, sim, steps, warmup)
+        pitch = sim.info()[1]
+    finally:
+        sim.close()
+    state = 2 * 5 * n * pitch * ELEM_BYTES[storage]
+    return {"glups": round(n * n * steps / sec / 1e9, 2), "ms_per_step": round(sec / steps * 1e3, 5),
+            "state_mb": round(state / 1e6, 1), "l2_resident": state < 129e6,
+            "grid": f"{n}^2", "steps": steps, "time_block": time_block}
+
+
 def _nested_variant(torch, LBSim, steps, warmup):
     """The slow-block workload with a nested patch: 2048^2 coarse grid, a 1025^2-node patch
     (2x) and inside it a 1025^2-node nested patch (4x to the coarse grid).  One site-step of
@@ -577,6 +597,11 @@ def run_ours(args):
             out = _refined_variant(torch, LBSim, args.steps, args.warmup)
         elif name == "dispersion":
             out = _dispersion_variant()
+        elif name.startswith("l2_resident"):  # l2_resident_<n>_<storage>[_tb8]
+            parts = name.split("_")
+            st = next(p for p in parts if p in ELEM_BYTES)
+            out = _l2_variant(torch, LBSim, int(parts[2]), st, args.steps, args.warmup,
+                              time_block=8 if "tb8" in parts else 1)
         elif name.startswith("d3q7"):
             out = _d3q7_variant(torch, LBSim, name.rsplit("_", 1)[1])
         elif name == "served":
@@ -678,6 +703,13 @@ def run_ours(args):
                     _peaks()[0] / bytes_per_site(5, "f32", True), 1)
             except Exception as ex:
                 v[name] = {"error": str(ex)[:200]}
+        for n, nsteps in ((256, 20000), (1024, 5000)):
+            for st, tb in (("f32", 1), ("bf16", 1), ("f32", 8)):
+                name = f"l2_resident_{n}_d2q5_bgk_{st}" + ("_tb8" if tb > 1 else "")
+                try:
+                    v[name] = _l2_variant(torch, LBSim, n, st, nsteps, time_block=tb)
+                except Exception as ex:
+                    v[name] = {"error": str(ex)[:200]}
         try:
             v["refined_block_2048_d2q5_mrt_f32"] = _refined_variant(torch, LBSim, 400, 10)
         except Exception as ex:
