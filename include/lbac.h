@@ -53,7 +53,13 @@ enum { LB_D2Q5 = 5, LB_D2Q9 = 9, LB_D3Q7 = 7 };   /* lattice (Table I; D3Q7: the
                                                       extension of D2Q5, w_0 = 1 - eta^2,
                                                       w_1..6 = eta^2 / 6, c_s^2 = eta^2 / 3) */
 enum { LB_BGK = 0, LB_MRT = 1 };                   /* collision operator */
-enum { LB_F32 = 0, LB_BF16 = 1, LB_F16 = 2 };      /* population storage in HBM */
+enum { LB_F32 = 0, LB_BF16 = 1, LB_F16 = 2,       /* population storage in HBM */
+       LB_F64 = 3 };                               /* test only: FP64 populations, medium,
+                                                      source and arithmetic (the same
+                                                      per-site code as FP32), a plain
+                                                      one-site-per-thread step; no patch,
+                                                      time blocking, adjoint, invariants,
+                                                      mode projection or serving */
 enum { LB_ZERO_GHOST = 0, LB_PERIODIC = 1 };       /* outer boundary */
 
 /* One refined patch (Sec. 4).  The fine grid covers the coarse rectangle of
@@ -72,7 +78,8 @@ typedef struct {
 typedef struct {
     int lattice;              /* LB_D2Q5 or LB_D2Q9 */
     int collision;            /* LB_BGK or LB_MRT */
-    int storage;              /* LB_F32, LB_BF16 or LB_F16 (16-bit: per-population scale) */
+    int storage;              /* LB_F32, LB_BF16, LB_F16 (FP16: per-population scale) or
+                                 LB_F64 (test only) */
     int boundary;             /* LB_ZERO_GHOST or LB_PERIODIC */
     int nx, ny;               /* grid size in nodes (coarse grid when refined) */
     int sponge_width;         /* absorbing layer width W in cells, 0 = none */
@@ -156,6 +163,15 @@ lb_status lb_get_pressure(lb_ctx *ctx, float *out, int on_device);
  * [Q][ny][nx] FP32.  lb_set_state is the inverse and resets nothing else. */
 lb_status lb_get_state(lb_ctx *ctx, float *out, int on_device);
 lb_status lb_set_state(lb_ctx *ctx, const float *in, int on_device);
+
+/* LB_F64 contexts only (LB_EINVAL otherwise): the same transforms in FP64 --
+ * populations g_i(x) [Q][ny][nx] (get and set, as above) and the pressure
+ * p = c_s^2 sum_i g_i [ny][nx] (Eq. state), so that results can be compared
+ * with an FP64 reference at rounding level.  Caller-owned arrays, host or
+ * device (on_device); synchronises the stream. */
+lb_status lb_get_state_f64(lb_ctx *ctx, double *out, int on_device);
+lb_status lb_set_state_f64(lb_ctx *ctx, const double *in, int on_device);
+lb_status lb_get_pressure_f64(lb_ctx *ctx, double *out, int on_device);
 
 /* Current time (steps taken since lb_init_pressure / lb_create). */
 lb_status lb_get_time(const lb_ctx *ctx, long long *t);

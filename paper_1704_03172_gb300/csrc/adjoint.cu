@@ -603,8 +603,9 @@ float *tape_row(const lb_ctx *ctx, long long t) {
 extern "C" lb_status lb_record_rho(lb_ctx *ctx, int nt_capacity) {
     if (!ctx) return LB_EINVAL;
     if (nt_capacity < 0) return fail(ctx, LB_EINVAL, "nt_capacity < 0");
-    if (nt_capacity > 0 && (ctx->Q == 7 || ctx->refined))
-        return fail(ctx, LB_ESTATE, "the rho tape serves the 2-D adjoint without a patch");
+    if (nt_capacity > 0 && (ctx->Q == 7 || ctx->refined || ctx->cfg.storage == LB_F64))
+        return fail(ctx, LB_ESTATE, "the rho tape serves the 2-D adjoint without a patch "
+                    "(FP32, BF16 or FP16 storage)");
     cudaError_t e = cudaStreamSynchronize(ctx->stream);  // steps may still write the old tape
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rho tape");
     if (ctx->rho_tape) dev_free(ctx, ctx->rho_tape);
@@ -633,6 +634,7 @@ extern "C" lb_status lb_checkpoint_every(lb_ctx *ctx, int every) {
 extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *grad_c,
                                 double *grad_src, float *grad_g0, int on_device) {
     if (!ctx) return LB_EINVAL;
+    if (ctx->cfg.storage == LB_F64) return fail(ctx, LB_ESTATE, "no adjoint for LB_F64 (test only)");
     if (nt < 1) return fail(ctx, LB_EINVAL, "nt < 1");
     if (ctx->nrec > 0 && !dJdp) return fail(ctx, LB_EINVAL, "dJdp is NULL");
     // The forward rho tape (lb_record_rho) covers the nt steps: no checkpoints, no replays.

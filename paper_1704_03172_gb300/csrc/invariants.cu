@@ -233,6 +233,8 @@ using namespace lbrt;
 
 extern "C" lb_status lb_invariants(lb_ctx *ctx, double *out) {
     if (ctx && ctx->Q == 7) return fail(ctx, LB_ESTATE, "invariants are 2-D (D2Q5 / D2Q9)");
+    if (ctx && ctx->cfg.storage == LB_F64)
+        return fail(ctx, LB_ESTATE, "invariants read FP32 / 16-bit storage, not LB_F64");
     if (!ctx) return LB_EINVAL;
     if (!out) return fail(ctx, LB_EINVAL, "out is NULL");
     if (!ctx->inv_scratch) {

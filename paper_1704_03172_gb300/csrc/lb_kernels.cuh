@@ -131,7 +131,31 @@ struct StepArgs {
     // rho_out + j rho_stride.
     float *rho_out;
     long long rho_stride;
+    // LB_F64 (test-only FP64 storage): eta^2 [ny][pitch], the source table S[n] and the
+    // collision / sponge coefficients (order of the kCo* indices below) in FP64; nullptr
+    // in every other context
+    const double *eta2_64;
+    const double *src64;
+    const double *coef64;
 };
+
+// The per-site arithmetic (collision, weights, source, sponge) is written once for an
+// arithmetic type R: FP32 in every production kernel, FP64 in the test-only LB_F64 step,
+// which takes its coefficients from coef64 instead of the FP32 fields.
+enum : int { kCoOmega = 0, kCoS = 1, kCoW1r = 10, kCoW5r, kCoC2r, kCoA1, kCoA5, kCoSmax,
+             kCoInvW, kNCo64 };
+template <typename R> __device__ __forceinline__ R co(const StepArgs &a, float f, int k);
+template <> __device__ __forceinline__ float co<float>(const StepArgs &, float f, int) { return f; }
+template <> __device__ __forceinline__ double co<double>(const StepArgs &a, float, int k) {
+    return a.coef64[k];
+}
+template <typename R> __device__ __forceinline__ R src_at(const StepArgs &a);
+template <> __device__ __forceinline__ float src_at<float>(const StepArgs &a) {
+    return a.src_tab[a.t];
+}
+template <> __device__ __forceinline__ double src_at<double>(const StepArgs &a) {
+    return a.src64[a.t];
+}
 
 constexpr int kMaxCopies = 8;          // spread of the per-block atomicMax targets
 constexpr float kStoredTarget = 8192.f; // 16-bit: |stored| <= 2^13 for the predicted bound
@@ -438,28 +462,28 @@ __device__ __forceinline__ int pull_row(const StepArgs &a, int r, int i) {
 // ------------------------------------------------------------- collision --
 // D2Q5: w_0 = 1 - eta^2, w_1..4 = eta^2 / 4, c_s^2 = eta^2 / 2, so
 // g^eq_0 = w_0 rho, g^eq_{1,3} = w_1 rho +- j_x / 2, g^eq_{2,4} = w_1 rho +- j_y / 2.
-template <bool MRT>
-__device__ __forceinline__ void collide5(float g[5], float e2, const StepArgs &a) {
-    const float rho = g[0] + g[1] + g[2] + g[3] + g[4];
-    const float jx = g[1] - g[3], jy = g[2] - g[4];
-    const float w0 = 1.f - e2, w1 = 0.25f * e2;
+template <bool MRT, typename R>
+__device__ __forceinline__ void collide5(R g[5], R e2, const StepArgs &a) {
+    const R rho = g[0] + g[1] + g[2] + g[3] + g[4];
+    const R jx = g[1] - g[3], jy = g[2] - g[4];
+    const R w0 = R(1) - e2, w1 = R(0.25) * e2;
     if (!MRT) {
-        const float om = a.omega;
-        const float eq0 = w0 * rho, b = w1 * rho;
+        const R om = co<R>(a, a.omega, kCoOmega);
+        const R eq0 = w0 * rho, b = w1 * rho;
         g[0] += om * (eq0 - g[0]);
-        g[1] += om * (b + 0.5f * jx - g[1]);
-        g[2] += om * (b + 0.5f * jy - g[2]);
-        g[3] += om * (b - 0.5f * jx - g[3]);
-        g[4] += om * (b - 0.5f * jy - g[4]);
+        g[1] += om * (b + R(0.5) * jx - g[1]);
+        g[2] += om * (b + R(0.5) * jy - g[2]);
+        g[3] += om * (b - R(0.5) * jx - g[3]);
+        g[4] += om * (b - R(0.5) * jy - g[4]);
     } else {
         // Only e and p_xx are not conserved.  e = -4 g0 + sum_{1..4} g = rho - 5 g0,
         // e^eq = (-4 + 10 c_s^2) rho (Eq. higher moments e), p_xx^eq = 0.
         // g* = g - M^-1 S (m - m^eq), M^-1 = M^T diag(1/5, 1/2, 1/2, 1/20, 1/4).
-        const float e_neq = (rho - 5.f * g[0]) - (-4.f + 5.f * e2) * rho;
-        const float pxx = g[1] - g[2] + g[3] - g[4];
-        const float de = a.s[3] * e_neq * (1.f / 20.f);
-        const float dp = a.s[4] * pxx * 0.25f;
-        g[0] += 4.f * de;
+        const R e_neq = (rho - R(5) * g[0]) - (R(-4) + R(5) * e2) * rho;
+        const R pxx = g[1] - g[2] + g[3] - g[4];
+        const R de = co<R>(a, a.s[3], kCoS + 3) * e_neq * (R(1) / R(20));
+        const R dp = co<R>(a, a.s[4], kCoS + 4) * pxx * R(0.25);
+        g[0] += R(4) * de;
         g[1] -= de + dp;
         g[2] -= de - dp;
         g[3] -= de + dp;
@@ -469,44 +493,49 @@ __device__ __forceinline__ void collide5(float g[5], float e2, const StepArgs &a
 
 // D2Q9 with the eta^2-scaled weights: w_{1..4} = eta^2 w1r, w_{5..8} = eta^2 w5r,
 // c_s^2 = eta^2 c2r, so w_i / c_s^2 = a1 or a5 does not depend on eta.
-template <bool MRT>
-__device__ __forceinline__ void collide9(float g[9], float e2, const StepArgs &a) {
-    const float rho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
-    const float jx = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
-    const float jy = g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
-    const float w1 = e2 * a.w1r, w5 = e2 * a.w5r;
-    const float w0 = 1.f - 4.f * (w1 + w5);
-    float eq[9];
+template <bool MRT, typename R>
+__device__ __forceinline__ void collide9(R g[9], R e2, const StepArgs &a) {
+    const R rho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+    const R jx = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
+    const R jy = g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
+    const R w1 = e2 * co<R>(a, a.w1r, kCoW1r), w5 = e2 * co<R>(a, a.w5r, kCoW5r);
+    const R w0 = R(1) - R(4) * (w1 + w5);
+    R eq[9];
     eq[0] = w0 * rho;
-    const float b1 = w1 * rho, b5 = w5 * rho;
-    const float ux = a.a1 * jx, uy = a.a1 * jy;
+    const R b1 = w1 * rho, b5 = w5 * rho;
+    const R ux = co<R>(a, a.a1, kCoA1) * jx, uy = co<R>(a, a.a1, kCoA1) * jy;
     eq[1] = b1 + ux; eq[3] = b1 - ux;
     eq[2] = b1 + uy; eq[4] = b1 - uy;
-    const float dp = a.a5 * (jx + jy), dm = a.a5 * (jx - jy);
+    const R a5 = co<R>(a, a.a5, kCoA5);
+    const R dp = a5 * (jx + jy), dm = a5 * (jx - jy);
     eq[5] = b5 + dp; eq[7] = b5 - dp;
     eq[6] = b5 - dm; eq[8] = b5 + dm;
     if constexpr (!MRT) {
 #pragma unroll
-        for (int i = 0; i < 9; i++) g[i] += a.omega * (eq[i] - g[i]);
+        for (int i = 0; i < 9; i++) g[i] += co<R>(a, a.omega, kCoOmega) * (eq[i] - g[i]);
     } else {
-        float n[9];
+        R n[9];
 #pragma unroll
         for (int i = 0; i < 9; i++) n[i] = g[i] - eq[i];
-        const float s14 = n[1] + n[2] + n[3] + n[4], s58 = n[5] + n[6] + n[7] + n[8];
+        const R s14 = n[1] + n[2] + n[3] + n[4], s58 = n[5] + n[6] + n[7] + n[8];
         // non-conserved moments of g - g^eq (rows 3..8 of M, App. A), scaled by s_k / |row_k|^2
-        const float d3 = a.s[3] * (-4.f * n[0] - s14 + 2.f * s58) * (1.f / 36.f);
-        const float d4 = a.s[4] * (n[1] - n[2] + n[3] - n[4]) * 0.25f;
-        const float d5 = a.s[5] * (4.f * n[0] - 2.f * s14 + s58) * (1.f / 36.f);
-        const float d6 = a.s[6] * (-2.f * n[1] + 2.f * n[3] + n[5] - n[6] - n[7] + n[8]) * (1.f / 12.f);
-        const float d7 = a.s[7] * (-2.f * n[2] + 2.f * n[4] + n[5] + n[6] - n[7] - n[8]) * (1.f / 12.f);
-        const float d8 = a.s[8] * (n[5] - n[6] + n[7] - n[8]) * 0.25f;
+        const R d3 =
+            co<R>(a, a.s[3], kCoS + 3) * (-R(4) * n[0] - s14 + R(2) * s58) * (R(1) / R(36));
+        const R d4 = co<R>(a, a.s[4], kCoS + 4) * (n[1] - n[2] + n[3] - n[4]) * R(0.25);
+        const R d5 =
+            co<R>(a, a.s[5], kCoS + 5) * (R(4) * n[0] - R(2) * s14 + s58) * (R(1) / R(36));
+        const R d6 = co<R>(a, a.s[6], kCoS + 6) *
+                     (-R(2) * n[1] + R(2) * n[3] + n[5] - n[6] - n[7] + n[8]) * (R(1) / R(12));
+        const R d7 = co<R>(a, a.s[7], kCoS + 7) *
+                     (-R(2) * n[2] + R(2) * n[4] + n[5] + n[6] - n[7] - n[8]) * (R(1) / R(12));
+        const R d8 = co<R>(a, a.s[8], kCoS + 8) * (n[5] - n[6] + n[7] - n[8]) * R(0.25);
         // g* = g - M^T (d3..d8)
-        g[0] -= -4.f * d3 + 4.f * d5;
-        g[1] -= -d3 + d4 - 2.f * d5 - 2.f * d6;
-        g[2] -= -d3 - d4 - 2.f * d5 - 2.f * d7;
-        g[3] -= -d3 + d4 - 2.f * d5 + 2.f * d6;
-        g[4] -= -d3 - d4 - 2.f * d5 + 2.f * d7;
-        const float c5 = 2.f * d3 + d5;
+        g[0] -= -R(4) * d3 + R(4) * d5;
+        g[1] -= -d3 + d4 - R(2) * d5 - R(2) * d6;
+        g[2] -= -d3 - d4 - R(2) * d5 - R(2) * d7;
+        g[3] -= -d3 + d4 - R(2) * d5 + R(2) * d6;
+        g[4] -= -d3 - d4 - R(2) * d5 + R(2) * d7;
+        const R c5 = R(2) * d3 + d5;
         g[5] -= c5 + d6 + d7 + d8;
         g[6] -= c5 - d6 + d7 - d8;
         g[7] -= c5 - d6 - d7 + d8;
@@ -517,30 +546,33 @@ __device__ __forceinline__ void collide9(float g[9], float e2, const StepArgs &a
 // D3Q7 BGK with w_0 = 1 - eta^2, w_1..6 = eta^2 / 6, c_s^2 = eta^2 / 3 (the D2Q5 rule of
 // Eq. 0th lattice weight carried to three dimensions), so w_i / c_s^2 = 1/2 and
 // g^eq_{1,3} = w_1 rho +- j_x / 2, g^eq_{2,4} = w_1 rho +- j_y / 2, g^eq_{5,6} = w_1 rho +- j_z / 2.
-__device__ __forceinline__ void collide7(float g[7], float e2, const StepArgs &a) {
-    const float rho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
-    const float jx = g[1] - g[3], jy = g[2] - g[4], jz = g[5] - g[6];
-    const float om = a.omega, eq0 = (1.f - e2) * rho, b = e2 * (1.f / 6.f) * rho;
+template <typename R>
+__device__ __forceinline__ void collide7(R g[7], R e2, const StepArgs &a) {
+    const R rho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+    const R jx = g[1] - g[3], jy = g[2] - g[4], jz = g[5] - g[6];
+    const R om = co<R>(a, a.omega, kCoOmega), eq0 = (R(1) - e2) * rho,
+            b = e2 * (R(1) / R(6)) * rho;
     g[0] += om * (eq0 - g[0]);
-    g[1] += om * (b + 0.5f * jx - g[1]);
-    g[2] += om * (b + 0.5f * jy - g[2]);
-    g[3] += om * (b - 0.5f * jx - g[3]);
-    g[4] += om * (b - 0.5f * jy - g[4]);
-    g[5] += om * (b + 0.5f * jz - g[5]);
-    g[6] += om * (b - 0.5f * jz - g[6]);
+    g[1] += om * (b + R(0.5) * jx - g[1]);
+    g[2] += om * (b + R(0.5) * jy - g[2]);
+    g[3] += om * (b - R(0.5) * jx - g[3]);
+    g[4] += om * (b - R(0.5) * jy - g[4]);
+    g[5] += om * (b + R(0.5) * jz - g[5]);
+    g[6] += om * (b - R(0.5) * jz - g[6]);
 }
 
-template <int Q>
-__device__ __forceinline__ float weight_i(int i, float e2, const StepArgs &a) {
-    if (Q == 5) return i == 0 ? 1.f - e2 : 0.25f * e2;
-    if (Q == 7) return i == 0 ? 1.f - e2 : e2 * (1.f / 6.f);  // D3Q7: w_0 = 1 - eta^2
-    if (i == 0) return 1.f - 4.f * e2 * (a.w1r + a.w5r);
-    return i < 5 ? e2 * a.w1r : e2 * a.w5r;
+template <int Q, typename R>
+__device__ __forceinline__ R weight_i(int i, R e2, const StepArgs &a) {
+    if (Q == 5) return i == 0 ? R(1) - e2 : R(0.25) * e2;
+    if (Q == 7) return i == 0 ? R(1) - e2 : e2 * (R(1) / R(6));  // D3Q7: w_0 = 1 - eta^2
+    const R w1r = co<R>(a, a.w1r, kCoW1r), w5r = co<R>(a, a.w5r, kCoW5r);
+    if (i == 0) return R(1) - R(4) * e2 * (w1r + w5r);
+    return i < 5 ? e2 * w1r : e2 * w5r;
 }
 
-template <int Q>
-__device__ __forceinline__ float cs2_of(float e2, const StepArgs &a) {
-    return Q == 5 ? 0.5f * e2 : (Q == 7 ? e2 * (1.f / 3.f) : e2 * a.c2r);
+template <int Q, typename R>
+__device__ __forceinline__ R cs2_of(R e2, const StepArgs &a) {
+    return Q == 5 ? R(0.5) * e2 : (Q == 7 ? e2 * (R(1) / R(3)) : e2 * co<R>(a, a.c2r, kCoC2r));
 }
 
 __device__ __forceinline__ float sponge_factor(int x, int y, const StepArgs &a) {
@@ -551,10 +583,11 @@ __device__ __forceinline__ float sponge_factor(int x, int y, const StepArgs &a) 
 }
 
 // sponge factor at distance d from the nearest face
-__device__ __forceinline__ float sponge_of_dist(int d, const StepArgs &a) {
-    if (d >= a.sponge_w) return 1.f;
-    const float q = (float)(a.sponge_w - d) * a.sponge_inv_w;
-    return 1.f - a.sponge_smax * q * q;
+template <typename R = float>
+__device__ __forceinline__ R sponge_of_dist(int d, const StepArgs &a) {
+    if (d >= a.sponge_w) return R(1);
+    const R q = (R)(a.sponge_w - d) * co<R>(a, a.sponge_inv_w, kCoInvW);
+    return R(1) - co<R>(a, a.sponge_smax, kCoSmax) * q * q;
 }
 
 // distance from row r to the nearest y face (D3Q7: y or z face)
@@ -614,12 +647,12 @@ __device__ __forceinline__ float next_scale(float maxval, float S, float keep) {
 // Collision, source and sponge for a thread's V sites, in place.  EDGE: some site of
 // the warp lies in the sponge or beyond the last column (damped / zeroed per site; dyz is
 // the row's distance to the nearest y / z face).
-template <int Q, bool MRT, int V, bool EDGE>
-__device__ __forceinline__ void collide_sites(float (&g)[Q][V], const float (&e2s)[V],
+template <int Q, bool MRT, int V, bool EDGE, typename R>
+__device__ __forceinline__ void collide_sites(R (&g)[Q][V], const R (&e2s)[V],
                                               const StepArgs &a, int x0, int dyz, bool has_src) {
 #pragma unroll
     for (int k = 0; k < V; k++) {
-        float gs[Q];
+        R gs[Q];
 #pragma unroll
         for (int i = 0; i < Q; i++) gs[i] = g[i][k];
         if (Q == 5)
@@ -629,17 +662,17 @@ __device__ __forceinline__ void collide_sites(float (&g)[Q][V], const float (&e2
         else
             collide7(gs, e2s[k], a);
         if (has_src && a.src_x == x0 + k) {
-            const float S = a.src_tab[a.t];
+            const R S = src_at<R>(a);
 #pragma unroll
             for (int i = 0; i < Q; i++) gs[i] += weight_i<Q>(i, e2s[k], a) * S;
         }
         if (EDGE) {
             const int x = x0 + k;
-            const float f =
-                a.sponge_w > 0 ? sponge_of_dist(min(min(x, a.nx - 1 - x), dyz), a) : 1.f;
+            const R f =
+                a.sponge_w > 0 ? sponge_of_dist<R>(min(min(x, a.nx - 1 - x), dyz), a) : R(1);
             const bool real = x0 + k < a.nx;
 #pragma unroll
-            for (int i = 0; i < Q; i++) g[i][k] = real ? gs[i] * f : 0.f;
+            for (int i = 0; i < Q; i++) g[i][k] = real ? gs[i] * f : R(0);
         } else {
 #pragma unroll
             for (int i = 0; i < Q; i++) g[i][k] = gs[i];

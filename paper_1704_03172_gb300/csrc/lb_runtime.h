@@ -42,6 +42,10 @@ struct lb_ctx {
     bool ckpt_raw0 = false;         // raw flag of the time-0 checkpoint
     float *src_tab = nullptr;
     int src_nt = 0, src_x = 0, src_y = 0;
+    // LB_F64 (test-only) storage: FP64 eta^2, source table and coefficients (f64.cu)
+    double *eta2_64 = nullptr;
+    double *src64 = nullptr;
+    double *coef64 = nullptr;
     int2 *rec = nullptr;
     int nrec = 0;
     std::vector<int> rec_xy;        // host copy of rec: (x, row) pairs
@@ -126,6 +130,14 @@ lb_status stream_launch(lb_ctx *ctx, const lbk::StepArgs &a, int rec_blocks);
 lb_status tb_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
 lb_status tb_launch(lb_ctx *ctx, int K);
 lb_status tb_launch_args(lb_ctx *ctx, const lbk::StepArgs &a, int K);
+
+// test-only FP64 storage (f64.cu): medium and coefficients, source table, steps, and the
+// state transforms (mode 0 pressure, 1 populations; FP32 arrays f or FP64 arrays d)
+lb_status f64_setup(lb_ctx *c, const float *cmap_dev, double cref);
+lb_status f64_set_source(lb_ctx *c, const double *wavelet, int nt);
+lb_status f64_step(lb_ctx *c, int n);
+lb_status f64_set(lb_ctx *c, const float *f, const double *d, int on_device, int mode);
+lb_status f64_get(lb_ctx *c, float *f, double *d, int on_device, int mode);
 
 // grid refinement (refine.cu)
 lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev);

@@ -63,7 +63,7 @@ void dev_free(lb_ctx *ctx, void *p) {
         cudaFree(p);
 }
 
-int elem_bytes(int storage) { return storage == LB_F32 ? 4 : 2; }
+int elem_bytes(int storage) { return storage == LB_F32 ? 4 : storage == LB_F64 ? 8 : 2; }
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -151,6 +151,9 @@ StepArgs base_args(const lb_ctx *c) {
     a.src_y = c->src_y;
     a.rec = c->rec;
     a.nrec = c->nrec;
+    a.eta2_64 = c->eta2_64;
+    a.src64 = c->src64;
+    a.coef64 = c->coef64;
     if (c->lp_scale) a.scale_in = c->lp_scale + c->lp_slot * 9;
     return a;
 }
@@ -243,8 +246,11 @@ lb_status validate(const lb_config *cfg) {
     }
     if (cfg->collision != LB_BGK && cfg->collision != LB_MRT)
         return fail(nullptr, LB_EINVAL, "collision must be LB_BGK or LB_MRT");
-    if (cfg->storage != LB_F32 && cfg->storage != LB_BF16 && cfg->storage != LB_F16)
-        return fail(nullptr, LB_EINVAL, "storage must be LB_F32, LB_BF16 or LB_F16");
+    if (cfg->storage != LB_F32 && cfg->storage != LB_BF16 && cfg->storage != LB_F16 &&
+        cfg->storage != LB_F64)
+        return fail(nullptr, LB_EINVAL, "storage must be LB_F32, LB_BF16, LB_F16 or LB_F64");
+    if (cfg->storage == LB_F64 && (cfg->n_patches > 0 || cfg->step_kernel == LB_STEP_STAGED))
+        return fail(nullptr, LB_EINVAL, "LB_F64 (test only): no refinement patch, no staged step");
     if (cfg->boundary != LB_ZERO_GHOST && cfg->boundary != LB_PERIODIC)
         return fail(nullptr, LB_EINVAL, "boundary must be LB_ZERO_GHOST or LB_PERIODIC");
     if (cfg->nx < 1 || cfg->ny < 1 || (long long)cfg->nx * cfg->ny * nz > (1LL << 34) ||
@@ -312,6 +318,7 @@ lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint,
     size_t q = cfg->lattice == LB_D2Q9 ? 9 : cfg->lattice == LB_D3Q7 ? 7 : 5;
     // populations (two buffers), eta^2 and, for piecewise-constant media, the medium index
     size_t b = 2 * q * plane * elem_bytes(cfg->storage) + plane * 4 + plane + 1024;
+    if (cfg->storage == LB_F64) b += plane * 8 + (size_t)std::max(nt, 0) * 8 + 256;
     if (nrec > 0 && nt > 0) b += (size_t)nt * nrec * 4 + (size_t)nrec * 8;
     if (nt > 0) b += (size_t)nt * 4;
     // refinement levels (refine.cu): per patch, two population buffers with a ghost ring and
@@ -408,7 +415,8 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     // threads, and for FP32 the register-streaming step is faster)
     c->staged = cfg->n_patches == 0 &&
                 (cfg->step_kernel == LB_STEP_STAGED ||
-                 (cfg->step_kernel == LB_STEP_AUTO && cfg->storage != LB_F32 && cfg->nx >= 1024));
+                 (cfg->step_kernel == LB_STEP_AUTO && (cfg->storage == LB_BF16 ||
+                                                       cfg->storage == LB_F16) && cfg->nx >= 1024));
     if (cfg->storage == LB_F16) {  // FP16 range scales (BF16 has FP32's range and needs none)
         c->lp_scale = static_cast<float *>(dev_alloc(c, 3 * 9 * sizeof(float)));
         c->lp_max = static_cast<unsigned *>(dev_alloc(c, (3 * 9 * kMaxCopies + 1) * sizeof(unsigned)));
@@ -453,7 +461,9 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     dev_free(c, flags);
     if (hflags & 1u) return bail(fail(c, LB_EINVAL, "c_map must be finite and > 0"));
     if (hflags & 2u) return bail(fail(c, LB_EINVAL, "c_map exceeds c_ref (eta > 1)"));
-    if (!cfg->c_map_on_device) {  // piecewise-constant media: 1-byte medium index
+    if (cfg->storage == LB_F64) {
+        if ((st = f64_setup(c, cmap_dev, cref)) != LB_OK) return bail(st);
+    } else if (!cfg->c_map_on_device) {  // piecewise-constant media: 1-byte medium index
         std::vector<uint8_t> map;
         std::vector<float> tab;
         if (medium_index(cfg->c_map, c->nx, c->ny, c->pitch, 1.0 / cref, map, tab)) {
@@ -515,6 +525,10 @@ static lb_status set_source_row(lb_ctx *ctx, int x, int y, const double *wavelet
     if (ctx->src_tab) dev_free(ctx, ctx->src_tab);
     ctx->src_tab = nullptr;
     ctx->src_nt = 0;
+    if (ctx->cfg.storage == LB_F64) {
+        lb_status st = f64_set_source(ctx, wavelet, nt);
+        if (st != LB_OK) return st;
+    }
     if (nt == 0) return LB_OK;
     std::vector<float> tab(wavelet, wavelet + nt);
     ctx->src_tab = static_cast<float *>(dev_alloc(ctx, (size_t)nt * 4));
@@ -607,6 +621,7 @@ static lb_status upload_f32(lb_ctx *ctx, const float *src, size_t n, int on_devi
 }
 
 static lb_status set_state_common(lb_ctx *ctx, const float *src, int on_device, int mode) {
+    if (ctx->cfg.storage == LB_F64) return f64_set(ctx, src, nullptr, on_device, mode);
     size_t n = (size_t)ctx->nx * ctx->ny * (mode == 0 ? 1 : ctx->Q);
     const float *dev = nullptr;
     float *tmp = nullptr;
@@ -667,6 +682,7 @@ lb_status lb_set_state(lb_ctx *ctx, const float *in, int on_device) {
 
 static lb_status get_common(lb_ctx *ctx, float *out, int on_device, int mode) {
     if (!out) return fail(ctx, LB_EINVAL, "out is NULL");
+    if (ctx->cfg.storage == LB_F64) return f64_get(ctx, out, nullptr, on_device, mode);
     size_t n = (size_t)ctx->nx * ctx->ny * (mode == 0 ? 1 : ctx->Q);
     float *dst = out;
     if (!on_device) {
@@ -769,6 +785,7 @@ lb_status lb_step(lb_ctx *ctx, int n) {
     if (!ctx) return LB_EINVAL;
     if (n < 0) return fail(ctx, LB_EINVAL, "n < 0");
     if (ctx->refined) return refine_step(ctx, n);
+    if (ctx->cfg.storage == LB_F64) return f64_step(ctx, n);
     StepFn fn = pick_step(ctx);
     StepArgs a = base_args(ctx);
     const int K = ctx->cfg.time_block;

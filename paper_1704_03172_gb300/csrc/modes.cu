@@ -111,6 +111,8 @@ extern "C" lb_status lb_mode_projection(lb_ctx *ctx, const int *modes, int n_mod
     if (!modes || !out || n_modes < 1) return fail(ctx, LB_EINVAL, "modes, out and n_modes >= 1");
     if (ctx->refined) return fail(ctx, LB_ESTATE, "mode projection of a refined context");
     if (ctx->Q == 7) return fail(ctx, LB_ESTATE, "mode projection is 2-D (D2Q5 / D2Q9)");
+    if (ctx->cfg.storage == LB_F64)
+        return fail(ctx, LB_ESTATE, "mode projection reads FP32 / 16-bit storage, not LB_F64");
     const int blocks = (int)std::min<long long>(
         kModeBlocks, ((long long)ctx->nx * ctx->ny + kModeThreads - 1) / kModeThreads);
     int *d_modes = static_cast<int *>(dev_alloc(ctx, (size_t)n_modes * 2 * sizeof(int)));

@@ -555,6 +555,8 @@ lb_status lb_server_submit(lb_server *S, const lb_request *q, long long *id) {
     if (q->cfg.n_patches > 0) return fail(nullptr, LB_EINVAL, "served shots have no patch");
     if (q->cfg.lattice == LB_D3Q7 || q->cfg.nz > 1)
         return fail(nullptr, LB_EINVAL, "served shots are 2-D (D2Q5 / D2Q9)");
+    if (q->cfg.storage == LB_F64)
+        return fail(nullptr, LB_EINVAL, "served shots store FP32, BF16 or FP16 (LB_F64 is test only)");
     Req *r = new Req();
     r->cfg = q->cfg;
     r->cmap.assign(q->cfg.c_map, q->cfg.c_map + (size_t)q->cfg.nx * q->cfg.ny);

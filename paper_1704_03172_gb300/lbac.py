@@ -21,7 +21,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE = 0, -1, -2, -3, -4, -5, -6
 LB_D2Q5, LB_D2Q9, LB_D3Q7 = 5, 9, 7
 LB_BGK, LB_MRT = 0, 1
-LB_F32, LB_BF16, LB_F16 = 0, 1, 2
+LB_F32, LB_BF16, LB_F16, LB_F64 = 0, 1, 2, 3
 LB_STEP_AUTO, LB_STEP_DIRECT, LB_STEP_STAGED = 0, 1, 2
 LB_ZERO_GHOST, LB_PERIODIC = 0, 1
 STATUS_NAMES = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOMEM", -3: "LB_ECUDA",
@@ -92,6 +92,9 @@ _SIGS = {
     "lb_get_pressure": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
     "lb_get_state": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
     "lb_set_state": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
+    "lb_get_state_f64": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
+    "lb_set_state_f64": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
+    "lb_get_pressure_f64": [_ctx_p, ctypes.c_void_p, ctypes.c_int],
     "lb_get_time": [_ctx_p, ctypes.POINTER(ctypes.c_longlong)],
     "lb_sync": [_ctx_p],
     "lb_wait_selftest": [_ctx_p, ctypes.c_int],
@@ -251,6 +254,18 @@ def lb_get_state(ctx, out_ptr, on_device):
 
 def lb_set_state(ctx, in_ptr, on_device):
     return _check(_lib.lb_set_state(ctx, in_ptr, int(on_device)), ctx)
+
+
+def lb_get_state_f64(ctx, out_ptr, on_device):
+    return _check(_lib.lb_get_state_f64(ctx, out_ptr, int(on_device)), ctx)
+
+
+def lb_set_state_f64(ctx, in_ptr, on_device):
+    return _check(_lib.lb_set_state_f64(ctx, in_ptr, int(on_device)), ctx)
+
+
+def lb_get_pressure_f64(ctx, out_ptr, on_device):
+    return _check(_lib.lb_get_pressure_f64(ctx, out_ptr, int(on_device)), ctx)
 
 
 def lb_get_time(ctx) -> int:

@@ -14,7 +14,8 @@ import torch
 
 from . import lbac
 
-_STORAGE = {"f32": lbac.LB_F32, "bf16": lbac.LB_BF16, "f16": lbac.LB_F16}
+_STORAGE = {"f32": lbac.LB_F32, "bf16": lbac.LB_BF16, "f16": lbac.LB_F16,
+            "f64": lbac.LB_F64}  # f64: test only (FP64 state, plain step kernel)
 _COLL = {"bgk": lbac.LB_BGK, "mrt": lbac.LB_MRT}
 _BOUND = {"zero": lbac.LB_ZERO_GHOST, "periodic": lbac.LB_PERIODIC}
 
@@ -42,6 +43,7 @@ class LBSim:
         cfg.lattice = int(lattice)
         cfg.collision = _COLL[collision] if isinstance(collision, str) else int(collision)
         cfg.storage = _STORAGE[storage] if isinstance(storage, str) else int(storage)
+        self.f64 = cfg.storage == lbac.LB_F64
         cfg.boundary = _BOUND[boundary] if isinstance(boundary, str) else int(boundary)
         if not torch.is_tensor(c_map):
             c_map = np.ascontiguousarray(c_map, dtype=np.float32)
@@ -134,9 +136,11 @@ class LBSim:
         self.stream.synchronize()
 
     def set_state(self, g):
-        t = torch.as_tensor(g, dtype=torch.float32, device=self.device).contiguous()
+        """Populations [Q][ny][nx]; FP64 contexts take them in FP64."""
+        dt = torch.float64 if self.f64 else torch.float32
+        t = torch.as_tensor(g, dtype=dt, device=self.device).contiguous()
         self.stream.wait_stream(torch.cuda.current_stream(self.device))
-        lbac.lb_set_state(self.ctx, _ptr(t), 1)
+        (lbac.lb_set_state_f64 if self.f64 else lbac.lb_set_state)(self.ctx, _ptr(t), 1)
         self.stream.synchronize()
 
     # -- stepping -----------------------------------------------------------------------
@@ -151,9 +155,9 @@ class LBSim:
         return lbac.lb_get_time(self.ctx)
 
     # -- outputs ------------------------------------------------------------------------
-    def _out(self, shape):
+    def _out(self, shape, dtype=torch.float32):
         with torch.cuda.stream(self.stream):
-            return torch.zeros(shape, dtype=torch.float32, device=self.device)
+            return torch.zeros(shape, dtype=dtype, device=self.device)
 
     def traces(self, nt_max=None):
         """Receiver traces [rows, nrec] (row n = pressure at time n); synchronises."""
@@ -163,11 +167,21 @@ class LBSim:
         return out[:n, :self.nrec]
 
     def pressure(self):
+        """p = c_s^2 sum_i g_i at the current time (FP64 for an FP64 context)."""
+        if self.f64:
+            out = self._out(self._grid, torch.float64)
+            lbac.lb_get_pressure_f64(self.ctx, _ptr(out), 1)
+            return out
         out = self._out(self._grid)
         lbac.lb_get_pressure(self.ctx, _ptr(out), 1)
         return out
 
     def state(self):
+        """Populations g_i(x) [Q][ny][nx] at the current time (FP64 for an FP64 context)."""
+        if self.f64:
+            out = self._out((self.Q,) + self._grid, torch.float64)
+            lbac.lb_get_state_f64(self.ctx, _ptr(out), 1)
+            return out
         out = self._out((self.Q,) + self._grid)
         lbac.lb_get_state(self.ctx, _ptr(out), 1)
         return out
