@@ -41,8 +41,8 @@ ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 # profiles/ give the commands); keyed by (kernel, medium index).  A kernel without an entry,
 # or one changed since its capture, reports null.
 NCU_TRAFFIC = {
-    ("lbk::step_kernel<5,false,false,float>", True): 640.35e6,
-    ("stream_step_kernel<5,false,false,__nv_bfloat16>", True): 301.9e6,
+    ("lbk::step_kernel<5,false,false,float>", True): 638.70e6,
+    ("stream_step_kernel<5,false,false,__nv_bfloat16>", True): 300.29e6,
     ("tb_kernel<5,false,false,8>", False): 703.2e6,
 }
 
