@@ -867,8 +867,11 @@ __global__ void __launch_bounds__(kThreads, Q == 5   ? (sizeof(ST) == 4 ? 5 : 4)
 
 // FP16, after each step (one block): the scale the next step writes with, from
 // this step's maxima (8 max|out| + |S[t+1]| at or below kStoredTarget), and a
-// cleared max slot for the next step.
+// cleared max slot for the next step.  Launched as a programmatic dependent of the
+// step (it waits for the step's grid before it reads the maxima), so its launch and
+// the next step's overlap the step's last blocks.
 static __global__ void scale_update_kernel(StepArgs a, int Q) {
+    pdl_trigger_and_wait();
     const int i = threadIdx.x;
     if (i >= Q) return;
     float m = 0.f;

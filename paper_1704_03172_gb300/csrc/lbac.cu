@@ -771,7 +771,10 @@ lb_status launch_step(lb_ctx *ctx, StepFn fn, StepArgs &a) {
                                    ctx->stream, a);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
     }
-    if (ctx->lp_scale) scale_update_kernel<<<1, 32, 0, ctx->stream>>>(a, ctx->Q);
+    if (ctx->lp_scale) {
+        cudaError_t e = launch_pdl(scale_update_kernel, dim3(1), dim3(32), 0, ctx->stream, a, ctx->Q);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "scale update launch");
+    }
     ctx->cur ^= 1;
     ctx->t += 1;
     return LB_OK;
