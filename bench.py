@@ -133,6 +133,20 @@ def _dist():
     return ws, rank, local
 
 
+def job_rate(sec, units, ws, device="cuda"):
+    """Whole-job throughput of ws independent replicas: the units all ranks processed over
+    the slowest rank's timed seconds (sum and max over ranks).  Returns (units / s, s)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(sec)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        sec, units = float(t.item()), float(u.item())
+    return units / sec, sec
+
+
 def _workload(lattice=5, storage="f32", collision="bgk"):
     wl = W.two_layer_workload(N_GRID, lattice=lattice, collision=collision)
     if lattice == 9 and collision == "mrt":
@@ -633,17 +647,13 @@ def run_ours(args):
         wall = time.perf_counter() - t0
     if ws > 1:
         dist.barrier()
-    sec = e0.elapsed_time(e1) / 1e3
-    if ws > 1:
-        t = torch.tensor([sec], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
+    sites = N_GRID * N_GRID
+    rate, sec = job_rate(e0.elapsed_time(e1) / 1e3, sites * args.steps, ws)
     tr = sim.traces(args.steps + args.warmup)
     finite = bool(torch.isfinite(tr).all().item())
     indexed = _indexed(sim)
     sim.close()
-    sites = N_GRID * N_GRID
-    value = ws * sites * args.steps / sec / 1e9
+    value = rate / 1e9
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
