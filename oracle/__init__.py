@@ -109,11 +109,13 @@ def _declare_refine(L):
     L.orc_ref_fine_pressure.argtypes = [vp, _dp]
     L.orc_ref_states.argtypes = [vp, _dp, _dp]
     L.orc_ref_nest.argtypes = [vp] + [ctypes.c_int] * 4
+    L.orc_ref_direction.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.orc_ref_level_dims.argtypes = [vp, ctypes.c_int, _ip, _ip]
     L.orc_ref_level_pressure.argtypes = [vp, ctypes.c_int, _dp]
     L.orc_ref_level_cmap.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     for n in ("orc_ref_dims", "orc_ref_fine_cmap", "orc_ref_init_pressure", "orc_ref_run",
               "orc_ref_pressure", "orc_ref_fine_pressure", "orc_ref_states", "orc_ref_nest",
+              "orc_ref_direction",
               "orc_ref_level_dims", "orc_ref_level_pressure", "orc_ref_level_cmap"):
         getattr(L, n).restype = ctypes.c_int
 
@@ -151,6 +153,15 @@ class Refined:
         if level < 0:
             raise ValueError("invalid nested patch")
         return level
+
+    def direction(self, coupling, level=1):
+        """Couple level `level` to the grid above it both ways ("both", population by
+        population, reading R3), or only "c2f" (coarse -> fine: the coarser grid is never
+        corrected) or "f2c" (fine -> coarse: nothing enters the finer grid), the paper's
+        switch on the direction of propagation (Sec. 4).  Before init_pressure."""
+        d = {"both": 0, "c2f": 1, "f2c": 2}[coupling]
+        if lib().orc_ref_direction(self.h, int(level), d):
+            raise ValueError("no such level")
 
     def level_dims(self, level):
         nx, ny = ctypes.c_int(), ctypes.c_int()

@@ -69,6 +69,9 @@ int orc_ref_fine_pressure(void *h, double *pf);
 int orc_ref_states(void *h, double *gc, double *gf);
 /* nested patches: a patch of the innermost fine grid (its node coordinates), refined by 2 */
 int orc_ref_nest(void *h, int x0, int y0, int nxp, int nyp);
+/* coupling direction of level `level` (1: the first patch): 0 both ways (population by
+ * population), 1 coarse -> fine only, 2 fine -> coarse only (Sec. 4) */
+int orc_ref_direction(void *h, int level, int dir);
 int orc_ref_level_dims(void *h, int level, int *nx, int *ny);
 int orc_ref_level_pressure(void *h, int level, double *p);
 int orc_ref_level_cmap(void *h, int level, float *c);

@@ -54,6 +54,11 @@ typedef struct ref_s {
     orc_problem C, F;
     struct ref_s *sub; /* nested patch inside F, or NULL */
     int rule;
+    /* direction of the coupling (Sec. 4, "specify the direction of wave propagation"):
+     * 0 both ways, population by population (reading R3); 1 coarse -> fine only (the
+     * coarse grid is never corrected from the fine one); 2 fine -> coarse only (no coarse
+     * population enters the fine grid: what enters it across I is zero, the zero ghost) */
+    int dir;
     int x0, y0, nxp, nyp, nxf, nyf, nI;
     float *cf;
     double *gc, *gf, *tc, *tf, *Uprev, *Unext;
@@ -331,8 +336,8 @@ static void init_level(ref_t *R, const double *pc, double *gcs) {
     if (R->sub) init_level(R->sub, pf, R->gf);
     free(pf);
     snapshot(R, gcs, R->Uprev);
-    c2f(R, R->gf, R->Uprev, R->Uprev, 1.0);
-    f2c(R, gcs, R->gf);
+    if (R->dir != 2) c2f(R, R->gf, R->Uprev, R->Uprev, 1.0);
+    if (R->dir != 1) f2c(R, gcs, R->gf);
 }
 
 /* g = g^eq(p0 / c_s^2, 0) on every grid (p0 interpolated bilinearly to the fine
@@ -388,10 +393,10 @@ static void pair_advance(ref_t *R, double *gin, double *gout, long T) {
     orc_step_grid(&R->C, R->Minv, (int)T, gin, gout); /* provisional coarse T+1 */
     snapshot(R, gout, R->Unext);
     fine_advance(R, R->gf, R->tf, 2 * T); /* fine 2T -> 2T+1 */
-    c2f(R, R->tf, R->Uprev, R->Unext, 0.5);
+    if (R->dir != 2) c2f(R, R->tf, R->Uprev, R->Unext, 0.5);
     fine_advance(R, R->tf, R->gf, 2 * T + 1); /* fine 2T+1 -> 2T+2 */
-    c2f(R, R->gf, R->Uprev, R->Unext, 1.0);
-    f2c(R, gout, R->gf);
+    if (R->dir != 2) c2f(R, R->gf, R->Uprev, R->Unext, 1.0);
+    if (R->dir != 1) f2c(R, gout, R->gf);
     double *s = R->Uprev;
     R->Uprev = R->Unext;
     R->Unext = s;
@@ -446,6 +451,17 @@ int orc_ref_nest(void *h, int x0, int y0, int nxp, int nyp) {
     if (!S) return -1;
     R->sub = S;
     return level + 1;
+}
+
+/* Direction of the coupling between level `level` - 1 and `level` (1: the first patch):
+ * 0 both ways, 1 coarse -> fine only, 2 fine -> coarse only.  Before init_pressure. */
+int orc_ref_direction(void *h, int level, int dir) {
+    ref_t *R = (ref_t *)h;
+    if (dir < 0 || dir > 2 || level < 1) return -1;
+    for (int l = 1; l < level && R; l++) R = R->sub;
+    if (!R) return -1;
+    R->dir = dir;
+    return 0;
 }
 
 static const ref_t *level_of(const ref_t *R, int level) {

@@ -219,3 +219,65 @@ def test_nested_viscous_rule_keeps_the_damping(oracle_mod, tau):
         out[rule] = amp(R.pressure()) / ref - 1
     assert abs(out["viscous"]) < 5e-3
     assert out["paper"] > 2 * abs(out["viscous"])    # coarse rates on every level damp less
+
+
+# One-way coupling (Sec. 4: the paper switches on the direction of propagation across the
+# interface).  Coarse -> fine only leaves the coarse grid exactly as an unrefined run; fine
+# -> coarse only leaves the fine grid exactly as a standalone zero-ghost run of its own
+# medium from the same initial state.  A dropped or misplaced switch fails one of these.
+@pytest.mark.parametrize("Q", [5, 9])
+def test_c2f_only_leaves_the_coarse_grid_unrefined(oracle_mod, Q):
+    n, steps = 40, 30
+    c = W.random_medium(n, n, 21, 0.5, 1.0)
+    src = (6, 20, W.ricker(steps, 0.08))
+    P = oracle_mod.Problem(Q, n, n, c, c_ref=1.0, tau=0.5, w_ref=(0.4, 0.11, 0.04),
+                           sponge_width=4, sponge_sigma_max=0.1, source=src)
+    p0 = W.gaussian_pulse(n, n, 22, 18, 3.0, 1e-3)
+    R = oracle_mod.Refined(P, 14, 10, 12, 14)
+    R.direction("c2f")
+    R.init_pressure(p0)
+    R.run(steps)
+    gc, gf = R.states()
+    g0 = oracle_mod.init_pressure(P, p0)
+    gp, _ = oracle_mod.run(P, g0, steps)
+    np.testing.assert_array_equal(gc, gp)
+    assert np.abs(gf).max() > 1e-6          # the fine grid did receive the wave
+
+
+@pytest.mark.parametrize("Q", [5, 9])
+def test_f2c_only_leaves_the_fine_grid_standalone(oracle_mod, Q):
+    n, steps = 40, 25
+    c = W.random_medium(n, n, 22, 0.5, 1.0)
+    P = oracle_mod.Problem(Q, n, n, c, c_ref=1.0, tau=0.5, w_ref=(0.4, 0.11, 0.04),
+                           source=(5, 5, W.ricker(steps, 0.08)))
+    p0 = W.gaussian_pulse(n, n, 20, 20, 2.5, 1e-3)
+    R = oracle_mod.Refined(P, 12, 13, 14, 12)
+    R.direction("f2c")
+    R.init_pressure(p0)
+    gc0, gf0 = R.states()
+    R.run(steps)
+    gc, gf = R.states()
+    Pf = oracle_mod.Problem(Q, R.nxf, R.nyf, R.fine_cmap(), c_ref=1.0, tau=0.5,
+                            w_ref=(0.4, 0.11, 0.04))
+    gp, _ = oracle_mod.run(Pf, gf0, 2 * steps)
+    np.testing.assert_array_equal(gf, gp)
+    # and the coarse grid does see the fine one: it differs from an unrefined run
+    gu, _ = oracle_mod.run(P, oracle_mod.init_pressure(P, p0), steps)
+    assert np.abs(gc - gu).max() > 1e-8
+
+
+def test_both_ways_differs_from_either_one_way_mode(oracle_mod):
+    n, steps = 40, 20
+    c = W.random_medium(n, n, 23, 0.5, 1.0)
+    P = oracle_mod.Problem(5, n, n, c, c_ref=1.0, tau=0.5)
+    p0 = W.gaussian_pulse(n, n, 20, 20, 3.0, 1e-3)
+    out = {}
+    for mode in ("both", "c2f", "f2c"):
+        R = oracle_mod.Refined(P, 12, 12, 14, 14)
+        R.direction(mode)
+        R.init_pressure(p0)
+        R.run(steps)
+        out[mode] = R.states()
+    for mode in ("c2f", "f2c"):
+        assert np.abs(out[mode][0] - out["both"][0]).max() > 1e-8
+        assert np.abs(out[mode][1] - out["both"][1]).max() > 1e-8
