@@ -73,7 +73,14 @@ typedef struct {
     int x0, y0;
     int nx_c, ny_c;
     int ratio;
+    int coupling;  /* LB_COUPLE_BOTH (0): both ways, population by population;
+                      LB_COUPLE_C2F: coarse -> fine only, the grid above is never corrected
+                      from this patch; LB_COUPLE_F2C: fine -> coarse only, nothing enters
+                      the patch across its interface (zero, as at a zero-ghost boundary) --
+                      the paper's switch on the direction of propagation (Sec. 4) */
 } lb_patch;
+
+enum { LB_COUPLE_BOTH = 0, LB_COUPLE_C2F = 1, LB_COUPLE_F2C = 2 };
 
 typedef struct {
     int lattice;              /* LB_D2Q5 or LB_D2Q9 */

@@ -58,6 +58,7 @@ using namespace lbrt;
 // One refined level: the fine grid of a patch and its coupling to the grid above it.
 struct lb_refine {
     int depth = 1;                   // 1: patch of the context's grid; k: patch of level k - 1
+    int coupling = LB_COUPLE_BOTH;   // direction of the coupling to the grid above
     int x0n = 0, y0n = 0;            // patch origin, parent grid node coordinates
     int x0 = 0, y0 = 0;              // patch origin, parent grid storage coordinates
     int nxp = 0, nyp = 0, nxf = 0, nyf = 0;  // patch (parent cells) and fine node counts
@@ -209,6 +210,25 @@ __global__ void ref_c2f_kernel(StepArgs af, StepArgs rs, const int4 *If, int nIf
         const long long pos =
             af.raw ? node : (long long)(ub + 1) * af.pitch + (ua + 1);
         in[i * af.plane + pos] = gh[i];
+    }
+}
+
+// Fine -> coarse coupling only: nothing enters the fine grid across I.  The entering
+// populations of the fine nodes of I, which the fine step left at the upstream ghost
+// nodes of its input, are set to zero (a zero-ghost boundary).  Not used on a raw input:
+// the state set at time 0 is kept, as the coupling at time 0 would keep it.
+template <int Q>
+__global__ void ref_zero_in_kernel(StepArgs af, const int4 *If, int nIf, int nxf, int nyf) {
+    pdl_trigger_and_wait();  // launched with launch_pdl
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nIf) return;
+    const int a = If[j].x, b = If[j].y;
+    float *in = static_cast<float *>(const_cast<void *>(af.in));
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int ua = a - Lat<Q>::cx(i), ub = b - Lat<Q>::cy(i);
+        if (ua >= 0 && ua < nxf && ub >= 0 && ub < nyf) continue;  // comes from the fine grid
+        in[i * af.plane + (long long)(ub + 1) * af.pitch + (ua + 1)] = 0.f;
     }
 }
 
@@ -402,6 +422,20 @@ void launch_snap_c2f(lb_ctx *ctx, const StepArgs &ap, lb_refine *R, const float 
     }
 }
 
+// fine -> coarse coupling only: zero what enters R across I before its next step (a raw
+// input keeps its state)
+void launch_zero_in(lb_ctx *ctx, lb_refine *R) {
+    if (R->raw) return;
+    StepArgs af = level_args(ctx, R);
+    af.in = R->pop[R->cur];
+    if (ctx->Q == 9)
+        launch_pdl(ref_zero_in_kernel<9>, dim3(blocks_for(R->nIf)), dim3(256), 0, ctx->stream, af,
+                   R->If, R->nIf, R->nxf, R->nyf);
+    else
+        launch_pdl(ref_zero_in_kernel<5>, dim3(blocks_for(R->nIf)), dim3(256), 0, ctx->stream, af,
+                   R->If, R->nIf, R->nxf, R->nyf);
+}
+
 // snapshot of the parent's populations on R's interface, from the parent's step input
 void launch_snapshot(lb_ctx *ctx, const StepArgs &ap, lb_refine *R, float *U) {
     if (ctx->Q == 9)
@@ -463,7 +497,13 @@ void level_step(lb_ctx *ctx, lb_refine *R, float *trace_row, long long t) {
 void child_steps(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, float *trace_row,
                  long long T) {
     float *Ucur = R->U[T & 1], *Uprev = R->U[(T + 1) & 1];
-    if (T >= 1) {  // snapshot U(T) fused with the midpoint transfer
+    if (R->coupling == LB_COUPLE_F2C) {  // nothing enters the patch: no snapshot, no transfer
+        if (T >= 1) {
+            launch_zero_in(ctx, R);
+            level_step(ctx, R, nullptr, 2 * T - 1);
+        }
+        launch_zero_in(ctx, R);
+    } else if (T >= 1) {  // snapshot U(T) fused with the midpoint transfer
         launch_snap_c2f(ctx, ap, R, Uprev, Ucur, 0.5f);
         level_step(ctx, R, nullptr, 2 * T - 1);
         launch_c2f(ctx, R, Ucur, Ucur, 1.0f);
@@ -473,7 +513,7 @@ void child_steps(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, f
     const float *fin_last = static_cast<const float *>(R->pop[R->cur]);
     const int fraw = R->raw ? 1 : 0;
     level_step(ctx, R, trace_row, 2 * T);
-    launch_f2c(ctx, ap, periodic, R, fin_last, fraw);
+    if (R->coupling != LB_COUPLE_C2F) launch_f2c(ctx, ap, periodic, R, fin_last, fraw);
 }
 
 void launch_overlay(lb_ctx *ctx, lb_refine *R, float *p) {
@@ -494,12 +534,20 @@ void launch_overlay(lb_ctx *ctx, lb_refine *R, float *p) {
 // committing, write the context-grid pressure of the nodes it covers, then recurse.
 void peek_level(lb_ctx *ctx, const StepArgs &ap, lb_refine *R, long long T, float *p) {
     float *Ucur = R->U[2], *Uprev = R->U[(T + 1) & 1];
-    launch_snapshot(ctx, ap, R, Ucur);
-    if (T >= 1) {
-        launch_c2f(ctx, R, Uprev, Ucur, 0.5f);
-        level_step(ctx, R, nullptr, 2 * T - 1);
+    if (R->coupling == LB_COUPLE_F2C) {
+        if (T >= 1) {
+            launch_zero_in(ctx, R);
+            level_step(ctx, R, nullptr, 2 * T - 1);
+        }
+        launch_zero_in(ctx, R);
+    } else {
+        launch_snapshot(ctx, ap, R, Ucur);
+        if (T >= 1) {
+            launch_c2f(ctx, R, Uprev, Ucur, 0.5f);
+            level_step(ctx, R, nullptr, 2 * T - 1);
+        }
+        launch_c2f(ctx, R, Ucur, Ucur, 1.0f);
     }
-    launch_c2f(ctx, R, Ucur, Ucur, 1.0f);
     launch_overlay(ctx, R, p);
     if (R->sub) {
         StepArgs af = level_args(ctx, R);
@@ -521,6 +569,8 @@ static lb_status setup_level(lb_ctx *ctx, const lb_config *cfg, lb_refine *paren
                              lb_refine **out) {
     const int pn_x = parent ? parent->nxf : ctx->nx, pn_y = parent ? parent->nyf : ctx->ny;
     if (P.ratio != 2) return fail(ctx, LB_EINVAL, "patch ratio must be 2");
+    if (P.coupling != LB_COUPLE_BOTH && P.coupling != LB_COUPLE_C2F && P.coupling != LB_COUPLE_F2C)
+        return fail(ctx, LB_EINVAL, "patch coupling must be LB_COUPLE_BOTH, _C2F or _F2C");
     if (P.nx_c < 1 || P.ny_c < 1 || P.x0 < 1 || P.y0 < 1 || P.x0 + P.nx_c > pn_x - 2 ||
         P.y0 + P.ny_c > pn_y - 2)
         return fail(ctx, LB_EINVAL,
@@ -529,6 +579,7 @@ static lb_status setup_level(lb_ctx *ctx, const lb_config *cfg, lb_refine *paren
                            : "patch must lie inside the grid with a 1-node margin");
     lb_refine *R = new lb_refine();
     *out = R;
+    R->coupling = P.coupling;
     R->depth = parent ? parent->depth + 1 : 1;
     {  // rates of this level (tau_f - 1/2 = 2 (tau_c - 1/2) per relaxed moment) and rescales
         auto fine_tau = [](double tc) { return 0.5 + 2.0 * (tc - 0.5); };

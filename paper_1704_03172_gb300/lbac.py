@@ -33,7 +33,10 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 class lb_patch(ctypes.Structure):
     _fields_ = [("x0", ctypes.c_int), ("y0", ctypes.c_int), ("nx_c", ctypes.c_int),
-                ("ny_c", ctypes.c_int), ("ratio", ctypes.c_int)]
+                ("ny_c", ctypes.c_int), ("ratio", ctypes.c_int), ("coupling", ctypes.c_int)]
+
+
+LB_COUPLE_BOTH, LB_COUPLE_C2F, LB_COUPLE_F2C = 0, 1, 2
 
 
 class lb_config(ctypes.Structure):

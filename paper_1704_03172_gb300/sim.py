@@ -29,7 +29,7 @@ class LBSim:
 
     def __init__(self, c_map, *, lattice=5, collision="bgk", tau=0.5, s=None, storage="f32",
                  boundary="zero", sponge_width=0, sponge_sigma_max=0.1, c_ref=None,
-                 w_ref=(4 / 9, 1 / 9, 1 / 36), patch=None, dx=0.0, time_block=1,
+                 w_ref=(4 / 9, 1 / 9, 1 / 36), patch=None, coupling="both", dx=0.0, time_block=1,
                  step_kernel="auto", device=None, stream=None, torch_allocator=True):
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.index is None:
@@ -79,10 +79,15 @@ class LBSim:
             cfg.c_map = host.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         if patch is not None:
             # one patch (x0, y0, nx_c, ny_c[, ratio]) or a list of nested patches, each in the
-            # node coordinates of the fine grid of the one before it
+            # node coordinates of the fine grid of the one before it; coupling "both", "c2f"
+            # or "f2c" (one value, or one per patch)
             plist = list(patch) if len(patch) and hasattr(patch[0], "__len__") else [patch]
+            modes = [coupling] * len(plist) if isinstance(coupling, str) else list(coupling)
+            code = {"both": lbac.LB_COUPLE_BOTH, "c2f": lbac.LB_COUPLE_C2F,
+                    "f2c": lbac.LB_COUPLE_F2C}
             self._patch = (lbac.lb_patch * len(plist))(
-                *[lbac.lb_patch(*[int(v) for v in q], *([2] if len(q) == 4 else [])) for q in plist])
+                *[lbac.lb_patch(*[int(v) for v in q[:4]], int(q[4]) if len(q) > 4 else 2, code[m])
+                  for q, m in zip(plist, modes)])
             cfg.patches = ctypes.cast(self._patch, ctypes.POINTER(lbac.lb_patch))
             cfg.n_patches = len(plist)
         cfg.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)

@@ -263,3 +263,88 @@ def test_footprint_covers_refined_levels(sim_cls):
 def ctypes_cast(arr, lbac):
     import ctypes
     return ctypes.cast(arr, ctypes.POINTER(lbac.lb_patch))
+
+
+ONE_WAY = [
+    # Q, collision, tau, s, periodic, heterogeneous, coupling
+    (5, "bgk", 0.5, None, False, True, "c2f"),
+    (5, "bgk", 0.5, None, False, True, "f2c"),
+    (5, "mrt", 0.5, [1.0, 1.0, 1.0, 1.4, 1.7], True, True, "f2c"),
+    (9, "bgk", 0.7, None, False, True, "c2f"),
+    (9, "mrt", 0.5, [1.0, 1.0, 1.0, 2.0, 2.0, 2.0, 1.0, 1.0, 2.0], True, False, "f2c"),
+]
+
+
+@pytest.mark.parametrize("Q,coll,tau,s,periodic,hetero,coupling", ONE_WAY)
+def test_one_way_coupling_matches_oracle(sim_cls, oracle_mod, Q, coll, tau, s, periodic, hetero,
+                                         coupling):
+    # the paper's switch on the direction of propagation (Sec. 4): coarse -> fine only, or
+    # fine -> coarse only (nothing enters the patch)
+    nx, ny, steps = 96, 80, 70
+    c = W.random_medium(nx, ny, 24, 0.6, 1.0) if hetero else W.uniform_map(nx, ny, 1.0)
+    patch = (40, 22, 30, 36)
+    wav = W.ricker(steps, 0.06)
+    rec = np.array([[20, 40], [40, 40], [52, 41], [70, 58], [69, 30], [85, 40]], np.int32)
+    kw = dict(tau=tau, s=s, w_ref=(0.4, 0.11, 0.04), c_ref=1.0)
+    sponge = 0 if periodic else 8
+    sim = sim_cls(c, lattice=Q, collision=coll, boundary="periodic" if periodic else "zero",
+                  sponge_width=sponge, sponge_sigma_max=0.1, patch=patch, coupling=coupling, **kw)
+    sim.set_source(15, 40, wav)
+    sim.set_receivers(rec, steps)
+    p0 = W.gaussian_pulse(nx, ny, 30, 50, 3.0, 1e-2).astype(np.float32)
+    p0 += W.gaussian_pulse(nx, ny, 55, 40, 2.5, 5e-3).astype(np.float32)   # inside the patch
+    sim.init_pressure(p0)
+    P = oracle_mod.Problem(Q, nx, ny, c, periodic=periodic, mrt=coll == "mrt",
+                           sponge_width=sponge, sponge_sigma_max=0.1,
+                           source=(15, 40, wav), receivers=rec, **kw)
+    R = oracle_mod.Refined(P, *patch)
+    R.direction(coupling)
+    R.init_pressure(p0.astype(np.float64))
+    assert rel(sim.pressure().cpu().numpy(), R.pressure()) < TOL
+    traces = []
+    for chunk in (1, 29, 40):
+        sim.step(chunk)
+        traces.append(R.run(chunk))
+        assert rel(sim.pressure().cpu().numpy(), R.pressure()) < TOL
+    tr = sim.traces().cpu().numpy()
+    sim.close()
+    assert rel(tr, np.concatenate(traces)) < TOL
+
+
+@pytest.mark.parametrize("modes", [("c2f", "f2c"), ("f2c", "both"), ("both", "c2f")])
+def test_nested_one_way_coupling_matches_oracle(sim_cls, oracle_mod, modes):
+    nx, ny, steps = 96, 80, 40
+    c = W.random_medium(nx, ny, 25, 0.6, 1.0)
+    patch, inner = (40, 22, 30, 36), (8, 14, 30, 30)
+    wav = W.ricker(steps, 0.06)
+    rec = np.array([[20, 40], [43, 41], [52, 38], [61, 47], [69, 30]], np.int32)
+    kw = dict(tau=0.5, w_ref=(0.4, 0.11, 0.04), c_ref=1.0)
+    sim = sim_cls(c, lattice=5, sponge_width=8, sponge_sigma_max=0.1, patch=[patch, inner],
+                  coupling=list(modes), **kw)
+    sim.set_source(15, 40, wav)
+    sim.set_receivers(rec, steps)
+    p0 = W.gaussian_pulse(nx, ny, 30, 50, 3.0, 1e-2).astype(np.float32)
+    p0 += W.gaussian_pulse(nx, ny, 52, 40, 2.0, 5e-3).astype(np.float32)
+    sim.init_pressure(p0)
+    P = oracle_mod.Problem(5, nx, ny, c, sponge_width=8, sponge_sigma_max=0.1,
+                           source=(15, 40, wav), receivers=rec, **kw)
+    R = oracle_mod.Refined(P, *patch)
+    R.nest(*inner)
+    R.direction(modes[0], level=1)
+    R.direction(modes[1], level=2)
+    R.init_pressure(p0.astype(np.float64))
+    traces = []
+    for chunk in (1, 19, 20):
+        sim.step(chunk)
+        traces.append(R.run(chunk))
+        assert rel(sim.pressure().cpu().numpy(), R.pressure()) < TOL
+    tr = sim.traces().cpu().numpy()
+    sim.close()
+    assert rel(tr, np.concatenate(traces)) < TOL
+
+
+def test_coupling_mode_is_checked(sim_cls):
+    from paper_1704_03172_gb300 import lbac
+    c = W.uniform_map(64, 48, 1.0)
+    with pytest.raises((lbac.LBError, KeyError)):
+        sim_cls(c, lattice=5, c_ref=1.0, patch=(10, 10, 20, 20), coupling="sideways")
