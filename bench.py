@@ -149,8 +149,6 @@ def job_rate(sec, units, ws, device="cuda"):
 
 def _workload(lattice=5, storage="f32", collision="bgk"):
     wl = W.two_layer_workload(N_GRID, lattice=lattice, collision=collision)
-    if lattice == 9 and collision == "mrt":
-        wl["s"] = [1.0, 1.0, 1.0, 2.0, 2.0, 2.0, 1.0, 1.0, 2.0]
     wl["storage"] = storage
     return wl
 

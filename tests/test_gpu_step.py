@@ -123,8 +123,6 @@ def test_two_layer_full_length_reduced_grid(sim_cls, oracle_mod, Q, coll):
     # the two-layer workload (contrast 1:2, sponge, Ricker source, line of receivers)
     # run for its full 5000 steps on a 256^2 version of the grid
     wl = W.two_layer_workload(256, lattice=Q, collision=coll, nrec=64)
-    if Q == 9 and coll == "mrt":
-        wl["s"] = [1.0, 1.0, 1.0, 2.0, 2.0, 2.0, 1.0, 1.0, 2.0]
     steps = wl["steps"]
     sim, P = _pair(sim_cls, oracle_mod, Q, 256, 256, wl["c_map"], collision=coll,
                    tau=wl["tau"], s=wl.get("s"), sponge=wl["sponge_width"],

@@ -384,3 +384,28 @@ def test_receiver_trace_is_pressure_before_step(oracle_mod):
         np.testing.assert_allclose(tr[t], eta2 / 2 * gg.sum(0)[rec[:, 1], rec[:, 0]],
                                    atol=1e-14)   # p = c_s^2 rho, c_s^2 = eta^2 / 2 (D2Q5)
         gg, _ = oracle_mod.run(P, gg, 1, t0=t)
+
+
+@pytest.mark.parametrize("Q", [5, 9])
+def test_seeded_mrt_rates_of_the_two_layer_workload_are_stable(Q):
+    # Reading A2: the seeded MRT rates must pass a stability precheck, max |lambda(k)| <= 1 +
+    # 1e-12 over a 64^2 wave-vector grid, at every speed of the medium (eta = 1/2 and 1 in
+    # the two-layer workload), with the workload's weights; built from the amplification
+    # matrix T(k) = D(k) (I - C A) written independently of the oracle's stepper
+    wl = W.two_layer_workload(64, lattice=Q, collision="mrt")
+    s, wref, n = wl["s"], wl["w_ref"], 64
+    worst = 0.0
+    for eta in sorted({float(v) / wl["c_ref"] for v in np.unique(wl["c_map"])}):
+        e2 = eta * eta
+        if Q == 5:
+            w, cs2 = np.array([1 - e2] + [e2 / 4] * 4), e2 / 2
+        else:
+            w1, w5 = e2 * wref[1], e2 * wref[2]
+            w = np.array([1 - 4 * (w1 + w5)] + [w1] * 4 + [w5] * 4)
+            cs2 = e2 * (2 * wref[1] + 4 * wref[2])
+        for a in range(n):
+            for b in range(n):
+                T = lbspec.amplification(Q, (2 * np.pi * a / n, 2 * np.pi * b / n), w, cs2,
+                                         mrt=True, s=s)
+                worst = max(worst, np.abs(np.linalg.eigvals(T)).max())
+    assert worst <= 1 + 1e-12
