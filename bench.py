@@ -624,7 +624,7 @@ def run_ours(args):
             print(json.dumps({"variant": name, **out}), flush=True)
         return 0
 
-    wl = _workload(args.lattice, args.storage, "bgk")
+    wl = _workload(args.lattice, args.storage, args.collision)
     wl["time_block"] = args.time_block
     wl["step_kernel"] = args.step_kernel
     sim = _make_sim(LBSim, wl, args.steps + args.warmup)
@@ -665,9 +665,10 @@ def run_ours(args):
     staged = K == 1 and (args.step_kernel == "staged" or
                          (args.step_kernel == "auto" and args.storage != "f32"))
     st_name = dict(f32='float', bf16='__nv_bfloat16', f16='__half')[args.storage]
-    kname = (f"tb_kernel<{args.lattice},false,false,{K}>" if K > 1 else
-             f"stream_step_kernel<{args.lattice},false,false,{st_name}>" if staged else
-             f"lbk::step_kernel<{args.lattice},false,false,{st_name}>")
+    mrt = "true" if args.collision == "mrt" else "false"
+    kname = (f"tb_kernel<{args.lattice},{mrt},false,{K}>" if K > 1 else
+             f"stream_step_kernel<{args.lattice},{mrt},false,{st_name}>" if staged else
+             f"lbk::step_kernel<{args.lattice},{mrt},false,{st_name}>")
     traffic = NCU_TRAFFIC.get((kname, bool(indexed and K == 1)))
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
@@ -675,7 +676,9 @@ def run_ours(args):
         "ms_per_step": round(sec / args.steps * 1e3, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
         "config": {"workload": f"two-layer {N_GRID}x{N_GRID} (c 1:2 at mid-depth), "
-                               f"D2Q{args.lattice} BGK tau=1/2, {args.storage.upper()} populations, "
+                               f"D2Q{args.lattice} " + ("BGK tau=1/2" if args.collision == "bgk"
+                                                         else "MRT (seeded rates)") +
+                               f", {args.storage.upper()} populations, "
                                "40-cell sponge, Ricker source, 512 receivers; one bench step = "
                                "one LB time step" + (f" ({K} steps fused per launch)" if K > 1 else ""),
                    "parallelism": f"replicas x{ws} (independent shots)",
@@ -782,6 +785,8 @@ def main():
                     help="shots in the served stream (0 skips it)")
     ap.add_argument("--served-calibration", type=int, default=64,
                     help="closed-loop shots that set the Poisson arrival rate")
+    ap.add_argument("--collision", choices=["bgk", "mrt"], default="bgk",
+                    help="main line only (profiling runs): BGK or MRT with the seeded rates")
     ap.add_argument("--lattice", type=int, choices=[5, 9], default=5,
                     help="main line's lattice (D2Q5 is the paper's recommended scheme)")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")
