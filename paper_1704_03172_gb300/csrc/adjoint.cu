@@ -100,8 +100,8 @@ __device__ __forceinline__ float adj_site(float (&m)[Q], float e2, const StepArg
         }
         // MRT: only e (row 3 of M, norm 20) and p_xx (row 4, norm 4) relax; both are even
         // in c, so B = 0, and v = (-4 e', e' + p', e' - p', e' + p', e' - p')
-        const float me = (-4.f * m[0] + s14) * a.s[3] * (1.f / 20.f);
-        const float mp = (m[1] - m[2] + m[3] - m[4]) * a.s[4] * 0.25f;
+        const float me = (-4.f * m[0] + s14) * a.s[3];  // rates arrive as s_e / 20, s_p / 4
+        const float mp = (m[1] - m[2] + m[3] - m[4]) * a.s[4];
         const float v13 = me + mp, v24 = me - mp;
         const float A = 4.f * me * (w1 - w0);  // w0 v0 + w1 (2 v13 + 2 v24)
         m[0] = m[0] + 4.f * me + A;
@@ -124,14 +124,13 @@ __device__ __forceinline__ float adj_site(float (&m)[Q], float e2, const StepArg
             for (int i = 0; i < Q; i++) v[i] = a.omega * m[i];
         } else {
             const float s14 = m[1] + m[2] + m[3] + m[4], s58 = m[5] + m[6] + m[7] + m[8];
-            const float d3 = a.s[3] * (-4.f * m[0] - s14 + 2.f * s58) * (1.f / 36.f);
-            const float d4 = a.s[4] * (m[1] - m[2] + m[3] - m[4]) * 0.25f;
-            const float d5 = a.s[5] * (4.f * m[0] - 2.f * s14 + s58) * (1.f / 36.f);
-            const float d6 = a.s[6] * (-2.f * m[1] + 2.f * m[3] + m[5] - m[6] - m[7] + m[8]) *
-                             (1.f / 12.f);
-            const float d7 = a.s[7] * (-2.f * m[2] + 2.f * m[4] + m[5] + m[6] - m[7] - m[8]) *
-                             (1.f / 12.f);
-            const float d8 = a.s[8] * (m[5] - m[6] + m[7] - m[8]) * 0.25f;
+            // rates arrive divided by the squared row norms (36, 4, 36, 12, 12, 4)
+            const float d3 = a.s[3] * (-4.f * m[0] - s14 + 2.f * s58);
+            const float d4 = a.s[4] * (m[1] - m[2] + m[3] - m[4]);
+            const float d5 = a.s[5] * (4.f * m[0] - 2.f * s14 + s58);
+            const float d6 = a.s[6] * (-2.f * m[1] + 2.f * m[3] + m[5] - m[6] - m[7] + m[8]);
+            const float d7 = a.s[7] * (-2.f * m[2] + 2.f * m[4] + m[5] + m[6] - m[7] - m[8]);
+            const float d8 = a.s[8] * (m[5] - m[6] + m[7] - m[8]);
             v[0] = -4.f * d3 + 4.f * d5;
             v[1] = -d3 + d4 - 2.f * d5 - 2.f * d6;
             v[2] = -d3 - d4 - 2.f * d5 - 2.f * d7;

@@ -188,7 +188,7 @@ lb_status f64_setup(lb_ctx *c, const float *cmap_dev, double cref) {
     std::vector<double> co(kNCo64, 0.0);
     const lb_config &g = c->cfg;
     co[kCoOmega] = 1.0 / g.tau;
-    for (int k = 0; k < 9; k++) co[kCoS + k] = g.s[k];
+    for (int k = 0; k < 9; k++) co[kCoS + k] = g.s[k] / mrt_norm(c->Q, k);
     const double c2r = 2.0 * g.w_ref[1] + 4.0 * g.w_ref[2];
     co[kCoW1r] = g.w_ref[1];
     co[kCoW5r] = g.w_ref[2];

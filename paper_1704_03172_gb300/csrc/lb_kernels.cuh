@@ -98,7 +98,7 @@ struct StepArgs {
     int main_blocks;         // blocks doing sites; the rest gather receivers
     // collision
     float omega;             // BGK: 1 / tau
-    float s[9];              // MRT: diagonal of S (moment order of App. A)
+    float s[9];              // MRT: diagonal of S (moment order of App. A), s_k / |row_k of M|^2
     float w1r, w5r, c2r;     // D2Q9 reference weights at eta = 1, c2r = 2 w1r + 4 w5r
     float a1, a5;            // D2Q9 w_i / c_s^2 of axis / diagonal links (eta independent)
     // sponge
@@ -481,8 +481,8 @@ __device__ __forceinline__ void collide5(R g[5], R e2, const StepArgs &a) {
         // g* = g - M^-1 S (m - m^eq), M^-1 = M^T diag(1/5, 1/2, 1/2, 1/20, 1/4).
         const R e_neq = (rho - R(5) * g[0]) - (R(-4) + R(5) * e2) * rho;
         const R pxx = g[1] - g[2] + g[3] - g[4];
-        const R de = co<R>(a, a.s[3], kCoS + 3) * e_neq * (R(1) / R(20));
-        const R dp = co<R>(a, a.s[4], kCoS + 4) * pxx * R(0.25);
+        const R de = co<R>(a, a.s[3], kCoS + 3) * e_neq;  // s_e / 20 (rates come normalised)
+        const R dp = co<R>(a, a.s[4], kCoS + 4) * pxx;    // s_p / 4
         g[0] += R(4) * de;
         g[1] -= de + dp;
         g[2] -= de - dp;
@@ -519,16 +519,15 @@ __device__ __forceinline__ void collide9(R g[9], R e2, const StepArgs &a) {
         for (int i = 0; i < 9; i++) n[i] = g[i] - eq[i];
         const R s14 = n[1] + n[2] + n[3] + n[4], s58 = n[5] + n[6] + n[7] + n[8];
         // non-conserved moments of g - g^eq (rows 3..8 of M, App. A), scaled by s_k / |row_k|^2
-        const R d3 =
-            co<R>(a, a.s[3], kCoS + 3) * (-R(4) * n[0] - s14 + R(2) * s58) * (R(1) / R(36));
-        const R d4 = co<R>(a, a.s[4], kCoS + 4) * (n[1] - n[2] + n[3] - n[4]) * R(0.25);
-        const R d5 =
-            co<R>(a, a.s[5], kCoS + 5) * (R(4) * n[0] - R(2) * s14 + s58) * (R(1) / R(36));
+        // (the rates arrive divided by the squared row norms: 36, 4, 36, 12, 12, 4)
+        const R d3 = co<R>(a, a.s[3], kCoS + 3) * (-R(4) * n[0] - s14 + R(2) * s58);
+        const R d4 = co<R>(a, a.s[4], kCoS + 4) * (n[1] - n[2] + n[3] - n[4]);
+        const R d5 = co<R>(a, a.s[5], kCoS + 5) * (R(4) * n[0] - R(2) * s14 + s58);
         const R d6 = co<R>(a, a.s[6], kCoS + 6) *
-                     (-R(2) * n[1] + R(2) * n[3] + n[5] - n[6] - n[7] + n[8]) * (R(1) / R(12));
+                     (-R(2) * n[1] + R(2) * n[3] + n[5] - n[6] - n[7] + n[8]);
         const R d7 = co<R>(a, a.s[7], kCoS + 7) *
-                     (-R(2) * n[2] + R(2) * n[4] + n[5] + n[6] - n[7] - n[8]) * (R(1) / R(12));
-        const R d8 = co<R>(a, a.s[8], kCoS + 8) * (n[5] - n[6] + n[7] - n[8]) * R(0.25);
+                     (-R(2) * n[2] + R(2) * n[4] + n[5] + n[6] - n[7] - n[8]);
+        const R d8 = co<R>(a, a.s[8], kCoS + 8) * (n[5] - n[6] + n[7] - n[8]);
         // g* = g - M^T (d3..d8)
         g[0] -= -R(4) * d3 + R(4) * d5;
         g[1] -= -d3 + d4 - R(2) * d5 - R(2) * d6;

@@ -85,6 +85,17 @@ inline cudaError_t launch_pdl(void (*kernel)(ExpTypes...), dim3 grid, dim3 block
     return cudaLaunchKernelEx(&lc, kernel, std::forward<ActTypes>(args)...);
 }
 
+// MRT rates as the collision kernels take them: s_k divided by the squared norm of row k of
+// M (App. A), so that the kernels' relaxation d_k = s_k m_k / |row_k|^2 costs one multiply.
+// D2Q5: e 20, p_xx 4; D2Q9: e and eps 36, p_xx and p_xy 4, q_x and q_y 12; 1 otherwise.
+inline double mrt_norm(int Q, int k) {
+    if (Q == 5) return k == 3 ? 20.0 : k == 4 ? 4.0 : 1.0;
+    if (Q == 9)
+        return (k == 3 || k == 5) ? 36.0 : (k == 4 || k == 8) ? 4.0 : (k == 6 || k == 7) ? 12.0 : 1.0;
+    return 1.0;
+}
+inline float mrt_rate_arg(int Q, int k, double s) { return (float)(s / mrt_norm(Q, k)); }
+
 using StepFn = void (*)(const lbk::StepArgs);
 using GetFn = void (*)(lbk::StepArgs, float *, int);
 lbk::StepArgs base_args(const lb_ctx *c);

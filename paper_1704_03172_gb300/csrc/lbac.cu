@@ -135,7 +135,7 @@ StepArgs base_args(const lb_ctx *c) {
     long long warps = (long long)a.segs * c->ny;
     a.main_blocks = (int)((warps + kWarps - 1) / kWarps);
     a.omega = (float)(1.0 / c->cfg.tau);
-    for (int k = 0; k < 9; k++) a.s[k] = (float)c->cfg.s[k];
+    for (int k = 0; k < 9; k++) a.s[k] = mrt_rate_arg(c->Q, k, c->cfg.s[k]);
     a.w1r = (float)c->cfg.w_ref[1];
     a.w5r = (float)c->cfg.w_ref[2];
     double c2r = 2.0 * c->cfg.w_ref[1] + 4.0 * c->cfg.w_ref[2];

@@ -352,7 +352,7 @@ StepArgs level_args(const lb_ctx *ctx, const lb_refine *R) {
     a.mid = nullptr;  // refined levels read their own eta^2 plane
     a.mid_tab = nullptr;
     a.omega = R->omega_f;  // viscosity-continuous relaxation of this level
-    for (int k = 0; k < 9; k++) a.s[k] = R->s_f[k];
+    for (int k = 0; k < 9; k++) a.s[k] = mrt_rate_arg(ctx->Q, k, R->s_f[k]);
     a.nx = R->gx;
     a.ny = R->gy;
     a.ny3 = R->gy;
@@ -373,9 +373,9 @@ StepArgs level_args(const lb_ctx *ctx, const lb_refine *R) {
 }
 
 // rates whose collision is the non-equilibrium rescale g^eq + F (g - g^eq)
-StepArgs rescale_args(StepArgs a, float omega, const float *s) {
+StepArgs rescale_args(StepArgs a, int Q, float omega, const float *s) {
     a.omega = omega;
-    for (int k = 0; k < 9; k++) a.s[k] = s[k];
+    for (int k = 0; k < 9; k++) a.s[k] = mrt_rate_arg(Q, k, s[k]);
     return a;
 }
 
@@ -383,7 +383,7 @@ template <int Q, bool MRT>
 void c2f_q(lb_ctx *ctx, lb_refine *R, const StepArgs &af, const float *Ua, const float *Ub,
            float alpha) {
     launch_pdl(ref_c2f_kernel<Q, MRT>, dim3(blocks_for(R->nIf)), dim3(256), 0, ctx->stream, af,
-               rescale_args(af, R->c2f_omega, R->c2f_s), R->If, R->nIf, Ua, Ub, alpha, R->nxf,
+               rescale_args(af, Q, R->c2f_omega, R->c2f_s), R->If, R->nIf, Ua, Ub, alpha, R->nxf,
                R->nyf);
 }
 
@@ -403,7 +403,7 @@ template <int Q, bool MRT>
 void snap_c2f_q(lb_ctx *ctx, const StepArgs &ap, lb_refine *R, const StepArgs &af, const float *Ua,
                 float *Ucur, float alpha) {
     launch_pdl(ref_snap_c2f_kernel<Q, MRT>, dim3(blocks_for(R->nIf)), dim3(256), 0, ctx->stream,
-               ap, af, rescale_args(af, R->c2f_omega, R->c2f_s), R->If, R->nIf, R->Ic, Ua, Ucur,
+               ap, af, rescale_args(af, Q, R->c2f_omega, R->c2f_s), R->If, R->nIf, R->Ic, Ua, Ucur,
                alpha, R->nxf, R->nyf);
 }
 
@@ -450,7 +450,7 @@ void f2c_q(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, const f
     long long fplane = (long long)R->gy * R->pitch;
     launch_pdl(periodic ? ref_f2c_kernel<Q, MRT, true> : ref_f2c_kernel<Q, MRT, false>,
                dim3(blocks_for(R->nI)), dim3(256), 0, ctx->stream, ap,
-               rescale_args(ap, R->f2c_omega, R->f2c_s), fin, fraw, R->pitch, fplane, R->Ic, R->nI,
+               rescale_args(ap, Q, R->f2c_omega, R->f2c_s), fin, fraw, R->pitch, fplane, R->Ic, R->nI,
                R->x0, R->y0, R->nxp, R->nyp);
 }
 
