@@ -83,8 +83,12 @@ class LBSim:
             # or "f2c" (one value, or one per patch)
             plist = list(patch) if len(patch) and hasattr(patch[0], "__len__") else [patch]
             modes = [coupling] * len(plist) if isinstance(coupling, str) else list(coupling)
+            if len(modes) != len(plist):
+                raise ValueError(f"coupling: {len(modes)} values for {len(plist)} patches")
             code = {"both": lbac.LB_COUPLE_BOTH, "c2f": lbac.LB_COUPLE_C2F,
                     "f2c": lbac.LB_COUPLE_F2C}
+            if any(m not in code for m in modes):
+                raise ValueError(f"coupling must be 'both', 'c2f' or 'f2c', not {modes}")
             self._patch = (lbac.lb_patch * len(plist))(
                 *[lbac.lb_patch(*[int(v) for v in q[:4]], int(q[4]) if len(q) > 4 else 2, code[m])
                   for q, m in zip(plist, modes)])

@@ -344,7 +344,9 @@ def test_nested_one_way_coupling_matches_oracle(sim_cls, oracle_mod, modes):
 
 
 def test_coupling_mode_is_checked(sim_cls):
-    from paper_1704_03172_gb300 import lbac
     c = W.uniform_map(64, 48, 1.0)
-    with pytest.raises((lbac.LBError, KeyError)):
+    with pytest.raises(ValueError):
         sim_cls(c, lattice=5, c_ref=1.0, patch=(10, 10, 20, 20), coupling="sideways")
+    with pytest.raises(ValueError):  # one value per patch
+        sim_cls(c, lattice=5, c_ref=1.0, patch=[(10, 10, 20, 20), (4, 4, 8, 8)],
+                coupling=["c2f"])
