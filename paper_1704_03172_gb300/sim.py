@@ -24,6 +24,24 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+_COUPLING = {"both": lbac.LB_COUPLE_BOTH, "c2f": lbac.LB_COUPLE_C2F, "f2c": lbac.LB_COUPLE_F2C}
+
+
+def patch_array(patch, coupling="both"):
+    """The lb_patch array of one patch (x0, y0, nx_c, ny_c[, ratio]) or of a list of nested
+    patches, each in the node coordinates of the fine grid of the one before it.  coupling:
+    "both", "c2f" or "f2c", one value for all patches or one per patch."""
+    plist = list(patch) if len(patch) and hasattr(patch[0], "__len__") else [patch]
+    modes = [coupling] * len(plist) if isinstance(coupling, str) else list(coupling)
+    if len(modes) != len(plist):
+        raise ValueError(f"coupling: {len(modes)} values for {len(plist)} patches")
+    if any(m not in _COUPLING for m in modes):
+        raise ValueError(f"coupling must be 'both', 'c2f' or 'f2c', not {modes}")
+    return (lbac.lb_patch * len(plist))(
+        *[lbac.lb_patch(*[int(v) for v in q[:4]], int(q[4]) if len(q) > 4 else 2, _COUPLING[m])
+          for q, m in zip(plist, modes)])
+
+
 class LBSim:
     """One linear-LB acoustic simulation ("shot") on the current CUDA device."""
 
@@ -78,22 +96,9 @@ class LBSim:
             self._cmap_keep = host
             cfg.c_map = host.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         if patch is not None:
-            # one patch (x0, y0, nx_c, ny_c[, ratio]) or a list of nested patches, each in the
-            # node coordinates of the fine grid of the one before it; coupling "both", "c2f"
-            # or "f2c" (one value, or one per patch)
-            plist = list(patch) if len(patch) and hasattr(patch[0], "__len__") else [patch]
-            modes = [coupling] * len(plist) if isinstance(coupling, str) else list(coupling)
-            if len(modes) != len(plist):
-                raise ValueError(f"coupling: {len(modes)} values for {len(plist)} patches")
-            code = {"both": lbac.LB_COUPLE_BOTH, "c2f": lbac.LB_COUPLE_C2F,
-                    "f2c": lbac.LB_COUPLE_F2C}
-            if any(m not in code for m in modes):
-                raise ValueError(f"coupling must be 'both', 'c2f' or 'f2c', not {modes}")
-            self._patch = (lbac.lb_patch * len(plist))(
-                *[lbac.lb_patch(*[int(v) for v in q[:4]], int(q[4]) if len(q) > 4 else 2, code[m])
-                  for q, m in zip(plist, modes)])
+            self._patch = patch_array(patch, coupling)
             cfg.patches = ctypes.cast(self._patch, ctypes.POINTER(lbac.lb_patch))
-            cfg.n_patches = len(plist)
+            cfg.n_patches = len(self._patch)
         cfg.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
         if torch_allocator:
             dev, strm = self.device, self.stream
