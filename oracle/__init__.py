@@ -88,7 +88,7 @@ def _declare(L):
                  "orc_collide", "orc_init_pressure", "orc_pressure", "orc_run",
                  "orc_max_threads"):
         getattr(L, name).restype = ctypes.c_int
-    if hasattr(L, "orc_refined_run"):
+    if hasattr(L, "orc_ref_create"):
         _declare_refine(L)
     if hasattr(L, "orc_adjoint"):
         _declare_adjoint(L)
@@ -113,10 +113,19 @@ def _declare_refine(L):
     L.orc_ref_level_dims.argtypes = [vp, ctypes.c_int, _ip, _ip]
     L.orc_ref_level_pressure.argtypes = [vp, ctypes.c_int, _dp]
     L.orc_ref_level_cmap.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
+    L.orc_ref_level_state.argtypes = [vp, ctypes.c_int, ctypes.c_int, _dp]
+    L.orc_ref_start.argtypes = [vp, ctypes.c_int]
+    L.orc_ref_transfer.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   _dp, _dp]
+    L.orc_ref_interface.argtypes = [vp, ctypes.c_int, _ip, _ip]
+    L.orc_ref_apply_c2f.argtypes = [vp, ctypes.c_int, _dp, _dp, ctypes.c_double]
+    L.orc_ref_apply_f2c.argtypes = [vp, ctypes.c_int]
     for n in ("orc_ref_dims", "orc_ref_fine_cmap", "orc_ref_init_pressure", "orc_ref_run",
               "orc_ref_pressure", "orc_ref_fine_pressure", "orc_ref_states", "orc_ref_nest",
               "orc_ref_direction",
-              "orc_ref_level_dims", "orc_ref_level_pressure", "orc_ref_level_cmap"):
+              "orc_ref_level_dims", "orc_ref_level_pressure", "orc_ref_level_cmap",
+              "orc_ref_level_state", "orc_ref_start", "orc_ref_transfer", "orc_ref_interface",
+              "orc_ref_apply_c2f", "orc_ref_apply_f2c"):
         getattr(L, n).restype = ctypes.c_int
 
 
@@ -207,6 +216,55 @@ class Refined:
         gf = np.zeros((self.P.Q, self.nyf, self.nxf))
         lib().orc_ref_states(self.h, _ptr(gc, ctypes.c_double), _ptr(gf, ctypes.c_double))
         return gc, gf
+
+    # --- access to the individual transfer functions (the tests that pin them) ---
+
+    def level_state(self, level):
+        """state [Q][ny][nx] of level `level` (0: the coarse grid, l >= 1: patch l's fine grid)"""
+        ny, nx = (self.P.ny, self.P.nx) if level == 0 else self.level_dims(level)
+        g = np.zeros((self.P.Q, ny, nx))
+        assert lib().orc_ref_level_state(self.h, int(level), 0, _ptr(g, ctypes.c_double)) == 0
+        return g
+
+    def set_level_state(self, level, g):
+        ny, nx = (self.P.ny, self.P.nx) if level == 0 else self.level_dims(level)
+        g = np.ascontiguousarray(g, np.float64).reshape(self.P.Q, ny, nx)
+        assert lib().orc_ref_level_state(self.h, int(level), 1, _ptr(g, ctypes.c_double)) == 0
+
+    def start(self, couple=True):
+        """time 0 from the states set with set_level_state: snapshots and (couple) the
+        coupling at time 0, as init_pressure does"""
+        lib().orc_ref_start(self.h, int(bool(couple)))
+        self.t = 0
+
+    def transfer(self, level, to_fine, ax, ay, g):
+        """one vector g[Q] carried into node (ax, ay) of the receiving grid of patch `level`
+        (its fine grid when to_fine, else the grid above): Eq. coarse-fine dist connect"""
+        g = np.ascontiguousarray(g, np.float64)
+        out = np.zeros(self.P.Q)
+        assert lib().orc_ref_transfer(self.h, int(level), int(bool(to_fine)), int(ax), int(ay),
+                                      _ptr(g, ctypes.c_double), _ptr(out, ctypes.c_double)) == 0
+        return out
+
+    def interface(self, level=1):
+        """interface nodes of patch `level`, (x, y) in the grid above, in snapshot order"""
+        n = lib().orc_ref_interface(self.h, int(level), None, None)
+        assert n >= 0
+        ix = np.zeros(n, np.int32)
+        iy = np.zeros(n, np.int32)
+        lib().orc_ref_interface(self.h, int(level), _ptr(ix, ctypes.c_int), _ptr(iy, ctypes.c_int))
+        return np.stack([ix, iy], 1)
+
+    def apply_c2f(self, level, Ua, Ub, alpha):
+        """one coarse -> fine transfer into patch `level` from snapshots Ua, Ub [nI][Q]"""
+        Ua = np.ascontiguousarray(Ua, np.float64)
+        Ub = np.ascontiguousarray(Ub, np.float64)
+        assert lib().orc_ref_apply_c2f(self.h, int(level), _ptr(Ua, ctypes.c_double),
+                                       _ptr(Ub, ctypes.c_double), float(alpha)) == 0
+
+    def apply_f2c(self, level):
+        """one fine -> coarse correction of the grid above patch `level`"""
+        assert lib().orc_ref_apply_f2c(self.h, int(level)) == 0
 
     def __del__(self):
         try:

@@ -75,6 +75,14 @@ int orc_ref_direction(void *h, int level, int dir);
 int orc_ref_level_dims(void *h, int level, int *nx, int *ny);
 int orc_ref_level_pressure(void *h, int level, double *p);
 int orc_ref_level_cmap(void *h, int level, float *c);
+/* access to the individual transfer functions (for the tests that pin them) */
+int orc_ref_level_state(void *h, int level, int set, double *g);
+int orc_ref_start(void *h, int couple);
+int orc_ref_transfer(void *h, int level, int to_fine, int ax, int ay, const double *g,
+                     double *out);
+int orc_ref_interface(void *h, int level, int *Ix, int *Iy);
+int orc_ref_apply_c2f(void *h, int level, const double *Ua, const double *Ub, double alpha);
+int orc_ref_apply_f2c(void *h, int level);
 
 /* Discrete adjoint (lbadjoint.c): gradients of J with dJ/dp^t_r = resid[t][r]
  * for nt steps from g0.  grad_c [ny][nx]; grad_src [nt] and grad_g0 [Q][ny][nx]

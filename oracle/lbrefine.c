@@ -17,8 +17,9 @@
  *   fine   <- coarse:  g^f = g^eq + (g^c - g^eq) / n,
  *   coarse <- fine:    g^c = g^eq + (g^f - g^eq) * n,
  * with g^eq formed from the moments of the transferred vector and the
- * receiving grid's weights.  "Specifying the direction of wave propagation"
- * is read per population: at a fine node of I the populations whose upstream
+ * receiving grid's weights.  Sec. 4 lets the direction in which waves cross the
+ * interface decide which grid supplies a value; that choice is read here per
+ * population (reading R3): at a fine node of I the populations whose upstream
  * node x - c_i lies outside the fine grid come from the coarse grid; at a
  * coarse node of I the populations whose upstream node lies strictly inside
  * the patch come from the fine grid.  The coarse grid keeps evolving under the
@@ -54,7 +55,7 @@ typedef struct ref_s {
     orc_problem C, F;
     struct ref_s *sub; /* nested patch inside F, or NULL */
     int rule;
-    /* direction of the coupling (Sec. 4, "specify the direction of wave propagation"):
+    /* direction of the coupling (Sec. 4, the switch on which way waves cross the interface):
      * 0 both ways, population by population (reading R3); 1 coarse -> fine only (the
      * coarse grid is never corrected from the fine one); 2 fine -> coarse only (no coarse
      * population enters the fine grid: what enters it across I is zero, the zero ghost) */
@@ -118,6 +119,26 @@ static int in_closed_patch(const ref_t *R, int X, int Y) {
     return X >= R->x0 && X <= R->x0 + R->nxp && Y >= R->y0 && Y <= R->y0 + R->nyp;
 }
 
+/* Eq. coarse-fine dist connect for one vector g that arrives at node idx of the receiving
+ * grid (the fine grid when to_fine, else the coarse one): g^eq is formed from g's own
+ * moments with the receiving grid's weights (Eq. grid refinement eqm dist), and the
+ * non-equilibrium part g - g^eq is scaled by that direction's factors (1/n and n at
+ * tau = 1/2; reading R6 otherwise). */
+static void transfer(const ref_t *R, int to_fine, size_t idx, const double *g, double *out) {
+    const int Q = R->C.Q;
+    const int(*cv)[2] = vel(Q);
+    double rho = 0, jx = 0, jy = 0;
+    for (int i = 0; i < Q; i++) {
+        rho += g[i];
+        jx += cv[i][0] * g[i];
+        jy += cv[i][1] * g[i];
+    }
+    double w[9], cs2, geq[9];
+    orc_site_weights(to_fine ? &R->F : &R->C, idx, w, &cs2);
+    orc_equilibrium(Q, w, cs2, rho, jx, jy, geq);
+    rescale_neq(R, to_fine ? R->fc2f : R->ff2c, g, geq, out);
+}
+
 static const double *U_at(const ref_t *R, const double *U, int X, int Y) {
     int k = R->idxI[(Y - R->y0) * (R->nxp + 1) + (X - R->x0)];
     return U + (size_t)k * R->C.Q;
@@ -153,19 +174,13 @@ static void c2f(const ref_t *R, double *gf, const double *Ua, const double *Ub, 
                 pb[1] = U_at(R, Ub, X, Y + 1);
                 np = 2;
             }
-            double gh[9], rho = 0, jx = 0, jy = 0;
+            double gh[9], gr[9];
             for (int i = 0; i < Q; i++) {
                 double s = 0;
                 for (int k = 0; k < np; k++) s += (1.0 - alpha) * pa[k][i] + alpha * pb[k][i];
                 gh[i] = s / np;
-                rho += gh[i];
-                jx += cv[i][0] * gh[i];
-                jy += cv[i][1] * gh[i];
             }
-            double w[9], cs2, geq[9], gr[9];
-            orc_site_weights(&R->F, (size_t)b * R->nxf + a, w, &cs2);
-            orc_equilibrium(Q, w, cs2, rho, jx, jy, geq);
-            rescale_neq(R, R->fc2f, gh, geq, gr);
+            transfer(R, 1, (size_t)b * R->nxf + a, gh, gr);
             for (int i = 0; i < Q; i++) {
                 int ua = a - cv[i][0], ub = b - cv[i][1];
                 if (ua >= 0 && ua < R->nxf && ub >= 0 && ub < R->nyf) continue;  /* from fine */
@@ -183,18 +198,10 @@ static void f2c(const ref_t *R, double *gc, const double *gf) {
     for (int k = 0; k < R->nI; k++) {
         int X = R->Ix[k], Y = R->Iy[k];
         size_t fidx = (size_t)(2 * (Y - R->y0)) * R->nxf + 2 * (X - R->x0);
-        double G[9], rho = 0, jx = 0, jy = 0;
-        for (int i = 0; i < Q; i++) {
-            G[i] = gf[(size_t)i * Nf + fidx];
-            rho += G[i];
-            jx += cv[i][0] * G[i];
-            jy += cv[i][1] * G[i];
-        }
-        double w[9], cs2, geq[9], gr[9];
+        double G[9], gr[9];
+        for (int i = 0; i < Q; i++) G[i] = gf[(size_t)i * Nf + fidx];
         size_t cidx = (size_t)Y * R->C.nx + X;
-        orc_site_weights(&R->C, cidx, w, &cs2);
-        orc_equilibrium(Q, w, cs2, rho, jx, jy, geq);
-        rescale_neq(R, R->ff2c, G, geq, gr);
+        transfer(R, 0, cidx, G, gr);
         for (int i = 0; i < Q; i++)
             if (strictly_inside(R, X - cv[i][0], Y - cv[i][1])) gc[(size_t)i * N + cidx] = gr[i];
     }
@@ -310,11 +317,21 @@ int orc_ref_fine_cmap(void *h, float *cf) {
     return 0;
 }
 
-/* Fine grid of R from the pressure pc on R's coarse grid (NULL: zero): g = g^eq(p / c_s^2, 0)
- * with p interpolated bilinearly, the same for every nested level, then the coupling at
- * time 0 of each pair (the couplings of different pairs touch different nodes when every
+/* The start of a run from states already set on every level: for each pair of adjacent
+ * levels, innermost first, the snapshot U(0) of the coarser side on I and the coupling at
+ * time 0 (when `couple`; the couplings of different pairs touch different nodes when every
  * patch keeps a margin of at least one node, so their order is immaterial). */
-static void init_level(ref_t *R, const double *pc, double *gcs) {
+static void start_level(ref_t *R, double *gcs, int couple) {
+    if (R->sub) start_level(R->sub, R->gf, couple);
+    snapshot(R, gcs, R->Uprev);
+    if (!couple) return;
+    if (R->dir != 2) c2f(R, R->gf, R->Uprev, R->Uprev, 1.0);
+    if (R->dir != 1) f2c(R, gcs, R->gf);
+}
+
+/* Fine grid of R from the pressure pc on R's coarse grid (NULL: zero): g = g^eq(p / c_s^2, 0)
+ * with p interpolated bilinearly, the same for every nested level. */
+static void init_level(ref_t *R, const double *pc) {
     const int nx = R->C.nx;
     const size_t Nf = (size_t)R->nxf * R->nyf;
     double *pf = NULL;
@@ -333,11 +350,8 @@ static void init_level(ref_t *R, const double *pc, double *gcs) {
             }
     }
     orc_init_pressure(&R->F, pf, R->gf);
-    if (R->sub) init_level(R->sub, pf, R->gf);
+    if (R->sub) init_level(R->sub, pf);
     free(pf);
-    snapshot(R, gcs, R->Uprev);
-    if (R->dir != 2) c2f(R, R->gf, R->Uprev, R->Uprev, 1.0);
-    if (R->dir != 1) f2c(R, gcs, R->gf);
 }
 
 /* g = g^eq(p0 / c_s^2, 0) on every grid (p0 interpolated bilinearly to the fine
@@ -345,7 +359,8 @@ static void init_level(ref_t *R, const double *pc, double *gcs) {
 int orc_ref_init_pressure(void *h, const double *p0) {
     ref_t *R = (ref_t *)h;
     orc_init_pressure(&R->C, p0, R->gc);
-    init_level(R, p0, R->gc);
+    init_level(R, p0);
+    start_level(R, R->gc, 1);
     R->t = 0;
     return 0;
 }
@@ -489,5 +504,89 @@ int orc_ref_level_cmap(void *h, int level, float *c) {
     const ref_t *R = level_of((const ref_t *)h, level);
     if (!R || level < 1) return -1;
     memcpy(c, R->cf, sizeof(float) * R->nxf * R->nyf);
+    return 0;
+}
+
+/* ---- Access to the individual transfer functions, for the tests that pin them ---- */
+
+/* the state array of level `level` (0: the coarse grid, l >= 1: the fine grid of patch l) and
+ * its node counts */
+static double *level_state(ref_t *R, int level, int *nx, int *ny) {
+    if (level == 0) {
+        *nx = R->C.nx;
+        *ny = R->C.ny;
+        return R->gc;
+    }
+    ref_t *L = (ref_t *)level_of(R, level);
+    if (!L) return NULL;
+    *nx = L->nxf;
+    *ny = L->nyf;
+    return L->gf;
+}
+
+/* Copy a state [Q][ny][nx] into (set != 0) or out of level `level` (0: coarse). */
+int orc_ref_level_state(void *h, int level, int set, double *g) {
+    ref_t *R = (ref_t *)h;
+    int nx = 0, ny = 0;
+    double *st = level < 0 ? NULL : level_state(R, level, &nx, &ny);
+    if (!st || !g) return -1;
+    const size_t n = sizeof(double) * (size_t)R->C.Q * nx * ny;
+    if (set)
+        memcpy(st, g, n);
+    else
+        memcpy(g, st, n);
+    return 0;
+}
+
+/* Start a run (time 0) from the states set with orc_ref_level_state: the snapshots U(0) and,
+ * when couple != 0, the coupling at time 0, exactly as orc_ref_init_pressure does. */
+int orc_ref_start(void *h, int couple) {
+    ref_t *R = (ref_t *)h;
+    start_level(R, R->gc, couple);
+    R->t = 0;
+    return 0;
+}
+
+/* The transfer of one vector g[Q] into node (ax, ay) of the receiving grid of the pair
+ * coupling level `level` to the level above it: the fine grid of patch `level` when
+ * to_fine, else the grid above (its node coordinates). */
+int orc_ref_transfer(void *h, int level, int to_fine, int ax, int ay, const double *g,
+                     double *out) {
+    const ref_t *R = level_of((const ref_t *)h, level);
+    if (!R || level < 1) return -1;
+    const orc_problem *P = to_fine ? &R->F : &R->C;
+    if (ax < 0 || ax >= P->nx || ay < 0 || ay >= P->ny) return -1;
+    transfer(R, to_fine, (size_t)ay * P->nx + ax, g, out);
+    return 0;
+}
+
+/* The interface nodes I of patch `level` in the coordinates of the grid above, in the
+ * order of the rows of the snapshots U; returns their number (Ix, Iy may be NULL). */
+int orc_ref_interface(void *h, int level, int *Ix, int *Iy) {
+    const ref_t *R = level_of((const ref_t *)h, level);
+    if (!R || level < 1) return -1;
+    for (int k = 0; k < R->nI; k++) {
+        if (Ix) Ix[k] = R->Ix[k];
+        if (Iy) Iy[k] = R->Iy[k];
+    }
+    return R->nI;
+}
+
+/* One coarse -> fine transfer into the fine grid of patch `level` from snapshots
+ * Ua, Ub [nI][Q] at weight alpha (the values (1 - alpha) Ua + alpha Ub), as the run applies
+ * it; or one fine -> coarse correction of the grid above from that fine grid. */
+int orc_ref_apply_c2f(void *h, int level, const double *Ua, const double *Ub, double alpha) {
+    ref_t *R = (ref_t *)level_of((const ref_t *)h, level);
+    if (!R || level < 1 || !Ua || !Ub) return -1;
+    c2f(R, R->gf, Ua, Ub, alpha);
+    return 0;
+}
+
+int orc_ref_apply_f2c(void *h, int level) {
+    ref_t *top = (ref_t *)h;
+    ref_t *R = (ref_t *)level_of(top, level);
+    if (!R || level < 1) return -1;
+    int nx, ny;
+    f2c(R, level_state(top, level - 1, &nx, &ny), R->gf);
     return 0;
 }
