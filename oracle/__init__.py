@@ -83,6 +83,8 @@ def _declare(L):
     L.orc_init_pressure.argtypes = [_pp, _dp, _dp]
     L.orc_pressure.argtypes = [_pp, _dp, _dp]
     L.orc_run.argtypes = [_pp, _dp, ctypes.c_int, ctypes.c_int, _dp]
+    L.orc_run_f32_stored.argtypes = [_pp, _dp, ctypes.c_int, ctypes.c_int, _dp]
+    L.orc_run_f32_stored.restype = ctypes.c_int
     L.orc_max_threads.argtypes = []
     for name in ("orc_velocities", "orc_moment_matrix", "orc_moment_inverse", "orc_weights",
                  "orc_collide", "orc_init_pressure", "orc_pressure", "orc_run",
@@ -383,6 +385,18 @@ def run(P: Problem, g: np.ndarray, nsteps: int, t0: int = 0):
     S = P._struct()
     rc = lib().orc_run(ctypes.byref(S), _ptr(g, ctypes.c_double), int(t0), int(nsteps),
                        _ptr(trace, ctypes.c_double))
+    assert rc == 0, rc
+    return g, trace
+
+
+def run_f32_stored(P: Problem, g: np.ndarray, nsteps: int, t0: int = 0):
+    """run() with the state rounded to FP32 after every step (FP64 arithmetic): what storing
+    the populations in FP32 alone does to the result."""
+    g = np.ascontiguousarray(g, dtype=np.float64).copy()
+    trace = np.zeros((nsteps, len(P.receivers)))
+    S = P._struct()
+    rc = lib().orc_run_f32_stored(ctypes.byref(S), _ptr(g, ctypes.c_double), int(t0),
+                                  int(nsteps), _ptr(trace, ctypes.c_double))
     assert rc == 0, rc
     return g, trace
 

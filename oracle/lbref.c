@@ -308,6 +308,30 @@ int orc_run(const orc_problem *P, double *g, int t0, int nsteps, double *trace) 
     return 0;
 }
 
+/* orc_run with the stored state rounded to FP32 (round to nearest even) after every step:
+ * the arithmetic stays FP64, so the result differs from orc_run's by what storing the
+ * populations in FP32 alone costs -- the floor below which no FP32-storage implementation
+ * of the scheme can agree with orc_run after nsteps steps. */
+int orc_run_f32_stored(const orc_problem *P, double *g, int t0, int nsteps, double *trace) {
+    double Minv[81];
+    if (P->Q != 5 && P->Q != 9) return -1;
+    if (orc_moment_inverse(P->Q, Minv)) return -2;
+#ifdef _OPENMP
+    if (P->nthreads > 0) omp_set_num_threads(P->nthreads);
+#endif
+    const size_t len = (size_t)P->Q * P->nx * P->ny;
+    double *gn = (double *)malloc(sizeof(double) * len);
+    if (!gn) return -3;
+    for (size_t i = 0; i < len; i++) g[i] = (double)(float)g[i];
+    for (int k = 0; k < nsteps; k++) {
+        if (trace && P->nrec > 0) record(P, g, trace + (size_t)k * P->nrec);
+        step(P, Minv, t0 + k, g, gn);
+        for (size_t i = 0; i < len; i++) g[i] = (double)(float)gn[i];
+    }
+    free(gn);
+    return 0;
+}
+
 int orc_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -44,6 +44,8 @@ double orc_sponge_sigma(int x, int y, int nx, int ny, int W, double smax);
 int orc_init_pressure(const orc_problem *P, const double *p0, double *g);
 int orc_pressure(const orc_problem *P, const double *g, double *p);
 int orc_run(const orc_problem *P, double *g, int t0, int nsteps, double *trace);
+/* orc_run with the state rounded to FP32 after every step (FP32-storage floor) */
+int orc_run_f32_stored(const orc_problem *P, double *g, int t0, int nsteps, double *trace);
 int orc_max_threads(void);
 
 /* building blocks shared by the oracle's own files (refinement, adjoint) */

@@ -180,6 +180,21 @@ def refined_nested_workload(n=2048, nrec=256, steps=4000):
     return wl
 
 
+def layered_workload(n=8192, nrec=512, steps=10000, seed=DEFAULT_SEED + 4, storage="f32"):
+    """The 8192^2 layered workload (scaled to n^2 when n differs): a 20-layer model with
+    dipping interfaces and 4 normal faults (speeds 1500-5500 m/s, throws 20-200 cells at
+    8192 scaled with the grid side), c_ref = 5500 m/s, 10 points per wavelength at
+    1500 m/s, Ricker source at (n/2, 80), ``nrec`` receivers on the source row between the
+    40-cell sponges, D2Q5 BGK tau = 1/2, ``steps`` steps."""
+    f = n / 8192.0
+    c = layered_fault_model(n, n, seed, n_layers=20, throw=(20.0 * f, 200.0 * f))
+    y = 80
+    return dict(nx=n, ny=n, c_map=c, c_ref=SERVED_C_REF, source=(n // 2, y, ricker(steps, SERVED_FC)),
+                receivers=line_receivers(nrec, y, 40, n - 80), steps=steps, lattice=5,
+                collision="bgk", tau=0.5, sponge_width=40, sponge_sigma_max=0.1, periodic=False,
+                storage=storage, w_ref=(4 / 9, 1 / 9, 1 / 36))
+
+
 # --- served shot stream ---------------------------------------------------------------
 
 SERVED_SIZES = (256, 512, 1024, 2048)

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from paper_1704_03172_gb300 import workloads as W
+from tests.traces import check_every_trace
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -71,6 +72,7 @@ def test_refined_matches_oracle(sim_cls, oracle_mod, Q, coll, tau, s, periodic, 
     tr = sim.traces().cpu().numpy()
     sim.close()
     assert rel(tr, np.concatenate(traces)) < TOL
+    check_every_trace(tr, np.concatenate(traces), TOL)
 
 
 def test_refined_block_workload_reduced_full_length(sim_cls, oracle_mod):
@@ -99,6 +101,7 @@ def test_refined_block_workload_reduced_full_length(sim_cls, oracle_mod):
     assert rel(ps, R.pressure()) < TOL
     t2 = R.run(steps - snap)
     assert rel(tr, np.concatenate([t1, t2])) < TOL
+    check_every_trace(tr, np.concatenate([t1, t2]), TOL)
 
 
 def test_refined_block_workload_full_size_truncated(sim_cls, oracle_mod):
@@ -126,6 +129,7 @@ def test_refined_block_workload_full_size_truncated(sim_cls, oracle_mod):
     tro = R.run(steps)
     assert rel(ps, R.pressure()) < TOL
     assert rel(tr, tro) < TOL
+    check_every_trace(tr, tro, TOL)
 
 
 def test_source_inside_patch_is_rejected(sim_cls):
@@ -187,6 +191,7 @@ def test_nested_refined_matches_oracle(sim_cls, oracle_mod, Q, coll, tau, s, per
     sim.close()
     ref = np.concatenate(traces)
     assert rel(tr, ref) < TOL
+    check_every_trace(tr, ref, TOL)
     for j in range(len(rec)):                    # every receiver, each from its own level
         assert np.linalg.norm(tr[:, j] - ref[:, j]) <= 1e-4 * np.linalg.norm(ref[:, j]) + 1e-9
 
@@ -231,6 +236,7 @@ def test_nested_block_workload_reduced_full_length(sim_cls, oracle_mod):
     assert rel(ps, R.pressure()) < TOL
     t2 = R.run(steps - snap)
     assert rel(tr, np.concatenate([t1, t2])) < TOL
+    check_every_trace(tr, np.concatenate([t1, t2]), TOL)
 
 
 def test_footprint_covers_refined_levels(sim_cls):
@@ -309,6 +315,7 @@ def test_one_way_coupling_matches_oracle(sim_cls, oracle_mod, Q, coll, tau, s, p
     tr = sim.traces().cpu().numpy()
     sim.close()
     assert rel(tr, np.concatenate(traces)) < TOL
+    check_every_trace(tr, np.concatenate(traces), TOL)
 
 
 @pytest.mark.parametrize("modes", [("c2f", "f2c"), ("f2c", "both"), ("both", "c2f")])
@@ -341,6 +348,7 @@ def test_nested_one_way_coupling_matches_oracle(sim_cls, oracle_mod, modes):
     tr = sim.traces().cpu().numpy()
     sim.close()
     assert rel(tr, np.concatenate(traces)) < TOL
+    check_every_trace(tr, np.concatenate(traces), TOL)
 
 
 def test_coupling_mode_is_checked(sim_cls):

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from paper_1704_03172_gb300 import workloads as W
+from tests.traces import check_every_trace
 
 pytestmark = pytest.mark.gpu
 
@@ -86,6 +87,7 @@ def test_step_matches_oracle_small(sim_cls, oracle_mod, Q, coll, tau, periodic, 
     assert rel(gs, go) < TOL
     assert np.abs(gs - go).max() < 10 * TOL * np.abs(go).max()
     assert rel(tr, tro) < TOL
+    check_every_trace(tr, tro, TOL)
     assert rel(ps, oracle_mod.pressure(P, go)) < TOL
 
 
@@ -116,6 +118,7 @@ def test_gaussian_pulse_128_periodic_500_steps(sim_cls, oracle_mod, tau):
     g, tro = oracle_mod.run(P, g, steps)
     assert rel(ps, oracle_mod.pressure(P, g)) < TOL
     assert rel(tr, tro) < TOL
+    check_every_trace(tr, tro, TOL)
 
 
 @pytest.mark.parametrize("Q,coll", [(5, "bgk"), (5, "mrt"), (9, "bgk"), (9, "mrt")])
@@ -139,6 +142,7 @@ def test_two_layer_full_length_reduced_grid(sim_cls, oracle_mod, Q, coll):
     assert rel(ps, oracle_mod.pressure(P, g)) < TOL
     _, tro2 = oracle_mod.run(P, g, steps - snap, t0=snap)
     assert rel(tr, np.concatenate([tro1, tro2])) < TOL
+    check_every_trace(tr, np.concatenate([tro1, tro2]), TOL)
 
 
 @pytest.mark.parametrize("Q,coll,steps", [(5, "bgk", 30), (9, "mrt", 12)])
@@ -162,6 +166,7 @@ def test_two_layer_4096_bench_configuration(sim_cls, oracle_mod, Q, coll, steps)
     go, tro = oracle_mod.run(P, g0.astype(np.float64), steps)
     assert rel(gs, go) < TOL
     assert rel(tr, tro) < TOL
+    check_every_trace(tr, tro, TOL)
 
 
 @pytest.mark.parametrize("Q,storage,periodic,n", [(5, "f32", False, 200), (5, "bf16", False, 333),

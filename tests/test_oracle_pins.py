@@ -409,3 +409,33 @@ def test_seeded_mrt_rates_of_the_two_layer_workload_are_stable(Q):
                                          mrt=True, s=s)
                 worst = max(worst, np.abs(np.linalg.eigvals(T)).max())
     assert worst <= 1 + 1e-12
+
+
+def test_oracle_window_equals_the_full_grid_run(oracle_mod):
+    # The parity test at 8192^2 runs the oracle on the window that a zero initial state can
+    # fill in T steps from the source (one cell per step in L1 distance for D2Q5) plus the
+    # sponge band of the window's own edges.  On a small grid the window run must equal the
+    # full run exactly -- traces of every receiver, the field inside the window, and exact
+    # zeros outside it -- heterogeneous medium, 12-cell sponge at the real edges.
+    from tests.test_gpu_fulllength import diamond_window
+    n, steps, W_s = 200, 60, 12
+    c = W.layered_fault_model(n, n, 7, n_layers=9, throw=(2.0, 20.0))
+    src = (100, 20, W.ricker(steps, 0.03))
+    rec = W.line_receivers(40, 20, 12, n - 24)
+    P = oracle_mod.Problem(5, n, n, c, c_ref=5500.0, tau=0.5, sponge_width=W_s,
+                           sponge_sigma_max=0.1, source=src, receivers=rec)
+    g, tr = oracle_mod.run(P, P.zeros(), steps)
+    x0, x1, y0, y1 = diamond_window(src[:2], steps, W_s, n)
+    assert (x0, y0) != (0, 0) and x1 < n and y1 < n                  # a true sub-window
+    inw = (rec[:, 0] >= x0) & (rec[:, 0] < x1)
+    Pw = oracle_mod.Problem(5, x1 - x0, y1 - y0, c[y0:y1, x0:x1], c_ref=5500.0, tau=0.5,
+                            sponge_width=W_s, sponge_sigma_max=0.1,
+                            source=(src[0] - x0, src[1] - y0, src[2]),
+                            receivers=rec[inw] - np.array([x0, y0], np.int32))
+    gw, trw = oracle_mod.run(Pw, Pw.zeros(), steps)
+    np.testing.assert_array_equal(trw, tr[:, inw])
+    assert not tr[:, ~inw].any()
+    np.testing.assert_array_equal(gw, g[:, y0:y1, x0:x1])
+    out = np.ones(g.shape[1:], bool)
+    out[y0:y1, x0:x1] = False
+    assert not g[:, out].any()
