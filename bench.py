@@ -195,6 +195,39 @@ def _variant(torch, LBSim, lattice, storage, collision, steps, warmup, time_bloc
             "achieved_gbs": round(glups * bps, 1), "ms_per_step": round(sec / steps * 1e3, 4)}
 
 
+_LAYERED = {}
+
+
+def _layered(n):
+    """The layered workload (20 layers, faults, 1500-5500 m/s) at n^2, generated once."""
+    if n not in _LAYERED:
+        _LAYERED[n] = W.layered_workload(n)
+    return _LAYERED[n]
+
+
+def _layered_variant(torch, LBSim, storage, steps, warmup, n=8192):
+    """The 8192^2 layered workload: D2Q5 BGK tau = 1/2, 40-cell sponge, Ricker source at
+    (4096, 80), 512 receivers on the source row; GLUPS and the algorithmic HBM rate."""
+    wl = dict(_layered(n))
+    wl["storage"] = storage
+    sim = LBSim(wl["c_map"], lattice=5, tau=0.5, storage=storage, c_ref=wl["c_ref"],
+                sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"])
+    try:
+        sim.set_source(*wl["source"])
+        sim.set_receivers(wl["receivers"], steps + warmup)
+        sim.init_pressure(None)
+        indexed = _indexed(sim)
+        sec = _time_steps(torch, sim, steps, warmup)
+    finally:
+        sim.close()
+    glups = n * n * steps / sec / 1e9
+    bps = bytes_per_site(5, storage, indexed)
+    return {"glups": round(glups, 2), "bytes_per_site": bps, "achieved_gbs": round(glups * bps, 1),
+            "frac_of_measured_hbm": round(glups * bps / _peaks()[0], 4),
+            "ms_per_step": round(sec / steps * 1e3, 4), "grid": f"{n}^2", "steps": steps,
+            "state_gb": round(2 * 5 * n * n * ELEM_BYTES[storage] / 1e9, 2)}
+
+
 def _refined_variant(torch, LBSim, steps, warmup):
     """Slow-block workload: 2048^2 coarse grid + 1025^2-node fine patch (2x in space and
     time).  One fine site-step counts as one update: 2048^2 + 2 * 1025^2 per coarse step."""
@@ -261,16 +294,19 @@ def _nested_variant(torch, LBSim, steps, warmup):
 
 def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32", mode="ckpt"):
     """Gradient of J = 1/2 sum p^2 over 512 receiver traces w.r.t. the sound-speed map and
-    the source, for a 20-layer faulted model: forward run with checkpoints, then lb_adjoint
-    (replay + reverse sweep); mode "tape": the forward run records rho (n^2 nt 4 bytes) and
-    lb_adjoint is the reverse sweep alone.  Rates count n^2 * nt site-steps of the gradient
-    call."""
-    c = W.layered_fault_model(n, n, W.DEFAULT_SEED + 4, n_layers=20,
-                              throw=(20.0 * n / 8192, 200.0 * n / 8192))
-    sim = LBSim(c, lattice=5, tau=0.5, c_ref=W.SERVED_C_REF, sponge_width=40, storage=storage)
+    the source, for the 20-layer faulted model (the layered workload at n^2): forward run
+    with checkpoints, then lb_adjoint (replay + reverse sweep); mode "tape": the forward run
+    records rho (n^2 nt 4 bytes) and lb_adjoint is the reverse sweep alone.  Rates count
+    n^2 * nt site-steps of the gradient call; peak device memory of the whole shot."""
+    wl = _layered(n)
+    sim = LBSim(wl["c_map"], lattice=5, tau=0.5, c_ref=wl["c_ref"], sponge_width=40,
+                storage=storage)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    mem0 = torch.cuda.memory_allocated()
     try:
-        sim.set_source(n // 2, 48, W.ricker(nt, W.SERVED_FC))
-        sim.set_receivers(W.line_receivers(512, 48, 40, n - 80), nt)
+        sim.set_source(wl["source"][0], wl["source"][1], W.ricker(nt, W.SERVED_FC))
+        sim.set_receivers(wl["receivers"], nt)
         sim.init_pressure(None)
         if mode == "tape":
             sim.record_rho(nt)
@@ -289,6 +325,7 @@ def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32", mo
         t_adj = time.perf_counter() - t0
         finite = bool(torch.isfinite(gc).all().item())
         indexed = _indexed(sim)
+        peak_gb = (torch.cuda.max_memory_allocated() - mem0) / 1e9
     finally:
         sim.close()
     T = min(every, (16 << 30) // (n * n * 4))
@@ -309,12 +346,14 @@ def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32", mo
                round(upd / t_fwd / 1e9, 2),
            "bytes_per_site_step": bps, "achieved_gbs": round(upd * bps / t_adj / 1e9, 1),
            "seconds": round(t_adj, 4), "finite": finite,
+           "peak_device_gb": round(peak_gb, 2),
            "workload": f"{n}x{n} 20-layer faulted model, D2Q5 BGK {storage.upper()}, {nt} steps, "
                        + (f"forward rho tape ({n * n * nt * 4 / 1e9:.0f} GB), no replay"
                           if mode == "tape" else f"checkpoint every {every}")
                        + ", 512 receivers, wall time of lb_adjoint"}
     if mode != "tape":
         out["replay_levels"] = levels
+        out["checkpoint_every"] = every
     return out
 
 
@@ -586,6 +625,60 @@ def run_reference(args):
     return 0
 
 
+def run_slabs(args, torch, LBSim, ws, rank, local):
+    """One shot of the 8192^2 layered workload split into ws row slabs, one per rank, the
+    cut rows exchanged after every step (torch.distributed point-to-point, NCCL): strong
+    scaling.  value = the grid's site updates over the slowest rank's timed seconds."""
+    from paper_1704_03172_gb300 import slabs
+    import torch.distributed as dist
+    wl = _layered(8192)
+    n = wl["nx"]
+    slab = slabs.DistSlab(wl["c_map"], rank, ws, lattice=5, tau=0.5, c_ref=wl["c_ref"],
+                          sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"])
+    slab.set_source(*wl["source"])
+    slab.set_receivers(wl["receivers"], args.steps + args.warmup)
+    slab.init_pressure(None)
+    slab.step(args.warmup)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        e0.record(slab.sim.stream)
+        slab.step(args.steps)
+        e1.record(slab.sim.stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    rows = slab.y1 - slab.y0
+    rate, sec = job_rate(e0.elapsed_time(e1) / 1e3, rows * n * args.steps, ws)
+    tr = slab.traces(args.steps + args.warmup)
+    slab.close()
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+    line = {"metric": METRIC, "value": round(rate / 1e9, 3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sec / args.steps * 1e3, 4), "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "layered 8192x8192 (20 layers, faults, 1500-5500 m/s), D2Q5 "
+                                   "BGK tau=1/2, FP32, 40-cell sponge, Ricker source, 512 "
+                                   "receivers; one shot split into row slabs",
+                       "parallelism": f"{ws} row slabs, cut rows exchanged every step",
+                       "l2": "inputs larger than L2 (population buffers >= 168 MB per slab "
+                             "up to 8 slabs)"},
+            "gpu_launches": args.steps, "clocks": clk.summary(),
+            "finite": bool(np.isfinite(tr).all())}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -597,6 +690,8 @@ def run_ours(args):
     build.build()
     from paper_1704_03172_gb300.sim import LBSim
 
+    if args.decompose == "slabs":
+        return run_slabs(args, torch, LBSim, ws, rank, local)
     if args.variant:  # one variant alone (profiling runs)
         name = args.variant
         if name.startswith("adjoint_"):  # adjoint_f32, adjoint_bf16, adjoint_tape_f32, ...
@@ -616,6 +711,8 @@ def run_ours(args):
                               time_block=8 if "tb8" in parts else 1)
         elif name.startswith("d3q7"):
             out = _d3q7_variant(torch, LBSim, name.rsplit("_", 1)[1])
+        elif name.startswith("layered_8192"):  # layered_8192_<storage>
+            out = _layered_variant(torch, LBSim, name.rsplit("_", 1)[1], args.steps, args.warmup)
         elif name == "served":
             out = _served(args.served_requests, args.served_calibration)
         else:
@@ -740,6 +837,17 @@ def run_ours(args):
                 v[f"adjoint_4096_d2q5_{st}"] = _adjoint_variant(torch, LBSim, storage=st)
             except Exception as ex:
                 v[f"adjoint_4096_d2q5_{st}"] = {"error": str(ex)[:200]}
+        for st in ("f32", "bf16", "f16"):
+            name = f"layered_8192_d2q5_bgk_{st}"
+            try:
+                v[name] = _layered_variant(torch, LBSim, st, max(200, args.steps // 5), 10)
+            except Exception as ex:
+                v[name] = {"error": str(ex)[:200]}
+        try:
+            v["adjoint_8192_d2q5_f32"] = _adjoint_variant(torch, LBSim, n=8192, nt=1000,
+                                                           every=200, storage="f32")
+        except Exception as ex:
+            v["adjoint_8192_d2q5_f32"] = {"error": str(ex)[:200]}
         for st in ("f32", "bf16"):
             try:
                 v[f"d3q7_bgk_{st}_256"] = _d3q7_variant(torch, LBSim, st)
@@ -793,6 +901,9 @@ def main():
     ap.add_argument("--step-kernel", choices=["auto", "direct", "staged"], default="auto",
                     help="auto (TMA-staged for wide 16-bit rows), direct (register-streaming) "
                          "or staged (TMA-staged persistent)")
+    ap.add_argument("--decompose", choices=["replicas", "slabs"], default="replicas",
+                    help="N > 1: independent shots, one per rank (weak scaling), or one 8192^2 "
+                         "shot split into row slabs with a cut-row exchange (strong scaling)")
     ap.add_argument("--time-block", type=int, default=1,
                     help="steps fused per launch for the main line (temporal blocking)")
     args = ap.parse_args()

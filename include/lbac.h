@@ -103,7 +103,9 @@ typedef struct {
     void *cuda_stream;        /* cudaStream_t to run on; NULL: the context creates its own
                                  non-blocking stream (pass cudaStreamLegacy for the legacy
                                  default stream, whose handle is NULL) */
-    int time_block;           /* steps fused per launch (temporal blocking); <= 1: one */
+    int time_block;           /* steps fused per launch (temporal blocking); <= 1: one.
+                                 D2Q5: 2, 4, 6, 8 or 16 with FP32 or BF16 storage (the fused
+                                 levels in between are FP32); D2Q9: 2 or 4 with FP32 storage */
     /* Optional device allocator (e.g. PyTorch's caching allocator).  NULL: cudaMalloc. */
     void *(*dev_alloc)(size_t bytes, void *user);
     void (*dev_free)(void *ptr, void *user);
@@ -127,8 +129,8 @@ lb_status lb_config_default(lb_config *cfg);
 /* Validate cfg, allocate the device state and build the per-site medium
  * (eta^2 = (c / c_ref)^2, from which every weight and c_s^2 follow).
  * Errors: LB_EINVAL (bad sizes, tau < 1/2, s outside (0, 2], eta > 1,
- * c <= 0, negative weights, bad patch), LB_ENOMEM, LB_ECUDA.  *out is NULL on
- * failure. */
+ * c <= 0, negative weights, bad patch, a linearly unstable scheme -- see
+ * lb_stability_radius), LB_ENOMEM, LB_ECUDA.  *out is NULL on failure. */
 lb_status lb_create(const lb_config *cfg, lb_ctx **out);
 lb_status lb_destroy(lb_ctx *ctx);
 
@@ -154,8 +156,33 @@ lb_status lb_set_receivers(lb_ctx *ctx, const int *xy, int nrec, int nt_capacity
  * every population to 0.  Resets the time to 0.  p0: [ny][nx] FP32. */
 lb_status lb_init_pressure(lb_ctx *ctx, const float *p0, int on_device);
 
-/* Advance n >= 0 steps (asynchronous). */
+/* Advance n >= 0 steps (asynchronous, unless lb_watch_stability is on). */
 lb_status lb_step(lb_ctx *ctx, int n);
+
+/* Linear (von Neumann) stability of a configuration's scheme, Sec. 3: the largest modulus
+ * of the eigenvalues of the one-step map T(k) = D(k) (I - C A) of a homogeneous medium
+ * (Eq. MRT-LB dispersion; A from Eq. linear eqm dist, C = I / tau or M^-1 S M, D(k) =
+ * diag(exp(-i k.c_i))) over the nk x nk wave vectors k = 2 pi (m, n) / nk, at eta =
+ * c / c_ref (0 < eta <= 1), with the rates of refinement level `level` (0: the coarse grid;
+ * level l relaxes with tau_l - 1/2 = 2^l (tau - 1/2), reading R6).  Uses cfg's lattice
+ * (D2Q5 / D2Q9), collision, tau, s and w_ref only.  Host computation, no CUDA call;
+ * results are cached per configuration.  Sec. 2.3 ties the stability of D2Q9 to its
+ * rates and weights.  lb_create runs the same computation with nk = 64 for D2Q9 and for
+ * MRT at the medium's eta values (its distinct values when there are at most 8, else 8
+ * values spread over its range) and every refinement level, and refuses the configuration
+ * with LB_EINVAL when the radius exceeds 1 + 1e-12.  Errors: LB_EINVAL for an invalid
+ * argument or an iteration that did not converge. */
+lb_status lb_stability_radius(const lb_config *cfg, double eta, int level, int nk,
+                              double *radius);
+
+/* Detect instability while stepping: with every > 0, lb_step stops after each multiple of
+ * `every` steps since this call, reads the FP64 invariants of the state (lb_invariants; the
+ * stream is synchronised) and returns LB_EUNSTABLE when a value is non-finite or, for
+ * max_growth > 0, when the energy sum_x sum_i g_i^2 / w_i grew by more than the factor
+ * max_growth since the previous check (a source adds energy: choose the bound above what
+ * it injects in `every` steps).  The steps before the failing check have been taken.
+ * every = 0 turns the watch off.  LB_ESTATE for 3-D and LB_F64 contexts. */
+lb_status lb_watch_stability(lb_ctx *ctx, int every, double max_growth);
 
 /* Copy trace rows [0, min(recorded, nt_max)) to out ([rows][nrec], FP32) and
  * report the row count in *nt_out.  Synchronises the stream. */
@@ -321,7 +348,9 @@ lb_status lb_invariants(lb_ctx *ctx, double *out);
  *   out     device, 4 doubles: mass, energy, max |g|, non-finite count
  *   cuda_stream  cudaStream_t to queue on (NULL: the legacy default stream)
  * The work is queued asynchronously; nothing is copied to the host.  Zero-ghost
- * (non-periodic) state only.
+ * (non-periodic) state only.  If an earlier CUDA call left an error pending on the
+ * calling thread, nothing is queued and LB_ECUDA is returned with a message saying
+ * so; that error is left pending for its owner.
  * Scratch: a file-scope static device array of 16384 x 4 + 4 doubles
  * (512 KiB), held by every GPU that loads the library until the process exits.
  * ny > 16384 (or nx * ny > 2^31) is rejected with LB_EINVAL and a message in
@@ -335,6 +364,41 @@ lb_status lb_invariants(lb_ctx *ctx, double *out);
 lb_status lb_invariants_noalloc(const float *g, const float *c_map, int lattice, int nx,
                                 int ny, double c_ref, const double *w_ref, double *out,
                                 void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Row-slab domain decomposition of one shot (the method is local: a step reads only the
+ * nearest neighbours, so a grid split into row slabs needs, per step and per cut, only
+ * the populations that cross the cut -- D2Q5: g2 up and g4 down; D2Q9: g2, g5, g6 up and
+ * g4, g7, g8 down).  Each slab is an ordinary context created for its own rows (its c_map
+ * rows, source and receivers in local coordinates) and then marked with lb_set_slab.
+ * Its steps pull across a cut from halo rows that the caller keeps filled with the
+ * neighbour's cut rows, and write their own cut rows into send buffers in the same
+ * launch.  lb_slab_step does the steps and the copies for slabs held by one process (on
+ * one or several devices: a copy goes into the receiving slab's own memory); across
+ * processes the caller moves the send buffers into the neighbours' halo buffers itself
+ * (e.g. NCCL send / recv) between steps.  The sponge is measured in the whole grid, so a
+ * decomposed run performs exactly the per-site arithmetic of the whole grid. */
+
+/* Mark ctx as the rows [y_offset, y_offset + ny) of a grid of ny_global rows.  The four
+ * buffers are caller-owned device memory of lb_slab_halo_bytes bytes each, 16-byte
+ * aligned, on the context's device: send_lo / send_hi receive, from every step, the
+ * crossing populations of the slab's first / last output row (stored type, [slot][pitch]);
+ * recv_lo / recv_hi must hold the same rows of the slab below / above before each step
+ * (NULL: no neighbour on that side -- the zero ghost, or the periodic wrap within the
+ * slab).  2-D, FP32 or BF16 storage, no patch, no time blocking (LB_ESTATE); a slab has
+ * no adjoint, checkpoints, rho tape or invariants.  The first step after lb_set_state /
+ * lb_init_pressure reads the state in place and needs no halo rows; lb_get_pressure and
+ * lb_get_state read the halo rows at the cuts. */
+lb_status lb_set_slab(lb_ctx *ctx, int y_offset, int ny_global, void *send_lo, void *send_hi,
+                      const void *recv_lo, const void *recv_hi);
+/* Size of one slab row buffer of ctx: crossing populations x row pitch x stored bytes. */
+lb_status lb_slab_halo_bytes(const lb_ctx *ctx, size_t *bytes);
+/* Advance n slabs that tile one grid (slabs[k] directly above slabs[k - 1]) by `steps`
+ * steps: every slab steps on its own stream, then each slab's halo rows are filled from
+ * its neighbours' send buffers (the last and the first slab are neighbours when the grid
+ * is periodic), ordered with events so that no step reads a halo row before its copy and
+ * no copy reads a send buffer that the next step overwrites.  Asynchronous. */
+lb_status lb_slab_step(lb_ctx **slabs, int n, int steps);
 
 /* Device bytes lb_create would allocate for cfg (refinement patches included),
  * plus the receiver trace for nt steps when nrec > 0, plus what lb_adjoint needs

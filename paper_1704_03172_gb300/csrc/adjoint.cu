@@ -601,6 +601,7 @@ float *tape_row(const lb_ctx *ctx, long long t) {
 
 extern "C" lb_status lb_record_rho(lb_ctx *ctx, int nt_capacity) {
     if (!ctx) return LB_EINVAL;
+    if (ctx->slab_nyg) return fail(ctx, LB_ESTATE, "a row slab has no adjoint");
     if (nt_capacity < 0) return fail(ctx, LB_EINVAL, "nt_capacity < 0");
     if (nt_capacity > 0 && (ctx->Q == 7 || ctx->refined || ctx->cfg.storage == LB_F64))
         return fail(ctx, LB_ESTATE, "the rho tape serves the 2-D adjoint without a patch "
@@ -621,6 +622,7 @@ extern "C" lb_status lb_record_rho(lb_ctx *ctx, int nt_capacity) {
 
 extern "C" lb_status lb_checkpoint_every(lb_ctx *ctx, int every) {
     if (!ctx) return LB_EINVAL;
+    if (ctx->slab_nyg) return fail(ctx, LB_ESTATE, "a row slab has no adjoint");
     if (every > 0 && ctx->Q == 7) return fail(ctx, LB_ESTATE, "the adjoint is 2-D (D2Q5 / D2Q9)");
     if (every < 0) return fail(ctx, LB_EINVAL, "every < 0");
     if (every > 0 && (ctx->refined || (ctx->cfg.storage != LB_F32 && ctx->cfg.storage != LB_BF16)))
@@ -633,6 +635,7 @@ extern "C" lb_status lb_checkpoint_every(lb_ctx *ctx, int every) {
 extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *grad_c,
                                 double *grad_src, float *grad_g0, int on_device) {
     if (!ctx) return LB_EINVAL;
+    if (ctx->slab_nyg) return fail(ctx, LB_ESTATE, "a row slab has no adjoint");
     if (ctx->cfg.storage == LB_F64) return fail(ctx, LB_ESTATE, "no adjoint for LB_F64 (test only)");
     if (nt < 1) return fail(ctx, LB_EINVAL, "nt < 1");
     if (ctx->nrec > 0 && !dJdp) return fail(ctx, LB_EINVAL, "dJdp is NULL");

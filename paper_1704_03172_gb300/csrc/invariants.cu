@@ -204,6 +204,14 @@ extern "C" lb_status lb_invariants_noalloc(const float *g, const float *c_map, i
         scratch = static_cast<double *>(p);
         g_noalloc_addr[dev].store(scratch, std::memory_order_release);
     }
+    // An error that an earlier call left pending on this thread would otherwise be read
+    // back after the launches below as if they had failed (and cleared for its owner):
+    // report it as such, queue nothing, and leave it pending.
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess)
+        return noalloc_fail(LB_ECUDA, std::string("an earlier CUDA call left an error pending "
+                                                  "on this thread (not cleared): ") +
+                                          cudaGetErrorString(e));
     lbinv::InvArgs a;
     memset(&a, 0, sizeof(a));
     a.pop = g;
@@ -237,6 +245,7 @@ extern "C" lb_status lb_invariants(lb_ctx *ctx, double *out) {
         return fail(ctx, LB_ESTATE, "invariants read FP32 / 16-bit storage, not LB_F64");
     if (!ctx) return LB_EINVAL;
     if (!out) return fail(ctx, LB_EINVAL, "out is NULL");
+    if (ctx->slab_nyg) return fail(ctx, LB_ESTATE, "invariants of a row slab (lb_set_slab)");
     if (!ctx->inv_scratch) {
         ctx->inv_scratch = static_cast<double *>(dev_alloc(ctx, ((size_t)ctx->ny * 4 + 4) * 8));
         if (!ctx->inv_scratch) return fail(ctx, LB_ENOMEM, "invariant scratch");

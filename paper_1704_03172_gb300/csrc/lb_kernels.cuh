@@ -137,7 +137,43 @@ struct StepArgs {
     const double *eta2_64;
     const double *src64;
     const double *coef64;
+    // Row slabs of one domain (domain decomposition; 2-D, FP32 / BF16 storage): this
+    // context's rows are rows y_off .. y_off + ny - 1 of a grid of ny_glob rows (0: not a
+    // slab), so the sponge measures distances in the whole grid.  halo_lo / halo_hi hold
+    // the stored populations of the row just below / above, written by the neighbouring
+    // slab's last step (the crossing populations only, [cross_slot][pitch]; nullptr: the
+    // zero ghost or the periodic wrap applies there).  send_lo / send_hi receive the same
+    // populations of this slab's first / last output row.
+    int y_off, ny_glob;
+    const void *halo_lo, *halo_hi;
+    void *send_lo, *send_hi;
 };
+
+// Slot of population i in a slab halo row: its rank among the populations that cross a
+// row cut in the same direction (D2Q5: g2 up, g4 down; D2Q9: g2, g5, g6 up and g4, g7, g8
+// down).
+template <int Q> __host__ __device__ constexpr int cross_slot(int i) {
+    int k = 0;
+    for (int j = 0; j < i; j++) k += Lat<Q>::cy(j) == Lat<Q>::cy(i);
+    return k;
+}
+template <int Q> __host__ __device__ constexpr int cross_count() {
+    int k = 0;
+    for (int j = 0; j < Q; j++) k += Lat<Q>::cy(j) == 1;
+    return k;
+}
+
+// The stored row population i pulls from for output row r of a 2-D slab when the pull
+// crosses into a neighbouring slab (nullptr otherwise: the caller's own rule applies).
+template <int Q, typename ST>
+__device__ __forceinline__ const ST *slab_halo_row(const StepArgs &a, int r, int i) {
+    if (Q == 7) return nullptr;
+    const int ys = r - Lat<Q>::cy(i);
+    if (ys < 0 && a.halo_lo) return static_cast<const ST *>(a.halo_lo) + cross_slot<Q>(i) * a.pitch;
+    if (ys >= a.ny && a.halo_hi)
+        return static_cast<const ST *>(a.halo_hi) + cross_slot<Q>(i) * a.pitch;
+    return nullptr;
+}
 
 // The per-site arithmetic (collision, weights, source, sponge) is written once for an
 // arithmetic type R: FP32 in every production kernel, FP64 in the test-only LB_F64 step,
@@ -592,7 +628,10 @@ __device__ __forceinline__ R sponge_of_dist(int d, const StepArgs &a) {
 // distance from row r to the nearest y face (D3Q7: y or z face)
 template <int Q>
 __device__ __forceinline__ int row_face_dist(int r, const StepArgs &a) {
-    if (Q != 7) return min(r, a.ny - 1 - r);
+    if (Q != 7) {  // slabs: the distance in the whole grid
+        const int yg = r + a.y_off, nyg = a.ny_glob > 0 ? a.ny_glob : a.ny;
+        return min(yg, nyg - 1 - yg);
+    }
     int y, z;
     row_yz<Q>(a, r, y, z);
     return min(min(y, a.ny3 - 1 - y), min(z, a.nz - 1 - z));
@@ -615,12 +654,13 @@ __device__ __forceinline__ void gather_receivers(const StepArgs &a, int r) {
     for (int i = 0; i < Q; i++) {
         int xs = xy.x - (a.raw ? 0 : Lat<Q>::cx(i));
         const int ys = a.raw ? xy.y : pull_row<Q, PERIODIC>(a, xy.y, i);  // xy.y: row
+        const ST *halo = a.raw ? nullptr : slab_halo_row<Q, ST>(a, xy.y, i);
         if (PERIODIC) {
             xs = (xs + a.nx) % a.nx;
-        } else if (xs < 0 || xs >= a.nx || ys < 0) {
+        } else if (xs < 0 || xs >= a.nx || (ys < 0 && !halo)) {
             continue;
         }
-        rho += Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch + xs) *
+        rho += Store<ST>::load1(halo ? halo + xs : in + i * a.plane + (long long)ys * a.pitch + xs) *
                scale_of(a.scale_in, i);
     }
     a.trace_row[a.rec_col ? a.rec_col[r] : r] =
@@ -683,7 +723,7 @@ __device__ __forceinline__ void collide_sites(R (&g)[Q][V], const R (&e2s)[V],
 // input scale, the adjoint replay's rho record, collision + source + sponge, and
 // the vector store of h(t) (FP16: scaled, with this thread's max |h_i| folded
 // into tmax).  Shared by the register-streaming and the TMA-staged kernels.
-template <int Q, bool MRT, typename ST>
+template <int Q, bool MRT, typename ST, bool SLAB = false>
 __device__ __forceinline__ void finish_sites(const StepArgs &a, float (&g)[Q][Store<ST>::V],
                                              const float (&e2s)[Store<ST>::V], int x0, int y,
                                              float tmax[Q]) {
@@ -744,11 +784,21 @@ __device__ __forceinline__ void finish_sites(const StepArgs &a, float (&g)[Q][St
         }
         Store<ST>::storeV(o + i * a.plane, g[i]);
     }
+    if (SLAB && Q != 7 && ((a.send_lo && y == 0) || (a.send_hi && y == a.ny - 1))) {
+        // slab cut rows: the populations the neighbouring slab pulls across the cut
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            if (Lat<Q>::cy(i) == -1 && a.send_lo && y == 0)
+                Store<ST>::storeV(static_cast<ST *>(a.send_lo) + cross_slot<Q>(i) * a.pitch + x0, g[i]);
+            if (Lat<Q>::cy(i) == 1 && a.send_hi && y == a.ny - 1)
+                Store<ST>::storeV(static_cast<ST *>(a.send_hi) + cross_slot<Q>(i) * a.pitch + x0, g[i]);
+        }
+    }
 }
 
 // The sites of one warp row-segment of block `blk`; tmax receives this
-// thread's max |out_i|.
-template <int Q, bool MRT, bool PERIODIC, typename ST>
+// thread's max |out_i|.  SLAB: the context is a row slab (halo rows at the cuts).
+template <int Q, bool MRT, bool PERIODIC, typename ST, bool SLAB = false>
 __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tmax[Q],
                                            const float *tab) {
 #pragma unroll
@@ -773,6 +823,10 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
         const int cx = a.raw ? 0 : Lat<Q>::cx(i);  // raw: read g(t) in place (warp-uniform)
         const int rs = a.raw ? y : pull_row_yz<Q, PERIODIC>(a, y, y3, z3, i);
         const ST *row = rs < 0 ? nullptr : in + i * a.plane + (long long)rs * a.pitch;
+        if (SLAB && !a.raw) {  // a pull across a slab cut reads the neighbour's row
+            const ST *halo = slab_halo_row<Q, ST>(a, y, i);
+            if (halo) row = halo;
+        }
         absent[i] = row == nullptr;
         if (cx == 1)
             pull_issue<1, PERIODIC>(row, x0, lane, a.nx, active, q[i], e[i]);
@@ -814,10 +868,10 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
             e2s[k] = e.x; e2s[k + 1] = e.y; e2s[k + 2] = e.z; e2s[k + 3] = e.w;
         }
     }
-    finish_sites<Q, MRT, ST>(a, g, e2s, x0, y, tmax);
+    finish_sites<Q, MRT, ST, SLAB>(a, g, e2s, x0, y, tmax);
 }
 
-template <int Q, bool MRT, bool PERIODIC, typename ST>
+template <int Q, bool MRT, bool PERIODIC, typename ST, bool SLAB = false>
 // Minimum resident blocks per SM: enough warps to keep ~100 KB of loads in
 // flight per SM (FP32 D2Q5 fits 5 blocks at <= 48 registers; the 8-site 16-bit
 // and the 9-population FP32 forms are held to 64 registers for 4 blocks; the
@@ -843,7 +897,7 @@ __global__ void __launch_bounds__(kThreads, Q == 5   ? (sizeof(ST) == 4 ? 5 : 4)
         __syncthreads();
     }
     float tmax[Q];
-    step_sites<Q, MRT, PERIODIC, ST>(a, blockIdx.x, tmax, s_tab);
+    step_sites<Q, MRT, PERIODIC, ST, SLAB>(a, blockIdx.x, tmax, s_tab);
     if (SC) {  // fold this block's max |output| per population into max_out
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -956,15 +1010,16 @@ __global__ void get_state_kernel(StepArgs a, float *dst, int mode) {
     for (int i = 0; i < Q; i++) {
         int xs = x - (a.raw ? 0 : Lat<Q>::cx(i));
         const int ys = a.raw ? y : pull_row<Q, PERIODIC>(a, y, i);  // y: row (z ny3 + y in 3-D)
+        const ST *halo = a.raw ? nullptr : slab_halo_row<Q, ST>(a, y, i);
         float v = 0.f;
         bool ok = true;
         if (PERIODIC) {
             xs = (xs + a.nx) % a.nx;
         } else {
-            ok = xs >= 0 && xs < a.nx && ys >= 0;
+            ok = xs >= 0 && xs < a.nx && (ys >= 0 || halo);
         }
         if (ok)
-            v = Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch + xs) *
+            v = Store<ST>::load1(halo ? halo + xs : in + i * a.plane + (long long)ys * a.pitch + xs) *
                 scale_of(a.scale_in, i);
         if (mode == 1) dst[(long long)i * total + idx] = v;
         rho += v;
@@ -1020,22 +1075,46 @@ static __global__ void init_scale_kernel(StepArgs a, int Q, float *scale_first) 
     for (int c = 0; c < kMaxCopies; c++) a.max_next[i * kMaxCopies + c] = 0u;
 }
 
-// eta^2 = (c / c_ref)^2 per site (pads 0); flags: bit0 c <= 0 or non-finite, bit1 eta > 1.
+// eta^2 = (c / c_ref)^2 per site (pads 0); flags[0]: bit0 c <= 0 or non-finite, bit1
+// eta > 1; flags[1] / flags[2]: the bits of the smallest / largest eta^2 over the real sites
+// (non-negative floats order as their bit patterns; the caller sets them to +inf and 0).
+// Launched with 256 threads per block.
 static __global__ void medium_kernel(const float *c_map, float *eta2, int nx, int ny, int pitch,
                               double inv_cref, unsigned *flags) {
+    __shared__ unsigned s_lo[8], s_hi[8];
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= (long long)ny * pitch) return;
-    int y = (int)(idx / pitch), x = (int)(idx - (long long)y * pitch);
-    float v = 0.f;
-    if (x < nx) {
-        float c = c_map[(long long)y * nx + x];
-        if (!(c > 0.f) || !isfinite(c)) atomicOr(flags, 1u);
-        double eta = (double)c * inv_cref;
-        if (eta > 1.0 + 1e-6) atomicOr(flags, 2u);
-        if (eta > 1.0) eta = 1.0;
-        v = (float)(eta * eta);
+    unsigned lo = 0x7f800000u, hi = 0u;
+    if (idx < (long long)ny * pitch) {
+        int y = (int)(idx / pitch), x = (int)(idx - (long long)y * pitch);
+        float v = 0.f;
+        if (x < nx) {
+            float c = c_map[(long long)y * nx + x];
+            if (!(c > 0.f) || !isfinite(c)) atomicOr(flags, 1u);
+            double eta = (double)c * inv_cref;
+            if (eta > 1.0 + 1e-6) atomicOr(flags, 2u);
+            if (eta > 1.0) eta = 1.0;
+            v = (float)(eta * eta);
+            if (v >= 0.f) lo = hi = __float_as_uint(v);
+        }
+        eta2[idx] = v;
     }
-    eta2[idx] = v;
+    for (int off = 16; off > 0; off >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo;
+        s_hi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            lo = min(lo, s_lo[w]);
+            hi = max(hi, s_hi[w]);
+        }
+        atomicMin(flags + 1, lo);
+        atomicMax(flags + 2, hi);
+    }
 }
 
 }  // namespace lbk

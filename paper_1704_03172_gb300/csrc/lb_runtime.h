@@ -39,6 +39,9 @@ struct lb_ctx {
     int tape_cap = 0;
     int *tb_off = nullptr;          // temporal blocking: per-tile receiver list offsets
     int *tb_rec = nullptr;          // receiver indices grouped by tile
+    int *tb5_off = nullptr;         // D2Q5 wavefront blocking: per-row receiver offsets [ny + 2]
+    int *tb5_x = nullptr;           // their x (ascending within a row)
+    int *tb5_id = nullptr;          // their receiver index
     bool ckpt_raw0 = false;         // raw flag of the time-0 checkpoint
     float *src_tab = nullptr;
     int src_nt = 0, src_x = 0, src_y = 0;
@@ -63,6 +66,17 @@ struct lb_ctx {
     void *alloc_user = nullptr;
     std::vector<void *> allocs;
     std::string err;
+    // lb_set_slab: this context is the row slab [slab_y0, slab_y0 + ny) of a grid of
+    // slab_nyg rows; halo rows and cut rows in caller-owned device buffers
+    int slab_y0 = 0, slab_nyg = 0;
+    const void *halo_lo = nullptr, *halo_hi = nullptr;
+    void *send_lo = nullptr, *send_hi = nullptr;
+    cudaEvent_t slab_ev[2] = {nullptr, nullptr};  // lb_slab_step: step done / cut rows read
+    // lb_watch_stability: every `watch_every` steps lb_step checks the invariants
+    int watch_every = 0;
+    double watch_growth = 0;        // energy ratio between checks above which it fails
+    double watch_energy = -1;       // energy at the last check (< 0: none yet)
+    long long watch_t0 = 0;
 };
 
 namespace lbrt {
@@ -141,6 +155,19 @@ lb_status stream_launch(lb_ctx *ctx, const lbk::StepArgs &a, int rec_blocks);
 lb_status tb_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
 lb_status tb_launch(lb_ctx *ctx, int K);
 lb_status tb_launch_args(lb_ctx *ctx, const lbk::StepArgs &a, int K);
+// D2Q5 wavefront temporal blocking (tblock5.cu)
+bool tb5_supported(int K);
+lb_status tb5_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
+lb_status tb5_launch_args(lb_ctx *ctx, const lbk::StepArgs &a, int K);
+// served batches of D2Q5 shots, K = 8 steps per launch (tblock5.cu): staging bytes of one
+// launch's descriptors, whether a shot can take K steps now, the fill (advancing the shots)
+// and the launch from the device copy of the staging block
+constexpr int kServeTb = 8;
+size_t tb5_batch_bytes(int n);
+bool tb5_batch_ready(const lb_ctx *ctx, int K);
+int tb5_batch_fill(lb_ctx *const *ctxs, int n, int K, void *h);
+cudaError_t tb5_batch_launch(const void *d, int n, int K, int blocks, bool mrt, bool per,
+                             int storage, cudaStream_t stream);
 
 // test-only FP64 storage (f64.cu): medium and coefficients, source table, steps, and the
 // state transforms (mode 0 pressure, 1 populations; FP32 arrays f or FP64 arrays d)
@@ -149,6 +176,16 @@ lb_status f64_set_source(lb_ctx *c, const double *wavelet, int nt);
 lb_status f64_step(lb_ctx *c, int n);
 lb_status f64_set(lb_ctx *c, const float *f, const double *d, int on_device, int mode);
 lb_status f64_get(lb_ctx *c, float *f, double *d, int on_device, int mode);
+
+// linear stability of a configuration (stability.cu): whether lb_create checks it, the etas
+// it checks, and the largest |lambda| of the one-step map over them and every refinement level
+namespace lbrt {
+bool stability_needed(const lb_config *cfg);
+std::vector<double> stability_etas(double eta_min, double eta_max, const std::vector<double> &distinct);
+double stability_worst(const lb_config *cfg, const std::vector<double> &etas, double *eta_at,
+                       int *level_at);
+constexpr double kStableBound = 1.0 + 1e-12;
+}  // namespace lbrt
 
 // grid refinement (refine.cu)
 lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev);

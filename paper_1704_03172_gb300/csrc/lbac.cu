@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -154,6 +155,12 @@ StepArgs base_args(const lb_ctx *c) {
     a.eta2_64 = c->eta2_64;
     a.src64 = c->src64;
     a.coef64 = c->coef64;
+    a.y_off = c->slab_y0;
+    a.ny_glob = c->slab_nyg;
+    a.halo_lo = c->halo_lo;
+    a.halo_hi = c->halo_hi;
+    a.send_lo = c->send_lo;
+    a.send_hi = c->send_hi;
     if (c->lp_scale) a.scale_in = c->lp_scale + c->lp_slot * 9;
     return a;
 }
@@ -188,9 +195,20 @@ StepFn pick_step_for(int Q, bool mrt, bool per, int storage) {
     }
 }
 
+// row slabs (lb_set_slab): the step with the halo-row pulls and the cut-row stores
+template <int Q, typename ST> StepFn slab_fn(bool mrt, bool per) {
+    if (mrt) return per ? step_kernel<Q, true, true, ST, true> : step_kernel<Q, true, false, ST, true>;
+    return per ? step_kernel<Q, false, true, ST, true> : step_kernel<Q, false, false, ST, true>;
+}
+
 StepFn pick_step(const lb_ctx *c) {
-    return pick_step_for(c->Q, c->cfg.collision == LB_MRT, c->cfg.boundary == LB_PERIODIC,
-                         c->cfg.storage);
+    const bool mrt = c->cfg.collision == LB_MRT, per = c->cfg.boundary == LB_PERIODIC;
+    if (c->slab_nyg) {
+        const bool bf = c->cfg.storage == LB_BF16;
+        if (c->Q == 9) return bf ? slab_fn<9, __nv_bfloat16>(mrt, per) : slab_fn<9, float>(mrt, per);
+        return bf ? slab_fn<5, __nv_bfloat16>(mrt, per) : slab_fn<5, float>(mrt, per);
+    }
+    return pick_step_for(c->Q, mrt, per, c->cfg.storage);
 }
 
 template <int Q, typename ST> SetFn set_fn_q(bool per) {
@@ -228,6 +246,22 @@ GetFn pick_get(const lb_ctx *c) {
 lb_status check_launch(lb_ctx *ctx, const char *what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    return LB_OK;
+}
+
+// lb_create's linear stability check (stability.cu): LB_EINVAL when the one-step map has an
+// eigenvalue of modulus above 1 + 1e-12 at a checked eta on any refinement level.
+lb_status stability_check(const lb_config *cfg, double eta_min, double eta_max,
+                          const std::vector<double> &distinct) {
+    double eta_at = 0;
+    int level = 0;
+    const double worst =
+        stability_worst(cfg, stability_etas(eta_min, eta_max, distinct), &eta_at, &level);
+    if (worst > kStableBound)
+        return fail(nullptr, LB_EINVAL,
+                    "linearly unstable: max |lambda(k)| of the one-step map is %.12g > 1 at "
+                    "eta = %.6g%s (refinement level %d); choose other rates or weights",
+                    worst, eta_at, worst > 1e299 ? " (no convergence)" : "", level);
     return LB_OK;
 }
 
@@ -279,13 +313,39 @@ lb_status validate(const lb_config *cfg) {
     if (cfg->time_block > 1) {
         if (!tb_supported(cfg->lattice, cfg->time_block))
             return fail(nullptr, LB_EINVAL, "time_block %d not supported for D2Q%d (D2Q5: 2, 4, 6, "
-                        "8; D2Q9: 2, 4)", cfg->time_block, cfg->lattice);
-        if (cfg->storage != LB_F32 || cfg->n_patches > 0)
-            return fail(nullptr, LB_EINVAL, "time_block needs FP32 storage and no patch");
+                        "8, 16; D2Q9: 2, 4)", cfg->time_block, cfg->lattice);
+        if (cfg->n_patches > 0 || !(cfg->storage == LB_F32 ||
+                                    (cfg->storage == LB_BF16 && cfg->lattice == LB_D2Q5)))
+            return fail(nullptr, LB_EINVAL, "time_block needs FP32 storage (D2Q5: or BF16) and no "
+                        "patch");
     }
     if (cfg->step_kernel != LB_STEP_AUTO && cfg->step_kernel != LB_STEP_DIRECT &&
         cfg->step_kernel != LB_STEP_STAGED)
         return fail(nullptr, LB_EINVAL, "step_kernel must be LB_STEP_AUTO, _DIRECT or _STAGED");
+    if (stability_needed(cfg) && !cfg->c_map_on_device) {
+        // linear stability at the medium's eta (a device c_map is checked in lb_create, once
+        // its range is known): the distinct speeds when there are at most 8, else a spread
+        const long long n = (long long)cfg->nx * cfg->ny * nz;
+        float mn = INFINITY, mx = 0.f, last = -1.f;
+        std::vector<float> dv;
+        for (long long i = 0; i < n; i++) {
+            const float c = cfg->c_map[i];
+            if (!(c > 0.f) || !std::isfinite(c)) continue;  // refused later, with the medium
+            mn = std::min(mn, c);
+            mx = std::max(mx, c);
+            if (c != last && dv.size() <= 8 && std::find(dv.begin(), dv.end(), c) == dv.end())
+                dv.push_back(c);
+            last = c;
+        }
+        const double cref = cfg->c_ref > 0 ? cfg->c_ref : (double)mx;
+        if (mx > 0.f && cref > 0) {
+            std::vector<double> de;
+            for (float c : dv) de.push_back(std::min(1.0, (double)c / cref));
+            if (de.size() > 8) de.clear();
+            lb_status st = stability_check(cfg, std::min(1.0, mn / cref), std::min(1.0, mx / cref), de);
+            if (st != LB_OK) return st;
+        }
+    }
     return LB_OK;
 }
 
@@ -446,7 +506,8 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
         return bail(fail(c, LB_EINVAL, "c_ref must be given when c_map is on the device"));
     }
     c->cfg.c_ref = cref;
-    cudaMemsetAsync(flags, 0, 4, c->stream);
+    const unsigned flags0[3] = {0u, 0x7f800000u, 0u};  // fault bits, min and max eta^2 (bits)
+    cudaMemcpyAsync(flags, flags0, sizeof(flags0), cudaMemcpyHostToDevice, c->stream);
     {
         long long total = (long long)c->ny * c->pitch;
         int blocks = (int)((total + 255) / 256);
@@ -454,13 +515,23 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
                                                       1.0 / cref, flags);
         if ((st = check_launch(c, "medium_kernel")) != LB_OK) return bail(st);
     }
-    unsigned hflags = 0;
-    cudaError_t e = cudaMemcpyAsync(&hflags, flags, 4, cudaMemcpyDeviceToHost, c->stream);
+    unsigned hf[3] = {0u, 0u, 0u};
+    cudaError_t e = cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "medium setup"));
     dev_free(c, flags);
-    if (hflags & 1u) return bail(fail(c, LB_EINVAL, "c_map must be finite and > 0"));
-    if (hflags & 2u) return bail(fail(c, LB_EINVAL, "c_map exceeds c_ref (eta > 1)"));
+    if (hf[0] & 1u) return bail(fail(c, LB_EINVAL, "c_map must be finite and > 0"));
+    if (hf[0] & 2u) return bail(fail(c, LB_EINVAL, "c_map exceeds c_ref (eta > 1)"));
+    if (stability_needed(cfg) && cfg->c_map_on_device) {  // checked over the medium's range
+        float e2min, e2max;
+        memcpy(&e2min, &hf[1], 4);
+        memcpy(&e2max, &hf[2], 4);
+        if ((st = stability_check(cfg, std::sqrt((double)e2min), std::sqrt((double)e2max), {})) !=
+            LB_OK) {
+            c->err = g_create_error;
+            return bail(st);
+        }
+    }
     if (cfg->storage == LB_F64) {
         if ((st = f64_setup(c, cmap_dev, cref)) != LB_OK) return bail(st);
     } else if (!cfg->c_map_on_device) {  // piecewise-constant media: 1-byte medium index
@@ -491,6 +562,8 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
 lb_status lb_destroy(lb_ctx *ctx) {
     if (!ctx) return LB_EINVAL;
     cudaStreamSynchronize(ctx->stream);
+    for (cudaEvent_t &e : ctx->slab_ev)
+        if (e) cudaEventDestroy(e);
     refine_destroy(ctx);
     std::vector<void *> all = ctx->allocs;
     for (void *p : all) dev_free(ctx, p);
@@ -784,9 +857,53 @@ lb_status launch_step(lb_ctx *ctx, StepFn fn, StepArgs &a) {
 
 extern "C" {
 
+static lb_status step_n(lb_ctx *ctx, int n);
+
+// lb_watch_stability's check: the FP64 invariants of the current state (lb_invariants
+// reports non-finite values as LB_EUNSTABLE), then the energy against the last check's
+static lb_status watch_check(lb_ctx *ctx) {
+    double v[4];
+    lb_status st = lb_invariants(ctx, v);
+    if (st != LB_OK) return st;
+    if (ctx->watch_growth > 0 && ctx->watch_energy > 0 &&
+        v[1] > ctx->watch_growth * ctx->watch_energy)
+        return fail(ctx, LB_EUNSTABLE, "energy grew by a factor %.6g in %d steps (bound %.6g) "
+                    "at time %lld", v[1] / ctx->watch_energy, ctx->watch_every,
+                    ctx->watch_growth, ctx->t);
+    ctx->watch_energy = v[1];
+    return LB_OK;
+}
+
+lb_status lb_watch_stability(lb_ctx *ctx, int every, double max_growth) {
+    if (!ctx) return LB_EINVAL;
+    if (every < 0 || max_growth < 0 || !std::isfinite(max_growth))
+        return fail(ctx, LB_EINVAL, "every >= 0 and a finite max_growth >= 0 required");
+    if (every > 0 && (ctx->Q == 7 || ctx->cfg.storage == LB_F64))
+        return fail(ctx, LB_ESTATE, "the watch reads the 2-D FP32 / 16-bit invariants");
+    ctx->watch_every = every;
+    ctx->watch_growth = max_growth;
+    ctx->watch_energy = -1;
+    ctx->watch_t0 = ctx->t;
+    return LB_OK;
+}
+
 lb_status lb_step(lb_ctx *ctx, int n) {
     if (!ctx) return LB_EINVAL;
     if (n < 0) return fail(ctx, LB_EINVAL, "n < 0");
+    if (ctx->watch_every <= 0) return step_n(ctx, n);
+    while (n > 0) {  // steps in chunks that end on the watch's check times
+        const int every = ctx->watch_every;
+        const long long since = (ctx->t - ctx->watch_t0) % every;
+        const int chunk = (int)std::min<long long>(n, every - since);
+        lb_status st = step_n(ctx, chunk);
+        if (st != LB_OK) return st;
+        n -= chunk;
+        if ((ctx->t - ctx->watch_t0) % every == 0 && (st = watch_check(ctx)) != LB_OK) return st;
+    }
+    return LB_OK;
+}
+
+static lb_status step_n(lb_ctx *ctx, int n) {
     if (ctx->refined) return refine_step(ctx, n);
     if (ctx->cfg.storage == LB_F64) return f64_step(ctx, n);
     StepFn fn = pick_step(ctx);
@@ -806,8 +923,10 @@ lb_status lb_step(lb_ctx *ctx, int n) {
             const bool straddle_trace =
                 ctx->trace && row < ctx->trace_cap && row + K > ctx->trace_cap;
             const long long trow = ctx->t - ctx->tape_t0;
+            // the time-blocked kernel records the rho tape for FP32 storage only
             const bool straddle_tape =
-                ctx->rho_tape && trow < ctx->tape_cap && trow + K > ctx->tape_cap;
+                ctx->rho_tape && trow < ctx->tape_cap &&
+                (trow + K > ctx->tape_cap || ctx->cfg.storage != LB_F32);
             if (!straddle_ckpt && !straddle_trace && !straddle_tape) {
                 lb_status st = tb_launch(ctx, K);
                 if (st != LB_OK) return st;
@@ -880,6 +999,111 @@ lb_status lb_info(const lb_ctx *ctx, double *info, int n_info) {
 const char *lb_last_error(const lb_ctx *ctx) {
     if (!ctx) return g_create_error.c_str();
     return ctx->err.c_str();
+}
+
+// ------------------------------------------------------ row-slab decomposition --
+lb_status lb_set_slab(lb_ctx *ctx, int y_offset, int ny_global, void *send_lo, void *send_hi,
+                      const void *recv_lo, const void *recv_hi) {
+    if (!ctx) return LB_EINVAL;
+    if (ctx->nz > 1 || ctx->refined || ctx->cfg.time_block > 1 ||
+        (ctx->cfg.storage != LB_F32 && ctx->cfg.storage != LB_BF16))
+        return fail(ctx, LB_ESTATE, "slabs are 2-D, FP32 or BF16, without patch or time blocking");
+    if (y_offset < 0 || ny_global < ctx->ny || y_offset + ctx->ny > ny_global)
+        return fail(ctx, LB_EINVAL, "slab rows [%d, %d) outside a grid of %d rows", y_offset,
+                    y_offset + ctx->ny, ny_global);
+    for (const void *p : {(const void *)send_lo, (const void *)send_hi, recv_lo, recv_hi})
+        if (p && (reinterpret_cast<uintptr_t>(p) & 15u))
+            return fail(ctx, LB_EINVAL, "slab row buffers must be 16-byte aligned");
+    if (ctx->rho_tape || ctx->ckpt_every > 0)
+        return fail(ctx, LB_ESTATE, "a slab has no adjoint (checkpoints or rho tape)");
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream");
+    for (cudaEvent_t &ev : ctx->slab_ev)
+        if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(ctx, e, "slab events");
+    ctx->slab_y0 = y_offset;
+    ctx->slab_nyg = ny_global;
+    ctx->send_lo = send_lo;
+    ctx->send_hi = send_hi;
+    ctx->halo_lo = recv_lo;
+    ctx->halo_hi = recv_hi;
+    ctx->staged = false;  // the register-streaming step reads the halo rows
+    return LB_OK;
+}
+
+lb_status lb_slab_halo_bytes(const lb_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return LB_EINVAL;
+    const int nc = ctx->Q == 9 ? cross_count<9>() : cross_count<5>();
+    *bytes = (size_t)nc * ctx->pitch * ctx->ebytes;
+    return LB_OK;
+}
+
+// Copy the cut rows of slab k into the halo rows of its neighbours, each copy on the
+// receiving slab's stream after that slab's step and before its next one; the sending slab
+// waits for the copies before its next step overwrites its cut rows.
+static lb_status slab_exchange(lb_ctx **s, int n, int periodic) {
+    for (int k = 0; k < n; k++) {
+        cudaError_t e = cudaEventRecord(s[k]->slab_ev[0], s[k]->stream);
+        if (e != cudaSuccess) return cuda_fail(s[k], e, "slab event");
+    }
+    size_t bytes = 0;
+    lb_slab_halo_bytes(s[0], &bytes);
+    for (int k = 0; k < n; k++) {  // slab k receives from k - 1 (below) and k + 1 (above)
+        const int lo = k > 0 ? k - 1 : (periodic ? n - 1 : -1);
+        const int hi = k + 1 < n ? k + 1 : (periodic ? 0 : -1);
+        for (int side = 0; side < 2; side++) {
+            const int src = side == 0 ? lo : hi;
+            void *dst = const_cast<void *>(side == 0 ? s[k]->halo_lo : s[k]->halo_hi);
+            const void *from = src < 0 ? nullptr : (side == 0 ? s[src]->send_hi : s[src]->send_lo);
+            if (src < 0 || !dst || !from) continue;
+            cudaError_t e = cudaStreamWaitEvent(s[k]->stream, s[src]->slab_ev[0], 0);
+            if (e == cudaSuccess) {
+                int d_dst = 0, d_src = 0;
+                cudaPointerAttributes at;
+                if (cudaPointerGetAttributes(&at, dst) == cudaSuccess) d_dst = at.device;
+                if (cudaPointerGetAttributes(&at, from) == cudaSuccess) d_src = at.device;
+                e = d_dst == d_src ? cudaMemcpyAsync(dst, from, bytes, cudaMemcpyDeviceToDevice,
+                                                     s[k]->stream)
+                                   : cudaMemcpyPeerAsync(dst, d_dst, from, d_src, bytes, s[k]->stream);
+            }
+            if (e != cudaSuccess) return cuda_fail(s[k], e, "slab halo copy");
+        }
+        cudaError_t e = cudaEventRecord(s[k]->slab_ev[1], s[k]->stream);
+        if (e != cudaSuccess) return cuda_fail(s[k], e, "slab event");
+    }
+    for (int k = 0; k < n; k++) {  // the senders wait for the copies that read their rows
+        for (int d = -1; d <= 1; d += 2) {
+            int j = k + d;
+            if (periodic) j = (j + n) % n;
+            if (j < 0 || j >= n || j == k) continue;
+            cudaError_t e = cudaStreamWaitEvent(s[k]->stream, s[j]->slab_ev[1], 0);
+            if (e != cudaSuccess) return cuda_fail(s[k], e, "slab event wait");
+        }
+    }
+    return LB_OK;
+}
+
+lb_status lb_slab_step(lb_ctx **slabs, int n, int steps) {
+    if (!slabs || n < 1 || steps < 0) return LB_EINVAL;
+    for (int k = 0; k < n; k++) {
+        if (!slabs[k]) return LB_EINVAL;
+        if (!slabs[k]->slab_nyg) return fail(slabs[k], LB_ESTATE, "not a slab (lb_set_slab)");
+        if (slabs[k]->Q != slabs[0]->Q || slabs[k]->pitch != slabs[0]->pitch ||
+            slabs[k]->ebytes != slabs[0]->ebytes ||
+            slabs[k]->slab_nyg != slabs[0]->slab_nyg ||
+            (k > 0 && slabs[k]->slab_y0 != slabs[k - 1]->slab_y0 + slabs[k - 1]->ny))
+            return fail(slabs[k], LB_EINVAL, "slabs must tile one grid, in row order");
+    }
+    const int periodic = slabs[0]->cfg.boundary == LB_PERIODIC;
+    for (int t = 0; t < steps; t++) {
+        for (int k = 0; k < n; k++) {
+            lb_status st = lb_step(slabs[k], 1);
+            if (st != LB_OK) return st;
+        }
+        lb_status st = slab_exchange(slabs, n, periodic);
+        if (st != LB_OK) return st;
+    }
+    return LB_OK;
 }
 
 }  // extern "C"

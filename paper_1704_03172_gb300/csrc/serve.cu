@@ -9,12 +9,21 @@
 //              batch_step_kernel launch per (lattice, collision, boundary,
 //              storage) group steps all the group's shots once, each shot
 //              reading its own StepArgs descriptor (uploaded once per pass), so
-//              many small shots share one launch and fill the GPU together.
+//              many small shots share one launch and fill the GPU together.  D2Q5
+//              FP32 / BF16 shots that are far enough from their end take their steps
+//              8 at a time instead: one time-blocked launch (tb5_batch_kernel,
+//              tblock5.cu) per group advances every such shot by 8 steps.
 //              Shots that finish leave the batch (their traces are copied to
 //              pinned host memory), shots that are ready join at the next pass;
 //   workers    run the adjoint of gradient requests (lb_adjoint) on their own
 //              streams, overlapping the batched forward work of others.
-// FP16 shots, whose per-step scale hand-off is per launch, step on their own.
+// FP16 shots, whose per-step scale hand-off is per launch, step on their own, on a
+// stream of their own (so they neither wait for nor delay the batched launches).
+//
+// Failures: a CUDA call that fails while a pass is queued (a descriptor copy, a
+// batched launch, an FP16 step) fails the shots it concerns with LB_ECUDA (a
+// descriptor-buffer allocation failure: LB_ENOMEM); they stop stepping and are
+// retired once their queued work has drained or the stream reports the error.
 //
 // Memory: every device buffer of a served shot comes from one stream-ordered
 // pool owned by the server (cudaMallocFromPoolAsync / cudaFreeAsync on the
@@ -77,6 +86,9 @@ struct Req {
     double t_submit = 0, t_start = 0, t_done = 0;
     lb_status status = LB_OK;
     std::string err;
+    lb_status fail_st = LB_OK;  // set by the scheduler when a queued operation failed
+    std::string fail_msg;
+    bool fail_event = false;    // its drain event is still to be recorded (retire())
 };
 
 __global__ void residual_kernel(const float *p, const float *d, float *r, long long n) {
@@ -107,6 +119,7 @@ struct lb_server {
     lb_server_config cfg;
     int device = 0;
     cudaStream_t stream = nullptr;   // batch stream (scheduler)
+    cudaStream_t stream16 = nullptr; // FP16 shots, stepped one by one (scheduler)
     cudaStream_t setup = nullptr;    // admission (admitter)
     cudaStream_t idle = nullptr;     // retirement of finished shots: nothing else runs on it
     cudaMemPool_t pool = nullptr;
@@ -124,6 +137,8 @@ struct lb_server {
     StepArgs *d_args = nullptr, *h_args = nullptr;
     int *d_first = nullptr, *h_first = nullptr;
     size_t cap = 0;
+    void *d_tb = nullptr, *h_tb = nullptr;  // time-blocked launches' descriptor blocks
+    size_t tb_cap = 0;
     cudaEvent_t staged = nullptr;
     std::mutex pin_mu;
     std::multimap<size_t, void *> pinned;  // free pinned trace buffers by size
@@ -191,6 +206,31 @@ void finish(lb_server *S, Req *r, lb_status st, const std::string &msg) {
     S->cv_work.notify_all();
 }
 
+void set_err(lb_server *S, const std::string &msg) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->err = msg;
+}
+
+// The scheduler gives up on a shot whose queued work failed: it stops stepping and
+// retire() releases it once its stream has drained (or reports the error).  The drain
+// event is recorded by retire(), after everything of the pass is queued, because later
+// launches of the same pass may still name the shot.
+void fail_shot(lb_server *, Req *r, lb_status st, const std::string &msg) {
+    if (r->fail_st == LB_OK) {
+        r->fail_st = st;
+        r->fail_msg = msg;
+    }
+    if (r->state == RS::Active) {
+        r->fail_event = true;
+        r->state = RS::Draining;
+    }
+}
+
+// The stream a shot steps on: FP16 shots on their own, the others on the batch stream.
+cudaStream_t shot_stream(const lb_server *S, const Req *r) {
+    return r->cfg.storage == LB_F16 ? S->stream16 : S->stream;
+}
+
 // Runs on the admitter thread: build the shot's context on the setup stream.
 // Every call below that touches the device synchronises the setup stream, so
 // the context is complete when it is handed to the scheduler.
@@ -210,6 +250,9 @@ void admit(lb_server *S, Req *r) {
     if (st == LB_OK && !r->wav.empty())
         st = lb_set_source(ctx, r->src_x, r->src_y, r->wav.data(), (int)r->wav.size());
     if (st == LB_OK) st = lb_set_receivers(ctx, r->rec.data(), (int)r->rec.size() / 2, r->nt);
+    if (st == LB_OK && c.lattice == LB_D2Q5 && (c.storage == LB_F32 || c.storage == LB_BF16) &&
+        !r->rec.empty())  // the receiver rows of the time-blocked batches
+        st = tb5_set_receivers(ctx, r->rec.data(), (int)r->rec.size() / 2);
     if (st == LB_OK) st = lb_init_pressure(ctx, nullptr, 0);
     if (st == LB_OK && r->want_grad)
         st = r->tape ? lb_record_rho(ctx, r->nt) : lb_checkpoint_every(ctx, r->ckpt);
@@ -229,10 +272,10 @@ void admit(lb_server *S, Req *r) {
         finish(S, r, st, msg);
         return;
     }
-    ctx->stream = S->stream;  // from here on the scheduler runs it
+    ctx->stream = shot_stream(S, r);  // from here on the scheduler runs it
     r->ctx = ctx;
     std::lock_guard<std::mutex> lk(S->mu);
-    r->astream.store(S->stream);
+    r->astream.store(shot_stream(S, r));
     r->state = RS::Ready;
     S->admitting--;
     S->ready.push_back(r);
@@ -256,6 +299,19 @@ void admitter(lb_server *S) {
         admit(S, r);
     }
 }
+bool ensure_tb_capacity(lb_server *S, size_t bytes) {
+    if (bytes <= S->tb_cap) return true;
+    const size_t cap = std::max(bytes, 2 * S->tb_cap);
+    if (S->d_tb) cudaFree(S->d_tb);
+    if (S->h_tb) cudaFreeHost(S->h_tb);
+    S->d_tb = S->h_tb = nullptr;
+    S->tb_cap = 0;
+    if (cudaMalloc(&S->d_tb, cap) != cudaSuccess || cudaMallocHost(&S->h_tb, cap) != cudaSuccess)
+        return false;
+    S->tb_cap = cap;
+    return true;
+}
+
 bool ensure_capacity(lb_server *S, size_t n) {
     if (n <= S->cap) return true;
     size_t cap = std::max(n, 2 * S->cap);
@@ -289,24 +345,87 @@ void pass(lb_server *S) {
     for (Req *r : shots) {
         if (r->cfg.storage == LB_F16) {
             int n = std::min(R, r->nt - r->steps);
-            lb_step(r->ctx, n);
+            const lb_status st = lb_step(r->ctx, n);
+            if (st != LB_OK) {
+                fail_shot(S, r, st, std::string("FP16 step: ") + lb_last_error(r->ctx));
+                continue;
+            }
             r->steps += n;
         } else {
             batched.push_back(r);
         }
     }
     if (batched.empty()) return;
-    // build every round's descriptors: groups of identical kernels, shots sorted by group
     using Key = std::tuple<int, int, int, int>;
     auto key = [](const Req *r) {
         return Key(r->cfg.lattice, r->cfg.collision, r->cfg.boundary, r->cfg.storage);
     };
+    // wait until the previous pass has consumed the staging buffers
+    if (S->staged) cudaEventSynchronize(S->staged);
+    // shots that take this pass's steps K at a time: one time-blocked launch per group and
+    // block of K steps
+    const int KB = kServeTb, nblk = R / KB;
+    std::vector<Req *> tbs, rest;
+    for (Req *r : batched) {
+        if (nblk > 0 && r->nt - r->steps >= nblk * KB && tb5_batch_ready(r->ctx, KB))
+            tbs.push_back(r);
+        else
+            rest.push_back(r);
+    }
+    batched.swap(rest);
+    std::stable_sort(tbs.begin(), tbs.end(),
+                     [&](const Req *a, const Req *b) { return key(a) < key(b); });
+    struct TbLaunch {
+        size_t off;
+        int n, blocks;
+        bool mrt, per;
+        int storage;
+        size_t g0, g1;
+    };
+    std::vector<TbLaunch> tb_launches;
+    size_t tb_bytes = 0;
+    if (!tbs.empty()) {
+        for (size_t g0 = 0; g0 < tbs.size();) {  // staging bytes of every launch
+            size_t g1 = g0;
+            while (g1 < tbs.size() && key(tbs[g1]) == key(tbs[g0])) g1++;
+            tb_bytes += nblk * tb5_batch_bytes((int)(g1 - g0));
+            g0 = g1;
+        }
+        if (!ensure_tb_capacity(S, tb_bytes)) {
+            cudaGetLastError();
+            set_err(S, "time-blocked descriptor buffers");
+            for (Req *r : tbs) fail_shot(S, r, LB_ENOMEM, "time-blocked descriptor buffers");
+            tbs.clear();
+        }
+        size_t off = 0;
+        std::vector<lb_ctx *> cs;
+        for (int j = 0; j < nblk && !tbs.empty(); j++) {
+            for (size_t g0 = 0; g0 < tbs.size();) {
+                size_t g1 = g0;
+                while (g1 < tbs.size() && key(tbs[g1]) == key(tbs[g0])) g1++;
+                cs.clear();
+                for (size_t q = g0; q < g1; q++) cs.push_back(tbs[q]->ctx);
+                const int n = (int)(g1 - g0);
+                const int blocks = tb5_batch_fill(cs.data(), n, KB, static_cast<char *>(S->h_tb) + off);
+                const lb_config &c0 = tbs[g0]->cfg;
+                tb_launches.push_back({off, n, blocks, c0.collision == LB_MRT,
+                                       c0.boundary == LB_PERIODIC, c0.storage, g0, g1});
+                off += tb5_batch_bytes(n);
+                g0 = g1;
+            }
+            for (Req *r : tbs) r->steps += KB;
+        }
+        tb_bytes = off;
+    }
+    if (batched.empty() && tb_launches.empty()) return;
+    // build every round's descriptors: groups of identical kernels, shots sorted by group
     std::stable_sort(batched.begin(), batched.end(),
                      [&](const Req *a, const Req *b) { return key(a) < key(b); });
     struct Launch {
         BatchFn fn;
         size_t arg0, first0;
         int n, blocks, round;
+        size_t g0, g1;  // its shots: batched[g0, g1)
     };
     struct Copy {  // adjoint checkpoint, queued just before its round's launches
         int round;
@@ -317,10 +436,10 @@ void pass(lb_server *S) {
     std::vector<Launch> launches;
     std::vector<Copy> copies;
     size_t need = (size_t)R * batched.size();
-    // wait until the previous pass has consumed the staging buffers
-    if (S->staged) cudaEventSynchronize(S->staged);
     if (!ensure_capacity(S, need + 1)) {
-        S->err = "descriptor buffers";
+        cudaGetLastError();
+        set_err(S, "descriptor buffers");
+        for (Req *r : batched) fail_shot(S, r, LB_ENOMEM, "batch descriptor buffers");
         return;
     }
     size_t na = 0, nf = 0;
@@ -329,7 +448,7 @@ void pass(lb_server *S) {
         while (g0 < batched.size()) {
             size_t g1 = g0;
             while (g1 < batched.size() && key(batched[g1]) == key(batched[g0])) g1++;
-            Launch L{pick_batch(batched[g0]->cfg), na, nf, 0, 0, k};
+            Launch L{pick_batch(batched[g0]->cfg), na, nf, 0, 0, k, g0, g1};
             for (size_t q = g0; q < g1; q++) {
                 Req *r = batched[q];
                 if (r->steps >= r->nt) continue;
@@ -352,18 +471,54 @@ void pass(lb_server *S) {
             g0 = g1;
         }
     }
-    cudaMemcpyAsync(S->d_args, S->h_args, na * sizeof(StepArgs), cudaMemcpyHostToDevice, S->stream);
-    cudaMemcpyAsync(S->d_first, S->h_first, nf * sizeof(int), cudaMemcpyHostToDevice, S->stream);
-    if (!S->staged) cudaEventCreateWithFlags(&S->staged, cudaEventDisableTiming);
-    cudaEventRecord(S->staged, S->stream);
+    cudaError_t e = cudaSuccess;
+    if (na > 0)
+        e = cudaMemcpyAsync(S->d_args, S->h_args, na * sizeof(StepArgs), cudaMemcpyHostToDevice,
+                            S->stream);
+    if (e == cudaSuccess && nf > 0)
+        e = cudaMemcpyAsync(S->d_first, S->h_first, nf * sizeof(int), cudaMemcpyHostToDevice,
+                            S->stream);
+    if (e == cudaSuccess && tb_bytes > 0)
+        e = cudaMemcpyAsync(S->d_tb, S->h_tb, tb_bytes, cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess && !S->staged)
+        e = cudaEventCreateWithFlags(&S->staged, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(S->staged, S->stream);
+    if (e != cudaSuccess) {  // nothing of this pass is queued: every batched shot fails
+        const std::string msg = std::string("batch descriptors: ") + cudaGetErrorString(e);
+        set_err(S, msg);
+        for (Req *r : batched) fail_shot(S, r, LB_ECUDA, msg);
+        for (Req *r : tbs) fail_shot(S, r, LB_ECUDA, msg);
+        return;
+    }
+    for (const TbLaunch &L : tb_launches) {  // time-blocked blocks of K steps
+        e = tb5_batch_launch(static_cast<char *>(S->d_tb) + L.off, L.n, KB, L.blocks, L.mrt, L.per,
+                             L.storage, S->stream);
+        if (e != cudaSuccess) {
+            const std::string msg = std::string("time-blocked batch: ") + cudaGetErrorString(e);
+            set_err(S, msg);
+            for (size_t q = L.g0; q < L.g1; q++) fail_shot(S, tbs[q], LB_ECUDA, msg);
+            e = cudaSuccess;
+            continue;
+        }
+        S->n_launch++;
+    }
     // rounds in order; a checkpoint copy reads the state its round starts from
     size_t ci = 0;
     for (const Launch &L : launches) {
-        for (; ci < copies.size() && copies[ci].round <= L.round; ci++)
-            cudaMemcpyAsync(copies[ci].dst, copies[ci].src, copies[ci].bytes,
-                            cudaMemcpyDeviceToDevice, S->stream);
-        launch_pdl(L.fn, dim3(L.blocks), dim3(kThreads), 0, S->stream,
-                   (const StepArgs *)(S->d_args + L.arg0), (const int *)(S->d_first + L.first0), L.n);
+        for (; ci < copies.size() && copies[ci].round <= L.round && e == cudaSuccess; ci++)
+            e = cudaMemcpyAsync(copies[ci].dst, copies[ci].src, copies[ci].bytes,
+                                cudaMemcpyDeviceToDevice, S->stream);
+        if (e == cudaSuccess)
+            e = launch_pdl(L.fn, dim3(L.blocks), dim3(kThreads), 0, S->stream,
+                           (const StepArgs *)(S->d_args + L.arg0),
+                           (const int *)(S->d_first + L.first0), L.n);
+        if (e != cudaSuccess) {  // this launch's shots, and every later round, stop here
+            const std::string msg = std::string("batched step: ") + cudaGetErrorString(e);
+            set_err(S, msg);
+            for (size_t q = L.g0; q < L.g1; q++) fail_shot(S, batched[q], LB_ECUDA, msg);
+            e = cudaSuccess;
+            continue;
+        }
         S->n_launch++;
     }
 }
@@ -372,28 +527,48 @@ void pass(lb_server *S) {
 void retire(lb_server *S) {
     std::vector<Req *> keep;
     for (Req *r : S->active) {
+        if (r->fail_event) {
+            r->fail_event = false;
+            cudaEventRecord(r->ev, r->ctx->stream);
+        }
         if (r->state == RS::Active && r->steps >= r->nt) {
             const size_t bytes = (size_t)r->nt * (r->rec.size() / 2) * 4;
-            if (bytes) cudaMemcpyAsync(r->h_traces, r->ctx->trace, bytes, cudaMemcpyDeviceToHost, S->stream);
-            cudaEventRecord(r->ev, S->stream);
-            if (r->want_grad) {
+            cudaError_t e = cudaSuccess;
+            if (bytes)
+                e = cudaMemcpyAsync(r->h_traces, r->ctx->trace, bytes, cudaMemcpyDeviceToHost,
+                                    r->ctx->stream);
+            if (e != cudaSuccess && r->fail_st == LB_OK) {
+                r->fail_st = LB_ECUDA;
+                r->fail_msg = std::string("trace copy: ") + cudaGetErrorString(e);
+            }
+            cudaEventRecord(r->ev, r->ctx->stream);
+            if (r->fail_st != LB_OK) r->state = RS::Draining;
+            if (r->state == RS::Active && r->want_grad) {
                 r->state = RS::Adjoint;
                 std::lock_guard<std::mutex> lk(S->mu);
                 S->adj_queue.push_back(r);
                 S->cv_adj.notify_one();
                 continue;  // leaves the active list; memory stays accounted
             }
-            r->state = RS::Draining;
+            if (r->state == RS::Active) r->state = RS::Draining;
         }
-        if (r->state == RS::Draining && cudaEventQuery(r->ev) == cudaSuccess) {
-            // all of the shot's work is complete: free on a stream with nothing queued,
-            // so neither lb_destroy's wait nor the frees hold up the batch stream
-            r->ctx->stream = S->idle;
-            r->astream.store(S->idle);
-            lb_destroy(r->ctx);
-            r->ctx = nullptr;
-            finish(S, r, LB_OK, "");
-            continue;
+        if (r->state == RS::Draining) {
+            const cudaError_t q = cudaEventQuery(r->ev);
+            if (q != cudaErrorNotReady) {
+                // all of the shot's work is complete (or its stream reports an error): free on
+                // a stream with nothing queued, so neither lb_destroy's wait nor the frees hold
+                // up the batch stream
+                if (q != cudaSuccess && r->fail_st == LB_OK) {
+                    r->fail_st = LB_ECUDA;
+                    r->fail_msg = std::string("shot's queued work: ") + cudaGetErrorString(q);
+                }
+                r->ctx->stream = S->idle;
+                r->astream.store(S->idle);
+                lb_destroy(r->ctx);
+                r->ctx = nullptr;
+                finish(S, r, r->fail_st, r->fail_msg);
+                continue;
+            }
         }
         keep.push_back(r);
     }
@@ -444,6 +619,7 @@ void scheduler(lb_server *S) {
         if (idle) std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     cudaStreamSynchronize(S->stream);
+    cudaStreamSynchronize(S->stream16);
 }
 
 void adjoint_worker(lb_server *S) {
@@ -525,11 +701,12 @@ lb_status lb_server_create(const lb_server_config *cfg, lb_server **out) {
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = S->device;
     if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->stream16, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&S->setup, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&S->idle, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMemPoolCreate(&S->pool, &props) != cudaSuccess) {
         cudaGetLastError();
-        for (cudaStream_t s : {S->stream, S->setup, S->idle})
+        for (cudaStream_t s : {S->stream, S->stream16, S->setup, S->idle})
             if (s) cudaStreamDestroy(s);
         delete S;
         return fail(nullptr, LB_ECUDA, "server streams or memory pool");
@@ -643,7 +820,7 @@ lb_status lb_server_result(lb_server *S, long long id, float *traces, float *gra
         times[2] = r->t_done;
     }
     lb_status st = r->status;
-    if (st != LB_OK) S->err = r->err;
+    if (st != LB_OK) set_err(S, r->err);
     pin_put(S, r->h_traces, r->h_cap);
     if (r->ev) cudaEventDestroy(r->ev);
     delete r;
@@ -686,9 +863,11 @@ lb_status lb_server_destroy(lb_server *S) {
     if (S->d_first) cudaFree(S->d_first);
     if (S->h_args) cudaFreeHost(S->h_args);
     if (S->h_first) cudaFreeHost(S->h_first);
+    if (S->d_tb) cudaFree(S->d_tb);
+    if (S->h_tb) cudaFreeHost(S->h_tb);
     for (auto &kv : S->pinned) cudaFreeHost(kv.second);
     if (S->staged) cudaEventDestroy(S->staged);
-    for (cudaStream_t s : {S->stream, S->setup, S->idle}) {
+    for (cudaStream_t s : {S->stream, S->stream16, S->setup, S->idle}) {
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
     }
@@ -697,6 +876,14 @@ lb_status lb_server_destroy(lb_server *S) {
     return LB_OK;
 }
 
-const char *lb_server_last_error(const lb_server *S) { return S ? S->err.c_str() : ""; }
+// The message is copied under the server's lock into a per-thread buffer, so the pointer
+// stays valid (until this thread's next call) while the scheduler records new errors.
+const char *lb_server_last_error(const lb_server *S) {
+    thread_local std::string copy;
+    if (!S) return "";
+    std::lock_guard<std::mutex> lk(const_cast<lb_server *>(S)->mu);
+    copy = S->err;
+    return copy.c_str();
+}
 
 }  // extern "C"

@@ -1,5 +1,6 @@
 // tblock.cu -- temporal blocking: K fused LB steps per launch with the tile
-// resident in shared memory (overlapped tiling).
+// resident in shared memory (overlapped tiling).  D2Q9 contexts use this kernel; D2Q5
+// contexts use the row wavefront of tblock5.cu (the dispatch below).
 //
 // Each CTA owns an OUT x OUT tile of output sites, OUT = 48 - 2K, and loads
 // the stored post-collision populations h^{t-1} of the 48 x 48 region made of
@@ -193,20 +194,18 @@ template <int K> TbFn tb_fn(int Q, bool mrt, bool per, bool rec) {
     if constexpr (K <= 4) {
         if (Q == 9) return mrt ? tb_fn_p<9, true, K>(per, rec) : tb_fn_p<9, false, K>(per, rec);
     }
-    if (Q == 9) return nullptr;  // not offered: see tb_supported
-    return mrt ? tb_fn_p<5, true, K>(per, rec) : tb_fn_p<5, false, K>(per, rec);
+    return nullptr;  // D2Q5 runs the wavefront kernel (tblock5.cu); see tb_supported
 }
 
 int tile_out(int K) { return kW - 2 * K; }
 
 }  // namespace
 
-// supported fused-step counts (shared memory: two copies of Q x 48^2 floats)
-bool tb_supported(int Q, int K) {
-    return Q == 5 ? (K == 2 || K == 4 || K == 6 || K == 8) : (K == 2 || K == 4);
-}
+// supported fused-step counts (D2Q9: shared memory holds two copies of 9 x 48^2 floats)
+bool tb_supported(int Q, int K) { return Q == 5 ? tb5_supported(K) : (K == 2 || K == 4); }
 
 lb_status tb_set_receivers(lb_ctx *ctx, const int *xy, int nrec) {
+    if (ctx->Q == 5) return tb5_set_receivers(ctx, xy, nrec);
     const int T = tile_out(ctx->cfg.time_block);
     const int tx = (ctx->nx + T - 1) / T, ty = (ctx->ny + T - 1) / T;
     std::vector<int> cnt((size_t)tx * ty + 1, 0), order(std::max(nrec, 1));
@@ -231,14 +230,13 @@ lb_status tb_set_receivers(lb_ctx *ctx, const int *xy, int nrec) {
 // tile lists exist.
 lb_status tb_launch_args(lb_ctx *ctx, const StepArgs &a, int K) {
     if (!tb_supported(ctx->Q, K)) return fail(ctx, LB_EINVAL, "time_block %d not supported", K);
+    if (ctx->Q == 5) return tb5_launch_args(ctx, a, K);
     const bool mrt = ctx->cfg.collision == LB_MRT, per = ctx->cfg.boundary == LB_PERIODIC;
     const bool rec = a.rho_out != nullptr;
     TbFn fn = nullptr;
     switch (K) {
         case 2: fn = tb_fn<2>(ctx->Q, mrt, per, rec); break;
         case 4: fn = tb_fn<4>(ctx->Q, mrt, per, rec); break;
-        case 6: fn = tb_fn<6>(ctx->Q, mrt, per, rec); break;
-        case 8: fn = tb_fn<8>(ctx->Q, mrt, per, rec); break;
         default: break;
     }
     if (!fn) return fail(ctx, LB_EINVAL, "time_block %d not supported", K);
@@ -265,7 +263,8 @@ lb_status tb_launch(lb_ctx *ctx, int K) {
     a.t = ctx->t;
     a.raw = 0;
     long long row = ctx->t - ctx->t_rec0;
-    a.trace_row = (ctx->trace && ctx->tb_off && row >= 0 && row + K <= ctx->trace_cap)
+    const int *lists = ctx->Q == 5 ? ctx->tb5_off : ctx->tb_off;
+    a.trace_row = (ctx->trace && lists && row >= 0 && row + K <= ctx->trace_cap)
                       ? ctx->trace + row * ctx->nrec : nullptr;
     // forward rho tape (the caller keeps K steps inside it): level j at rho_out + j plane
     a.rho_out = tape_row(ctx, ctx->t);

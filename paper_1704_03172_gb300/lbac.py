@@ -110,6 +110,12 @@ _SIGS = {
     "lb_invariants_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                               ctypes.c_int, ctypes.c_double, _dp, ctypes.c_void_p,
                               ctypes.c_void_p],
+    "lb_stability_radius": [_cfgp, ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp],
+    "lb_watch_stability": [_ctx_p, ctypes.c_int, ctypes.c_double],
+    "lb_set_slab": [_ctx_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                    ctypes.c_void_p, ctypes.c_void_p],
+    "lb_slab_halo_bytes": [_ctx_p, ctypes.POINTER(ctypes.c_size_t)],
+    "lb_slab_step": [ctypes.POINTER(_ctx_p), ctypes.c_int, ctypes.c_int],
 }
 _srv_p = ctypes.c_void_p
 _SIGS.update({
@@ -314,6 +320,36 @@ def lb_invariants_noalloc(g_ptr, c_map_ptr, lattice, nx, ny, c_ref, w_ref, out_p
     wr = (ctypes.c_double * 3)(*w_ref) if w_ref is not None else None
     return _check(_lib.lb_invariants_noalloc(g_ptr, c_map_ptr, int(lattice), int(nx), int(ny),
                                              float(c_ref), wr, out_ptr, stream))
+
+
+def lb_stability_radius(cfg: lb_config, eta, level=0, nk=64) -> float:
+    """max |lambda| of the one-step map over an nk x nk grid of wave vectors (host only)."""
+    r = ctypes.c_double()
+    _check(_lib.lb_stability_radius(ctypes.byref(cfg), float(eta), int(level), int(nk),
+                                    ctypes.byref(r)))
+    return r.value
+
+
+def lb_watch_stability(ctx, every, max_growth=0.0):
+    return _check(_lib.lb_watch_stability(ctx, int(every), float(max_growth)), ctx)
+
+
+def lb_set_slab(ctx, y_offset, ny_global, send_lo, send_hi, recv_lo, recv_hi):
+    """Mark ctx as rows [y_offset, y_offset + ny) of a grid of ny_global rows; the four row
+    buffers are device pointers (or None)."""
+    return _check(_lib.lb_set_slab(ctx, int(y_offset), int(ny_global), send_lo, send_hi,
+                                   recv_lo, recv_hi), ctx)
+
+
+def lb_slab_halo_bytes(ctx) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.lb_slab_halo_bytes(ctx, ctypes.byref(b)), ctx)
+    return b.value
+
+
+def lb_slab_step(ctxs, steps):
+    arr = (_ctx_p * len(ctxs))(*ctxs)
+    return _check(_lib.lb_slab_step(arr, len(ctxs), int(steps)), ctxs[0])
 
 
 def lb_mode_projection(ctx, modes):
