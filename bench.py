@@ -546,6 +546,59 @@ def _served(n_req, n_cal, seed=W.DEFAULT_SEED + 5, load=0.7, max_active=64):
                     "{256,512,1024,2048}, 2000-8000 steps"}
 
 
+def _served_classes(n_per_class=32, nt=2000, sizes=W.SERVED_SIZES, seed=W.DEFAULT_SEED + 7):
+    """Batching gain per grid size: n_per_class FP32 forward shots of one size (layered
+    models, Ricker source, 128 receivers, nt steps) submitted at once to the server,
+    against the same shots one after another through LBSim (create, step, traces)."""
+    import torch
+    from paper_1704_03172_gb300.sim import LBServer, LBSim
+    out = {}
+    for n in sizes:
+        descs = [dict(id=seed + 100 * n + k, n=n, nt=nt, storage="f32", grad=False, layers=8)
+                 for k in range(4)]
+        shots = [W.served_shot(d) for d in descs]
+        shots = [shots[k % len(shots)] for k in range(n_per_class)]
+
+        def kw(s):
+            d = dict(s)
+            d.pop("c_map")
+            return d
+
+        srv = LBServer(max_active=n_per_class, rounds_per_pass=16, adjoint_workers=1)
+        try:
+            t0 = time.monotonic()
+            ids = [srv.submit(s["c_map"], **kw(s)) for s in shots]
+            res = []
+            for i in ids:
+                srv.wait(i)
+                res.append(srv.result(i))
+            served_s = time.monotonic() - t0
+        finally:
+            srv.close()
+        torch.cuda.synchronize()
+        t0 = time.monotonic()
+        for s in shots:
+            sim = LBSim(s["c_map"], lattice=5, tau=0.5, sponge_width=s["sponge_width"],
+                        sponge_sigma_max=s["sponge_sigma_max"], c_ref=s["c_ref"])
+            sim.set_source(*s["source"])
+            sim.set_receivers(s["receivers"], nt)
+            sim.init_pressure(None)
+            sim.step(nt)
+            sim.traces(nt).cpu()
+            sim.close()
+        torch.cuda.synchronize()
+        plain_s = time.monotonic() - t0
+        upd = n * n * nt * n_per_class
+        out[f"{n}^2"] = {"shots": n_per_class, "steps": nt,
+                         "served_shots_per_s": round(n_per_class / served_s, 2),
+                         "one_by_one_shots_per_s": round(n_per_class / plain_s, 2),
+                         "batching_gain": round(plain_s / served_s, 3),
+                         "served_glups": round(upd / served_s / 1e9, 2),
+                         "one_by_one_glups": round(upd / plain_s / 1e9, 2),
+                         "finite": bool(all(np.isfinite(r["traces"]).all() for r in res))}
+    return out
+
+
 def _cpu_sample(target_s=12.0, lattice=5):
     """Time the FP64 oracle on a bounded sample of the workload (rows of the 4096^2 grid)."""
     import oracle
@@ -715,6 +768,8 @@ def run_ours(args):
             out = _layered_variant(torch, LBSim, name.rsplit("_", 1)[1], args.steps, args.warmup)
         elif name == "served":
             out = _served(args.served_requests, args.served_calibration)
+        elif name == "served_classes":
+            out = _served_classes()
         else:
             raise SystemExit(f"unknown variant {name}")
         if rank == 0:
@@ -865,6 +920,10 @@ def run_ours(args):
             line["served"] = _served(args.served_requests, args.served_calibration)
         except Exception as ex:  # report, do not hide
             line["served"] = {"error": str(ex)[:300]}
+        try:
+            line["served_by_size"] = _served_classes()
+        except Exception as ex:
+            line["served_by_size"] = {"error": str(ex)[:300]}
     if not args.no_cpu:
         line["cpu_baseline"] = _cpu_sample(args.cpu_seconds)
     print(json.dumps(line), flush=True)

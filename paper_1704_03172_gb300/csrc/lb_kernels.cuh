@@ -498,14 +498,17 @@ __device__ __forceinline__ int pull_row(const StepArgs &a, int r, int i) {
 // ------------------------------------------------------------- collision --
 // D2Q5: w_0 = 1 - eta^2, w_1..4 = eta^2 / 4, c_s^2 = eta^2 / 2, so
 // g^eq_0 = w_0 rho, g^eq_{1,3} = w_1 rho +- j_x / 2, g^eq_{2,4} = w_1 rho +- j_y / 2.
+// g^eq_0 is formed as rho - 4 w_1 rho (= w_0 rho): the equilibrium then carries the mass
+// rho up to one unbiased rounding, where fl(1 - eta^2) + eta^2 != 1 would make every
+// BGK collision create mass in a fixed ratio that a lossless run keeps forever.
 template <bool MRT, typename R>
 __device__ __forceinline__ void collide5(R g[5], R e2, const StepArgs &a) {
     const R rho = g[0] + g[1] + g[2] + g[3] + g[4];
     const R jx = g[1] - g[3], jy = g[2] - g[4];
-    const R w0 = R(1) - e2, w1 = R(0.25) * e2;
+    const R w1 = R(0.25) * e2;
     if (!MRT) {
         const R om = co<R>(a, a.omega, kCoOmega);
-        const R eq0 = w0 * rho, b = w1 * rho;
+        const R b = w1 * rho, eq0 = rho - R(4) * b;
         g[0] += om * (eq0 - g[0]);
         g[1] += om * (b + R(0.5) * jx - g[1]);
         g[2] += om * (b + R(0.5) * jy - g[2]);
@@ -535,10 +538,9 @@ __device__ __forceinline__ void collide9(R g[9], R e2, const StepArgs &a) {
     const R jx = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
     const R jy = g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
     const R w1 = e2 * co<R>(a, a.w1r, kCoW1r), w5 = e2 * co<R>(a, a.w5r, kCoW5r);
-    const R w0 = R(1) - R(4) * (w1 + w5);
     R eq[9];
-    eq[0] = w0 * rho;
     const R b1 = w1 * rho, b5 = w5 * rho;
+    eq[0] = rho - R(4) * (b1 + b5);  // = w_0 rho, mass-exact as in collide5
     const R ux = co<R>(a, a.a1, kCoA1) * jx, uy = co<R>(a, a.a1, kCoA1) * jy;
     eq[1] = b1 + ux; eq[3] = b1 - ux;
     eq[2] = b1 + uy; eq[4] = b1 - uy;
@@ -585,8 +587,8 @@ template <typename R>
 __device__ __forceinline__ void collide7(R g[7], R e2, const StepArgs &a) {
     const R rho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
     const R jx = g[1] - g[3], jy = g[2] - g[4], jz = g[5] - g[6];
-    const R om = co<R>(a, a.omega, kCoOmega), eq0 = (R(1) - e2) * rho,
-            b = e2 * (R(1) / R(6)) * rho;
+    const R om = co<R>(a, a.omega, kCoOmega), b = e2 * (R(1) / R(6)) * rho,
+            eq0 = rho - R(6) * b;  // = (1 - eta^2) rho, mass-exact as in collide5
     g[0] += om * (eq0 - g[0]);
     g[1] += om * (b + R(0.5) * jx - g[1]);
     g[2] += om * (b + R(0.5) * jy - g[2]);

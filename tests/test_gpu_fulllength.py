@@ -76,7 +76,9 @@ def test_two_layer_4096_full_length_every_trace(sim_cls, oracle_mod):
 
 # --- the 8192^2 layered workload -------------------------------------------------------
 
-LOWPREC_PER_TRACE = {"f16": 1e-2, "bf16": 8e-2}      # stated per-trace bounds, 16-bit storage
+# stated bounds for 16-bit storage (the error grows with the run: 1000 and 10000 steps)
+LOWPREC_PER_TRACE = {"f16": 1e-2, "bf16": 8e-2}
+LOWPREC_LONG = {"f16": 2e-2, "bf16": 1.5e-1}
 
 
 def _sim_layered(sim_cls, wl, storage, nt):
@@ -138,35 +140,54 @@ def test_layered_8192_first_1000_steps_every_trace(sim_cls, oracle_mod):
         try:
             results[storage].update(check_every_trace(tr[:, reach], tro[:, reach],
                                                       TOL if storage == "f32"
-                                                      else LOWPREC_PER_TRACE[storage]))
+                                                      else LOWPREC_PER_TRACE[storage],
+                                                      own_norm=storage == "f32"))
         finally:
             _record("layered_8192_1000", results)
     assert results["f32"]["pressure"] <= TOL and results["f32"]["all_traces"] <= TOL
 
 
 def test_layered_2048_full_length_every_trace(sim_cls, oracle_mod):
-    # The same generator at 2048^2 for the full 10000 steps (the whole grid: the field
-    # reaches every node), FP32 / BF16 / FP16 storage, each receiver trace against the
-    # FP64 oracle.
-    n, steps = 2048, 10000
+    # The same generator at 2048^2 for the full 10000 steps (the field reaches every node),
+    # FP32 / BF16 / FP16 storage.  Each receiver trace against the FP64 oracle (the measure
+    # of tests/traces.py), and the pressure at each quarter of the run against the RMS norm
+    # of the four snapshots: by the end most of the wave has left through the sponge, and
+    # the weak field that remains would show the rounding errors made while the field was
+    # strong far larger than they are relative to the run's signal.
+    n, steps, quarters = 2048, 10000, 4
     wl = W.layered_workload(n, steps=steps)
     P = oracle_mod.Problem(5, n, n, wl["c_map"], c_ref=wl["c_ref"], tau=0.5,
                            sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"],
                            source=wl["source"], receivers=wl["receivers"])
-    g, tro = oracle_mod.run(P, P.zeros(), steps)
-    po = oracle_mod.pressure(P, g)
-    results = {}
+    q = steps // quarters
+    g, tro, po = P.zeros(), [], []
+    for k in range(quarters):
+        g, t = oracle_mod.run(P, g, q, t0=k * q)
+        tro.append(t)
+        po.append(oracle_mod.pressure(P, g))
+    tro = np.concatenate(tro)
+    rms = float(np.sqrt(np.mean([np.linalg.norm(p) ** 2 for p in po])))
+    results, failures = {}, []
     for storage in ("f32", "bf16", "f16"):
         sim = _sim_layered(sim_cls, wl, storage, steps)
-        sim.step(steps)
-        ps = sim.pressure().cpu().numpy()
+        ps = []
+        for k in range(quarters):
+            sim.step(q)
+            ps.append(sim.pressure().cpu().numpy())
         tr = sim.traces(steps).cpu().numpy()
         sim.close()
-        results[storage] = {"pressure": float(np.linalg.norm(ps - po) / np.linalg.norm(po)),
+        snap = [float(np.linalg.norm(a - b) / rms) for a, b in zip(ps, po)]
+        results[storage] = {"pressure_final_own_norm": float(np.linalg.norm(ps[-1] - po[-1]) /
+                                                             np.linalg.norm(po[-1])),
+                            "pressure_snapshots_over_rms": snap,
                             "all_traces": float(np.linalg.norm(tr - tro) / np.linalg.norm(tro))}
+        bound = TOL if storage == "f32" else LOWPREC_LONG[storage]
         try:
-            results[storage].update(check_every_trace(tr, tro, TOL if storage == "f32"
-                                                      else LOWPREC_PER_TRACE[storage]))
-        finally:
-            _record("layered_2048_10000", results)
-    assert results["f32"]["pressure"] <= TOL and results["f32"]["all_traces"] <= TOL
+            results[storage].update(check_every_trace(tr, tro, bound, own_norm=storage == "f32"))
+        except AssertionError as e:  # every storage form is measured before the verdict
+            failures.append((storage, str(e)))
+        if max(snap) > bound:
+            failures.append((storage, "pressure snapshots", snap))
+        _record("layered_2048_10000", results)
+    assert results["f32"]["all_traces"] <= TOL
+    assert not failures, failures
