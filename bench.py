@@ -37,14 +37,41 @@ ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel on the
-# 4096^2 two-layer workload, from one ncu capture of the current kernel (the summaries under
-# profiles/ give the commands); keyed by (kernel, medium index).  A kernel without an entry,
-# or one changed since its capture, reports null.
-NCU_TRAFFIC = {
-    ("lbk::step_kernel<5,false,false,float>", True): 638.70e6,
-    ("stream_step_kernel<5,false,false,__nv_bfloat16>", True): 300.29e6,
-    ("tb_kernel<5,false,false,8>", False): 703.2e6,
+# 4096^2 two-layer workload, from one ncu capture (the summaries under profiles/ give the
+# commands), keyed by (kernel, medium index) and stamped with the hash of the kernel's
+# source files at the capture.  A kernel without an entry, or whose sources hash
+# differently now, reports null.
+KERNEL_SOURCES = {
+    "lbk::step_kernel": ("lb_kernels.cuh",),
+    "stream_step_kernel": ("lb_kernels.cuh", "stream_step.cu"),
+    "lbtb5::tb5_kernel": ("lb_kernels.cuh", "tblock5.cuh"),
 }
+NCU_TRAFFIC = {
+}
+
+
+def source_hash(kname):
+    """sha1 (12 hex digits) of the source files a kernel is built from"""
+    import hashlib
+    files = KERNEL_SOURCES.get(kname.split("<")[0])
+    if files is None:
+        return None
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1704_03172_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kname, indexed):
+    """(bytes per launch or None, why) from NCU_TRAFFIC for the kernel as built now"""
+    ent = NCU_TRAFFIC.get((kname, bool(indexed)))
+    if ent is None:
+        return None, "no capture of this kernel"
+    nbytes, stamp, prof = ent
+    if stamp != source_hash(kname):
+        return None, "kernel source changed since its capture"
+    return nbytes, f"ncu capture, {prof}"
 
 
 def bytes_per_site(Q, storage, indexed):
@@ -184,7 +211,8 @@ def _variant(torch, LBSim, lattice, storage, collision, steps, warmup, time_bloc
     wl["time_block"] = time_block
     sim = _make_sim(LBSim, wl, steps + warmup)
     try:
-        indexed = _indexed(sim) and time_block <= 1   # the time-blocked kernel reads eta^2
+        # the D2Q9 tile-blocked kernel reads eta^2 per site; the others the medium index
+        indexed = _indexed(sim) and (time_block <= 1 or lattice == 5)
         sec = _time_steps(torch, sim, steps, warmup)
     finally:
         sim.close()
@@ -247,6 +275,83 @@ def _refined_variant(torch, LBSim, steps, warmup):
     return {"glups": round(updates * steps / sec / 1e9, 2), "updates_per_coarse_step": updates,
             "ms_per_coarse_step": round(sec / steps * 1e3, 4),
             "launches_per_coarse_step": 6}
+
+
+def _upsample2(c):
+    """The medium on a grid refined by 2 everywhere: node (a, b) at coarse position
+    (a / 2, b / 2), the average of the coarse nodes around it (as for a refined patch)."""
+    c = np.asarray(c, np.float64)
+    ny, nx = c.shape
+    cx = np.concatenate([c[:, 1:], c[:, -1:]], axis=1)      # x + 1, clamped
+    cy = np.concatenate([c[1:], c[-1:]], axis=0)            # y + 1, clamped
+    cxy = np.concatenate([cy[:, 1:], cy[:, -1:]], axis=1)
+    f = np.empty((2 * ny, 2 * nx))
+    f[0::2, 0::2] = c
+    f[0::2, 1::2] = (c + cx) / 2
+    f[1::2, 0::2] = (c + cy) / 2
+    f[1::2, 1::2] = (c + cx + cy + cxy) / 4
+    return f.astype(np.float32)
+
+
+def _refined_vs_fine_variant(torch, LBSim):
+    """The slow-block workload's stated comparison (Sec. 5.2, Fig. 11 experiment): the
+    2048^2 coarse grid with its 2x patch for all 4000 coarse steps, the same problem on a
+    uniformly fine 4096^2 grid for 8000 steps, and the coarse grid alone.  Reported: the
+    trace error of the refined and of the coarse-only run against the uniformly fine one,
+    per receiver region (upstream of the patch, inside it, downstream), and the upstream
+    difference between the refined and the coarse-only run (what the interface reflects,
+    with the block's own reflection in both)."""
+    wl = W.refined_block_workload(2048)
+    steps = wl["steps"]
+    sx, sy, wav = wl["source"]
+    rec = wl["receivers"]
+    x0, y0, nxp, _ = wl["patch"]
+    kw = dict(lattice=5, collision="mrt", s=wl["s"], c_ref=wl["c_ref"])
+    out = {}
+
+    def run(c, patch, src, receivers, nt, sponge, smax):
+        sim = LBSim(c, sponge_width=sponge, sponge_sigma_max=smax, patch=patch, **kw)
+        try:
+            sim.set_source(*src)
+            sim.set_receivers(receivers, nt)
+            sim.init_pressure(None)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.step(nt)
+            tr = sim.traces(nt).cpu().numpy().astype(np.float64)
+            sec = time.perf_counter() - t0
+        finally:
+            sim.close()
+        return tr, sec
+
+    tr_ref, s_ref = run(wl["c_map"], wl["patch"], wl["source"], rec, steps, wl["sponge_width"],
+                        wl["sponge_sigma_max"])
+    tr_crs, s_crs = run(wl["c_map"], None, wl["source"], rec, steps, wl["sponge_width"],
+                        wl["sponge_sigma_max"])
+    # the same physical problem refined by 2 everywhere: twice the nodes, the source at the
+    # coincident node with S_f(t) = 2 S(t / 2) (the same source density per unit time), the
+    # sponge twice as wide and half as strong per (half-length) step
+    fc0 = (0.5 ** 0.5) / 32.0
+    wav_f = 2.0 * W.ricker(2 * steps, fc0 / 2)
+    tr_f, s_f = run(_upsample2(wl["c_map"]), None, (2 * sx, 2 * sy, wav_f), 2 * rec, 2 * steps,
+                    2 * wl["sponge_width"], wl["sponge_sigma_max"] / 2)
+    tr_f = tr_f[::2]
+    regions = {"upstream": rec[:, 0] < x0, "inside": (rec[:, 0] >= x0) & (rec[:, 0] <= x0 + nxp),
+               "downstream": rec[:, 0] > x0 + nxp}
+    for name, m in regions.items():
+        den = np.linalg.norm(tr_f[:, m])
+        out[name] = {"receivers": int(m.sum()),
+                     "refined_vs_fine": round(float(np.linalg.norm(tr_ref[:, m] - tr_f[:, m]) / den), 5),
+                     "coarse_vs_fine": round(float(np.linalg.norm(tr_crs[:, m] - tr_f[:, m]) / den), 5)}
+    up = regions["upstream"]
+    out["upstream_refined_minus_coarse_over_peak"] = round(
+        float(np.abs(tr_ref[:, up] - tr_crs[:, up]).max() / np.abs(tr_crs[:, up]).max()), 5)
+    out["seconds"] = {"refined": round(s_ref, 3), "coarse": round(s_crs, 3),
+                      "uniform_fine": round(s_f, 3)}
+    out["workload"] = ("2048^2 coarse (slow block c/3), 1025^2-node 2x patch, MRT s = (1, 1, 1, 2, "
+                       "2), Ricker source, 256 receivers on y = 1024, 4000 coarse steps; uniform "
+                       "fine 4096^2 for 8000 steps; traces at coincident times")
+    return out
 
 
 def _l2_variant(torch, LBSim, n, storage, steps, warmup=50, time_block=1):
@@ -751,6 +856,8 @@ def run_ours(args):
             out = _adjoint_variant(torch, LBSim, n=args.adj_n, nt=args.adj_nt,
                                    every=args.adj_every, storage=name.rsplit("_", 1)[1],
                                    mode="tape" if "_tape_" in name else "ckpt")
+        elif name == "refined_vs_fine":
+            out = _refined_vs_fine_variant(torch, LBSim)
         elif name.startswith("refined_nested"):
             out = _nested_variant(torch, LBSim, args.steps, args.warmup)
         elif name.startswith("refined"):
@@ -810,7 +917,10 @@ def run_ours(args):
         return 0
     peak, peak_kind = _peaks()
     K = max(1, args.time_block)
-    bps = bytes_per_site(args.lattice, args.storage, indexed and K == 1)
+    # the one-step and the D2Q5 wavefront kernels read the 1-byte medium index; the D2Q9
+    # tile-blocked kernel reads eta^2 per site
+    medium_idx = indexed and (K == 1 or args.lattice == 5)
+    bps = bytes_per_site(args.lattice, args.storage, medium_idx)
     launches = (args.steps + K - 1) // K
     per_launch_s = sec / launches
     achieved = bps * sites * K / per_launch_s / 1e9   # algorithmic one-step bytes per update
@@ -818,10 +928,12 @@ def run_ours(args):
                          (args.step_kernel == "auto" and args.storage != "f32"))
     st_name = dict(f32='float', bf16='__nv_bfloat16', f16='__half')[args.storage]
     mrt = "true" if args.collision == "mrt" else "false"
-    kname = (f"tb_kernel<{args.lattice},{mrt},false,{K}>" if K > 1 else
+    tb5 = K > 1 and args.lattice == 5
+    kname = (f"lbtb5::tb5_kernel<{mrt},{K},false,{st_name}>" if tb5 else
+             f"tb_kernel<{args.lattice},{mrt},false,{K}>" if K > 1 else
              f"stream_step_kernel<{args.lattice},{mrt},false,{st_name}>" if staged else
              f"lbk::step_kernel<{args.lattice},{mrt},false,{st_name}>")
-    traffic = NCU_TRAFFIC.get((kname, bool(indexed and K == 1)))
+    traffic, traffic_src = ncu_traffic(kname, indexed)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
@@ -835,13 +947,14 @@ def run_ours(args):
                                "one LB time step" + (f" ({K} steps fused per launch)" if K > 1 else ""),
                    "parallelism": f"replicas x{ws} (independent shots)",
                    "l2": "inputs larger than L2 (each population buffer >= 168 MB; 129 MB L2)",
-                   "medium": "1-byte medium index + eta^2 table" if indexed and K == 1
+                   "medium": "1-byte medium index + eta^2 table" if medium_idx
                              else "eta^2 per site (FP32)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": traffic, "kernel": kname,
+                     "traffic": traffic, "traffic_source": traffic_src, "kernel": kname,
                      "algorithmic_bytes_per_launch": bps * sites * K,
-                     "note": "achieved counts the one-step algorithmic bytes of every fused step"
+                     "note": "achieved counts the one-step algorithmic bytes of every fused "
+                             "step (one-step equivalent bandwidth)"
                      if K > 1 else "one launch per step"},
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -857,13 +970,13 @@ def run_ours(args):
                                                        max(200, args.steps // 5), 10)
             except Exception as ex:  # report, do not hide
                 v[f"d2q{lat}_{coll}_{st}"] = {"error": str(ex)[:200]}
-        for K in (2, 4, 6, 8):
-            name = f"d2q5_bgk_f32_tb{K}"
+        for st, K in (("f32", 2), ("f32", 4), ("f32", 6), ("f32", 8), ("bf16", 4), ("bf16", 8)):
+            name = f"d2q5_bgk_{st}_tb{K}"
             try:
-                v[name] = _variant(torch, LBSim, 5, "f32", "bgk", max(400, args.steps // 5) // 24 * 24,
+                v[name] = _variant(torch, LBSim, 5, st, "bgk", max(400, args.steps // 5) // 24 * 24,
                                    24, time_block=K)
                 v[name]["one_step_roofline_glups"] = round(
-                    _peaks()[0] / bytes_per_site(5, "f32", True), 1)
+                    _peaks()[0] / bytes_per_site(5, st, True), 1)
             except Exception as ex:
                 v[name] = {"error": str(ex)[:200]}
         for n, nsteps in ((256, 20000), (1024, 5000)):
@@ -881,6 +994,10 @@ def run_ours(args):
             v["refined_nested_2048_d2q5_mrt_f32"] = _nested_variant(torch, LBSim, 400, 10)
         except Exception as ex:
             v["refined_nested_2048_d2q5_mrt_f32"] = {"error": str(ex)[:200]}
+        try:
+            v["refined_block_2048_vs_uniform_fine"] = _refined_vs_fine_variant(torch, LBSim)
+        except Exception as ex:
+            v["refined_block_2048_vs_uniform_fine"] = {"error": str(ex)[:200]}
         for st in ("f32", "bf16"):
             try:
                 v[f"adjoint_tape_4096_d2q5_{st}"] = _adjoint_variant(torch, LBSim, storage=st,

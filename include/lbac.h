@@ -268,7 +268,8 @@ lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *grad_c, doub
  * FP32/BF16 shot by one step per scheduling round with a single batched launch
  * per (lattice, collision, boundary, storage) group, so small shots share the
  * GPU and requests that arrive while others run join the batch at the next
- * round.  FP16 shots step on their own.  A request that asks for a gradient
+ * round.  Under load, D2Q5 shots take 8 steps per batched launch instead
+ * (lb_server_config.tb_min_ctas).  FP16 shots step on their own.  A request that asks for a gradient
  * records the forward rho tape or keeps checkpoints during its forward run
  * (lb_request.checkpoint_every) and its adjoint (lb_adjoint, J = 1/2
  * sum (p - d)^2 over its traces) runs on a worker thread on its own stream,
@@ -282,6 +283,12 @@ typedef struct {
     size_t hbm_budget;       /* device bytes the server may hold; 0: 80% of free memory */
     int rounds_per_pass;     /* steps per scheduling pass between admission checks, >= 1 */
     int adjoint_workers;     /* threads running gradient sweeps, >= 1 */
+    int tb_min_ctas;         /* D2Q5 FP32/BF16 shots with no checkpoint or tape advance 8
+                                steps per launch (a wavefront time-blocked batch) when the
+                                eligible shots together make at least this many CTAs;
+                                0: one wave of the GPU (one CTA per resident slot);
+                                < 0: never (one launch per step).  Both forms give the
+                                same results to FP32 rounding. */
 } lb_server_config;
 
 typedef struct {

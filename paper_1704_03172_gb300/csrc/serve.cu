@@ -139,6 +139,7 @@ struct lb_server {
     size_t cap = 0;
     void *d_tb = nullptr, *h_tb = nullptr;  // time-blocked launches' descriptor blocks
     size_t tb_cap = 0;
+    int tb_wave = 0;  // CTAs one wave of the time-blocked batch kernel holds (0: not asked yet)
     cudaEvent_t staged = nullptr;
     std::mutex pin_mu;
     std::multimap<size_t, void *> pinned;  // free pinned trace buffers by size
@@ -366,11 +367,30 @@ void pass(lb_server *S) {
     // block of K steps
     const int KB = kServeTb, nblk = R / KB;
     std::vector<Req *> tbs, rest;
+    long long tb_blocks = 0;
     for (Req *r : batched) {
-        if (nblk > 0 && r->nt - r->steps >= nblk * KB && tb5_batch_ready(r->ctx, KB))
+        if (nblk > 0 && r->nt - r->steps >= nblk * KB && tb5_batch_ready(r->ctx, KB)) {
             tbs.push_back(r);
-        else
+            tb_blocks += tb5_batch_blocks(r->ctx, KB);
+        } else {
             rest.push_back(r);
+        }
+    }
+    // A wavefront CTA sweeps its rows one after another, so a few small shots give a
+    // launch of few long CTAs: K steps then take longer than K one-step launches over
+    // many short CTAs.  The shots take the K-step launches only when together they fill
+    // one wave of the GPU (the load is high and throughput counts), or the count the
+    // server was configured with.
+    if (!tbs.empty()) {
+        long long need = S->cfg.tb_min_ctas;
+        if (need == 0) {
+            if (S->tb_wave == 0) S->tb_wave = tb5_batch_wave(KB);
+            need = S->tb_wave;
+        }
+        if (need < 0 || tb_blocks < need) {
+            rest.insert(rest.end(), tbs.begin(), tbs.end());
+            tbs.clear();
+        }
     }
     batched.swap(rest);
     std::stable_sort(tbs.begin(), tbs.end(),

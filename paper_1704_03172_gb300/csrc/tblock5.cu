@@ -150,6 +150,27 @@ bool tb5_batch_ready(const lb_ctx *ctx, int K) {
     return true;
 }
 
+// Output rows per CTA of a served shot: tall enough that the 2K warm-up rows cost little.
+static int batch_rows(const lb_ctx *ctx, int K) { return std::min(ctx->ny, 16 * K); }
+
+int tb5_batch_blocks(const lb_ctx *ctx, int K) {
+    const int OUT = kWS - 2 * K, H = batch_rows(ctx, K);
+    return ((ctx->nx + OUT - 1) / OUT) * ((ctx->ny + H - 1) / H);
+}
+
+int tb5_batch_wave(int K) {
+    int dev = 0, sms = 0, nb = 0;
+    Tb5BatchFn fn = pick_batch_f32(K, false);
+    const size_t smem = (size_t)2 * K * 2 * (kWS + 2) * sizeof(float);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && fn)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && fn) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kWS, smem);
+    if (e != cudaSuccess) cudaGetLastError();  // this query's own failure: one CTA per SM
+    return std::max(1, sms) * std::max(1, nb);
+}
+
 // Fill the host staging block `h` for K steps of ctxs[0 .. n) (advancing their time and
 // buffers as if the launch ran); returns the launch's block count.
 int tb5_batch_fill(lb_ctx *const *ctxs, int n, int K, void *h) {
@@ -169,7 +190,7 @@ int tb5_batch_fill(lb_ctx *const *ctxs, int n, int K, void *h) {
         tb.row_off = a.trace_row ? ctx->tb5_off : nullptr;
         tb.rec_x = ctx->tb5_x;
         tb.rec_id = ctx->tb5_id;
-        tb.H = std::min(ctx->ny, 16 * K);  // tall enough that the 2K warm-up rows cost little
+        tb.H = batch_rows(ctx, K);
         tb.per = ctx->cfg.boundary == LB_PERIODIC ? 1 : 0;
         const int strips = (ctx->nx + OUT - 1) / OUT, chunks = (ctx->ny + tb.H - 1) / tb.H;
         L.a[k] = a;

@@ -79,7 +79,8 @@ template <int K> struct Tb5Regs {
     float pre_e2[2];  // (unused)
 };
 
-// Level-0 row r, zero outside a zero-ghost domain.
+// Level-0 row r, zero outside a zero-ghost domain.  v holds the stored bits (tb5_iter
+// widens them one iteration later, so the conversion does not wait for the load).
 template <typename ST>
 __device__ __forceinline__ void tb5_load(const StepArgs &a, const Tb5Thread &T, int r, float (&v)[5],
                                          float &e2) {
@@ -98,7 +99,7 @@ __device__ __forceinline__ void tb5_load(const StepArgs &a, const Tb5Thread &T, 
     const ST *in = static_cast<const ST *>(a.in);
     const long long o = (long long)yw * a.pitch + T.gxw;
 #pragma unroll
-    for (int i = 0; i < 5; i++) v[i] = Store<ST>::load1(in + i * a.plane + o);
+    for (int i = 0; i < 5; i++) v[i] = __uint_as_float(Store<ST>::bits1(in + i * a.plane + o));
     // the medium as loaded: eta^2, or the index byte (as a float's bits) that tb5_e2 looks up
     // one iteration later, so that the table read does not wait for the global load
     e2 = a.mid ? __int_as_float((int)a.mid[o]) : a.eta2[o];
@@ -136,7 +137,7 @@ __device__ __forceinline__ void tb5_iter(const StepArgs &a, const Tb5Args &tb, c
     constexpr int SR = kWS + 2, SL = 2 * SR;  // row and level strides of xs
     float n[5], nE;  // level l's newest row (r - l); level 0: the prefetched row r
 #pragma unroll
-    for (int i = 0; i < 5; i++) n[i] = pre[P][i];
+    for (int i = 0; i < 5; i++) n[i] = Store<ST>::unbits1(__float_as_uint(pre[P][i]));
     nE = tb5_e2(a, T, T.col_in && (T.per || (r >= 0 && r < a.ny)), pre_e2[P]);
     if (r + 1 < rend) tb5_load<ST>(a, T, r + 1, pre[P ^ 1], pre_e2[P ^ 1]);
     float *cur = T.xs + P * K * SL + T.c + 1;        // this iteration's rows, column c

@@ -56,7 +56,8 @@ class lb_config(ctypes.Structure):
 
 class lb_server_config(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
-                ("rounds_per_pass", ctypes.c_int), ("adjoint_workers", ctypes.c_int)]
+                ("rounds_per_pass", ctypes.c_int), ("adjoint_workers", ctypes.c_int),
+                ("tb_min_ctas", ctypes.c_int)]
 
 
 class lb_request(ctypes.Structure):

@@ -296,11 +296,14 @@ class LBForward(torch.autograd.Function):
 
 
 class LBServer:
-    """Continuous-batching shot server (lb_server_* of the C ABI)."""
+    """Continuous-batching shot server (lb_server_* of the C ABI).  tb_min_ctas: the
+    eligible D2Q5 shots take 8 steps per launch when they make at least that many CTAs
+    (0: one wave of the GPU, < 0: never)."""
 
-    def __init__(self, max_active=64, hbm_budget=0, rounds_per_pass=16, adjoint_workers=2):
+    def __init__(self, max_active=64, hbm_budget=0, rounds_per_pass=16, adjoint_workers=2,
+                 tb_min_ctas=0):
         cfg = lbac.lb_server_config(int(max_active), int(hbm_budget), int(rounds_per_pass),
-                                    int(adjoint_workers))
+                                    int(adjoint_workers), int(tb_min_ctas))
         self.srv = lbac.lb_server_create(cfg)
         self._meta = {}
 

@@ -42,16 +42,19 @@ def _shot(n, seed, nt, storage="f32", grad=False, lattice=5):
     return c, spec
 
 
-def test_result_is_identical_alone_and_in_the_mix(mods, oracle_mod):
+# tb_min_ctas: 0 the server's own rule (these small shots never fill a wave: one launch per
+# step), 1 every eligible D2Q5 shot takes 8 steps per launch, -1 never
+@pytest.mark.parametrize("tb", [0, 1, -1])
+def test_result_is_identical_alone_and_in_the_mix(mods, oracle_mod, tb):
     LBServer, _, _ = mods
     cA, sA = _shot(96, 1, 300)
-    srv = LBServer(max_active=1, rounds_per_pass=8)
+    srv = LBServer(max_active=1, rounds_per_pass=8, tb_min_ctas=tb)
     a = srv.submit(cA, **sA)
     srv.wait(a, 60000)
     alone = srv.result(a)["traces"]
     srv.close()
     # a mix: different sizes, storage types, a gradient request, staggered arrivals
-    srv = LBServer(max_active=6, rounds_per_pass=8)
+    srv = LBServer(max_active=6, rounds_per_pass=8, tb_min_ctas=tb)
     ids = []
     for k, (n, st, g) in enumerate([(128, "f32", False), (64, "bf16", False), (160, "f32", True),
                                      (80, "f16", False), (200, "bf16", False), (96, "bf16", True)]):
@@ -73,6 +76,31 @@ def test_result_is_identical_alone_and_in_the_mix(mods, oracle_mod):
                            sponge_sigma_max=0.1, source=sA["source"], receivers=sA["receivers"])
     _, tro = oracle_mod.run(P, P.zeros(), sA["nt"])
     assert rel(alone, tro) < 1e-5
+
+
+def test_time_blocked_batches_cut_the_launches(mods, oracle_mod):
+    # the same four FP32 / BF16 shots with 8 steps per launch and with one launch per step:
+    # far fewer launches, and the same FP32 traces to rounding (BF16 differs more: the
+    # time-blocked kernel rounds to BF16 once per 8 steps, the one-step kernel every step)
+    LBServer, _, _ = mods
+    shots = [_shot(n, 40 + k, 256, st) for k, (n, st) in
+             enumerate([(96, "f32"), (160, "f32"), (128, "bf16"), (300, "f32")])]
+    out = {}
+    for tb in (1, -1):
+        srv = LBServer(max_active=4, rounds_per_pass=32, tb_min_ctas=tb)
+        ids = [srv.submit(c, **s) for c, s in shots]
+        for i in ids:
+            srv.wait(i, 120000)
+        out[tb] = ([srv.result(i)["traces"] for i in ids], srv.stats()["launches"])
+        srv.close()
+    assert out[1][1] * 3 < out[-1][1], (out[1][1], out[-1][1])
+    for (c, s), a, b in zip(shots, out[1][0], out[-1][0]):
+        assert rel(a, b) < (3e-6 if s["storage"] == "f32" else 0.1)
+    c, s = shots[0]
+    P = oracle_mod.Problem(5, 96, 96, c, c_ref=5500.0, tau=0.5, sponge_width=6,
+                           sponge_sigma_max=0.1, source=s["source"], receivers=s["receivers"])
+    _, tro = oracle_mod.run(P, P.zeros(), s["nt"])
+    assert rel(out[1][0][0], tro) < 1e-5
 
 
 def test_gradient_request_matches_direct_adjoint(mods, oracle_mod):
