@@ -185,7 +185,7 @@ def _make_sim(LBSim, wl, nt_cap):
                 s=wl.get("s"), storage=wl["storage"], c_ref=wl["c_ref"],
                 sponge_width=wl["sponge_width"], sponge_sigma_max=wl["sponge_sigma_max"],
                 w_ref=wl["w_ref"], time_block=wl.get("time_block", 1),
-                step_kernel=wl.get("step_kernel", "auto"))
+                step_kernel=wl.get("step_kernel", "auto"), streaming=wl.get("streaming", "ab"))
     sx, sy, wav = wl["source"]
     sim.set_source(sx, sy, wav)
     sim.set_receivers(wl["receivers"], nt_cap)
@@ -206,9 +206,11 @@ def _time_steps(torch, sim, steps, warmup):
     return e0.elapsed_time(e1) / 1e3
 
 
-def _variant(torch, LBSim, lattice, storage, collision, steps, warmup, time_block=1):
+def _variant(torch, LBSim, lattice, storage, collision, steps, warmup, time_block=1,
+             streaming="ab"):
     wl = _workload(lattice, storage, collision)
     wl["time_block"] = time_block
+    wl["streaming"] = streaming
     sim = _make_sim(LBSim, wl, steps + warmup)
     try:
         # the D2Q9 tile-blocked kernel reads eta^2 per site; the others the medium index
@@ -219,8 +221,13 @@ def _variant(torch, LBSim, lattice, storage, collision, steps, warmup, time_bloc
     sites = N_GRID * N_GRID
     glups = sites * steps / sec / 1e9
     bps = bytes_per_site(lattice, storage, indexed)
-    return {"glups": round(glups, 2), "bytes_per_site": bps,
-            "achieved_gbs": round(glups * bps, 1), "ms_per_step": round(sec / steps * 1e3, 4)}
+    out = {"glups": round(glups, 2), "bytes_per_site": bps,
+           "achieved_gbs": round(glups * bps, 1), "ms_per_step": round(sec / steps * 1e3, 4)}
+    if streaming == "aa":
+        out["frac_of_measured_hbm"] = round(glups * bps / _peaks()[0], 4)
+        out["population_gb"] = round(lattice * sites * ELEM_BYTES[storage] / 1e9, 3)
+        out["streaming"] = "in place: one population buffer (two-buffer form: twice this)"
+    return out
 
 
 _LAYERED = {}
@@ -869,6 +876,10 @@ def run_ours(args):
             st = next(p for p in parts if p in ELEM_BYTES)
             out = _l2_variant(torch, LBSim, int(parts[2]), st, args.steps, args.warmup,
                               time_block=8 if "tb8" in parts else 1)
+        elif name.startswith("aa_"):  # aa_d2q<Q>_<collision>_<storage>: in-place streaming
+            _, q, coll, st = name.split("_")
+            out = _variant(torch, LBSim, int(q[3:]), st, coll, args.steps, args.warmup,
+                           streaming="aa")
         elif name.startswith("d3q7"):
             out = _d3q7_variant(torch, LBSim, name.rsplit("_", 1)[1])
         elif name.startswith("layered_8192"):  # layered_8192_<storage>
@@ -977,6 +988,13 @@ def run_ours(args):
                                    24, time_block=K)
                 v[name]["one_step_roofline_glups"] = round(
                     _peaks()[0] / bytes_per_site(5, st, True), 1)
+            except Exception as ex:
+                v[name] = {"error": str(ex)[:200]}
+        for lat, st, coll in ((5, "f32", "bgk"), (5, "bf16", "bgk"), (9, "f32", "mrt")):
+            name = f"aa_d2q{lat}_{coll}_{st}"
+            try:
+                v[name] = _variant(torch, LBSim, lat, st, coll, max(200, args.steps // 5), 10,
+                                   streaming="aa")
             except Exception as ex:
                 v[name] = {"error": str(ex)[:200]}
         for n, nsteps in ((256, 20000), (1024, 5000)):

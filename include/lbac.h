@@ -117,9 +117,17 @@ typedef struct {
     int nz;                   /* planes of a 3-D grid (LB_D3Q7 only, BGK, no patch, no time
                                  blocking); <= 1: 2-D.  3-D arrays are [nz][ny][nx] (c_map,
                                  pressure) and [Q][nz][ny][nx] (state). */
+    int streaming;            /* LB_STREAM_AB (0): each step pulls from one population buffer
+                                 into the other (two buffers).  LB_STREAM_AA (1): in place, one
+                                 buffer (half the population memory): steps alternate between
+                                 a site-local update and a neighbour exchange in which every
+                                 slot is read and written by one thread only.  D2Q5 / D2Q9,
+                                 FP32 or BF16, no patch, time blocking, slab, checkpoint, tape
+                                 or adjoint.  Results equal LB_STREAM_AB's bit for bit. */
 } lb_config;
 
 enum { LB_STEP_AUTO = 0, LB_STEP_DIRECT = 1, LB_STEP_STAGED = 2 };
+enum { LB_STREAM_AB = 0, LB_STREAM_AA = 1 };
 enum { LB_MAX_PATCHES = 3 };  /* nesting depth: ratio up to 8 to the coarse grid */
 
 /* Fill *cfg with defaults: D2Q5, BGK tau = 1/2, F32, zero ghost, no sponge,

@@ -1,0 +1,322 @@
+// aa.cu -- in-place streaming: one population buffer instead of two (the "AA" pattern).
+//
+// The pull step streams g_i(x, t) = h_i(x - c_i, t - 1) (Eq. BGK-LB) from one buffer and
+// writes the collided h(t) to the other.  Here the steps alternate between two forms that
+// both work in one buffer:
+//   site-local step   the buffer holds g(t) at its own site, population i in slot i.  The
+//                     thread of site x reads slot i at x, collides, and writes h_i(x, t)
+//                     to slot opp(i) at x.
+//   exchange step     the buffer holds h(t - 1) at its own site, population i in slot
+//                     opp(i).  The thread of site x reads g_i(x, t) = h_i(x - c_i, t - 1)
+//                     from slot opp(i) at x - c_i, collides, and writes h_i(x, t) to slot i
+//                     at x + c_i, which is g_i(x + c_i, t + 1) for the next site-local step.
+// In the exchange step slot i at site y is read and written by the thread of site y - c_i
+// alone (its population opp(i) in, its population i out); in the site-local step a thread
+// touches only its own site.  No slot is shared between threads in either form, so one
+// launch per step needs no barrier and no second buffer.  Under the zero ghost no site
+// writes slot i at the sites whose x - c_i lies outside the domain: their own threads write
+// the zero that the ghost streams in.
+//
+// The per-site arithmetic is that of step_kernel (collide_sites: collision, source,
+// sponge; receivers summed in the same order), so results equal the two-buffer step bit for
+// bit.  A thread owns V consecutive sites of a row (4 FP32, 8 16-bit) as step_kernel does.
+// The site-local step moves 16-byte vectors only.  The exchange step pulls with the same
+// vector-and-shuffle loads as step_kernel; of its pushes, those with no x component are
+// 16-byte vectors and the two (D2Q9: six) that move one site in x are element stores.
+//
+// Loads and stores of one thread's slots never meet another thread's: a vector load of the
+// exchange step also covers one element that the neighbouring lane (or, at a warp's edge,
+// the neighbouring warp) owns and may be writing; that element is only passed on by the
+// shuffle to the lane that owns it, never used, and at a warp's edge the owner loads it
+// itself.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "lb_kernels.cuh"
+#include "lb_runtime.h"
+
+namespace lbaa {
+
+using namespace lbk;
+
+struct AaRec {           // receivers by row, x ascending (tb5_set_receivers' lists)
+    const int *row_off;  // [ny + 1], or nullptr: no receivers this step
+    const int *rec_x;
+    const int *rec_id;
+};
+
+// Row of a site in direction dy from row y: wrapped, or -1 outside a zero-ghost domain.
+template <bool PERIODIC> __device__ __forceinline__ int row_at(int y, int dy, int ny) {
+    int r = y + dy;
+    if (r < 0 || r >= ny) {
+        if (!PERIODIC) return -1;
+        r = r < 0 ? r + ny : r - ny;
+    }
+    return r;
+}
+
+// Push a thread's V values of one population one site along x into the target row dst:
+// the value of site x goes to x + CX.  A lane stores a 16-byte vector when every element's
+// source site is real and held in its warp (the element next to its own sites comes from
+// the neighbouring lane by a shuffle), else element by element; the element a warp's edge
+// lane cannot get is stored by the neighbouring warp's edge lane, and the periodic images
+// by the owners of the first and last site.  Every lane of the warp calls it.
+template <int CX, bool PERIODIC, typename ST>
+__device__ __forceinline__ void push_x(ST *dst, const float (&v)[Store<ST>::V], int x0, int lane,
+                                       int nx, bool active) {
+    constexpr int V = Store<ST>::V;
+    if (CX == 1) {  // position p takes site p - 1
+        const float left = __shfl_up_sync(0xffffffffu, v[V - 1], 1);
+        if (!active) return;
+        if (lane > 0) {
+            float out[V];
+            out[0] = left;
+#pragma unroll
+            for (int k = 1; k < V; k++) out[k] = v[k - 1];
+            Store<ST>::storeV(dst + x0, out);  // positions past nx are padding
+        } else {  // position x0 is stored by the previous warp's last lane
+#pragma unroll
+            for (int k = 1; k < V; k++)
+                if (x0 + k < nx) Store<ST>::store1(dst + x0 + k, v[k - 1]);
+        }
+        if (lane == 31 && x0 + V < nx) Store<ST>::store1(dst + x0 + V, v[V - 1]);
+        if (PERIODIC) {  // site nx - 1 wraps to position 0
+            const int last = nx - 1 - x0;
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (k == last) Store<ST>::store1(dst, v[k]);
+        }
+    } else {  // CX == -1: position p takes site p + 1
+        const float right = __shfl_down_sync(0xffffffffu, v[0], 1);
+        if (!active) return;
+        if (lane < 31 && x0 + V < nx) {
+            float out[V];
+#pragma unroll
+            for (int k = 0; k + 1 < V; k++) out[k] = v[k + 1];
+            out[V - 1] = right;
+            Store<ST>::storeV(dst + x0, out);
+        } else {  // position x0 + V - 1 takes the next warp's site, or none
+#pragma unroll
+            for (int k = 0; k + 1 < V; k++)
+                if (x0 + k + 1 < nx) Store<ST>::store1(dst + x0 + k, v[k + 1]);
+        }
+        if (lane == 0 && x0 > 0) Store<ST>::store1(dst + x0 - 1, v[0]);
+        if (PERIODIC && x0 == 0) Store<ST>::store1(dst + nx - 1, v[0]);  // site 0 wraps
+    }
+}
+
+// The exchange step's stores: h_i(x) into slot i at x + c_i, and the ghost's zeros.  Every
+// lane of the warp calls it (inactive lanes take part in the shuffles only).
+template <int Q, bool PERIODIC, typename ST>
+__device__ __forceinline__ void exchange_stores(const StepArgs &a, ST *pop,
+                                                const float (&g)[Q][Store<ST>::V], int y, int x0,
+                                                int lane, bool active) {
+    constexpr int V = Store<ST>::V;
+    const long long row = (long long)y * a.pitch;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {  // h_i(x) into slot i at x + c_i
+        const int cx = Lat<Q>::cx(i);
+        ST *plane = pop + i * a.plane;
+        const int rd = row_at<PERIODIC>(y, Lat<Q>::cy(i), a.ny);  // warp-uniform
+        if (rd >= 0) {
+            ST *dst = plane + (long long)rd * a.pitch;
+            if (cx == 0) {
+                if (active) Store<ST>::storeV(dst + x0, g[i]);  // padding sites carry zeros
+            } else if (cx == 1) {
+                push_x<1, PERIODIC, ST>(dst, g[i], x0, lane, a.nx, active);
+            } else {
+                push_x<-1, PERIODIC, ST>(dst, g[i], x0, lane, a.nx, active);
+            }
+        }
+        if (!PERIODIC && i != 0 && active) {
+            // the ghost's zero in slot i of this thread's sites x whose x - c_i lies outside
+            // (no site pushes there)
+            const bool row_out = row_at<false>(y, -Lat<Q>::cy(i), a.ny) < 0;
+            if (row_out) {
+                float z[V];
+#pragma unroll
+                for (int k = 0; k < V; k++) z[k] = 0.f;
+                Store<ST>::storeV(plane + row + x0, z);
+            } else if (cx == 1 && x0 == 0) {
+                Store<ST>::store1(plane + row, 0.f);
+            } else if (cx == -1 && a.nx - 1 - x0 < V) {
+                Store<ST>::store1(plane + row + a.nx - 1, 0.f);
+            }
+        }
+    }
+}
+
+// Receivers, medium and collision of one thread's V sites, as step_kernel does them.
+template <int Q, bool MRT, typename ST>
+__device__ __forceinline__ void collide_site_vector(const StepArgs &a, const AaRec &r,
+                                                    const float *tab,
+                                                    float (&g)[Q][Store<ST>::V], int y, int x0) {
+    constexpr int V = Store<ST>::V;
+    const long long row = (long long)y * a.pitch;
+    float e2s[V];
+    if (a.mid) {  // 1-byte medium index, eta^2 from the shared table
+        const uint8_t *mp = a.mid + row + x0;
+        uint32_t w[V / 4];
+        if (V == 4) {
+            w[0] = *reinterpret_cast<const uint32_t *>(mp);
+        } else {
+            const uint2 u = *reinterpret_cast<const uint2 *>(mp);
+            w[0] = u.x;
+            w[V / 4 - 1] = u.y;
+        }
+#pragma unroll
+        for (int k = 0; k < V; k++) e2s[k] = tab[(w[k >> 2] >> (8 * (k & 3))) & 0xffu];
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; k += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(a.eta2 + row + x0 + k);
+            e2s[k] = v.x; e2s[k + 1] = v.y; e2s[k + 2] = v.z; e2s[k + 3] = v.w;
+        }
+    }
+    if (a.trace_row && r.row_off) {  // receivers among this thread's sites (x ascending)
+        int lo = r.row_off[y];
+        const int hi = r.row_off[y + 1];
+        if (lo < hi) {
+            int h = hi;
+            while (lo < h) {
+                const int m = (lo + h) >> 1;
+                if (r.rec_x[m] < x0)
+                    lo = m + 1;
+                else
+                    h = m;
+            }
+            for (; lo < hi && r.rec_x[lo] < x0 + V; lo++) {
+                const int k = r.rec_x[lo] - x0;
+                float rho = 0.f;
+#pragma unroll
+                for (int kk = 0; kk < V; kk++)
+                    if (kk == k) {
+#pragma unroll
+                        for (int i = 0; i < Q; i++) rho += g[i][kk];
+                    }
+                const int q = r.rec_id[lo];
+                a.trace_row[a.rec_col ? a.rec_col[q] : q] =
+                    cs2_of<Q>(a.eta2[row + x0 + k], a) * rho;
+            }
+        }
+    }
+    // collision, source and sponge as in finish_sites (the damping variant for a warp that
+    // holds sponge or padding sites; elsewhere both give the same values)
+    const int dyz = row_face_dist<Q>(y, a);
+    bool edge = (a.sponge_w > 0 && (dyz < a.sponge_w || x0 < a.sponge_w ||
+                                    x0 + V - 1 >= a.nx - a.sponge_w)) ||
+                x0 + V > a.nx;
+    edge = __any_sync(__activemask(), edge);
+    const bool has_src = (y == a.src_y) && (a.src_x >= x0) && (a.src_x < x0 + V) &&
+                         a.src_tab != nullptr && a.t < a.src_nt;
+    if (!edge)
+        collide_sites<Q, MRT, V, false>(g, e2s, a, x0, dyz, has_src);
+    else
+        collide_sites<Q, MRT, V, true>(g, e2s, a, x0, dyz, has_src);
+}
+
+
+template <int Q, bool MRT, bool PERIODIC, typename ST, bool EXCHANGE>
+__global__ void __launch_bounds__(kThreads, Q == 5 ? (sizeof(ST) == 4 ? 5 : 3)
+                                                   : (sizeof(ST) == 4 ? 4 : 2))
+    aa_step_kernel(const StepArgs a, const AaRec r) {
+    pdl_trigger_and_wait();
+    __shared__ float tab[kThreads];
+    if (a.mid) {  // block-uniform
+        tab[threadIdx.x] = a.mid_tab[threadIdx.x];
+        __syncthreads();
+    }
+    constexpr int V = Store<ST>::V;
+    const int lane = threadIdx.x & 31;
+    const int wid = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int y = wid / a.segs;
+    if (y >= a.ny) return;  // warp-uniform
+    const int x0 = (wid - y * a.segs) * (32 * V) + lane * V;
+    const bool active = x0 < a.nx;
+    ST *pop = static_cast<ST *>(a.out);  // a.in == a.out
+    const long long row = (long long)y * a.pitch;
+    float g[Q][V];
+    if constexpr (!EXCHANGE) {
+        if (!active) return;  // no shuffles in this form
+#pragma unroll
+        for (int i = 0; i < Q; i++) Store<ST>::loadV(pop + i * a.plane + row + x0, g[i]);
+    } else {  // g_i(x) = slot opp(i) at x - c_i: the pull of step_kernel from the other slot
+        uint4 q[Q];
+        uint32_t e[Q];
+        bool absent[Q];
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const int rs = row_at<PERIODIC>(y, -Lat<Q>::cy(i), a.ny);
+            const ST *src = rs < 0 ? nullptr
+                                   : pop + Lat<Q>::opp(i) * a.plane + (long long)rs * a.pitch;
+            absent[i] = src == nullptr;
+            if (Lat<Q>::cx(i) == 1)
+                pull_issue<1, PERIODIC>(src, x0, lane, a.nx, active, q[i], e[i]);
+            else if (Lat<Q>::cx(i) == -1)
+                pull_issue<-1, PERIODIC>(src, x0, lane, a.nx, active, q[i], e[i]);
+            else
+                pull_issue<0, PERIODIC>(src, x0, lane, a.nx, active, q[i], e[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            if (Lat<Q>::cx(i) == 1)
+                pull_finish<1, PERIODIC, ST>(absent[i], x0, lane, a.nx, q[i], e[i], g[i]);
+            else if (Lat<Q>::cx(i) == -1)
+                pull_finish<-1, PERIODIC, ST>(absent[i], x0, lane, a.nx, q[i], e[i], g[i]);
+            else
+                pull_finish<0, PERIODIC, ST>(absent[i], x0, lane, a.nx, q[i], e[i], g[i]);
+        }
+    }
+    // the exchange step keeps inactive lanes for the shuffles of its pushes
+    if (active) collide_site_vector<Q, MRT, ST>(a, r, tab, g, y, x0);
+    if constexpr (!EXCHANGE) {  // h_i(x) into slot opp(i) at x
+#pragma unroll
+        for (int i = 0; i < Q; i++) Store<ST>::storeV(pop + Lat<Q>::opp(i) * a.plane + row + x0, g[i]);
+    } else {
+        exchange_stores<Q, PERIODIC, ST>(a, pop, g, y, x0, lane, active);
+    }
+}
+
+using AaFn = void (*)(const StepArgs, const AaRec);
+
+template <int Q, typename ST, bool EX> AaFn aa_fn(bool mrt, bool per) {
+    if (mrt) return per ? aa_step_kernel<Q, true, true, ST, EX> : aa_step_kernel<Q, true, false, ST, EX>;
+    return per ? aa_step_kernel<Q, false, true, ST, EX> : aa_step_kernel<Q, false, false, ST, EX>;
+}
+template <typename ST> AaFn aa_pick(int Q, bool mrt, bool per, bool ex) {
+    if (Q == 9) return ex ? aa_fn<9, ST, true>(mrt, per) : aa_fn<9, ST, false>(mrt, per);
+    return ex ? aa_fn<5, ST, true>(mrt, per) : aa_fn<5, ST, false>(mrt, per);
+}
+
+}  // namespace lbaa
+
+using namespace lbaa;
+using namespace lbrt;
+
+// n steps in place.  The buffer's form alternates: g(t) at its own site (ctx->raw) before a
+// site-local step, h(t - 1) in the opposite slots (ctx->swap) before an exchange step.
+lb_status aa_step(lb_ctx *ctx, int n) {
+    const bool mrt = ctx->cfg.collision == LB_MRT, per = ctx->cfg.boundary == LB_PERIODIC;
+    const bool bf = ctx->cfg.storage == LB_BF16;
+    for (int k = 0; k < n; k++) {
+        const bool ex = !ctx->raw;  // the state is h(t - 1) in the opposite slots
+        StepArgs a = base_args(ctx);
+        a.in = ctx->pop[0];
+        a.out = ctx->pop[0];
+        a.t = ctx->t;
+        const long long row = ctx->t - ctx->t_rec0;
+        a.trace_row = (ctx->trace && row >= 0 && row < ctx->trace_cap)
+                          ? ctx->trace + row * ctx->nrec
+                          : nullptr;
+        AaRec r{a.trace_row ? ctx->tb5_off : nullptr, ctx->tb5_x, ctx->tb5_id};
+        AaFn fn = bf ? aa_pick<__nv_bfloat16>(ctx->Q, mrt, per, ex)
+                     : aa_pick<float>(ctx->Q, mrt, per, ex);
+        // a warp per row segment of 32 V sites, as step_kernel (base_args: segs, main_blocks)
+        cudaError_t e = launch_pdl(fn, dim3(a.main_blocks), dim3(kThreads), 0, ctx->stream, a, r);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "in-place step launch");
+        ctx->raw = ex;  // after an exchange step: g(t + 1) at its own site
+        ctx->swap = !ex;
+        ctx->t += 1;
+    }
+    return LB_OK;
+}

@@ -603,6 +603,8 @@ extern "C" lb_status lb_record_rho(lb_ctx *ctx, int nt_capacity) {
     if (!ctx) return LB_EINVAL;
     if (ctx->slab_nyg) return fail(ctx, LB_ESTATE, "a row slab has no adjoint");
     if (nt_capacity < 0) return fail(ctx, LB_EINVAL, "nt_capacity < 0");
+    if (nt_capacity > 0 && ctx->aa)
+        return fail(ctx, LB_ESTATE, "no rho tape with in-place streaming (LB_STREAM_AA)");
     if (nt_capacity > 0 && (ctx->Q == 7 || ctx->refined || ctx->cfg.storage == LB_F64))
         return fail(ctx, LB_ESTATE, "the rho tape serves the 2-D adjoint without a patch "
                     "(FP32, BF16 or FP16 storage)");
@@ -625,6 +627,8 @@ extern "C" lb_status lb_checkpoint_every(lb_ctx *ctx, int every) {
     if (ctx->slab_nyg) return fail(ctx, LB_ESTATE, "a row slab has no adjoint");
     if (every > 0 && ctx->Q == 7) return fail(ctx, LB_ESTATE, "the adjoint is 2-D (D2Q5 / D2Q9)");
     if (every < 0) return fail(ctx, LB_EINVAL, "every < 0");
+    if (every > 0 && ctx->aa)
+        return fail(ctx, LB_ESTATE, "no checkpoints with in-place streaming (LB_STREAM_AA)");
     if (every > 0 && (ctx->refined || (ctx->cfg.storage != LB_F32 && ctx->cfg.storage != LB_BF16)))
         return fail(ctx, LB_ESTATE, "the adjoint needs an FP32 or BF16 context without a patch");
     ctx->ckpt_every = every;
@@ -637,6 +641,7 @@ extern "C" lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *g
     if (!ctx) return LB_EINVAL;
     if (ctx->slab_nyg) return fail(ctx, LB_ESTATE, "a row slab has no adjoint");
     if (ctx->cfg.storage == LB_F64) return fail(ctx, LB_ESTATE, "no adjoint for LB_F64 (test only)");
+    if (ctx->aa) return fail(ctx, LB_ESTATE, "no adjoint with in-place streaming (LB_STREAM_AA)");
     if (nt < 1) return fail(ctx, LB_EINVAL, "nt < 1");
     if (ctx->nrec > 0 && !dJdp) return fail(ctx, LB_EINVAL, "dJdp is NULL");
     // The forward rho tape (lb_record_rho) covers the nt steps: no checkpoints, no replays.

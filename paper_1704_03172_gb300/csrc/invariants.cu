@@ -24,6 +24,7 @@ using namespace lbk;
 struct InvArgs {
     const void *pop;     // populations
     int raw;             // 1: pop holds g(t) unshifted; 0: post-collision h(t-1) (pull)
+    int swap;            // in-place streaming: h(t-1)'s population i in slot opp(i)
     int periodic;
     const float *eta2;   // per-site eta^2 [ny][pitch], or nullptr when c_map is given
     const float *c_map;  // per-site c [ny][nx] (used when eta2 == nullptr)
@@ -92,7 +93,8 @@ __global__ void __launch_bounds__(256) rows_kernel(InvArgs a, double *partial) {
                 } else {
                     ok = xs >= 0 && xs < a.nx && ys >= 0 && ys < a.ny;
                 }
-                if (ok) g = Store<ST>::load1(pop + i * a.plane + (long long)ys * a.pitch + xs) *
+                const int slot = a.swap ? Lat<Q>::opp(i) : i;
+                if (ok) g = Store<ST>::load1(pop + slot * a.plane + (long long)ys * a.pitch + xs) *
                             (a.scale_in ? a.scale_in[i] : 1.f);
                 if (!isfinite(g)) {
                     v[2] += 1.0;
@@ -254,6 +256,7 @@ extern "C" lb_status lb_invariants(lb_ctx *ctx, double *out) {
     memset(&a, 0, sizeof(a));
     a.pop = ctx->pop[ctx->cur];
     a.raw = ctx->raw ? 1 : 0;
+    a.swap = ctx->swap ? 1 : 0;
     a.periodic = ctx->cfg.boundary == LB_PERIODIC;
     a.eta2 = ctx->eta2;
     a.nx = ctx->nx;

@@ -58,10 +58,12 @@ __device__ __forceinline__ void pdl_trigger_and_wait() {
 }
 
 template <int Q> struct Lat;
+// opp(i): the population with velocity -c_i
 template <> struct Lat<5> {
     __host__ __device__ static constexpr int cx(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
     __host__ __device__ static constexpr int cy(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
     __host__ __device__ static constexpr int cz(int) { return 0; }
+    __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i + 1) % 4 + 1; }
 };
 template <> struct Lat<9> {
     __host__ __device__ static constexpr int cx(int i) {
@@ -71,13 +73,24 @@ template <> struct Lat<9> {
         return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
     }
     __host__ __device__ static constexpr int cz(int) { return 0; }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : (i < 5 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5);
+    }
 };
 // D3Q7, the 3-D extension of D2Q5: c_0 = 0, c_1,3 = +-e_x, c_2,4 = +-e_y, c_5,6 = +-e_z
 template <> struct Lat<7> {
     __host__ __device__ static constexpr int cx(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
     __host__ __device__ static constexpr int cy(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
     __host__ __device__ static constexpr int cz(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : (i < 5 ? (i + 1) % 4 + 1 : 11 - i);
+    }
 };
+static_assert(Lat<5>::opp(1) == 3 && Lat<5>::opp(2) == 4 && Lat<5>::opp(3) == 1 &&
+                  Lat<5>::opp(4) == 2, "D2Q5 opposites");
+static_assert(Lat<9>::opp(5) == 7 && Lat<9>::opp(6) == 8 && Lat<9>::opp(7) == 5 &&
+                  Lat<9>::opp(8) == 6 && Lat<9>::opp(3) == 1, "D2Q9 opposites");
+static_assert(Lat<7>::opp(5) == 6 && Lat<7>::opp(6) == 5, "D3Q7 opposites");
 
 // Arguments of one step launch (passed by value).
 struct StepArgs {
@@ -109,6 +122,8 @@ struct StepArgs {
     int src_nt, src_x, src_y;
     long long t;             // time of the state being collided
     int raw;                 // 1: `in` holds g(t) itself (set by lb_set_state / lb_init_pressure)
+    int swap;                // in-place streaming: `in` holds h(t-1) at its own site, population
+                             // i in slot opp(i), so g_i(x, t) = in[opp(i)](x - c_i)
     // receivers
     const int2 *rec;
     int nrec;
@@ -1020,8 +1035,9 @@ __global__ void get_state_kernel(StepArgs a, float *dst, int mode) {
         } else {
             ok = xs >= 0 && xs < a.nx && (ys >= 0 || halo);
         }
+        const int slot = a.swap ? Lat<Q>::opp(i) : i;
         if (ok)
-            v = Store<ST>::load1(halo ? halo + xs : in + i * a.plane + (long long)ys * a.pitch + xs) *
+            v = Store<ST>::load1(halo ? halo + xs : in + slot * a.plane + (long long)ys * a.pitch + xs) *
                 scale_of(a.scale_in, i);
         if (mode == 1) dst[(long long)i * total + idx] = v;
         rho += v;

@@ -20,6 +20,9 @@ struct lb_ctx {
     void *pop[2] = {nullptr, nullptr};
     int cur = 0;                    // pop[cur] holds the post-collision state of step t-1
     bool raw = false;               // ... or, when raw, the state g(t) itself (unshifted)
+    bool aa = false;                // in-place streaming: one buffer, pop[1] == pop[0]
+    bool swap = false;              // in-place streaming after a site-local step: h(t-1) at
+                                    // its own site, population i in slot opp(i)
     float *eta2 = nullptr;
     uint8_t *mid = nullptr;         // medium index (<= 256 distinct speeds), or nullptr
     float *mid_tab = nullptr;       // [256] eta^2 per index
@@ -155,6 +158,8 @@ lb_status stream_launch(lb_ctx *ctx, const lbk::StepArgs &a, int rec_blocks);
 lb_status tb_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
 lb_status tb_launch(lb_ctx *ctx, int K);
 lb_status tb_launch_args(lb_ctx *ctx, const lbk::StepArgs &a, int K);
+// in-place streaming (aa.cu): n steps of an LB_STREAM_AA context
+lb_status aa_step(lb_ctx *ctx, int n);
 // D2Q5 wavefront temporal blocking (tblock5.cu)
 bool tb5_supported(int K);
 lb_status tb5_set_receivers(lb_ctx *ctx, const int *xy, int nrec);

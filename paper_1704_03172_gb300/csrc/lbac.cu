@@ -322,6 +322,13 @@ lb_status validate(const lb_config *cfg) {
     if (cfg->step_kernel != LB_STEP_AUTO && cfg->step_kernel != LB_STEP_DIRECT &&
         cfg->step_kernel != LB_STEP_STAGED)
         return fail(nullptr, LB_EINVAL, "step_kernel must be LB_STEP_AUTO, _DIRECT or _STAGED");
+    if (cfg->streaming != LB_STREAM_AB && cfg->streaming != LB_STREAM_AA)
+        return fail(nullptr, LB_EINVAL, "streaming must be LB_STREAM_AB or LB_STREAM_AA");
+    if (cfg->streaming == LB_STREAM_AA &&
+        (cfg->lattice == LB_D3Q7 || (cfg->storage != LB_F32 && cfg->storage != LB_BF16) ||
+         cfg->n_patches > 0 || cfg->time_block > 1 || cfg->step_kernel == LB_STEP_STAGED))
+        return fail(nullptr, LB_EINVAL, "LB_STREAM_AA: D2Q5 or D2Q9, FP32 or BF16 storage, no "
+                    "patch, no time blocking, no staged step");
     if (stability_needed(cfg) && !cfg->c_map_on_device) {
         // linear stability at the medium's eta (a device c_map is checked in lb_create, once
         // its range is known): the distinct speeds when there are at most 8, else a spread
@@ -376,8 +383,10 @@ lb_status lb_footprint(const lb_config *cfg, int nt, int nrec, int want_adjoint,
     size_t pitch = (size_t)round_up(std::max(cfg->nx, 1), 32);
     size_t plane = pitch * (size_t)std::max(cfg->ny, 1) * (size_t)std::max(cfg->nz, 1);
     size_t q = cfg->lattice == LB_D2Q9 ? 9 : cfg->lattice == LB_D3Q7 ? 7 : 5;
-    // populations (two buffers), eta^2 and, for piecewise-constant media, the medium index
-    size_t b = 2 * q * plane * elem_bytes(cfg->storage) + plane * 4 + plane + 1024;
+    // populations (two buffers; one in place), eta^2 and, for piecewise-constant media, the
+    // medium index
+    const size_t nbuf = cfg->streaming == LB_STREAM_AA ? 1 : 2;
+    size_t b = nbuf * q * plane * elem_bytes(cfg->storage) + plane * 4 + plane + 1024;
     if (cfg->storage == LB_F64) b += plane * 8 + (size_t)std::max(nt, 0) * 8 + 256;
     if (nrec > 0 && nt > 0) b += (size_t)nt * nrec * 4 + (size_t)nrec * 8;
     if (nt > 0) b += (size_t)nt * 4;
@@ -457,12 +466,17 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
         return s;
     };
     const size_t plane = (size_t)c->ny * c->pitch;
-    for (int b = 0; b < 2; b++) {
+    c->aa = cfg->streaming == LB_STREAM_AA;
+    for (int b = 0; b < (c->aa ? 1 : 2); b++) {
         c->pop[b] = dev_alloc(c, (size_t)c->Q * plane * c->ebytes);
         if (!c->pop[b]) return bail(fail(c, LB_ENOMEM, "population buffer (%zu bytes)",
                                          (size_t)c->Q * plane * c->ebytes));
         cudaError_t e = cudaMemsetAsync(c->pop[b], 0, (size_t)c->Q * plane * c->ebytes, c->stream);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemsetAsync"));
+    }
+    if (c->aa) {  // one buffer, holding g(t) at its own site (zero) until the first step
+        c->pop[1] = c->pop[0];
+        c->raw = true;
     }
     c->eta2 = static_cast<float *>(dev_alloc(c, plane * 4));
     unsigned *flags = static_cast<unsigned *>(dev_alloc(c, 256));
@@ -473,7 +487,7 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     // TMA-staged persistent step: forced, or automatic for 16-bit storage on rows of at least
     // 1024 sites (a task is one row segment of 2048 16-bit sites: narrower rows idle most
     // threads, and for FP32 the register-streaming step is faster)
-    c->staged = cfg->n_patches == 0 &&
+    c->staged = cfg->n_patches == 0 && !c->aa &&
                 (cfg->step_kernel == LB_STEP_STAGED ||
                  (cfg->step_kernel == LB_STEP_AUTO && (cfg->storage == LB_BF16 ||
                                                        cfg->storage == LB_F16) && cfg->nx >= 1024));
@@ -670,6 +684,7 @@ static lb_status set_receivers_rows(lb_ctx *ctx, const int *xy, int nrec, int nt
     ctx->rec_xy.assign(xy, xy + 2 * (size_t)nrec);
     ctx->trace_cap = nt_capacity;
     if (ctx->refined) return refine_set_receivers(ctx, xy, nrec);
+    if (ctx->aa) return tb5_set_receivers(ctx, xy, nrec);  // rows of receivers, x ascending
     if (ctx->cfg.time_block > 1) return tb_set_receivers(ctx, xy, nrec);
     return LB_OK;
 }
@@ -725,6 +740,7 @@ static lb_status set_state_common(lb_ctx *ctx, const float *src, int on_device, 
     }
     long long total = (long long)ctx->ny * ctx->pitch;
     pick_set(ctx)<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(a, dev, mode);
+    ctx->swap = false;
     st = check_launch(ctx, "set_state_kernel");
     if (st == LB_OK && ctx->refined) st = refine_after_set_state(ctx, dev);
     if (tmp) {
@@ -765,6 +781,7 @@ static lb_status get_common(lb_ctx *ctx, float *out, int on_device, int mode) {
     StepArgs a = base_args(ctx);
     a.in = ctx->pop[ctx->cur];
     a.raw = ctx->raw ? 1 : 0;
+    a.swap = ctx->swap ? 1 : 0;
     long long total = (long long)ctx->ny * ctx->nx;
     pick_get(ctx)<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(a, dst, mode);
     lb_status st = check_launch(ctx, "get_state_kernel");
@@ -906,6 +923,10 @@ lb_status lb_step(lb_ctx *ctx, int n) {
 static lb_status step_n(lb_ctx *ctx, int n) {
     if (ctx->refined) return refine_step(ctx, n);
     if (ctx->cfg.storage == LB_F64) return f64_step(ctx, n);
+    if (ctx->aa) {
+        lb_status st = aa_step(ctx, n);
+        return st != LB_OK ? st : check_launch(ctx, "aa_step_kernel");
+    }
     StepFn fn = pick_step(ctx);
     StepArgs a = base_args(ctx);
     const int K = ctx->cfg.time_block;
@@ -1005,9 +1026,10 @@ const char *lb_last_error(const lb_ctx *ctx) {
 lb_status lb_set_slab(lb_ctx *ctx, int y_offset, int ny_global, void *send_lo, void *send_hi,
                       const void *recv_lo, const void *recv_hi) {
     if (!ctx) return LB_EINVAL;
-    if (ctx->nz > 1 || ctx->refined || ctx->cfg.time_block > 1 ||
+    if (ctx->nz > 1 || ctx->refined || ctx->cfg.time_block > 1 || ctx->aa ||
         (ctx->cfg.storage != LB_F32 && ctx->cfg.storage != LB_BF16))
-        return fail(ctx, LB_ESTATE, "slabs are 2-D, FP32 or BF16, without patch or time blocking");
+        return fail(ctx, LB_ESTATE, "slabs are 2-D, FP32 or BF16, without patch, time blocking or "
+                    "in-place streaming");
     if (y_offset < 0 || ny_global < ctx->ny || y_offset + ctx->ny > ny_global)
         return fail(ctx, LB_EINVAL, "slab rows [%d, %d) outside a grid of %d rows", y_offset,
                     y_offset + ctx->ny, ny_global);

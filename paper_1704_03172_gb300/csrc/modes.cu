@@ -31,6 +31,7 @@ constexpr int kModeBlocks = 304;    // 2 per SM on GB300, grid-stride over the s
 struct ModeArgs {
     const void *pop;        // current buffer
     int raw;                // 1: g(t) unshifted; 0: post-collision h(t-1), pulled
+    int swap;               // in-place streaming: h(t-1)'s population i in slot opp(i)
     int periodic;
     const float *eta2;
     const float *scale;     // per-population scale (FP16 storage) or nullptr
@@ -62,7 +63,8 @@ __global__ void __launch_bounds__(kModeThreads) mode_partial_kernel(const ModeAr
             } else if (xs < 0 || xs >= a.nx || ys < 0 || ys >= a.ny) {
                 continue;
             }
-            rho += (double)Store<ST>::load1(pop + i * a.plane + (long long)ys * a.pitch + xs) *
+            const int slot = a.swap ? Lat<Q>::opp(i) : i;
+            rho += (double)Store<ST>::load1(pop + slot * a.plane + (long long)ys * a.pitch + xs) *
                    (double)(a.scale ? a.scale[i] : 1.f);
         }
         const double e2 = (double)a.eta2[(long long)y * a.pitch + x];
@@ -130,6 +132,7 @@ extern "C" lb_status lb_mode_projection(lb_ctx *ctx, const int *modes, int n_mod
     ModeArgs a;
     a.pop = ctx->pop[ctx->cur];
     a.raw = ctx->raw ? 1 : 0;
+    a.swap = ctx->swap ? 1 : 0;
     a.periodic = ctx->cfg.boundary == LB_PERIODIC;
     a.eta2 = ctx->eta2;
     a.scale = current_scale(ctx);

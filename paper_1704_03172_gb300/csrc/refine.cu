@@ -88,7 +88,18 @@ struct lb_refine {
     lb_refine *sub = nullptr;        // nested patch inside this level's grid
     void *bak = nullptr;             // depth >= 2: input buffer saved around pressure peeks
     float *Ubak[2] = {nullptr, nullptr};
-    ~lb_refine() { delete sub; }
+    // depth 1: the stream that runs the patch's part of each coarse step beside the coarse
+    // step itself, and the events that order the two (ev[0]: the coarse input is final,
+    // ev[1]: the patch's part is done)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    ~lb_refine() {
+        if (side) cudaStreamSynchronize(side);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (side) cudaStreamDestroy(side);
+        delete sub;
+    }
 };
 
 namespace {
@@ -465,8 +476,16 @@ void launch_f2c(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, co
     }
 }
 
+// the fine -> coarse correction that ends a patch's part of a parent step, when the caller
+// launches it itself (on another stream than the rest)
+struct F2cTail {
+    const float *fin = nullptr;
+    int fraw = 0;
+    bool pending = false;
+};
+
 void child_steps(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, float *trace_row,
-                 long long T);
+                 long long T, F2cTail *tail = nullptr);
 
 // one step t of refined level R (pull from pop[cur], store into pop[cur ^ 1]), with every
 // level nested in it; receivers of R at trace row `trace_row`
@@ -495,7 +514,7 @@ void level_step(lb_ctx *ctx, lb_refine *R, float *trace_row, long long t) {
 // U(T), two steps of R with the coarse-to-fine transfers, and the correction of the parent's
 // step output (ap: the parent's step arguments, in / out / raw of step T).
 void child_steps(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, float *trace_row,
-                 long long T) {
+                 long long T, F2cTail *tail) {
     float *Ucur = R->U[T & 1], *Uprev = R->U[(T + 1) & 1];
     if (R->coupling == LB_COUPLE_F2C) {  // nothing enters the patch: no snapshot, no transfer
         if (T >= 1) {
@@ -513,7 +532,14 @@ void child_steps(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, f
     const float *fin_last = static_cast<const float *>(R->pop[R->cur]);
     const int fraw = R->raw ? 1 : 0;
     level_step(ctx, R, trace_row, 2 * T);
-    if (R->coupling != LB_COUPLE_C2F) launch_f2c(ctx, ap, periodic, R, fin_last, fraw);
+    if (R->coupling == LB_COUPLE_C2F) return;
+    if (tail) {
+        tail->fin = fin_last;
+        tail->fraw = fraw;
+        tail->pending = true;
+    } else {
+        launch_f2c(ctx, ap, periodic, R, fin_last, fraw);
+    }
 }
 
 void launch_overlay(lb_ctx *ctx, lb_refine *R, float *p) {
@@ -705,6 +731,15 @@ lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev
         pnx = R->nxf;
     }
     ctx->refined = true;
+    lb_refine *R = ctx->ref;
+    // the side stream gets the highest priority: its short interface launches and fine
+    // steps are scheduled ahead of the coarse step's remaining blocks instead of after them
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&R->side, cudaStreamNonBlocking, greatest);
+    for (int k = 0; k < 2 && e == cudaSuccess; k++)
+        e = cudaEventCreateWithFlags(&R->ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refinement stream");
     return LB_OK;
 }
 
@@ -803,9 +838,23 @@ lb_status refine_step(lb_ctx *ctx, int n) {
         ac.rec_col = R->col_c;
         ac.trace_row = R->nrec_c > 0 ? trace_row : nullptr;
         int rec_blocks = ac.trace_row ? (R->nrec_c + kThreads - 1) / kThreads : 0;
-        launch_pdl(coarse_fn, dim3(ac.main_blocks + rec_blocks), dim3(kThreads), 0, ctx->stream,
-                   ac);
-        child_steps(ctx, ac, periodic, R, trace_row, T);
+        // The coarse step and the patch's part of it (snapshot of the coarse input, two fine
+        // steps with their transfers) read the same coarse input and write disjoint
+        // buffers, so the patch's launches run on the side stream beside the coarse step;
+        // the fine -> coarse correction of the coarse output waits for both.
+        cudaStream_t main = ctx->stream;
+        cudaError_t e = cudaEventRecord(R->ev[0], main);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(R->side, R->ev[0], 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "refined step: fork");
+        launch_pdl(coarse_fn, dim3(ac.main_blocks + rec_blocks), dim3(kThreads), 0, main, ac);
+        F2cTail tail;
+        ctx->stream = R->side;
+        child_steps(ctx, ac, periodic, R, trace_row, T, &tail);
+        ctx->stream = main;
+        e = cudaEventRecord(R->ev[1], R->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, R->ev[1], 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "refined step: join");
+        if (tail.pending) launch_f2c(ctx, ac, periodic, R, tail.fin, tail.fraw);
         ctx->cur ^= 1;
         ctx->raw = false;
         ctx->t += 1;

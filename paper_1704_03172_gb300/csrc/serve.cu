@@ -750,6 +750,8 @@ lb_status lb_server_submit(lb_server *S, const lb_request *q, long long *id) {
         (q->nt_wavelet > 0 && !q->wavelet) || (q->want_gradient && q->nrec > 0 && !q->observed))
         return fail(nullptr, LB_EINVAL, "incomplete request");
     if (q->cfg.n_patches > 0) return fail(nullptr, LB_EINVAL, "served shots have no patch");
+    if (q->cfg.streaming != LB_STREAM_AB)
+        return fail(nullptr, LB_EINVAL, "served shots stream between two buffers (LB_STREAM_AB)");
     if (q->cfg.lattice == LB_D3Q7 || q->cfg.nz > 1)
         return fail(nullptr, LB_EINVAL, "served shots are 2-D (D2Q5 / D2Q9)");
     if (q->cfg.storage == LB_F64)

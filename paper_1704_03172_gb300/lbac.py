@@ -23,6 +23,7 @@ LB_D2Q5, LB_D2Q9, LB_D3Q7 = 5, 9, 7
 LB_BGK, LB_MRT = 0, 1
 LB_F32, LB_BF16, LB_F16, LB_F64 = 0, 1, 2, 3
 LB_STEP_AUTO, LB_STEP_DIRECT, LB_STEP_STAGED = 0, 1, 2
+LB_STREAM_AB, LB_STREAM_AA = 0, 1
 LB_ZERO_GHOST, LB_PERIODIC = 0, 1
 STATUS_NAMES = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOMEM", -3: "LB_ECUDA",
                 -4: "LB_EUNSTABLE", -5: "LB_ETIMEOUT", -6: "LB_ESTATE"}
@@ -50,7 +51,7 @@ class lb_config(ctypes.Structure):
         ("patches", ctypes.POINTER(lb_patch)), ("n_patches", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p), ("time_block", ctypes.c_int),
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", ctypes.c_void_p),
-        ("step_kernel", ctypes.c_int), ("nz", ctypes.c_int),
+        ("step_kernel", ctypes.c_int), ("nz", ctypes.c_int), ("streaming", ctypes.c_int),
     ]
 
 

@@ -48,7 +48,8 @@ class LBSim:
     def __init__(self, c_map, *, lattice=5, collision="bgk", tau=0.5, s=None, storage="f32",
                  boundary="zero", sponge_width=0, sponge_sigma_max=0.1, c_ref=None,
                  w_ref=(4 / 9, 1 / 9, 1 / 36), patch=None, coupling="both", dx=0.0, time_block=1,
-                 step_kernel="auto", device=None, stream=None, torch_allocator=True):
+                 step_kernel="auto", streaming="ab", device=None, stream=None,
+                 torch_allocator=True):
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
@@ -82,6 +83,8 @@ class LBSim:
         cfg.time_block = int(time_block)
         cfg.step_kernel = {"auto": lbac.LB_STEP_AUTO, "direct": lbac.LB_STEP_DIRECT,
                            "staged": lbac.LB_STEP_STAGED}[step_kernel]
+        # "ab": pull from one population buffer into the other; "aa": in place, one buffer
+        cfg.streaming = {"ab": lbac.LB_STREAM_AB, "aa": lbac.LB_STREAM_AA}[streaming]
         cfg.c_ref = float(c_ref) if c_ref is not None else 0.0
         if torch.is_tensor(c_map) and c_map.is_cuda:
             self._cmap_keep = c_map.to(torch.float32).contiguous()

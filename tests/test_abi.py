@@ -92,8 +92,14 @@ BAD = [
     (dict(sponge_width=4, sponge_sigma_max=1.5), "sponge"),
     (dict(n_patches=5), "n_patches"),
     (dict(time_block=3), "time_block"),
-    (dict(time_block=4, storage=1), "FP32"),
+    (dict(time_block=4, storage=2), "FP32"),
+    (dict(lattice=9, time_block=4, storage=1), "FP32"),
     (dict(step_kernel=9), "step_kernel"),
+    (dict(streaming=2), "streaming"),
+    (dict(streaming=1, storage=2), "LB_STREAM_AA"),
+    (dict(streaming=1, time_block=4), "LB_STREAM_AA"),
+    (dict(streaming=1, step_kernel=2), "LB_STREAM_AA"),
+    (dict(streaming=1, lattice=7), "LB_STREAM_AA"),
 ]
 
 
@@ -128,3 +134,26 @@ def test_footprint_of_fp64_storage_without_gpu(lib):
     # coefficient table
     expect = 2 * 5 * plane * 8 + plane * 4 + plane + 1024 + plane * 8 + 256
     assert lib.lb_footprint(cfg, 0, 0, 0) == expect
+
+
+def test_footprint_of_in_place_streaming_without_gpu(lib):
+    # LB_STREAM_AA keeps one population buffer: the footprint drops by exactly one buffer
+    for lattice, storage, eb in ((5, 0, 4), (9, 0, 4), (5, 1, 2), (9, 1, 2)):
+        cfg = lib.lb_config_default()
+        cfg.nx, cfg.ny, cfg.lattice, cfg.storage = 1000, 700, lattice, storage
+        two = lib.lb_footprint(cfg, 100, 8, 0)
+        cfg.streaming = lib.LB_STREAM_AA
+        one = lib.lb_footprint(cfg, 100, 8, 0)
+        assert two - one == lattice * 700 * 1024 * eb   # pitch 1024 (multiple of 32)
+
+
+def test_create_refuses_in_place_streaming_with_a_patch_without_gpu(lib):
+    import numpy as np
+    c = np.ones((32, 32), np.float32)
+    p = (lib.lb_patch * 1)(lib.lb_patch(8, 8, 8, 8, 2, 0))
+    cfg = _cfg(lib, c, streaming=1)
+    cfg.patches = lib.ctypes.cast(p, lib.ctypes.POINTER(lib.lb_patch))
+    cfg.n_patches = 1
+    with pytest.raises(lib.LBError) as e:
+        lib.lb_create(cfg)
+    assert e.value.status == lib.LB_EINVAL and "LB_STREAM_AA" in lib.lb_last_error(None)
