@@ -281,7 +281,9 @@ def _refined_variant(torch, LBSim, steps, warmup):
     updates = 2048 * 2048 + 2 * nf * nf
     return {"glups": round(updates * steps / sec / 1e9, 2), "updates_per_coarse_step": updates,
             "ms_per_coarse_step": round(sec / steps * 1e3, 4),
-            "launches_per_coarse_step": 6}
+            "launches_per_coarse_step": 3,
+            "launches": "coarse step + snapshot transfer; fine step + midpoint transfer; fine "
+                        "step + fine -> coarse correction (coupling tasks in trailing blocks)"}
 
 
 def _upsample2(c):
@@ -1079,7 +1081,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--variant", default="",
-                    help="run one variant alone: adjoint_f32, adjoint_bf16, adjoint_tape_f32, adjoint_tape_bf16, refined, refined_nested, served")
+                    help="run one variant alone: adjoint_f32, adjoint_bf16, adjoint_tape_f32, "
+                         "adjoint_tape_bf16, refined, refined_nested, refined_vs_fine, served, "
+                         "served_classes, aa_d2q<Q>_<collision>_<storage>, "
+                         "layered_8192_<storage>, l2_resident_<n>_<storage>[_tb8], d3q7_<storage>, "
+                         "dispersion")
     ap.add_argument("--adj-n", type=int, default=4096, help="adjoint variant grid side")
     ap.add_argument("--adj-nt", type=int, default=1000, help="adjoint variant steps")
     ap.add_argument("--adj-every", type=int, default=200, help="adjoint checkpoint interval")

@@ -209,10 +209,7 @@ __device__ __forceinline__ void collide_site_vector(const StepArgs &a, const AaR
     edge = __any_sync(__activemask(), edge);
     const bool has_src = (y == a.src_y) && (a.src_x >= x0) && (a.src_x < x0 + V) &&
                          a.src_tab != nullptr && a.t < a.src_nt;
-    if (!edge)
-        collide_sites<Q, MRT, V, false>(g, e2s, a, x0, dyz, has_src);
-    else
-        collide_sites<Q, MRT, V, true>(g, e2s, a, x0, dyz, has_src);
+    collide_sites_any<Q, MRT, V>(g, e2s, a, x0, dyz, has_src, edge);
 }
 
 

@@ -122,6 +122,9 @@ struct StepArgs {
     int src_nt, src_x, src_y;
     long long t;             // time of the state being collided
     int raw;                 // 1: `in` holds g(t) itself (set by lb_set_state / lb_init_pressure)
+    int ring;                // 1: store nothing on the outermost rows and columns (a refined
+                             // patch's ghost ring, whose entering populations the coarse ->
+                             // fine transfer of the same launch writes)
     int swap;                // in-place streaming: `in` holds h(t-1) at its own site, population
                              // i in slot opp(i), so g_i(x, t) = in[opp(i)](x - c_i)
     // receivers
@@ -545,6 +548,21 @@ __device__ __forceinline__ void collide5(R g[5], R e2, const StepArgs &a) {
     }
 }
 
+// BGK with tau = 1/2 (omega = 2, the paper's lossless choice): g* = 2 g^eq - g, with g^eq
+// formed as in collide5.  One fused multiply-add per population instead of three
+// operations; the same values up to rounding.
+template <typename R>
+__device__ __forceinline__ void collide5_lossless(R g[5], R e2) {
+    const R rho = g[0] + g[1] + g[2] + g[3] + g[4];
+    const R jx = g[1] - g[3], jy = g[2] - g[4];
+    const R b = R(0.25) * e2 * rho, eq0 = rho - R(4) * b;
+    g[0] = fma(R(2), eq0, -g[0]);
+    g[1] = fma(R(2), fma(R(0.5), jx, b), -g[1]);
+    g[2] = fma(R(2), fma(R(0.5), jy, b), -g[2]);
+    g[3] = fma(R(2), fma(R(-0.5), jx, b), -g[3]);
+    g[4] = fma(R(2), fma(R(-0.5), jy, b), -g[4]);
+}
+
 // D2Q9 with the eta^2-scaled weights: w_{1..4} = eta^2 w1r, w_{5..8} = eta^2 w5r,
 // c_s^2 = eta^2 c2r, so w_i / c_s^2 = a1 or a5 does not depend on eta.
 template <bool MRT, typename R>
@@ -703,7 +721,8 @@ __device__ __forceinline__ float next_scale(float maxval, float S, float keep) {
 // Collision, source and sponge for a thread's V sites, in place.  EDGE: some site of
 // the warp lies in the sponge or beyond the last column (damped / zeroed per site; dyz is
 // the row's distance to the nearest y / z face).
-template <int Q, bool MRT, int V, bool EDGE, typename R>
+// LOSSLESS: D2Q5 BGK with omega = 2 (collide5_lossless); the caller tests a.omega once.
+template <int Q, bool MRT, int V, bool EDGE, typename R, bool LOSSLESS = false>
 __device__ __forceinline__ void collide_sites(R (&g)[Q][V], const R (&e2s)[V],
                                               const StepArgs &a, int x0, int dyz, bool has_src) {
 #pragma unroll
@@ -711,7 +730,9 @@ __device__ __forceinline__ void collide_sites(R (&g)[Q][V], const R (&e2s)[V],
         R gs[Q];
 #pragma unroll
         for (int i = 0; i < Q; i++) gs[i] = g[i][k];
-        if (Q == 5)
+        if (Q == 5 && LOSSLESS)
+            collide5_lossless(gs, e2s[k]);
+        else if (Q == 5)
             collide5<MRT>(gs, e2s[k], a);
         else if (Q == 9)
             collide9<MRT>(gs, e2s[k], a);
@@ -733,6 +754,24 @@ __device__ __forceinline__ void collide_sites(R (&g)[Q][V], const R (&e2s)[V],
 #pragma unroll
             for (int i = 0; i < Q; i++) g[i][k] = gs[i];
         }
+    }
+}
+
+// collide_sites with the damping variant (edge) and the lossless form chosen once per call.
+template <int Q, bool MRT, int V, typename R>
+__device__ __forceinline__ void collide_sites_any(R (&g)[Q][V], const R (&e2s)[V],
+                                                  const StepArgs &a, int x0, int dyz, bool has_src,
+                                                  bool edge) {
+    if (!MRT && Q == 5 && a.omega == 2.f) {  // uniform
+        if (!edge)
+            collide_sites<Q, MRT, V, false, R, true>(g, e2s, a, x0, dyz, has_src);
+        else
+            collide_sites<Q, MRT, V, true, R, true>(g, e2s, a, x0, dyz, has_src);
+    } else {
+        if (!edge)
+            collide_sites<Q, MRT, V, false, R>(g, e2s, a, x0, dyz, has_src);
+        else
+            collide_sites<Q, MRT, V, true, R>(g, e2s, a, x0, dyz, has_src);
     }
 }
 
@@ -782,11 +821,10 @@ __device__ __forceinline__ void finish_sites(const StepArgs &a, float (&g)[Q][St
                          a.src_tab != nullptr && a.t < a.src_nt;
     // collide site by site, in place: g[i][k] becomes the stored output.  Warps whose
     // sites are all real and outside the sponge (almost all) skip damping and masking.
-    if (!edge)
-        collide_sites<Q, MRT, V, false>(g, e2s, a, x0, dyz, has_src);
-    else
-        collide_sites<Q, MRT, V, true>(g, e2s, a, x0, dyz, has_src);
+    collide_sites_any<Q, MRT, V>(g, e2s, a, x0, dyz, has_src, edge);
     ST *o = static_cast<ST *>(a.out) + (long long)y * a.pitch + x0;
+    const bool ring_row = a.ring && (y == 0 || y == a.ny - 1);        // warp-uniform
+    const bool ring_col = a.ring && (x0 == 0 || x0 + V >= a.nx);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         if (SC) {
@@ -799,7 +837,14 @@ __device__ __forceinline__ void finish_sites(const StepArgs &a, float (&g)[Q][St
             }
             tmax[i] = fmaxf(tmax[i], m);
         }
-        Store<ST>::storeV(o + i * a.plane, g[i]);
+        if (ring_row) continue;
+        if (!ring_col) {
+            Store<ST>::storeV(o + i * a.plane, g[i]);
+        } else {  // all but the first and last column
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (x0 + k >= 1 && x0 + k < a.nx - 1) Store<ST>::store1(o + i * a.plane + k, g[i][k]);
+        }
     }
     if (SLAB && Q != 7 && ((a.send_lo && y == 0) || (a.send_hi && y == a.ny - 1))) {
         // slab cut rows: the populations the neighbouring slab pulls across the cut

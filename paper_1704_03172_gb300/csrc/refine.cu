@@ -88,21 +88,11 @@ struct lb_refine {
     lb_refine *sub = nullptr;        // nested patch inside this level's grid
     void *bak = nullptr;             // depth >= 2: input buffer saved around pressure peeks
     float *Ubak[2] = {nullptr, nullptr};
-    // depth 1: the stream that runs the patch's part of each coarse step beside the coarse
-    // step itself, and the events that order the two (ev[0]: the coarse input is final,
-    // ev[1]: the patch's part is done)
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    ~lb_refine() {
-        if (side) cudaStreamSynchronize(side);
-        for (cudaEvent_t e : ev)
-            if (e) cudaEventDestroy(e);
-        if (side) cudaStreamDestroy(side);
-        delete sub;
-    }
+    ~lb_refine() { delete sub; }
 };
 
 namespace {
+
 
 // fine sound speed and eta^2 (with the ghost ring: nearest real node) from the parent's
 // sound speed pc [..][pnx] (node coordinates), bilinearly; cf gets the real nodes' speeds
@@ -188,13 +178,12 @@ __global__ void ref_snapshot_kernel(StepArgs ac, const int2 *Ic, int nI, float *
 }
 
 // coarse -> fine: write the entering populations of the fine nodes of I into
-// the fine input buffer (at the upstream ghost node, or in place when raw).
+// the fine input buffer (at the upstream ghost node, or in place when raw).  The body
+// handles interface node j (of nIf); the kernels below and ref_step_kernel call it.
 template <int Q, bool MRT>
-__global__ void ref_c2f_kernel(StepArgs af, StepArgs rs, const int4 *If, int nIf, const float *Ua,
-                               const float *Ub, float alpha, int nxf, int nyf) {
-    pdl_trigger_and_wait();  // launched with launch_pdl
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nIf) return;
+__device__ __forceinline__ void c2f_node(const StepArgs &af, const StepArgs &rs, const int4 *If,
+                                         int j, const float *Ua, const float *Ub, float alpha,
+                                         int nxf, int nyf) {
     const int4 e = If[j];
     const int a = e.x, b = e.y;
     float gh[Q];
@@ -224,6 +213,15 @@ __global__ void ref_c2f_kernel(StepArgs af, StepArgs rs, const int4 *If, int nIf
     }
 }
 
+template <int Q, bool MRT>
+__global__ void ref_c2f_kernel(StepArgs af, StepArgs rs, const int4 *If, int nIf, const float *Ua,
+                               const float *Ub, float alpha, int nxf, int nyf) {
+    pdl_trigger_and_wait();  // launched with launch_pdl
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nIf) return;
+    c2f_node<Q, MRT>(af, rs, If, j, Ua, Ub, alpha, nxf, nyf);
+}
+
 // Fine -> coarse coupling only: nothing enters the fine grid across I.  The entering
 // populations of the fine nodes of I, which the fine step left at the upstream ghost
 // nodes of its input, are set to zero (a zero-ghost boundary).  Not used on a raw input:
@@ -249,12 +247,10 @@ __global__ void ref_zero_in_kernel(StepArgs af, const int4 *If, int nIf, int nxf
 // interpolates them with Ua = U(T - 1) (alpha = 1/2) or takes them alone (alpha = 1, T = 0).
 // Same values as the snapshot kernel followed by ref_c2f_kernel.
 template <int Q, bool MRT>
-__global__ void ref_snap_c2f_kernel(StepArgs ap, StepArgs af, StepArgs rs, const int4 *If, int nIf,
-                                    const int2 *Ic, const float *Ua, float *Ucur, float alpha,
-                                    int nxf, int nyf) {
-    pdl_trigger_and_wait();  // launched with launch_pdl
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nIf) return;
+__device__ __forceinline__ void snap_c2f_node(const StepArgs &ap, const StepArgs &af,
+                                              const StepArgs &rs, const int4 *If, int j,
+                                              const int2 *Ic, const float *Ua, float *Ucur,
+                                              float alpha, int nxf, int nyf) {
     const int4 e = If[j];
     const int a = e.x, b = e.y;
     const float *pin = static_cast<const float *>(ap.in);
@@ -299,14 +295,22 @@ __global__ void ref_snap_c2f_kernel(StepArgs ap, StepArgs af, StepArgs rs, const
     }
 }
 
-// fine -> coarse on I, then collide (+ sponge) and overwrite the parent's step output
-template <int Q, bool MRT, bool PERIODIC>
-__global__ void ref_f2c_kernel(StepArgs ac, StepArgs rs, const float *fin, int fraw, int fpitch,
-                               long long fplane, const int2 *Ic, int nI, int x0, int y0, int nxp,
-                               int nyp) {
+template <int Q, bool MRT>
+__global__ void ref_snap_c2f_kernel(StepArgs ap, StepArgs af, StepArgs rs, const int4 *If, int nIf,
+                                    const int2 *Ic, const float *Ua, float *Ucur, float alpha,
+                                    int nxf, int nyf) {
     pdl_trigger_and_wait();  // launched with launch_pdl
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nI) return;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nIf) return;
+    snap_c2f_node<Q, MRT>(ap, af, rs, If, j, Ic, Ua, Ucur, alpha, nxf, nyf);
+}
+
+// fine -> coarse on I, then collide (+ sponge) and overwrite the parent's step output
+// (coarse interface node k of nI)
+template <int Q, bool MRT, bool PERIODIC>
+__device__ __forceinline__ void f2c_node(const StepArgs &ac, const StepArgs &rs, const float *fin,
+                                         int fraw, int fpitch, long long fplane, const int2 *Ic,
+                                         int k, int x0, int y0, int nxp, int nyp) {
     const int2 X = Ic[k];
     const float *cin = static_cast<const float *>(ac.in);
     float g[Q], G[Q];
@@ -335,6 +339,69 @@ __global__ void ref_f2c_kernel(StepArgs ac, StepArgs rs, const float *fin, int f
     float *out = static_cast<float *>(ac.out);
 #pragma unroll
     for (int i = 0; i < Q; i++) out[i * ac.plane + (long long)X.y * ac.pitch + X.x] = g[i] * f;
+}
+
+template <int Q, bool MRT, bool PERIODIC>
+__global__ void ref_f2c_kernel(StepArgs ac, StepArgs rs, const float *fin, int fraw, int fpitch,
+                               long long fplane, const int2 *Ic, int nI, int x0, int y0, int nxp,
+                               int nyp) {
+    pdl_trigger_and_wait();  // launched with launch_pdl
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nI) return;
+    f2c_node<Q, MRT, PERIODIC>(ac, rs, fin, fraw, fpitch, fplane, Ic, k, x0, y0, nxp, nyp);
+}
+
+// One step of a grid (step_kernel's blocks: sites, then receivers) with one coupling task
+// of a patch in the trailing blocks of the same launch.  The task must touch nothing the
+// step reads or writes (ref_fused_ok): the snapshot transfer reads the step's input and
+// writes the patch's input ring; the midpoint transfer writes the ring of the fine step's
+// output, which that step leaves alone (StepArgs::ring); the fine -> coarse correction reads
+// the fine step's input and rewrites the coarse output that the previous launch finished.
+enum { kTaskSnapC2f = 1, kTaskC2f = 2, kTaskF2c = 3 };
+struct RefTask {
+    int first;        // first block of the task (sites and receiver blocks come before)
+    int n;            // interface nodes
+    StepArgs p, f, rs;  // parent step, fine level and rescale arguments of the task
+    const int4 *If;
+    const int2 *Ic;
+    const float *Ua, *Ub;
+    float *Ucur;
+    float alpha;
+    int nxf, nyf;
+    const float *fin;  // f2c: the fine state
+    int fraw, fpitch;
+    long long fplane;
+    int x0, y0, nxp, nyp;
+};
+
+template <int Q, bool MRT, bool PERIODIC, int TASK, bool TASK_PER>
+__global__ void __launch_bounds__(kThreads, Q == 5 ? 5 : 4)
+    ref_step_kernel(const StepArgs a, const RefTask x) {
+    pdl_trigger_and_wait();
+    __shared__ float s_tab[kThreads];
+    const int blk = (int)blockIdx.x;
+    if (blk >= x.first) {  // block-uniform: the coupling task
+        const int j = (blk - x.first) * kThreads + (int)threadIdx.x;
+        if (j >= x.n) return;
+        if (TASK == kTaskSnapC2f)
+            snap_c2f_node<Q, MRT>(x.p, x.f, x.rs, x.If, j, x.Ic, x.Ua, x.Ucur, x.alpha, x.nxf, x.nyf);
+        else if (TASK == kTaskC2f)
+            c2f_node<Q, MRT>(x.f, x.rs, x.If, j, x.Ua, x.Ub, x.alpha, x.nxf, x.nyf);
+        else
+            f2c_node<Q, MRT, TASK_PER>(x.p, x.rs, x.fin, x.fraw, x.fpitch, x.fplane, x.Ic, j, x.x0,
+                                       x.y0, x.nxp, x.nyp);
+        return;
+    }
+    if (blk >= a.main_blocks) {  // block-uniform: receivers
+        gather_receivers<Q, PERIODIC, float>(a, (blk - a.main_blocks) * kThreads + (int)threadIdx.x);
+        return;
+    }
+    if (a.mid) {  // block-uniform
+        s_tab[threadIdx.x] = a.mid_tab[threadIdx.x];
+        __syncthreads();
+    }
+    float tmax[Q];
+    step_sites<Q, MRT, PERIODIC, float>(a, blk, tmax, s_tab);
 }
 
 // context-grid pressure at the coarse nodes covered by a level, from its coincident nodes:
@@ -476,16 +543,8 @@ void launch_f2c(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, co
     }
 }
 
-// the fine -> coarse correction that ends a patch's part of a parent step, when the caller
-// launches it itself (on another stream than the rest)
-struct F2cTail {
-    const float *fin = nullptr;
-    int fraw = 0;
-    bool pending = false;
-};
-
 void child_steps(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, float *trace_row,
-                 long long T, F2cTail *tail = nullptr);
+                 long long T);
 
 // one step t of refined level R (pull from pop[cur], store into pop[cur ^ 1]), with every
 // level nested in it; receivers of R at trace row `trace_row`
@@ -514,7 +573,7 @@ void level_step(lb_ctx *ctx, lb_refine *R, float *trace_row, long long t) {
 // U(T), two steps of R with the coarse-to-fine transfers, and the correction of the parent's
 // step output (ap: the parent's step arguments, in / out / raw of step T).
 void child_steps(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, float *trace_row,
-                 long long T, F2cTail *tail) {
+                 long long T) {
     float *Ucur = R->U[T & 1], *Uprev = R->U[(T + 1) & 1];
     if (R->coupling == LB_COUPLE_F2C) {  // nothing enters the patch: no snapshot, no transfer
         if (T >= 1) {
@@ -532,14 +591,7 @@ void child_steps(lb_ctx *ctx, const StepArgs &ap, bool periodic, lb_refine *R, f
     const float *fin_last = static_cast<const float *>(R->pop[R->cur]);
     const int fraw = R->raw ? 1 : 0;
     level_step(ctx, R, trace_row, 2 * T);
-    if (R->coupling == LB_COUPLE_C2F) return;
-    if (tail) {
-        tail->fin = fin_last;
-        tail->fraw = fraw;
-        tail->pending = true;
-    } else {
-        launch_f2c(ctx, ap, periodic, R, fin_last, fraw);
-    }
+    if (R->coupling != LB_COUPLE_C2F) launch_f2c(ctx, ap, periodic, R, fin_last, fraw);
 }
 
 void launch_overlay(lb_ctx *ctx, lb_refine *R, float *p) {
@@ -731,15 +783,6 @@ lb_status refine_setup(lb_ctx *ctx, const lb_config *cfg, const float *c_map_dev
         pnx = R->nxf;
     }
     ctx->refined = true;
-    lb_refine *R = ctx->ref;
-    // the side stream gets the highest priority: its short interface launches and fine
-    // steps are scheduled ahead of the coarse step's remaining blocks instead of after them
-    int least = 0, greatest = 0;
-    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&R->side, cudaStreamNonBlocking, greatest);
-    for (int k = 0; k < 2 && e == cudaSuccess; k++)
-        e = cudaEventCreateWithFlags(&R->ev[k], cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "refinement stream");
     return LB_OK;
 }
 
@@ -818,6 +861,118 @@ lb_status refine_after_set_state(lb_ctx *ctx, const float *p0_dev) {
     return check_launch(ctx, "refined initial state");
 }
 
+template <int Q, bool MRT>
+cudaError_t launch_task_q(lb_ctx *ctx, int task, bool per, bool task_per, const StepArgs &a,
+                          int rec_blocks, RefTask x) {
+    x.first = a.main_blocks + rec_blocks;
+    const dim3 grid(x.first + blocks_for(x.n)), block(kThreads);
+    if (task == kTaskSnapC2f)  // in the parent's step (coarse grid: either boundary)
+        return per ? launch_pdl(ref_step_kernel<Q, MRT, true, kTaskSnapC2f, false>, grid, block, 0,
+                                ctx->stream, a, x)
+                   : launch_pdl(ref_step_kernel<Q, MRT, false, kTaskSnapC2f, false>, grid, block, 0,
+                                ctx->stream, a, x);
+    if (task == kTaskC2f)  // in a fine step (zero ghost)
+        return launch_pdl(ref_step_kernel<Q, MRT, false, kTaskC2f, false>, grid, block, 0,
+                          ctx->stream, a, x);
+    // in a fine step; the correction reads and writes the parent's grid
+    return task_per ? launch_pdl(ref_step_kernel<Q, MRT, false, kTaskF2c, true>, grid, block, 0,
+                                 ctx->stream, a, x)
+                    : launch_pdl(ref_step_kernel<Q, MRT, false, kTaskF2c, false>, grid, block, 0,
+                                 ctx->stream, a, x);
+}
+
+// A step with a coupling task in its trailing blocks (ref_step_kernel).
+cudaError_t launch_task(lb_ctx *ctx, int task, bool per, bool task_per, const StepArgs &a,
+                        int rec_blocks, const RefTask &x) {
+    const bool mrt = ctx->cfg.collision == LB_MRT;
+    if (ctx->Q == 9)
+        return mrt ? launch_task_q<9, true>(ctx, task, per, task_per, a, rec_blocks, x)
+                   : launch_task_q<9, false>(ctx, task, per, task_per, a, rec_blocks, x);
+    return mrt ? launch_task_q<5, true>(ctx, task, per, task_per, a, rec_blocks, x)
+               : launch_task_q<5, false>(ctx, task, per, task_per, a, rec_blocks, x);
+}
+
+// Coarse step T of a two-level grid (one patch, coupled both ways, T >= 1, no raw state) in
+// three launches instead of six: each coupling task rides in the trailing blocks of a step
+// whose buffers it does not touch.
+//   1. coarse step T + the snapshot of U(T) fused with the midpoint transfer into the ring
+//      of the patch's input;
+//   2. fine step 2T - 1, its ring left alone, + the transfer at time 2T into that ring;
+//   3. fine step 2T (receivers), ring left alone, + the fine -> coarse correction of the
+//      coarse output of step T (launch 1 finished it) from the input of step 2T.
+// The same kernels' per-node code, in the same order of dependence: the results equal the
+// six-launch sequence bit for bit.
+lb_status fused_coarse_step(lb_ctx *ctx, lb_refine *R, const StepArgs &ac, int rec_blocks,
+                            bool periodic, float *trace_row, long long T) {
+    const int Q = ctx->Q;
+    float *Ucur = R->U[T & 1], *Uprev = R->U[(T + 1) & 1];
+    RefTask x1 = {};
+    x1.n = R->nIf;
+    x1.p = ac;
+    x1.f = level_args(ctx, R);
+    x1.f.in = R->pop[R->cur];
+    x1.rs = rescale_args(x1.f, Q, R->c2f_omega, R->c2f_s);
+    x1.If = R->If;
+    x1.Ic = R->Ic;
+    x1.Ua = Uprev;
+    x1.Ucur = Ucur;
+    x1.alpha = 0.5f;
+    x1.nxf = R->nxf;
+    x1.nyf = R->nyf;
+    cudaError_t e = launch_task(ctx, kTaskSnapC2f, periodic, false, ac, rec_blocks, x1);
+
+    StepArgs f1 = level_args(ctx, R);
+    f1.in = R->pop[R->cur];
+    f1.out = R->pop[R->cur ^ 1];
+    f1.t = 2 * T - 1;
+    f1.ring = 1;
+    RefTask x2 = {};
+    x2.n = R->nIf;
+    x2.f = level_args(ctx, R);
+    x2.f.in = R->pop[R->cur ^ 1];  // the ring of step 2T - 1's output
+    x2.rs = rescale_args(x2.f, Q, R->c2f_omega, R->c2f_s);
+    x2.If = R->If;
+    x2.Ua = Ucur;
+    x2.Ub = Ucur;
+    x2.alpha = 1.f;
+    x2.nxf = R->nxf;
+    x2.nyf = R->nyf;
+    if (e == cudaSuccess) e = launch_task(ctx, kTaskC2f, false, false, f1, 0, x2);
+    R->cur ^= 1;
+
+    StepArgs f2 = level_args(ctx, R);
+    f2.in = R->pop[R->cur];
+    f2.out = R->pop[R->cur ^ 1];
+    f2.t = 2 * T;
+    f2.ring = 1;
+    int frec = 0;
+    if (trace_row && R->nrec_f > 0) {
+        f2.rec = R->rec_f;
+        f2.nrec = R->nrec_f;
+        f2.rec_col = R->col_f;
+        f2.trace_row = trace_row;
+        frec = (R->nrec_f + kThreads - 1) / kThreads;
+    }
+    RefTask x3 = {};
+    x3.n = R->nI;
+    x3.p = ac;
+    x3.rs = rescale_args(ac, Q, R->f2c_omega, R->f2c_s);
+    x3.fin = static_cast<const float *>(R->pop[R->cur]);
+    x3.fraw = 0;
+    x3.fpitch = R->pitch;
+    x3.fplane = (long long)R->gy * R->pitch;
+    x3.Ic = R->Ic;
+    x3.x0 = R->x0;
+    x3.y0 = R->y0;
+    x3.nxp = R->nxp;
+    x3.nyp = R->nyp;
+    if (e == cudaSuccess) e = launch_task(ctx, kTaskF2c, false, periodic, f2, frec, x3);
+    R->cur ^= 1;
+    R->raw = false;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refined step launch");
+    return LB_OK;
+}
+
 lb_status refine_step(lb_ctx *ctx, int n) {
     lb_refine *R = ctx->ref;
     StepFn coarse_fn = pick_step(ctx);
@@ -838,23 +993,14 @@ lb_status refine_step(lb_ctx *ctx, int n) {
         ac.rec_col = R->col_c;
         ac.trace_row = R->nrec_c > 0 ? trace_row : nullptr;
         int rec_blocks = ac.trace_row ? (R->nrec_c + kThreads - 1) / kThreads : 0;
-        // The coarse step and the patch's part of it (snapshot of the coarse input, two fine
-        // steps with their transfers) read the same coarse input and write disjoint
-        // buffers, so the patch's launches run on the side stream beside the coarse step;
-        // the fine -> coarse correction of the coarse output waits for both.
-        cudaStream_t main = ctx->stream;
-        cudaError_t e = cudaEventRecord(R->ev[0], main);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(R->side, R->ev[0], 0);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "refined step: fork");
-        launch_pdl(coarse_fn, dim3(ac.main_blocks + rec_blocks), dim3(kThreads), 0, main, ac);
-        F2cTail tail;
-        ctx->stream = R->side;
-        child_steps(ctx, ac, periodic, R, trace_row, T, &tail);
-        ctx->stream = main;
-        e = cudaEventRecord(R->ev[1], R->side);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, R->ev[1], 0);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "refined step: join");
-        if (tail.pending) launch_f2c(ctx, ac, periodic, R, tail.fin, tail.fraw);
+        if (R->sub == nullptr && R->coupling == LB_COUPLE_BOTH && !R->raw && T >= 1) {
+            lb_status st = fused_coarse_step(ctx, R, ac, rec_blocks, periodic, trace_row, T);
+            if (st != LB_OK) return st;
+        } else {
+            launch_pdl(coarse_fn, dim3(ac.main_blocks + rec_blocks), dim3(kThreads), 0, ctx->stream,
+                       ac);
+            child_steps(ctx, ac, periodic, R, trace_row, T);
+        }
         ctx->cur ^= 1;
         ctx->raw = false;
         ctx->t += 1;

@@ -110,19 +110,6 @@ __device__ __forceinline__ float tb5_e2(const StepArgs &a, const Tb5Thread &T, b
     return (a.mid && live) ? T.s_tab[__float_as_int(m)] : m;
 }
 
-// BGK with tau = 1/2 (the lossless setting, omega = 2): g* = 2 g^eq - g, with g^eq formed
-// as in collide5.
-__device__ __forceinline__ void collide5_lossless(float (&g)[5], float e2) {
-    const float rho = g[0] + g[1] + g[2] + g[3] + g[4];
-    const float jx = g[1] - g[3], jy = g[2] - g[4];
-    const float b = 0.25f * e2 * rho, eq0 = rho - 4.f * b;  // as in collide5
-    g[0] = fmaf(2.f, eq0, -g[0]);
-    g[1] = fmaf(2.f, fmaf(0.5f, jx, b), -g[1]);
-    g[2] = fmaf(2.f, fmaf(0.5f, jy, b), -g[2]);
-    g[3] = fmaf(2.f, fmaf(-0.5f, jx, b), -g[3]);
-    g[4] = fmaf(2.f, fmaf(-0.5f, jy, b), -g[4]);
-}
-
 // One wavefront iteration r (parity P).  FAST: every level's row lies inside the chunk's
 // output rows, inside the domain and outside the sponge, holds neither the source nor a
 // receiver, and the strip's columns are all live and outside the sponge: no per-site
