@@ -283,7 +283,7 @@ def _refined_variant(torch, LBSim, steps, warmup):
             "ms_per_coarse_step": round(sec / steps * 1e3, 4),
             "launches_per_coarse_step": 3,
             "launches": "coarse step + snapshot transfer; fine step + midpoint transfer; fine "
-                        "step + fine -> coarse correction (coupling tasks in trailing blocks)"}
+                        "step + fine -> coarse correction (each coupling task in extra blocks of a step launch)"}
 
 
 def _upsample2(c):

@@ -352,14 +352,15 @@ __global__ void ref_f2c_kernel(StepArgs ac, StepArgs rs, const float *fin, int f
 }
 
 // One step of a grid (step_kernel's blocks: sites, then receivers) with one coupling task
-// of a patch in the trailing blocks of the same launch.  The task must touch nothing the
+// of a patch in leading blocks of the same launch.  The task must touch nothing the
 // step reads or writes (ref_fused_ok): the snapshot transfer reads the step's input and
 // writes the patch's input ring; the midpoint transfer writes the ring of the fine step's
 // output, which that step leaves alone (StepArgs::ring); the fine -> coarse correction reads
 // the fine step's input and rewrites the coarse output that the previous launch finished.
 enum { kTaskSnapC2f = 1, kTaskC2f = 2, kTaskF2c = 3 };
 struct RefTask {
-    int first;        // first block of the task (sites and receiver blocks come before)
+    int blocks;       // blocks of the task: the first of the launch, so that its short chain
+                      // of dependent loads starts at once instead of behind the last wave
     int n;            // interface nodes
     StepArgs p, f, rs;  // parent step, fine level and rescale arguments of the task
     const int4 *If;
@@ -379,9 +380,9 @@ __global__ void __launch_bounds__(kThreads, Q == 5 ? 5 : 4)
     ref_step_kernel(const StepArgs a, const RefTask x) {
     pdl_trigger_and_wait();
     __shared__ float s_tab[kThreads];
-    const int blk = (int)blockIdx.x;
-    if (blk >= x.first) {  // block-uniform: the coupling task
-        const int j = (blk - x.first) * kThreads + (int)threadIdx.x;
+    const int blk = (int)blockIdx.x - x.blocks;
+    if (blk < 0) {  // block-uniform: the coupling task
+        const int j = (int)blockIdx.x * kThreads + (int)threadIdx.x;
         if (j >= x.n) return;
         if (TASK == kTaskSnapC2f)
             snap_c2f_node<Q, MRT>(x.p, x.f, x.rs, x.If, j, x.Ic, x.Ua, x.Ucur, x.alpha, x.nxf, x.nyf);
@@ -864,8 +865,8 @@ lb_status refine_after_set_state(lb_ctx *ctx, const float *p0_dev) {
 template <int Q, bool MRT>
 cudaError_t launch_task_q(lb_ctx *ctx, int task, bool per, bool task_per, const StepArgs &a,
                           int rec_blocks, RefTask x) {
-    x.first = a.main_blocks + rec_blocks;
-    const dim3 grid(x.first + blocks_for(x.n)), block(kThreads);
+    x.blocks = blocks_for(x.n);
+    const dim3 grid(x.blocks + a.main_blocks + rec_blocks), block(kThreads);
     if (task == kTaskSnapC2f)  // in the parent's step (coarse grid: either boundary)
         return per ? launch_pdl(ref_step_kernel<Q, MRT, true, kTaskSnapC2f, false>, grid, block, 0,
                                 ctx->stream, a, x)
@@ -881,7 +882,7 @@ cudaError_t launch_task_q(lb_ctx *ctx, int task, bool per, bool task_per, const 
                                  ctx->stream, a, x);
 }
 
-// A step with a coupling task in its trailing blocks (ref_step_kernel).
+// A step with a coupling task in its leading blocks (ref_step_kernel).
 cudaError_t launch_task(lb_ctx *ctx, int task, bool per, bool task_per, const StepArgs &a,
                         int rec_blocks, const RefTask &x) {
     const bool mrt = ctx->cfg.collision == LB_MRT;
@@ -893,7 +894,7 @@ cudaError_t launch_task(lb_ctx *ctx, int task, bool per, bool task_per, const St
 }
 
 // Coarse step T of a two-level grid (one patch, coupled both ways, T >= 1, no raw state) in
-// three launches instead of six: each coupling task rides in the trailing blocks of a step
+// three launches instead of six: each coupling task rides in the leading blocks of a step
 // whose buffers it does not touch.
 //   1. coarse step T + the snapshot of U(T) fused with the midpoint transfer into the ring
 //      of the patch's input;
