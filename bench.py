@@ -47,6 +47,16 @@ KERNEL_SOURCES = {
     "lbtb5::tb5_kernel": ("lb_kernels.cuh", "tblock5.cuh"),
 }
 NCU_TRAFFIC = {
+    ("lbk::step_kernel<5,false,false,float>", True):
+        (638.2e6, "4981af4f74d3", "profiles/step_kernel_d2q5_f32_4096.md"),
+    ("stream_step_kernel<5,false,false,__nv_bfloat16>", True):
+        (300.6e6, "a94f2a9b01cf", "profiles/stream_step_kernel_d2q5_bf16_4096.md"),
+    ("lbtb5::tb5_kernel<false,4,false,float>", True):
+        (656.4e6, "8e6aa48e247b", "profiles/tb5_kernel_d2q5_4096.md"),
+    ("lbtb5::tb5_kernel<false,4,false,__nv_bfloat16>", True):
+        (314.9e6, "8e6aa48e247b", "profiles/tb5_kernel_d2q5_4096.md"),
+    ("lbtb5::tb5_kernel<false,8,false,float>", True):
+        (674.2e6, "8e6aa48e247b", "profiles/tb5_kernel_d2q5_4096.md"),
 }
 
 
