@@ -413,15 +413,42 @@ def _nested_variant(torch, LBSim, steps, warmup):
     updates = 2048 * 2048 + 2 * n1 * n1 + 4 * n2 * n2
     return {"glups": round(updates * steps / sec / 1e9, 2), "updates_per_coarse_step": updates,
             "ms_per_coarse_step": round(sec / steps * 1e3, 4),
-            "launches_per_coarse_step": 16}
+            "launches_per_coarse_step": 7,
+            "launches": "coarse step + level-1 snapshot; per level-1 step: that step with its "
+                        "transfer or correction and the level-2 snapshot, then two level-2 steps "
+                        "with theirs"}
+
+
+_OBSERVED = {}
+
+
+def _observed(torch, LBSim, n, nt):
+    """Data d of the misfit: the 512 traces of a Gaussian-smoothed (sigma = 20 cells) copy of
+    the layered model at n^2 (FP32, same source and receivers), computed once per size."""
+    if (n, nt) not in _OBSERVED:
+        from scipy.ndimage import gaussian_filter
+        wl = _layered(n)
+        cs = gaussian_filter(np.asarray(wl["c_map"], np.float32), 20.0, mode="nearest")
+        sim = LBSim(cs, lattice=5, tau=0.5, c_ref=wl["c_ref"], sponge_width=40)
+        try:
+            sim.set_source(wl["source"][0], wl["source"][1], W.ricker(nt, W.SERVED_FC))
+            sim.set_receivers(wl["receivers"], nt)
+            sim.init_pressure(None)
+            sim.step(nt)
+            _OBSERVED[(n, nt)] = sim.traces(nt).clone()
+        finally:
+            sim.close()
+    return _OBSERVED[(n, nt)]
 
 
 def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32", mode="ckpt"):
-    """Gradient of J = 1/2 sum p^2 over 512 receiver traces w.r.t. the sound-speed map and
-    the source, for the 20-layer faulted model (the layered workload at n^2): forward run
-    with checkpoints, then lb_adjoint (replay + reverse sweep); mode "tape": the forward run
-    records rho (n^2 nt 4 bytes) and lb_adjoint is the reverse sweep alone.  Rates count
-    n^2 * nt site-steps of the gradient call; peak device memory of the whole shot."""
+    """Gradient of J = 1/2 sum (p - d)^2 over 512 receiver traces w.r.t. the sound-speed map
+    and the source, for the 20-layer faulted model (the layered workload at n^2), with d the
+    traces of a smoothed copy of the model: forward run with checkpoints, then lb_adjoint
+    (replay + reverse sweep); mode "tape": the forward run records rho (n^2 nt 4 bytes) and
+    lb_adjoint is the reverse sweep alone.  Rates count n^2 * nt site-steps of the gradient
+    call; peak device memory of the whole shot."""
+    d = _observed(torch, LBSim, n, nt)
     wl = _layered(n)
     sim = LBSim(wl["c_map"], lattice=5, tau=0.5, c_ref=wl["c_ref"], sponge_width=40,
                 storage=storage)
@@ -441,7 +468,7 @@ def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32", mo
         sim.step(nt)
         torch.cuda.synchronize()
         t_fwd = time.perf_counter() - t0
-        R = sim.traces(nt).clone()
+        R = sim.traces(nt) - d  # dJ/dp
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         gc, gs, _ = sim.adjoint(R, nt)
@@ -474,7 +501,8 @@ def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32", mo
            "workload": f"{n}x{n} 20-layer faulted model, D2Q5 BGK {storage.upper()}, {nt} steps, "
                        + (f"forward rho tape ({n * n * nt * 4 / 1e9:.0f} GB), no replay"
                           if mode == "tape" else f"checkpoint every {every}")
-                       + ", 512 receivers, wall time of lb_adjoint"}
+                       + ", 512 receivers, J = 1/2 sum (p - d)^2 with d from the model "
+                         "smoothed by a Gaussian of 20 cells, wall time of lb_adjoint"}
     if mode != "tape":
         out["replay_levels"] = levels
         out["checkpoint_every"] = every

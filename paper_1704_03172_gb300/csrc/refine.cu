@@ -351,16 +351,18 @@ __global__ void ref_f2c_kernel(StepArgs ac, StepArgs rs, const float *fin, int f
     f2c_node<Q, MRT, PERIODIC>(ac, rs, fin, fraw, fpitch, fplane, Ic, k, x0, y0, nxp, nyp);
 }
 
-// One step of a grid (step_kernel's blocks: sites, then receivers) with one coupling task
-// of a patch in leading blocks of the same launch.  The task must touch nothing the
-// step reads or writes (ref_fused_ok): the snapshot transfer reads the step's input and
-// writes the patch's input ring; the midpoint transfer writes the ring of the fine step's
-// output, which that step leaves alone (StepArgs::ring); the fine -> coarse correction reads
-// the fine step's input and rewrites the coarse output that the previous launch finished.
-enum { kTaskSnapC2f = 1, kTaskC2f = 2, kTaskF2c = 3 };
+// One step of a grid (step_kernel's blocks: sites, then receivers) with one or two coupling
+// tasks of patches in leading blocks of the same launch, so that their short chains of
+// dependent loads start with the first wave.  A task touches nothing the step reads or
+// writes:
+// - the snapshot transfer reads the step's input and writes the patch's input ring;
+// - the transfer at the parent's later time writes the ring of the fine step's output,
+//   which that step leaves alone (StepArgs::ring);
+// - the fine -> coarse correction reads the fine step's input and rewrites the parent's
+//   output, which an earlier launch finished.
+enum { kTaskNone = 0, kTaskSnapC2f = 1, kTaskC2f = 2, kTaskF2c = 3 };
 struct RefTask {
-    int blocks;       // blocks of the task: the first of the launch, so that its short chain
-                      // of dependent loads starts at once instead of behind the last wave
+    int blocks;       // blocks of the task
     int n;            // interface nodes
     StepArgs p, f, rs;  // parent step, fine level and rescale arguments of the task
     const int4 *If;
@@ -375,24 +377,34 @@ struct RefTask {
     int x0, y0, nxp, nyp;
 };
 
-template <int Q, bool MRT, bool PERIODIC, int TASK, bool TASK_PER>
+template <int Q, bool MRT, int TASK, bool TASK_PER>
+__device__ __forceinline__ void run_task(const RefTask &x, int j) {
+    if (j >= x.n) return;
+    if (TASK == kTaskSnapC2f)
+        snap_c2f_node<Q, MRT>(x.p, x.f, x.rs, x.If, j, x.Ic, x.Ua, x.Ucur, x.alpha, x.nxf, x.nyf);
+    else if (TASK == kTaskC2f)
+        c2f_node<Q, MRT>(x.f, x.rs, x.If, j, x.Ua, x.Ub, x.alpha, x.nxf, x.nyf);
+    else if (TASK == kTaskF2c)
+        f2c_node<Q, MRT, TASK_PER>(x.p, x.rs, x.fin, x.fraw, x.fpitch, x.fplane, x.Ic, j, x.x0,
+                                   x.y0, x.nxp, x.nyp);
+}
+
+template <int Q, bool MRT, bool PERIODIC, int T1, bool P1, int T2, bool P2>
 __global__ void __launch_bounds__(kThreads, Q == 5 ? 5 : 4)
-    ref_step_kernel(const StepArgs a, const RefTask x) {
+    ref_step_kernel(const StepArgs a, const RefTask x1, const RefTask x2) {
     pdl_trigger_and_wait();
     __shared__ float s_tab[kThreads];
-    const int blk = (int)blockIdx.x - x.blocks;
-    if (blk < 0) {  // block-uniform: the coupling task
-        const int j = (int)blockIdx.x * kThreads + (int)threadIdx.x;
-        if (j >= x.n) return;
-        if (TASK == kTaskSnapC2f)
-            snap_c2f_node<Q, MRT>(x.p, x.f, x.rs, x.If, j, x.Ic, x.Ua, x.Ucur, x.alpha, x.nxf, x.nyf);
-        else if (TASK == kTaskC2f)
-            c2f_node<Q, MRT>(x.f, x.rs, x.If, j, x.Ua, x.Ub, x.alpha, x.nxf, x.nyf);
-        else
-            f2c_node<Q, MRT, TASK_PER>(x.p, x.rs, x.fin, x.fraw, x.fpitch, x.fplane, x.Ic, j, x.x0,
-                                       x.y0, x.nxp, x.nyp);
+    const int b0 = (int)blockIdx.x;
+    if (b0 < x1.blocks) {  // block-uniform: the first task
+        run_task<Q, MRT, T1, P1>(x1, b0 * kThreads + (int)threadIdx.x);
         return;
     }
+    const int b1 = b0 - x1.blocks;
+    if (T2 != kTaskNone && b1 < x2.blocks) {  // block-uniform: the second task
+        run_task<Q, MRT, T2, P2>(x2, b1 * kThreads + (int)threadIdx.x);
+        return;
+    }
+    const int blk = b1 - (T2 != kTaskNone ? x2.blocks : 0);
     if (blk >= a.main_blocks) {  // block-uniform: receivers
         gather_receivers<Q, PERIODIC, float>(a, (blk - a.main_blocks) * kThreads + (int)threadIdx.x);
         return;
@@ -862,116 +874,153 @@ lb_status refine_after_set_state(lb_ctx *ctx, const float *p0_dev) {
     return check_launch(ctx, "refined initial state");
 }
 
+// The task shapes a fused launch takes: the coarse step with the snapshot transfer; a fine
+// step with its own midpoint transfer (and, above a nested patch, that patch's snapshot);
+// a fine step with its correction of the parent (and the nested patch's snapshot).  The
+// correction is periodic only towards a periodic coarse grid.
 template <int Q, bool MRT>
-cudaError_t launch_task_q(lb_ctx *ctx, int task, bool per, bool task_per, const StepArgs &a,
-                          int rec_blocks, RefTask x) {
-    x.blocks = blocks_for(x.n);
-    const dim3 grid(x.blocks + a.main_blocks + rec_blocks), block(kThreads);
-    if (task == kTaskSnapC2f)  // in the parent's step (coarse grid: either boundary)
-        return per ? launch_pdl(ref_step_kernel<Q, MRT, true, kTaskSnapC2f, false>, grid, block, 0,
-                                ctx->stream, a, x)
-                   : launch_pdl(ref_step_kernel<Q, MRT, false, kTaskSnapC2f, false>, grid, block, 0,
-                                ctx->stream, a, x);
-    if (task == kTaskC2f)  // in a fine step (zero ghost)
-        return launch_pdl(ref_step_kernel<Q, MRT, false, kTaskC2f, false>, grid, block, 0,
-                          ctx->stream, a, x);
-    // in a fine step; the correction reads and writes the parent's grid
-    return task_per ? launch_pdl(ref_step_kernel<Q, MRT, false, kTaskF2c, true>, grid, block, 0,
-                                 ctx->stream, a, x)
-                    : launch_pdl(ref_step_kernel<Q, MRT, false, kTaskF2c, false>, grid, block, 0,
-                                 ctx->stream, a, x);
+cudaError_t launch_tasks_q(lb_ctx *ctx, int t1, int t2, bool per, bool f2c_per, const StepArgs &a,
+                           int rec_blocks, RefTask x1, RefTask x2) {
+    x1.blocks = blocks_for(x1.n);
+    x2.blocks = t2 != kTaskNone ? blocks_for(x2.n) : 0;
+    const dim3 grid(x1.blocks + x2.blocks + a.main_blocks + rec_blocks), block(kThreads);
+    cudaStream_t st = ctx->stream;
+    if (t1 == kTaskSnapC2f && t2 == kTaskNone)  // the coarse step (either boundary)
+        return per ? launch_pdl(ref_step_kernel<Q, MRT, true, kTaskSnapC2f, false, kTaskNone, false>,
+                                grid, block, 0, st, a, x1, x2)
+                   : launch_pdl(ref_step_kernel<Q, MRT, false, kTaskSnapC2f, false, kTaskNone, false>,
+                                grid, block, 0, st, a, x1, x2);
+    if (t1 == kTaskC2f && t2 == kTaskNone)
+        return launch_pdl(ref_step_kernel<Q, MRT, false, kTaskC2f, false, kTaskNone, false>, grid,
+                          block, 0, st, a, x1, x2);
+    if (t1 == kTaskC2f && t2 == kTaskSnapC2f)
+        return launch_pdl(ref_step_kernel<Q, MRT, false, kTaskC2f, false, kTaskSnapC2f, false>, grid,
+                          block, 0, st, a, x1, x2);
+    if (t1 == kTaskF2c && t2 == kTaskNone)
+        return f2c_per ? launch_pdl(ref_step_kernel<Q, MRT, false, kTaskF2c, true, kTaskNone, false>,
+                                    grid, block, 0, st, a, x1, x2)
+                       : launch_pdl(ref_step_kernel<Q, MRT, false, kTaskF2c, false, kTaskNone, false>,
+                                    grid, block, 0, st, a, x1, x2);
+    if (t1 == kTaskF2c && t2 == kTaskSnapC2f)
+        return f2c_per
+                   ? launch_pdl(ref_step_kernel<Q, MRT, false, kTaskF2c, true, kTaskSnapC2f, false>,
+                                grid, block, 0, st, a, x1, x2)
+                   : launch_pdl(ref_step_kernel<Q, MRT, false, kTaskF2c, false, kTaskSnapC2f, false>,
+                                grid, block, 0, st, a, x1, x2);
+    return cudaErrorInvalidValue;
 }
 
-// A step with a coupling task in its leading blocks (ref_step_kernel).
-cudaError_t launch_task(lb_ctx *ctx, int task, bool per, bool task_per, const StepArgs &a,
-                        int rec_blocks, const RefTask &x) {
+cudaError_t launch_tasks(lb_ctx *ctx, int t1, int t2, bool per, bool f2c_per, const StepArgs &a,
+                         int rec_blocks, const RefTask &x1, const RefTask &x2) {
     const bool mrt = ctx->cfg.collision == LB_MRT;
     if (ctx->Q == 9)
-        return mrt ? launch_task_q<9, true>(ctx, task, per, task_per, a, rec_blocks, x)
-                   : launch_task_q<9, false>(ctx, task, per, task_per, a, rec_blocks, x);
-    return mrt ? launch_task_q<5, true>(ctx, task, per, task_per, a, rec_blocks, x)
-               : launch_task_q<5, false>(ctx, task, per, task_per, a, rec_blocks, x);
+        return mrt ? launch_tasks_q<9, true>(ctx, t1, t2, per, f2c_per, a, rec_blocks, x1, x2)
+                   : launch_tasks_q<9, false>(ctx, t1, t2, per, f2c_per, a, rec_blocks, x1, x2);
+    return mrt ? launch_tasks_q<5, true>(ctx, t1, t2, per, f2c_per, a, rec_blocks, x1, x2)
+               : launch_tasks_q<5, false>(ctx, t1, t2, per, f2c_per, a, rec_blocks, x1, x2);
 }
 
-// Coarse step T of a two-level grid (one patch, coupled both ways, T >= 1, no raw state) in
-// three launches instead of six: each coupling task rides in the leading blocks of a step
-// whose buffers it does not touch.
-//   1. coarse step T + the snapshot of U(T) fused with the midpoint transfer into the ring
-//      of the patch's input;
-//   2. fine step 2T - 1, its ring left alone, + the transfer at time 2T into that ring;
-//   3. fine step 2T (receivers), ring left alone, + the fine -> coarse correction of the
-//      coarse output of step T (launch 1 finished it) from the input of step 2T.
-// The same kernels' per-node code, in the same order of dependence: the results equal the
-// six-launch sequence bit for bit.
-lb_status fused_coarse_step(lb_ctx *ctx, lb_refine *R, const StepArgs &ac, int rec_blocks,
-                            bool periodic, float *trace_row, long long T) {
-    const int Q = ctx->Q;
-    float *Ucur = R->U[T & 1], *Uprev = R->U[(T + 1) & 1];
-    RefTask x1 = {};
-    x1.n = R->nIf;
-    x1.p = ac;
-    x1.f = level_args(ctx, R);
-    x1.f.in = R->pop[R->cur];
-    x1.rs = rescale_args(x1.f, Q, R->c2f_omega, R->c2f_s);
-    x1.If = R->If;
-    x1.Ic = R->Ic;
-    x1.Ua = Uprev;
-    x1.Ucur = Ucur;
-    x1.alpha = 0.5f;
-    x1.nxf = R->nxf;
-    x1.nyf = R->nyf;
-    cudaError_t e = launch_task(ctx, kTaskSnapC2f, periodic, false, ac, rec_blocks, x1);
+// R's snapshot of its parent's step T (args ap) fused with the midpoint transfer into the
+// ring of R's input
+RefTask snap_task(lb_ctx *ctx, lb_refine *R, const StepArgs &ap, long long T) {
+    RefTask x = {};
+    x.n = R->nIf;
+    x.p = ap;
+    x.f = level_args(ctx, R);
+    x.f.in = R->pop[R->cur];
+    x.rs = rescale_args(x.f, ctx->Q, R->c2f_omega, R->c2f_s);
+    x.If = R->If;
+    x.Ic = R->Ic;
+    x.Ua = R->U[(T + 1) & 1];
+    x.Ucur = R->U[T & 1];
+    x.alpha = 0.5f;
+    x.nxf = R->nxf;
+    x.nyf = R->nyf;
+    return x;
+}
 
-    StepArgs f1 = level_args(ctx, R);
-    f1.in = R->pop[R->cur];
-    f1.out = R->pop[R->cur ^ 1];
-    f1.t = 2 * T - 1;
-    f1.ring = 1;
-    RefTask x2 = {};
-    x2.n = R->nIf;
-    x2.f = level_args(ctx, R);
-    x2.f.in = R->pop[R->cur ^ 1];  // the ring of step 2T - 1's output
-    x2.rs = rescale_args(x2.f, Q, R->c2f_omega, R->c2f_s);
-    x2.If = R->If;
-    x2.Ua = Ucur;
-    x2.Ub = Ucur;
-    x2.alpha = 1.f;
-    x2.nxf = R->nxf;
-    x2.nyf = R->nyf;
-    if (e == cudaSuccess) e = launch_task(ctx, kTaskC2f, false, false, f1, 0, x2);
-    R->cur ^= 1;
+// R's transfer at the parent's time T into the ring of the output of R's step running now
+RefTask c2f_task(lb_ctx *ctx, lb_refine *R, long long T) {
+    RefTask x = {};
+    x.n = R->nIf;
+    x.f = level_args(ctx, R);
+    x.f.in = R->pop[R->cur ^ 1];
+    x.rs = rescale_args(x.f, ctx->Q, R->c2f_omega, R->c2f_s);
+    x.If = R->If;
+    x.Ua = R->U[T & 1];
+    x.Ub = R->U[T & 1];
+    x.alpha = 1.f;
+    x.nxf = R->nxf;
+    x.nyf = R->nyf;
+    return x;
+}
 
-    StepArgs f2 = level_args(ctx, R);
-    f2.in = R->pop[R->cur];
-    f2.out = R->pop[R->cur ^ 1];
-    f2.t = 2 * T;
-    f2.ring = 1;
-    int frec = 0;
+// R's correction of its parent's step output (args ap) from R's state at its input now
+RefTask f2c_task(lb_ctx *ctx, lb_refine *R, const StepArgs &ap) {
+    RefTask x = {};
+    x.n = R->nI;
+    x.p = ap;
+    x.rs = rescale_args(ap, ctx->Q, R->f2c_omega, R->f2c_s);
+    x.fin = static_cast<const float *>(R->pop[R->cur]);
+    x.fraw = 0;
+    x.fpitch = R->pitch;
+    x.fplane = (long long)R->gy * R->pitch;
+    x.Ic = R->Ic;
+    x.x0 = R->x0;
+    x.y0 = R->y0;
+    x.nxp = R->nxp;
+    x.nyp = R->nyp;
+    return x;
+}
+
+// Arguments of R's step t (pull from pop[cur] into pop[cur ^ 1], ring left alone), with R's
+// receivers at trace_row; *rec_blocks gets their gather blocks.
+StepArgs ring_step_args(lb_ctx *ctx, lb_refine *R, long long t, float *trace_row, int *rec_blocks) {
+    StepArgs a = level_args(ctx, R);
+    a.in = R->pop[R->cur];
+    a.out = R->pop[R->cur ^ 1];
+    a.t = t;
+    a.ring = 1;
+    *rec_blocks = 0;
     if (trace_row && R->nrec_f > 0) {
-        f2.rec = R->rec_f;
-        f2.nrec = R->nrec_f;
-        f2.rec_col = R->col_f;
-        f2.trace_row = trace_row;
-        frec = (R->nrec_f + kThreads - 1) / kThreads;
+        a.rec = R->rec_f;
+        a.nrec = R->nrec_f;
+        a.rec_col = R->col_f;
+        a.trace_row = trace_row;
+        *rec_blocks = (R->nrec_f + kThreads - 1) / kThreads;
     }
-    RefTask x3 = {};
-    x3.n = R->nI;
-    x3.p = ac;
-    x3.rs = rescale_args(ac, Q, R->f2c_omega, R->f2c_s);
-    x3.fin = static_cast<const float *>(R->pop[R->cur]);
-    x3.fraw = 0;
-    x3.fpitch = R->pitch;
-    x3.fplane = (long long)R->gy * R->pitch;
-    x3.Ic = R->Ic;
-    x3.x0 = R->x0;
-    x3.y0 = R->y0;
-    x3.nxp = R->nxp;
-    x3.nyp = R->nyp;
-    if (e == cudaSuccess) e = launch_task(ctx, kTaskF2c, false, periodic, f2, frec, x3);
+    return a;
+}
+
+// R's two steps within its parent's step T (parent step arguments ap; T >= 1, every level
+// coupled both ways and none raw), each coupling task in a step launch whose buffers it does
+// not touch:
+//   R step 2T - 1 (ring left alone) + R's transfer at T into that step's output ring
+//     [+ the nested patch's snapshot of this step];  then the nested patch's two steps;
+//   R step 2T (receivers) + R's correction of the parent's output of step T from R's input
+//     [+ the nested patch's snapshot];  then the nested patch's two steps.
+// The parent's snapshot for R rode in the parent's own step launch.  Same per-node code and
+// order of dependence as child_steps: the results equal it bit for bit.  A two-level grid
+// takes three launches per coarse step instead of six; two nested patches seven instead of
+// sixteen.
+cudaError_t fused_pair(lb_ctx *ctx, lb_refine *R, const StepArgs &ap, bool ap_periodic,
+                       float *trace_row, long long T) {
+    lb_refine *S = R->sub;
+    int rb = 0;
+    StepArgs a1 = ring_step_args(ctx, R, 2 * T - 1, nullptr, &rb);
+    RefTask none = {};
+    cudaError_t e = launch_tasks(ctx, kTaskC2f, S ? kTaskSnapC2f : kTaskNone, false, false, a1, rb,
+                                 c2f_task(ctx, R, T), S ? snap_task(ctx, S, a1, 2 * T - 1) : none);
+    if (e == cudaSuccess && S) e = fused_pair(ctx, S, a1, false, nullptr, 2 * T - 1);
+    R->cur ^= 1;
+    StepArgs a2 = ring_step_args(ctx, R, 2 * T, trace_row, &rb);
+    if (e == cudaSuccess)
+        e = launch_tasks(ctx, kTaskF2c, S ? kTaskSnapC2f : kTaskNone, false, ap_periodic, a2, rb,
+                         f2c_task(ctx, R, ap), S ? snap_task(ctx, S, a2, 2 * T) : none);
+    if (e == cudaSuccess && S) e = fused_pair(ctx, S, a2, false, trace_row, 2 * T);
     R->cur ^= 1;
     R->raw = false;
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "refined step launch");
-    return LB_OK;
+    return e;
 }
 
 lb_status refine_step(lb_ctx *ctx, int n) {
@@ -994,9 +1043,14 @@ lb_status refine_step(lb_ctx *ctx, int n) {
         ac.rec_col = R->col_c;
         ac.trace_row = R->nrec_c > 0 ? trace_row : nullptr;
         int rec_blocks = ac.trace_row ? (R->nrec_c + kThreads - 1) / kThreads : 0;
-        if (R->sub == nullptr && R->coupling == LB_COUPLE_BOTH && !R->raw && T >= 1) {
-            lb_status st = fused_coarse_step(ctx, R, ac, rec_blocks, periodic, trace_row, T);
-            if (st != LB_OK) return st;
+        bool fused = T >= 1;
+        for (const lb_refine *L = R; L; L = L->sub)
+            fused = fused && L->coupling == LB_COUPLE_BOTH && !L->raw;
+        if (fused) {  // the coarse step with level 1's snapshot, then the levels' pairs
+            cudaError_t e = launch_tasks(ctx, kTaskSnapC2f, kTaskNone, periodic, false, ac,
+                                         rec_blocks, snap_task(ctx, R, ac, T), RefTask{});
+            if (e == cudaSuccess) e = fused_pair(ctx, R, ac, periodic, trace_row, T);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "refined step launch");
         } else {
             launch_pdl(coarse_fn, dim3(ac.main_blocks + rec_blocks), dim3(kThreads), 0, ctx->stream,
                        ac);

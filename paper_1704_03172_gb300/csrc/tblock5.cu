@@ -85,12 +85,13 @@ lb_status tb5_launch_args(lb_ctx *ctx, const StepArgs &a, int K) {
     }
     const int OUT = kWS - 2 * K;
     const int strips = (ctx->nx + OUT - 1) / OUT;
-    // rows per CTA: one wave of CTAs over the SMs when the chunks stay tall (>= 8K rows, so
-    // the 2K warm-up rows cost little), else chunks of 8K rows
+    // rows per CTA: the chunks of one wave of CTAs over the SMs.  A CTA sweeps its H + 2K
+    // rows one after another, so a wave of short chunks beats fewer tall ones even though
+    // each chunk recomputes 2K warm-up rows (GB300, two-layer 1024^2, K = 8: chunks of at
+    // least 8K rows gave 80 CTAs and 60 GLUPS)
     const int slots = std::max(1, occ[K] * std::max(sms, 1));
-    int chunks = std::max(1, slots / strips);
-    int H = (ctx->ny + chunks - 1) / chunks;
-    H = std::max(H, std::min(ctx->ny, 8 * K));
+    const int chunks = std::max(1, slots / strips);
+    const int H = std::max(1, (ctx->ny + chunks - 1) / chunks);
     Tb5Args tb;
     tb.row_off = a.trace_row ? ctx->tb5_off : nullptr;
     tb.rec_x = ctx->tb5_x;
