@@ -48,15 +48,15 @@ KERNEL_SOURCES = {
 }
 NCU_TRAFFIC = {
     ("lbk::step_kernel<5,false,false,float>", True):
-        (638.2e6, "4981af4f74d3", "profiles/step_kernel_d2q5_f32_4096.md"),
+        (638.3e6, "7cddfe4a6dae", "profiles/step_kernel_d2q5_f32_4096.md"),
     ("stream_step_kernel<5,false,false,__nv_bfloat16>", True):
-        (300.6e6, "a94f2a9b01cf", "profiles/stream_step_kernel_d2q5_bf16_4096.md"),
+        (300.2e6, "7389c23bc8d9", "profiles/stream_step_kernel_d2q5_bf16_4096.md"),
     ("lbtb5::tb5_kernel<false,4,false,float>", True):
-        (656.4e6, "8e6aa48e247b", "profiles/tb5_kernel_d2q5_4096.md"),
+        (656.4e6, "fb0dd3b5c69e", "profiles/tb5_kernel_d2q5_4096.md"),
     ("lbtb5::tb5_kernel<false,4,false,__nv_bfloat16>", True):
-        (314.9e6, "8e6aa48e247b", "profiles/tb5_kernel_d2q5_4096.md"),
+        (314.8e6, "fb0dd3b5c69e", "profiles/tb5_kernel_d2q5_4096.md"),
     ("lbtb5::tb5_kernel<false,8,false,float>", True):
-        (674.2e6, "8e6aa48e247b", "profiles/tb5_kernel_d2q5_4096.md"),
+        (671.9e6, "fb0dd3b5c69e", "profiles/tb5_kernel_d2q5_4096.md"),
 }
 
 

@@ -124,7 +124,8 @@ struct StepArgs {
     int raw;                 // 1: `in` holds g(t) itself (set by lb_set_state / lb_init_pressure)
     int ring;                // 1: store nothing on the outermost rows and columns (a refined
                              // patch's ghost ring, whose entering populations the coarse ->
-                             // fine transfer of the same launch writes)
+                             // fine transfer of the same launch writes); read by the RING
+                             // instances of step_sites only
     int swap;                // in-place streaming: `in` holds h(t-1) at its own site, population
                              // i in slot opp(i), so g_i(x, t) = in[opp(i)](x - c_i)
     // receivers
@@ -779,7 +780,7 @@ __device__ __forceinline__ void collide_sites_any(R (&g)[Q][V], const R (&e2s)[V
 // input scale, the adjoint replay's rho record, collision + source + sponge, and
 // the vector store of h(t) (FP16: scaled, with this thread's max |h_i| folded
 // into tmax).  Shared by the register-streaming and the TMA-staged kernels.
-template <int Q, bool MRT, typename ST, bool SLAB = false>
+template <int Q, bool MRT, typename ST, bool SLAB = false, bool RING = false>
 __device__ __forceinline__ void finish_sites(const StepArgs &a, float (&g)[Q][Store<ST>::V],
                                              const float (&e2s)[Store<ST>::V], int x0, int y,
                                              float tmax[Q]) {
@@ -823,8 +824,10 @@ __device__ __forceinline__ void finish_sites(const StepArgs &a, float (&g)[Q][St
     // sites are all real and outside the sponge (almost all) skip damping and masking.
     collide_sites_any<Q, MRT, V>(g, e2s, a, x0, dyz, has_src, edge);
     ST *o = static_cast<ST *>(a.out) + (long long)y * a.pitch + x0;
-    const bool ring_row = a.ring && (y == 0 || y == a.ny - 1);        // warp-uniform
-    const bool ring_col = a.ring && (x0 == 0 || x0 + V >= a.nx);
+    // RING: the instance that honours StepArgs::ring (refined fine steps only; the test
+    // costs the register-heavy 16-bit forms up to 15 %)
+    const bool ring_row = RING && a.ring && (y == 0 || y == a.ny - 1);  // warp-uniform
+    const bool ring_col = RING && a.ring && (x0 == 0 || x0 + V >= a.nx);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         if (SC) {
@@ -860,7 +863,7 @@ __device__ __forceinline__ void finish_sites(const StepArgs &a, float (&g)[Q][St
 
 // The sites of one warp row-segment of block `blk`; tmax receives this
 // thread's max |out_i|.  SLAB: the context is a row slab (halo rows at the cuts).
-template <int Q, bool MRT, bool PERIODIC, typename ST, bool SLAB = false>
+template <int Q, bool MRT, bool PERIODIC, typename ST, bool SLAB = false, bool RING = false>
 __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tmax[Q],
                                            const float *tab) {
 #pragma unroll
@@ -930,7 +933,7 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
             e2s[k] = e.x; e2s[k + 1] = e.y; e2s[k + 2] = e.z; e2s[k + 3] = e.w;
         }
     }
-    finish_sites<Q, MRT, ST, SLAB>(a, g, e2s, x0, y, tmax);
+    finish_sites<Q, MRT, ST, SLAB, RING>(a, g, e2s, x0, y, tmax);
 }
 
 template <int Q, bool MRT, bool PERIODIC, typename ST, bool SLAB = false>

@@ -414,7 +414,8 @@ __global__ void __launch_bounds__(kThreads, Q == 5 ? 5 : 4)
         __syncthreads();
     }
     float tmax[Q];
-    step_sites<Q, MRT, PERIODIC, float>(a, blk, tmax, s_tab);
+    // every fused fine step leaves its ring to a transfer; the coarse step has none
+    step_sites<Q, MRT, PERIODIC, float, false, T1 != kTaskSnapC2f>(a, blk, tmax, s_tab);
 }
 
 // context-grid pressure at the coarse nodes covered by a level, from its coincident nodes:
