@@ -1001,7 +1001,8 @@ StepArgs ring_step_args(lb_ctx *ctx, lb_refine *R, long long t, float *trace_row
 //   R step 2T (receivers) + R's correction of the parent's output of step T from R's input
 //     [+ the nested patch's snapshot];  then the nested patch's two steps.
 // The parent's snapshot for R rode in the parent's own step launch.  Same per-node code and
-// order of dependence as child_steps: the results equal it bit for bit.  A two-level grid
+// order of dependence as child_steps (the refined-block workload's 256 receiver traces after
+// 4000 coarse steps agree with the six-launch run to every printed digit).  A two-level grid
 // takes three launches per coarse step instead of six; two nested patches seven instead of
 // sixteen.
 cudaError_t fused_pair(lb_ctx *ctx, lb_refine *R, const StepArgs &ap, bool ap_periodic,
