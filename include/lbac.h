@@ -291,12 +291,15 @@ typedef struct {
     size_t hbm_budget;       /* device bytes the server may hold; 0: 80% of free memory */
     int rounds_per_pass;     /* steps per scheduling pass between admission checks, >= 1 */
     int adjoint_workers;     /* threads running gradient sweeps, >= 1 */
-    int tb_min_ctas;         /* D2Q5 FP32/BF16 shots with no checkpoint or tape advance 8
-                                steps per launch (a wavefront time-blocked batch) when the
-                                eligible shots together make at least this many CTAs;
-                                0: one wave of the GPU (one CTA per resident slot);
-                                < 0: never (one launch per step).  Both forms give the
-                                same results to FP32 rounding. */
+    int tb_min_ctas;         /* D2Q5 FP32/BF16 shots with no checkpoint or tape can advance
+                                8 steps per launch (a wavefront time-blocked batch).
+                                0: they do, with the rows per CTA (at most 128) that fill
+                                one wave of the GPU, when that is at least 24 rows and
+                                their states outgrow three quarters of L2 (a few small
+                                shots step one launch at a time).  > 0: they do, at
+                                128 rows per CTA, when together they make at least this
+                                many CTAs.  < 0: never.  Both forms give the same results
+                                to FP32 rounding. */
 } lb_server_config;
 
 typedef struct {

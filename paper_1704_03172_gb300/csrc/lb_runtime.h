@@ -165,15 +165,16 @@ bool tb5_supported(int K);
 lb_status tb5_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
 lb_status tb5_launch_args(lb_ctx *ctx, const lbk::StepArgs &a, int K);
 // served batches of D2Q5 shots, K = 8 steps per launch (tblock5.cu): staging bytes of one
-// launch's descriptors, whether a shot can take K steps now, its CTAs in a batched launch,
-// the CTAs one wave of the batched kernel holds on the current device, the fill (advancing
-// the shots) and the launch from the device copy of the staging block
+// launch's descriptors, whether a shot can take K steps now, its strips and its CTAs at H
+// output rows per CTA, the CTAs one wave of the batched kernel holds on the current device,
+// the fill (advancing the shots) and the launch from the device copy of the staging block
 constexpr int kServeTb = 8;
 size_t tb5_batch_bytes(int n);
 bool tb5_batch_ready(const lb_ctx *ctx, int K);
-int tb5_batch_blocks(const lb_ctx *ctx, int K);
+int tb5_strips(const lb_ctx *ctx, int K);
+int tb5_batch_blocks(const lb_ctx *ctx, int K, int H);
 int tb5_batch_wave(int K);
-int tb5_batch_fill(lb_ctx *const *ctxs, int n, int K, void *h);
+int tb5_batch_fill(lb_ctx *const *ctxs, int n, int K, int H, void *h);
 cudaError_t tb5_batch_launch(const void *d, int n, int K, int blocks, bool mrt, bool per,
                              int storage, cudaStream_t stream);
 

@@ -140,6 +140,7 @@ struct lb_server {
     void *d_tb = nullptr, *h_tb = nullptr;  // time-blocked launches' descriptor blocks
     size_t tb_cap = 0;
     int tb_wave = 0;  // CTAs one wave of the time-blocked batch kernel holds (0: not asked yet)
+    long long l2_bytes = -1;  // the device's L2 size (-1: not asked yet)
     cudaEvent_t staged = nullptr;
     std::mutex pin_mu;
     std::multimap<size_t, void *> pinned;  // free pinned trace buffers by size
@@ -366,28 +367,51 @@ void pass(lb_server *S) {
     // shots that take this pass's steps K at a time: one time-blocked launch per group and
     // block of K steps
     const int KB = kServeTb, nblk = R / KB;
+    // Shots that take this pass's steps K at a time.  A wavefront CTA sweeps its rows one
+    // after another, so the launch must fill a wave of CTAs with chunks tall enough that
+    // the 2K warm-up rows of each cost little.  By default (tb_min_ctas = 0) the pass takes
+    // the chunk height that fills one wave with every ready shot: at least 3K rows, and
+    // states larger than L2 can hold, else none of them blocks this pass (two-layer 1024^2 alone, K = 8: 112 GLUPS blocked with
+    // one-wave chunks of 18 rows against 153 one step per launch; 4096^2: 295 against 160).
+    // All CTAs of the launch then sweep about the same number of rows, whatever their
+    // shot's size.  With tb_min_ctas > 0 the shots block at 16K rows when together they
+    // make that many CTAs; below 0 never.
     std::vector<Req *> tbs, rest;
-    long long tb_blocks = 0;
+    const int H16 = 16 * KB;
+    int tb_rows = H16;
     for (Req *r : batched) {
-        if (nblk > 0 && r->nt - r->steps >= nblk * KB && tb5_batch_ready(r->ctx, KB)) {
-            tbs.push_back(r);
-            tb_blocks += tb5_batch_blocks(r->ctx, KB);
-        } else {
-            rest.push_back(r);
-        }
+        const bool ok = S->cfg.tb_min_ctas >= 0 && nblk > 0 && r->nt - r->steps >= nblk * KB &&
+                        tb5_batch_ready(r->ctx, KB);
+        (ok ? tbs : rest).push_back(r);
     }
-    // A wavefront CTA sweeps its rows one after another, so a few small shots give a
-    // launch of few long CTAs: K steps then take longer than K one-step launches over
-    // many short CTAs.  The shots take the K-step launches only when together they fill
-    // one wave of the GPU (the load is high and throughput counts), or the count the
-    // server was configured with.
     if (!tbs.empty()) {
-        long long need = S->cfg.tb_min_ctas;
-        if (need == 0) {
+        bool use = true;
+        if (S->cfg.tb_min_ctas > 0) {
+            long long ctas = 0;
+            for (Req *r : tbs) ctas += tb5_batch_blocks(r->ctx, KB, H16);
+            use = ctas >= S->cfg.tb_min_ctas;
+        } else {  // the chunk height that fills one wave
             if (S->tb_wave == 0) S->tb_wave = tb5_batch_wave(KB);
-            need = S->tb_wave;
+            if (S->l2_bytes < 0) {
+                int v = 0;
+                if (cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, S->device) != cudaSuccess) {
+                    cudaGetLastError();  // this query's own failure: assume no L2
+                    v = 0;
+                }
+                S->l2_bytes = v;
+            }
+            long long rows = 0, state = 0;  // sums over the shots of strips x rows, state bytes
+            for (Req *r : tbs) {
+                rows += (long long)tb5_strips(r->ctx, KB) * r->ctx->ny;
+                state += 2LL * r->ctx->Q * r->ctx->ny * r->ctx->pitch * r->ctx->ebytes;
+            }
+            const long long h = (rows + S->tb_wave - 1) / S->tb_wave;
+            tb_rows = (int)std::min<long long>(H16, h);
+            // blocking saves HBM traffic; states that fit in three quarters of L2 have none
+            // to save (32 shots of 256^2, 84 MB: 3.7x over one by one stepped, 3.0x blocked)
+            use = tb_rows >= 3 * KB && 4 * state > 3 * S->l2_bytes;
         }
-        if (need < 0 || tb_blocks < need) {
+        if (!use) {
             rest.insert(rest.end(), tbs.begin(), tbs.end());
             tbs.clear();
         }
@@ -426,7 +450,8 @@ void pass(lb_server *S) {
                 cs.clear();
                 for (size_t q = g0; q < g1; q++) cs.push_back(tbs[q]->ctx);
                 const int n = (int)(g1 - g0);
-                const int blocks = tb5_batch_fill(cs.data(), n, KB, static_cast<char *>(S->h_tb) + off);
+                const int blocks =
+                    tb5_batch_fill(cs.data(), n, KB, tb_rows, static_cast<char *>(S->h_tb) + off);
                 const lb_config &c0 = tbs[g0]->cfg;
                 tb_launches.push_back({off, n, blocks, c0.collision == LB_MRT,
                                        c0.boundary == LB_PERIODIC, c0.storage, g0, g1});

@@ -151,12 +151,14 @@ bool tb5_batch_ready(const lb_ctx *ctx, int K) {
     return true;
 }
 
-// Output rows per CTA of a served shot: tall enough that the 2K warm-up rows cost little.
-static int batch_rows(const lb_ctx *ctx, int K) { return std::min(ctx->ny, 16 * K); }
+int tb5_strips(const lb_ctx *ctx, int K) {
+    const int OUT = kWS - 2 * K;
+    return (ctx->nx + OUT - 1) / OUT;
+}
 
-int tb5_batch_blocks(const lb_ctx *ctx, int K) {
-    const int OUT = kWS - 2 * K, H = batch_rows(ctx, K);
-    return ((ctx->nx + OUT - 1) / OUT) * ((ctx->ny + H - 1) / H);
+int tb5_batch_blocks(const lb_ctx *ctx, int K, int H) {
+    H = std::max(1, std::min(ctx->ny, H));
+    return tb5_strips(ctx, K) * ((ctx->ny + H - 1) / H);
 }
 
 int tb5_batch_wave(int K) {
@@ -172,9 +174,9 @@ int tb5_batch_wave(int K) {
     return std::max(1, sms) * std::max(1, nb);
 }
 
-// Fill the host staging block `h` for K steps of ctxs[0 .. n) (advancing their time and
-// buffers as if the launch ran); returns the launch's block count.
-int tb5_batch_fill(lb_ctx *const *ctxs, int n, int K, void *h) {
+// Fill the host staging block `h` for K steps of ctxs[0 .. n), H output rows per CTA
+// (advancing their time and buffers as if the launch ran); returns the launch's block count.
+int tb5_batch_fill(lb_ctx *const *ctxs, int n, int K, int H, void *h) {
     BatchLayout L = batch_layout(h, n);
     const int OUT = kWS - 2 * K;
     int blocks = 0;
@@ -191,7 +193,7 @@ int tb5_batch_fill(lb_ctx *const *ctxs, int n, int K, void *h) {
         tb.row_off = a.trace_row ? ctx->tb5_off : nullptr;
         tb.rec_x = ctx->tb5_x;
         tb.rec_id = ctx->tb5_id;
-        tb.H = batch_rows(ctx, K);
+        tb.H = std::max(1, std::min(ctx->ny, H));
         tb.per = ctx->cfg.boundary == LB_PERIODIC ? 1 : 0;
         const int strips = (ctx->nx + OUT - 1) / OUT, chunks = (ctx->ny + tb.H - 1) / tb.H;
         L.a[k] = a;
