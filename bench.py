@@ -481,15 +481,14 @@ def _adjoint_variant(torch, LBSim, n=4096, nt=1000, every=200, storage="f32", mo
         sim.close()
     T = min(every, (16 << 30) // (n * n * 4))
     levels = 1 if T >= every else 2
-    if storage == "f32":  # replays run 8 steps per launch (48^2 regions, 32^2 tiles)
-        bps_fwd = ((48 / 32) ** 2 * (5 + 1) * 4 + 5 * 4) / 8
+    if storage == "f32":  # replays run 8 steps per launch (the D2Q5 wavefront kernel)
+        bps_fwd = bytes_per_site(5, storage, indexed) / 8
     else:
         bps_fwd = bytes_per_site(5, storage, indexed)
-    # per adjoint site-step: `levels` replays (+4 B rho store on the recorded one) and the
-    # blocked reverse sweep, 8 levels per launch on 32^2 tiles of 48^2 regions: lambda and
-    # eta^2 loads over the region, lambda store and FP64 gradient RMW over the tile once per
-    # 8 levels, and the rho tape read at every level
-    bps_adj = ((48 / 32) ** 2 * (5 * 4 + 4) + 5 * 4 + 16) / 8 + 4
+    # per adjoint site-step: the wavefront reverse sweep, 4 levels per launch: lambda read and
+    # written, eta^2 read and the FP64 gradient read-modify-write once per 4 levels, and the
+    # rho tape read at every level
+    bps_adj = (2 * 5 * 4 + 4 + 16) / 4 + 4
     bps = round(bps_adj if mode == "tape" else levels * bps_fwd + 4 + bps_adj, 2)
     upd = n * n * nt
     out = {"gradient_glups": round(upd / t_adj / 1e9, 2),
