@@ -276,7 +276,7 @@ lb_status lb_adjoint(lb_ctx *ctx, const float *dJdp, int nt, float *grad_c, doub
  * FP32/BF16 shot by one step per scheduling round with a single batched launch
  * per (lattice, collision, boundary, storage) group, so small shots share the
  * GPU and requests that arrive while others run join the batch at the next
- * round.  Under load, D2Q5 shots take 8 steps per batched launch instead
+ * round.  Under load, D2Q5 shots take 4 steps per batched launch instead
  * (lb_server_config.tb_min_ctas).  FP16 shots step on their own.  A request that asks for a gradient
  * records the forward rho tape or keeps checkpoints during its forward run
  * (lb_request.checkpoint_every) and its adjoint (lb_adjoint, J = 1/2
@@ -292,12 +292,12 @@ typedef struct {
     int rounds_per_pass;     /* steps per scheduling pass between admission checks, >= 1 */
     int adjoint_workers;     /* threads running gradient sweeps, >= 1 */
     int tb_min_ctas;         /* D2Q5 FP32/BF16 shots with no checkpoint or tape can advance
-                                8 steps per launch (a wavefront time-blocked batch).
-                                0: they do, with the rows per CTA (at most 128) that fill
-                                one wave of the GPU, when that is at least 24 rows and
+                                4 steps per launch (a wavefront time-blocked batch).
+                                0: they do, with the rows per CTA (at most 64) that fill
+                                one wave of the GPU, when that is at least 12 rows and
                                 their states outgrow three quarters of L2 (a few small
                                 shots step one launch at a time).  > 0: they do, at
-                                128 rows per CTA, when together they make at least this
+                                64 rows per CTA, when together they make at least this
                                 many CTAs.  < 0: never.  Both forms give the same results
                                 to FP32 rounding. */
 } lb_server_config;

@@ -164,11 +164,12 @@ lb_status aa_step(lb_ctx *ctx, int n);
 bool tb5_supported(int K);
 lb_status tb5_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
 lb_status tb5_launch_args(lb_ctx *ctx, const lbk::StepArgs &a, int K);
-// served batches of D2Q5 shots, K = 8 steps per launch (tblock5.cu): staging bytes of one
+// served batches of D2Q5 shots, K = kServeTb steps per launch (tblock5.cu; 4: the fastest
+// wavefront depth, 3 CTAs per SM at 72 registers): staging bytes of one
 // launch's descriptors, whether a shot can take K steps now, its strips and its CTAs at H
 // output rows per CTA, the CTAs one wave of the batched kernel holds on the current device,
 // the fill (advancing the shots) and the launch from the device copy of the staging block
-constexpr int kServeTb = 8;
+constexpr int kServeTb = 4;
 size_t tb5_batch_bytes(int n);
 bool tb5_batch_ready(const lb_ctx *ctx, int K);
 int tb5_strips(const lb_ctx *ctx, int K);

@@ -11,8 +11,9 @@
 //              reading its own StepArgs descriptor (uploaded once per pass), so
 //              many small shots share one launch and fill the GPU together.  D2Q5
 //              FP32 / BF16 shots that are far enough from their end take their steps
-//              8 at a time instead: one time-blocked launch (tb5_batch_kernel,
-//              tblock5.cu) per group advances every such shot by 8 steps.
+//              kServeTb at a time instead: one time-blocked launch
+//              (tb5_batch_kernel, tblock5.cu) per group advances every such shot by
+//              kServeTb steps.
 //              Shots that finish leave the batch (their traces are copied to
 //              pinned host memory), shots that are ready join at the next pass;
 //   workers    run the adjoint of gradient requests (lb_adjoint) on their own
@@ -370,12 +371,13 @@ void pass(lb_server *S) {
     // Shots that take this pass's steps K at a time.  A wavefront CTA sweeps its rows one
     // after another, so the launch must fill a wave of CTAs with chunks tall enough that
     // the 2K warm-up rows of each cost little.  By default (tb_min_ctas = 0) the pass takes
-    // the chunk height that fills one wave with every ready shot: at least 3K rows, and
-    // states larger than L2 can hold, else none of them blocks this pass (two-layer 1024^2 alone, K = 8: 112 GLUPS blocked with
-    // one-wave chunks of 18 rows against 153 one step per launch; 4096^2: 295 against 160).
-    // All CTAs of the launch then sweep about the same number of rows, whatever their
-    // shot's size.  With tb_min_ctas > 0 the shots block at 16K rows when together they
-    // make that many CTAs; below 0 never.
+    // the chunk height (at most 16K rows) that fills one wave with every ready shot: at
+    // least 3K rows, and states larger than L2 can hold, else none of them blocks this pass
+    // (two-layer 1024^2 alone, K = 8: 112 GLUPS blocked with one-wave chunks of 18 rows
+    // against 153 one step per launch; 4096^2: 295 against 160).  All CTAs of the launch
+    // then sweep about the same number of rows, whatever their shot's size.  With
+    // tb_min_ctas > 0 the shots block at 16K rows when together they make that many CTAs;
+    // below 0 never.
     std::vector<Req *> tbs, rest;
     const int H16 = 16 * KB;
     int tb_rows = H16;

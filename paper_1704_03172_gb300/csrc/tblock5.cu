@@ -25,8 +25,8 @@ Tb5Fn pick_f32(int K, bool mrt, bool rec) {
     }
 }
 Tb5BatchFn pick_batch_f32(int K, bool mrt) {
-    if (K != 8) return nullptr;
-    return mrt ? tb5_batch_kernel<true, 8, float> : tb5_batch_kernel<false, 8, float>;
+    if (K != kServeTb) return nullptr;
+    return mrt ? tb5_batch_kernel<true, kServeTb, float> : tb5_batch_kernel<false, kServeTb, float>;
 }
 }  // namespace lbtb5
 

@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kWS, tb5_min_blocks<K>()) tb5_kernel(const Ste
 // blocks [first[k], first[k + 1]) of the grid, laid out as its strips x row chunks, and
 // reads its own descriptors (the served batches; no rho tape).
 template <bool MRT, int K, typename ST>
-__global__ void __launch_bounds__(kWS, 2)
+__global__ void __launch_bounds__(kWS, tb5_min_blocks<K>())
     tb5_batch_kernel(const StepArgs *__restrict__ args, const Tb5Args *__restrict__ tbs,
                      const int *__restrict__ strips, const int *__restrict__ first, int nshots) {
     pdl_trigger_and_wait();

@@ -3,6 +3,7 @@
 // recorded by FP32 contexts only, so there is no recording instance here.
 #include <cuda_runtime.h>
 
+#include "lb_runtime.h"
 #include "tblock5.cuh"
 
 namespace lbtb5 {
@@ -18,7 +19,8 @@ Tb5Fn pick_bf16(int K, bool mrt, bool rec) {
     }
 }
 Tb5BatchFn pick_batch_bf16(int K, bool mrt) {
-    if (K != 8) return nullptr;
-    return mrt ? tb5_batch_kernel<true, 8, __nv_bfloat16> : tb5_batch_kernel<false, 8, __nv_bfloat16>;
+    if (K != kServeTb) return nullptr;
+    return mrt ? tb5_batch_kernel<true, kServeTb, __nv_bfloat16>
+               : tb5_batch_kernel<false, kServeTb, __nv_bfloat16>;
 }
 }  // namespace lbtb5

@@ -300,8 +300,8 @@ class LBForward(torch.autograd.Function):
 
 class LBServer:
     """Continuous-batching shot server (lb_server_* of the C ABI).  tb_min_ctas: 0 (default)
-    lets the eligible D2Q5 shots take 8 steps per launch when together they fill a wave of
-    the GPU with chunks of at least 24 rows; > 0 when they make that many CTAs at 128 rows;
+    lets the eligible D2Q5 shots take 4 steps per launch when together they fill a wave of
+    the GPU with chunks of at least 12 rows; > 0 when they make that many CTAs at 64 rows;
     < 0 never."""
 
     def __init__(self, max_active=64, hbm_budget=0, rounds_per_pass=16, adjoint_workers=2,
