@@ -52,11 +52,11 @@ NCU_TRAFFIC = {
     ("stream_step_kernel<5,false,false,__nv_bfloat16>", True):
         (300.2e6, "7389c23bc8d9", "profiles/stream_step_kernel_d2q5_bf16_4096.md"),
     ("lbtb5::tb5_kernel<false,4,false,float>", True):
-        (656.4e6, "fb0dd3b5c69e", "profiles/tb5_kernel_d2q5_4096.md"),
+        (656.3e6, "69235138f170", "profiles/tb5_kernel_d2q5_4096.md"),
     ("lbtb5::tb5_kernel<false,4,false,__nv_bfloat16>", True):
-        (314.8e6, "fb0dd3b5c69e", "profiles/tb5_kernel_d2q5_4096.md"),
+        (314.8e6, "69235138f170", "profiles/tb5_kernel_d2q5_4096.md"),
     ("lbtb5::tb5_kernel<false,8,false,float>", True):
-        (671.9e6, "fb0dd3b5c69e", "profiles/tb5_kernel_d2q5_4096.md"),
+        (672.0e6, "69235138f170", "profiles/tb5_kernel_d2q5_4096.md"),
 }
 
 

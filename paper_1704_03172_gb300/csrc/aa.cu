@@ -213,9 +213,97 @@ __device__ __forceinline__ void collide_site_vector(const StepArgs &a, const AaR
 }
 
 
+// The exchange step of a warp whose sites and neighbours are all interior: rows y - 1 and
+// y + 1 exist, the warp's first site has a left neighbour and its last a right one, and no
+// site is padding.  Nothing is wrapped, absent or a ghost, so the bounds and ghost logic of
+// the general form drops out.  The slot that population i pulls from, opp(i) at x - c_i,
+// lies in the row that population opp(i) pushes to, so one row pointer per slot serves
+// both.  Same values as the general form.
+template <int Q, bool MRT, typename ST>
+__device__ __forceinline__ void exchange_inner(const StepArgs &a, const AaRec &r,
+                                               const float *tab, ST *pop, int y, int x0,
+                                               int lane) {
+    constexpr int V = Store<ST>::V;
+    // slot s in row y + c_s,y holds h_opp(s), read as g_opp(s), and takes h_s; the pointers
+    // are formed again for the stores rather than held across the collision
+    ST *const rowp = pop + (long long)y * a.pitch + x0;
+    auto slot = [&](int s) { return rowp + s * a.plane + Lat<Q>::cy(s) * a.pitch; };
+    uint4 q[Q];
+    uint32_t e[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {  // all loads in flight together
+        const ST *src = slot(Lat<Q>::opp(i));
+        q[i] = *reinterpret_cast<const uint4 *>(src);
+        e[i] = 0u;
+        if (Lat<Q>::cx(i) == 1 && lane == 0) e[i] = Store<ST>::bits1(src - 1);
+        if (Lat<Q>::cx(i) == -1 && lane == 31) e[i] = Store<ST>::bits1(src + V);
+    }
+    float g[Q][V];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        float f[V];
+        Store<ST>::unpackV(q[i], f);
+        if (Lat<Q>::cx(i) == 1) {  // value from x - 1
+            float left = __shfl_up_sync(0xffffffffu, f[V - 1], 1);
+            if (lane == 0) left = Store<ST>::unbits1(e[i]);
+            g[i][0] = left;
+#pragma unroll
+            for (int k = 1; k < V; k++) g[i][k] = f[k - 1];
+        } else if (Lat<Q>::cx(i) == -1) {  // value from x + 1
+            float right = __shfl_down_sync(0xffffffffu, f[0], 1);
+            if (lane == 31) right = Store<ST>::unbits1(e[i]);
+#pragma unroll
+            for (int k = 0; k + 1 < V; k++) g[i][k] = f[k + 1];
+            g[i][V - 1] = right;
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++) g[i][k] = f[k];
+        }
+    }
+    collide_site_vector<Q, MRT, ST>(a, r, tab, g, y, x0);
+#pragma unroll
+    for (int s = 0; s < Q; s++) {  // h_s into slot s at x + c_s
+        ST *dst = slot(s) - x0;
+        if (Lat<Q>::cx(s) == 0) {
+            Store<ST>::storeV(dst + x0, g[s]);
+        } else if (Lat<Q>::cx(s) == 1) {  // position p takes site p - 1
+            const float left = __shfl_up_sync(0xffffffffu, g[s][V - 1], 1);
+            if (lane > 0) {
+                float out[V];
+                out[0] = left;
+#pragma unroll
+                for (int k = 1; k < V; k++) out[k] = g[s][k - 1];
+                Store<ST>::storeV(dst + x0, out);
+            } else {  // position x0 is the previous warp's
+#pragma unroll
+                for (int k = 1; k < V; k++) Store<ST>::store1(dst + x0 + k, g[s][k - 1]);
+            }
+            if (lane == 31) Store<ST>::store1(dst + x0 + V, g[s][V - 1]);
+        } else {  // position p takes site p + 1
+            const float right = __shfl_down_sync(0xffffffffu, g[s][0], 1);
+            if (lane < 31) {
+                float out[V];
+#pragma unroll
+                for (int k = 0; k + 1 < V; k++) out[k] = g[s][k + 1];
+                out[V - 1] = right;
+                Store<ST>::storeV(dst + x0, out);
+            } else {  // position x0 + V - 1 is the next warp's
+#pragma unroll
+                for (int k = 0; k + 1 < V; k++) Store<ST>::store1(dst + x0 + k, g[s][k + 1]);
+            }
+            if (lane == 0) Store<ST>::store1(dst + x0 - 1, g[s][0]);
+        }
+    }
+}
+
+// CTAs per SM: the FP32 exchange form holds row pointers and shifted vectors across the
+// collision and gets one CTA fewer (more registers) than the site-local form.
+template <int Q, typename ST, bool EXCHANGE> constexpr int aa_min_ctas() {
+    return sizeof(ST) == 4 ? (Q == 5 ? 5 : 4) - (EXCHANGE && Q == 9 ? 1 : 0) : (Q == 5 ? 3 : 2);
+}
+
 template <int Q, bool MRT, bool PERIODIC, typename ST, bool EXCHANGE>
-__global__ void __launch_bounds__(kThreads, Q == 5 ? (sizeof(ST) == 4 ? 5 : 3)
-                                                   : (sizeof(ST) == 4 ? 4 : 2))
+__global__ void __launch_bounds__(kThreads, (aa_min_ctas<Q, ST, EXCHANGE>()))
     aa_step_kernel(const StepArgs a, const AaRec r) {
     pdl_trigger_and_wait();
     __shared__ float tab[kThreads];
@@ -238,6 +326,11 @@ __global__ void __launch_bounds__(kThreads, Q == 5 ? (sizeof(ST) == 4 ? 5 : 3)
 #pragma unroll
         for (int i = 0; i < Q; i++) Store<ST>::loadV(pop + i * a.plane + row + x0, g[i]);
     } else {  // g_i(x) = slot opp(i) at x - c_i: the pull of step_kernel from the other slot
+        const int sx0 = x0 - lane * V;  // the warp's first site (warp-uniform test)
+        if (y > 0 && y + 1 < a.ny && sx0 > 0 && sx0 + 32 * V < a.nx) {
+            exchange_inner<Q, MRT, ST>(a, r, tab, pop, y, x0, lane);
+            return;
+        }
         uint4 q[Q];
         uint32_t e[Q];
         bool absent[Q];

@@ -568,38 +568,49 @@ __device__ __forceinline__ void collide5_lossless(R g[5], R e2) {
 // c_s^2 = eta^2 c2r, so w_i / c_s^2 = a1 or a5 does not depend on eta.
 template <bool MRT, typename R>
 __device__ __forceinline__ void collide9(R g[9], R e2, const StepArgs &a) {
-    const R rho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
-    const R jx = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
-    const R jy = g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
-    const R w1 = e2 * co<R>(a, a.w1r, kCoW1r), w5 = e2 * co<R>(a, a.w5r, kCoW5r);
-    R eq[9];
-    const R b1 = w1 * rho, b5 = w5 * rho;
-    eq[0] = rho - R(4) * (b1 + b5);  // = w_0 rho, mass-exact as in collide5
-    const R ux = co<R>(a, a.a1, kCoA1) * jx, uy = co<R>(a, a.a1, kCoA1) * jy;
-    eq[1] = b1 + ux; eq[3] = b1 - ux;
-    eq[2] = b1 + uy; eq[4] = b1 - uy;
-    const R a5 = co<R>(a, a.a5, kCoA5);
-    const R dp = a5 * (jx + jy), dm = a5 * (jx - jy);
-    eq[5] = b5 + dp; eq[7] = b5 - dp;
-    eq[6] = b5 - dm; eq[8] = b5 + dm;
     if constexpr (!MRT) {
+        const R rho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+        const R jx = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
+        const R jy = g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
+        const R w1 = e2 * co<R>(a, a.w1r, kCoW1r), w5 = e2 * co<R>(a, a.w5r, kCoW5r);
+        R eq[9];
+        const R b1 = w1 * rho, b5 = w5 * rho;
+        eq[0] = rho - R(4) * (b1 + b5);  // = w_0 rho, mass-exact as in collide5
+        const R ux = co<R>(a, a.a1, kCoA1) * jx, uy = co<R>(a, a.a1, kCoA1) * jy;
+        eq[1] = b1 + ux; eq[3] = b1 - ux;
+        eq[2] = b1 + uy; eq[4] = b1 - uy;
+        const R a5 = co<R>(a, a.a5, kCoA5);
+        const R dp = a5 * (jx + jy), dm = a5 * (jx - jy);
+        eq[5] = b5 + dp; eq[7] = b5 - dp;
+        eq[6] = b5 - dm; eq[8] = b5 + dm;
 #pragma unroll
         for (int i = 0; i < 9; i++) g[i] += co<R>(a, a.omega, kCoOmega) * (eq[i] - g[i]);
     } else {
-        R n[9];
-#pragma unroll
-        for (int i = 0; i < 9; i++) n[i] = g[i] - eq[i];
-        const R s14 = n[1] + n[2] + n[3] + n[4], s58 = n[5] + n[6] + n[7] + n[8];
-        // non-conserved moments of g - g^eq (rows 3..8 of M, App. A), scaled by s_k / |row_k|^2
-        // (the rates arrive divided by the squared row norms: 36, 4, 36, 12, 12, 4)
-        const R d3 = co<R>(a, a.s[3], kCoS + 3) * (-R(4) * n[0] - s14 + R(2) * s58);
-        const R d4 = co<R>(a, a.s[4], kCoS + 4) * (n[1] - n[2] + n[3] - n[4]);
-        const R d5 = co<R>(a, a.s[5], kCoS + 5) * (R(4) * n[0] - R(2) * s14 + s58);
-        const R d6 = co<R>(a, a.s[6], kCoS + 6) *
-                     (-R(2) * n[1] + R(2) * n[3] + n[5] - n[6] - n[7] + n[8]);
-        const R d7 = co<R>(a, a.s[7], kCoS + 7) *
-                     (-R(2) * n[2] + R(2) * n[4] + n[5] + n[6] - n[7] - n[8]);
-        const R d8 = co<R>(a, a.s[8], kCoS + 8) * (n[5] - n[6] + n[7] - n[8]);
+        // The non-conserved moments of g - g^eq (rows 3..8 of M, App. A) straight from g.
+        // With b1 = w_1 rho, b5 = w_5 rho and the equilibrium above, the moments of g^eq are
+        //   e^eq = -4 rho + 12 b1 + 24 b5,   eps^eq = 4 rho - 24 b1 - 12 b5,
+        //   q_x^eq = 4 (a5 - a1) j_x,  q_y^eq = 4 (a5 - a1) j_y,  p_xx^eq = p_xy^eq = 0,
+        // and with rho = g_0 + s14 + s58 the g_0 terms cancel:
+        //   e - e^eq = 3 s14 + 6 s58 - (12 w1r + 24 w5r) eta^2 rho,
+        //   eps - eps^eq = (24 w1r + 12 w5r) eta^2 rho - 6 s14 - 3 s58,
+        //   q_x - q_x^eq = -2 X1 + X5 - 4 (a5 - a1) (X1 + X5), with j_x = X1 + X5 (q_y alike).
+        const R A = g[1] + g[3], B = g[2] + g[4], C = g[5] + g[7], D = g[6] + g[8];
+        const R s14 = A + B, s58 = C + D;
+        const R re2 = (g[0] + s14 + s58) * e2;
+        const R w1r = co<R>(a, a.w1r, kCoW1r), w5r = co<R>(a, a.w5r, kCoW5r);
+        const R kq = R(4) * (co<R>(a, a.a5, kCoA5) - co<R>(a, a.a1, kCoA1));
+        const R X1 = g[1] - g[3], Y1 = g[2] - g[4];
+        const R u = g[5] - g[7], v = g[6] - g[8];
+        const R X5 = u - v, Y5 = u + v;
+        // rates arrive divided by the squared row norms: 36, 4, 36, 12, 12, 4
+        const R d3 = co<R>(a, a.s[3], kCoS + 3) *
+                     (R(3) * s14 + R(6) * s58 - (R(12) * w1r + R(24) * w5r) * re2);
+        const R d4 = co<R>(a, a.s[4], kCoS + 4) * (A - B);
+        const R d5 = co<R>(a, a.s[5], kCoS + 5) *
+                     ((R(24) * w1r + R(12) * w5r) * re2 - R(6) * s14 - R(3) * s58);
+        const R d6 = co<R>(a, a.s[6], kCoS + 6) * ((-R(2) - kq) * X1 + (R(1) - kq) * X5);
+        const R d7 = co<R>(a, a.s[7], kCoS + 7) * ((-R(2) - kq) * Y1 + (R(1) - kq) * Y5);
+        const R d8 = co<R>(a, a.s[8], kCoS + 8) * (C - D);
         // g* = g - M^T (d3..d8)
         g[0] -= -R(4) * d3 + R(4) * d5;
         g[1] -= -d3 + d4 - R(2) * d5 - R(2) * d6;

@@ -45,6 +45,11 @@ CASES = [
     (9, "mrt", "f32", True, 96, 96),
     (9, "mrt", "bf16", False, 513, 40),
     (5, "mrt", "f32", False, 1, 70),      # one column: every site on two faces
+    # rows wide enough for warps with no site on a face (the exchange step's interior form:
+    # 128 FP32 / 256 16-bit sites a warp)
+    (9, "bgk", "f32", True, 400, 40),
+    (9, "mrt", "f32", False, 390, 20),
+    (5, "mrt", "bf16", True, 700, 24),
 ]
 
 
