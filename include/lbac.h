@@ -438,7 +438,8 @@ lb_status lb_mode_projection(lb_ctx *ctx, const int *modes, int n_modes, double 
  * info[2] = bytes per stored population value, info[3] = physical time step
  * dt = dx c_s(eta=1) / c_ref (seconds; 0 when dx or c_ref is 0), info[4] = number
  * of distinct speeds when the step reads a 1-byte medium index (host c_map with at
- * most 256 distinct values), 0 when it reads eta^2 per site. */
+ * most 256 distinct values), 0 when it reads eta^2 per site, info[5] = 1 when a step
+ * runs the TMA-staged persistent kernel, else 0.  Fills min(n_info, 6) entries. */
 lb_status lb_info(const lb_ctx *ctx, double *info, int n_info);
 
 const char *lb_last_error(const lb_ctx *ctx);

@@ -155,6 +155,10 @@ float *tape_row(const lb_ctx *ctx, long long t);
 bool tb_supported(int Q, int K);
 // TMA-staged persistent step (stream_step.cu): one LB step of the context's grid
 lb_status stream_launch(lb_ctx *ctx, const lbk::StepArgs &a, int rec_blocks);
+// its in-place form (BF16, D2Q5 / D2Q9): the site-local step, or the exchange step; receivers
+// from the per-row lists of tb5_set_receivers (rec_off nullptr: none this step)
+lb_status stream_launch_aa(lb_ctx *ctx, const lbk::StepArgs &a, bool exchange, const int *rec_off,
+                           const int *rec_x, const int *rec_id);
 lb_status tb_set_receivers(lb_ctx *ctx, const int *xy, int nrec);
 lb_status tb_launch(lb_ctx *ctx, int K);
 lb_status tb_launch_args(lb_ctx *ctx, const lbk::StepArgs &a, int K);

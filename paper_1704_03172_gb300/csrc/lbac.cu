@@ -326,9 +326,10 @@ lb_status validate(const lb_config *cfg) {
         return fail(nullptr, LB_EINVAL, "streaming must be LB_STREAM_AB or LB_STREAM_AA");
     if (cfg->streaming == LB_STREAM_AA &&
         (cfg->lattice == LB_D3Q7 || (cfg->storage != LB_F32 && cfg->storage != LB_BF16) ||
-         cfg->n_patches > 0 || cfg->time_block > 1 || cfg->step_kernel == LB_STEP_STAGED))
+         cfg->n_patches > 0 || cfg->time_block > 1 ||
+         (cfg->step_kernel == LB_STEP_STAGED && cfg->storage != LB_BF16)))
         return fail(nullptr, LB_EINVAL, "LB_STREAM_AA: D2Q5 or D2Q9, FP32 or BF16 storage, no "
-                    "patch, no time blocking, no staged step");
+                    "patch, no time blocking, a staged step with BF16 storage only");
     if (stability_needed(cfg) && !cfg->c_map_on_device) {
         // linear stability at the medium's eta (a device c_map is checked in lb_create, once
         // its range is known): the distinct speeds when there are at most 8, else a spread
@@ -487,7 +488,8 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     // TMA-staged persistent step: forced, or automatic for 16-bit storage on rows of at least
     // 1024 sites (a task is one row segment of 2048 16-bit sites: narrower rows idle most
     // threads, and for FP32 the register-streaming step is faster)
-    c->staged = cfg->n_patches == 0 && !c->aa &&
+    // (in place: BF16 only, the form the staged kernel has)
+    c->staged = cfg->n_patches == 0 && (!c->aa || cfg->storage == LB_BF16) &&
                 (cfg->step_kernel == LB_STEP_STAGED ||
                  (cfg->step_kernel == LB_STEP_AUTO && (cfg->storage == LB_BF16 ||
                                                        cfg->storage == LB_F16) && cfg->nx >= 1024));
@@ -1005,7 +1007,7 @@ lb_status lb_sync(lb_ctx *ctx) {
 
 lb_status lb_info(const lb_ctx *ctx, double *info, int n_info) {
     if (!ctx || !info) return LB_EINVAL;
-    double v[5];
+    double v[6];
     v[0] = ctx->Q;
     v[1] = ctx->pitch;
     v[2] = ctx->ebytes;
@@ -1013,7 +1015,8 @@ lb_status lb_info(const lb_ctx *ctx, double *info, int n_info) {
                                 : std::sqrt(2 * ctx->cfg.w_ref[1] + 4 * ctx->cfg.w_ref[2]);
     v[3] = (ctx->cfg.dx > 0 && ctx->cfg.c_ref > 0) ? ctx->cfg.dx * cs_ref / ctx->cfg.c_ref : 0.0;
     v[4] = ctx->n_mid;
-    for (int k = 0; k < n_info && k < 5; k++) info[k] = v[k];
+    v[5] = ctx->staged ? 1.0 : 0.0;
+    for (int k = 0; k < n_info && k < 6; k++) info[k] = v[k];
     return LB_OK;
 }
 

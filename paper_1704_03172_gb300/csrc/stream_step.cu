@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "aa_sites.cuh"
 #include "lb_kernels.cuh"
 #include "lb_runtime.h"
 
@@ -67,6 +68,7 @@ struct SArgs {
     int stages;        // shared-memory stages per CTA (2 .. kMaxStages)
     int stage_bytes;   // bytes per stage (a multiple of 16)
     unsigned *fault;   // raised when a bounded wait gives up
+    lbaa::AaRec rec;   // in-place forms: receivers by row (their sums are taken in the step)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -134,8 +136,13 @@ __device__ __forceinline__ int source_row(const StepArgs &a, int i, int y, int y
     return pull_row_yz<Q, PERIODIC>(a, y, y3, z3, i);  // y (and, for D3Q7, z) shift of the row
 }
 
+// In-place forms of the step (AA == 1: site-local, 2: exchange; 0: the two-buffer pull).
+// The site-local form stages population i's own row; the exchange form stages slot opp(i)
+// of the row population i pulls from, which holds h_i(t - 1).  Either way stage slot i
+// then holds what g_i(x) is pulled from, as in the two-buffer step.
+//
 // Thread 0: queue the bulk copies of task `task` into `stage`, completing on *bar.
-template <int Q, bool PERIODIC, typename ST>
+template <int Q, bool PERIODIC, typename ST, int AA>
 __device__ void issue_task(const StepArgs &a, const SArgs &s, int task, unsigned char *stage,
                            uint64_t *bar) {
     using G = Geom<ST>;
@@ -150,7 +157,7 @@ __device__ void issue_task(const StepArgs &a, const SArgs &s, int task, unsigned
     row_yz<Q>(a, y, y3, z3);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        ys[i] = source_row<Q, PERIODIC>(a, i, y, y3, z3);
+        ys[i] = AA == 1 ? y : source_row<Q, PERIODIC>(a, i, y, y3, z3);
         if (ys[i] >= 0) total += rowb;
     }
     mbar_expect_tx(bar, total);
@@ -158,7 +165,8 @@ __device__ void issue_task(const StepArgs &a, const SArgs &s, int task, unsigned
 #pragma unroll
     for (int i = 0; i < Q; i++)
         if (ys[i] >= 0)
-            bulk_g2s(stage + i * G::ROWB + dst, in + i * a.plane + (long long)ys[i] * a.pitch + lo,
+            bulk_g2s(stage + i * G::ROWB + dst,
+                     in + (AA == 2 ? Lat<Q>::opp(i) : i) * a.plane + (long long)ys[i] * a.pitch + lo,
                      rowb, bar);
     const long long m0 = (long long)y * a.pitch + xs;
     const void *msrc = a.mid ? static_cast<const void *>(a.mid + m0)
@@ -169,7 +177,7 @@ __device__ void issue_task(const StepArgs &a, const SArgs &s, int task, unsigned
 // All threads: one task from its stage.  Thread t owns sites x0 = xs + t V .. + V - 1;
 // the +-1 x-shifts come from the neighbouring lane (shuffle) or, at lanes 0 / 31, from
 // the staged neighbour element (the 16-byte halo at the task's ends).
-template <int Q, bool MRT, bool PERIODIC, typename ST>
+template <int Q, bool MRT, bool PERIODIC, typename ST, int AA>
 __device__ __forceinline__ void compute_task(const StepArgs &a, const SArgs &s, int task,
                                              const unsigned char *stage, const float *tab,
                                              float tmax[Q]) {
@@ -185,8 +193,9 @@ __device__ __forceinline__ void compute_task(const StepArgs &a, const SArgs &s, 
     row_yz<Q>(a, y, y3, z3);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        const int cx = a.raw ? 0 : Lat<Q>::cx(i);
-        const int ys = source_row<Q, PERIODIC>(a, i, y, y3, z3);
+        const int cx = (AA == 1 || (AA == 0 && a.raw)) ? 0 : Lat<Q>::cx(i);
+        const int ys = AA == 1 ? y : source_row<Q, PERIODIC>(a, i, y, y3, z3);
+        const int pl = AA == 2 ? Lat<Q>::opp(i) : i;  // the plane staged in slot i
         const ST *sp = reinterpret_cast<const ST *>(stage + i * G::ROWB) + G::H + tid * V;
         uint4 q = make_uint4(0u, 0u, 0u, 0u);
         if (ys >= 0 && active) q = *reinterpret_cast<const uint4 *>(sp);
@@ -203,7 +212,7 @@ __device__ __forceinline__ void compute_task(const StepArgs &a, const SArgs &s, 
                 else if (x0 > 0)
                     left = Store<ST>::load1(sp - 1);
                 else
-                    left = PERIODIC ? Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch +
+                    left = PERIODIC ? Store<ST>::load1(in + pl * a.plane + (long long)ys * a.pitch +
                                                        a.nx - 1)
                                     : 0.f;
             }
@@ -219,7 +228,7 @@ __device__ __forceinline__ void compute_task(const StepArgs &a, const SArgs &s, 
             const int last = a.nx - 1 - x0;  // the last real site's image: periodic row[0]
             if (last >= 0 && last < V) {
                 const float b = (PERIODIC && ys >= 0)
-                                    ? Store<ST>::load1(in + i * a.plane + (long long)ys * a.pitch)
+                                    ? Store<ST>::load1(in + pl * a.plane + (long long)ys * a.pitch)
                                     : 0.f;
 #pragma unroll
                 for (int j = 0; j < V; j++)
@@ -227,7 +236,7 @@ __device__ __forceinline__ void compute_task(const StepArgs &a, const SArgs &s, 
             }
         }
     }
-    if (!active) return;  // no shuffles below
+    if (AA != 2 && !active) return;  // no shuffles below (the exchange form's pushes have)
     float e2s[V];
     const unsigned char *mp = stage + Stage<Q, ST>::kPops;
     if (a.mid) {
@@ -249,7 +258,28 @@ __device__ __forceinline__ void compute_task(const StepArgs &a, const SArgs &s, 
             e2s[k] = e.x; e2s[k + 1] = e.y; e2s[k + 2] = e.z; e2s[k + 3] = e.w;
         }
     }
-    finish_sites<Q, MRT, ST>(a, g, e2s, x0, y, tmax);
+    if constexpr (AA == 0) {
+        finish_sites<Q, MRT, ST>(a, g, e2s, x0, y, tmax);
+    } else {  // the receivers' sums, the collision, and the in-place stores
+        if (active) {
+            lbaa::aa_receivers<Q, ST>(a, s.rec, g, y, x0);
+            lbaa::aa_collide<Q, MRT, V>(a, g, e2s, y, x0);
+        }
+        ST *pop = static_cast<ST *>(a.out);  // a.in == a.out
+        if constexpr (AA == 1) {  // h_i(x) into slot opp(i) at x
+#pragma unroll
+            for (int i = 0; i < Q; i++)
+                Store<ST>::storeV(pop + Lat<Q>::opp(i) * a.plane + (long long)y * a.pitch + x0, g[i]);
+        } else if (y > 0 && y + 1 < a.ny && xs > 0 && xs + G::W < a.nx) {
+            // a task with no site on a face and no padding (task-uniform)
+#pragma unroll
+            for (int i = 0; i < Q; i++)
+                lbaa::push_inner<Q, ST>(pop + i * a.plane + (long long)(y + Lat<Q>::cy(i)) * a.pitch,
+                                        i, g[i], x0, lane);
+        } else {  // h_i(x) into slot i at x + c_i, and the ghost's zeros (all lanes)
+            lbaa::exchange_stores<Q, PERIODIC, ST>(a, pop, g, y, x0, lane, active);
+        }
+    }
 }
 
 }  // namespace
@@ -320,7 +350,7 @@ __device__ __forceinline__ void fold_max(const StepArgs &a, const float (&tmax)[
 // Every wait is bounded (one second); whoever gives up raises the context's fault flag (and,
 // with a producer warp, the block's abort flag), the warps leave, and the issuing thread
 // waits (bounded) for the copies still in flight before it returns.
-template <int Q, bool MRT, bool PERIODIC, typename ST>
+template <int Q, bool MRT, bool PERIODIC, typename ST, int AA>
 __global__ void __launch_bounds__((stream_threads<Q, ST>())) __maxnreg__((stream_max_regs<Q, ST>()))
     stream_step_kernel(const StepArgs a, const SArgs s) {
     constexpr bool SC = Scaled<ST>::value;
@@ -367,7 +397,7 @@ __global__ void __launch_bounds__((stream_threads<Q, ST>())) __maxnreg__((stream
                     break;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_task<Q, PERIODIC, ST>(a, s, task, smem + st * SB, &full[st]);
+                issue_task<Q, PERIODIC, ST, AA>(a, s, task, smem + st * SB, &full[st]);
             }
             // the block must not retire with copies landing in its shared memory: wait
             // (bounded) for the last (at most S) issued tasks' copies, which the compute
@@ -388,7 +418,7 @@ __global__ void __launch_bounds__((stream_threads<Q, ST>())) __maxnreg__((stream
                 }
                 return;
             }
-            compute_task<Q, MRT, PERIODIC, ST>(a, s, task, smem + st * SB, s_tab, tmax);
+            compute_task<Q, MRT, PERIODIC, ST, AA>(a, s, task, smem + st * SB, s_tab, tmax);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
         }
@@ -398,7 +428,8 @@ __global__ void __launch_bounds__((stream_threads<Q, ST>())) __maxnreg__((stream
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
             for (int st = 0; st < S; st++) {  // prologue: the first S tasks in flight
                 const int task = (int)blockIdx.x + st * s.ncta;
-                if (task < s.ntasks) issue_task<Q, PERIODIC, ST>(a, s, task, smem + st * SB, &full[st]);
+                if (task < s.ntasks)
+                    issue_task<Q, PERIODIC, ST, AA>(a, s, task, smem + st * SB, &full[st]);
             }
         }
         __syncthreads();
@@ -408,7 +439,7 @@ __global__ void __launch_bounds__((stream_threads<Q, ST>())) __maxnreg__((stream
             const int st = k % S;
             // warp-uniform outcome: compute_task shuffles with all 32 lanes
             const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[st], (unsigned)(k / S) & 1u));
-            if (ok) compute_task<Q, MRT, PERIODIC, ST>(a, s, task, smem + st * SB, s_tab, tmax);
+            if (ok) compute_task<Q, MRT, PERIODIC, ST, AA>(a, s, task, smem + st * SB, s_tab, tmax);
             // every thread is done with stage st (and every wait succeeded) before it is refilled
             if (!__syncthreads_and(ok)) {
                 failed = true;
@@ -418,7 +449,7 @@ __global__ void __launch_bounds__((stream_threads<Q, ST>())) __maxnreg__((stream
                 const int next = task + S * s.ncta;
                 if (next < s.ntasks) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue_task<Q, PERIODIC, ST>(a, s, next, smem + st * SB, &full[st]);
+                    issue_task<Q, PERIODIC, ST, AA>(a, s, next, smem + st * SB, &full[st]);
                 }
             }
         }
@@ -460,9 +491,9 @@ struct SInfo {
     int threads = 0;  // per CTA
 };
 
-template <int Q, bool MRT, bool PER, typename ST> SInfo make_info(bool indexed) {
+template <int Q, bool MRT, bool PER, typename ST, int AA = 0> SInfo make_info(bool indexed) {
     SInfo in;
-    in.fn = stream_step_kernel<Q, MRT, PER, ST>;
+    in.fn = stream_step_kernel<Q, MRT, PER, ST, AA>;
     constexpr int kCtas = stream_min_ctas<Q, ST>();
     in.stage_bytes = Stage<Q, ST>::bytes(indexed);
     in.stages = stages_for(in.stage_bytes, kCtas);
@@ -517,6 +548,30 @@ const SInfo &stream_info(int Q, bool mrt, bool per, int storage, bool ix) {
     return cache[q][m][p][st][ix];
 }
 
+// The in-place forms (BF16 storage, D2Q5 / D2Q9), AA = 1 site-local, 2 exchange.
+template <int AA> SInfo info_aa(int Q, bool mrt, bool per, bool ix) {
+    using B = __nv_bfloat16;
+    if (Q == 9)
+        return mrt ? (per ? make_info<9, true, true, B, AA>(ix) : make_info<9, true, false, B, AA>(ix))
+                   : (per ? make_info<9, false, true, B, AA>(ix)
+                          : make_info<9, false, false, B, AA>(ix));
+    return mrt ? (per ? make_info<5, true, true, B, AA>(ix) : make_info<5, true, false, B, AA>(ix))
+               : (per ? make_info<5, false, true, B, AA>(ix) : make_info<5, false, false, B, AA>(ix));
+}
+
+const SInfo &stream_info_aa(int Q, bool mrt, bool per, bool ix, bool exchange) {
+    static std::mutex mu;
+    static SInfo cache[2][2][2][2][2];
+    static bool ready[2][2][2][2][2] = {};
+    const int q = Q == 9, m = mrt, p = per, x = ix, f = exchange;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready[q][m][p][x][f]) {
+        cache[q][m][p][x][f] = exchange ? info_aa<2>(Q, mrt, per, ix) : info_aa<1>(Q, mrt, per, ix);
+        ready[q][m][p][x][f] = true;
+    }
+    return cache[q][m][p][x][f];
+}
+
 }  // namespace
 
 namespace {
@@ -558,8 +613,32 @@ lb_status stream_launch(lb_ctx *ctx, const StepArgs &a, int rec_blocks) {
     s.stages = in.stages;
     s.stage_bytes = in.stage_bytes;
     s.fault = ctx->fault;
+    s.rec = lbaa::AaRec{nullptr, nullptr, nullptr};
     cudaError_t e = launch_pdl(in.fn, dim3(s.ncta + rec_blocks), dim3(in.threads),
                                (size_t)in.smem, ctx->stream, a, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "TMA-staged step launch");
+    return LB_OK;
+}
+
+lb_status stream_launch_aa(lb_ctx *ctx, const StepArgs &a, bool exchange, const int *rec_off,
+                           const int *rec_x, const int *rec_id) {
+    if (ctx->cfg.storage != LB_BF16 || (ctx->Q != 5 && ctx->Q != 9))
+        return fail(ctx, LB_EINVAL, "TMA-staged in-place step: D2Q5 / D2Q9 with BF16 storage");
+    const SInfo &in = stream_info_aa(ctx->Q, ctx->cfg.collision == LB_MRT,
+                                     ctx->cfg.boundary == LB_PERIODIC, a.mid != nullptr, exchange);
+    if (in.ctas < 1) return fail(ctx, LB_ECUDA, "TMA-staged in-place step: no resident CTA fits");
+    SArgs s;
+    s.tasks_per_row = (ctx->nx + in.W - 1) / in.W;
+    s.ntasks = s.tasks_per_row * ctx->ny;
+    s.ncta = std::min(s.ntasks, in.ctas);
+    s.stages = in.stages;
+    s.stage_bytes = in.stage_bytes;
+    s.fault = ctx->fault;
+    s.rec = lbaa::AaRec{rec_off, rec_x, rec_id};
+    StepArgs b = a;
+    b.raw = 0;  // the form, not the raw flag, says where g(t) is read
+    cudaError_t e = launch_pdl(in.fn, dim3(s.ncta), dim3(in.threads), (size_t)in.smem,
+                               ctx->stream, b, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "TMA-staged in-place step launch");
     return LB_OK;
 }

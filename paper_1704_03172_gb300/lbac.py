@@ -305,8 +305,8 @@ def lb_footprint(cfg: lb_config, nt, nrec, want_adjoint) -> int:
 
 
 def lb_info(ctx):
-    v = (ctypes.c_double * 5)()
-    _check(_lib.lb_info(ctx, v, 5), ctx)
+    v = (ctypes.c_double * 6)()
+    _check(_lib.lb_info(ctx, v, 6), ctx)
     return list(v)
 
 

@@ -50,6 +50,12 @@ CASES = [
     (9, "bgk", "f32", True, 400, 40),
     (9, "mrt", "f32", False, 390, 20),
     (5, "mrt", "bf16", True, 700, 24),
+    # BF16 rows of >= 1024 sites take the TMA-staged kernel in both forms (2048-site tasks;
+    # ragged last tasks)
+    (5, "bgk", "bf16", False, 1100, 40),
+    (5, "mrt", "bf16", True, 2100, 20),
+    (9, "bgk", "bf16", False, 4200, 12),
+    (9, "mrt", "bf16", True, 1024, 16),
 ]
 
 
@@ -86,6 +92,8 @@ def _same(ab, aa):
 def test_in_place_equals_two_buffers_bitwise(mods, Q, coll, storage, periodic, nx, ny):
     LBSim, lbac = mods
     (ab, aa), _, _, _, _ = _pair(LBSim, Q, coll, storage, periodic, nx, ny, nx * 7 + ny)
+    staged = storage == "bf16" and nx >= 1024   # the TMA-staged kernel (info[5]) in both
+    assert aa.info()[5] == ab.info()[5] == (1.0 if staged else 0.0)
     rng = np.random.default_rng(3)
     g0 = (rng.normal(size=(Q, ny, nx)) * 1e-2).astype(np.float32)
     for s in (ab, aa):
