@@ -270,8 +270,8 @@ __device__ __forceinline__ void compute_task(const StepArgs &a, const SArgs &s, 
 #pragma unroll
             for (int i = 0; i < Q; i++)
                 Store<ST>::storeV(pop + Lat<Q>::opp(i) * a.plane + (long long)y * a.pitch + x0, g[i]);
-        } else if (y > 0 && y + 1 < a.ny && xs > 0 && xs + G::W < a.nx) {
-            // a task with no site on a face and no padding (task-uniform)
+        } else if (y > 0 && y + 1 < a.ny && x0 - lane * V > 0 && x0 + (32 - lane) * V < a.nx) {
+            // a warp with no site on a face and no padding (warp-uniform)
 #pragma unroll
             for (int i = 0; i < Q; i++)
                 lbaa::push_inner<Q, ST>(pop + i * a.plane + (long long)(y + Lat<Q>::cy(i)) * a.pitch,
