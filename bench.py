@@ -48,15 +48,15 @@ KERNEL_SOURCES = {
 }
 NCU_TRAFFIC = {
     ("lbk::step_kernel<5,false,false,float>", True):
-        (638.3e6, "7cddfe4a6dae", "profiles/step_kernel_d2q5_f32_4096.md"),
+        (638.4e6, "d248b0751429", "profiles/step_kernel_d2q5_f32_4096.md"),
     ("stream_step_kernel<5,false,false,__nv_bfloat16>", True):
-        (300.2e6, "7389c23bc8d9", "profiles/stream_step_kernel_d2q5_bf16_4096.md"),
+        (300.3e6, "8d3e1f20c888", "profiles/stream_step_kernel_d2q5_bf16_4096.md"),
     ("lbtb5::tb5_kernel<false,4,false,float>", True):
-        (656.3e6, "69235138f170", "profiles/tb5_kernel_d2q5_4096.md"),
+        (656.3e6, "7820e2330eaf", "profiles/tb5_kernel_d2q5_4096.md"),
     ("lbtb5::tb5_kernel<false,4,false,__nv_bfloat16>", True):
-        (314.8e6, "69235138f170", "profiles/tb5_kernel_d2q5_4096.md"),
+        (314.9e6, "7820e2330eaf", "profiles/tb5_kernel_d2q5_4096.md"),
     ("lbtb5::tb5_kernel<false,8,false,float>", True):
-        (672.0e6, "69235138f170", "profiles/tb5_kernel_d2q5_4096.md"),
+        (672.1e6, "7820e2330eaf", "profiles/tb5_kernel_d2q5_4096.md"),
 }
 
 
