@@ -43,14 +43,14 @@ ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 # differently now, reports null.
 KERNEL_SOURCES = {
     "lbk::step_kernel": ("lb_kernels.cuh",),
-    "stream_step_kernel": ("lb_kernels.cuh", "stream_step.cu"),
+    "stream_step_kernel": ("lb_kernels.cuh", "aa_sites.cuh", "stream_step.cu"),
     "lbtb5::tb5_kernel": ("lb_kernels.cuh", "tblock5.cuh"),
 }
 NCU_TRAFFIC = {
     ("lbk::step_kernel<5,false,false,float>", True):
         (638.4e6, "d248b0751429", "profiles/step_kernel_d2q5_f32_4096.md"),
     ("stream_step_kernel<5,false,false,__nv_bfloat16>", True):
-        (300.3e6, "8d3e1f20c888", "profiles/stream_step_kernel_d2q5_bf16_4096.md"),
+        (300.3e6, "8400c20d8d50", "profiles/stream_step_kernel_d2q5_bf16_4096.md"),
     ("lbtb5::tb5_kernel<false,4,false,float>", True):
         (656.3e6, "7820e2330eaf", "profiles/tb5_kernel_d2q5_4096.md"),
     ("lbtb5::tb5_kernel<false,4,false,__nv_bfloat16>", True):

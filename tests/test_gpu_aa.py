@@ -164,6 +164,31 @@ def test_in_place_from_pressure_two_layer(mods):
     np.testing.assert_array_equal(out[1][1], out[0][1])
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_in_place_4096_bench_configuration(mods, storage):
+    # the bench's in-place lines: the 4096^2 two-layer workload with its sponge, source and
+    # receiver line (BF16 on the TMA-staged kernel), both forms of the step, against the
+    # two-buffer step bit for bit
+    LBSim, _ = mods
+    n = 4096
+    c = W.two_layer(n, n, 1.0, 2.0)
+    out = []
+    for streaming in ("ab", "aa"):
+        s = LBSim(c, lattice=5, tau=0.5, sponge_width=40, sponge_sigma_max=0.1,
+                  storage=storage, streaming=streaming)
+        s.set_source(n // 2, n // 4, W.ricker(64, 1.0 / 30))
+        s.set_receivers(W.line_receivers(512, n // 4 + 3, 0, n - 1), 64)
+        s.init_pressure(None)
+        assert s.info()[5] == (1.0 if storage == "bf16" else 0.0)
+        s.step(7)                     # 4 site-local and 3 exchange steps in place
+        out.append((s.traces().cpu().numpy(), s.pressure().cpu().numpy(),
+                    s.state().cpu().numpy()))
+        s.close()
+    for a, b in zip(out[1], out[0]):
+        np.testing.assert_array_equal(a, b)
+    assert np.abs(out[0][0]).max() > 0   # the source reached the receiver line
+
+
 def test_in_place_holds_one_population_buffer(mods):
     import torch
     LBSim, lbac = mods
