@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "lbac.h"
@@ -70,51 +71,149 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 namespace {
 
-// Medium index: when the host map holds at most 256 distinct speeds, map[y][x]
-// (row pitch `pitch`) indexes tab, whose entries are eta^2 formed exactly as
-// medium_kernel forms them (so both forms give bit-identical steps).  Returns
-// false as soon as a 257th value appears.
-bool medium_index(const float *c, int nx, int ny, int pitch, double inv_cref,
-                  std::vector<uint8_t> &map, std::vector<float> &tab) {
-    constexpr unsigned kSlots = 512;  // open addressing, linear probing
+// Host passes over a speed map run on several threads, each over a band of rows; the
+// results are merged in band order, so they do not depend on timing.
+template <class F> void for_row_bands(int nrows, F f) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int T = (int)std::max(1u, std::min({hw, 16u, (unsigned)(nrows / 64 + 1)}));
+    if (T == 1) {
+        f(0, nrows, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 1; t < T; t++)
+        th.emplace_back(f, (int)((long long)nrows * t / T), (int)((long long)nrows * (t + 1) / T), t);
+    f(0, (int)((long long)nrows / T), 0);
+    for (auto &x : th) x.join();
+}
+
+int row_bands(int nrows) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    return (int)std::max(1u, std::min({hw, 16u, (unsigned)(nrows / 64 + 1)}));
+}
+
+// Open-addressed set of at most 256 float bit patterns, with their first-seen order.
+struct SpeedSet {
+    static constexpr unsigned kSlots = 512;  // linear probing
     uint32_t key[kSlots];
     int val[kSlots];
     bool used[kSlots] = {};
-    std::vector<uint32_t> distinct;
-    map.assign((size_t)ny * pitch, 0);
-    uint32_t last = 0;
-    int last_i = -1;
-    for (int y = 0; y < ny; y++) {
-        const float *row = c + (size_t)y * nx;
-        uint8_t *mrow = map.data() + (size_t)y * pitch;
-        for (int x = 0; x < nx; x++) {
-            uint32_t b;
-            memcpy(&b, row + x, 4);
-            if (b != last || last_i < 0) {  // runs of equal speeds skip the table
-                unsigned h = (b * 2654435761u) >> 23;
-                while (used[h] && key[h] != b) h = (h + 1) & (kSlots - 1);
-                if (!used[h]) {
-                    if (distinct.size() == 256) return false;
-                    used[h] = true;
-                    key[h] = b;
-                    val[h] = (int)distinct.size();
-                    distinct.push_back(b);
+    std::vector<uint32_t> order;
+    // index of b, inserting it; -1 once a 257th value would be needed
+    int find_or_add(uint32_t b) {
+        unsigned h = (b * 2654435761u) >> 23;
+        while (used[h] && key[h] != b) h = (h + 1) & (kSlots - 1);
+        if (!used[h]) {
+            if (order.size() == 256) return -1;
+            used[h] = true;
+            key[h] = b;
+            val[h] = (int)order.size();
+            order.push_back(b);
+        }
+        return val[h];
+    }
+    int find(uint32_t b) const {  // b must be present
+        unsigned h = (b * 2654435761u) >> 23;
+        while (key[h] != b) h = (h + 1) & (kSlots - 1);
+        return val[h];
+    }
+};
+
+// Medium index: when the host map holds at most 256 distinct speeds, map[y][x]
+// (row pitch `pitch`) indexes tab, whose entries are eta^2 formed exactly as
+// medium_kernel forms them (so both forms give bit-identical steps).  Returns
+// false when a 257th value appears.  Each band of rows collects its distinct values;
+// the bands' lists are merged in band order, then every band writes its rows' indices.
+bool medium_index(const float *c, int nx, int ny, int pitch, double inv_cref,
+                  std::vector<uint8_t> &map, std::vector<float> &tab) {
+    const int T = row_bands(ny);
+    std::vector<SpeedSet> local(T);
+    std::vector<char> over(T, 0);
+    for_row_bands(ny, [&](int y0, int y1, int t) {
+        SpeedSet &S = local[t];
+        uint32_t last = 0;
+        bool have = false;
+        for (int y = y0; y < y1 && !over[t]; y++) {
+            const float *row = c + (size_t)y * nx;
+            for (int x = 0; x < nx; x++) {
+                uint32_t b;
+                memcpy(&b, row + x, 4);
+                if (have && b == last) continue;  // runs of equal speeds skip the table
+                if (S.find_or_add(b) < 0) {
+                    over[t] = 1;
+                    break;
                 }
                 last = b;
-                last_i = val[h];
+                have = true;
             }
-            mrow[x] = (uint8_t)last_i;
         }
+    });
+    SpeedSet all;
+    for (int t = 0; t < T; t++) {
+        if (over[t]) return false;
+        for (uint32_t b : local[t].order)
+            if (all.find_or_add(b) < 0) return false;
     }
+    map.assign((size_t)ny * pitch, 0);
+    for_row_bands(ny, [&](int y0, int y1, int) {
+        uint32_t last = 0;
+        int last_i = -1;
+        for (int y = y0; y < y1; y++) {
+            const float *row = c + (size_t)y * nx;
+            uint8_t *mrow = map.data() + (size_t)y * pitch;
+            for (int x = 0; x < nx; x++) {
+                uint32_t b;
+                memcpy(&b, row + x, 4);
+                if (last_i < 0 || b != last) {
+                    last = b;
+                    last_i = all.find(b);
+                }
+                mrow[x] = (uint8_t)last_i;
+            }
+        }
+    });
     tab.assign(256, 0.f);
-    for (size_t i = 0; i < distinct.size(); i++) {
+    for (size_t i = 0; i < all.order.size(); i++) {
         float cv;
-        memcpy(&cv, &distinct[i], 4);
+        memcpy(&cv, &all.order[i], 4);
         double eta = (double)cv * inv_cref;
         if (eta > 1.0) eta = 1.0;
         tab[i] = (float)(eta * eta);
     }
     return true;
+}
+
+// min and max over the positive finite speeds of a host map, and its distinct speeds while
+// there are at most 8 (dv holds 9 once there are more)
+void speed_range(const float *c, long long n, int nx, float &mn, float &mx, std::vector<float> &dv) {
+    const int ny = (int)(n / nx);
+    const int T = row_bands(ny);
+    std::vector<float> lmn(T, INFINITY), lmx(T, 0.f);
+    std::vector<std::vector<float>> ldv(T);
+    for_row_bands(ny, [&](int y0, int y1, int t) {
+        float a = INFINITY, b = 0.f, last = -1.f;
+        std::vector<float> &d = ldv[t];
+        for (long long i = (long long)y0 * nx; i < (long long)y1 * nx; i++) {
+            const float v = c[i];
+            if (!(v > 0.f) || !std::isfinite(v)) continue;  // refused later, with the medium
+            a = std::min(a, v);
+            b = std::max(b, v);
+            if (v != last && d.size() <= 8 && std::find(d.begin(), d.end(), v) == d.end())
+                d.push_back(v);
+            last = v;
+        }
+        lmn[t] = a;
+        lmx[t] = b;
+    });
+    mn = INFINITY;
+    mx = 0.f;
+    dv.clear();
+    for (int t = 0; t < T; t++) {
+        mn = std::min(mn, lmn[t]);
+        mx = std::max(mx, lmx[t]);
+        for (float v : ldv[t])
+            if (dv.size() <= 8 && std::find(dv.begin(), dv.end(), v) == dv.end()) dv.push_back(v);
+    }
 }
 
 }  // namespace
@@ -334,17 +433,9 @@ lb_status validate(const lb_config *cfg) {
         // linear stability at the medium's eta (a device c_map is checked in lb_create, once
         // its range is known): the distinct speeds when there are at most 8, else a spread
         const long long n = (long long)cfg->nx * cfg->ny * nz;
-        float mn = INFINITY, mx = 0.f, last = -1.f;
+        float mn, mx;
         std::vector<float> dv;
-        for (long long i = 0; i < n; i++) {
-            const float c = cfg->c_map[i];
-            if (!(c > 0.f) || !std::isfinite(c)) continue;  // refused later, with the medium
-            mn = std::min(mn, c);
-            mx = std::max(mx, c);
-            if (c != last && dv.size() <= 8 && std::find(dv.begin(), dv.end(), c) == dv.end())
-                dv.push_back(c);
-            last = c;
-        }
+        speed_range(cfg->c_map, n, cfg->nx, mn, mx, dv);
         const double cref = cfg->c_ref > 0 ? cfg->c_ref : (double)mx;
         if (mx > 0.f && cref > 0) {
             std::vector<double> de;
@@ -508,8 +599,15 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     double cref = cfg->c_ref;
     if (!cfg->c_map_on_device) {
         if (!(cref > 0)) {
+            std::vector<float> bmx(row_bands(c->ny), 0.f);
+            for_row_bands(c->ny, [&](int y0, int y1, int t) {
+                float m = 0.f;
+                for (long long i = (long long)y0 * c->nx; i < (long long)y1 * c->nx; i++)
+                    m = std::max(m, cfg->c_map[i]);
+                bmx[t] = m;
+            });
             float mx = 0.f;
-            for (long long i = 0; i < (long long)c->nx * c->ny; i++) mx = std::max(mx, cfg->c_map[i]);
+            for (float m : bmx) mx = std::max(mx, m);
             cref = mx;
         }
         staging = static_cast<float *>(dev_alloc(c, (size_t)c->nx * c->ny * 4));
