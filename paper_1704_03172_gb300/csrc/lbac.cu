@@ -71,11 +71,18 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 namespace {
 
-// Host passes over a speed map run on several threads, each over a band of rows; the
-// results are merged in band order, so they do not depend on timing.
-template <class F> void for_row_bands(int nrows, F f) {
+// Host passes over a speed map run on several threads, each over a band of rows: about one
+// thread per million sites, at most 16 (small maps stay on the calling thread, where a
+// thread's start would cost more than the pass).  The results are merged in band order, so
+// they do not depend on timing.
+int row_bands(int nrows, int ncols) {
     const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const int T = (int)std::max(1u, std::min({hw, 16u, (unsigned)(nrows / 64 + 1)}));
+    const long long per = ((long long)nrows * ncols) >> 20;
+    return (int)std::max(1u, std::min({hw, 16u, (unsigned)std::min<long long>(per, nrows / 64) + 1u}));
+}
+
+template <class F> void for_row_bands(int nrows, int ncols, F f) {
+    const int T = row_bands(nrows, ncols);
     if (T == 1) {
         f(0, nrows, 0);
         return;
@@ -85,11 +92,6 @@ template <class F> void for_row_bands(int nrows, F f) {
         th.emplace_back(f, (int)((long long)nrows * t / T), (int)((long long)nrows * (t + 1) / T), t);
     f(0, (int)((long long)nrows / T), 0);
     for (auto &x : th) x.join();
-}
-
-int row_bands(int nrows) {
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    return (int)std::max(1u, std::min({hw, 16u, (unsigned)(nrows / 64 + 1)}));
 }
 
 // Open-addressed set of at most 256 float bit patterns, with their first-seen order.
@@ -126,10 +128,10 @@ struct SpeedSet {
 // the bands' lists are merged in band order, then every band writes its rows' indices.
 bool medium_index(const float *c, int nx, int ny, int pitch, double inv_cref,
                   std::vector<uint8_t> &map, std::vector<float> &tab) {
-    const int T = row_bands(ny);
+    const int T = row_bands(ny, nx);
     std::vector<SpeedSet> local(T);
     std::vector<char> over(T, 0);
-    for_row_bands(ny, [&](int y0, int y1, int t) {
+    for_row_bands(ny, nx, [&](int y0, int y1, int t) {
         SpeedSet &S = local[t];
         uint32_t last = 0;
         bool have = false;
@@ -155,7 +157,7 @@ bool medium_index(const float *c, int nx, int ny, int pitch, double inv_cref,
             if (all.find_or_add(b) < 0) return false;
     }
     map.assign((size_t)ny * pitch, 0);
-    for_row_bands(ny, [&](int y0, int y1, int) {
+    for_row_bands(ny, nx, [&](int y0, int y1, int) {
         uint32_t last = 0;
         int last_i = -1;
         for (int y = y0; y < y1; y++) {
@@ -187,10 +189,10 @@ bool medium_index(const float *c, int nx, int ny, int pitch, double inv_cref,
 // there are at most 8 (dv holds 9 once there are more)
 void speed_range(const float *c, long long n, int nx, float &mn, float &mx, std::vector<float> &dv) {
     const int ny = (int)(n / nx);
-    const int T = row_bands(ny);
+    const int T = row_bands(ny, nx);
     std::vector<float> lmn(T, INFINITY), lmx(T, 0.f);
     std::vector<std::vector<float>> ldv(T);
-    for_row_bands(ny, [&](int y0, int y1, int t) {
+    for_row_bands(ny, nx, [&](int y0, int y1, int t) {
         float a = INFINITY, b = 0.f, last = -1.f;
         std::vector<float> &d = ldv[t];
         for (long long i = (long long)y0 * nx; i < (long long)y1 * nx; i++) {
@@ -599,8 +601,8 @@ lb_status lb_create(const lb_config *cfg, lb_ctx **out) {
     double cref = cfg->c_ref;
     if (!cfg->c_map_on_device) {
         if (!(cref > 0)) {
-            std::vector<float> bmx(row_bands(c->ny), 0.f);
-            for_row_bands(c->ny, [&](int y0, int y1, int t) {
+            std::vector<float> bmx(row_bands(c->ny, c->nx), 0.f);
+            for_row_bands(c->ny, c->nx, [&](int y0, int y1, int t) {
                 float m = 0.f;
                 for (long long i = (long long)y0 * c->nx; i < (long long)y1 * c->nx; i++)
                     m = std::max(m, cfg->c_map[i]);
