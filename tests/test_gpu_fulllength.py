@@ -184,7 +184,7 @@ def test_layered_2048_full_length_every_trace(sim_cls, oracle_mod):
         bound = TOL if storage == "f32" else LOWPREC_LONG[storage]
         try:
             results[storage].update(check_every_trace(tr, tro, bound, own_norm=storage == "f32"))
-        except AssertionError as e:  # every storage form is measured before the verdict
+        except AssertionError as e:  # every storage form is measured before the test fails
             failures.append((storage, str(e)))
         if max(snap) > bound:
             failures.append((storage, "pressure snapshots", snap))
