@@ -142,6 +142,26 @@ def test_create_checks_the_speeds_of_the_medium(lib):
         assert "unstable" not in lib.lb_last_error(None)
 
 
+@pytest.mark.parametrize("nspeeds", [3, 12])
+def test_large_maps_are_scanned_like_small_ones(lib, nspeeds):
+    # a map of millions of sites is scanned on several host threads, band by band; the
+    # speeds it reports to the stability check (the distinct ones up to 8, else the range)
+    # and so the refusal are those of a small map holding the same speeds in the same order
+    s = [1.89, 0.44, 0.44, 0.1, 0.37, 1.77, 1.59, 1.59, 0.48]
+    w = (0.42, 0.139, 0.006)
+    speeds = np.linspace(0.45, 0.8, nspeeds).astype(np.float32)
+    msgs = []
+    for ny, nx in ((2048, 2048), (nspeeds, 8)):
+        c = np.empty((ny, nx), np.float32)
+        for k, band in enumerate(np.array_split(np.arange(ny), nspeeds)):
+            c[band] = speeds[k]               # each speed in its own band of rows
+        with pytest.raises(lib.LBError) as e:
+            lib.lb_create(_cfg_with_map(lib, 9, True, s, w, c))
+        assert e.value.status == lib.LB_EINVAL
+        msgs.append(lib.lb_last_error(None))
+    assert "unstable" in msgs[0] and msgs[0] == msgs[1], msgs
+
+
 def test_bad_arguments(lib):
     cfg = config(lib, 5, False, 0.5, None, (4 / 9, 1 / 9, 1 / 36))
     for eta, level, nk in ((0.0, 0, 16), (1.2, 0, 16), (0.5, -1, 16), (0.5, 0, 1)):
