@@ -94,6 +94,25 @@ def test_d2q5_equilibrium_higher_moments(oracle_mod, eta):
         assert abs(m[4]) < 1e-14
 
 
+@pytest.mark.parametrize("eta,w_ref", [(1.0, (4 / 9, 1 / 9, 1 / 36)), (0.63, (0.4, 0.11, 0.04)),
+                                       (0.31, (0.0, 0.01, 0.24))])
+def test_d2q9_equilibrium_non_conserved_moments(oracle_mod, eta, w_ref):
+    # the closed forms the D2Q9 MRT collision relaxes against (rows 3..8 of App. A's M):
+    # e^eq = -4 rho + 12 w1 rho + 24 w5 rho, eps^eq = 4 rho - 24 w1 rho - 12 w5 rho,
+    # q^eq = 4 (w5 - w1) / c_s^2 j, p_xx^eq = p_xy^eq = 0
+    w, cs2 = oracle_mod.weights(9, eta, w_ref)
+    w1, w5 = w[1], w[5]
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        rho, jx, jy = rng.normal(size=3)
+        m = lbspec.moment_matrix(9) @ oracle_mod.equilibrium(9, w, cs2, rho, jx, jy)
+        np.testing.assert_allclose(m[:3], [rho, jx, jy], atol=1e-14)
+        kq = 4 * (w5 - w1) / cs2
+        np.testing.assert_allclose(
+            m[3:], [(-4 + 12 * w1 + 24 * w5) * rho, 0.0, (4 - 24 * w1 - 12 * w5) * rho,
+                    kq * jx, kq * jy, 0.0], atol=1e-13)
+
+
 @pytest.mark.parametrize("Q", [5, 9])
 def test_equilibrium_map_is_printed_A(oracle_mod, Q):
     # A = I - dg^eq/dg, printed for D2Q5 in Sec. 3.2 (Eq. D2Q5/D2Q9 dist to eqm dist)
