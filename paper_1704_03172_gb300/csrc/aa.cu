@@ -40,32 +40,45 @@ namespace lbaa {
 
 using namespace lbk;
 
-// Receivers, medium and collision of one thread's V sites, as step_kernel does them.
-template <int Q, bool MRT, typename ST>
-__device__ __forceinline__ void collide_site_vector(const StepArgs &a, const AaRec &r,
-                                                    const float *tab,
-                                                    float (&g)[Q][Store<ST>::V], int y, int x0) {
-    constexpr int V = Store<ST>::V;
-    const long long row = (long long)y * a.pitch;
-    float e2s[V];
-    if (a.mid) {  // 1-byte medium index, eta^2 from the shared table
-        const uint8_t *mp = a.mid + row + x0;
-        uint32_t w[V / 4];
+// The medium of a thread's V sites as stored: with a 1-byte medium index its V / 4 words of
+// indices (as float bits), else eta^2 itself.  Loaded together with the populations, so that
+// a warp waits on memory once.
+template <int V>
+__device__ __forceinline__ void medium_load(const StepArgs &a, long long off, float (&raw)[V]) {
+    if (a.mid) {
+        const uint8_t *mp = a.mid + off;
         if (V == 4) {
-            w[0] = *reinterpret_cast<const uint32_t *>(mp);
+            raw[0] = __uint_as_float(*reinterpret_cast<const uint32_t *>(mp));
         } else {
             const uint2 u = *reinterpret_cast<const uint2 *>(mp);
-            w[0] = u.x;
-            w[V / 4 - 1] = u.y;
+            raw[0] = __uint_as_float(u.x);
+            raw[1] = __uint_as_float(u.y);
         }
-#pragma unroll
-        for (int k = 0; k < V; k++) e2s[k] = tab[(w[k >> 2] >> (8 * (k & 3))) & 0xffu];
     } else {
 #pragma unroll
         for (int k = 0; k < V; k += 4) {
-            const float4 v = *reinterpret_cast<const float4 *>(a.eta2 + row + x0 + k);
-            e2s[k] = v.x; e2s[k + 1] = v.y; e2s[k + 2] = v.z; e2s[k + 3] = v.w;
+            const float4 v = *reinterpret_cast<const float4 *>(a.eta2 + off + k);
+            raw[k] = v.x; raw[k + 1] = v.y; raw[k + 2] = v.z; raw[k + 3] = v.w;
         }
+    }
+}
+
+// Receivers, medium and collision of one thread's V sites, as step_kernel does them; raw is
+// the sites' medium from medium_load.
+template <int Q, bool MRT, typename ST>
+__device__ __forceinline__ void collide_site_vector(const StepArgs &a, const AaRec &r,
+                                                    const float *tab,
+                                                    float (&g)[Q][Store<ST>::V], int y, int x0,
+                                                    const float (&raw)[Store<ST>::V]) {
+    constexpr int V = Store<ST>::V;
+    float e2s[V];
+    if (a.mid) {  // eta^2 from the shared table
+#pragma unroll
+        for (int k = 0; k < V; k++)
+            e2s[k] = tab[(__float_as_uint(raw[k >> 2]) >> (8 * (k & 3))) & 0xffu];
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; k++) e2s[k] = raw[k];
     }
     aa_receivers<Q, ST>(a, r, g, y, x0);
     aa_collide<Q, MRT, V>(a, g, e2s, y, x0);
@@ -89,6 +102,8 @@ __device__ __forceinline__ void exchange_inner(const StepArgs &a, const AaRec &r
     auto slot = [&](int s) { return rowp + s * a.plane + Lat<Q>::cy(s) * a.pitch; };
     uint4 q[Q];
     uint32_t e[Q];
+    float med[V];
+    medium_load<V>(a, (long long)y * a.pitch + x0, med);
 #pragma unroll
     for (int i = 0; i < Q; i++) {  // all loads in flight together
         const ST *src = slot(Lat<Q>::opp(i));
@@ -119,7 +134,7 @@ __device__ __forceinline__ void exchange_inner(const StepArgs &a, const AaRec &r
             for (int k = 0; k < V; k++) g[i][k] = f[k];
         }
     }
-    collide_site_vector<Q, MRT, ST>(a, r, tab, g, y, x0);
+    collide_site_vector<Q, MRT, ST>(a, r, tab, g, y, x0, med);
 #pragma unroll
     for (int s = 0; s < Q; s++) push_inner<Q, ST>(slot(s) - x0, s, g[s], x0, lane);
 }
@@ -149,8 +164,10 @@ __global__ void __launch_bounds__(kThreads, (aa_min_ctas<Q, ST, EXCHANGE>()))
     ST *pop = static_cast<ST *>(a.out);  // a.in == a.out
     const long long row = (long long)y * a.pitch;
     float g[Q][V];
+    float med[V];
     if constexpr (!EXCHANGE) {
         if (!active) return;  // no shuffles in this form
+        medium_load<V>(a, row + x0, med);
 #pragma unroll
         for (int i = 0; i < Q; i++) Store<ST>::loadV(pop + i * a.plane + row + x0, g[i]);
     } else {  // g_i(x) = slot opp(i) at x - c_i: the pull of step_kernel from the other slot
@@ -162,6 +179,7 @@ __global__ void __launch_bounds__(kThreads, (aa_min_ctas<Q, ST, EXCHANGE>()))
         uint4 q[Q];
         uint32_t e[Q];
         bool absent[Q];
+        if (active) medium_load<V>(a, row + x0, med);
 #pragma unroll
         for (int i = 0; i < Q; i++) {
             const int rs = row_at<PERIODIC>(y, -Lat<Q>::cy(i), a.ny);
@@ -186,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, (aa_min_ctas<Q, ST, EXCHANGE>()))
         }
     }
     // the exchange step keeps inactive lanes for the shuffles of its pushes
-    if (active) collide_site_vector<Q, MRT, ST>(a, r, tab, g, y, x0);
+    if (active) collide_site_vector<Q, MRT, ST>(a, r, tab, g, y, x0, med);
     if constexpr (!EXCHANGE) {  // h_i(x) into slot opp(i) at x
 #pragma unroll
         for (int i = 0; i < Q; i++) Store<ST>::storeV(pop + Lat<Q>::opp(i) * a.plane + row + x0, g[i]);
