@@ -48,15 +48,15 @@ KERNEL_SOURCES = {
 }
 NCU_TRAFFIC = {
     ("lbk::step_kernel<5,false,false,float>", True):
-        (638.4e6, "d248b0751429", "profiles/step_kernel_d2q5_f32_4096.md"),
+        (638.5e6, "df1c40b8bd02", "profiles/step_kernel_d2q5_f32_4096.md"),
     ("stream_step_kernel<5,false,false,__nv_bfloat16>", True):
-        (300.3e6, "8400c20d8d50", "profiles/stream_step_kernel_d2q5_bf16_4096.md"),
+        (300.3e6, "3a52a69fc363", "profiles/stream_step_kernel_d2q5_bf16_4096.md"),
     ("lbtb5::tb5_kernel<false,4,false,float>", True):
-        (656.3e6, "7820e2330eaf", "profiles/tb5_kernel_d2q5_4096.md"),
+        (656.4e6, "be28d81b9dd6", "profiles/tb5_kernel_d2q5_4096.md"),
     ("lbtb5::tb5_kernel<false,4,false,__nv_bfloat16>", True):
-        (314.9e6, "7820e2330eaf", "profiles/tb5_kernel_d2q5_4096.md"),
+        (314.8e6, "be28d81b9dd6", "profiles/tb5_kernel_d2q5_4096.md"),
     ("lbtb5::tb5_kernel<false,8,false,float>", True):
-        (672.1e6, "7820e2330eaf", "profiles/tb5_kernel_d2q5_4096.md"),
+        (671.9e6, "be28d81b9dd6", "profiles/tb5_kernel_d2q5_4096.md"),
 }
 
 

@@ -911,6 +911,29 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
         else
             pull_issue<0, PERIODIC>(row, x0, lane, a.nx, active, q[i], e[i]);
     }
+    // the medium (index words or eta^2), loaded with the populations so that a warp waits
+    // on memory once (D2Q9 loads it after the pull: its 72 values leave no registers to hold
+    // it across)
+    constexpr bool kMedEarly = Q != 9;
+    float med[V];
+    if (kMedEarly && active) {
+        const long long mo = (long long)y * a.pitch + x0;
+        if (a.mid) {  // warp-uniform: 1-byte medium index
+            if (V == 4) {
+                med[0] = __uint_as_float(*reinterpret_cast<const uint32_t *>(a.mid + mo));
+            } else {
+                const uint2 u = *reinterpret_cast<const uint2 *>(a.mid + mo);
+                med[0] = __uint_as_float(u.x);
+                med[V / 4 - 1] = __uint_as_float(u.y);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k += 4) {
+                const float4 e = *reinterpret_cast<const float4 *>(a.eta2 + mo + k);
+                med[k] = e.x; med[k + 1] = e.y; med[k + 2] = e.z; med[k + 3] = e.w;
+            }
+        }
+    }
     // phase 2: shifts and assembly
     float g[Q][V];
 #pragma unroll
@@ -924,25 +947,32 @@ __device__ __forceinline__ void step_sites(const StepArgs &a, int blk, float tma
             pull_finish<0, PERIODIC, ST>(absent[i], x0, lane, a.nx, q[i], e[i], g[i]);
     }
     if (!active) return;  // no shuffles below
-    float e2s[V];
-    if (a.mid) {  // warp-uniform: 1-byte medium index, eta^2 from the shared table
-        const uint8_t *mp = a.mid + (long long)y * a.pitch + x0;
-        uint32_t w[V / 4];
-        if (V == 4) {
-            w[0] = *reinterpret_cast<const uint32_t *>(mp);
+    if (!kMedEarly) {
+        const long long mo = (long long)y * a.pitch + x0;
+        if (a.mid) {
+            if (V == 4) {
+                med[0] = __uint_as_float(*reinterpret_cast<const uint32_t *>(a.mid + mo));
+            } else {
+                const uint2 u = *reinterpret_cast<const uint2 *>(a.mid + mo);
+                med[0] = __uint_as_float(u.x);
+                med[V / 4 - 1] = __uint_as_float(u.y);
+            }
         } else {
-            const uint2 u = *reinterpret_cast<const uint2 *>(mp);
-            w[0] = u.x;
-            w[V / 4 - 1] = u.y;
-        }
 #pragma unroll
-        for (int k = 0; k < V; k++) e2s[k] = tab[(w[k >> 2] >> (8 * (k & 3))) & 0xffu];
+            for (int k = 0; k < V; k += 4) {
+                const float4 e = *reinterpret_cast<const float4 *>(a.eta2 + mo + k);
+                med[k] = e.x; med[k + 1] = e.y; med[k + 2] = e.z; med[k + 3] = e.w;
+            }
+        }
+    }
+    float e2s[V];
+    if (a.mid) {  // eta^2 from the shared table
+#pragma unroll
+        for (int k = 0; k < V; k++)
+            e2s[k] = tab[(__float_as_uint(med[k >> 2]) >> (8 * (k & 3))) & 0xffu];
     } else {
 #pragma unroll
-        for (int k = 0; k < V; k += 4) {
-            float4 e = *reinterpret_cast<const float4 *>(a.eta2 + (long long)y * a.pitch + x0 + k);
-            e2s[k] = e.x; e2s[k + 1] = e.y; e2s[k + 2] = e.z; e2s[k + 3] = e.w;
-        }
+        for (int k = 0; k < V; k++) e2s[k] = med[k];
     }
     finish_sites<Q, MRT, ST, SLAB, RING>(a, g, e2s, x0, y, tmax);
 }
