@@ -88,9 +88,16 @@ template <class F> void for_row_bands(int nrows, int ncols, F f) {
         return;
     }
     std::vector<std::thread> th;
-    for (int t = 1; t < T; t++)
-        th.emplace_back(f, (int)((long long)nrows * t / T), (int)((long long)nrows * (t + 1) / T), t);
+    int t = 1;
+    try {  // a thread that cannot start leaves its band, and the rest, to the calling thread
+        for (; t < T; t++)
+            th.emplace_back(f, (int)((long long)nrows * t / T),
+                            (int)((long long)nrows * (t + 1) / T), t);
+    } catch (...) {
+    }
     f(0, (int)((long long)nrows / T), 0);
+    for (int u = t; u < T; u++)
+        f((int)((long long)nrows * u / T), (int)((long long)nrows * (u + 1) / T), u);
     for (auto &x : th) x.join();
 }
 
